@@ -1,0 +1,174 @@
+"""FP64 CPU oracle for the smoothed level-set function (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never does, and
+this package never imports the product library: the two share nothing but
+the seeded input arrays produced by ``synth``.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, direct summation over all
+pairs).  This module compiles it with gcc on first use and wraps it with
+ctypes; every wrapper names the paper passage its C function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ST_CONVERGED = 0
+ST_MAXITER = 1
+ST_ZERODERIV = 2
+ST_NONFINITE = 3
+ST_CLAMPED_BIT = 256
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (gcc, OpenMP, no fast-math)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            lib.or_gauss_legendre01.argtypes = [ctypes.c_int, P, P]
+            lib.or_simplex_rule.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
+            lib.or_geometry.argtypes = [I64, P, I64, P, P, P, P, P, P, P]
+            lib.or_sources.argtypes = [I64, P, I64, P, P, P, ctypes.c_int, P, P, P, P, P, P]
+            lib.or_radial.argtypes = [ctypes.c_double, ctypes.c_double, P, P]
+            lib.or_phi_grad.argtypes = [I64, P, P, P, I64, P, P, P, ctypes.c_int]
+            lib.or_chart_nodes.argtypes = [P, I64, P, P, P, ctypes.c_int, P, P, P, P, P]
+            lib.or_solve_charts.argtypes = [I64, P, P, P, I64, P, P, P, ctypes.c_double,
+                                            ctypes.c_int, P, P, P, P, P, ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def gauss_legendre01(n: int):
+    """n-point Gauss-Legendre nodes and weights on [0,1]."""
+    x = np.empty(n)
+    w = np.empty(n)
+    if _load().or_gauss_legendre01(n, _p(x), _p(w)) != 0:
+        raise ValueError("bad n")
+    return x, w
+
+
+def simplex_rule(n: int, subdiv: int = 0):
+    """Duffy-collapsed n x n Gauss-Legendre rule on the standard simplex,
+    composite over ``subdiv`` midpoint splits (Sec. 4.3 and 4.5)."""
+    cnt = n * n * 4 ** subdiv
+    u, v, w = np.empty(cnt), np.empty(cnt), np.empty(cnt)
+    m = _load().or_simplex_rule(n, subdiv, _p(u), _p(v), _p(w))
+    if m != cnt:
+        raise ValueError("bad rule parameters")
+    return u, v, w
+
+
+def geometry(verts, tris, sigma=None):
+    """Per-triangle T_u, T_v, N (eq. tparam), sigma_j, and the vertex
+    pseudonormals H(P) (eq. mkvertexpn)."""
+    verts = _f64(verts)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    nv, m = len(verts), len(tris)
+    tu, tv, nrm = np.empty((m, 3)), np.empty((m, 3)), np.empty((m, 3))
+    sig = np.empty(m)
+    vpn = np.empty((nv, 3))
+    sig_in = _f64(sigma) if sigma is not None else None
+    rc = _load().or_geometry(nv, _p(verts), m, _p(tris),
+                             _p(sig_in) if sig_in is not None else None,
+                             _p(tu), _p(tv), _p(nrm), _p(sig), _p(vpn))
+    if rc != 0:
+        raise ValueError("a vertex has no incident triangle")
+    return dict(tu=tu, tv=tv, nrm=nrm, sigma=sig, vpn=vpn)
+
+
+def sources(verts, tris, sigma=None, n: int = 4, subdiv: int = 0):
+    """Source nodes y, nw = w |N| N_hat and sigma of the discrete sum
+    (eq. discrete_int) for the n x n Duffy rule with ``subdiv`` splits."""
+    verts = _f64(verts)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    geo = geometry(verts, tris, sigma)
+    ru, rv, rw = simplex_rule(n, subdiv)
+    m, nq = len(tris), len(ru)
+    y, nw, sg = np.empty((m * nq, 3)), np.empty((m * nq, 3)), np.empty(m * nq)
+    _load().or_sources(len(verts), _p(verts), m, _p(tris), _p(geo["nrm"]), _p(geo["sigma"]),
+                       nq, _p(ru), _p(rv), _p(rw), _p(y), _p(nw), _p(sg))
+    return y, nw, sg
+
+
+def radial(rho: float, sigma: float):
+    """Radial factors f(rho) and F(rho) = f'(rho)/rho of the pair kernel."""
+    f = ctypes.c_double()
+    F = ctypes.c_double()
+    _load().or_radial(float(rho), float(sigma), ctypes.byref(f), ctypes.byref(F))
+    return f.value, F.value
+
+
+def phi_grad(y, nw, sig, x, nthreads: int = 0):
+    """Phi and grad Phi at targets x by the full direct sum (eq. discrete_int,
+    eq. gradPhi with corrected sign)."""
+    y, nw, sig, x = _f64(y), _f64(nw), _f64(sig), _f64(x)
+    nt = len(x)
+    phi = np.empty(nt)
+    grad = np.empty((nt, 3))
+    _load().or_phi_grad(len(y), _p(y), _p(nw), _p(sig), nt, _p(x), _p(phi), _p(grad), nthreads)
+    return phi, grad
+
+
+def chart_nodes(verts, tris, sigma=None, n: int = 6):
+    """Chart nodes x0 = T^j(u_i,v_i), directions H^j(u_i,v_i) (eq. mkpseudovec)
+    and the triangle's sigma, for the n x n Duffy chart rule."""
+    verts = _f64(verts)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    geo = geometry(verts, tris, sigma)
+    cu, cv, _ = simplex_rule(n, 0)
+    m, npn = len(tris), len(cu)
+    x0, hd, sl = np.empty((m * npn, 3)), np.empty((m * npn, 3)), np.empty(m * npn)
+    _load().or_chart_nodes(_p(verts), m, _p(tris), _p(geo["vpn"]), _p(geo["sigma"]), npn,
+                           _p(cu), _p(cv), _p(x0), _p(hd), _p(sl))
+    return x0, hd, sl
+
+
+def solve_charts(y, nw, sig, x0, hdir, sloc, tol: float = 1e-12, max_iter: int = 20,
+                 nthreads: int = 0):
+    """Newton's method for h at each chart node (eq. newtoneq), h0 = 0."""
+    y, nw, sig = _f64(y), _f64(nw), _f64(sig)
+    x0, hdir, sloc = _f64(x0), _f64(hdir), _f64(sloc)
+    n = len(x0)
+    xo, ho = np.empty((n, 3)), np.empty(n)
+    st, it = np.empty(n, dtype=np.int32), np.empty(n, dtype=np.int32)
+    dh = np.empty(n)
+    _load().or_solve_charts(len(y), _p(y), _p(nw), _p(sig), n, _p(x0), _p(hdir), _p(sloc),
+                            float(tol), int(max_iter), _p(xo), _p(ho), _p(st), _p(it), _p(dh),
+                            nthreads)
+    return dict(x=xo, h=ho, status=st, iters=it, last_dh=dh)

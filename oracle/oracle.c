@@ -1,0 +1,404 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the smoothed level-set function.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load this code.  It shares no source,
+ * header, table or helper with the CUDA library; the two meet only through
+ * the seeded input arrays of the synth/ package.
+ *
+ * Everything here is the plain definition, written for a reader to check
+ * against the paper by eye:
+ *   - triangle chart T^j(u,v) = P1 + u (P2-P1) + v (P3-P1), T_u, T_v,
+ *     N = T_u x T_v                                     (Sec. 3, eq. tparam)
+ *   - vertex pseudonormal H(P) = sum(theta * N_hat) / sum(theta), the
+ *     angle-weighted mean, not renormalised                 (eq. mkvertexpn)
+ *   - pseudonormal field H^j(u,v) by linear interpolation   (eq. mkpseudovec)
+ *   - the discrete boundary sum Phi(x) = sum_{j,k} w_k |N_j| psi(x, T^j(u_k,v_k))
+ *                                                 (eq. discrete_int, kerpsi)
+ *   - grad Phi by differentiating psi in x                   (eq. gradPhi, with
+ *     the sign of the second term corrected; see below)
+ *   - Newton on h: h <- h - (Phi(T + hH) - 1/2) / (H . grad Phi),  h0 = 0
+ *                                                    (eq. newton, newtoneq)
+ *
+ * Notation.  r = y - x (source node minus target), rho = |r|,
+ * a = 1/(sqrt(2) sigma), u = rho a,
+ * g(u) = erf(u) - (2u/sqrt(pi)) exp(-u^2),  f(rho) = g(u) / (4 pi rho^3),
+ * so psi * da = (nw . r) f(rho) with nw = w |N| N_hat  (eq. kerpsi).
+ * Gradient in x: -( nw f + (nw . r) F r ) with F = f'(rho)/rho.  The paper's
+ * eq. gradPhi prints the second term with a plus sign; its sigma -> 0 limit
+ * must be the gradient of the Laplace double layer, -nw/(4 pi rho^3) +
+ * 3 (nw.r) r/(4 pi rho^5), which the minus sign gives.  Its F is the same
+ * function as ours: F = [sqrt(2/pi)(rho/sigma)^3 e^{-u^2} - 3 g] / (4 pi rho^5).
+ *
+ * For small u both f and F are written as power series in u (the paper's
+ * eq. kerpsi_asymp gives the first five terms of f's series; eq.
+ * kerpsi_asymp2 drops the (nw.r) F r term, which we keep).  The series is
+ * used for u < 0.5 and summed until the next term is below 1e-18 of the sum;
+ * the closed forms with libm erf/exp are used otherwise.
+ *
+ * sigma belongs to the source triangle (one sigma_j per skeleton triangle),
+ * so there is no grad-sigma term.  With a constant sigma this is exactly the
+ * paper's Phi (eq. basemodelg).
+ *
+ * Parity: every function here is pinned by the not-gpu tests in
+ * tests/test_oracle_pins.py (closed forms, limits, finite differences,
+ * brute-force volume quadrature), except the positions returned by the
+ * Newton solve on meshes other than a flat face: those are checked only by
+ * Phi(x) = 1/2 re-evaluated, and are marked "parity unpinned" there.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846264338327950288
+
+/* ------------------------------------------------------------------ */
+/* 1-D Gauss-Legendre rule on [0,1] (n points), by Newton's method on the
+ * three-term recurrence of the Legendre polynomials.  Nodes ascending. */
+int or_gauss_legendre01(int n, double* x, double* w)
+{
+    if (n < 1) return -1;
+    for (int i = 0; i < n; i++) {
+        double z = cos(OR_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 200; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-17) break;
+        }
+        {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+        }
+        /* z descends with i; map to [0,1] ascending */
+        x[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Rule on the standard simplex T0 = {u,v >= 0, u+v <= 1}:
+ * the simplex is split `subdiv` times into four midpoint children
+ * (Sec. 4.5), and each (sub)triangle (A,B,C) carries the Duffy-collapsed
+ * n x n Gauss-Legendre rule
+ *     p = A + xi (1-eta) (B-A) + xi eta (C-A),
+ *     weight = w_xi w_eta xi |det(B-A, C-A)|,
+ * collapsed at A.  Child order of (A,B,C) with edge midpoints
+ * mAB, mBC, mCA: (A,mAB,mCA), (mAB,B,mBC), (mCA,mBC,C), (mBC,mCA,mAB).
+ * Node order: subtriangle, then xi, then eta.  Sum of weights = 1/2.
+ * Returns the node count n*n*4^subdiv. */
+int or_simplex_rule(int n, int subdiv, double* u, double* v, double* w)
+{
+    if (n < 1 || subdiv < 0 || subdiv > 6) return -1;
+    int nsub = 1;
+    for (int s = 0; s < subdiv; s++) nsub *= 4;
+    double* tri = (double*)malloc(sizeof(double) * 6 * nsub);
+    double* nxt = (double*)malloc(sizeof(double) * 6 * nsub);
+    tri[0] = 0; tri[1] = 0; tri[2] = 1; tri[3] = 0; tri[4] = 0; tri[5] = 1;
+    int cnt = 1;
+    for (int s = 0; s < subdiv; s++) {
+        for (int t = 0; t < cnt; t++) {
+            double ax = tri[6*t+0], ay = tri[6*t+1];
+            double bx = tri[6*t+2], by = tri[6*t+3];
+            double cx = tri[6*t+4], cy = tri[6*t+5];
+            double abx = 0.5*(ax+bx), aby = 0.5*(ay+by);
+            double bcx = 0.5*(bx+cx), bcy = 0.5*(by+cy);
+            double cax = 0.5*(cx+ax), cay = 0.5*(cy+ay);
+            double kids[4][6] = {
+                {ax, ay, abx, aby, cax, cay},
+                {abx, aby, bx, by, bcx, bcy},
+                {cax, cay, bcx, bcy, cx, cy},
+                {bcx, bcy, cax, cay, abx, aby},
+            };
+            for (int c = 0; c < 4; c++)
+                memcpy(nxt + 6*(4*t + c), kids[c], sizeof(double) * 6);
+        }
+        cnt *= 4;
+        double* tmp = tri; tri = nxt; nxt = tmp;
+    }
+    double* gx = (double*)malloc(sizeof(double) * n);
+    double* gw = (double*)malloc(sizeof(double) * n);
+    or_gauss_legendre01(n, gx, gw);
+    int m = 0;
+    for (int t = 0; t < cnt; t++) {
+        double ax = tri[6*t+0], ay = tri[6*t+1];
+        double e1x = tri[6*t+2] - ax, e1y = tri[6*t+3] - ay;
+        double e2x = tri[6*t+4] - ax, e2y = tri[6*t+5] - ay;
+        double jac = fabs(e1x * e2y - e1y * e2x);
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++) {
+                double s = gx[i] * (1.0 - gx[j]);
+                double q = gx[i] * gx[j];
+                u[m] = ax + s * e1x + q * e2x;
+                v[m] = ay + s * e1y + q * e2y;
+                w[m] = gw[i] * gw[j] * gx[i] * jac;
+                m++;
+            }
+    }
+    free(gx); free(gw); free(tri); free(nxt);
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+static void cross3(const double* a, const double* b, double* c)
+{
+    c[0] = a[1]*b[2] - a[2]*b[1];
+    c[1] = a[2]*b[0] - a[0]*b[2];
+    c[2] = a[0]*b[1] - a[1]*b[0];
+}
+static double dot3(const double* a, const double* b)
+{
+    return a[0]*b[0] + a[1]*b[1] + a[2]*b[2];
+}
+static double norm3(const double* a) { return sqrt(dot3(a, a)); }
+
+/* interior angle at vertex p between edges to q and s */
+static double angle_at(const double* p, const double* q, const double* s)
+{
+    double a[3] = {q[0]-p[0], q[1]-p[1], q[2]-p[2]};
+    double b[3] = {s[0]-p[0], s[1]-p[1], s[2]-p[2]};
+    double c[3];
+    cross3(a, b, c);
+    return atan2(norm3(c), dot3(a, b));
+}
+
+/* Per-triangle geometry (eq. tparam) and vertex pseudonormals
+ * (eq. mkvertexpn).
+ *   verts [nv][3], tris [m][3] (0-based, counter-clockwise seen from outside)
+ *   sigma_in [m] or NULL -> sigma_j = 0.5 sqrt(2 area_j)
+ * Outputs: tu,tv,nrm [m][3] (nrm = T_u x T_v), sigma [m], vpn [nv][3].
+ * Returns 0, or -1 when a vertex has zero total angle. */
+int or_geometry(int64_t nv, const double* verts, int64_t m, const int32_t* tris,
+                const double* sigma_in, double* tu, double* tv, double* nrm,
+                double* sigma, double* vpn)
+{
+    double* asum = (double*)calloc((size_t)nv, sizeof(double));
+    memset(vpn, 0, sizeof(double) * 3 * (size_t)nv);
+    for (int64_t j = 0; j < m; j++) {
+        const double* p1 = verts + 3 * (int64_t)tris[3*j+0];
+        const double* p2 = verts + 3 * (int64_t)tris[3*j+1];
+        const double* p3 = verts + 3 * (int64_t)tris[3*j+2];
+        double a[3], b[3], n[3];
+        for (int k = 0; k < 3; k++) { a[k] = p2[k] - p1[k]; b[k] = p3[k] - p1[k]; }
+        cross3(a, b, n);
+        double nn = norm3(n);
+        for (int k = 0; k < 3; k++) { tu[3*j+k] = a[k]; tv[3*j+k] = b[k]; nrm[3*j+k] = n[k]; }
+        sigma[j] = sigma_in ? sigma_in[j] : 0.5 * sqrt(2.0 * 0.5 * nn);
+        double th[3] = { angle_at(p1, p2, p3), angle_at(p2, p3, p1), angle_at(p3, p1, p2) };
+        for (int c = 0; c < 3; c++) {
+            int64_t vi = tris[3*j+c];
+            asum[vi] += th[c];
+            for (int k = 0; k < 3; k++) vpn[3*vi+k] += th[c] * n[k] / nn;
+        }
+    }
+    int bad = 0;
+    for (int64_t i = 0; i < nv; i++) {
+        if (asum[i] > 0) {
+            for (int k = 0; k < 3; k++) vpn[3*i+k] /= asum[i];
+        } else {
+            bad = 1;
+        }
+    }
+    free(asum);
+    return bad ? -1 : 0;
+}
+
+/* Source nodes of the discrete sum (eq. discrete_int):
+ * y_jk = T^j(u_k, v_k), nw_jk = w_k |N_j| N_hat_j = w_k N_j, sig_jk = sigma_j.
+ * Node order: triangle-major, then rule order.  Outputs [m*nq][3], [m*nq]. */
+void or_sources(int64_t nv, const double* verts, int64_t m, const int32_t* tris,
+                const double* nrm, const double* sigma, int nq,
+                const double* ru, const double* rv, const double* rw,
+                double* y, double* nw, double* sig)
+{
+    (void)nv;
+    for (int64_t j = 0; j < m; j++) {
+        const double* p1 = verts + 3 * (int64_t)tris[3*j+0];
+        const double* p2 = verts + 3 * (int64_t)tris[3*j+1];
+        const double* p3 = verts + 3 * (int64_t)tris[3*j+2];
+        for (int k = 0; k < nq; k++) {
+            int64_t s = j * nq + k;
+            for (int c = 0; c < 3; c++) {
+                y[3*s+c] = p1[c] + ru[k] * (p2[c] - p1[c]) + rv[k] * (p3[c] - p1[c]);
+                nw[3*s+c] = rw[k] * nrm[3*j+c];
+            }
+            sig[s] = sigma[j];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Radial factors of the pair kernel at rho = u / a, a = 1/(sqrt2 sigma):
+ *   f = g(u) / (4 pi rho^3),      F = f'(rho) / rho.
+ * Series form: with h(u) = g(u)/u^3 = (2/sqrt pi) sum_{k>=1} c_k u^{2k-2},
+ * c_k = (-1)^{k+1} 2k / (k! (2k+1)),
+ *   f = h(u) a^3 / (4 pi),   F = (h'(u)/u) a^5 / (4 pi),
+ *   h'(u)/u = (2/sqrt pi) sum_{k>=2} c_k (2k-2) u^{2k-4}. */
+void or_radial(double rho, double sig, double* f_out, double* F_out)
+{
+    const double a = 1.0 / (sqrt(2.0) * sig);
+    const double u = rho * a;
+    const double tsp = 2.0 / sqrt(OR_PI);
+    if (u < 0.5) {
+        double h = 0.0, hp = 0.0;
+        double fact = 1.0;      /* k! */
+        double upow = 1.0;      /* u^{2k-2} */
+        double upow2 = 1.0;     /* u^{2k-4}, for k >= 2 */
+        for (int k = 1; k < 60; k++) {
+            fact *= k;
+            double ck = ((k & 1) ? 1.0 : -1.0) * (2.0 * k) / (fact * (2.0 * k + 1.0));
+            double th = ck * upow;
+            h += th;
+            if (k >= 2) {
+                double tp = ck * (2.0 * k - 2.0) * upow2;
+                hp += tp;
+                upow2 *= u * u;
+                if (fabs(th) < 1e-18 * fabs(h) && fabs(tp) < 1e-18 * fabs(hp)) break;
+            }
+            upow *= u * u;
+        }
+        h *= tsp;
+        hp *= tsp;
+        *f_out = h * a * a * a / (4.0 * OR_PI);
+        *F_out = hp * a * a * a * a * a / (4.0 * OR_PI);
+    } else {
+        double e = exp(-u * u);
+        double g = erf(u) - tsp * u * e;
+        double r3 = rho * rho * rho;
+        double q = rho / sig;
+        *f_out = g / (4.0 * OR_PI * r3);
+        *F_out = (sqrt(2.0 / OR_PI) * q * q * q * e - 3.0 * g) / (4.0 * OR_PI * r3 * rho * rho);
+    }
+}
+
+/* One source node's contribution at target x (eq. kerpsi and gradient). */
+static void or_pair(const double* y, const double* nw, double sig, const double* x,
+                    double* phi, double* gr)
+{
+    double r[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+    double rho = norm3(r);
+    double f, F;
+    or_radial(rho, sig, &f, &F);
+    double d = dot3(nw, r);
+    *phi += d * f;
+    for (int c = 0; c < 3; c++) gr[c] -= nw[c] * f + d * F * r[c];
+}
+
+/* Phi and grad Phi at nt targets by direct summation over all ns source
+ * nodes: full kernel, no cutoff, no far-field approximation.  grad may be
+ * NULL.  nthreads <= 0 uses the OpenMP default. */
+void or_phi_grad(int64_t ns, const double* y, const double* nw, const double* sig,
+                 int64_t nt, const double* x, double* phi, double* grad, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        double p = 0.0, g[3] = {0.0, 0.0, 0.0};
+        for (int64_t s = 0; s < ns; s++)
+            or_pair(y + 3*s, nw + 3*s, sig[s], x + 3*t, &p, g);
+        phi[t] = p;
+        if (grad) { grad[3*t] = g[0]; grad[3*t+1] = g[1]; grad[3*t+2] = g[2]; }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Chart nodes (Sec. 3.2): x0 = T^j(u_i, v_i), H = H^j(u_i, v_i) by linear
+ * interpolation of the vertex pseudonormals (eq. mkpseudovec), sig = sigma_j.
+ * Node order: triangle-major, then rule order. */
+void or_chart_nodes(const double* verts, int64_t m, const int32_t* tris,
+                    const double* vpn, const double* sigma, int np,
+                    const double* cu, const double* cv,
+                    double* x0, double* hdir, double* sloc)
+{
+    for (int64_t j = 0; j < m; j++) {
+        const double* p1 = verts + 3 * (int64_t)tris[3*j+0];
+        const double* p2 = verts + 3 * (int64_t)tris[3*j+1];
+        const double* p3 = verts + 3 * (int64_t)tris[3*j+2];
+        const double* h1 = vpn + 3 * (int64_t)tris[3*j+0];
+        const double* h2 = vpn + 3 * (int64_t)tris[3*j+1];
+        const double* h3 = vpn + 3 * (int64_t)tris[3*j+2];
+        for (int i = 0; i < np; i++) {
+            int64_t s = j * np + i;
+            for (int c = 0; c < 3; c++) {
+                x0[3*s+c] = p1[c] + cu[i] * (p2[c] - p1[c]) + cv[i] * (p3[c] - p1[c]);
+                hdir[3*s+c] = h1[c] + cu[i] * (h2[c] - h1[c]) + cv[i] * (h3[c] - h1[c]);
+            }
+            sloc[s] = sigma[j];
+        }
+    }
+}
+
+/* Status codes of the Newton solve, one per chart node. */
+#define OR_ST_CONVERGED 0
+#define OR_ST_MAXITER 1
+#define OR_ST_ZERODERIV 2
+#define OR_ST_NONFINITE 3
+
+/* Newton's method on h for each chart node (eq. newtoneq), h0 = 0.
+ * Iteration: x = x0 + h H; evaluate Phi, grad Phi by or_phi_grad's direct sum;
+ * stop when |Phi - 1/2| < tol; else h <- h - (Phi - 1/2)/(H . grad Phi), the
+ * step clamped to at most 4 sigma_loc (a clamped step sets bit 8 of the
+ * status).  At most max_iter evaluations.
+ * Outputs: x [n][3], h [n], status [n], iters [n], last |dh| [n]. */
+void or_solve_charts(int64_t ns, const double* y, const double* nw, const double* sig,
+                     int64_t n, const double* x0, const double* hdir, const double* sloc,
+                     double tol, int max_iter, double* xout, double* hout,
+                     int32_t* status, int32_t* iters, double* lastdh, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; i++) {
+        const double* H = hdir + 3*i;
+        double h = 0.0, dh = 0.0;
+        int st = OR_ST_MAXITER, clamped = 0, it = 0;
+        double x[3];
+        for (it = 0; it < max_iter; it++) {
+            for (int c = 0; c < 3; c++) x[c] = x0[3*i+c] + h * H[c];
+            double p = 0.0, g[3] = {0.0, 0.0, 0.0};
+            for (int64_t s = 0; s < ns; s++)
+                or_pair(y + 3*s, nw + 3*s, sig[s], x, &p, g);
+            double res = p - 0.5;
+            if (!isfinite(res)) { st = OR_ST_NONFINITE; it++; break; }
+            if (fabs(res) < tol) { st = OR_ST_CONVERGED; it++; break; }
+            double d = dot3(H, g);
+            if (!isfinite(d)) { st = OR_ST_NONFINITE; it++; break; }
+            if (d == 0.0) { st = OR_ST_ZERODERIV; it++; break; }
+            double step = -res / d;
+            double lim = 4.0 * sloc[i];
+            if (step > lim) { step = lim; clamped = 1; }
+            if (step < -lim) { step = -lim; clamped = 1; }
+            h += step;
+            dh = fabs(step);
+        }
+        for (int c = 0; c < 3; c++) xout[3*i+c] = x0[3*i+c] + h * H[c];
+        hout[i] = h;
+        status[i] = st | (clamped ? 256 : 0);
+        iters[i] = it;
+        lastdh[i] = dh;
+    }
+}

@@ -1,0 +1,358 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, a limit, a library routine, brute-force volume quadrature, finite
+differences, or a value printed in the paper.  A plausible mistake in the
+oracle (a dropped term, a wrong sign, a transposed operand, a wrong weight)
+fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+from scipy.special import erf
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SQ2 = math.sqrt(2.0)
+
+
+def box_phi(x, a, s):
+    """Constant-sigma Gaussian convolution of the box [-a,a]^3 (eq. basemodelg)."""
+    t = 0.5 * (erf((a - x) / (SQ2 * s)) + erf((a + x) / (SQ2 * s)))
+    return np.prod(t, axis=1)
+
+
+def box_grad(x, a, s):
+    t = 0.5 * (erf((a - x) / (SQ2 * s)) + erf((a + x) / (SQ2 * s)))
+    c = 1.0 / (math.sqrt(2.0 * math.pi) * s)
+    dt = c * (np.exp(-(a + x) ** 2 / (2 * s * s)) - np.exp(-(a - x) ** 2 / (2 * s * s)))
+    g = np.empty_like(x)
+    for i in range(3):
+        o = [k for k in range(3) if k != i]
+        g[:, i] = dt[:, i] * t[:, o[0]] * t[:, o[1]]
+    return g
+
+
+# ---------------------------------------------------------------- rules
+def test_gauss_legendre_matches_library(oracle_mod):
+    for n in (1, 2, 3, 4, 6, 8, 12, 16):
+        x, w = oracle_mod.gauss_legendre01(n)
+        z, wz = np.polynomial.legendre.leggauss(n)
+        np.testing.assert_allclose(x, np.sort(0.5 * (z + 1.0)), atol=1e-15)
+        np.testing.assert_allclose(w, 0.5 * wz[np.argsort(z)], atol=1e-15)
+
+
+@pytest.mark.parametrize("n,subdiv", [(1, 0), (3, 0), (4, 1), (6, 0), (5, 2)])
+def test_simplex_rule_exact_on_monomials(oracle_mod, n, subdiv):
+    u, v, w = oracle_mod.simplex_rule(n, subdiv)
+    assert len(u) == n * n * 4 ** subdiv
+    assert np.all(u >= 0) and np.all(v >= 0) and np.all(u + v <= 1 + 1e-15)
+    assert abs(w.sum() - 0.5) < 1e-15
+    # int_{T0} u^a v^b = a! b! / (a+b+2)!, exact for a+b <= 2n-2
+    for a in range(0, 2 * n - 1):
+        for b in range(0, 2 * n - 1 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs((w * u ** a * v ** b).sum() - exact) < 1e-15 * max(1.0, 1.0 / exact) * 10
+
+
+# ---------------------------------------------------------------- kernel
+def _golden_series():
+    num, den = [], []
+    with open(os.path.join(GOLDEN, "kerpsi_series.txt")) as fh:
+        for ln in fh:
+            ln = ln.strip()
+            if not ln or ln.startswith("#"):
+                continue
+            a, b = ln.split()
+            if a in ("accuracy", "umax"):
+                continue
+            num.append(float(a))
+            den.append(float(b))
+    return np.array(num) / np.array(den)
+
+
+def test_small_u_series_matches_paper_coefficients(oracle_mod):
+    """eq. kerpsi_asymp: f = (2/3 - 2u^2/5 + u^4/7 - u^6/27 + u^8/132) / (4 sqrt(2 pi^3) sigma^3)
+    to about 1e-13 relative for u < 0.1."""
+    c = _golden_series()
+    sig = 0.37
+    for u in np.linspace(0.0, 0.1, 23):
+        rho = u * SQ2 * sig
+        f, _ = oracle_mod.radial(rho, sig)
+        p = sum(c[k] * u ** (2 * k) for k in range(5))
+        ref = p / (4.0 * math.sqrt(2.0 * math.pi ** 3) * sig ** 3)
+        assert abs(f - ref) <= 3e-13 * abs(ref)
+
+
+def test_series_and_closed_form_agree_on_overlap(oracle_mod):
+    """The oracle switches from series to closed form at u = 0.5; compare each
+    side with the closed forms evaluated here with scipy's erf (P8)."""
+    sig = 0.05
+    for u in np.linspace(0.3, 0.75, 40):
+        rho = u * SQ2 * sig
+        f, F = oracle_mod.radial(rho, sig)
+        g = erf(u) - 2.0 * u / math.sqrt(math.pi) * math.exp(-u * u)
+        f_ref = g / (4 * math.pi * rho ** 3)
+        F_ref = (math.sqrt(2 / math.pi) * (rho / sig) ** 3 * math.exp(-u * u) - 3 * g) / (4 * math.pi * rho ** 5)
+        assert abs(f - f_ref) <= 1e-13 * abs(f_ref)
+        assert abs(F - F_ref) <= 1e-11 * abs(F_ref)
+
+
+def test_radial_derivative_is_consistent(oracle_mod):
+    """F = f'(rho)/rho, by Richardson-extrapolated central differences of f."""
+    sig = 0.2
+    for u in (0.05, 0.2, 0.45, 0.55, 1.0, 2.5, 6.0):
+        rho = u * SQ2 * sig
+        h = 1e-3 * rho
+        d1 = (oracle_mod.radial(rho + h, sig)[0] - oracle_mod.radial(rho - h, sig)[0]) / (2 * h)
+        d2 = (oracle_mod.radial(rho + h / 2, sig)[0] - oracle_mod.radial(rho - h / 2, sig)[0]) / h
+        d = (4 * d2 - d1) / 3
+        F = oracle_mod.radial(rho, sig)[1]
+        assert abs(d / rho - F) <= 1e-8 * abs(F)
+
+
+def test_laplace_limit_beyond_8_sigma(oracle_mod):
+    """Sec. 4.4: beyond 8 sigma the kernel is the Laplace double layer
+    (eq. kerapprox) to near double precision.  The neglected relative part is
+    erfc(u) + (2u/sqrt pi) e^{-u^2}, below 1e-13 at 8 sigma."""
+    txt = open(os.path.join(GOLDEN, "cutoff_8sigma.txt")).read().split()
+    eb = float(txt[txt.index("erf_bound") + 1])
+    xb = float(txt[txt.index("exp_bound") + 1])
+    assert 1 - erf(8 / SQ2) <= eb and math.exp(-32) <= xb
+    sig = 0.01
+    for c in (8.0, 9.0, 12.0, 40.0):
+        rho = c * sig
+        f, F = oracle_mod.radial(rho, sig)
+        tail = math.erfc(c / SQ2) + c * math.sqrt(2 / math.pi) * math.exp(-c * c / 2)
+        assert abs(f * 4 * math.pi * rho ** 3 - 1.0) <= tail + 1e-15
+        assert tail < 1e-13
+        # the gradient's radial factor keeps a (rho/sigma)^3 e^{-u^2} term: at
+        # 8 sigma it is still 5e-12 relative, which bounds the FP64 cutoff error
+        ftail = 3 * tail + math.sqrt(2 / math.pi) * c ** 3 * math.exp(-c * c / 2)
+        assert abs(F * 4 * math.pi * rho ** 5 + 3.0) <= ftail + 1e-14
+
+
+# ---------------------------------------------------------------- Phi
+@pytest.fixture(scope="module")
+def c1_fine(oracle_mod):
+    w = synth.cube_c1(400)
+    m = w["mesh"]
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 8, 2)
+    phi, gr = oracle_mod.phi_grad(y, nw, sg, w["targets"])
+    return w, phi, gr
+
+
+def test_box_closed_form_phi_and_grad(c1_fine):
+    """P1: the cube's discrete sum converges to the separable erf product
+    (eq. basemodelg with V = [-1,1]^3, sigma = 0.1) and its gradient."""
+    w, phi, gr = c1_fine
+    x = w["targets"]
+    assert np.abs(phi - box_phi(x, 1.0, 0.1)).max() < 1e-12
+    assert np.abs(gr - box_grad(x, 1.0, 0.1)).max() < 1e-11
+
+
+def test_box_spectral_convergence(oracle_mod):
+    """P1, convergence: the C1 rule (4x4 on 4 children) is accurate to about
+    1e-5; refining the rule drives the error toward rounding."""
+    w = synth.cube_c1(300)
+    m, x = w["mesh"], w["targets"]
+    ex = box_phi(x, 1.0, 0.1)
+    errs = []
+    for n, sd in ((4, 1), (6, 1), (8, 1), (8, 2)):
+        y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, n, sd)
+        phi, _ = oracle_mod.phi_grad(y, nw, sg, x)
+        errs.append(np.abs(phi - ex).max())
+    assert errs[0] < 5e-5
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[3] < 1e-12
+
+
+def _solid_angle(x, verts, tris):
+    """Van Oosterom-Strackee signed solid angle of each triangle seen from x."""
+    a = verts[tris[:, 0]] - x
+    b = verts[tris[:, 1]] - x
+    c = verts[tris[:, 2]] - x
+    la, lb, lc = (np.linalg.norm(v, axis=1) for v in (a, b, c))
+    num = np.einsum("ij,ij->i", a, np.cross(b, c))
+    den = la * lb * lc + np.einsum("ij,ij->i", a, b) * lc + np.einsum("ij,ij->i", a, c) * lb \
+        + np.einsum("ij,ij->i", b, c) * la
+    return 2.0 * np.arctan2(num, den)
+
+
+def test_sigma_to_zero_is_solid_angle(oracle_mod):
+    """P2: as sigma -> 0, Phi off the surface is sum(solid angle)/(4 pi):
+    1 inside, 0 outside (Sec. 5, Gauss flux).  Per-triangle sigma varies."""
+    g = synth.rng(11)
+    m = synth.icosphere(1)
+    sig = g.uniform(5e-4, 2e-3, m.m)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, sig, 10, 3)
+    x = np.concatenate([g.uniform(-0.5, 0.5, (6, 3)), g.normal(size=(6, 3))])
+    x[6:] *= (1.6 / np.linalg.norm(x[6:], axis=1))[:, None]
+    phi, _ = oracle_mod.phi_grad(y, nw, sg, x)
+    ref = np.array([_solid_angle(p, m.verts, m.tris).sum() / (4 * math.pi) for p in x])
+    np.testing.assert_allclose(ref[:6], 1.0, atol=1e-12)
+    np.testing.assert_allclose(ref[6:], 0.0, atol=1e-12)
+    assert np.abs(phi - ref).max() < 1e-9
+
+
+def _tet_volume_rule(P, n):
+    """Tensor Gauss-Legendre rule on a tetrahedron by collapsing the unit cube."""
+    z, wz = np.polynomial.legendre.leggauss(n)
+    t, wt = 0.5 * (z + 1), 0.5 * wz
+    A, B, C = np.meshgrid(t, t, t, indexing="ij")
+    W = (wt[:, None, None] * wt[None, :, None] * wt[None, None, :])
+    s1 = A
+    s2 = A * B
+    s3 = A * B * C
+    jac = A * A * B
+    bary1 = s1 - s2
+    bary2 = s2 - s3
+    bary3 = s3
+    pts = (P[0][None, :] + bary1.ravel()[:, None] * (P[1] - P[0]) + bary2.ravel()[:, None] * (P[2] - P[0])
+           + bary3.ravel()[:, None] * (P[3] - P[0]))
+    vol6 = abs(np.linalg.det(np.stack([P[1] - P[0], P[2] - P[0], P[3] - P[0]])))
+    return pts, (W * jac).ravel() * vol6
+
+
+def test_tetrahedron_volume_quadrature(oracle_mod):
+    """P5: the boundary form (eq. surf) equals brute-force volume quadrature of
+    the Gaussian convolution (eq. basemodelg) on a tetrahedron, for Phi and
+    grad Phi (grad G = -(x - x') G / sigma^2)."""
+    P = np.array([[0.0, 0.0, 0.0], [1.0, 0.1, 0.0], [0.2, 0.9, 0.1], [0.3, 0.2, 0.8]])
+    tris = np.array([[0, 2, 1], [0, 1, 3], [1, 2, 3], [0, 3, 2]], dtype=np.int32)
+    s = 0.25
+    y, nw, sg = oracle_mod.sources(P, tris, np.full(4, s), 14, 2)
+    x = np.array([[0.35, 0.3, 0.25], [0.0, 0.0, 0.0], [0.9, 0.9, 0.9], [-0.3, 0.5, 0.2],
+                  [0.5, 0.05, 0.0]])
+    phi, gr = oracle_mod.phi_grad(y, nw, sg, x)
+    pts, wv = _tet_volume_rule(P, 40)
+    for i, xi in enumerate(x):
+        d = xi[None, :] - pts
+        G = np.exp(-(d ** 2).sum(1) / (2 * s * s)) / (2 * math.pi * s * s) ** 1.5
+        assert abs((wv * G).sum() - phi[i]) < 1e-11
+        gref = -(wv[:, None] * d * G[:, None]).sum(0) / (s * s)
+        assert np.abs(gref - gr[i]).max() < 1e-10
+
+
+def _ball_phi(rho, R, s):
+    rho = np.asarray(rho, dtype=np.float64)
+    out = np.empty_like(rho)
+    z = rho < 1e-8
+    r = rho[~z]
+    out[~z] = 0.5 * (erf((R - r) / (SQ2 * s)) + erf((R + r) / (SQ2 * s))) + \
+        s / (r * math.sqrt(2 * math.pi)) * (np.exp(-(R + r) ** 2 / (2 * s * s)) - np.exp(-(R - r) ** 2 / (2 * s * s)))
+    out[z] = erf(R / (SQ2 * s)) - math.sqrt(2 / math.pi) * (R / s) * math.exp(-R * R / (2 * s * s))
+    return out
+
+
+def test_ball_closed_form_on_icosphere(oracle_mod):
+    """P4 (approximate): a fine icosphere with constant sigma approaches the
+    Gaussian convolution of the unit ball, up to the O(h^2) geometric error."""
+    s = 0.15
+    rr = np.array([0.4, 0.8, 0.95, 1.0, 1.05, 1.3])
+    x = np.stack([rr / math.sqrt(3)] * 3, axis=1)
+    errs = []
+    for level in (3, 4, 5):
+        m = synth.icosphere(level)
+        y, nw, sg = oracle_mod.sources(m.verts, m.tris, np.full(m.m, s), 3, 0)
+        phi, _ = oracle_mod.phi_grad(y, nw, sg, x)
+        errs.append(np.abs(phi - _ball_phi(rr, 1.0, s)).max())
+    # each level halves the edge: the inscribed polyhedron's error drops ~4x
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+    assert errs[2] < 6e-4
+
+
+def test_limits_deep_inside_and_far_outside(oracle_mod):
+    """P6: Phi -> 1 deep inside, -> 0 far outside; Laplace limit far away."""
+    m = synth.cube(1.0, 3)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, np.full(m.m, 0.05), 8, 1)
+    phi, gr = oracle_mod.phi_grad(y, nw, sg, np.array([[0.0, 0.0, 0.0], [0.2, -0.1, 0.3],
+                                                       [30.0, 0.0, 0.0], [0, -25.0, 10.0]]))
+    assert abs(phi[0] - 1) < 1e-13 and abs(phi[1] - 1) < 1e-13
+    assert abs(phi[2]) < 1e-12 and abs(phi[3]) < 1e-12
+    assert np.abs(gr).max() < 1e-10
+
+
+def test_gradient_by_finite_differences(oracle_mod):
+    """P7: grad Phi against Richardson-extrapolated central differences of Phi,
+    on a jittered graded torus with per-triangle sigma (pins the sign of the
+    second term of eq. gradPhi for variable sigma)."""
+    m = synth.torus(1.0, 0.3, 24, 8, 5.0, 0.05, seed=7)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 3, 0)
+    g = synth.rng(12)
+    x = synth.targets_near_surface(m, 12, g, 2.0)
+    _, gr = oracle_mod.phi_grad(y, nw, sg, x)
+    h = 2e-4
+    fd = np.empty_like(gr)
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = 1.0
+        d1 = (oracle_mod.phi_grad(y, nw, sg, x + h * e)[0] - oracle_mod.phi_grad(y, nw, sg, x - h * e)[0]) / (2 * h)
+        d2 = (oracle_mod.phi_grad(y, nw, sg, x + h / 2 * e)[0] - oracle_mod.phi_grad(y, nw, sg, x - h / 2 * e)[0]) / h
+        fd[:, i] = (4 * d2 - d1) / 3
+    assert np.abs(fd - gr).max() < 1e-7 * np.abs(gr).max()
+
+
+# ---------------------------------------------------------------- geometry
+def test_sigma_rule_and_pseudonormals(oracle_mod):
+    """Default sigma rule (0.5 sqrt(2 area)); pseudonormals (eq. mkvertexpn) of
+    a cube: n_hat at face-interior vertices, (n1+n2+n3)/3 at corners (each face
+    contributes a total angle pi/2), (n1+n2)/2 on edges."""
+    m = synth.cube(1.0, 4)
+    geo = oracle_mod.geometry(m.verts, m.tris, None)
+    np.testing.assert_allclose(geo["sigma"], synth.sigma_half_sqrt2area(m.verts, m.tris), rtol=1e-15)
+    v = m.verts
+    nb = (np.abs(np.abs(v) - 1.0) < 1e-12).sum(1)
+    for i in range(len(v)):
+        n = np.where(np.abs(np.abs(v[i]) - 1.0) < 1e-12, np.sign(v[i]), 0.0)
+        np.testing.assert_allclose(geo["vpn"][i], n / nb[i], atol=1e-15)
+
+
+def test_chart_nodes_on_flat_face_match_closed_form_root(oracle_mod):
+    """P3: on triangles interior to a cube face H = n_hat, so Newton's root
+    h solves Phi_box(x0 + h n_hat) = 1/2 (a 1-D root of the erf product); the
+    oracle's h agrees with brentq on the closed form to quadrature error."""
+    m = synth.cube(1.0, 4)
+    s = 0.1
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, np.full(m.m, s), 8, 2)
+    x0, hd, sl = oracle_mod.chart_nodes(m.verts, m.tris, np.full(m.m, s), 3)
+    v = m.verts
+    inner = np.all(np.abs(v) < 1 - 1e-9, axis=1) | (np.sum(np.abs(np.abs(v) - 1) < 1e-9, axis=1) == 1)
+    tri_ok = np.all(inner[m.tris], axis=1)
+    sel = np.repeat(tri_ok, 9)
+    x0, hd, sl = x0[sel][:40], hd[sel][:40], sl[sel][:40]
+    out = oracle_mod.solve_charts(y, nw, sg, x0, hd, sl, tol=1e-13, max_iter=20)
+    assert np.all(out["status"] == oracle_mod.ST_CONVERGED)
+    for i in range(len(x0)):
+        n = hd[i]
+        assert abs(np.linalg.norm(n) - 1) < 1e-14
+        root = brentq(lambda h: box_phi((x0[i] + h * n)[None, :], 1.0, s)[0] - 0.5, -0.3, 0.3, xtol=1e-16)
+        assert abs(out["h"][i] - root) < 1e-12
+
+
+def test_newton_reaches_half_level_on_torus(oracle_mod):
+    """Chart positions on a curved mesh: parity unpinned beyond Phi(x) = 1/2,
+    which is re-evaluated here by the direct sum."""
+    m = synth.torus(1.0, 0.3, 24, 8, 5.0, 0.05, seed=9)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 3, 0)
+    x0, hd, sl = oracle_mod.chart_nodes(m.verts, m.tris, m.sigma, 2)
+    out = oracle_mod.solve_charts(y, nw, sg, x0[:64], hd[:64], sl[:64], tol=1e-12)
+    assert np.all(out["status"] == 0)
+    phi, _ = oracle_mod.phi_grad(y, nw, sg, out["x"])
+    assert np.abs(phi - 0.5).max() < 1e-12
+    assert np.all(out["iters"] <= 8)
+
+
+def test_newton_reports_nonconvergence(oracle_mod):
+    """A capped solve reports MAXITER per node instead of failing (the paper's
+    failure mode, Sec. 5, must be reported, not crash)."""
+    m = synth.cube(1.0, 2)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, np.full(m.m, 0.2), 3, 0)
+    x0, hd, sl = oracle_mod.chart_nodes(m.verts, m.tris, np.full(m.m, 0.2), 2)
+    out = oracle_mod.solve_charts(y, nw, sg, x0, hd, sl, tol=1e-14, max_iter=1)
+    assert np.all((out["status"] & 255) == oracle_mod.ST_MAXITER)
+    assert np.all(out["iters"] == 1)
