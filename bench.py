@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Benchmark: Phi + grad Phi evaluations and the batched Newton chart solve
+on the graded-torus workload (30,720 triangles, Duffy 6x6 sources =
+1,105,920 nodes, 1e6 targets within 3 sigma, order-8 charts = 1,105,920
+chart nodes), one GB300.
+
+A step = one Phi/grad-Phi evaluation at the 1e6 targets + one chart solve
+(all Newton sweeps).  value = target evaluations per second over the step
+(the targets plus every active chart node of every sweep), with inputs
+resident on the device.  e2e = the same through the C ABI with host buffers
+(pinned), the copies inside the timed region.  The dominant kernel's
+roofline is measured live with CUDA events recorded by the library on its
+launch stream.  The CPU baseline is the FP64 oracle on a bounded target
+sample on this host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 SMSPs x 32)
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+FLOPS_FAR_PAIR = 31              # Laplace double layer, Phi + grad (1 rsqrt not counted)
+FLOPS_NEAR_PAIR = 60             # full smoothed kernel, Phi + grad (erfc, exp, rsqrt not counted)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--targets", type=int, default=1_000_000)
+    ap.add_argument("--order", type=int, default=8)
+    ap.add_argument("--small", action="store_true", help="small torus (quick check)")
+    ap.add_argument("--no-charts", action="store_true", help="time the evaluation only")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    import synth
+    if args.small:
+        w = synth.torus_c2(n_targets=min(args.targets, 50_000), nu=60, nv=16)
+    else:
+        w = synth.torus_c2(n_targets=args.targets)
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, seconds: float, rule_n: int):
+    """The FP64 oracle (direct sum, all pairs) on a target sample, all host cores."""
+    import oracle
+    m = w["mesh"]
+    y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, rule_n, 0)
+    x = w["targets"]
+    t0 = time.perf_counter()
+    oracle.phi_grad(y, nw, sg, x[:8])
+    dt = time.perf_counter() - t0
+    n = int(max(8, min(len(x), 8 * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.phi_grad(y, nw, sg, x[:n])
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} of {len(x)} targets, full FP64 direct sum over {len(y)} source nodes "
+                      f"({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step evaluates a bounded sample."""
+    if rank != 0:
+        return
+    w = workload(args)
+    import oracle
+    m = w["mesh"]
+    y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, w["rule"]["n"], 0)
+    x = w["targets"]
+    t0 = time.perf_counter()
+    oracle.phi_grad(y, nw, sg, x[:8])
+    per = (time.perf_counter() - t0) / 8
+    n = int(max(8, min(2000, 20.0 / max(per, 1e-9) / max(1, args.steps + args.warmup))))
+    for _ in range(args.warmup):
+        oracle.phi_grad(y, nw, sg, x[:n])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.phi_grad(y, nw, sg, x[:n])
+    dt = time.perf_counter() - t0
+    val = n * args.steps / dt
+    cb = {"value": val, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"{n} targets per step of {len(x)}, FP64 direct sum over {len(y)} nodes"}
+    print(json.dumps({
+        "impl": "reference", "metric": "phi_grad_evals_per_s", "value": val, "unit": "evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "targets": len(x), "sources": len(y), "sample_targets": n},
+        "cpu_baseline": cb,
+        "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1909_13356_gb300 as lsm
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = lsm.MIXED if args.precision == "mixed" else lsm.FP64
+
+    w = workload(args)
+    m = w["mesh"]
+    ctx = lsm.Context(local)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
+    info = mesh.info()
+    x_dev = torch.from_numpy(w["targets"]).to(dev)
+    nt = x_dev.shape[0]
+    phi = torch.empty(nt, dtype=torch.float64, device=dev)
+    grad = torch.empty((nt, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        mesh.eval_phi_grad(x_dev, prec, phi=phi, grad=grad)
+        if args.no_charts:
+            return nt, None
+        _, _, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=prec, device_out=True)
+        return nt + sum(st.active_per_iter), st
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    ctx.read_stats(reset=True)
+    ctx.set_profiling(True)
+    launches0 = ctx.launch_count
+    clk = ClockSampler(local)
+    clk.start()
+    total_units = 0
+    step_ms = []
+    last_stats = None
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        units, last_stats = step()
+        b.record()
+        torch.cuda.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        total_units += units
+    barrier()
+    clocks = clk.stop()
+    ctx.set_profiling(False)
+    stats = ctx.read_stats(reset=True)
+    launches = ctx.launch_count - launches0
+    t_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        u = torch.tensor([float(total_units)], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_units = int(u.item())
+    value = total_units / (t_ms / 1e3)
+
+    # dominant kernel: the pair kernel, timed per launch by the library
+    flops = stats["pairs_far"] * FLOPS_FAR_PAIR + stats["pairs_near"] * FLOPS_NEAR_PAIR
+    kern_ms = stats["pair_kernel_ms"]
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if prec == lsm.FP64:
+        peak = peak / 64.0
+    achieved = flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "k_eval_mixed" if prec == lsm.MIXED else "k_eval_fp64",
+                "launches": stats["pair_kernel_launches"],
+                "avg_launch_ms": kern_ms / max(1, stats["pair_kernel_launches"]),
+                "pairs_far": stats["pairs_far"], "pairs_near": stats["pairs_near"],
+                "share_of_step": kern_ms / sum(step_ms) if step_ms else None,
+                "peak_source": "FP32 FMA lanes 152 SM x 128 x 2 flops x 2070 MHz"
+                               + (" / 64 (FP64 rate)" if prec == lsm.FP64 else "")}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        xh = torch.from_numpy(w["targets"]).pin_memory()
+        ph = torch.empty(nt, dtype=torch.float64).pin_memory()
+        gh = torch.empty((nt, 3), dtype=torch.float64).pin_memory()
+        units = 0
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ncn = 0
+        for _ in range(e2e_steps):
+            mesh.eval_phi_grad(xh, prec, phi=ph, grad=gh)
+            units += nt
+            if not args.no_charts:
+                _, _, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=prec)
+                units += sum(st.active_per_iter)
+                ncn = st.n_nodes
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": nt * 24,
+               "d2h_bytes_per_step": nt * 32 + ncn * (24 + 8 + 4), "steps": e2e_steps}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(w, args.cpu_seconds, w["rule"]["n"])
+
+    if rank == 0:
+        st = last_stats
+        out = {
+            "metric": "phi_grad_evals_per_s",
+            "value": value,
+            "unit": "evals/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64" if prec == lsm.MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "triangles": m.m, "sources": info["n_sources"],
+                       "targets": nt, "chart_order": args.order, "chart_nodes": st.n_nodes if st else 0,
+                       "newton_tol": args.tol, "precision": args.precision,
+                       "l2": "flushed (256 MB write) before each timed step"},
+            "chart_nodes_per_s": st.n_converged / (t_ms / args.steps / 1e3) if st else None,
+            "newton": {"iterations": st.iterations, "active_per_iter": st.active_per_iter,
+                       "n_failed": st.n_failed, "eps_newton": st.eps_newton,
+                       "max_residual": st.max_residual, "evals_fp64": st.evals_fp64} if st else None,
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * lsm.h -- C ABI of the GB300 level-set mesher library (liblsm.so).
+ *
+ * The library evaluates the Gaussian-smoothed indicator function Phi of a
+ * closed triangulated solid, and its gradient, at batches of target points,
+ * and solves for chart nodes on the level set Phi = 1/2 by Newton's method.
+ * It follows Vico, Greengard, O'Neil, Rachh, "A fast boundary integral method
+ * for high-order multiscale mesh generation" (arXiv 1909.13356):
+ *   Phi(x) = sum_j sum_k w_k |N_j| psi_sigma(x, T^j(u_k, v_k))   (Sec. 4.3,
+ *   eq. discrete_int, with psi from eq. kerpsi), i.e. a sum over source nodes
+ *   y with weighted normals nw of (nw . (y-x)) g(u) / (4 pi |y-x|^3),
+ *   g(u) = erf(u) - (2u/sqrt pi) e^{-u^2}, u = |y-x| / (sqrt2 sigma).
+ * sigma belongs to the source triangle (one value per skeleton triangle).
+ *
+ * Conventions for every entry point:
+ *   - Return value: LSM_OK (0) or a negative lsm_status; no exceptions cross
+ *     the ABI.  lsm_last_error(ctx) returns a message for the last failure
+ *     on that context (thread-unsafe, owned by the context).
+ *   - Handles are opaque.  Device state belongs to the library until the
+ *     matching *_free / lsm_destroy.
+ *   - Array arguments may be host or device pointers (detected with
+ *     cudaPointerGetAttributes).  With device pointers the call is
+ *     asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) unless stated otherwise; with host pointers the call copies in
+ *     and out and returns after the stream has finished.  Mixing host and
+ *     device pointers in one call is allowed.
+ *   - Layouts are row-major: points are double[n][3] (x, y, z), triangles
+ *     int32[m][3] (0-based vertex indices, counter-clockwise seen from
+ *     outside, Sec. 3).
+ *   - Calls on the same mesh must be serialised by the caller (one stream at
+ *     a time); different meshes may run concurrently on different streams.
+ */
+#ifndef LSM_H
+#define LSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsm_ctx lsm_ctx;
+typedef struct lsm_mesh lsm_mesh;
+
+typedef enum {
+    LSM_OK = 0,
+    LSM_E_INVALID_ARG = -1,
+    LSM_E_OOM = -2,
+    LSM_E_CUDA = -3,
+    LSM_E_MESH = -4,          /* not watertight / not conforming / orientation */
+    LSM_E_NOT_CONVERGED = -5, /* reserved: per-node failures go to status arrays */
+    LSM_E_TIMEOUT = -6
+} lsm_status;
+
+typedef enum {
+    LSM_FP64 = 0,   /* every kernel in FP64 */
+    LSM_MIXED = 1   /* FP32 pair kernels, compensated per-tile accumulation,
+                       FP64 results; Newton finishes with FP64 steps when the
+                       tolerance asks for more than FP32 gives */
+} lsm_precision;
+
+/* Per-node status of the chart solve (low byte); bit 8 set when a Newton
+ * step was clamped to 4 sigma. */
+enum {
+    LSM_NODE_CONVERGED = 0,
+    LSM_NODE_MAXITER = 1,
+    LSM_NODE_ZERODERIV = 2,   /* H . grad Phi == 0 */
+    LSM_NODE_NONFINITE = 3,
+    LSM_NODE_CLAMPED_BIT = 256
+};
+
+/* Source quadrature rule on each skeleton triangle (Sec. 4.3): the triangle
+ * is split `subdiv` times into four midpoint children (Sec. 4.5, 0..5) and
+ * each (sub)triangle carries the Duffy-collapsed n_gl x n_gl Gauss-Legendre
+ * rule, collapsed at its first vertex.  Nodes per triangle:
+ * n_gl^2 * 4^subdiv.  (The paper's Vioreanu-Rokhlin rules are not used.) */
+typedef struct {
+    int32_t n_gl;
+    int32_t subdiv;
+} lsm_quad;
+
+/* Context options; pass NULL for the defaults shown. */
+typedef struct {
+    double cutoff_fp64;    /* near-field radius in sigma, FP64 path (8.0,
+                              Sec. 4.4: the kernel is the Laplace double
+                              layer beyond 8 sigma to 1e-13 relative) */
+    double cutoff_mixed;   /* same for the mixed path (6.5: neglected
+                              relative term 4e-9 < FP32 rounding) */
+    double mixed_switch;   /* mixed Newton: a node moves to FP64 steps once
+                              |Phi - 1/2| < mixed_switch (1e-6) */
+    double mixed_accept;   /* mixed Newton: a tolerance >= mixed_accept
+                              (1e-7, the mixed kernels' accuracy on Phi) is
+                              met on mixed evaluations alone, with no FP64
+                              steps */
+    int32_t reserved[8];
+} lsm_options;
+
+/* Statistics of one chart solve. */
+typedef struct {
+    int32_t iterations;       /* Newton sweeps (evaluations of the active set) */
+    int32_t n_nodes;
+    int32_t n_converged;
+    int32_t n_failed;         /* status != CONVERGED */
+    double eps_newton;        /* max |h^(k) - h^(k-1)| over nodes' last steps
+                                 (the paper's epsilon_N, Sec. 5) */
+    double max_residual;      /* max |Phi - 1/2| at the converged nodes' last
+                                 evaluation */
+    int64_t evals_fp32;       /* target evaluations done by the mixed kernels */
+    int64_t evals_fp64;       /* target evaluations done by FP64 kernels */
+    int32_t active_per_iter[32];
+} lsm_solve_stats;
+
+/* Counts describing an uploaded mesh. */
+typedef struct {
+    int64_t n_vertices;
+    int64_t n_triangles;
+    int64_t n_sources;        /* n_triangles * nodes per triangle */
+    int64_t n_tiles;          /* source tiles of the tiled kernels */
+    int64_t device_bytes;     /* device memory held by the mesh */
+    double sigma_min, sigma_max;
+} lsm_mesh_info;
+
+/* Create a context on CUDA device `device`.  Allocates no large memory.
+ * Errors: LSM_E_INVALID_ARG (bad device or options), LSM_E_CUDA. */
+int lsm_create(lsm_ctx** out, int device, const lsm_options* opt);
+/* Destroy a context; every mesh created from it must be freed first. */
+int lsm_destroy(lsm_ctx* ctx);
+/* Message of the last failed call on ctx (never NULL). */
+const char* lsm_last_error(const lsm_ctx* ctx);
+/* Number of kernel launches the library issued on this context so far. */
+int64_t lsm_launch_count(const lsm_ctx* ctx);
+
+/* Work counters of a context, for roofline accounting. */
+typedef struct {
+    int64_t launches;              /* every kernel launch (as lsm_launch_count) */
+    int64_t pairs_near;            /* (target, source) pairs evaluated with the
+                                      full smoothed kernel (near tiles) */
+    int64_t pairs_far;             /* pairs evaluated with the Laplace double
+                                      layer (far tiles) */
+    int64_t pair_kernel_launches;  /* pair-kernel launches timed while
+                                      profiling was on */
+    double pair_kernel_ms;         /* their summed device time (CUDA events
+                                      recorded on the launching stream) */
+} lsm_ctx_stats;
+
+/* Turn per-launch timing of the pair kernels on or off (off by default). */
+int lsm_set_profiling(lsm_ctx* ctx, int enable);
+/* Read (and with reset != 0, clear) the counters.  Synchronises the device. */
+int lsm_read_stats(lsm_ctx* ctx, lsm_ctx_stats* out, int reset);
+
+/*
+ * Upload a skeleton triangulation and build its resident device state
+ * (Sec. 3 and 4.3): per-triangle frames T_u, T_v, N = T_u x T_v
+ * (eq. tparam), sigma_j, vertex pseudonormals H(P) = sum(theta N_hat) /
+ * sum(theta) (eq. mkvertexpn, not renormalised), the source nodes
+ * y = T^j(u_k, v_k) with nw = w_k N_j, sorted along a Morton curve into
+ * tiles, and their FP32 tile-local copies.
+ *   verts  double[nv][3]; tris int32[nt][3]; sigma double[nt] or NULL for
+ *          sigma_j = 0.5 sqrt(2 area_j).  Copied; the caller keeps them.
+ *   rule   source rule (NULL = {4, 0}).
+ * Host-side checks: every index in range; the mesh is closed and
+ * consistently oriented (each directed edge once, its reverse once);
+ * device check: signed volume > 0 and every sigma > 0.  Any failure
+ * returns LSM_E_MESH.  Synchronises `stream` before returning.
+ */
+int lsm_mesh_upload(lsm_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris,
+                    int64_t nt, const double* sigma, const lsm_quad* rule, void* stream,
+                    lsm_mesh** out);
+int lsm_mesh_free(lsm_mesh* mesh);
+int lsm_mesh_get_info(const lsm_mesh* mesh, lsm_mesh_info* out);
+
+/*
+ * Phi and grad Phi at n targets (Sec. 4.4, eq. kerdecomp): source tiles
+ * farther than cutoff * sigma_max(tile) from a target block use the Laplace
+ * double layer (eq. kerapprox); all other pairs use the full kernel
+ * (eq. kerpsi and the gradient of eq. gradPhi with the sign of its second
+ * term corrected), with a power series for small u (eq. kerpsi_asymp).
+ *   x     double[n][3] targets
+ *   phi   double[n] out
+ *   grad  double[n][3] out, or NULL
+ *   precision  LSM_FP64 or LSM_MIXED
+ * n == 0 is a no-op.  Errors: LSM_E_INVALID_ARG, LSM_E_CUDA.
+ */
+int lsm_eval_phi_grad(lsm_mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
+                      int precision, void* stream);
+
+/*
+ * Chart nodes on Phi = 1/2 (Sec. 3.2): for each triangle j and each node
+ * (u_i, v_i) of the Duffy n x n chart rule with n = order/2 + 2, Newton's
+ * method on h (eq. newtoneq) from h = 0:
+ *   x = T^j(u_i, v_i) + h H^j(u_i, v_i)   (H^j from eq. mkpseudovec)
+ *   h <- h - (Phi(x) - 1/2) / (H^j . grad Phi(x)),
+ * each step clamped to 4 sigma_j, until |Phi(x) - 1/2| < tol or max_iter
+ * evaluations.  Converged nodes leave the active set (Sec. 5).
+ *   x_out   double[nt * n^2][3] (triangle-major, then rule order) or NULL
+ *   h_out   double[nt * n^2] or NULL
+ *   status  int32[nt * n^2] or NULL  (LSM_NODE_*)
+ *   stats   may be NULL
+ * Synchronises `stream` (the active-set size is read each sweep).
+ */
+int lsm_solve_charts(lsm_mesh* mesh, int order, double tol, int max_iter, int precision,
+                     double* x_out, double* h_out, int32_t* status, lsm_solve_stats* stats,
+                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSM_H */

@@ -1,0 +1,290 @@
+"""GB300 level-set mesher: Python binding of liblsm (the C ABI in include/lsm.h).
+
+This module only marshals arguments: every step of the evaluation and of the
+Newton chart solve runs in the library's CUDA kernels.  Arrays may be numpy
+arrays (host memory) or torch tensors (host or CUDA); outputs are allocated
+on the same side as the input points unless given.  There is no CPU fallback:
+without the compiled library or a CUDA device the calls raise.
+
+Names follow the paper (Vico, Greengard, O'Neil, Rachh, arXiv 1909.13356):
+Phi, grad Phi (Sec. 4), chart nodes, h, pseudonormals H (Sec. 3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["FP64", "MIXED", "Context", "Mesh", "SolveStats", "LsmError", "lib", "load"]
+
+FP64 = 0
+MIXED = 1
+
+NODE_CONVERGED = 0
+NODE_MAXITER = 1
+NODE_ZERODERIV = 2
+NODE_NONFINITE = 3
+NODE_CLAMPED_BIT = 256
+
+_ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVERGED", -6: "TIMEOUT"}
+
+# every symbol include/lsm.h declares
+EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "lsm_set_profiling",
+           "lsm_read_stats", "lsm_mesh_upload", "lsm_mesh_free", "lsm_mesh_get_info", "lsm_eval_phi_grad",
+           "lsm_solve_charts")
+
+
+class LsmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lsm error {code} ({_ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _Quad(ctypes.Structure):
+    _fields_ = [("n_gl", ctypes.c_int32), ("subdiv", ctypes.c_int32)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("cutoff_fp64", ctypes.c_double), ("cutoff_mixed", ctypes.c_double),
+                ("mixed_switch", ctypes.c_double), ("mixed_accept", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("n_converged", ctypes.c_int32), ("n_failed", ctypes.c_int32),
+                ("eps_newton", ctypes.c_double), ("max_residual", ctypes.c_double),
+                ("evals_fp32", ctypes.c_int64), ("evals_fp64", ctypes.c_int64),
+                ("active_per_iter", ctypes.c_int32 * 32)]
+
+
+class _CtxStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("pairs_near", ctypes.c_int64),
+                ("pairs_far", ctypes.c_int64), ("pair_kernel_launches", ctypes.c_int64),
+                ("pair_kernel_ms", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("n_sources", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("sigma_min", ctypes.c_double),
+                ("sigma_max", ctypes.c_double)]
+
+
+@dataclass
+class SolveStats:
+    iterations: int
+    n_nodes: int
+    n_converged: int
+    n_failed: int
+    eps_newton: float
+    max_residual: float
+    evals_fp32: int
+    evals_fp64: int
+    active_per_iter: list
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build_if_needed: bool = True):
+    """Load liblsm.so (building it with nvcc first when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_needed and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"liblsm.so not built ({_build.LIB}); run paper_1909_13356_gb300/build.py")
+        L = ctypes.CDLL(_build.LIB)
+        P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.lsm_create.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(_Options)]
+        L.lsm_destroy.argtypes = [P]
+        L.lsm_last_error.argtypes = [P]
+        L.lsm_last_error.restype = ctypes.c_char_p
+        L.lsm_launch_count.argtypes = [P]
+        L.lsm_launch_count.restype = I64
+        L.lsm_set_profiling.argtypes = [P, I32]
+        L.lsm_read_stats.argtypes = [P, ctypes.POINTER(_CtxStats), I32]
+        L.lsm_mesh_upload.argtypes = [P, P, I64, P, I64, P, ctypes.POINTER(_Quad), P, ctypes.POINTER(P)]
+        L.lsm_mesh_free.argtypes = [P]
+        L.lsm_mesh_get_info.argtypes = [P, ctypes.POINTER(_Info)]
+        L.lsm_eval_phi_grad.argtypes = [P, P, I64, P, P, I32, P]
+        L.lsm_solve_charts.argtypes = [P, I32, D, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
+        for name in EXPORTS:
+            getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
+        _lib = L
+        return L
+
+
+def lib():
+    return load()
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _as(a, dtype):
+    """Contiguous array of the requested dtype on the same side as `a`."""
+    if _is_torch(a):
+        import torch
+        td = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        return a.to(td).contiguous()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Context:
+    """A library context on one CUDA device (lsm_create)."""
+
+    def __init__(self, device: int = 0, cutoff_fp64: float = 0.0, cutoff_mixed: float = 0.0,
+                 mixed_switch: float = 0.0, mixed_accept: float = 0.0):
+        self._L = load()
+        opt = _Options(cutoff_fp64, cutoff_mixed, mixed_switch, mixed_accept)
+        h = ctypes.c_void_p()
+        rc = self._L.lsm_create(ctypes.byref(h), int(device), ctypes.byref(opt))
+        if rc != 0:
+            raise LsmError(rc, "lsm_create failed (no CUDA device?)")
+        self._h = h
+        self.device = device
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LsmError(rc, self._L.lsm_last_error(self._h).decode(errors="replace"))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._L.lsm_launch_count(self._h))
+
+    def set_profiling(self, enable: bool = True):
+        """Time every pair-kernel launch with CUDA events on its stream."""
+        self._check(self._L.lsm_set_profiling(self._h, 1 if enable else 0))
+
+    def read_stats(self, reset: bool = False) -> dict:
+        """Launch count, pairs evaluated (near / far tiles) and pair-kernel time."""
+        st = _CtxStats()
+        self._check(self._L.lsm_read_stats(self._h, ctypes.byref(st), 1 if reset else 0))
+        return {k: getattr(st, k) for k, _ in _CtxStats._fields_}
+
+    def upload(self, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0, stream=None) -> "Mesh":
+        return Mesh(self, verts, tris, sigma, n_gl, subdiv, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lsm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    """Resident device state of one skeleton triangulation (lsm_mesh_upload)."""
+
+    def __init__(self, ctx: Context, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0,
+                 stream=None):
+        self.ctx = ctx
+        v = _as(verts, np.float64)
+        t = _as(tris, np.int32)
+        s = _as(sigma, np.float64) if sigma is not None else None
+        q = _Quad(int(n_gl), int(subdiv))
+        h = ctypes.c_void_p()
+        rc = ctx._L.lsm_mesh_upload(ctx._h, _ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]),
+                                    _ptr(s), ctypes.byref(q), _stream_handle(stream), ctypes.byref(h))
+        ctx._check(rc)
+        self._h = h
+        self.n_triangles = int(t.shape[0])
+
+    def info(self) -> dict:
+        inf = _Info()
+        self.ctx._check(self.ctx._L.lsm_mesh_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in _Info._fields_}
+
+    def eval_phi_grad(self, x, precision: int = FP64, phi=None, grad=None, with_grad: bool = True,
+                      stream=None):
+        """Phi and grad Phi at targets x [n, 3] (lsm_eval_phi_grad)."""
+        xs = _as(x, np.float64)
+        n = int(xs.shape[0])
+        if phi is None:
+            if _is_torch(xs):
+                import torch
+                phi = torch.empty(n, dtype=torch.float64, device=xs.device)
+                if with_grad and grad is None:
+                    grad = torch.empty((n, 3), dtype=torch.float64, device=xs.device)
+            else:
+                phi = np.empty(n)
+                if with_grad and grad is None:
+                    grad = np.empty((n, 3))
+        rc = self.ctx._L.lsm_eval_phi_grad(self._h, _ptr(xs), n, _ptr(phi), _ptr(grad), int(precision),
+                                           _stream_handle(stream))
+        self.ctx._check(rc)
+        return phi, grad
+
+    def solve_charts(self, order: int = 8, tol: float = 1e-12, max_iter: int = 20,
+                     precision: int = FP64, device_out: bool = False, stream=None):
+        """Chart nodes on Phi = 1/2 by Newton's method (lsm_solve_charts).
+        Returns (x [N,3], h [N], status [N], SolveStats)."""
+        n_gl = order // 2 + 2
+        N = self.n_triangles * n_gl * n_gl
+        if device_out:
+            import torch
+            dev = torch.device("cuda", self.ctx.device)
+            x = torch.empty((N, 3), dtype=torch.float64, device=dev)
+            h = torch.empty(N, dtype=torch.float64, device=dev)
+            st = torch.empty(N, dtype=torch.int32, device=dev)
+        else:
+            x, h, st = np.empty((N, 3)), np.empty(N), np.empty(N, dtype=np.int32)
+        stats = _Stats()
+        rc = self.ctx._L.lsm_solve_charts(self._h, int(order), float(tol), int(max_iter), int(precision),
+                                          _ptr(x), _ptr(h), _ptr(st), ctypes.byref(stats),
+                                          _stream_handle(stream))
+        self.ctx._check(rc)
+        s = SolveStats(stats.iterations, stats.n_nodes, stats.n_converged, stats.n_failed,
+                       stats.eps_newton, stats.max_residual, stats.evals_fp32, stats.evals_fp64,
+                       list(stats.active_per_iter)[:max(stats.iterations, 0)])
+        return x, h, st, s
+
+    def free(self):
+        if getattr(self, "_h", None):
+            self.ctx._L.lsm_mesh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

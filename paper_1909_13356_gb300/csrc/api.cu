@@ -1,0 +1,518 @@
+// api.cu -- the extern "C" entry points declared in include/lsm.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lsm_internal.cuh"
+
+namespace lsm {
+
+// Duffy-collapsed n x n Gauss-Legendre rule on the standard simplex,
+// composite over `subdiv` midpoint splits (Sec. 4.3 and 4.5).  For each
+// (sub)triangle (A, B, C) with children (A,mAB,mCA), (mAB,B,mBC),
+// (mCA,mBC,C), (mBC,mCA,mAB): node A + s (B-A) + t (C-A) with
+// s = xi (1 - eta), t = xi eta, weight w_xi w_eta xi |det(B-A, C-A)|.
+// Output uvw[cnt][3] = (u, v, w); order: subtriangle, xi, eta.
+void simplex_rule_host(int n, int subdiv, double* uvw)
+{
+    // Gauss-Legendre on [-1, 1] by Newton iteration on P_n, then mapped to [0, 1]
+    std::vector<double> xg(n), wg(n);
+    for (int i = 0; i < n; i++) {
+        double z = std::cos(M_PI * (n - i - 0.25) / (n + 0.5));  // ascending roots
+        double dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double pm = 1.0, p = z;
+            for (int k = 2; k <= n; k++) {
+                const double pk = ((2 * k - 1) * z * p - (k - 1) * pm) / k;
+                pm = p;
+                p = pk;
+            }
+            dp = n * (pm - z * p) / (1.0 - z * z);
+            const double dz = p / dp;
+            z -= dz;
+            if (std::fabs(dz) <= 1e-16) {
+                double q0 = 1.0, q1 = z;
+                for (int k = 2; k <= n; k++) {
+                    const double qk = ((2 * k - 1) * z * q1 - (k - 1) * q0) / k;
+                    q0 = q1;
+                    q1 = qk;
+                }
+                dp = n * (q0 - z * q1) / (1.0 - z * z);
+                break;
+            }
+        }
+        xg[i] = 0.5 * (z + 1.0);
+        wg[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+    struct Tri {
+        double a[2], b[2], c[2];
+    };
+    std::vector<Tri> cur{{{0, 0}, {1, 0}, {0, 1}}}, nxt;
+    for (int l = 0; l < subdiv; l++) {
+        nxt.clear();
+        for (const Tri& t : cur) {
+            const double ab[2] = {0.5 * (t.a[0] + t.b[0]), 0.5 * (t.a[1] + t.b[1])};
+            const double bc[2] = {0.5 * (t.b[0] + t.c[0]), 0.5 * (t.b[1] + t.c[1])};
+            const double ca[2] = {0.5 * (t.c[0] + t.a[0]), 0.5 * (t.c[1] + t.a[1])};
+            nxt.push_back({{t.a[0], t.a[1]}, {ab[0], ab[1]}, {ca[0], ca[1]}});
+            nxt.push_back({{ab[0], ab[1]}, {t.b[0], t.b[1]}, {bc[0], bc[1]}});
+            nxt.push_back({{ca[0], ca[1]}, {bc[0], bc[1]}, {t.c[0], t.c[1]}});
+            nxt.push_back({{bc[0], bc[1]}, {ca[0], ca[1]}, {ab[0], ab[1]}});
+        }
+        cur.swap(nxt);
+    }
+    size_t o = 0;
+    for (const Tri& t : cur) {
+        const double e1[2] = {t.b[0] - t.a[0], t.b[1] - t.a[1]};
+        const double e2[2] = {t.c[0] - t.a[0], t.c[1] - t.a[1]};
+        const double det = std::fabs(e1[0] * e2[1] - e1[1] * e2[0]);
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++) {
+                const double s = xg[i] * (1.0 - xg[j]), q = xg[i] * xg[j];
+                uvw[o++] = t.a[0] + s * e1[0] + q * e2[0];
+                uvw[o++] = t.a[1] + s * e1[1] + q * e2[1];
+                uvw[o++] = wg[i] * wg[j] * xg[i] * det;
+            }
+    }
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void* p)
+{
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Input array as a device pointer: either the caller's or a stream-ordered copy.
+template <class T>
+int to_device(Ctx* ctx, Scratch& s, const T* p, size_t count, const T** out, cudaStream_t st)
+{
+    if (p == nullptr || count == 0) {
+        *out = p;
+        return LSM_OK;
+    }
+    if (is_device_ptr(p)) {
+        *out = p;
+        return LSM_OK;
+    }
+    T* d;
+    LSM_CUDA_TRY(ctx, s.get(&d, count));
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(d, p, sizeof(T) * count, cudaMemcpyHostToDevice, st));
+    *out = d;
+    return LSM_OK;
+}
+
+// Host-side topology check: indices in range, no repeated vertex, and every
+// directed edge (a, b) appears exactly once with its reverse (b, a) present:
+// the surface is closed, edge-manifold and consistently oriented.
+bool check_topology(const int32_t* tris, int64_t m, int64_t nv, std::string& why)
+{
+    std::vector<uint64_t> e;
+    e.reserve(3 * (size_t)m);
+    for (int64_t j = 0; j < m; j++) {
+        const int32_t a = tris[3 * j], b = tris[3 * j + 1], c = tris[3 * j + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) {
+            why = "triangle index out of range";
+            return false;
+        }
+        if (a == b || b == c || c == a) {
+            why = "degenerate triangle (repeated vertex)";
+            return false;
+        }
+        e.push_back((uint64_t)a * (uint64_t)nv + (uint64_t)b);
+        e.push_back((uint64_t)b * (uint64_t)nv + (uint64_t)c);
+        e.push_back((uint64_t)c * (uint64_t)nv + (uint64_t)a);
+    }
+    std::sort(e.begin(), e.end());
+    for (size_t i = 1; i < e.size(); i++)
+        if (e[i] == e[i - 1]) {
+            why = "directed edge used twice (inconsistent orientation or non-manifold edge)";
+            return false;
+        }
+    for (uint64_t k : e) {
+        const uint64_t a = k / (uint64_t)nv, b = k % (uint64_t)nv;
+        if (!std::binary_search(e.begin(), e.end(), b * (uint64_t)nv + a)) {
+            why = "open edge (mesh not watertight)";
+            return false;
+        }
+    }
+    return true;
+}
+
+// SoA sorted targets from AoS x and a permutation
+__global__ void k_gather_points(const double* __restrict__ x, const uint32_t* __restrict__ perm, int n,
+                                double* __restrict__ T)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t i = perm[k];
+    for (int c = 0; c < 3; c++) T[(int64_t)c * n + k] = x[3 * i + c];
+}
+
+__global__ void k_scatter_results(const double* __restrict__ R, const uint32_t* __restrict__ perm, int n,
+                                  double* __restrict__ phi, double* __restrict__ grad)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t i = perm[k];
+    phi[i] = R[k];
+    if (grad) {
+        grad[3 * i] = R[(int64_t)n + k];
+        grad[3 * i + 1] = R[2 * (int64_t)n + k];
+        grad[3 * i + 2] = R[3 * (int64_t)n + k];
+    }
+}
+
+int check_flag(Ctx* ctx, cudaStream_t st)
+{
+    int h = 0;
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (h != 0) {
+        ctx->err = "device wait limit reached in a pair kernel (error word " + std::to_string(h) + ")";
+        cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st);
+        return LSM_E_TIMEOUT;
+    }
+    return LSM_OK;
+}
+
+}  // namespace
+}  // namespace lsm
+
+using namespace lsm;
+
+extern "C" {
+
+int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
+{
+    if (!out) return LSM_E_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return LSM_E_INVALID_ARG;
+    lsm_ctx* c = new (std::nothrow) lsm_ctx();
+    if (!c) return LSM_E_OOM;
+    Ctx* ctx = &c->c;
+    ctx->device = device;
+    ctx->opt.cutoff_fp64 = 8.0;
+    ctx->opt.cutoff_mixed = 6.5;
+    ctx->opt.mixed_switch = 1e-6;
+    ctx->opt.mixed_accept = 1e-7;
+    if (opt) {
+        if (opt->mixed_accept > 0) ctx->opt.mixed_accept = opt->mixed_accept;
+        if (opt->cutoff_fp64 > 0) ctx->opt.cutoff_fp64 = opt->cutoff_fp64;
+        if (opt->cutoff_mixed > 0) ctx->opt.cutoff_mixed = opt->cutoff_mixed;
+        if (opt->mixed_switch > 0) ctx->opt.mixed_switch = opt->mixed_switch;
+    }
+    DeviceGuard g(device);
+    int rc = LSM_OK;
+    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&ctx->d_flag, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_flag, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_pairs, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_pairs, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        delete c;
+        return LSM_E_CUDA;
+    }
+    rc = eval_init_constants(ctx);
+    if (rc != LSM_OK) {
+        cudaFree(ctx->d_flag);
+        delete c;
+        return rc;
+    }
+    // keep freed scratch in the stream-ordered pool between calls
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return LSM_OK;
+}
+
+int lsm_destroy(lsm_ctx* c)
+{
+    if (!c) return LSM_E_INVALID_ARG;
+    DeviceGuard g(c->c.device);
+    cudaFree(c->c.d_flag);
+    cudaFree(c->c.d_pairs);
+    for (auto& e : c->c.prof_events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    delete c;
+    return LSM_OK;
+}
+
+int lsm_set_profiling(lsm_ctx* c, int enable)
+{
+    if (!c) return LSM_E_INVALID_ARG;
+    c->c.profiling = enable != 0;
+    return LSM_OK;
+}
+
+int lsm_read_stats(lsm_ctx* c, lsm_ctx_stats* out, int reset)
+{
+    if (!c || !out) return LSM_E_INVALID_ARG;
+    Ctx* ctx = &c->c;
+    DeviceGuard g(ctx->device);
+    LSM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    for (auto& e : ctx->prof_events) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) ctx->prof_ms += ms;
+        ctx->prof_launches++;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    ctx->prof_events.clear();
+    unsigned long long pr[2] = {0, 0};
+    LSM_CUDA_TRY(ctx, cudaMemcpy(pr, ctx->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
+    out->launches = ctx->launches;
+    out->pairs_near = (int64_t)pr[0];
+    out->pairs_far = (int64_t)pr[1];
+    out->pair_kernel_launches = ctx->prof_launches;
+    out->pair_kernel_ms = ctx->prof_ms;
+    if (reset) {
+        LSM_CUDA_TRY(ctx, cudaMemset(ctx->d_pairs, 0, sizeof(pr)));
+        ctx->prof_ms = 0.0;
+        ctx->prof_launches = 0;
+    }
+    return LSM_OK;
+}
+
+const char* lsm_last_error(const lsm_ctx* c)
+{
+    if (!c) return "null context";
+    return c->c.err.c_str();
+}
+
+int64_t lsm_launch_count(const lsm_ctx* c) { return c ? c->c.launches : -1; }
+
+int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                    const double* sigma, const lsm_quad* rule, void* stream, lsm_mesh** out)
+{
+    if (!c || !out) return LSM_E_INVALID_ARG;
+    *out = nullptr;
+    Ctx* ctx = &c->c;
+    if (!verts || !tris || nv < 3 || nt < 4) {
+        ctx->err = "mesh_upload: need at least 3 vertices and 4 triangles";
+        return LSM_E_INVALID_ARG;
+    }
+    lsm_quad q = rule ? *rule : lsm_quad{4, 0};
+    if (q.n_gl < 1 || q.n_gl > 32 || q.subdiv < 0 || q.subdiv > 5) {
+        ctx->err = "mesh_upload: rule needs 1 <= n_gl <= 32 and 0 <= subdiv <= 5";
+        return LSM_E_INVALID_ARG;
+    }
+    const int nq = q.n_gl * q.n_gl * (1 << (2 * q.subdiv));
+    const int64_t ns = nt * (int64_t)nq;
+    if (ns >= ((int64_t)1 << 31) - kTile || nv >= ((int64_t)1 << 31)) {
+        ctx->err = "mesh_upload: too many source nodes (limit 2^31)";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // topology on the host
+    std::vector<int32_t> htris;
+    const int32_t* tp = tris;
+    if (is_device_ptr(tris)) {
+        htris.resize(3 * (size_t)nt);
+        LSM_CUDA_TRY(ctx, cudaMemcpy(htris.data(), tris, sizeof(int32_t) * 3 * nt, cudaMemcpyDeviceToHost));
+        tp = htris.data();
+    }
+    std::string why;
+    if (!check_topology(tp, nt, nv, why)) {
+        ctx->err = "mesh_upload: " + why;
+        return LSM_E_MESH;
+    }
+    lsm_mesh* mh = new (std::nothrow) lsm_mesh();
+    if (!mh) return LSM_E_OOM;
+    Mesh* me = &mh->m;
+    me->ctx = ctx;
+    me->nv = nv;
+    me->m = nt;
+    me->nq = nq;
+    me->rule = q;
+    me->ns = ns;
+    me->ntiles = (ns + kTile - 1) / kTile;
+    auto fail = [&](int rc) {
+        lsm_mesh_free(mh);
+        return rc;
+    };
+    auto alloc = [&](auto** p, size_t count) -> bool {
+        using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
+        const size_t bytes = count * sizeof(T);
+        if (cudaMalloc((void**)p, bytes) != cudaSuccess) return false;
+        me->bytes += bytes;
+        return true;
+    };
+    const size_t ntl = (size_t)me->ntiles;
+    if (!alloc(&me->verts, 3 * nv) || !alloc(&me->tris, 3 * nt) || !alloc(&me->tri_sigma, nt) ||
+        !alloc(&me->tri_n, 3 * nt) || !alloc(&me->vpn, 3 * nv) || !alloc(&me->s64_pos, ns) ||
+        !alloc(&me->s64_nw, ns) || !alloc(&me->s32_pos, ns) || !alloc(&me->s32_nw, ns) || !alloc(&me->s32_lo, ns) ||
+        !alloc(&me->tile_lo, ntl) || !alloc(&me->tile_hi, ntl) || !alloc(&me->tile_chi, ntl) ||
+        !alloc(&me->tile_clo, ntl)) {
+        cudaGetLastError();
+        ctx->err = "mesh_upload: out of device memory";
+        return fail(LSM_E_OOM);
+    }
+    const cudaMemcpyKind kv = is_device_ptr(verts) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kt = is_device_ptr(tris) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(me->verts, verts, sizeof(double) * 3 * nv, kv, st) != cudaSuccess ||
+        cudaMemcpyAsync(me->tris, tris, sizeof(int32_t) * 3 * nt, kt, st) != cudaSuccess) {
+        ctx->err = "mesh_upload: copy failed";
+        return fail(LSM_E_CUDA);
+    }
+    int rc;
+    {
+        Scratch s(st);
+        const double* sig_d = nullptr;
+        rc = to_device(ctx, s, sigma, (size_t)nt, &sig_d, st);
+        if (rc) return fail(rc);
+        std::vector<double> rh((size_t)nq * 3);
+        simplex_rule_host(q.n_gl, q.subdiv, rh.data());
+        double* rd;
+        if (s.get(&rd, rh.size()) != cudaSuccess ||
+            cudaMemcpyAsync(rd, rh.data(), sizeof(double) * rh.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            ctx->err = "mesh_upload: rule upload failed";
+            return fail(LSM_E_CUDA);
+        }
+        double red[8];
+        rc = build_mesh_device(ctx, me, sig_d, rd, red, st);
+        if (rc == LSM_E_MESH) {
+            ctx->err = red[3] > 0 ? "mesh_upload: zero-area triangle or sigma <= 0"
+                     : red[4] > 0 ? "mesh_upload: vertex not used by any triangle"
+                                  : "mesh_upload: signed volume <= 0 (triangles must be counter-clockwise seen from outside)";
+        }
+        if (rc) return fail(rc);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        ctx->err = "mesh_upload: stream failed";
+        return fail(LSM_E_CUDA);
+    }
+    *out = mh;
+    return LSM_OK;
+}
+
+int lsm_mesh_free(lsm_mesh* mh)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    DeviceGuard g(me->ctx ? me->ctx->device : 0);
+    void* ps[] = {me->verts, me->tris, me->tri_sigma, me->tri_n, me->vpn, me->s64_pos, me->s64_nw,
+                  me->s32_pos, me->s32_nw, me->s32_lo, me->tile_lo, me->tile_hi, me->tile_chi, me->tile_clo};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete mh;
+    return LSM_OK;
+}
+
+int lsm_mesh_get_info(const lsm_mesh* mh, lsm_mesh_info* out)
+{
+    if (!mh || !out) return LSM_E_INVALID_ARG;
+    const Mesh* me = &mh->m;
+    out->n_vertices = me->nv;
+    out->n_triangles = me->m;
+    out->n_sources = me->ns;
+    out->n_tiles = me->ntiles;
+    out->device_bytes = (int64_t)me->bytes;
+    out->sigma_min = me->sigma_min;
+    out->sigma_max = me->sigma_max;
+    return LSM_OK;
+}
+
+int lsm_eval_phi_grad(lsm_mesh* mh, const double* x, int64_t n, double* phi, double* grad, int precision,
+                      void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (n == 0) return LSM_OK;
+    if (n < 0 || n >= ((int64_t)1 << 31) || !x || !phi ||
+        (precision != LSM_FP64 && precision != LSM_MIXED)) {
+        ctx->err = "eval_phi_grad: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ni = (int)n;
+    Scratch s(st);
+    const double* xd;
+    int rc = to_device(ctx, s, x, 3 * (size_t)n, &xd, st);
+    if (rc) return rc;
+    uint32_t* perm;
+    double *T, *R;
+    LSM_CUDA_TRY(ctx, s.get(&perm, n));
+    LSM_CUDA_TRY(ctx, s.get(&T, 3 * (size_t)n));
+    LSM_CUDA_TRY(ctx, s.get(&R, 4 * (size_t)n));
+    rc = morton_order_points(ctx, xd, 3, ni, perm, st);
+    if (rc) return rc;
+    k_gather_points<<<(ni + 255) / 256, 256, 0, st>>>(xd, perm, ni, T);
+    LSM_LAUNCHED(ctx);
+    Targets tg{T, n, ni};
+    rc = eval_sorted(ctx, me, tg, R, precision, st);
+    if (rc) return rc;
+    const bool phi_dev = is_device_ptr(phi);
+    const bool grad_dev = grad && is_device_ptr(grad);
+    double* pd = phi;
+    double* gd = grad;
+    if (!phi_dev) LSM_CUDA_TRY(ctx, s.get(&pd, n));
+    if (grad && !grad_dev) LSM_CUDA_TRY(ctx, s.get(&gd, 3 * (size_t)n));
+    k_scatter_results<<<(ni + 255) / 256, 256, 0, st>>>(R, perm, ni, pd, gd);
+    LSM_LAUNCHED(ctx);
+    if (!phi_dev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(phi, pd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (grad && !grad_dev)
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(grad, gd, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (!phi_dev || (grad && !grad_dev) || !is_device_ptr(x)) return check_flag(ctx, st);
+    return LSM_OK;
+}
+
+int lsm_solve_charts(lsm_mesh* mh, int order, double tol, int max_iter, int precision, double* x_out,
+                     double* h_out, int32_t* status, lsm_solve_stats* stats, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (order < 0 || order > 40 || !(tol > 0) || max_iter < 1 || max_iter > 1000 ||
+        (precision != LSM_FP64 && precision != LSM_MIXED)) {
+        ctx->err = "solve_charts: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_gl = order / 2 + 2;
+    const int64_t N = me->m * (int64_t)n_gl * n_gl;
+    Scratch s(st);
+    double *xo = x_out, *ho = h_out;
+    int32_t* so = status;
+    const bool xdev = x_out && is_device_ptr(x_out);
+    const bool hdev = h_out && is_device_ptr(h_out);
+    const bool sdev = status && is_device_ptr(status);
+    if (!xdev) LSM_CUDA_TRY(ctx, s.get(&xo, 3 * (size_t)N));
+    if (!hdev) LSM_CUDA_TRY(ctx, s.get(&ho, (size_t)N));
+    if (!sdev) LSM_CUDA_TRY(ctx, s.get(&so, (size_t)N));
+    int rc = solve_charts_device(ctx, me, n_gl, tol, max_iter, precision, xo, ho, so, stats, st);
+    if (rc) return rc;
+    if (x_out && !xdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(x_out, xo, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+    if (h_out && !hdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(h_out, ho, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    if (status && !sdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(status, so, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+    return check_flag(ctx, st);
+}
+
+}  // extern "C"

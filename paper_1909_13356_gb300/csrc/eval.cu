@@ -1,0 +1,679 @@
+// eval.cu -- Phi and grad Phi at Morton-sorted targets (Sec. 4.4).
+//
+// The sum over source nodes is split by tile (eq. kerdecomp): a source tile
+// whose bounding box lies farther than cutoff * sigma_max(tile) from the
+// bounding box of a block of targets contributes through the Laplace double
+// layer (eq. kerapprox); every other tile contributes through the full
+// smoothed kernel (eq. kerpsi, and its gradient from eq. gradPhi with the
+// sign of the second term corrected), whose radial factors switch to a power
+// series for small u (eq. kerpsi_asymp, completed with the term eq.
+// kerpsi_asymp2 drops).  Nothing is dropped: a near tile evaluates the full
+// kernel for all of its pairs.
+//
+// With nw' = nw / (4 pi), a = 1/(sqrt2 sigma), r = y - x, u = |r| a:
+//   phi  += (nw'.r) a^3 Hs(u)
+//   grad -= nw' a^3 Hs(u) + (nw'.r) a^5 Ks(u) r
+//   Hs(u) = g(u)/u^3,  Ks(u) = Hs'(u)/u = ((4/sqrt pi) e^{-u^2} - 3 Hs(u)) / u^2,
+//   g(u) = erf(u) - (2u/sqrt pi) e^{-u^2};
+// the Laplace limits are a^3 Hs -> 1/|r|^3 and a^5 Ks -> -3/|r|^5.
+//
+// Layout: one CTA owns a block of kEvalThreads * TPT consecutive sorted
+// targets and walks a contiguous range of source tiles; each tile (kTile
+// nodes, pos and nw arrays) is staged into shared memory by the bulk-copy
+// engine (cp.async.bulk, completion on an mbarrier), double buffered.  A grid
+// y-dimension splits the tile range when there are too few target blocks to
+// fill the GPU; the partial sums are then reduced in a fixed order.
+//
+// Mixed precision: pair arithmetic in FP32 on tile-local coordinates (source
+// offsets from the tile centre, and the target offset formed from hi/lo
+// float parts of the FP64 target and of the centre), FP32 sums within a tile,
+// and a compensated (two-sum) float-float accumulator across tiles; results
+// are returned in FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "lsm_internal.cuh"
+
+#ifndef LSM_RSQRT_REFINE
+#define LSM_RSQRT_REFINE 1
+#endif
+
+namespace lsm {
+namespace {
+
+constexpr int kSer64 = 14;  // series terms, FP64, used for u^2 < 0.25
+constexpr int kSer32 = 11;  // series terms, FP32, used for u^2 < 0.5625
+constexpr double kUs64 = 0.25;
+constexpr float kUs32 = 0.5625f;
+constexpr double kTwoOverSqrtPi = 1.12837916709551257390;
+constexpr double kFourOverSqrtPi = 2.25675833419102514780;
+
+// Hs(u) = sum_m A_m w^m, Ks(u) = sum_m B_m w^m, w = u^2 (filled by the host)
+__constant__ double c_A64[kSer64];
+__constant__ double c_B64[kSer64];
+__constant__ float c_A32[kSer32];
+__constant__ float c_B32[kSer32];
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared; `bytes` and both addresses are multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls (each poll may suspend the
+// thread for a hardware-defined time slice).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit)
+{
+    for (int i = 0; i < limit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+constexpr int kWaitLimit = 1 << 22;
+constexpr int kChunk = 64;  // far-tile sources summed in FP32 before compensation
+constexpr int kErrWaitTimeout = 1;
+
+// ---------------------------------------------------------------- radial factors
+__device__ __forceinline__ void radial64(double r2, double a, double sqrt2sig, double& fH, double& FK)
+{
+    const double w = r2 * a * a;
+    double H, K;
+    if (w < kUs64) {
+        H = c_A64[kSer64 - 1];
+        K = c_B64[kSer64 - 1];
+#pragma unroll
+        for (int m = kSer64 - 2; m >= 0; m--) {
+            H = fma(H, w, c_A64[m]);
+            K = fma(K, w, c_B64[m]);
+        }
+    } else {
+        const double rinv = rsqrt(r2);
+        const double u = r2 * rinv * a;
+        const double e = exp(-w);
+        const double g = erf(u) - kTwoOverSqrtPi * u * e;
+        const double ui = rinv * sqrt2sig;
+        const double ui2 = ui * ui;
+        H = g * ui2 * ui;
+        K = ui2 * (kFourOverSqrtPi * e - 3.0 * H);
+    }
+    const double a3 = a * a * a;
+    fH = a3 * H;
+    FK = a3 * a * a * K;
+}
+
+// FP32 radial factors.  Small u: the power series.  Otherwise the Laplace
+// part is separated from the smoothing correction, so that rounding of
+// erf(u) near 1 does not bias the result:
+//   g = 1 - G,  G(u) = erfc(u) + (2u/sqrt pi) e^{-u^2},
+//   a^3 Hs = (1 - G)/rho^3,   a^5 Ks = (3G - 3)/rho^5 + (4/sqrt pi) a^3 e^{-u^2}/rho^2.
+__device__ __forceinline__ float rsqrt_refined(float r2)
+{
+    // one Newton step on the hardware estimate: the result is within about
+    // one ulp and carries no systematic bias
+    const float r = rsqrtf(r2);
+#if LSM_RSQRT_REFINE
+    const float t = r2 * r;
+    const float e = fmaf(-t, r, 1.0f);
+    return fmaf(0.5f * r, e, r);
+#else
+    return r;
+#endif
+}
+
+__device__ __forceinline__ void radial32(float r2, float a, float& fH, float& FK)
+{
+    const float w = r2 * a * a;
+    const float a3 = a * a * a;
+    if (w < kUs32) {
+        float H = c_A32[kSer32 - 1];
+        float K = c_B32[kSer32 - 1];
+#pragma unroll
+        for (int m = kSer32 - 2; m >= 0; m--) {
+            H = fmaf(H, w, c_A32[m]);
+            K = fmaf(K, w, c_B32[m]);
+        }
+        fH = a3 * H;
+        FK = a3 * a * a * K;
+    } else {
+        const float ri = rsqrt_refined(r2);
+        const float u = r2 * ri * a;
+        const float e = expf(-w);
+        const float G = erfcf(u) + (float)kTwoOverSqrtPi * u * e;
+        const float ri2 = ri * ri;
+        const float ri3 = ri2 * ri;
+        fH = fmaf(-G, ri3, ri3);
+        FK = fmaf(3.0f * G - 3.0f, ri3 * ri2, ri2 * ((float)kFourOverSqrtPi * a3 * e));
+    }
+}
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
+// Block-wide min/max of three floats each, result in shared s[0..6).
+__device__ __forceinline__ void block_bbox(float lo[3], float hi[3], float* s)
+{
+    __shared__ float part[6][kEvalThreads / 32];
+    for (int c = 0; c < 3; c++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        for (int c = 0; c < 3; c++) {
+            part[c][w] = lo[c];
+            part[3 + c][w] = hi[c];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 3; c++) {
+            float L = part[c][0], H = part[3 + c][0];
+            for (int k = 1; k < kEvalThreads / 32; k++) {
+                L = fminf(L, part[c][k]);
+                H = fmaxf(H, part[3 + c][k]);
+            }
+            s[c] = L;
+            s[3 + c] = H;
+        }
+    }
+    __syncthreads();
+}
+
+// True when every pair between the target block box and the source tile box
+// is at least cutoff * sigma_max(tile) apart (conservative in FP32).
+__device__ __forceinline__ bool tile_is_far(const float* bb, float4 lo, float4 hi, float cut2)
+{
+    const float gx = fmaxf(0.0f, fmaxf(lo.x - bb[3], bb[0] - hi.x));
+    const float gy = fmaxf(0.0f, fmaxf(lo.y - bb[4], bb[1] - hi.y));
+    const float gz = fmaxf(0.0f, fmaxf(lo.z - bb[5], bb[2] - hi.z));
+    const float d2 = gx * gx + gy * gy + gz * gz;
+    return d2 > cut2 * lo.w * lo.w * 1.0001f;
+}
+
+struct EvalArgs {
+    const float4* tlo;
+    const float4* thi;
+    const float4* tchi;
+    const float4* tclo;
+    int ns, ntiles, tiles_per_split;
+    const double* tx;  // SoA targets, component stride ld
+    int64_t ld;
+    int nt;
+    float cut2;
+    double* out;       // [split][4][nt] (phi, gx, gy, gz) when splitting, else [4][nt]
+    int* flag;
+    unsigned long long* pairs;  // [2] pairs evaluated in near / far tiles
+};
+
+// Block-wide sums of the pair counts, added once per CTA.
+__device__ __forceinline__ void count_pairs(unsigned long long* dst, unsigned long long n, unsigned long long f)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+        f += __shfl_xor_sync(0xffffffffu, f, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n) atomicAdd(dst, n);
+        if (f) atomicAdd(dst + 1, f);
+    }
+}
+
+// ---------------------------------------------------------------- mixed kernel
+template <int TPT>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __restrict__ spos,
+                                                            const float4* __restrict__ snw,
+                                                            const float4* __restrict__ slo, EvalArgs A)
+{
+    __shared__ __align__(128) float4 sh_pos[2][kTile];
+    __shared__ __align__(128) float4 sh_nw[2][kTile];
+    __shared__ __align__(128) float4 sh_lo[2][kTile];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float s_bb[6];
+
+    const int tid = threadIdx.x;
+    const int base = blockIdx.x * (kEvalThreads * TPT);
+    const int t0 = blockIdx.y * A.tiles_per_split;
+    const int t1 = min(A.ntiles, t0 + A.tiles_per_split);
+
+    float xh[TPT][3], xl[TPT][3];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int nvalid = 0;
+#pragma unroll
+    for (int k = 0; k < TPT; k++) {
+        const int i = base + k * kEvalThreads + tid;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double v = i < A.nt ? A.tx[c * A.ld + i] : 0.0;
+            xh[k][c] = __double2float_rn(v);
+            xl[k][c] = __double2float_rn(v - (double)xh[k][c]);
+            if (i < A.nt) {
+                lo[c] = fminf(lo[c], __double2float_rd(v));
+                hi[c] = fmaxf(hi[c], __double2float_ru(v));
+            }
+        }
+        nvalid += i < A.nt ? 1 : 0;
+    }
+    block_bbox(lo, hi, s_bb);
+
+    float acc_h[TPT][4], acc_l[TPT][4];
+#pragma unroll
+    for (int k = 0; k < TPT; k++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc_h[k][c] = acc_l[k][c] = 0.0f;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // thread 0 stages a tile; the low parts of the positions only for near tiles
+    auto issue = [&](int t, int b) {
+        const int cnt = min(kTile, A.ns - t * kTile);
+        const uint32_t bytes = (uint32_t)cnt * 16u;
+        const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+        mbar_expect_tx(&bar[b], (far ? 2u : 3u) * bytes);
+        bulk_g2s(&sh_pos[b][0], spos + (size_t)t * kTile, bytes, &bar[b]);
+        bulk_g2s(&sh_nw[b][0], snw + (size_t)t * kTile, bytes, &bar[b]);
+        if (!far) bulk_g2s(&sh_lo[b][0], slo + (size_t)t * kTile, bytes, &bar[b]);
+    };
+    if (tid == 0 && t0 < t1) issue(t0, 0);
+
+    unsigned long long pairs_near = 0, pairs_far = 0;
+    for (int t = t0; t < t1; t++) {
+        const int it = t - t0;
+        const int b = it & 1;
+        if (tid == 0 && t + 1 < t1) issue(t + 1, b ^ 1);
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), kWaitLimit);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(A.flag, kErrWaitTimeout);
+                // let any copy still in flight land before the CTA exits
+                if (t + 1 < t1) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
+            }
+            break;
+        }
+        const float4 tl = A.tlo[t], th = A.thi[t];
+        const float4 ch = A.tchi[t], cl = A.tclo[t];
+        const int cnt = min(kTile, A.ns - t * kTile);
+        const bool far = tile_is_far(s_bb, tl, th, A.cut2);
+        const float4* sp = sh_pos[b];
+        const float4* sn = sh_nw[b];
+        if (far) {
+            pairs_far += (unsigned long long)cnt * nvalid;
+            float xq[TPT][3];
+#pragma unroll
+            for (int k = 0; k < TPT; k++) {
+                xq[k][0] = (xh[k][0] - ch.x) + (xl[k][0] - cl.x);
+                xq[k][1] = (xh[k][1] - ch.y) + (xl[k][1] - cl.y);
+                xq[k][2] = (xh[k][2] - ch.z) + (xl[k][2] - cl.z);
+            }
+            // FP32 sums over chunks of kChunk sources, each folded into the
+            // float-float accumulator
+            for (int c0 = 0; c0 < cnt; c0 += kChunk) {
+                const int c1 = min(cnt, c0 + kChunk);
+                float p[TPT][4];
+#pragma unroll
+                for (int k = 0; k < TPT; k++) p[k][0] = p[k][1] = p[k][2] = p[k][3] = 0.0f;
+#pragma unroll 4
+                for (int s = c0; s < c1; s++) {
+                    const float4 y = sp[s];
+                    const float4 n = sn[s];
+#pragma unroll
+                    for (int k = 0; k < TPT; k++) {
+                        const float dx = y.x - xq[k][0], dy = y.y - xq[k][1], dz = y.z - xq[k][2];
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float ri = rsqrt_refined(r2);
+                        const float ri2 = ri * ri;
+                        const float ri3 = ri2 * ri;
+                        const float d = fmaf(n.x, dx, fmaf(n.y, dy, n.z * dz));
+                        const float q = d * ri3;
+                        p[k][0] += q;
+                        const float tq = 3.0f * q * ri2;
+                        p[k][1] = fmaf(tq, dx, fmaf(-n.x, ri3, p[k][1]));
+                        p[k][2] = fmaf(tq, dy, fmaf(-n.y, ri3, p[k][2]));
+                        p[k][3] = fmaf(tq, dz, fmaf(-n.z, ri3, p[k][3]));
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < TPT; k++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) two_sum_acc(acc_h[k][c], acc_l[k][c], p[k][c]);
+            }
+        } else {
+            pairs_near += (unsigned long long)cnt * nvalid;
+            // target offset from the tile centre as a float-float pair
+            float qh[TPT][3], ql[TPT][3];
+#pragma unroll
+            for (int k = 0; k < TPT; k++) {
+                const float cc[3] = {ch.x, ch.y, ch.z}, cc2[3] = {cl.x, cl.y, cl.z};
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float s0 = xh[k][c] - cc[c];
+                    const float bb = s0 - xh[k][c];
+                    const float e0 = (xh[k][c] - (s0 - bb)) + (-cc[c] - bb);
+                    const float tt = (xl[k][c] - cc2[c]) + e0;
+                    const float hh = s0 + tt;
+                    qh[k][c] = hh;
+                    ql[k][c] = tt - (hh - s0);
+                }
+            }
+            const float4* sl = sh_lo[b];
+            // near pairs carry the large terms: every pair is folded into the
+            // float-float accumulator
+#pragma unroll 2
+            for (int s = 0; s < cnt; s++) {
+                const float4 y = sp[s];
+                const float4 n = sn[s];
+                const float4 yl = sl[s];
+#pragma unroll
+                for (int k = 0; k < TPT; k++) {
+                    const float dx = (y.x - qh[k][0]) + (yl.x - ql[k][0]);
+                    const float dy = (y.y - qh[k][1]) + (yl.y - ql[k][1]);
+                    const float dz = (y.z - qh[k][2]) + (yl.z - ql[k][2]);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float fH, FK;
+                    radial32(r2, y.w, fH, FK);
+                    const float d = fmaf(n.x, dx, fmaf(n.y, dy, n.z * dz));
+                    const float tq = d * FK;
+                    two_sum_acc(acc_h[k][0], acc_l[k][0], d * fH);
+                    two_sum_acc(acc_h[k][1], acc_l[k][1], -fmaf(n.x, fH, tq * dx));
+                    two_sum_acc(acc_h[k][2], acc_l[k][2], -fmaf(n.y, fH, tq * dy));
+                    two_sum_acc(acc_h[k][3], acc_l[k][3], -fmaf(n.z, fH, tq * dz));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t plane = (int64_t)A.nt;
+    double* out = A.out + (int64_t)blockIdx.y * 4 * plane;
+#pragma unroll
+    for (int k = 0; k < TPT; k++) {
+        const int i = base + k * kEvalThreads + tid;
+        if (i < A.nt) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) out[c * plane + i] = (double)acc_h[k][c] + (double)acc_l[k][c];
+        }
+    }
+    count_pairs(A.pairs, pairs_near, pairs_far);
+}
+
+// ---------------------------------------------------------------- FP64 kernel
+template <int TPT>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* __restrict__ spos,
+                                                           const double4_32a* __restrict__ snw, EvalArgs A)
+{
+    __shared__ __align__(128) double4_32a sh_pos[2][kTile];
+    __shared__ __align__(128) double4_32a sh_nw[2][kTile];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float s_bb[6];
+
+    const int tid = threadIdx.x;
+    const int base = blockIdx.x * (kEvalThreads * TPT);
+    const int t0 = blockIdx.y * A.tiles_per_split;
+    const int t1 = min(A.ntiles, t0 + A.tiles_per_split);
+
+    double x[TPT][3];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int k = 0; k < TPT; k++) {
+        const int i = base + k * kEvalThreads + tid;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double v = i < A.nt ? A.tx[c * A.ld + i] : 0.0;
+            x[k][c] = v;
+            if (i < A.nt) {
+                lo[c] = fminf(lo[c], __double2float_rd(v));
+                hi[c] = fmaxf(hi[c], __double2float_ru(v));
+            }
+        }
+    }
+    block_bbox(lo, hi, s_bb);
+
+    double acc[TPT][4];
+#pragma unroll
+    for (int k = 0; k < TPT; k++) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0;
+    int nvalid = 0;
+#pragma unroll
+    for (int k = 0; k < TPT; k++) nvalid += (base + k * kEvalThreads + tid) < A.nt ? 1 : 0;
+    unsigned long long pairs_near = 0, pairs_far = 0;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int b) {
+        const int cnt = min(kTile, A.ns - t * kTile);
+        const uint32_t bytes = (uint32_t)cnt * 32u;
+        mbar_expect_tx(&bar[b], 2u * bytes);
+        bulk_g2s(&sh_pos[b][0], spos + (size_t)t * kTile, bytes, &bar[b]);
+        bulk_g2s(&sh_nw[b][0], snw + (size_t)t * kTile, bytes, &bar[b]);
+    };
+    if (tid == 0 && t0 < t1) issue(t0, 0);
+
+    for (int t = t0; t < t1; t++) {
+        const int it = t - t0;
+        const int b = it & 1;
+        if (tid == 0 && t + 1 < t1) issue(t + 1, b ^ 1);
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), kWaitLimit);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(A.flag, kErrWaitTimeout);
+                if (t + 1 < t1) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
+            }
+            break;
+        }
+        const float4 tl = A.tlo[t], th = A.thi[t];
+        const int cnt = min(kTile, A.ns - t * kTile);
+        const bool far = tile_is_far(s_bb, tl, th, A.cut2);
+        const double4_32a* sp = sh_pos[b];
+        const double4_32a* sn = sh_nw[b];
+        if (far) pairs_far += (unsigned long long)cnt * nvalid;
+        else pairs_near += (unsigned long long)cnt * nvalid;
+        if (far) {
+#pragma unroll 2
+            for (int s = 0; s < cnt; s++) {
+                const double4_32a y = sp[s];
+                const double4_32a n = sn[s];
+#pragma unroll
+                for (int k = 0; k < TPT; k++) {
+                    const double dx = y.x - x[k][0], dy = y.y - x[k][1], dz = y.z - x[k][2];
+                    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    const double ri = rsqrt(r2);
+                    const double ri2 = ri * ri;
+                    const double ri3 = ri2 * ri;
+                    const double d = fma(n.x, dx, fma(n.y, dy, n.z * dz));
+                    const double q = d * ri3;
+                    acc[k][0] += q;
+                    const double tq = 3.0 * q * ri2;
+                    acc[k][1] = fma(tq, dx, fma(-n.x, ri3, acc[k][1]));
+                    acc[k][2] = fma(tq, dy, fma(-n.y, ri3, acc[k][2]));
+                    acc[k][3] = fma(tq, dz, fma(-n.z, ri3, acc[k][3]));
+                }
+            }
+        } else {
+            for (int s = 0; s < cnt; s++) {
+                const double4_32a y = sp[s];
+                const double4_32a n = sn[s];
+#pragma unroll
+                for (int k = 0; k < TPT; k++) {
+                    const double dx = y.x - x[k][0], dy = y.y - x[k][1], dz = y.z - x[k][2];
+                    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    double fH, FK;
+                    radial64(r2, y.w, n.w, fH, FK);
+                    const double d = fma(n.x, dx, fma(n.y, dy, n.z * dz));
+                    acc[k][0] = fma(d, fH, acc[k][0]);
+                    const double tq = d * FK;
+                    acc[k][1] -= fma(n.x, fH, tq * dx);
+                    acc[k][2] -= fma(n.y, fH, tq * dy);
+                    acc[k][3] -= fma(n.z, fH, tq * dz);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t plane = (int64_t)A.nt;
+    double* out = A.out + (int64_t)blockIdx.y * 4 * plane;
+#pragma unroll
+    for (int k = 0; k < TPT; k++) {
+        const int i = base + k * kEvalThreads + tid;
+        if (i < A.nt) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) out[c * plane + i] = acc[k][c];
+        }
+    }
+    count_pairs(A.pairs, pairs_near, pairs_far);
+}
+
+// Sum of the split partials in split order into res [4][nt].
+__global__ void k_reduce_splits(const double* __restrict__ part, int nsplit, int nt, double* __restrict__ res)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < nsplit; k++)
+        for (int c = 0; c < 4; c++) s[c] += part[((int64_t)k * 4 + c) * nt + i];
+    for (int c = 0; c < 4; c++) res[(int64_t)c * nt + i] = s[c];
+}
+
+bool g_consts_ready[64] = {false};
+
+int upload_series_constants(Ctx* ctx)
+{
+    if (ctx->device >= 0 && ctx->device < 64 && g_consts_ready[ctx->device]) return LSM_OK;
+    // c_k = (-1)^{k+1} 2k / (k! (2k+1)); Hs = (2/sqrt pi) sum_{k>=1} c_k w^{k-1},
+    // Ks = (2/sqrt pi) sum_{k>=2} c_k (2k-2) w^{k-2}
+    double A[kSer64 + 1], B[kSer64];
+    double fact = 1.0;
+    double c[kSer64 + 2];
+    for (int k = 1; k <= kSer64 + 1; k++) {
+        fact *= k;
+        c[k] = ((k % 2) ? 1.0 : -1.0) * (2.0 * k) / (fact * (2.0 * k + 1.0));
+    }
+    for (int m = 0; m < kSer64; m++) {
+        A[m] = kTwoOverSqrtPi * c[m + 1];
+        B[m] = kTwoOverSqrtPi * c[m + 2] * (2.0 * (m + 2) - 2.0);
+    }
+    float A32[kSer32], B32[kSer32];
+    for (int m = 0; m < kSer32; m++) {
+        A32[m] = (float)A[m];
+        B32[m] = (float)B[m];
+    }
+    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_A64, A, sizeof(double) * kSer64));
+    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_B64, B, sizeof(double) * kSer64));
+    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_A32, A32, sizeof(A32)));
+    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_B32, B32, sizeof(B32)));
+    if (ctx->device >= 0 && ctx->device < 64) g_consts_ready[ctx->device] = true;
+    return LSM_OK;
+}
+
+#ifndef LSM_TPT32
+#define LSM_TPT32 2
+#endif
+constexpr int kTPT32 = LSM_TPT32;
+constexpr int kTPT64 = 1;
+
+}  // namespace
+
+int eval_init_constants(Ctx* ctx) { return upload_series_constants(ctx); }
+
+// Phi and grad at n sorted targets (SoA x with stride ld) into res [4][n]
+// (phi, then the three gradient components).
+int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int precision, cudaStream_t st)
+{
+    if (t.n <= 0) return LSM_OK;
+    const bool mixed = precision == LSM_MIXED;
+    const int tpb = kEvalThreads * (mixed ? kTPT32 : kTPT64);
+    const int nblk = (t.n + tpb - 1) / tpb;
+    const int ntiles = (int)me->ntiles;
+    // split the tile range so that the grid covers the GPU a few times over
+    const int want = ctx->num_sms * 16;
+    int nsplit = 1;
+    if (nblk < want) nsplit = std::min((want + nblk - 1) / nblk, std::max(1, ntiles / 4));
+    const int tps = (ntiles + nsplit - 1) / nsplit;
+    nsplit = (ntiles + tps - 1) / tps;
+
+    Scratch s(st);
+    double* part = res;
+    if (nsplit > 1) LSM_CUDA_TRY(ctx, s.get(&part, (size_t)nsplit * 4 * t.n));
+    EvalArgs A;
+    A.tlo = me->tile_lo;
+    A.thi = me->tile_hi;
+    A.tchi = me->tile_chi;
+    A.tclo = me->tile_clo;
+    A.ns = (int)me->ns;
+    A.ntiles = ntiles;
+    A.tiles_per_split = tps;
+    A.tx = t.x;
+    A.ld = t.ld;
+    A.nt = t.n;
+    const double cut = mixed ? ctx->opt.cutoff_mixed : ctx->opt.cutoff_fp64;
+    A.cut2 = (float)(cut * cut);
+    A.out = part;
+    A.flag = ctx->d_flag;
+    A.pairs = ctx->d_pairs;
+    dim3 grid(nblk, nsplit);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (ctx->profiling) {
+        LSM_CUDA_TRY(ctx, cudaEventCreate(&ev0));
+        LSM_CUDA_TRY(ctx, cudaEventCreate(&ev1));
+        LSM_CUDA_TRY(ctx, cudaEventRecord(ev0, st));
+    }
+    if (mixed) {
+        k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, A);
+    } else {
+        k_eval_fp64<kTPT64><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
+    }
+    LSM_LAUNCHED(ctx);
+    if (ctx->profiling) {
+        LSM_CUDA_TRY(ctx, cudaEventRecord(ev1, st));
+        ctx->prof_events.emplace_back(ev0, ev1);
+    }
+    if (nsplit > 1) {
+        k_reduce_splits<<<(t.n + 255) / 256, 256, 0, st>>>(part, nsplit, t.n, res);
+        LSM_LAUNCHED(ctx);
+    }
+    return LSM_OK;
+}
+
+}  // namespace lsm

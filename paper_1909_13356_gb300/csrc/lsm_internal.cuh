@@ -1,0 +1,144 @@
+// lsm_internal.cuh -- internal types and helpers of liblsm (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "lsm.h"
+
+namespace lsm {
+
+// Source nodes per tile.  Tiles are runs of consecutive Morton-sorted source
+// nodes; a tile is the unit of the near/far decision and of shared-memory
+// staging in the pair kernels.
+constexpr int kTile = 128;
+// Targets per thread block row of the pair kernels (threads * targets/thread).
+constexpr int kEvalThreads = 128;
+
+struct Ctx {
+    int device = 0;
+    int num_sms = 0;
+    lsm_options opt{};
+    std::string err;
+    int64_t launches = 0;
+    int* d_flag = nullptr;   // device error word (bounded waits, bad sizes)
+    unsigned long long* d_pairs = nullptr;  // [2]: pairs evaluated in near / far tiles
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+};
+
+struct Mesh {
+    Ctx* ctx = nullptr;
+    int64_t nv = 0, m = 0, ns = 0, ntiles = 0;
+    int nq = 0;
+    lsm_quad rule{4, 0};
+    double sigma_min = 0, sigma_max = 0;
+    size_t bytes = 0;
+    // geometry, triangle order of the input
+    double* verts = nullptr;     // [nv][3]
+    int32_t* tris = nullptr;     // [m][3]
+    double* tri_sigma = nullptr; // [m]
+    double* tri_n = nullptr;     // [m][3] N = T_u x T_v (not normalised)
+    double* vpn = nullptr;       // [nv][3] vertex pseudonormals
+    // sources in Morton order
+    double4_32a* s64_pos = nullptr;  // (x, y, z, a = 1/(sqrt2 sigma))
+    double4_32a* s64_nw = nullptr;   // (nw / 4 pi, 0)
+    float4* s32_pos = nullptr;   // (y - c_tile in FP32, a)
+    float4* s32_nw = nullptr;    // (nw / 4 pi, sqrt2 sigma) in FP32
+    float4* s32_lo = nullptr;    // FP32 remainder of the tile-local position, 0
+    float4* tile_lo = nullptr;   // bbox lower corner rounded down, w = sigma_max rounded up
+    float4* tile_hi = nullptr;   // bbox upper corner rounded up
+    float4* tile_chi = nullptr;  // tile centre, FP32 high part
+    float4* tile_clo = nullptr;  // tile centre, FP32 remainder
+};
+
+// ---------------------------------------------------------------- errors
+#define LSM_CUDA_TRY(ctx, call)                                                   \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);      \
+            return LSM_E_CUDA;                                                    \
+        }                                                                         \
+    } while (0)
+
+#define LSM_LAUNCHED(ctx)                                                         \
+    do {                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                      \
+        (ctx)->launches++;                                                        \
+        if (e_ != cudaSuccess) {                                                  \
+            (ctx)->err = std::string("kernel launch: ") + cudaGetErrorString(e_); \
+            return LSM_E_CUDA;                                                    \
+        }                                                                         \
+    } while (0)
+
+// ---------------------------------------------------------------- scratch
+// Stream-ordered scratch allocation for one call.
+struct Scratch {
+    cudaStream_t st;
+    void* ptrs[32];
+    int n = 0;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    template <class T>
+    cudaError_t get(T** p, size_t count) {
+        if (n >= 32) return cudaErrorMemoryAllocation;
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 16, st);
+        if (e != cudaSuccess) return e;
+        ptrs[n++] = q;
+        *p = reinterpret_cast<T*>(q);
+        return cudaSuccess;
+    }
+    ~Scratch() {
+        for (int i = 0; i < n; i++) cudaFreeAsync(ptrs[i], st);
+    }
+};
+
+// ---------------------------------------------------------------- launches
+// sort.cu
+int radix_sort_pairs(Ctx* ctx, uint32_t* keys, uint32_t* vals, int n, int key_bits,
+                     cudaStream_t st);
+int compact_flags(Ctx* ctx, const int32_t* flags, int want, const int32_t* in, int n,
+                  int32_t* out, int32_t* d_count, cudaStream_t st);
+
+// geometry.cu
+int build_mesh_device(Ctx* ctx, Mesh* mesh, const double* sigma_in_dev, const double* rule_dev,
+                      double* host_vol, cudaStream_t st);
+int morton_order_points(Ctx* ctx, const double* pts, int stride, int n, uint32_t* perm,
+                        cudaStream_t st);
+int chart_nodes_init(Ctx* ctx, const Mesh* mesh, const double* chart_rule_dev, int np,
+                     double* x0, double* hdir, double* sloc, cudaStream_t st);
+
+// eval.cu
+struct Targets {
+    const double* x;  // SoA: x[0..n), y = x + ld, z = x + 2 ld
+    int64_t ld;
+    int n;
+};
+int eval_init_constants(Ctx* ctx);
+int eval_sorted(Ctx* ctx, const Mesh* mesh, const Targets& t, double* res, int precision,
+                cudaStream_t st);
+
+// newton.cu
+int solve_charts_device(Ctx* ctx, Mesh* mesh, int n_gl, double tol, int max_iter,
+                        int precision, double* x_out, double* h_out, int32_t* status_out,
+                        lsm_solve_stats* stats, cudaStream_t st);
+
+// host helpers (api.cu)
+void simplex_rule_host(int n, int subdiv, double* uvw);  // [cnt][3]
+
+}  // namespace lsm
+
+struct lsm_ctx {
+    lsm::Ctx c;
+};
+struct lsm_mesh {
+    lsm::Mesh m;
+};

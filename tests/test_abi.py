@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/lsm.h declares.  No compute call is made here (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1909_13356_gb300 as lsm
+from paper_1909_13356_gb300 import build as lsm_build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "lsm.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(lsm_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("lsm_create", "lsm_mesh_upload", "lsm_eval_phi_grad", "lsm_solve_charts"):
+        assert s in syms
+    assert set(syms) == set(lsm.EXPORTS)
+
+
+def test_library_builds_and_exports_every_symbol():
+    path = lsm_build.build()
+    L = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert hasattr(L, s), s
+
+
+def test_library_is_built_for_sm_103a():
+    assert "arch=compute_103a,code=sm_103a" in " ".join(lsm_build.ARCH)
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle and the CUDA path are independent: neither includes or
+    imports the other."""
+    root = os.path.dirname(os.path.dirname(__file__))
+    bad = re.compile(r"(import\s+oracle|from\s+oracle|#include\s+[\"<].*oracle)")
+    for dirpath, _, files in os.walk(os.path.join(root, "paper_1909_13356_gb300")):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                assert not bad.search(open(os.path.join(dirpath, f)).read()), f
+    for f in ("oracle.c", "__init__.py"):
+        txt = open(os.path.join(root, "oracle", f)).read()
+        assert "lsm.h" not in txt and "paper_1909_13356_gb300" not in txt
+
+
+def test_create_without_device_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lsm.LsmError):
+        lsm.Context(0)
