@@ -185,6 +185,37 @@ int lsm_eval_phi_grad(lsm_mesh* mesh, const double* x, int64_t n, double* phi, d
                       int precision, void* stream);
 
 /*
+ * Phi and grad Phi at n targets without allocating any memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc while they run -- for example a latency-critical loop in which
+ * an allocation or free could synchronise the device, or a process whose
+ * device memory is already reserved in full by another allocator (a
+ * framework's caching pool), so that a further cudaMalloc would fail.
+ *
+ * It computes what lsm_eval_phi_grad computes, with the same kernels and
+ * tolerances, but it does not sort the targets (they are evaluated in the
+ * caller's order) and it takes its scratch from one fixed device array of
+ * 8 MiB inside the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   x     double[n][3], device pointer
+ *   phi   double[n], device pointer
+ *   grad  double[n][3], device pointer, or NULL
+ *   n     0 <= n <= 16384; larger n returns LSM_E_INVALID_ARG with a
+ *         message naming the limit.  Host pointers also return
+ *         LSM_E_INVALID_ARG.
+ * Asynchronous on `stream`.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one array and leaves its contents behind for the next call; the kernels
+ * overwrite every element they read, so nothing needs clearing, but calls
+ * whose executions overlap on the GPU (different streams, or several host
+ * threads) race on the array and must be serialised by the caller.
+ */
+int lsm_eval_phi_grad_noalloc(lsm_mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
+                              int precision, void* stream);
+
+/*
  * Chart nodes on Phi = 1/2 (Sec. 3.2): for each triangle j and each node
  * (u_i, v_i) of the Duffy n x n chart rule with n = order/2 + 2, Newton's
  * method on h (eq. newtoneq) from h = 0:

@@ -36,7 +36,7 @@ _ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVER
 # every symbol include/lsm.h declares
 EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "lsm_set_profiling",
            "lsm_read_stats", "lsm_mesh_upload", "lsm_mesh_free", "lsm_mesh_get_info", "lsm_eval_phi_grad",
-           "lsm_solve_charts")
+           "lsm_eval_phi_grad_noalloc", "lsm_solve_charts")
 
 
 class LsmError(RuntimeError):
@@ -117,6 +117,7 @@ def load(build_if_needed: bool = True):
         L.lsm_mesh_free.argtypes = [P]
         L.lsm_mesh_get_info.argtypes = [P, ctypes.POINTER(_Info)]
         L.lsm_eval_phi_grad.argtypes = [P, P, I64, P, P, I32, P]
+        L.lsm_eval_phi_grad_noalloc.argtypes = [P, P, I64, P, P, I32, P]
         L.lsm_solve_charts.argtypes = [P, I32, D, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int

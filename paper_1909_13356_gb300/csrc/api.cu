@@ -515,4 +515,14 @@ int lsm_solve_charts(lsm_mesh* mh, int order, double tol, int max_iter, int prec
     return check_flag(ctx, st);
 }
 
+int lsm_eval_phi_grad_noalloc(lsm_mesh* mh, const double* x, int64_t n, double* phi, double* grad,
+                              int precision, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    DeviceGuard g(ctx->device);
+    return eval_noalloc(ctx, me, x, n, phi, grad, precision, (cudaStream_t)stream);
+}
+
 }  // extern "C"

@@ -31,6 +31,7 @@
 // are returned in FP64.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "lsm_internal.cuh"
 
@@ -673,6 +674,141 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         k_reduce_splits<<<(t.n + 255) / 256, 256, 0, st>>>(part, nsplit, t.n, res);
         LSM_LAUNCHED(ctx);
     }
+    return LSM_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation variant
+//
+// lsm_eval_phi_grad_noalloc runs the same pair kernels without allocating:
+// its scratch (SoA targets, result planes, split partials) lives in one
+// file-scope device array.  The array's name is a host-side stand-in in host
+// code, so its device address is fetched once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;   // 8 MiB on every device that loads the library
+constexpr int kNoAllocMaxTargets = 16384;                  // 7 doubles per target for targets and results
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_dev_ptr[64] = {nullptr};
+
+__global__ void k_noalloc_to_soa(const double* __restrict__ x, int n, double* __restrict__ T)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < 3; c++) T[(int64_t)c * n + i] = x[3 * (int64_t)i + c];
+}
+
+__global__ void k_noalloc_store(const double* __restrict__ R, int n, double* __restrict__ phi,
+                                double* __restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    phi[i] = R[i];
+    if (grad) {
+        for (int c = 0; c < 3; c++) grad[3 * (int64_t)i + c] = R[(int64_t)(c + 1) * n + i];
+    }
+}
+
+bool on_device(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+int eval_noalloc(Ctx* ctx, const Mesh* me, const double* x, int64_t n, double* phi, double* grad,
+                 int precision, cudaStream_t st)
+{
+    if (n == 0) return LSM_OK;
+    if (n < 0 || n > kNoAllocMaxTargets) {
+        ctx->err = "eval_phi_grad_noalloc: n = " + std::to_string(n) + " is outside [0, " +
+                   std::to_string(kNoAllocMaxTargets) + "], the size its fixed 8 MiB scratch holds";
+        return LSM_E_INVALID_ARG;
+    }
+    if (!x || !phi || (precision != LSM_FP64 && precision != LSM_MIXED)) {
+        ctx->err = "eval_phi_grad_noalloc: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    if (!on_device(x) || !on_device(phi) || (grad && !on_device(grad))) {
+        ctx->err = "eval_phi_grad_noalloc: x, phi and grad must be device pointers";
+        return LSM_E_INVALID_ARG;
+    }
+    if (ctx->device < 0 || ctx->device >= 64) {
+        ctx->err = "eval_phi_grad_noalloc: device index out of range";
+        return LSM_E_INVALID_ARG;
+    }
+    // set-up, once per device, with the context's device current
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_dev_ptr[ctx->device]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                ctx->err = std::string("eval_phi_grad_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+                return LSM_E_CUDA;
+            }
+            g_noalloc_dev_ptr[ctx->device] = p;
+        }
+        base = static_cast<unsigned char*>(g_noalloc_dev_ptr[ctx->device]);
+    }
+    const int nt = (int)n;
+    double* T = reinterpret_cast<double*>(base);
+    double* R = T + 3 * (size_t)nt;
+    double* part = R + 4 * (size_t)nt;
+    const size_t room = kNoAllocScratchBytes - sizeof(double) * 7 * (size_t)nt;
+    const int max_split = (int)std::max<size_t>(1, room / (sizeof(double) * 4 * (size_t)nt));
+
+    const bool mixed = precision == LSM_MIXED;
+    const int tpb = kEvalThreads * (mixed ? kTPT32 : kTPT64);
+    const int nblk = (nt + tpb - 1) / tpb;
+    const int ntiles = (int)me->ntiles;
+    const int want = ctx->num_sms * 16;
+    int nsplit = 1;
+    if (nblk < want) nsplit = std::min((want + nblk - 1) / nblk, std::max(1, ntiles / 4));
+    nsplit = std::min(nsplit, max_split);
+    const int tps = (ntiles + nsplit - 1) / nsplit;
+    nsplit = (ntiles + tps - 1) / tps;
+
+    k_noalloc_to_soa<<<(nt + 255) / 256, 256, 0, st>>>(x, nt, T);
+    LSM_LAUNCHED(ctx);
+    EvalArgs A;
+    A.tlo = me->tile_lo;
+    A.thi = me->tile_hi;
+    A.tchi = me->tile_chi;
+    A.tclo = me->tile_clo;
+    A.ns = (int)me->ns;
+    A.ntiles = ntiles;
+    A.tiles_per_split = tps;
+    A.tx = T;
+    A.ld = nt;
+    A.nt = nt;
+    const double cut = mixed ? ctx->opt.cutoff_mixed : ctx->opt.cutoff_fp64;
+    A.cut2 = (float)(cut * cut);
+    A.out = nsplit > 1 ? part : R;
+    A.flag = ctx->d_flag;
+    A.pairs = ctx->d_pairs;
+    dim3 grid(nblk, nsplit);
+    if (mixed) {
+        k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, A);
+    } else {
+        k_eval_fp64<kTPT64><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
+    }
+    LSM_LAUNCHED(ctx);
+    if (nsplit > 1) {
+        k_reduce_splits<<<(nt + 255) / 256, 256, 0, st>>>(part, nsplit, nt, R);
+        LSM_LAUNCHED(ctx);
+    }
+    k_noalloc_store<<<(nt + 255) / 256, 256, 0, st>>>(R, nt, phi, grad);
+    LSM_LAUNCHED(ctx);
     return LSM_OK;
 }
 

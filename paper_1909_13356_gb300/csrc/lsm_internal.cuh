@@ -125,6 +125,8 @@ struct Targets {
 int eval_init_constants(Ctx* ctx);
 int eval_sorted(Ctx* ctx, const Mesh* mesh, const Targets& t, double* res, int precision,
                 cudaStream_t st);
+int eval_noalloc(Ctx* ctx, const Mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
+                 int precision, cudaStream_t st);
 
 // newton.cu
 int solve_charts_device(Ctx* ctx, Mesh* mesh, int n_gl, double tol, int max_iter,
