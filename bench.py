@@ -121,10 +121,11 @@ def cpu_baseline(w, seconds: float, rule_n: int):
     m = w["mesh"]
     y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, rule_n, 0)
     x = w["targets"]
+    ncal = 8 * (os.cpu_count() or 1)
     t0 = time.perf_counter()
-    oracle.phi_grad(y, nw, sg, x[:8])
+    oracle.phi_grad(y, nw, sg, x[:ncal])
     dt = time.perf_counter() - t0
-    n = int(max(8, min(len(x), 8 * seconds / max(dt, 1e-6))))
+    n = int(max(ncal, min(len(x), ncal * seconds / max(dt, 1e-6))))
     t0 = time.perf_counter()
     oracle.phi_grad(y, nw, sg, x[:n])
     dt = time.perf_counter() - t0
@@ -142,10 +143,11 @@ def run_reference(args, rank, world):
     m = w["mesh"]
     y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, w["rule"]["n"], 0)
     x = w["targets"]
+    ncal = 8 * (os.cpu_count() or 1)
     t0 = time.perf_counter()
-    oracle.phi_grad(y, nw, sg, x[:8])
-    per = (time.perf_counter() - t0) / 8
-    n = int(max(8, min(2000, 20.0 / max(per, 1e-9) / max(1, args.steps + args.warmup))))
+    oracle.phi_grad(y, nw, sg, x[:ncal])
+    per = (time.perf_counter() - t0) / ncal
+    n = int(max(ncal, min(len(x), 60.0 / max(per, 1e-9) / max(1, args.steps + args.warmup))))
     for _ in range(args.warmup):
         oracle.phi_grad(y, nw, sg, x[:n])
     t0 = time.perf_counter()
