@@ -54,9 +54,12 @@ typedef enum {
 
 typedef enum {
     LSM_FP64 = 0,   /* every kernel in FP64 */
-    LSM_MIXED = 1   /* FP32 pair kernels, compensated per-tile accumulation,
-                       FP64 results; Newton finishes with FP64 steps when the
-                       tolerance asks for more than FP32 gives */
+    LSM_MIXED = 1,  /* FP32 pair kernels, compensated per-tile accumulation,
+                       FP64 results; Newton finishes with LSM_FF steps when
+                       the tolerance asks for more than FP32 gives */
+    LSM_FF = 2      /* Phi to FP64 accuracy on the FP32 pipes: far tiles in
+                       float-float arithmetic (about 44 significant bits),
+                       near tiles in FP64; grad Phi to mixed accuracy */
 } lsm_precision;
 
 /* Per-node status of the chart solve (low byte); bit 8 set when a Newton
@@ -178,7 +181,7 @@ int lsm_mesh_get_info(const lsm_mesh* mesh, lsm_mesh_info* out);
  *   x     double[n][3] targets
  *   phi   double[n] out
  *   grad  double[n][3] out, or NULL
- *   precision  LSM_FP64 or LSM_MIXED
+ *   precision  LSM_FP64, LSM_MIXED or LSM_FF
  * n == 0 is a no-op.  Errors: LSM_E_INVALID_ARG, LSM_E_CUDA.
  */
 int lsm_eval_phi_grad(lsm_mesh* mesh, const double* x, int64_t n, double* phi, double* grad,

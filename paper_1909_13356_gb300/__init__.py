@@ -20,10 +20,11 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["FP64", "MIXED", "Context", "Mesh", "SolveStats", "LsmError", "lib", "load"]
+__all__ = ["FP64", "MIXED", "FF", "Context", "Mesh", "SolveStats", "LsmError", "lib", "load"]
 
 FP64 = 0
 MIXED = 1
+FF = 2
 
 NODE_CONVERGED = 0
 NODE_MAXITER = 1

@@ -365,7 +365,7 @@ int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* 
     const size_t ntl = (size_t)me->ntiles;
     if (!alloc(&me->verts, 3 * nv) || !alloc(&me->tris, 3 * nt) || !alloc(&me->tri_sigma, nt) ||
         !alloc(&me->tri_n, 3 * nt) || !alloc(&me->vpn, 3 * nv) || !alloc(&me->s64_pos, ns) ||
-        !alloc(&me->s64_nw, ns) || !alloc(&me->s32_pos, ns) || !alloc(&me->s32_nw, ns) || !alloc(&me->s32_lo, ns) ||
+        !alloc(&me->s64_nw, ns) || !alloc(&me->s32_pos, ns) || !alloc(&me->s32_nw, ns) || !alloc(&me->s32_lo, ns) || !alloc(&me->s32_nwlo, ns) ||
         !alloc(&me->tile_lo, ntl) || !alloc(&me->tile_hi, ntl) || !alloc(&me->tile_chi, ntl) ||
         !alloc(&me->tile_clo, ntl)) {
         cudaGetLastError();
@@ -416,7 +416,7 @@ int lsm_mesh_free(lsm_mesh* mh)
     Mesh* me = &mh->m;
     DeviceGuard g(me->ctx ? me->ctx->device : 0);
     void* ps[] = {me->verts, me->tris, me->tri_sigma, me->tri_n, me->vpn, me->s64_pos, me->s64_nw,
-                  me->s32_pos, me->s32_nw, me->s32_lo, me->tile_lo, me->tile_hi, me->tile_chi, me->tile_clo};
+                  me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, me->tile_lo, me->tile_hi, me->tile_chi, me->tile_clo};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete mh;
@@ -445,7 +445,7 @@ int lsm_eval_phi_grad(lsm_mesh* mh, const double* x, int64_t n, double* phi, dou
     Ctx* ctx = me->ctx;
     if (n == 0) return LSM_OK;
     if (n < 0 || n >= ((int64_t)1 << 31) || !x || !phi ||
-        (precision != LSM_FP64 && precision != LSM_MIXED)) {
+        (precision != LSM_FP64 && precision != LSM_MIXED && precision != LSM_FF)) {
         ctx->err = "eval_phi_grad: bad arguments";
         return LSM_E_INVALID_ARG;
     }

@@ -186,6 +186,15 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
     lo += err;
 }
 
+__device__ __forceinline__ void two_sum_acc64(double& hi, double& lo, double x)
+{
+    const double s = hi + x;
+    const double bp = s - hi;
+    const double err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
 // Block-wide min/max of three floats each, result in shared s[0..6).
 __device__ __forceinline__ void block_bbox(float lo[3], float hi[3], float* s)
 {
@@ -469,9 +478,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
     }
     block_bbox(lo, hi, s_bb);
 
-    double acc[TPT][4];
+    double acc[TPT][4], accl[TPT][4];   // running sums, double-double
 #pragma unroll
-    for (int k = 0; k < TPT; k++) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0;
+    for (int k = 0; k < TPT; k++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[k][c] = accl[k][c] = 0.0;
     int nvalid = 0;
 #pragma unroll
     for (int k = 0; k < TPT; k++) nvalid += (base + k * kEvalThreads + tid) < A.nt ? 1 : 0;
@@ -511,6 +522,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
         const double4_32a* sn = sh_nw[b];
         if (far) pairs_far += (unsigned long long)cnt * nvalid;
         else pairs_near += (unsigned long long)cnt * nvalid;
+        double p[TPT][4];
+#pragma unroll
+        for (int k = 0; k < TPT; k++) p[k][0] = p[k][1] = p[k][2] = p[k][3] = 0.0;
         if (far) {
 #pragma unroll 2
             for (int s = 0; s < cnt; s++) {
@@ -525,11 +539,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
                     const double ri3 = ri2 * ri;
                     const double d = fma(n.x, dx, fma(n.y, dy, n.z * dz));
                     const double q = d * ri3;
-                    acc[k][0] += q;
+                    p[k][0] += q;
                     const double tq = 3.0 * q * ri2;
-                    acc[k][1] = fma(tq, dx, fma(-n.x, ri3, acc[k][1]));
-                    acc[k][2] = fma(tq, dy, fma(-n.y, ri3, acc[k][2]));
-                    acc[k][3] = fma(tq, dz, fma(-n.z, ri3, acc[k][3]));
+                    p[k][1] = fma(tq, dx, fma(-n.x, ri3, p[k][1]));
+                    p[k][2] = fma(tq, dy, fma(-n.y, ri3, p[k][2]));
+                    p[k][3] = fma(tq, dz, fma(-n.z, ri3, p[k][3]));
                 }
             }
         } else {
@@ -543,14 +557,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
                     double fH, FK;
                     radial64(r2, y.w, n.w, fH, FK);
                     const double d = fma(n.x, dx, fma(n.y, dy, n.z * dz));
-                    acc[k][0] = fma(d, fH, acc[k][0]);
+                    p[k][0] = fma(d, fH, p[k][0]);
                     const double tq = d * FK;
-                    acc[k][1] -= fma(n.x, fH, tq * dx);
-                    acc[k][2] -= fma(n.y, fH, tq * dy);
-                    acc[k][3] -= fma(n.z, fH, tq * dz);
+                    p[k][1] -= fma(n.x, fH, tq * dx);
+                    p[k][2] -= fma(n.y, fH, tq * dy);
+                    p[k][3] -= fma(n.z, fH, tq * dz);
                 }
             }
         }
+#pragma unroll
+        for (int k = 0; k < TPT; k++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) two_sum_acc64(acc[k][c], accl[k][c], p[k][c]);
         __syncthreads();
     }
     const int64_t plane = (int64_t)A.nt;
@@ -560,8 +578,227 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
         const int i = base + k * kEvalThreads + tid;
         if (i < A.nt) {
 #pragma unroll
-            for (int c = 0; c < 4; c++) out[c * plane + i] = acc[k][c];
+            for (int c = 0; c < 4; c++) out[c * plane + i] = acc[k][c] + accl[k][c];
         }
+    }
+    count_pairs(A.pairs, pairs_near, pairs_far);
+}
+
+// ---------------------------------------------------------------- float-float kernel
+// Phi to FP64 accuracy without the FP64 pipe for far tiles: every far-tile
+// quantity that Phi depends on is carried as an unevaluated sum of two
+// floats (about 44 significant bits): the tile-local pair difference, |r|^2,
+// 1/|r| (hardware estimate plus one Newton step evaluated in float-float),
+// 1/|r|^3, nw . r and their product.  grad Phi of far tiles uses the FP32
+// high parts (it only steers Newton).  Near tiles run the FP64 code path.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e)
+{
+    s = a - b;
+    const float bb = s - a;
+    e = (a - (s - bb)) - (b + bb);
+}
+
+constexpr int kFFStage = kTile * 64;  // bytes per stage: 4 float4 or 2 double4 arrays
+
+__global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
+    const float4* __restrict__ spos, const float4* __restrict__ snw, const float4* __restrict__ slo,
+    const float4* __restrict__ snwlo, const double4_32a* __restrict__ dpos, const double4_32a* __restrict__ dnw,
+    EvalArgs A)
+{
+    __shared__ __align__(128) unsigned char sh[2][kFFStage];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float s_bb[6];
+
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kEvalThreads + tid;
+    const int t0 = blockIdx.y * A.tiles_per_split;
+    const int t1 = min(A.ntiles, t0 + A.tiles_per_split);
+    const bool valid = i < A.nt;
+
+    double x[3];
+    float xh[3], xl[3];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        x[c] = valid ? A.tx[c * A.ld + i] : 0.0;
+        xh[c] = __double2float_rn(x[c]);
+        xl[c] = __double2float_rn(x[c] - (double)xh[c]);
+        if (valid) {
+            lo[c] = __double2float_rd(x[c]);
+            hi[c] = __double2float_ru(x[c]);
+        }
+    }
+    block_bbox(lo, hi, s_bb);
+
+    double accd[4] = {0.0, 0.0, 0.0, 0.0};   // near tiles, FP64 (double-double sum)
+    double accl[4] = {0.0, 0.0, 0.0, 0.0};
+    float ph = 0.0f, pl = 0.0f;               // far Phi, float-float
+    float gh[3] = {0.0f, 0.0f, 0.0f}, gl[3] = {0.0f, 0.0f, 0.0f};  // far grad, compensated FP32
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int b) {
+        const int cnt = min(kTile, A.ns - t * kTile);
+        const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+        mbar_expect_tx(&bar[b], (uint32_t)cnt * 64u);
+        const size_t o = (size_t)t * kTile;
+        if (far) {
+            const uint32_t by = (uint32_t)cnt * 16u;
+            bulk_g2s(sh[b] + 0 * kTile * 16, spos + o, by, &bar[b]);
+            bulk_g2s(sh[b] + 1 * kTile * 16, snw + o, by, &bar[b]);
+            bulk_g2s(sh[b] + 2 * kTile * 16, slo + o, by, &bar[b]);
+            bulk_g2s(sh[b] + 3 * kTile * 16, snwlo + o, by, &bar[b]);
+        } else {
+            const uint32_t by = (uint32_t)cnt * 32u;
+            bulk_g2s(sh[b] + 0, dpos + o, by, &bar[b]);
+            bulk_g2s(sh[b] + kTile * 32, dnw + o, by, &bar[b]);
+        }
+    };
+    if (tid == 0 && t0 < t1) issue(t0, 0);
+
+    unsigned long long pairs_near = 0, pairs_far = 0;
+    for (int t = t0; t < t1; t++) {
+        const int it = t - t0;
+        const int b = it & 1;
+        if (tid == 0 && t + 1 < t1) issue(t + 1, b ^ 1);
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), kWaitLimit);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(A.flag, kErrWaitTimeout);
+                if (t + 1 < t1) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
+            }
+            break;
+        }
+        const int cnt = min(kTile, A.ns - t * kTile);
+        const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+        if (far) {
+            pairs_far += valid ? cnt : 0;
+            const float4 ch = A.tchi[t], cl = A.tclo[t];
+            const float cc[3] = {ch.x, ch.y, ch.z}, cc2[3] = {cl.x, cl.y, cl.z};
+            float qh[3], ql[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float s0, e0;
+                two_diff(xh[c], cc[c], s0, e0);
+                const float tt = (xl[c] - cc2[c]) + e0;
+                qh[c] = s0 + tt;
+                ql[c] = tt - (qh[c] - s0);
+            }
+            const float4* sp = reinterpret_cast<const float4*>(sh[b]);
+            const float4* sn = sp + kTile;
+            const float4* sl = sp + 2 * kTile;
+            const float4* snl = sp + 3 * kTile;
+            for (int c0 = 0; c0 < cnt; c0 += kChunk) {
+                const int c1 = min(cnt, c0 + kChunk);
+                float g[3] = {0.0f, 0.0f, 0.0f};
+                float cph = 0.0f, cpl = 0.0f;   // this chunk's Phi, float-float
+#pragma unroll 2
+                for (int s = c0; s < c1; s++) {
+                    const float4 y = sp[s], n = sn[s], yl = sl[s], nl = snl[s];
+                    float dxh, dxl, dyh, dyl, dzh, dzl, e;
+                    two_diff(y.x, qh[0], dxh, e);
+                    dxl = e + (yl.x - ql[0]);
+                    two_diff(y.y, qh[1], dyh, e);
+                    dyl = e + (yl.y - ql[1]);
+                    two_diff(y.z, qh[2], dzh, e);
+                    dzl = e + (yl.z - ql[2]);
+                    // |r|^2
+                    const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
+                    float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
+                    e0 = fmaf(2.0f * dxh, dxl, e0);
+                    e1 = fmaf(2.0f * dyh, dyl, e1);
+                    e2 = fmaf(2.0f * dzh, dzl, e2);
+                    float s01, t01, rh, t2;
+                    two_sum(p0, p1, s01, t01);
+                    two_sum(s01, p2, rh, t2);
+                    const float rl = ((e0 + e1) + e2) + (t01 + t2);
+                    // 1/|r| = r0 (1 + delta/2), delta = 1 - |r|^2 r0^2
+                    const float r0 = rsqrtf(rh);
+                    const float a = r0 * r0, ae = fmaf(r0, r0, -a);
+                    const float hh = rh * a;
+                    float he = fmaf(rh, a, -hh);
+                    he = fmaf(rh, ae, he);
+                    he = fmaf(rl, a, he);
+                    const float delta = (1.0f - hh) - he;
+                    const float ril = 0.5f * r0 * delta;
+                    // 1/|r|^3
+                    const float q2l = fmaf(2.0f * r0, ril, ae);
+                    const float q3h = a * r0;
+                    const float q3l = fmaf(a, r0, -q3h) + fmaf(a, ril, q2l * r0);
+                    // nw . r
+                    const float d0 = n.x * dxh, d1 = n.y * dyh, d2 = n.z * dzh;
+                    const float f0 = fmaf(n.x, dxh, -d0), f1 = fmaf(n.y, dyh, -d1), f2 = fmaf(n.z, dzh, -d2);
+                    float sd, u1, dh, u2;
+                    two_sum(d0, d1, sd, u1);
+                    two_sum(sd, d2, dh, u2);
+                    const float dl = ((f0 + f1) + f2) + (u1 + u2) +
+                                     fmaf(n.x, dxl, fmaf(n.y, dyl, n.z * dzl)) +
+                                     fmaf(nl.x, dxh, fmaf(nl.y, dyh, nl.z * dzh));
+                    // q = (nw . r) / |r|^3, added to the float-float Phi
+                    const float qh_ = dh * q3h;
+                    const float ql_ = fmaf(dh, q3h, -qh_) + fmaf(dh, q3l, dl * q3h);
+                    float sph, tph;
+                    two_sum(cph, qh_, sph, tph);
+                    cph = sph;
+                    cpl += tph + ql_;
+                    // grad from the high parts
+                    const float rif = r0 + ril;
+                    const float ri2 = rif * rif;
+                    const float ri3 = ri2 * rif;
+                    const float tq = 3.0f * dh * ri3 * ri2;
+                    g[0] = fmaf(tq, dxh, fmaf(-n.x, ri3, g[0]));
+                    g[1] = fmaf(tq, dyh, fmaf(-n.y, ri3, g[1]));
+                    g[2] = fmaf(tq, dzh, fmaf(-n.z, ri3, g[2]));
+                }
+#pragma unroll
+                for (int c = 0; c < 3; c++) two_sum_acc(gh[c], gl[c], g[c]);
+                // fold the chunk into the running float-float Phi and renormalise
+                float sh_, eh_;
+                two_sum(ph, cph, sh_, eh_);
+                eh_ += pl + cpl;
+                ph = sh_ + eh_;
+                pl = eh_ - (ph - sh_);
+            }
+        } else {
+            pairs_near += valid ? cnt : 0;
+            const double4_32a* sp = reinterpret_cast<const double4_32a*>(sh[b]);
+            const double4_32a* sn = reinterpret_cast<const double4_32a*>(sh[b] + kTile * 32);
+            double p[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int s = 0; s < cnt; s++) {
+                const double4_32a y = sp[s];
+                const double4_32a n = sn[s];
+                const double dx = y.x - x[0], dy = y.y - x[1], dz = y.z - x[2];
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                double fH, FK;
+                radial64(r2, y.w, n.w, fH, FK);
+                const double d = fma(n.x, dx, fma(n.y, dy, n.z * dz));
+                p[0] = fma(d, fH, p[0]);
+                const double tq = d * FK;
+                p[1] -= fma(n.x, fH, tq * dx);
+                p[2] -= fma(n.y, fH, tq * dy);
+                p[3] -= fma(n.z, fH, tq * dz);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) two_sum_acc64(accd[c], accl[c], p[c]);
+        }
+        __syncthreads();
+    }
+    if (valid) {
+        const int64_t plane = (int64_t)A.nt;
+        double* out = A.out + (int64_t)blockIdx.y * 4 * plane;
+        out[i] = (accd[0] + ((double)ph + (double)pl)) + accl[0];
+        for (int c = 0; c < 3; c++)
+            out[(c + 1) * plane + i] = (accd[c + 1] + ((double)gh[c] + (double)gl[c])) + accl[c + 1];
     }
     count_pairs(A.pairs, pairs_near, pairs_far);
 }
@@ -624,6 +861,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
 {
     if (t.n <= 0) return LSM_OK;
     const bool mixed = precision == LSM_MIXED;
+    const bool ff = precision == LSM_FF;
     const int tpb = kEvalThreads * (mixed ? kTPT32 : kTPT64);
     const int nblk = (t.n + tpb - 1) / tpb;
     const int ntiles = (int)me->ntiles;
@@ -662,6 +900,9 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     }
     if (mixed) {
         k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, A);
+    } else if (ff) {
+        k_eval_ff<<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, me->s64_pos,
+                                                  me->s64_nw, A);
     } else {
         k_eval_fp64<kTPT64><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
     }

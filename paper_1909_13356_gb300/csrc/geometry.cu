@@ -223,7 +223,8 @@ __global__ void k_gather_sources(const double4_32a* __restrict__ pin, const doub
 // centre (split in two floats) and the FP32 tile-local copies of its nodes.
 __global__ void __launch_bounds__(kTile) k_tile_meta(
     const double4_32a* __restrict__ pos, const double4_32a* __restrict__ nw, int ns,
-    float4* __restrict__ s32p, float4* __restrict__ s32n, float4* __restrict__ s32l, float4* __restrict__ tlo,
+    float4* __restrict__ s32p, float4* __restrict__ s32n, float4* __restrict__ s32l,
+    float4* __restrict__ s32nl, float4* __restrict__ tlo,
     float4* __restrict__ thi, float4* __restrict__ tchi, float4* __restrict__ tclo)
 {
     __shared__ double red[7][kTile / 32];
@@ -290,8 +291,10 @@ __global__ void __launch_bounds__(kTile) k_tile_meta(
         s32p[i] = make_float4(hx, hy, hz, __double2float_rn(p.w));
         s32l[i] = make_float4(__double2float_rn(lx - (double)hx), __double2float_rn(ly - (double)hy),
                               __double2float_rn(lz - (double)hz), 0.0f);
-        s32n[i] = make_float4(__double2float_rn(q.x), __double2float_rn(q.y), __double2float_rn(q.z),
-                              __double2float_rn(q.w));
+        const float nx = __double2float_rn(q.x), ny = __double2float_rn(q.y), nz = __double2float_rn(q.z);
+        s32n[i] = make_float4(nx, ny, nz, __double2float_rn(q.w));
+        s32nl[i] = make_float4(__double2float_rn(q.x - (double)nx), __double2float_rn(q.y - (double)ny),
+                               __double2float_rn(q.z - (double)nz), 0.0f);
     }
 }
 
@@ -383,7 +386,7 @@ int build_mesh_device(Ctx* ctx, Mesh* me, const double* sigma_in_dev, const doub
     k_gather_sources<<<blocks_for(ns, 256), 256, 0, st>>>(p0, n0, perm, ns, me->s64_pos, me->s64_nw);
     LSM_LAUNCHED(ctx);
     k_tile_meta<<<(unsigned)me->ntiles, kTile, 0, st>>>(me->s64_pos, me->s64_nw, ns, me->s32_pos,
-                                                        me->s32_nw, me->s32_lo, me->tile_lo, me->tile_hi,
+                                                        me->s32_nw, me->s32_lo, me->s32_nwlo, me->tile_lo, me->tile_hi,
                                                         me->tile_chi, me->tile_clo);
     LSM_LAUNCHED(ctx);
     LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));

@@ -11,8 +11,9 @@
 // so that it keeps the Morton order the nodes were sorted into once.
 //
 // Mixed precision: nodes start on the FP32 pair kernels; a node whose
-// residual falls below opt.mixed_switch moves to the FP64 kernels for its
-// last steps, unless the requested tolerance is itself looser than that.
+// residual falls below opt.mixed_switch moves to the float-float kernel
+// (Phi to FP64 accuracy on the FP32 pipes) for its last steps, unless the
+// requested tolerance is one the FP32 kernels already meet (opt.mixed_accept).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -251,7 +252,7 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
             k_gather_targets<<<nb(nl), 256, 0, st>>>(L, nl, S, T);
             LSM_LAUNCHED(ctx);
             Targets tg{T, nl, nl};
-            rc = eval_sorted(ctx, me, tg, R, m == 0 ? LSM_MIXED : LSM_FP64, st);
+            rc = eval_sorted(ctx, me, tg, R, m == 0 ? LSM_MIXED : (mixed ? LSM_FF : LSM_FP64), st);
             if (rc) return rc;
             k_newton_update<<<nb(nl), 256, 0, st>>>(L, nl, R, S, m == 0 ? 1 : 0, accept_mixed, tol,
                                                      ctx->opt.mixed_switch, max_iter);

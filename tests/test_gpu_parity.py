@@ -90,6 +90,17 @@ def test_torus_matches_oracle(lsm, torus_case, prec, tol):
     _check(phi, grad, c["phi"], c["grad"], tol, c["m"].sigma.min())
 
 
+@pytest.mark.parametrize("case", ["cube", "torus"])
+def test_float_float_path_reaches_fp64_accuracy_on_phi(lsm, cube_case, torus_case, case):
+    """LSM_FF: far tiles in float-float on the FP32 pipes, near tiles in FP64.
+    Phi within the FP64 tolerance; grad Phi within the mixed tolerance."""
+    c = cube_case if case == "cube" else torus_case
+    smin = 0.1 if case == "cube" else c["m"].sigma.min()
+    phi, grad = c["mesh"].eval_phi_grad(c["x"], lsm.FF)
+    assert np.abs(phi - c["phi"]).max() <= TOL64
+    assert np.abs(grad - c["grad"]).max() <= TOL32 / smin
+
+
 @pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, TOL32)])
 def test_device_and_host_pointers_agree(lsm, torus_case, prec, tol):
     c = torus_case
