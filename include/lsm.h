@@ -41,6 +41,7 @@ extern "C" {
 
 typedef struct lsm_ctx lsm_ctx;
 typedef struct lsm_mesh lsm_mesh;
+typedef struct lsm_batch lsm_batch;
 
 typedef enum {
     LSM_OK = 0,
@@ -235,6 +236,30 @@ int lsm_eval_phi_grad_noalloc(lsm_mesh* mesh, const double* x, int64_t n, double
 int lsm_solve_charts(lsm_mesh* mesh, int order, double tol, int max_iter, int precision,
                      double* x_out, double* h_out, int32_t* status, lsm_solve_stats* stats,
                      void* stream);
+
+/*
+ * Batches: many meshes solved together (the paper treats one mesh at a
+ * time; batching many independent charts problems is this library's
+ * addition).  lsm_batch_create copies the resident state of n uploaded
+ * meshes of one context into concatenated arrays (each mesh's source nodes
+ * start on a tile boundary, so no work item mixes meshes); the meshes stay
+ * valid and independent.  Synchronises `stream`.
+ */
+int lsm_batch_create(lsm_ctx* ctx, lsm_mesh* const* meshes, int n, void* stream, lsm_batch** out);
+int lsm_batch_free(lsm_batch* batch);
+
+/*
+ * lsm_solve_charts for every mesh of a batch at once: each Newton sweep is
+ * one set of launches over all meshes' active nodes, with the work items
+ * (blocks of one mesh's nodes and that mesh's tile range) built on the
+ * device.  With use_graph != 0, two sweeps are captured once as a CUDA graph
+ * on a private stream and replayed until no node is active or max_iter
+ * sweeps have run.  Outputs are concatenated in mesh order, each mesh
+ * triangle-major then rule order, as lsm_solve_charts would return them.
+ * precision: LSM_FP64 or LSM_MIXED.  Synchronises `stream`.
+ */
+int lsm_batch_solve_charts(lsm_batch* batch, int order, double tol, int max_iter, int precision, int use_graph,
+                           double* x_out, double* h_out, int32_t* status, lsm_solve_stats* stats, void* stream);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["FP64", "MIXED", "FF", "Context", "Mesh", "SolveStats", "LsmError", "lib", "load"]
+__all__ = ["FP64", "MIXED", "FF", "Context", "Mesh", "Batch", "SolveStats", "LsmError", "lib", "load"]
 
 FP64 = 0
 MIXED = 1
@@ -37,7 +37,8 @@ _ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVER
 # every symbol include/lsm.h declares
 EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "lsm_set_profiling",
            "lsm_read_stats", "lsm_mesh_upload", "lsm_mesh_free", "lsm_mesh_get_info", "lsm_eval_phi_grad",
-           "lsm_eval_phi_grad_noalloc", "lsm_solve_charts")
+           "lsm_eval_phi_grad_noalloc", "lsm_solve_charts", "lsm_batch_create", "lsm_batch_free",
+           "lsm_batch_solve_charts")
 
 
 class LsmError(RuntimeError):
@@ -120,6 +121,9 @@ def load(build_if_needed: bool = True):
         L.lsm_eval_phi_grad.argtypes = [P, P, I64, P, P, I32, P]
         L.lsm_eval_phi_grad_noalloc.argtypes = [P, P, I64, P, P, I32, P]
         L.lsm_solve_charts.argtypes = [P, I32, D, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
+        L.lsm_batch_create.argtypes = [P, ctypes.POINTER(P), I32, P, ctypes.POINTER(P)]
+        L.lsm_batch_free.argtypes = [P]
+        L.lsm_batch_solve_charts.argtypes = [P, I32, D, I32, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -283,6 +287,55 @@ class Mesh:
     def free(self):
         if getattr(self, "_h", None):
             self.ctx._L.lsm_mesh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _stats(st: "_Stats") -> SolveStats:
+    return SolveStats(st.iterations, st.n_nodes, st.n_converged, st.n_failed, st.eps_newton, st.max_residual,
+                      st.evals_fp32, st.evals_fp64, list(st.active_per_iter)[:max(min(st.iterations, 32), 0)])
+
+
+class Batch:
+    """Many uploaded meshes solved together (lsm_batch_create)."""
+
+    def __init__(self, ctx: Context, meshes, stream=None):
+        self.ctx = ctx
+        self.meshes = list(meshes)
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        h = ctypes.c_void_p()
+        ctx._check(ctx._L.lsm_batch_create(ctx._h, arr, len(self.meshes), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.n_triangles = sum(m.n_triangles for m in self.meshes)
+
+    def solve_charts(self, order: int = 6, tol: float = 1e-10, max_iter: int = 20, precision: int = MIXED,
+                     use_graph: bool = True, device_out: bool = False, stream=None):
+        """Chart nodes of every mesh (lsm_batch_solve_charts), concatenated in mesh order."""
+        n_gl = order // 2 + 2
+        N = self.n_triangles * n_gl * n_gl
+        if device_out:
+            import torch
+            dev = torch.device("cuda", self.ctx.device)
+            x = torch.empty((N, 3), dtype=torch.float64, device=dev)
+            h = torch.empty(N, dtype=torch.float64, device=dev)
+            st = torch.empty(N, dtype=torch.int32, device=dev)
+        else:
+            x, h, st = np.empty((N, 3)), np.empty(N), np.empty(N, dtype=np.int32)
+        stats = _Stats()
+        rc = self.ctx._L.lsm_batch_solve_charts(self._h, int(order), float(tol), int(max_iter), int(precision),
+                                                1 if use_graph else 0, _ptr(x), _ptr(h), _ptr(st),
+                                                ctypes.byref(stats), _stream_handle(stream))
+        self.ctx._check(rc)
+        return x, h, st, _stats(stats)
+
+    def free(self):
+        if getattr(self, "_h", None):
+            self.ctx._L.lsm_batch_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -525,4 +525,68 @@ int lsm_eval_phi_grad_noalloc(lsm_mesh* mh, const double* x, int64_t n, double* 
     return eval_noalloc(ctx, me, x, n, phi, grad, precision, (cudaStream_t)stream);
 }
 
+int lsm_batch_create(lsm_ctx* c, lsm_mesh* const* meshes, int n, void* stream, lsm_batch** out)
+{
+    if (!c || !out || !meshes || n < 1) return LSM_E_INVALID_ARG;
+    *out = nullptr;
+    Ctx* ctx = &c->c;
+    DeviceGuard g(ctx->device);
+    for (int i = 0; i < n; i++)
+        if (!meshes[i]) {
+            ctx->err = "batch_create: null mesh";
+            return LSM_E_INVALID_ARG;
+        }
+    lsm_batch* bh = new (std::nothrow) lsm_batch();
+    if (!bh) return LSM_E_OOM;
+    int rc = batch_build(ctx, &bh->b, meshes, n, (cudaStream_t)stream);
+    if (rc) {
+        batch_release(&bh->b);
+        delete bh;
+        return rc;
+    }
+    *out = bh;
+    return LSM_OK;
+}
+
+int lsm_batch_free(lsm_batch* bh)
+{
+    if (!bh) return LSM_E_INVALID_ARG;
+    DeviceGuard g(bh->b.ctx ? bh->b.ctx->device : 0);
+    batch_release(&bh->b);
+    delete bh;
+    return LSM_OK;
+}
+
+int lsm_batch_solve_charts(lsm_batch* bh, int order, double tol, int max_iter, int precision, int use_graph,
+                           double* x_out, double* h_out, int32_t* status, lsm_solve_stats* stats, void* stream)
+{
+    if (!bh) return LSM_E_INVALID_ARG;
+    Batch* b = &bh->b;
+    Ctx* ctx = b->ctx;
+    if (order < 0 || order > 40 || !(tol > 0) || max_iter < 1 || max_iter > 1000 ||
+        (precision != LSM_FP64 && precision != LSM_MIXED)) {
+        ctx->err = "batch_solve_charts: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_gl = order / 2 + 2;
+    const int64_t N = b->m * (int64_t)n_gl * n_gl;
+    Scratch s(st);
+    double *xo = x_out, *ho = h_out;
+    int32_t* so = status;
+    const bool xdev = x_out && is_device_ptr(x_out);
+    const bool hdev = h_out && is_device_ptr(h_out);
+    const bool sdev = status && is_device_ptr(status);
+    if (!xdev) LSM_CUDA_TRY(ctx, s.get(&xo, 3 * (size_t)N));
+    if (!hdev) LSM_CUDA_TRY(ctx, s.get(&ho, (size_t)N));
+    if (!sdev) LSM_CUDA_TRY(ctx, s.get(&so, (size_t)N));
+    int rc = solve_charts_batch(ctx, b, n_gl, tol, max_iter, precision, use_graph, xo, ho, so, stats, st);
+    if (rc) return rc;
+    if (x_out && !xdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(x_out, xo, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+    if (h_out && !hdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(h_out, ho, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    if (status && !sdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(status, so, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+    return check_flag(ctx, st);
+}
+
 }  // extern "C"

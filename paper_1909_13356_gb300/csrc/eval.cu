@@ -250,6 +250,8 @@ struct EvalArgs {
     float cut2;
     double* out;       // [split][4][nt] (phi, gx, gy, gz) when splitting, else [4][nt]
     int* flag;
+    const int4* items; // optional work items (first target, count, first tile, end tile)
+    const int* n_items;
     unsigned long long* pairs;  // [2] pairs evaluated in near / far tiles
 };
 
@@ -279,9 +281,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
     __shared__ float s_bb[6];
 
     const int tid = threadIdx.x;
-    const int base = blockIdx.x * (kEvalThreads * TPT);
-    const int t0 = blockIdx.y * A.tiles_per_split;
-    const int t1 = min(A.ntiles, t0 + A.tiles_per_split);
+    int base, tend, t0, t1;
+    if (A.items) {
+        if ((int)blockIdx.x >= *A.n_items) return;  // whole CTA, before any barrier
+        const int4 w = A.items[blockIdx.x];
+        base = w.x;
+        tend = w.x + w.y;
+        t0 = w.z;
+        t1 = w.w;
+    } else {
+        base = blockIdx.x * (kEvalThreads * TPT);
+        tend = A.nt;
+        t0 = blockIdx.y * A.tiles_per_split;
+        t1 = min(A.ntiles, t0 + A.tiles_per_split);
+    }
 
     float xh[TPT][3], xl[TPT][3];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -291,15 +304,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
         const int i = base + k * kEvalThreads + tid;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const double v = i < A.nt ? A.tx[c * A.ld + i] : 0.0;
+            const double v = i < tend ? A.tx[c * A.ld + i] : 0.0;
             xh[k][c] = __double2float_rn(v);
             xl[k][c] = __double2float_rn(v - (double)xh[k][c]);
-            if (i < A.nt) {
+            if (i < tend) {
                 lo[c] = fminf(lo[c], __double2float_rd(v));
                 hi[c] = fmaxf(hi[c], __double2float_ru(v));
             }
         }
-        nvalid += i < A.nt ? 1 : 0;
+        nvalid += i < tend ? 1 : 0;
     }
     block_bbox(lo, hi, s_bb);
 
@@ -317,7 +330,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
     __syncthreads();
     // thread 0 stages a tile; the low parts of the positions only for near tiles
     auto issue = [&](int t, int b) {
-        const int cnt = min(kTile, A.ns - t * kTile);
+        const int cnt = (int)A.thi[t].w;
         const uint32_t bytes = (uint32_t)cnt * 16u;
         const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
         mbar_expect_tx(&bar[b], (far ? 2u : 3u) * bytes);
@@ -343,7 +356,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
         }
         const float4 tl = A.tlo[t], th = A.thi[t];
         const float4 ch = A.tchi[t], cl = A.tclo[t];
-        const int cnt = min(kTile, A.ns - t * kTile);
+        const int cnt = (int)A.thi[t].w;
         const bool far = tile_is_far(s_bb, tl, th, A.cut2);
         const float4* sp = sh_pos[b];
         const float4* sn = sh_nw[b];
@@ -438,7 +451,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
 #pragma unroll
     for (int k = 0; k < TPT; k++) {
         const int i = base + k * kEvalThreads + tid;
-        if (i < A.nt) {
+        if (i < tend) {
 #pragma unroll
             for (int c = 0; c < 4; c++) out[c * plane + i] = (double)acc_h[k][c] + (double)acc_l[k][c];
         }
@@ -457,9 +470,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
     __shared__ float s_bb[6];
 
     const int tid = threadIdx.x;
-    const int base = blockIdx.x * (kEvalThreads * TPT);
-    const int t0 = blockIdx.y * A.tiles_per_split;
-    const int t1 = min(A.ntiles, t0 + A.tiles_per_split);
+    int base, tend, t0, t1;
+    if (A.items) {
+        if ((int)blockIdx.x >= *A.n_items) return;
+        const int4 w = A.items[blockIdx.x];
+        base = w.x;
+        tend = w.x + w.y;
+        t0 = w.z;
+        t1 = w.w;
+    } else {
+        base = blockIdx.x * (kEvalThreads * TPT);
+        tend = A.nt;
+        t0 = blockIdx.y * A.tiles_per_split;
+        t1 = min(A.ntiles, t0 + A.tiles_per_split);
+    }
 
     double x[TPT][3];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -468,9 +492,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
         const int i = base + k * kEvalThreads + tid;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const double v = i < A.nt ? A.tx[c * A.ld + i] : 0.0;
+            const double v = i < tend ? A.tx[c * A.ld + i] : 0.0;
             x[k][c] = v;
-            if (i < A.nt) {
+            if (i < tend) {
                 lo[c] = fminf(lo[c], __double2float_rd(v));
                 hi[c] = fmaxf(hi[c], __double2float_ru(v));
             }
@@ -485,7 +509,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
         for (int c = 0; c < 4; c++) acc[k][c] = accl[k][c] = 0.0;
     int nvalid = 0;
 #pragma unroll
-    for (int k = 0; k < TPT; k++) nvalid += (base + k * kEvalThreads + tid) < A.nt ? 1 : 0;
+    for (int k = 0; k < TPT; k++) nvalid += (base + k * kEvalThreads + tid) < tend ? 1 : 0;
     unsigned long long pairs_near = 0, pairs_far = 0;
 
     if (tid == 0) {
@@ -495,7 +519,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
     }
     __syncthreads();
     auto issue = [&](int t, int b) {
-        const int cnt = min(kTile, A.ns - t * kTile);
+        const int cnt = (int)A.thi[t].w;
         const uint32_t bytes = (uint32_t)cnt * 32u;
         mbar_expect_tx(&bar[b], 2u * bytes);
         bulk_g2s(&sh_pos[b][0], spos + (size_t)t * kTile, bytes, &bar[b]);
@@ -516,7 +540,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
             break;
         }
         const float4 tl = A.tlo[t], th = A.thi[t];
-        const int cnt = min(kTile, A.ns - t * kTile);
+        const int cnt = (int)A.thi[t].w;
         const bool far = tile_is_far(s_bb, tl, th, A.cut2);
         const double4_32a* sp = sh_pos[b];
         const double4_32a* sn = sh_nw[b];
@@ -576,7 +600,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
 #pragma unroll
     for (int k = 0; k < TPT; k++) {
         const int i = base + k * kEvalThreads + tid;
-        if (i < A.nt) {
+        if (i < tend) {
 #pragma unroll
             for (int c = 0; c < 4; c++) out[c * plane + i] = acc[k][c] + accl[k][c];
         }
@@ -616,10 +640,22 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     __shared__ float s_bb[6];
 
     const int tid = threadIdx.x;
-    const int i = blockIdx.x * kEvalThreads + tid;
-    const int t0 = blockIdx.y * A.tiles_per_split;
-    const int t1 = min(A.ntiles, t0 + A.tiles_per_split);
-    const bool valid = i < A.nt;
+    int base, tend, t0, t1;
+    if (A.items) {
+        if ((int)blockIdx.x >= *A.n_items) return;
+        const int4 w = A.items[blockIdx.x];
+        base = w.x;
+        tend = w.x + w.y;
+        t0 = w.z;
+        t1 = w.w;
+    } else {
+        base = blockIdx.x * kEvalThreads;
+        tend = A.nt;
+        t0 = blockIdx.y * A.tiles_per_split;
+        t1 = min(A.ntiles, t0 + A.tiles_per_split);
+    }
+    const int i = base + tid;
+    const bool valid = i < tend;
 
     double x[3];
     float xh[3], xl[3];
@@ -648,7 +684,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     }
     __syncthreads();
     auto issue = [&](int t, int b) {
-        const int cnt = min(kTile, A.ns - t * kTile);
+        const int cnt = (int)A.thi[t].w;
         const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
         mbar_expect_tx(&bar[b], (uint32_t)cnt * 64u);
         const size_t o = (size_t)t * kTile;
@@ -679,7 +715,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             }
             break;
         }
-        const int cnt = min(kTile, A.ns - t * kTile);
+        const int cnt = (int)A.thi[t].w;
         const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
         if (far) {
             pairs_far += valid ? cnt : 0;
@@ -891,6 +927,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     A.out = part;
     A.flag = ctx->d_flag;
     A.pairs = ctx->d_pairs;
+    A.items = nullptr;
+    A.n_items = nullptr;
     dim3 grid(nblk, nsplit);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (ctx->profiling) {
@@ -915,6 +953,43 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         k_reduce_splits<<<(t.n + 255) / 256, 256, 0, st>>>(part, nsplit, t.n, res);
         LSM_LAUNCHED(ctx);
     }
+    return LSM_OK;
+}
+
+int eval_item_targets(int precision) { return kEvalThreads * (precision == LSM_MIXED ? kTPT32 : kTPT64); }
+
+int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* items, const int* n_items,
+               int max_items, double* res, int precision, cudaStream_t st)
+{
+    if (max_items <= 0) return LSM_OK;
+    EvalArgs A;
+    A.tlo = v.tile_lo;
+    A.thi = v.tile_hi;
+    A.tchi = v.tile_chi;
+    A.tclo = v.tile_clo;
+    A.ns = 0;
+    A.ntiles = v.ntiles;
+    A.tiles_per_split = v.ntiles;
+    A.tx = t.x;
+    A.ld = t.ld;
+    A.nt = t.n;
+    const bool mixed = precision == LSM_MIXED;
+    const double cut = mixed ? ctx->opt.cutoff_mixed : ctx->opt.cutoff_fp64;
+    A.cut2 = (float)(cut * cut);
+    A.out = res;
+    A.flag = ctx->d_flag;
+    A.pairs = ctx->d_pairs;
+    A.items = items;
+    A.n_items = n_items;
+    if (mixed) {
+        k_eval_mixed<kTPT32><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, A);
+    } else if (precision == LSM_FF) {
+        k_eval_ff<<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, v.s64_pos,
+                                                       v.s64_nw, A);
+    } else {
+        k_eval_fp64<kTPT64><<<max_items, kEvalThreads, 0, st>>>(v.s64_pos, v.s64_nw, A);
+    }
+    LSM_LAUNCHED(ctx);
     return LSM_OK;
 }
 
@@ -1037,6 +1112,8 @@ int eval_noalloc(Ctx* ctx, const Mesh* me, const double* x, int64_t n, double* p
     A.out = nsplit > 1 ? part : R;
     A.flag = ctx->d_flag;
     A.pairs = ctx->d_pairs;
+    A.items = nullptr;
+    A.n_items = nullptr;
     dim3 grid(nblk, nsplit);
     if (mixed) {
         k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, A);

@@ -278,8 +278,9 @@ __global__ void __launch_bounds__(kTile) k_tile_meta(
     if (threadIdx.x == 0) {
         tlo[t] = make_float4(__double2float_rd(L[0]), __double2float_rd(L[1]), __double2float_rd(L[2]),
                              __double2float_ru(S));
+        const int cnt = min(kTile, ns - t * kTile);
         thi[t] = make_float4(__double2float_ru(Hh[0]), __double2float_ru(Hh[1]), __double2float_ru(Hh[2]),
-                             0.0f);
+                             (float)cnt);
         tchi[t] = make_float4(ch[0], ch[1], ch[2], 0.0f);
         tclo[t] = make_float4(__double2float_rn(C[0] - (double)ch[0]), __double2float_rn(C[1] - (double)ch[1]),
                               __double2float_rn(C[2] - (double)ch[2]), 0.0f);
@@ -399,6 +400,17 @@ int chart_nodes_init(Ctx* ctx, const Mesh* me, const double* chart_rule_dev, int
     const int64_t n = me->m * np;
     k_chart_nodes<<<blocks_for(n, 256), 256, 0, st>>>(me->verts, me->tris, me->vpn, me->tri_sigma, me->m,
                                                     chart_rule_dev, np, x0, hdir, sloc);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
+int chart_nodes_raw(Ctx* ctx, const double* verts, const int32_t* tris, const double* vpn, const double* tri_sigma,
+                    int64_t m, const double* chart_rule_dev, int np, double* x0, double* hdir, double* sloc,
+                    cudaStream_t st)
+{
+    const int64_t n = m * np;
+    k_chart_nodes<<<blocks_for(n, 256), 256, 0, st>>>(verts, tris, vpn, tri_sigma, m, chart_rule_dev, np, x0, hdir,
+                                                    sloc);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }

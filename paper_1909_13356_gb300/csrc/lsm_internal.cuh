@@ -11,6 +11,8 @@
 
 #include "lsm.h"
 
+struct lsm_mesh;
+
 namespace lsm {
 
 // Source nodes per tile.  Tiles are runs of consecutive Morton-sorted source
@@ -55,9 +57,28 @@ struct Mesh {
     float4* s32_lo = nullptr;    // FP32 remainder of the tile-local position, 0
     float4* s32_nwlo = nullptr;  // FP32 remainder of nw / 4 pi, 0 (float-float kernel)
     float4* tile_lo = nullptr;   // bbox lower corner rounded down, w = sigma_max rounded up
-    float4* tile_hi = nullptr;   // bbox upper corner rounded up
+    float4* tile_hi = nullptr;   // bbox upper corner rounded up, w = number of nodes in the tile
     float4* tile_chi = nullptr;  // tile centre, FP32 high part
     float4* tile_clo = nullptr;  // tile centre, FP32 remainder
+};
+
+// Many meshes evaluated and solved together: their tiles and geometry are
+// concatenated (each mesh's sources start on a tile boundary).
+struct Batch {
+    Ctx* ctx = nullptr;
+    int nmesh = 0;
+    int64_t nv = 0, m = 0, ntiles = 0;
+    size_t bytes = 0;
+    double* verts = nullptr;     // [nv][3]
+    int32_t* tris = nullptr;     // [m][3], global vertex indices
+    double* tri_sigma = nullptr; // [m]
+    double* vpn = nullptr;       // [nv][3]
+    int32_t* tri_mesh = nullptr; // [m] mesh of each triangle
+    float4 *s32_pos = nullptr, *s32_nw = nullptr, *s32_lo = nullptr, *s32_nwlo = nullptr;
+    double4_32a *s64_pos = nullptr, *s64_nw = nullptr;
+    float4 *tile_lo = nullptr, *tile_hi = nullptr, *tile_chi = nullptr, *tile_clo = nullptr;
+    int2* mesh_tiles = nullptr;  // [nmesh] (first tile, end tile)
+    std::vector<int64_t> tri_off;  // host [nmesh + 1]
 };
 
 // ---------------------------------------------------------------- errors
@@ -108,6 +129,10 @@ int radix_sort_pairs(Ctx* ctx, uint32_t* keys, uint32_t* vals, int n, int key_bi
                      cudaStream_t st);
 int compact_flags(Ctx* ctx, const int32_t* flags, int want, const int32_t* in, int n,
                   int32_t* out, int32_t* d_count, cudaStream_t st);
+int scan_exclusive(Ctx* ctx, uint32_t* a, int64_t len, uint32_t* total, cudaStream_t st);
+int compact_blocks(int n_max);
+int compact_flags_dev(Ctx* ctx, const int32_t* flags, int want, const int32_t* in, const int* n_dev, int n_max,
+                      int32_t* out, int32_t* d_count, uint32_t* bc, cudaStream_t st);
 
 // geometry.cu
 int build_mesh_device(Ctx* ctx, Mesh* mesh, const double* sigma_in_dev, const double* rule_dev,
@@ -116,6 +141,28 @@ int morton_order_points(Ctx* ctx, const double* pts, int stride, int n, uint32_t
                         cudaStream_t st);
 int chart_nodes_init(Ctx* ctx, const Mesh* mesh, const double* chart_rule_dev, int np,
                      double* x0, double* hdir, double* sloc, cudaStream_t st);
+int chart_nodes_raw(Ctx* ctx, const double* verts, const int32_t* tris, const double* vpn, const double* tri_sigma,
+                    int64_t m, const double* chart_rule_dev, int np, double* x0, double* hdir, double* sloc,
+                    cudaStream_t st);
+
+// Source-side arrays the pair kernels read: one mesh, or a batch of meshes
+// whose tiles are concatenated.
+struct SourceView {
+    const float4 *s32_pos, *s32_nw, *s32_lo, *s32_nwlo;
+    const double4_32a *s64_pos, *s64_nw;
+    const float4 *tile_lo, *tile_hi, *tile_chi, *tile_clo;
+    int ntiles;
+};
+inline SourceView view_of(const Mesh* m)
+{
+    return SourceView{m->s32_pos, m->s32_nw, m->s32_lo, m->s32_nwlo, m->s64_pos, m->s64_nw,
+                      m->tile_lo, m->tile_hi, m->tile_chi, m->tile_clo, (int)m->ntiles};
+}
+inline SourceView view_of_batch(const Batch* b)
+{
+    return SourceView{b->s32_pos, b->s32_nw, b->s32_lo, b->s32_nwlo, b->s64_pos, b->s64_nw,
+                      b->tile_lo, b->tile_hi, b->tile_chi, b->tile_clo, (int)b->ntiles};
+}
 
 // eval.cu
 struct Targets {
@@ -126,6 +173,12 @@ struct Targets {
 int eval_init_constants(Ctx* ctx);
 int eval_sorted(Ctx* ctx, const Mesh* mesh, const Targets& t, double* res, int precision,
                 cudaStream_t st);
+// Targets grouped by work items (int4: first target, count, first tile, end
+// tile; at most eval_item_targets(precision) targets each); the number of
+// items is read on the device from *n_items, the grid covers max_items.
+int eval_item_targets(int precision);
+int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* items, const int* n_items,
+               int max_items, double* res, int precision, cudaStream_t st);
 int eval_noalloc(Ctx* ctx, const Mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
                  int precision, cudaStream_t st);
 
@@ -133,6 +186,15 @@ int eval_noalloc(Ctx* ctx, const Mesh* mesh, const double* x, int64_t n, double*
 int solve_charts_device(Ctx* ctx, Mesh* mesh, int n_gl, double tol, int max_iter,
                         int precision, double* x_out, double* h_out, int32_t* status_out,
                         lsm_solve_stats* stats, cudaStream_t st);
+
+int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, int precision, int use_graph,
+                       double* x_out, double* h_out, int32_t* status_out, lsm_solve_stats* stats,
+                       cudaStream_t st);
+int batch_build(Ctx* ctx, Batch* b, lsm_mesh* const* meshes, int n, cudaStream_t st);
+void batch_release(Batch* b);
+int build_items(Ctx* ctx, const int32_t* list, const int* n_list, int n_max, const int32_t* node_mesh,
+                const int2* mesh_tiles, int nmesh, int bs, uint32_t* cnt, uint32_t* nblk, int4* items, int* n_items,
+                cudaStream_t st);
 
 // host helpers (api.cu)
 void simplex_rule_host(int n, int subdiv, double* uvw);  // [cnt][3]
@@ -144,4 +206,7 @@ struct lsm_ctx {
 };
 struct lsm_mesh {
     lsm::Mesh m;
+};
+struct lsm_batch {
+    lsm::Batch b;
 };

@@ -85,14 +85,11 @@ __global__ void k_gather_targets(const int32_t* __restrict__ list, int n, NodeSt
     for (int c = 0; c < 3; c++) T[(int64_t)c * n + k] = S.x0[c * S.n + i] + h * S.hd[c * S.n + i];
 }
 
-// One Newton update per listed node from res = [phi | gx | gy | gz] ([4][n]).
-__global__ void k_newton_update(const int32_t* __restrict__ list, int n, const double* __restrict__ R,
-                                NodeState S, int mixed_eval, int accept_mixed, double tol, double sw,
-                                int max_iter)
+// One Newton update of node i from row k of res = [phi | gx | gy | gz] (plane stride p).
+__device__ __forceinline__ void newton_update_one(int i, int k, int64_t p, const double* __restrict__ R,
+                                                  NodeState& S, int mixed_eval, int accept_mixed, double tol,
+                                                  double sw, int max_iter)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int i = list[k];
     const double r = R[k] - 0.5;
     const int it = S.it[i] + 1;
     S.it[i] = it;
@@ -106,8 +103,7 @@ __global__ void k_newton_update(const int32_t* __restrict__ list, int n, const d
         return;
     }
     if (mixed_eval && !accept_mixed && fabs(r) < sw) S.mode[i] = 1;
-    const double d = S.hd[i] * R[(int64_t)n + k] + S.hd[S.n + i] * R[2 * (int64_t)n + k] +
-                     S.hd[2 * S.n + i] * R[3 * (int64_t)n + k];
+    const double d = S.hd[i] * R[p + k] + S.hd[S.n + i] * R[2 * p + k] + S.hd[2 * S.n + i] * R[3 * p + k];
     if (!isfinite(d)) {
         S.st[i] = LSM_NODE_NONFINITE;
         return;
@@ -125,6 +121,90 @@ __global__ void k_newton_update(const int32_t* __restrict__ list, int n, const d
     S.h[i] += step;
     S.dh[i] = fabs(step);
     if (it >= max_iter) S.st[i] = LSM_NODE_MAXITER;
+}
+
+__global__ void k_newton_update(const int32_t* __restrict__ list, int n, const double* __restrict__ R,
+                                NodeState S, int mixed_eval, int accept_mixed, double tol, double sw,
+                                int max_iter)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    newton_update_one(list[k], k, n, R, S, mixed_eval, accept_mixed, tol, sw, max_iter);
+}
+
+// ---- device-counted variants (launch shapes fixed by the capacity, so a
+// whole sweep can be captured in a CUDA graph)
+__global__ void k_newton_update_dev(const int32_t* __restrict__ list, const int* __restrict__ n_dev,
+                                    const double* __restrict__ R, int64_t plane, NodeState S, int mixed_eval,
+                                    int accept_mixed, double tol, double sw, int max_iter)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *n_dev) return;
+    newton_update_one(list[k], k, plane, R, S, mixed_eval, accept_mixed, tol, sw, max_iter);
+}
+
+__global__ void k_list_mode_flags(const int32_t* __restrict__ list, const int* __restrict__ n_dev,
+                                  const int32_t* __restrict__ mode, int32_t* __restrict__ flags)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < *n_dev) flags[k] = mode[list[k]];
+}
+
+__global__ void k_list_pending_flags(const int32_t* __restrict__ list, const int* __restrict__ n_dev,
+                                     const int32_t* __restrict__ st, int32_t* __restrict__ flags)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < *n_dev) flags[k] = st[list[k]] == kPending ? 1 : 0;
+}
+
+__global__ void k_gather_targets_dev(const int32_t* __restrict__ list, const int* __restrict__ n_dev, NodeState S,
+                                     double* __restrict__ T, int64_t ld)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *n_dev) return;
+    const int i = list[k];
+    const double h = S.h[i];
+    for (int c = 0; c < 3; c++) T[(int64_t)c * ld + k] = S.x0[c * S.n + i] + h * S.hd[c * S.n + i];
+}
+
+// active-count history: hist[sweep] = n after the sweep (sweeps with work only)
+__global__ void k_record_sweep(const int* __restrict__ n_before, const int* __restrict__ n_after,
+                               int* __restrict__ counter, int* __restrict__ hist)
+{
+    if (threadIdx.x == 0 && *n_before > 0) {
+        const int s = *counter;
+        if (s < 32) hist[s] = *n_before;
+        *counter = s + 1;
+    }
+}
+
+// work items: blocks of at most bs consecutive listed nodes of one mesh
+__global__ void k_mesh_hist(const int32_t* __restrict__ list, const int* __restrict__ n_dev,
+                            const int32_t* __restrict__ node_mesh, uint32_t* __restrict__ cnt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < *n_dev) atomicAdd(&cnt[node_mesh[list[k]]], 1u);
+}
+
+__global__ void k_mesh_blocks(const uint32_t* __restrict__ cnt, int nmesh, int bs, uint32_t* __restrict__ nblk)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < nmesh) nblk[m] = (cnt[m] + bs - 1) / bs;
+}
+
+__global__ void k_write_items(const uint32_t* __restrict__ seg, const uint32_t* __restrict__ cnt,
+                              const uint32_t* __restrict__ blk, const int2* __restrict__ mesh_tiles, int nmesh,
+                              int bs, int4* __restrict__ items)
+{
+    const int m = blockIdx.x;
+    if (m >= nmesh) return;
+    const int c = (int)cnt[m];
+    const int nb = (c + bs - 1) / bs;
+    const int2 tr = mesh_tiles[m];
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const int first = (int)seg[m] + j * bs;
+        items[blk[m] + j] = make_int4(first, min(bs, c - j * bs), tr.x, tr.y);
+    }
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double* a, double v)
@@ -288,6 +368,302 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
     S0.max_residual = hred[1];
     S0.n_converged = hcnt[0];
     S0.n_failed = hcnt[1];
+    if (stats) *stats = S0;
+    return LSM_OK;
+}
+
+// Work items for the listed nodes (the list is ordered by mesh, at most
+// n_max long).  Scratch: cnt [2*nmesh] (counts, then segment starts),
+// nblk [nmesh] (block counts, then block starts).  *n_items (device) =
+// number of items written.  Launch shapes depend on n_max and nmesh only.
+int build_items(Ctx* ctx, const int32_t* list, const int* n_list, int n_max, const int32_t* node_mesh,
+                const int2* mesh_tiles, int nmesh, int bs, uint32_t* cnt, uint32_t* nblk, int4* items, int* n_items,
+                cudaStream_t st)
+{
+    uint32_t* seg = cnt + nmesh;
+    LSM_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nmesh, st));
+    k_mesh_hist<<<nb(n_max), 256, 0, st>>>(list, n_list, node_mesh, cnt);
+    LSM_LAUNCHED(ctx);
+    k_mesh_blocks<<<nb(nmesh), 256, 0, st>>>(cnt, nmesh, bs, nblk);
+    LSM_LAUNCHED(ctx);
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(seg, cnt, sizeof(uint32_t) * nmesh, cudaMemcpyDeviceToDevice, st));
+    int rc = scan_exclusive(ctx, seg, nmesh, nullptr, st);
+    if (rc) return rc;
+    rc = scan_exclusive(ctx, nblk, nmesh, reinterpret_cast<uint32_t*>(n_items), st);
+    if (rc) return rc;
+    k_write_items<<<nmesh, 128, 0, st>>>(seg, cnt, nblk, mesh_tiles, nmesh, bs, items);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
+namespace {
+
+// sort key: the mesh of the node at Morton position k
+__global__ void k_node_mesh(const int32_t* __restrict__ tri_mesh, int np, int n, const uint32_t* __restrict__ perm,
+                            uint32_t* __restrict__ key)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) key[k] = (uint32_t)tri_mesh[perm[k] / np];
+}
+
+__global__ void k_gather_mesh(const int32_t* __restrict__ tri_mesh, int np, int n, const uint32_t* __restrict__ perm,
+                              int32_t* __restrict__ mesh_of_sorted)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) mesh_of_sorted[k] = tri_mesh[perm[k] / np];
+}
+
+struct BatchSweep {
+    int N, nmesh, max_items_mixed, max_items_other;
+    int32_t *flags, *lst, *node_mesh;
+    int *n_lst, *n_items, *sweep_counter, *hist;
+    double *T, *R;
+    int4* items;
+    uint32_t *bc, *cnt, *nblk;
+    const int2* mesh_tiles;
+    SourceView view;
+    NodeState S;
+    bool mixed;
+    int accept_mixed, max_iter;
+    double tol, sw;
+};
+
+int batch_sweep(Ctx* ctx, const BatchSweep& B, const int32_t* act, const int* n_act, int32_t* act_out,
+                int* n_act_out, cudaStream_t st)
+{
+    int rc;
+    for (int m = B.mixed ? 0 : 1; m <= 1; m++) {
+        const int prec = m == 0 ? LSM_MIXED : (B.mixed ? LSM_FF : LSM_FP64);
+        const int32_t* L = act;
+        const int* nL = n_act;
+        if (B.mixed) {
+            k_list_mode_flags<<<nb(B.N), 256, 0, st>>>(act, n_act, B.S.mode, B.flags);
+            LSM_LAUNCHED(ctx);
+            rc = compact_flags_dev(ctx, B.flags, m, act, n_act, B.N, B.lst, B.n_lst, B.bc, st);
+            if (rc) return rc;
+            L = B.lst;
+            nL = B.n_lst;
+        }
+        k_gather_targets_dev<<<nb(B.N), 256, 0, st>>>(L, nL, B.S, B.T, B.N);
+        LSM_LAUNCHED(ctx);
+        const int bs = eval_item_targets(prec);
+        rc = build_items(ctx, L, nL, B.N, B.node_mesh, B.mesh_tiles, B.nmesh, bs, B.cnt, B.nblk, B.items, B.n_items,
+                         st);
+        if (rc) return rc;
+        Targets tg{B.T, B.N, B.N};
+        rc = eval_items(ctx, B.view, tg, B.items, B.n_items, prec == LSM_MIXED ? B.max_items_mixed : B.max_items_other,
+                        B.R, prec, st);
+        if (rc) return rc;
+        k_newton_update_dev<<<nb(B.N), 256, 0, st>>>(L, nL, B.R, B.N, B.S, m == 0 ? 1 : 0, B.accept_mixed, B.tol, B.sw,
+                                                     B.max_iter);
+        LSM_LAUNCHED(ctx);
+    }
+    k_list_pending_flags<<<nb(B.N), 256, 0, st>>>(act, n_act, B.S.st, B.flags);
+    LSM_LAUNCHED(ctx);
+    rc = compact_flags_dev(ctx, B.flags, 1, act, n_act, B.N, act_out, n_act_out, B.bc, st);
+    if (rc) return rc;
+    k_record_sweep<<<1, 32, 0, st>>>(n_act, n_act_out, B.sweep_counter, B.hist);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
+}  // namespace
+
+// Chart solve for every mesh of a batch in one set of launches per sweep.
+// With use_graph, two sweeps (A -> B -> A) are captured once as a CUDA graph
+// and replayed until no node is active or max_iter sweeps have run.
+int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, int precision, int use_graph,
+                       double* x_out, double* h_out, int32_t* status_out, lsm_solve_stats* stats, cudaStream_t caller)
+{
+    const int np = n_gl * n_gl;
+    const int64_t N64 = b->m * (int64_t)np;
+    if (N64 <= 0 || N64 >= ((int64_t)1 << 31) - 1024) {
+        ctx->err = "batch chart solve: node count out of range";
+        return LSM_E_INVALID_ARG;
+    }
+    const int N = (int)N64;
+    // a private stream (graph capture needs one), ordered after the caller's work
+    cudaStream_t st;
+    LSM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct StreamFree {
+        cudaStream_t s;
+        ~StreamFree() { cudaStreamDestroy(s); }
+    } sfree{st};
+    cudaEvent_t ev;
+    LSM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    struct EventFree {
+        cudaEvent_t e;
+        ~EventFree() { cudaEventDestroy(e); }
+    } efree{ev};
+    LSM_CUDA_TRY(ctx, cudaEventRecord(ev, caller));
+    LSM_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ev, 0));
+
+    lsm_solve_stats S0;
+    memset(&S0, 0, sizeof(S0));
+    S0.n_nodes = N;
+    int rc;
+    {
+        Scratch s(st);
+        std::vector<double> rule((size_t)np * 3);
+        simplex_rule_host(n_gl, 0, rule.data());
+        double* rule_d;
+        LSM_CUDA_TRY(ctx, s.get(&rule_d, rule.size()));
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(rule_d, rule.data(), sizeof(double) * rule.size(), cudaMemcpyHostToDevice, st));
+        double *x0a, *hda, *sla;
+        LSM_CUDA_TRY(ctx, s.get(&x0a, 3 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&hda, 3 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&sla, (size_t)N));
+        rc = chart_nodes_raw(ctx, b->verts, b->tris, b->vpn, b->tri_sigma, b->m, rule_d, np, x0a, hda, sla, st);
+        if (rc) return rc;
+        // order: mesh, then Morton within the batch's box
+        uint32_t *perm, *key;
+        LSM_CUDA_TRY(ctx, s.get(&perm, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&key, (size_t)N));
+        rc = morton_order_points(ctx, x0a, 3, N, perm, st);
+        if (rc) return rc;
+        k_node_mesh<<<nb(N), 256, 0, st>>>(b->tri_mesh, np, N, perm, key);
+        LSM_LAUNCHED(ctx);
+        int bits = 1;
+        while ((1 << bits) < b->nmesh) bits++;
+        rc = radix_sort_pairs(ctx, key, perm, N, bits, st);
+        if (rc) return rc;
+
+        BatchSweep B;
+        B.N = N;
+        B.nmesh = b->nmesh;
+        B.max_items_mixed = (N + eval_item_targets(LSM_MIXED) - 1) / eval_item_targets(LSM_MIXED) + b->nmesh;
+        B.max_items_other = (N + eval_item_targets(LSM_FP64) - 1) / eval_item_targets(LSM_FP64) + b->nmesh;
+        B.mesh_tiles = b->mesh_tiles;
+        B.view = view_of_batch(b);
+        B.mixed = precision == LSM_MIXED;
+        B.accept_mixed = tol >= ctx->opt.mixed_accept ? 1 : 0;
+        B.max_iter = max_iter;
+        B.tol = tol;
+        B.sw = ctx->opt.mixed_switch;
+        NodeState& S = B.S;
+        S.n = N;
+        LSM_CUDA_TRY(ctx, s.get(&S.x0, 3 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.hd, 3 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.sl, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.h, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.dh, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.res, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.st, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.it, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.mode, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&S.clamp, (size_t)N));
+        k_sort_state<<<nb(N), 256, 0, st>>>(x0a, hda, sla, perm, N, S, B.mixed ? 0 : 1);
+        LSM_LAUNCHED(ctx);
+        LSM_CUDA_TRY(ctx, s.get(&B.node_mesh, (size_t)N));
+        k_gather_mesh<<<nb(N), 256, 0, st>>>(b->tri_mesh, np, N, perm, B.node_mesh);
+        LSM_LAUNCHED(ctx);
+
+        int32_t *actA, *actB;
+        int* cnts;  // n_actA, n_actB, n_lst, n_items, sweep counter, hist[32]
+        LSM_CUDA_TRY(ctx, s.get(&actA, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&actB, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&B.lst, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&B.flags, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&B.T, 3 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&B.R, 4 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&B.items, (size_t)std::max(B.max_items_mixed, B.max_items_other)));
+        LSM_CUDA_TRY(ctx, s.get(&B.bc, (size_t)compact_blocks(N) + 1));
+        LSM_CUDA_TRY(ctx, s.get(&B.cnt, 2 * (size_t)b->nmesh));
+        LSM_CUDA_TRY(ctx, s.get(&B.nblk, (size_t)b->nmesh));
+        LSM_CUDA_TRY(ctx, s.get(&cnts, 40));
+        LSM_CUDA_TRY(ctx, cudaMemsetAsync(cnts, 0, sizeof(int) * 40, st));
+        int* n_actA = cnts;
+        int* n_actB = cnts + 1;
+        B.n_lst = cnts + 2;
+        B.n_items = cnts + 3;
+        B.sweep_counter = cnts + 4;
+        B.hist = cnts + 5;
+        // identity active list
+        LSM_CUDA_TRY(ctx, cudaMemsetAsync(B.flags, 0, sizeof(int32_t) * N, st));
+        rc = compact_flags(ctx, B.flags, 0, nullptr, N, actA, n_actA, st);
+        if (rc) return rc;
+
+        int32_t* hcount = nullptr;
+        LSM_CUDA_TRY(ctx, cudaMallocHost(&hcount, sizeof(int32_t) * 40));
+        struct PinnedFree {
+            int32_t* p;
+            ~PinnedFree() { cudaFreeHost(p); }
+        } pf{hcount};
+
+        int sweeps = 0;
+        if (use_graph) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            const int64_t l0 = ctx->launches;
+            LSM_CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            int rc1 = batch_sweep(ctx, B, actA, n_actA, actB, n_actB, st);
+            int rc2 = rc1 ? rc1 : batch_sweep(ctx, B, actB, n_actB, actA, n_actA, st);
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (rc2 || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                if (!rc2) ctx->err = std::string("graph capture: ") + cudaGetErrorString(ce);
+                return rc2 ? rc2 : LSM_E_CUDA;
+            }
+            const int64_t per_replay = ctx->launches - l0;
+            ctx->launches = l0;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                ctx->err = std::string("graph instantiate: ") + cudaGetErrorString(ce);
+                return LSM_E_CUDA;
+            }
+            struct ExecFree {
+                cudaGraphExec_t e;
+                ~ExecFree() { cudaGraphExecDestroy(e); }
+            } xfree{exec};
+            while (sweeps < max_iter) {
+                LSM_CUDA_TRY(ctx, cudaGraphLaunch(exec, st));
+                ctx->launches += per_replay;
+                sweeps += 2;
+                LSM_CUDA_TRY(ctx, cudaMemcpyAsync(hcount, n_actA, sizeof(int), cudaMemcpyDeviceToHost, st));
+                LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+                if (hcount[0] == 0) break;
+            }
+        } else {
+            int32_t *a = actA, *c = actB;
+            int *na = n_actA, *nc = n_actB;
+            while (sweeps < max_iter) {
+                rc = batch_sweep(ctx, B, a, na, c, nc, st);
+                if (rc) return rc;
+                sweeps++;
+                LSM_CUDA_TRY(ctx, cudaMemcpyAsync(hcount, nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+                LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+                std::swap(a, c);
+                std::swap(na, nc);
+                if (hcount[0] == 0) break;
+            }
+        }
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(hcount, cnts, sizeof(int) * 40, cudaMemcpyDeviceToHost, st));
+        LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        S0.iterations = hcount[4];
+        for (int k = 0; k < 32 && k < hcount[4]; k++) S0.active_per_iter[k] = hcount[5 + k];
+
+        double* red;
+        int* cnt;
+        LSM_CUDA_TRY(ctx, s.get(&red, 2));
+        LSM_CUDA_TRY(ctx, s.get(&cnt, 2));
+        LSM_CUDA_TRY(ctx, cudaMemsetAsync(red, 0, sizeof(double) * 2, st));
+        LSM_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(int) * 2, st));
+        k_unsort_state<<<nb(N), 256, 0, st>>>(perm, S, x_out, h_out, status_out, red, cnt);
+        LSM_LAUNCHED(ctx);
+        double hred[2];
+        int hcnt[2];
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(hred, red, sizeof(hred), cudaMemcpyDeviceToHost, st));
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(hcnt, cnt, sizeof(hcnt), cudaMemcpyDeviceToHost, st));
+        LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        S0.eps_newton = hred[0];
+        S0.max_residual = hred[1];
+        S0.n_converged = hcnt[0];
+        S0.n_failed = hcnt[1];
+    }
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    LSM_CUDA_TRY(ctx, cudaEventRecord(ev, st));
+    LSM_CUDA_TRY(ctx, cudaStreamWaitEvent(caller, ev, 0));
     if (stats) *stats = S0;
     return LSM_OK;
 }

@@ -154,6 +154,56 @@ __global__ void k_flag_scatter(const int32_t* __restrict__ flags, int want,
     }
 }
 
+// Same as k_flag_count / k_flag_scatter with the length read on the device.
+__global__ void k_flag_count_dev(const int32_t* __restrict__ flags, int want, const int* __restrict__ n_dev,
+                                 uint32_t* bc)
+{
+    __shared__ uint32_t ws[kCompThreads / 32];
+    const int n = *n_dev;
+    const int base = blockIdx.x * kCompChunk + threadIdx.x * kCompItems;
+    uint32_t c = 0;
+    for (int k = 0; k < kCompItems; k++) {
+        int i = base + k;
+        if (i < n && flags[i] == want) c++;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < kCompThreads / 32; k++) t += ws[k];
+        bc[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_flag_scatter_dev(const int32_t* __restrict__ flags, int want, const int32_t* __restrict__ in,
+                                   const int* __restrict__ n_dev, const uint32_t* __restrict__ bc,
+                                   int32_t* __restrict__ out)
+{
+    __shared__ uint32_t ws[kCompThreads / 32];
+    const int n = *n_dev;
+    const int base = blockIdx.x * kCompChunk + threadIdx.x * kCompItems;
+    uint32_t c = 0;
+    for (int k = 0; k < kCompItems; k++) {
+        int i = base + k;
+        if (i < n && flags[i] == want) c++;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t v = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) ws[w] = v;
+    __syncthreads();
+    uint32_t off = bc[blockIdx.x] + v - c;
+    for (int k = 0; k < w; k++) off += ws[k];
+    for (int k = 0; k < kCompItems; k++) {
+        int i = base + k;
+        if (i < n && flags[i] == want) out[off++] = in ? in[i] : i;
+    }
+}
+
 }  // namespace
 
 // Sorts (keys, vals) by the low key_bits bits of keys, stably, in place.
@@ -205,6 +255,32 @@ int compact_flags(Ctx* ctx, const int32_t* flags, int want, const int32_t* in, i
     k_scan_exclusive<<<1, kScanThreads, 0, st>>>(bc, nb, reinterpret_cast<uint32_t*>(d_count));
     LSM_LAUNCHED(ctx);
     k_flag_scatter<<<nb, kCompThreads, 0, st>>>(flags, want, in, n, bc, out);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
+// Exclusive scan of a[0..len) in place; *total (device, may be NULL) = sum.
+int scan_exclusive(Ctx* ctx, uint32_t* a, int64_t len, uint32_t* total, cudaStream_t st)
+{
+    k_scan_exclusive<<<1, kScanThreads, 0, st>>>(a, len, total);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
+// compact_flags with the input length read on the device (*n_dev <= n_max);
+// `bc` is caller scratch of compact_blocks(n_max) words.  Launch shapes
+// depend on n_max only, so the sequence can be captured in a CUDA graph.
+int compact_blocks(int n_max) { return (n_max + kCompChunk - 1) / kCompChunk; }
+int compact_flags_dev(Ctx* ctx, const int32_t* flags, int want, const int32_t* in, const int* n_dev, int n_max,
+                      int32_t* out, int32_t* d_count, uint32_t* bc, cudaStream_t st)
+{
+    const int nb = compact_blocks(n_max);
+    if (nb <= 0) return LSM_OK;
+    k_flag_count_dev<<<nb, kCompThreads, 0, st>>>(flags, want, n_dev, bc);
+    LSM_LAUNCHED(ctx);
+    k_scan_exclusive<<<1, kScanThreads, 0, st>>>(bc, nb, reinterpret_cast<uint32_t*>(d_count));
+    LSM_LAUNCHED(ctx);
+    k_flag_scatter_dev<<<nb, kCompThreads, 0, st>>>(flags, want, in, n_dev, bc, out);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }

@@ -1,0 +1,54 @@
+"""Batched chart solves: many meshes in one set of launches per Newton sweep
+(optionally replayed from a captured CUDA graph) give each mesh the result of
+its own solve, within the chart-position tolerance."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1909_13356_gb300 as lsm
+    ctx = lsm.Context(0)
+    g = synth.rng(44)
+    ms = [synth.ellipsoid(int(T), g) for T in (200, 340, 520, 260, 800, 230, 410, 300)]
+    meshes = [ctx.upload(m.verts, m.tris, m.sigma, n_gl=4) for m in ms]
+    return lsm, ctx, ms, meshes
+
+
+@pytest.mark.parametrize("prec,tol,pos_tol", [(1, 1e-10, 1e-9), (0, 1e-12, 1e-10)])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_matches_each_mesh_alone(setup, prec, tol, pos_tol, use_graph):
+    lsm, ctx, ms, meshes = setup
+    b = lsm.Batch(ctx, meshes)
+    x, h, st, stats = b.solve_charts(order=6, tol=tol, precision=prec, use_graph=use_graph)
+    assert stats.n_nodes == sum(m.m for m in ms) * 25
+    assert np.all(st & 255 == 0), np.unique(st)
+    o = 0
+    for mesh in meshes:
+        xa, ha, sa, _ = mesh.solve_charts(order=6, tol=tol, precision=prec)
+        n = len(ha)
+        assert np.all(sa & 255 == 0)
+        assert np.abs(x[o:o + n] - xa).max() < pos_tol
+        o += n
+    b.free()
+
+
+def test_batch_residual_against_oracle(setup, oracle_mod):
+    lsm, ctx, ms, meshes = setup
+    b = lsm.Batch(ctx, meshes[:3])
+    x, h, st, stats = b.solve_charts(order=6, tol=1e-11, precision=lsm.MIXED)
+    o = 0
+    for m in ms[:3]:
+        n = m.m * 25
+        y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 4, 0)
+        phi, _ = oracle_mod.phi_grad(y, nw, sg, x[o:o + n:11])
+        assert np.abs(phi - 0.5).max() < 1e-11
+        o += n
+    b.free()
