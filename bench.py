@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--targets", type=int, default=1_000_000)
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--small", action="store_true", help="small torus (quick check)")
+    ap.add_argument("--workload", default="torus", choices=["torus", "ellipsoids", "serve"],
+                    help="torus: the default line; ellipsoids: 512 meshes in one batched, graph-captured "
+                         "solve; serve: a Poisson request stream through the server")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=5.0)
+    ap.add_argument("--tmax", type=float, default=1e4)
     ap.add_argument("--no-charts", action="store_true", help="time the evaluation only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -169,8 +175,102 @@ def run_reference(args, rank, world):
     }))
 
 
+def bench_ellipsoids(args):
+    """512 ellipsoids (200-5,000 triangles), order-6 charts, one batched solve
+    per step: every Newton sweep is one captured CUDA graph over all meshes."""
+    import torch
+    import paper_1909_13356_gb300 as lsm
+    import synth
+    w = synth.ellipsoid_batch_c4()
+    ctx = lsm.Context(0)
+    meshes = [ctx.upload(m.verts, m.tris, m.sigma, n_gl=4) for m in w["meshes"]]
+    batch = lsm.Batch(ctx, meshes)
+    tol = 1e-10
+    for _ in range(args.warmup):
+        batch.solve_charts(order=6, tol=tol, precision=lsm.MIXED, use_graph=True, device_out=True)
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x, h, st, stats = batch.solve_charts(order=6, tol=tol, precision=lsm.MIXED, use_graph=True, device_out=True)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    launches = (ctx.launch_count - l0) // args.steps
+    # the same work mesh by mesh, for comparison
+    t1 = time.perf_counter()
+    n_alone = 0
+    for mesh in meshes:
+        _, _, _, s1 = mesh.solve_charts(order=6, tol=tol, precision=lsm.MIXED, device_out=True)
+        n_alone += s1.n_converged
+    torch.cuda.synchronize()
+    dt_alone = time.perf_counter() - t1
+    print(json.dumps({
+        "metric": "chart_nodes_per_s", "value": stats.n_converged / dt, "unit": "nodes/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
+        "config": {"workload": w["name"], "meshes": len(meshes), "triangles": sum(m.m for m in w["meshes"]),
+                   "chart_nodes": stats.n_nodes, "order": 6, "tol": tol, "graph": True},
+        "newton": {"sweeps": stats.iterations, "active_per_iter": stats.active_per_iter,
+                   "n_failed": stats.n_failed, "max_residual": stats.max_residual},
+        "gpu_launches_per_step": launches,
+        "unbatched": {"seconds": dt_alone, "nodes_per_s": n_alone / dt_alone},
+    }))
+
+
+def bench_serve(args):
+    """A Poisson stream of mesh requests (ellipsoid, graded torus, bumped
+    icosphere; triangles log-uniform in [1e3, tmax]), order-8 charts to 1e-10,
+    submitted at their arrival times to the continuous-batching server."""
+    import paper_1909_13356_gb300 as lsm
+    import synth
+    from synth.workloads import make_request_mesh
+    reqs = synth.serve_stream_c5(nreq=args.requests, rate=args.rate, tmax=args.tmax)
+    meshes = [make_request_mesh(r) for r in reqs]
+    ctx = lsm.Context(0)
+    # warm the kernels once
+    m0 = meshes[0]
+    wm = ctx.upload(m0.verts, m0.tris, m0.sigma, n_gl=4)
+    wm.solve_charts(order=8, tol=1e-10, precision=lsm.MIXED)
+    wm.free()
+    srv = lsm.Server(ctx, slots=4)
+    t_start = time.perf_counter()
+    tickets = []
+    max_queue = 0
+    for r, m in zip(reqs, meshes):
+        delay = r["arrival"] - (time.perf_counter() - t_start)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(m.verts, m.tris, m.sigma, n_gl=4, order=8, tol=1e-10))
+        max_queue = max(max_queue, srv.info()["queued"])
+    res = [srv.result(t) for t in tickets]
+    wall = time.perf_counter() - t_start
+    info = srv.info()
+    srv.close()
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in res])
+    nodes = sum(r["stats"].n_converged for r in res if r["status"] == 0)
+    half = len(lat) // 2
+    print(json.dumps({
+        "metric": "serve_latency_p50_ms", "value": float(np.percentile(lat, 50)), "unit": "ms", "n_gpus": 1,
+        "steps": len(res), "warmup": 1, "ms_per_step": wall * 1e3 / len(res), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
+        "config": {"workload": "serve_stream", "requests": len(res), "rate_per_s": args.rate,
+                   "triangles": [1000, args.tmax], "order": 8, "tol": 1e-10, "slots": 4},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "chart_nodes_per_s": nodes / wall, "failed": sum(r["status"] != 0 for r in res),
+        "max_queued": max_queue, "max_running": info["max_running"],
+        "peak_device_bytes": info["peak_in_use_bytes"],
+        "stable": bool(np.median(lat[half:]) < 2.0 * np.median(lat[:half]) + 1000.0),
+    }))
+
+
 def main():
     args = parse()
+    if args.workload == "ellipsoids" and args.impl == "ours":
+        bench_ellipsoids(args)
+        return
+    if args.workload == "serve" and args.impl == "ours":
+        bench_serve(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

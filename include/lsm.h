@@ -42,6 +42,7 @@ extern "C" {
 typedef struct lsm_ctx lsm_ctx;
 typedef struct lsm_mesh lsm_mesh;
 typedef struct lsm_batch lsm_batch;
+typedef struct lsm_server lsm_server;
 
 typedef enum {
     LSM_OK = 0,
@@ -50,7 +51,8 @@ typedef enum {
     LSM_E_CUDA = -3,
     LSM_E_MESH = -4,          /* not watertight / not conforming / orientation */
     LSM_E_NOT_CONVERGED = -5, /* reserved: per-node failures go to status arrays */
-    LSM_E_TIMEOUT = -6
+    LSM_E_TIMEOUT = -6,
+    LSM_PENDING = 1           /* lsm_server_poll: the request has not finished */
 } lsm_status;
 
 typedef enum {
@@ -260,6 +262,61 @@ int lsm_batch_free(lsm_batch* batch);
  */
 int lsm_batch_solve_charts(lsm_batch* batch, int order, double tol, int max_iter, int precision, int use_graph,
                            double* x_out, double* h_out, int32_t* status, lsm_solve_stats* stats, void* stream);
+
+/*
+ * Serving: a continuous-batching request server over one context (the paper
+ * has no serving layer; this is this library's addition).  Requests are
+ * queued in arrival order; `slots` worker threads, each with its own CUDA
+ * stream, take the head of the queue as soon as a slot is free and the
+ * request's estimated device footprint (mesh state plus chart-solve state)
+ * fits in the HBM budget next to the running requests (a request larger
+ * than the whole budget runs alone).  Each admitted request is uploaded
+ * (lsm_mesh_upload), solved (lsm_solve_charts) on its slot's stream, copied
+ * back and freed; requests on different slots overlap on the GPU.
+ *   hbm_budget_bytes <= 0: 80% of the device memory free at creation.
+ * lsm_server_submit copies the request's arrays and returns at once.
+ * lsm_server_poll returns LSM_PENDING until the request is done (or blocks
+ * with wait != 0), then fills `out`; the result arrays stay owned by the
+ * server until lsm_server_release.  Times are milliseconds on the server's
+ * clock.  lsm_server_destroy finishes every queued request first.
+ * Per-launch profiling (lsm_set_profiling) must be off while a server runs.
+ */
+typedef struct {
+    const double* verts;     /* host double[nv][3] */
+    int64_t nv;
+    const int32_t* tris;     /* host int32[nt][3] */
+    int64_t nt;
+    const double* sigma;     /* host double[nt] or NULL (0.5 sqrt(2 area)) */
+    lsm_quad rule;           /* source rule; n_gl == 0 selects {4, 0} */
+    int32_t order;           /* chart order, as lsm_solve_charts */
+    double tol;
+    int32_t max_iter;        /* <= 0 selects 20 */
+    int32_t precision;       /* LSM_FP64 or LSM_MIXED */
+} lsm_request;
+
+typedef struct {
+    int32_t status;          /* LSM_OK or the error of the request */
+    int64_t n_nodes;
+    double t_submit_ms, t_start_ms, t_done_ms;
+    int64_t device_bytes;    /* footprint charged against the budget */
+    lsm_solve_stats stats;
+    const double* x;         /* [n_nodes][3], server-owned */
+    const double* h;         /* [n_nodes] */
+    const int32_t* node_status;
+} lsm_result;
+
+typedef struct {
+    int64_t queued, running, max_running;
+    int64_t budget_bytes, in_use_bytes, peak_in_use_bytes;
+    double now_ms;
+} lsm_server_info_t;
+
+int lsm_server_create(lsm_ctx* ctx, int slots, int64_t hbm_budget_bytes, lsm_server** out);
+int lsm_server_submit(lsm_server* server, const lsm_request* request, int64_t* ticket);
+int lsm_server_poll(lsm_server* server, int64_t ticket, int wait, lsm_result* out);
+int lsm_server_release(lsm_server* server, int64_t ticket);
+int lsm_server_info(lsm_server* server, lsm_server_info_t* out);
+int lsm_server_destroy(lsm_server* server);
 
 #ifdef __cplusplus
 }

@@ -38,7 +38,8 @@ _ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVER
 EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "lsm_set_profiling",
            "lsm_read_stats", "lsm_mesh_upload", "lsm_mesh_free", "lsm_mesh_get_info", "lsm_eval_phi_grad",
            "lsm_eval_phi_grad_noalloc", "lsm_solve_charts", "lsm_batch_create", "lsm_batch_free",
-           "lsm_batch_solve_charts")
+           "lsm_batch_solve_charts", "lsm_server_create", "lsm_server_submit", "lsm_server_poll", "lsm_server_release",
+           "lsm_server_info", "lsm_server_destroy")
 
 
 class LsmError(RuntimeError):
@@ -76,6 +77,25 @@ class _Info(ctypes.Structure):
                 ("n_sources", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("sigma_min", ctypes.c_double),
                 ("sigma_max", ctypes.c_double)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("nv", ctypes.c_int64), ("tris", ctypes.c_void_p),
+                ("nt", ctypes.c_int64), ("sigma", ctypes.c_void_p), ("rule", _Quad), ("order", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("t_submit_ms", ctypes.c_double),
+                ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("stats", _Stats), ("x", ctypes.POINTER(ctypes.c_double)), ("h", ctypes.POINTER(ctypes.c_double)),
+                ("node_status", ctypes.POINTER(ctypes.c_int32))]
+
+
+class _ServerInfo(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("max_running", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("in_use_bytes", ctypes.c_int64),
+                ("peak_in_use_bytes", ctypes.c_int64), ("now_ms", ctypes.c_double)]
 
 
 @dataclass
@@ -121,6 +141,12 @@ def load(build_if_needed: bool = True):
         L.lsm_eval_phi_grad.argtypes = [P, P, I64, P, P, I32, P]
         L.lsm_eval_phi_grad_noalloc.argtypes = [P, P, I64, P, P, I32, P]
         L.lsm_solve_charts.argtypes = [P, I32, D, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
+        L.lsm_server_create.argtypes = [P, I32, I64, ctypes.POINTER(P)]
+        L.lsm_server_submit.argtypes = [P, ctypes.POINTER(_Request), ctypes.POINTER(I64)]
+        L.lsm_server_poll.argtypes = [P, I64, I32, ctypes.POINTER(_Result)]
+        L.lsm_server_release.argtypes = [P, I64]
+        L.lsm_server_info.argtypes = [P, ctypes.POINTER(_ServerInfo)]
+        L.lsm_server_destroy.argtypes = [P]
         L.lsm_batch_create.argtypes = [P, ctypes.POINTER(P), I32, P, ctypes.POINTER(P)]
         L.lsm_batch_free.argtypes = [P]
         L.lsm_batch_solve_charts.argtypes = [P, I32, D, I32, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
@@ -341,5 +367,62 @@ class Batch:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (lsm_server_*): requests are admitted
+    in arrival order as worker slots and HBM budget free up, and run
+    concurrently on their slots' streams."""
+
+    def __init__(self, ctx: Context, slots: int = 4, hbm_budget_bytes: int = 0):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._check(ctx._L.lsm_server_create(ctx._h, int(slots), int(hbm_budget_bytes), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0, order: int = 8,
+               tol: float = 1e-10, max_iter: int = 20, precision: int = MIXED) -> int:
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        s = np.ascontiguousarray(sigma, dtype=np.float64) if sigma is not None else None
+        rq = _Request(v.ctypes.data, len(v), t.ctypes.data, len(t), s.ctypes.data if s is not None else None,
+                      _Quad(int(n_gl), int(subdiv)), int(order), float(tol), int(max_iter), int(precision))
+        tk = ctypes.c_int64()
+        self.ctx._check(self.ctx._L.lsm_server_submit(self._h, ctypes.byref(rq), ctypes.byref(tk)))
+        return int(tk.value)
+
+    def result(self, ticket: int, wait: bool = True, release: bool = True):
+        """The finished request as a dict (arrays copied), or None while pending."""
+        r = _Result()
+        rc = self.ctx._L.lsm_server_poll(self._h, int(ticket), 1 if wait else 0, ctypes.byref(r))
+        if rc == 1:
+            return None
+        self.ctx._check(rc)
+        n = int(r.n_nodes)
+        out = {"status": int(r.status), "n_nodes": n, "t_submit_ms": r.t_submit_ms, "t_start_ms": r.t_start_ms,
+               "t_done_ms": r.t_done_ms, "device_bytes": int(r.device_bytes), "stats": _stats(r.stats)}
+        if r.status == 0 and n > 0:
+            out["x"] = np.ctypeslib.as_array(r.x, shape=(n, 3)).copy()
+            out["h"] = np.ctypeslib.as_array(r.h, shape=(n,)).copy()
+            out["node_status"] = np.ctypeslib.as_array(r.node_status, shape=(n,)).copy()
+        if release:
+            self.ctx._L.lsm_server_release(self._h, int(ticket))
+        return out
+
+    def info(self) -> dict:
+        inf = _ServerInfo()
+        self.ctx._check(self.ctx._L.lsm_server_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in _ServerInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.ctx._L.lsm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

@@ -284,7 +284,7 @@ int lsm_read_stats(lsm_ctx* c, lsm_ctx_stats* out, int reset)
     ctx->prof_events.clear();
     unsigned long long pr[2] = {0, 0};
     LSM_CUDA_TRY(ctx, cudaMemcpy(pr, ctx->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
-    out->launches = ctx->launches;
+    out->launches = ctx->launches.load();
     out->pairs_near = (int64_t)pr[0];
     out->pairs_far = (int64_t)pr[1];
     out->pair_kernel_launches = ctx->prof_launches;
@@ -303,7 +303,7 @@ const char* lsm_last_error(const lsm_ctx* c)
     return c->c.err.c_str();
 }
 
-int64_t lsm_launch_count(const lsm_ctx* c) { return c ? c->c.launches : -1; }
+int64_t lsm_launch_count(const lsm_ctx* c) { return c ? c->c.launches.load() : -1; }
 
 int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     const double* sigma, const lsm_quad* rule, void* stream, lsm_mesh** out)

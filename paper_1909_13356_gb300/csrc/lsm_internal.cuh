@@ -5,6 +5,8 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -22,12 +24,27 @@ constexpr int kTile = 128;
 // Targets per thread block row of the pair kernels (threads * targets/thread).
 constexpr int kEvalThreads = 128;
 
+// Last-error message, safe to set from several host threads.
+class ErrorText {
+public:
+    ErrorText& operator=(const std::string& s) {
+        std::lock_guard<std::mutex> lk(mu_);
+        text_ = s;
+        return *this;
+    }
+    const char* c_str() const { return text_.c_str(); }
+
+private:
+    std::mutex mu_;
+    std::string text_;
+};
+
 struct Ctx {
     int device = 0;
     int num_sms = 0;
     lsm_options opt{};
-    std::string err;
-    int64_t launches = 0;
+    ErrorText err;
+    std::atomic<int64_t> launches{0};
     int* d_flag = nullptr;   // device error word (bounded waits, bad sizes)
     unsigned long long* d_pairs = nullptr;  // [2]: pairs evaluated in near / far tiles
     bool profiling = false;

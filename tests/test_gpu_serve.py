@@ -1,0 +1,74 @@
+"""Serving: requests admitted as slots and HBM budget free up run concurrently
+on separate streams; each result equals the same request solved alone, a
+failing request reports its error without affecting the others, and a tight
+budget serialises admission without changing results."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1909_13356_gb300 as lsm
+    ctx = lsm.Context(0)
+    g = synth.rng(55)
+    ms = [synth.ellipsoid(int(T), g) for T in (300, 900, 500, 1500, 240, 700)]
+    ms.append(synth.torus(1.0, 0.3, 40, 12, 20.0, 0.05, seed=56))
+    alone = []
+    for m in ms:
+        mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
+        alone.append(mesh.solve_charts(order=8, tol=1e-10, precision=lsm.MIXED))
+        mesh.free()
+    return lsm, ctx, ms, alone
+
+
+def _check(res, ref):
+    x, h, st, stats = ref
+    assert res["status"] == 0
+    assert np.all(res["node_status"] & 255 == 0)
+    assert np.abs(res["x"] - x).max() < 1e-9
+
+
+def test_served_results_equal_alone(setup):
+    lsm, ctx, ms, alone = setup
+    srv = lsm.Server(ctx, slots=3)
+    tickets = [srv.submit(m.verts, m.tris, m.sigma, n_gl=4, order=8, tol=1e-10) for m in ms]
+    results = [srv.result(t) for t in tickets]
+    info = srv.info()
+    srv.close()
+    for r, ref in zip(results, alone):
+        _check(r, ref)
+    assert info["max_running"] >= 2          # requests overlapped
+    assert all(r["t_done_ms"] >= r["t_start_ms"] >= r["t_submit_ms"] for r in results)
+
+
+def test_tight_budget_serialises_admission(setup):
+    lsm, ctx, ms, alone = setup
+    srv = lsm.Server(ctx, slots=4, hbm_budget_bytes=1)   # every request is larger than the budget
+    tickets = [srv.submit(m.verts, m.tris, m.sigma, n_gl=4, order=8, tol=1e-10) for m in ms[:4]]
+    results = [srv.result(t) for t in tickets]
+    info = srv.info()
+    srv.close()
+    assert info["max_running"] == 1
+    for r, ref in zip(results, alone[:4]):
+        _check(r, ref)
+
+
+def test_failing_request_is_isolated(setup):
+    lsm, ctx, ms, alone = setup
+    srv = lsm.Server(ctx, slots=2)
+    bad = synth.cube(1.0, 2)
+    t_ok = srv.submit(ms[0].verts, ms[0].tris, ms[0].sigma, n_gl=4, order=8, tol=1e-10)
+    t_bad = srv.submit(bad.verts, bad.tris[:-1], None, order=8)     # open mesh
+    t_ok2 = srv.submit(ms[2].verts, ms[2].tris, ms[2].sigma, n_gl=4, order=8, tol=1e-10)
+    r_bad = srv.result(t_bad)
+    assert r_bad["status"] == -4
+    _check(srv.result(t_ok), alone[0])
+    _check(srv.result(t_ok2), alone[2])
+    srv.close()
