@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "lsm_internal.cuh"
 
@@ -609,12 +610,16 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
 }
 
 // ---------------------------------------------------------------- float-float kernel
-// Phi to FP64 accuracy without the FP64 pipe for far tiles: every far-tile
-// quantity that Phi depends on is carried as an unevaluated sum of two
-// floats (about 44 significant bits): the tile-local pair difference, |r|^2,
-// 1/|r| (hardware estimate plus one Newton step evaluated in float-float),
-// 1/|r|^3, nw . r and their product.  grad Phi of far tiles uses the FP32
-// high parts (it only steers Newton).  Near tiles run the FP64 code path.
+// Phi to FP64 accuracy on the FP32 pipes.  Every quantity Phi depends on is
+// carried as an unevaluated sum of two floats (about 44 significant bits):
+// the tile-local pair difference r, |r|^2, 1/|r| (hardware estimate plus one
+// Newton step evaluated in float-float), nw . r and their products.  Far
+// tiles use the Laplace factor 1/|r|^3.  Near pairs use a^3 H(w), w = u^2,
+// H = g(u)/u^3, read from a piecewise polynomial table (kHTabPerUnit
+// intervals per unit of w up to kHTabWmax, degree 6 in the local variable,
+// the three leading coefficients in float-float); beyond kHTabWmax H equals
+// 1/u^3 to 1e-14.  grad Phi keeps mixed accuracy (FP32, compensated sums):
+// it only steers Newton.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
     s = a + b;
@@ -628,14 +633,35 @@ __device__ __forceinline__ void two_diff(float a, float b, float& s, float& e)
     e = (a - (s - bb)) - (b + bb);
 }
 
-constexpr int kFFStage = kTile * 64;  // bytes per stage: 4 float4 or 2 double4 arrays
+constexpr int kHTabPerUnit = 16;
+constexpr int kHTabN = 520;                   // covers w < 32.5 (u < 5.70)
+constexpr float kHTabWmax = (float)kHTabN / kHTabPerUnit;
+__device__ float4 g_htab[kHTabN * 3];         // filled once per device by the host
+
+// ff product of (ah, al) and (bh, bl)
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& h, float& l)
+{
+    h = ah * bh;
+    l = fmaf(ah, bh, -h) + fmaf(ah, bl, al * bh);
+}
+// ff sum (ah, al) + (bh, bl), renormalised
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& h, float& l)
+{
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    h = s + e;
+    l = e - (h - s);
+}
+
+constexpr int kFFStage = kTile * 64;  // bytes per stage: 4 float4 arrays
 
 __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     const float4* __restrict__ spos, const float4* __restrict__ snw, const float4* __restrict__ slo,
-    const float4* __restrict__ snwlo, const double4_32a* __restrict__ dpos, const double4_32a* __restrict__ dnw,
-    EvalArgs A)
+    const float4* __restrict__ snwlo, EvalArgs A)
 {
     __shared__ __align__(128) unsigned char sh[2][kFFStage];
+    __shared__ __align__(16) float4 s_htab[kHTabN * 3];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float s_bb[6];
 
@@ -656,26 +682,24 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     }
     const int i = base + tid;
     const bool valid = i < tend;
+    for (int k = tid; k < kHTabN * 3; k += kEvalThreads) s_htab[k] = g_htab[k];
 
-    double x[3];
     float xh[3], xl[3];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        x[c] = valid ? A.tx[c * A.ld + i] : 0.0;
-        xh[c] = __double2float_rn(x[c]);
-        xl[c] = __double2float_rn(x[c] - (double)xh[c]);
+        const double v = valid ? A.tx[c * A.ld + i] : 0.0;
+        xh[c] = __double2float_rn(v);
+        xl[c] = __double2float_rn(v - (double)xh[c]);
         if (valid) {
-            lo[c] = __double2float_rd(x[c]);
-            hi[c] = __double2float_ru(x[c]);
+            lo[c] = __double2float_rd(v);
+            hi[c] = __double2float_ru(v);
         }
     }
-    block_bbox(lo, hi, s_bb);
+    block_bbox(lo, hi, s_bb);   // also orders the table fill before its first use
 
-    double accd[4] = {0.0, 0.0, 0.0, 0.0};   // near tiles, FP64 (double-double sum)
-    double accl[4] = {0.0, 0.0, 0.0, 0.0};
-    float ph = 0.0f, pl = 0.0f;               // far Phi, float-float
-    float gh[3] = {0.0f, 0.0f, 0.0f}, gl[3] = {0.0f, 0.0f, 0.0f};  // far grad, compensated FP32
+    float ph = 0.0f, pl = 0.0f;                                     // Phi, float-float
+    float gh[3] = {0.0f, 0.0f, 0.0f}, gl[3] = {0.0f, 0.0f, 0.0f};   // grad, compensated FP32
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -685,20 +709,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     __syncthreads();
     auto issue = [&](int t, int b) {
         const int cnt = (int)A.thi[t].w;
-        const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
-        mbar_expect_tx(&bar[b], (uint32_t)cnt * 64u);
+        const uint32_t by = (uint32_t)cnt * 16u;
+        mbar_expect_tx(&bar[b], 4u * by);
         const size_t o = (size_t)t * kTile;
-        if (far) {
-            const uint32_t by = (uint32_t)cnt * 16u;
-            bulk_g2s(sh[b] + 0 * kTile * 16, spos + o, by, &bar[b]);
-            bulk_g2s(sh[b] + 1 * kTile * 16, snw + o, by, &bar[b]);
-            bulk_g2s(sh[b] + 2 * kTile * 16, slo + o, by, &bar[b]);
-            bulk_g2s(sh[b] + 3 * kTile * 16, snwlo + o, by, &bar[b]);
-        } else {
-            const uint32_t by = (uint32_t)cnt * 32u;
-            bulk_g2s(sh[b] + 0, dpos + o, by, &bar[b]);
-            bulk_g2s(sh[b] + kTile * 32, dnw + o, by, &bar[b]);
-        }
+        bulk_g2s(sh[b] + 0 * kTile * 16, spos + o, by, &bar[b]);
+        bulk_g2s(sh[b] + 1 * kTile * 16, snw + o, by, &bar[b]);
+        bulk_g2s(sh[b] + 2 * kTile * 16, slo + o, by, &bar[b]);
+        bulk_g2s(sh[b] + 3 * kTile * 16, snwlo + o, by, &bar[b]);
     };
     if (tid == 0 && t0 < t1) issue(t0, 0);
 
@@ -717,48 +734,78 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         }
         const int cnt = (int)A.thi[t].w;
         const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
-        if (far) {
-            pairs_far += valid ? cnt : 0;
-            const float4 ch = A.tchi[t], cl = A.tclo[t];
-            const float cc[3] = {ch.x, ch.y, ch.z}, cc2[3] = {cl.x, cl.y, cl.z};
-            float qh[3], ql[3];
+        if (far) pairs_far += valid ? cnt : 0;
+        else pairs_near += valid ? cnt : 0;
+        const float4 ch = A.tchi[t], cl = A.tclo[t];
+        const float cc[3] = {ch.x, ch.y, ch.z}, cc2[3] = {cl.x, cl.y, cl.z};
+        float qh[3], ql[3];
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                float s0, e0;
-                two_diff(xh[c], cc[c], s0, e0);
-                const float tt = (xl[c] - cc2[c]) + e0;
-                qh[c] = s0 + tt;
-                ql[c] = tt - (qh[c] - s0);
-            }
-            const float4* sp = reinterpret_cast<const float4*>(sh[b]);
-            const float4* sn = sp + kTile;
-            const float4* sl = sp + 2 * kTile;
-            const float4* snl = sp + 3 * kTile;
-            for (int c0 = 0; c0 < cnt; c0 += kChunk) {
-                const int c1 = min(cnt, c0 + kChunk);
-                float g[3] = {0.0f, 0.0f, 0.0f};
-                float cph = 0.0f, cpl = 0.0f;   // this chunk's Phi, float-float
+        for (int c = 0; c < 3; c++) {
+            float s0, e0;
+            two_diff(xh[c], cc[c], s0, e0);
+            const float tt = (xl[c] - cc2[c]) + e0;
+            qh[c] = s0 + tt;
+            ql[c] = tt - (qh[c] - s0);
+        }
+        const float4* sp = reinterpret_cast<const float4*>(sh[b]);
+        const float4* sn = sp + kTile;
+        const float4* sl = sp + 2 * kTile;
+        const float4* snl = sp + 3 * kTile;
+        for (int c0 = 0; c0 < cnt; c0 += kChunk) {
+            const int c1 = min(cnt, c0 + kChunk);
+            float g[3] = {0.0f, 0.0f, 0.0f};
+            float cph = 0.0f, cpl = 0.0f;   // this chunk's Phi, float-float
 #pragma unroll 2
-                for (int s = c0; s < c1; s++) {
-                    const float4 y = sp[s], n = sn[s], yl = sl[s], nl = snl[s];
-                    float dxh, dxl, dyh, dyl, dzh, dzl, e;
-                    two_diff(y.x, qh[0], dxh, e);
-                    dxl = e + (yl.x - ql[0]);
-                    two_diff(y.y, qh[1], dyh, e);
-                    dyl = e + (yl.y - ql[1]);
-                    two_diff(y.z, qh[2], dzh, e);
-                    dzl = e + (yl.z - ql[2]);
-                    // |r|^2
-                    const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
-                    float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
-                    e0 = fmaf(2.0f * dxh, dxl, e0);
-                    e1 = fmaf(2.0f * dyh, dyl, e1);
-                    e2 = fmaf(2.0f * dzh, dzl, e2);
-                    float s01, t01, rh, t2;
-                    two_sum(p0, p1, s01, t01);
-                    two_sum(s01, p2, rh, t2);
-                    const float rl = ((e0 + e1) + e2) + (t01 + t2);
-                    // 1/|r| = r0 (1 + delta/2), delta = 1 - |r|^2 r0^2
+            for (int s = c0; s < c1; s++) {
+                const float4 y = sp[s], n = sn[s], yl = sl[s], nl = snl[s];
+                float dxh, dxl, dyh, dyl, dzh, dzl, e;
+                two_diff(y.x, qh[0], dxh, e);
+                dxl = e + (yl.x - ql[0]);
+                two_diff(y.y, qh[1], dyh, e);
+                dyl = e + (yl.y - ql[1]);
+                two_diff(y.z, qh[2], dzh, e);
+                dzl = e + (yl.z - ql[2]);
+                // |r|^2
+                const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
+                float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
+                e0 = fmaf(2.0f * dxh, dxl, e0);
+                e1 = fmaf(2.0f * dyh, dyl, e1);
+                e2 = fmaf(2.0f * dzh, dzl, e2);
+                float s01, t01, rh, t2;
+                two_sum(p0, p1, s01, t01);
+                two_sum(s01, p2, rh, t2);
+                const float rl = ((e0 + e1) + e2) + (t01 + t2);
+                // radial factor fH (float-float)
+                float fHh, fHl;
+                float wh = 0.0f, aah = 0.0f, aal = 0.0f;
+                if (!far) {
+                    aah = y.w * y.w;
+                    aal = fmaf(y.w, y.w, -aah) + 2.0f * y.w * yl.w;
+                    wh = rh * aah;
+                }
+                if (!far && wh < kHTabWmax) {
+                    const float wl = fmaf(rh, aah, -wh) + fmaf(rh, aal, rl * aah);
+                    const int k = min((int)(wh * (float)kHTabPerUnit), kHTabN - 1);
+                    const float wc = ((float)k + 0.5f) * (1.0f / kHTabPerUnit);
+                    float th, te;
+                    two_diff(wh, wc, th, te);
+                    const float tl = te + wl;
+                    const float4 c01 = s_htab[3 * k], c23 = s_htab[3 * k + 1], c45 = s_htab[3 * k + 2];
+                    // tail in FP32, then three float-float Horner steps
+                    const float q = fmaf(fmaf(fmaf(c45.y, th, c45.x), th, c23.w), th, c23.z);
+                    float Hh, Hl, mh, ml;
+                    ff_mul(th, tl, q, 0.0f, mh, ml);
+                    ff_add(c23.x, c23.y, mh, ml, Hh, Hl);
+                    ff_mul(th, tl, Hh, Hl, mh, ml);
+                    ff_add(c01.z, c01.w, mh, ml, Hh, Hl);
+                    ff_mul(th, tl, Hh, Hl, mh, ml);
+                    ff_add(c01.x, c01.y, mh, ml, Hh, Hl);
+                    // a^3 = a^2 a
+                    float a3h, a3l;
+                    ff_mul(aah, aal, y.w, yl.w, a3h, a3l);
+                    ff_mul(a3h, a3l, Hh, Hl, fHh, fHl);
+                } else {
+                    // 1/|r| = r0 (1 + delta/2), delta = 1 - |r|^2 r0^2; fH = 1/|r|^3
                     const float r0 = rsqrtf(rh);
                     const float a = r0 * r0, ae = fmaf(r0, r0, -a);
                     const float hh = rh * a;
@@ -767,74 +814,58 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                     he = fmaf(rl, a, he);
                     const float delta = (1.0f - hh) - he;
                     const float ril = 0.5f * r0 * delta;
-                    // 1/|r|^3
                     const float q2l = fmaf(2.0f * r0, ril, ae);
-                    const float q3h = a * r0;
-                    const float q3l = fmaf(a, r0, -q3h) + fmaf(a, ril, q2l * r0);
-                    // nw . r
-                    const float d0 = n.x * dxh, d1 = n.y * dyh, d2 = n.z * dzh;
-                    const float f0 = fmaf(n.x, dxh, -d0), f1 = fmaf(n.y, dyh, -d1), f2 = fmaf(n.z, dzh, -d2);
-                    float sd, u1, dh, u2;
-                    two_sum(d0, d1, sd, u1);
-                    two_sum(sd, d2, dh, u2);
-                    const float dl = ((f0 + f1) + f2) + (u1 + u2) +
-                                     fmaf(n.x, dxl, fmaf(n.y, dyl, n.z * dzl)) +
-                                     fmaf(nl.x, dxh, fmaf(nl.y, dyh, nl.z * dzh));
-                    // q = (nw . r) / |r|^3, added to the float-float Phi
-                    const float qh_ = dh * q3h;
-                    const float ql_ = fmaf(dh, q3h, -qh_) + fmaf(dh, q3l, dl * q3h);
-                    float sph, tph;
-                    two_sum(cph, qh_, sph, tph);
-                    cph = sph;
-                    cpl += tph + ql_;
-                    // grad from the high parts
-                    const float rif = r0 + ril;
-                    const float ri2 = rif * rif;
-                    const float ri3 = ri2 * rif;
+                    fHh = a * r0;
+                    fHl = fmaf(a, r0, -fHh) + fmaf(a, ril, q2l * r0);
+                }
+                // nw . r
+                const float d0 = n.x * dxh, d1 = n.y * dyh, d2 = n.z * dzh;
+                const float f0 = fmaf(n.x, dxh, -d0), f1 = fmaf(n.y, dyh, -d1), f2 = fmaf(n.z, dzh, -d2);
+                float sd, u1, dh, u2;
+                two_sum(d0, d1, sd, u1);
+                two_sum(sd, d2, dh, u2);
+                const float dl = ((f0 + f1) + f2) + (u1 + u2) + fmaf(n.x, dxl, fmaf(n.y, dyl, n.z * dzl)) +
+                                 fmaf(nl.x, dxh, fmaf(nl.y, dyh, nl.z * dzh));
+                // Phi term
+                float qh_, ql_;
+                ff_mul(dh, dl, fHh, fHl, qh_, ql_);
+                float sph, tph;
+                two_sum(cph, qh_, sph, tph);
+                cph = sph;
+                cpl += tph + ql_;
+                // grad from the high parts (FP32)
+                if (far) {
+                    const float ri = rsqrtf(rh);
+                    const float ri2 = ri * ri;
+                    const float ri3 = ri2 * ri;
                     const float tq = 3.0f * dh * ri3 * ri2;
                     g[0] = fmaf(tq, dxh, fmaf(-n.x, ri3, g[0]));
                     g[1] = fmaf(tq, dyh, fmaf(-n.y, ri3, g[1]));
                     g[2] = fmaf(tq, dzh, fmaf(-n.z, ri3, g[2]));
+                } else {
+                    float fH, FK;
+                    radial32(rh, y.w, fH, FK);
+                    const float tq = dh * FK;
+                    two_sum_acc(gh[0], gl[0], -fmaf(n.x, fH, tq * dxh));
+                    two_sum_acc(gh[1], gl[1], -fmaf(n.y, fH, tq * dyh));
+                    two_sum_acc(gh[2], gl[2], -fmaf(n.z, fH, tq * dzh));
                 }
-#pragma unroll
-                for (int c = 0; c < 3; c++) two_sum_acc(gh[c], gl[c], g[c]);
-                // fold the chunk into the running float-float Phi and renormalise
-                float sh_, eh_;
-                two_sum(ph, cph, sh_, eh_);
-                eh_ += pl + cpl;
-                ph = sh_ + eh_;
-                pl = eh_ - (ph - sh_);
-            }
-        } else {
-            pairs_near += valid ? cnt : 0;
-            const double4_32a* sp = reinterpret_cast<const double4_32a*>(sh[b]);
-            const double4_32a* sn = reinterpret_cast<const double4_32a*>(sh[b] + kTile * 32);
-            double p[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int s = 0; s < cnt; s++) {
-                const double4_32a y = sp[s];
-                const double4_32a n = sn[s];
-                const double dx = y.x - x[0], dy = y.y - x[1], dz = y.z - x[2];
-                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                double fH, FK;
-                radial64(r2, y.w, n.w, fH, FK);
-                const double d = fma(n.x, dx, fma(n.y, dy, n.z * dz));
-                p[0] = fma(d, fH, p[0]);
-                const double tq = d * FK;
-                p[1] -= fma(n.x, fH, tq * dx);
-                p[2] -= fma(n.y, fH, tq * dy);
-                p[3] -= fma(n.z, fH, tq * dz);
             }
 #pragma unroll
-            for (int c = 0; c < 4; c++) two_sum_acc64(accd[c], accl[c], p[c]);
+            for (int c = 0; c < 3; c++) two_sum_acc(gh[c], gl[c], g[c]);
+            // fold the chunk into the running float-float Phi, renormalised
+            float nh_, nl_;
+            ff_add(ph, pl, cph, cpl, nh_, nl_);
+            ph = nh_;
+            pl = nl_;
         }
         __syncthreads();
     }
     if (valid) {
         const int64_t plane = (int64_t)A.nt;
         double* out = A.out + (int64_t)blockIdx.y * 4 * plane;
-        out[i] = (accd[0] + ((double)ph + (double)pl)) + accl[0];
-        for (int c = 0; c < 3; c++)
-            out[(c + 1) * plane + i] = (accd[c + 1] + ((double)gh[c] + (double)gl[c])) + accl[c + 1];
+        out[i] = (double)ph + (double)pl;
+        for (int c = 0; c < 3; c++) out[(c + 1) * plane + i] = (double)gh[c] + (double)gl[c];
     }
     count_pairs(A.pairs, pairs_near, pairs_far);
 }
@@ -848,6 +879,70 @@ __global__ void k_reduce_splits(const double* __restrict__ part, int nsplit, int
     for (int k = 0; k < nsplit; k++)
         for (int c = 0; c < 4; c++) s[c] += part[((int64_t)k * 4 + c) * nt + i];
     for (int c = 0; c < 4; c++) res[(int64_t)c * nt + i] = s[c];
+}
+
+// H(w) = g(u)/u^3, w = u^2, in long double: the power series for w < 1,
+// the closed form with erfl/expl otherwise.
+long double h_of_w(long double w)
+{
+    const long double tsp = 2.0L / sqrtl(3.14159265358979323846264338327950288L);
+    if (w < 1.0L) {
+        long double sum = 0.0L, fact = 1.0L, wp = 1.0L;
+        for (int k = 1; k < 60; k++) {
+            fact *= k;
+            const long double ck = ((k & 1) ? 1.0L : -1.0L) * (2.0L * k) / (fact * (2.0L * k + 1.0L));
+            const long double term = ck * wp;
+            sum += term;
+            if (fabsl(term) < 1e-30L) break;
+            wp *= w;
+        }
+        return tsp * sum;
+    }
+    const long double u = sqrtl(w);
+    const long double g = erfl(u) - tsp * u * expl(-w);
+    return g / (u * u * u);
+}
+
+// Piecewise polynomial table of H: interval k covers w in [k, k+1)/kHTabPerUnit,
+// p(t) = sum_j c_j t^j with t = w - centre, interpolating H at 7 Chebyshev
+// points (monomial coefficients by solving the Vandermonde system).
+// Layout per interval: {c0h, c0l, c1h, c1l}, {c2h, c2l, c3, c4}, {c5, c6, 0, 0}.
+void build_h_table(float4* out)
+{
+    const int deg = 6;
+    const long double h = 0.5L / kHTabPerUnit;
+    for (int k = 0; k < kHTabN; k++) {
+        const long double wc = (k + 0.5L) / kHTabPerUnit;
+        long double V[7][8];
+        for (int r = 0; r <= deg; r++) {
+            const long double t = h * cosl(3.14159265358979323846264338327950288L * (r + 0.5L) / (deg + 1));
+            long double tp = 1.0L;
+            for (int j = 0; j <= deg; j++) {
+                V[r][j] = tp;
+                tp *= t;
+            }
+            V[r][deg + 1] = h_of_w(wc + t);
+        }
+        // Gaussian elimination with partial pivoting
+        for (int c = 0; c <= deg; c++) {
+            int piv = c;
+            for (int r = c + 1; r <= deg; r++)
+                if (fabsl(V[r][c]) > fabsl(V[piv][c])) piv = r;
+            for (int j = 0; j <= deg + 1; j++) std::swap(V[c][j], V[piv][j]);
+            for (int r = 0; r <= deg; r++) {
+                if (r == c) continue;
+                const long double f = V[r][c] / V[c][c];
+                for (int j = c; j <= deg + 1; j++) V[r][j] -= f * V[c][j];
+            }
+        }
+        long double cf[7];
+        for (int j = 0; j <= deg; j++) cf[j] = V[j][deg + 1] / V[j][j];
+        auto hi = [](long double v) { return (float)v; };
+        auto lo = [](long double v) { return (float)(v - (long double)(float)v); };
+        out[3 * k + 0] = make_float4(hi(cf[0]), lo(cf[0]), hi(cf[1]), lo(cf[1]));
+        out[3 * k + 1] = make_float4(hi(cf[2]), lo(cf[2]), (float)cf[3], (float)cf[4]);
+        out[3 * k + 2] = make_float4((float)cf[5], (float)cf[6], 0.0f, 0.0f);
+    }
 }
 
 bool g_consts_ready[64] = {false};
@@ -877,6 +972,11 @@ int upload_series_constants(Ctx* ctx)
     LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_B64, B, sizeof(double) * kSer64));
     LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_A32, A32, sizeof(A32)));
     LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_B32, B32, sizeof(B32)));
+    {
+        std::vector<float4> tab(kHTabN * 3);
+        build_h_table(tab.data());
+        LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(g_htab, tab.data(), sizeof(float4) * tab.size()));
+    }
     if (ctx->device >= 0 && ctx->device < 64) g_consts_ready[ctx->device] = true;
     return LSM_OK;
 }
@@ -939,8 +1039,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     if (mixed) {
         k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, A);
     } else if (ff) {
-        k_eval_ff<<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, me->s64_pos,
-                                                  me->s64_nw, A);
+        k_eval_ff<<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else {
         k_eval_fp64<kTPT64><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
     }
@@ -984,8 +1083,7 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
     if (mixed) {
         k_eval_mixed<kTPT32><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, A);
     } else if (precision == LSM_FF) {
-        k_eval_ff<<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, v.s64_pos,
-                                                       v.s64_nw, A);
+        k_eval_ff<<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
     } else {
         k_eval_fp64<kTPT64><<<max_items, kEvalThreads, 0, st>>>(v.s64_pos, v.s64_nw, A);
     }

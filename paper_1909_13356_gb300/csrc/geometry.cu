@@ -289,9 +289,10 @@ __global__ void __launch_bounds__(kTile) k_tile_meta(
         const double4_32a q = nw[i];
         const double lx = p.x - C[0], ly = p.y - C[1], lz = p.z - C[2];
         const float hx = __double2float_rn(lx), hy = __double2float_rn(ly), hz = __double2float_rn(lz);
-        s32p[i] = make_float4(hx, hy, hz, __double2float_rn(p.w));
+        const float ah = __double2float_rn(p.w);
+        s32p[i] = make_float4(hx, hy, hz, ah);
         s32l[i] = make_float4(__double2float_rn(lx - (double)hx), __double2float_rn(ly - (double)hy),
-                              __double2float_rn(lz - (double)hz), 0.0f);
+                              __double2float_rn(lz - (double)hz), __double2float_rn(p.w - (double)ah));
         const float nx = __double2float_rn(q.x), ny = __double2float_rn(q.y), nz = __double2float_rn(q.z);
         s32n[i] = make_float4(nx, ny, nz, __double2float_rn(q.w));
         s32nl[i] = make_float4(__double2float_rn(q.x - (double)nx), __double2float_rn(q.y - (double)ny),

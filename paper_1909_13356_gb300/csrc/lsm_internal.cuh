@@ -71,7 +71,7 @@ struct Mesh {
     double4_32a* s64_nw = nullptr;   // (nw / 4 pi, 0)
     float4* s32_pos = nullptr;   // (y - c_tile in FP32, a)
     float4* s32_nw = nullptr;    // (nw / 4 pi, sqrt2 sigma) in FP32
-    float4* s32_lo = nullptr;    // FP32 remainder of the tile-local position, 0
+    float4* s32_lo = nullptr;    // FP32 remainders of the tile-local position and of a
     float4* s32_nwlo = nullptr;  // FP32 remainder of nw / 4 pi, 0 (float-float kernel)
     float4* tile_lo = nullptr;   // bbox lower corner rounded down, w = sigma_max rounded up
     float4* tile_hi = nullptr;   // bbox upper corner rounded up, w = number of nodes in the tile
