@@ -253,6 +253,12 @@ struct EvalArgs {
     int* flag;
     const int4* items; // optional work items (first target, count, first tile, end tile)
     const int* n_items;
+    // float-float kernel only: 0 plain; 1 record the far-tile part into
+    // far_io [4][nt]; 2 evaluate near tiles only and add the recorded far part
+    // moved to x by its gradient (x_old: SoA targets of the record call)
+    int ff_mode;
+    double* far_io;
+    const double* x_old;
     unsigned long long* pairs;  // [2] pairs evaluated in near / far tiles
 };
 
@@ -655,6 +661,7 @@ __device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, f
 }
 
 constexpr int kFFStage = kTile * 64;  // bytes per stage: 4 float4 arrays
+constexpr int kMaxNearTiles = 768;    // near-tile list of one block (incremental mode)
 
 __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     const float4* __restrict__ spos, const float4* __restrict__ snw, const float4* __restrict__ slo,
@@ -664,6 +671,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     __shared__ __align__(16) float4 s_htab[kHTabN * 3];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float s_bb[6];
+    __shared__ int s_near[kMaxNearTiles];
+    __shared__ int s_warp[kEvalThreads / 32];
+    __shared__ int s_nnear;
 
     const int tid = threadIdx.x;
     int base, tend, t0, t1;
@@ -683,6 +693,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     const int i = base + tid;
     const bool valid = i < tend;
     for (int k = tid; k < kHTabN * 3; k += kEvalThreads) s_htab[k] = g_htab[k];
+    int mode = A.ff_mode;
 
     float xh[3], xl[3];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -698,8 +709,42 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     }
     block_bbox(lo, hi, s_bb);   // also orders the table fill before its first use
 
-    float ph = 0.0f, pl = 0.0f;                                     // Phi, float-float
-    float gh[3] = {0.0f, 0.0f, 0.0f}, gl[3] = {0.0f, 0.0f, 0.0f};   // grad, compensated FP32
+    // incremental mode: the block's near tiles, in tile order
+    int nlist = t1 - t0;
+    if (mode == 2) {
+        if (tid == 0) s_nnear = 0;
+        __syncthreads();
+        const int lane = tid & 31, wp = tid >> 5;
+        for (int tb = t0; tb < t1; tb += kEvalThreads) {
+            const int t = tb + tid;
+            const bool nr = t < t1 && !tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+            const unsigned bal = __ballot_sync(0xffffffffu, nr);
+            if (lane == 0) s_warp[wp] = __popc(bal);
+            __syncthreads();
+            int off = s_nnear;
+            for (int k = 0; k < wp; k++) off += s_warp[k];
+            off += __popc(bal & ((1u << lane) - 1u));
+            if (nr && off < kMaxNearTiles) s_near[off] = t;
+            __syncthreads();
+            if (tid == 0) {
+                int tot = 0;
+                for (int k = 0; k < kEvalThreads / 32; k++) tot += s_warp[k];
+                s_nnear += tot;
+            }
+            __syncthreads();
+        }
+        nlist = s_nnear;
+        if (nlist > kMaxNearTiles) {   // too many to list: evaluate everything
+            mode = 0;
+            nlist = t1 - t0;
+        }
+    }
+    auto tile_at = [&](int k) { return mode == 2 ? s_near[k] : t0 + k; };
+
+    float ph = 0.0f, pl = 0.0f;                                     // near Phi, float-float
+    float gh[3] = {0.0f, 0.0f, 0.0f}, gl[3] = {0.0f, 0.0f, 0.0f};   // near grad, compensated FP32
+    float fph = 0.0f, fpl = 0.0f;                                   // far Phi
+    float fgh[3] = {0.0f, 0.0f, 0.0f}, fgl[3] = {0.0f, 0.0f, 0.0f}; // far grad
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -717,18 +762,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         bulk_g2s(sh[b] + 2 * kTile * 16, slo + o, by, &bar[b]);
         bulk_g2s(sh[b] + 3 * kTile * 16, snwlo + o, by, &bar[b]);
     };
-    if (tid == 0 && t0 < t1) issue(t0, 0);
+    if (tid == 0 && nlist > 0) issue(tile_at(0), 0);
 
     unsigned long long pairs_near = 0, pairs_far = 0;
-    for (int t = t0; t < t1; t++) {
-        const int it = t - t0;
+    for (int it = 0; it < nlist; it++) {
+        const int t = tile_at(it);
         const int b = it & 1;
-        if (tid == 0 && t + 1 < t1) issue(t + 1, b ^ 1);
+        if (tid == 0 && it + 1 < nlist) issue(tile_at(it + 1), b ^ 1);
         const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), kWaitLimit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(A.flag, kErrWaitTimeout);
-                if (t + 1 < t1) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
+                if (it + 1 < nlist) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
             }
             break;
         }
@@ -851,21 +896,52 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                     two_sum_acc(gh[2], gl[2], -fmaf(n.z, fH, tq * dzh));
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 3; c++) two_sum_acc(gh[c], gl[c], g[c]);
-            // fold the chunk into the running float-float Phi, renormalised
+            // fold the chunk into the running float-float sums, renormalised
             float nh_, nl_;
-            ff_add(ph, pl, cph, cpl, nh_, nl_);
-            ph = nh_;
-            pl = nl_;
+            if (far) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) two_sum_acc(fgh[c], fgl[c], g[c]);
+                ff_add(fph, fpl, cph, cpl, nh_, nl_);
+                fph = nh_;
+                fpl = nl_;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; c++) two_sum_acc(gh[c], gl[c], g[c]);
+                ff_add(ph, pl, cph, cpl, nh_, nl_);
+                ph = nh_;
+                pl = nl_;
+            }
         }
         __syncthreads();
     }
     if (valid) {
         const int64_t plane = (int64_t)A.nt;
         double* out = A.out + (int64_t)blockIdx.y * 4 * plane;
-        out[i] = (double)ph + (double)pl;
-        for (int c = 0; c < 3; c++) out[(c + 1) * plane + i] = (double)gh[c] + (double)gl[c];
+        double phi = (double)ph + (double)pl;
+        double gr[3];
+        for (int c = 0; c < 3; c++) gr[c] = (double)gh[c] + (double)gl[c];
+        const double fphi = (double)fph + (double)fpl;
+        double fgr[3];
+        for (int c = 0; c < 3; c++) fgr[c] = (double)fgh[c] + (double)fgl[c];
+        if (mode == 2) {
+            // recorded far part, moved to x along its gradient
+            double fp = A.far_io[i];
+            for (int c = 0; c < 3; c++) {
+                const double g0 = A.far_io[(c + 1) * plane + i];
+                fp += g0 * (A.tx[c * A.ld + i] - A.x_old[c * A.ld + i]);
+                gr[c] += g0;
+            }
+            phi += fp;
+        } else {
+            if (mode == 1) {
+                A.far_io[i] = fphi;
+                for (int c = 0; c < 3; c++) A.far_io[(c + 1) * plane + i] = fgr[c];
+            }
+            phi += fphi;
+            for (int c = 0; c < 3; c++) gr[c] += fgr[c];
+        }
+        out[i] = phi;
+        for (int c = 0; c < 3; c++) out[(c + 1) * plane + i] = gr[c];
     }
     count_pairs(A.pairs, pairs_near, pairs_far);
 }
@@ -993,7 +1069,8 @@ int eval_init_constants(Ctx* ctx) { return upload_series_constants(ctx); }
 
 // Phi and grad at n sorted targets (SoA x with stride ld) into res [4][n]
 // (phi, then the three gradient components).
-int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int precision, cudaStream_t st)
+int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int precision, cudaStream_t st,
+                const FFIncremental* inc)
 {
     if (t.n <= 0) return LSM_OK;
     const bool mixed = precision == LSM_MIXED;
@@ -1005,6 +1082,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     const int want = ctx->num_sms * 16;
     int nsplit = 1;
     if (nblk < want) nsplit = std::min((want + nblk - 1) / nblk, std::max(1, ntiles / 4));
+    if (ff && inc && inc->mode != 0) nsplit = 1;   // the recorded far part is per target, not per split
     const int tps = (ntiles + nsplit - 1) / nsplit;
     nsplit = (ntiles + tps - 1) / tps;
 
@@ -1029,6 +1107,14 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     A.pairs = ctx->d_pairs;
     A.items = nullptr;
     A.n_items = nullptr;
+    A.ff_mode = 0;
+    A.far_io = nullptr;
+    A.x_old = nullptr;
+    if (ff && inc) {
+        A.ff_mode = inc->mode;
+        A.far_io = inc->far_io;
+        A.x_old = inc->x_old;
+    }
     dim3 grid(nblk, nsplit);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (ctx->profiling) {
@@ -1080,6 +1166,9 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
     A.pairs = ctx->d_pairs;
     A.items = items;
     A.n_items = n_items;
+    A.ff_mode = 0;
+    A.far_io = nullptr;
+    A.x_old = nullptr;
     if (mixed) {
         k_eval_mixed<kTPT32><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, A);
     } else if (precision == LSM_FF) {
@@ -1212,6 +1301,9 @@ int eval_noalloc(Ctx* ctx, const Mesh* me, const double* x, int64_t n, double* p
     A.pairs = ctx->d_pairs;
     A.items = nullptr;
     A.n_items = nullptr;
+    A.ff_mode = 0;
+    A.far_io = nullptr;
+    A.x_old = nullptr;
     dim3 grid(nblk, nsplit);
     if (mixed) {
         k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, A);

@@ -188,8 +188,17 @@ struct Targets {
     int n;
 };
 int eval_init_constants(Ctx* ctx);
+// Float-float evaluation in two calls on the same targets: mode 1 records the
+// far-tile part of Phi and grad Phi into far_io [4][n]; mode 2 then
+// evaluates only the near tiles and adds the recorded far part moved to the
+// new positions along its gradient (x_old = the targets of the mode 1 call).
+struct FFIncremental {
+    int mode;
+    double* far_io;
+    const double* x_old;
+};
 int eval_sorted(Ctx* ctx, const Mesh* mesh, const Targets& t, double* res, int precision,
-                cudaStream_t st);
+                cudaStream_t st, const FFIncremental* inc = nullptr);
 // Targets grouped by work items (int4: first target, count, first tile, end
 // tile; at most eval_item_targets(precision) targets each); the number of
 // items is read on the device from *n_items, the grid covers max_items.

@@ -90,6 +90,7 @@ __device__ __forceinline__ void newton_update_one(int i, int k, int64_t p, const
                                                   NodeState& S, int mixed_eval, int accept_mixed, double tol,
                                                   double sw, int max_iter)
 {
+    if (S.st[i] != kPending) return;   // listed again after it stopped
     const double r = R[k] - 0.5;
     const int it = S.it[i] + 1;
     S.it[i] = it;
@@ -312,12 +313,43 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
     if (rc) return rc;
     int nact = N;
     const int accept_mixed = tol >= ctx->opt.mixed_accept ? 1 : 0;
+    // float-float sweeps come in pairs: the first records the far-tile part
+    // of Phi for its list of nodes, the second re-evaluates the same list
+    // (same blocks, so the same near/far split) with near tiles only and the
+    // recorded far part moved along its gradient; the Newton steps between
+    // them are ~1e-8 sigma, where the far part is linear to ~1e-14
+    int32_t* Lrec = nullptr;
+    double *Trec = nullptr, *Rfar = nullptr;
+    int nrec = 0, ff_stage = 0;
+    if (mixed) {
+        LSM_CUDA_TRY(ctx, s.get(&Lrec, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&Trec, 3 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&Rfar, 4 * (size_t)N));
+    }
     int iter = 0;
     for (; iter < max_iter && nact > 0; iter++) {
         if (iter < 32) S0.active_per_iter[iter] = nact;
         for (int m = mixed ? 0 : 1; m <= 1; m++) {
             const int32_t* L = act;
             int nl = nact;
+            if (mixed && m == 1 && ff_stage == 1) {
+                // verification sweep on the recorded list
+                L = Lrec;
+                nl = nrec;
+                ff_stage = 0;
+                if (nl == 0) continue;
+                k_gather_targets<<<nb(nl), 256, 0, st>>>(L, nl, S, T);
+                LSM_LAUNCHED(ctx);
+                Targets tg{T, nl, nl};
+                FFIncremental inc{2, Rfar, Trec};
+                rc = eval_sorted(ctx, me, tg, R, LSM_FF, st, &inc);
+                if (rc) return rc;
+                k_newton_update<<<nb(nl), 256, 0, st>>>(L, nl, R, S, 0, accept_mixed, tol, ctx->opt.mixed_switch,
+                                                         max_iter);
+                LSM_LAUNCHED(ctx);
+                S0.evals_fp64 += nl;
+                continue;
+            }
             if (mixed) {
                 k_mode_flags<<<nb(nact), 256, 0, st>>>(act, S.mode, nact, flags);
                 LSM_LAUNCHED(ctx);
@@ -332,8 +364,19 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
             k_gather_targets<<<nb(nl), 256, 0, st>>>(L, nl, S, T);
             LSM_LAUNCHED(ctx);
             Targets tg{T, nl, nl};
-            rc = eval_sorted(ctx, me, tg, R, m == 0 ? LSM_MIXED : (mixed ? LSM_FF : LSM_FP64), st);
-            if (rc) return rc;
+            if (mixed && m == 1) {
+                // recording float-float sweep
+                FFIncremental inc{1, Rfar, nullptr};
+                rc = eval_sorted(ctx, me, tg, R, LSM_FF, st, &inc);
+                if (rc) return rc;
+                LSM_CUDA_TRY(ctx, cudaMemcpyAsync(Lrec, L, sizeof(int32_t) * nl, cudaMemcpyDeviceToDevice, st));
+                LSM_CUDA_TRY(ctx, cudaMemcpyAsync(Trec, T, sizeof(double) * 3 * nl, cudaMemcpyDeviceToDevice, st));
+                nrec = nl;
+                ff_stage = 1;
+            } else {
+                rc = eval_sorted(ctx, me, tg, R, m == 0 ? LSM_MIXED : LSM_FP64, st);
+                if (rc) return rc;
+            }
             k_newton_update<<<nb(nl), 256, 0, st>>>(L, nl, R, S, m == 0 ? 1 : 0, accept_mixed, tol,
                                                      ctx->opt.mixed_switch, max_iter);
             LSM_LAUNCHED(ctx);
