@@ -44,12 +44,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "ff"],
+                    help="precision of the evaluation (ff: with --no-charts only)")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--targets", type=int, default=1_000_000)
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--small", action="store_true", help="small torus (quick check)")
-    ap.add_argument("--workload", default="torus", choices=["torus", "ellipsoids", "serve"],
+    ap.add_argument("--workload", default="torus", choices=["torus", "ellipsoids", "serve", "icosphere"],
                     help="torus: the default line; ellipsoids: 512 meshes in one batched, graph-captured "
                          "solve; serve: a Poisson request stream through the server")
     ap.add_argument("--requests", type=int, default=200)
@@ -263,8 +264,56 @@ def bench_serve(args):
     }))
 
 
+def bench_icosphere(args):
+    """Bumped icosphere, level 8 (1,310,720 triangles, Duffy 4x4 sources =
+    20,971,520 nodes): mixed-path Phi/grad-Phi on a 1e5-target subsample of
+    the targets within 3 sigma; error of the mixed path against the
+    float-float path on 1e4 of them and against the FP64 oracle on 64."""
+    import torch
+    import oracle
+    import paper_1909_13356_gb300 as lsm
+    import synth
+    w = synth.icosphere_c3(n_targets=100_000)
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    t0 = time.perf_counter()
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
+    t_up = time.perf_counter() - t0
+    x = torch.from_numpy(w["targets"]).cuda()
+    for _ in range(max(1, args.warmup)):
+        mesh.eval_phi_grad(x[:2000], lsm.MIXED)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        p32, g32 = mesh.eval_phi_grad(x, lsm.MIXED)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    pff, gff = mesh.eval_phi_grad(x[:10_000], lsm.FF)
+    err_ff = float((p32[:10_000] - pff).abs().max())
+    y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, 4, 0)
+    xs = w["targets"][:64]
+    po, _ = oracle.phi_grad(y, nw, sg, xs)
+    err_or = float(np.abs(p32[:64].cpu().numpy() - po).max())
+    err_ff_or = float(np.abs(pff[:64].cpu().numpy() - po).max())
+    print(json.dumps({
+        "metric": "phi_grad_evals_per_s", "value": x.shape[0] / (ms / 1e3), "unit": "evals/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": w["name"], "triangles": m.m, "sources": mesh.info()["n_sources"],
+                   "targets": int(x.shape[0]), "precision": "mixed", "upload_s": t_up},
+        "pairs_per_s": x.shape[0] * mesh.info()["n_sources"] / (ms / 1e3),
+        "err_mixed_vs_ff_1e4": err_ff, "err_mixed_vs_oracle_64": err_or, "err_ff_vs_oracle_64": err_ff_or,
+    }))
+
+
 def main():
     args = parse()
+    if args.workload == "icosphere" and args.impl == "ours":
+        bench_icosphere(args)
+        return
     if args.workload == "ellipsoids" and args.impl == "ours":
         bench_ellipsoids(args)
         return
@@ -287,7 +336,9 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = lsm.MIXED if args.precision == "mixed" else lsm.FP64
+    prec = {"mixed": lsm.MIXED, "fp64": lsm.FP64, "ff": lsm.FF}[args.precision]
+    if prec == lsm.FF and not args.no_charts:
+        raise SystemExit("--precision ff evaluates only (add --no-charts)")
 
     w = workload(args)
     m = w["mesh"]
@@ -349,22 +400,29 @@ def main():
         total_units = int(u.item())
     value = total_units / (t_ms / 1e3)
 
-    # dominant kernel: the pair kernel, timed per launch by the library
-    flops = stats["pairs_far"] * FLOPS_FAR_PAIR + stats["pairs_near"] * FLOPS_NEAR_PAIR
-    kern_ms = stats["pair_kernel_ms"]
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    if prec == lsm.FP64:
-        peak = peak / 64.0
-    achieved = flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
-                "kernel": "k_eval_mixed" if prec == lsm.MIXED else "k_eval_fp64",
-                "launches": stats["pair_kernel_launches"],
-                "avg_launch_ms": kern_ms / max(1, stats["pair_kernel_launches"]),
-                "pairs_far": stats["pairs_far"], "pairs_near": stats["pairs_near"],
-                "share_of_step": kern_ms / sum(step_ms) if step_ms else None,
-                "peak_source": "FP32 FMA lanes 152 SM x 128 x 2 flops x 2070 MHz"
-                               + (" / 64 (FP64 rate)" if prec == lsm.FP64 else "")}
+    # rooflines of the pair kernels, timed per launch by the library; the
+    # dominant one (largest device time in the timed region) is "roofline"
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    names = ["k_eval_mixed", "k_eval_ff", "k_eval_fp64"]
+    kern = {}
+    for k in range(3):
+        ms_k = stats["kind_ms"][k]
+        if ms_k <= 0:
+            continue
+        fl = stats["kind_pairs_far"][k] * FLOPS_FAR_PAIR + stats["kind_pairs_near"][k] * FLOPS_NEAR_PAIR
+        pk = fp32_peak if k < 2 else fp32_peak / 64.0
+        ach = fl / (ms_k / 1e3) / 1e12
+        kern[names[k]] = {
+            "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "traffic": None, "launches": stats["kind_launches"][k],
+            "avg_launch_ms": ms_k / max(1, stats["kind_launches"][k]),
+            "pairs_far": stats["kind_pairs_far"][k], "pairs_near": stats["kind_pairs_near"][k],
+            "share_of_step": ms_k / sum(step_ms) if step_ms else None,
+            "peak_source": ("FP32 FMA lanes: 152 SM x 128 x 2 flops x 2070 MHz" if k < 2 else
+                            "FP32 FMA peak / 64 (GB300 FP64 rate)"),
+        }
+    dom = max(kern, key=lambda n: kern[n]["avg_launch_ms"] * kern[n]["launches"]) if kern else None
+    roofline = dict(kern[dom], kernel=dom) if dom else None
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -406,7 +464,7 @@ def main():
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32+f64" if prec == lsm.MIXED else "f64",
+            "dtype": {lsm.MIXED: "f32+ff", lsm.FF: "ff", lsm.FP64: "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": w["name"], "triangles": m.m, "sources": info["n_sources"],
                        "targets": nt, "chart_order": args.order, "chart_nodes": st.n_nodes if st else 0,
@@ -418,6 +476,7 @@ def main():
                        "max_residual": st.max_residual, "evals_fp64": st.evals_fp64} if st else None,
             "gpu_launches": launches,
             "roofline": roofline,
+            "roofline_kernels": kern,
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -69,7 +69,9 @@ class _Stats(ctypes.Structure):
 class _CtxStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("pairs_near", ctypes.c_int64),
                 ("pairs_far", ctypes.c_int64), ("pair_kernel_launches", ctypes.c_int64),
-                ("pair_kernel_ms", ctypes.c_double)]
+                ("pair_kernel_ms", ctypes.c_double), ("kind_pairs_near", ctypes.c_int64 * 3),
+                ("kind_pairs_far", ctypes.c_int64 * 3), ("kind_launches", ctypes.c_int64 * 3),
+                ("kind_ms", ctypes.c_double * 3)]
 
 
 class _Info(ctypes.Structure):
@@ -227,7 +229,11 @@ class Context:
         """Launch count, pairs evaluated (near / far tiles) and pair-kernel time."""
         st = _CtxStats()
         self._check(self._L.lsm_read_stats(self._h, ctypes.byref(st), 1 if reset else 0))
-        return {k: getattr(st, k) for k, _ in _CtxStats._fields_}
+        out = {}
+        for k, _ in _CtxStats._fields_:
+            v = getattr(st, k)
+            out[k] = list(v) if k.startswith("kind_") else v
+        return out
 
     def upload(self, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0, stream=None) -> "Mesh":
         return Mesh(self, verts, tris, sigma, n_gl, subdiv, stream)

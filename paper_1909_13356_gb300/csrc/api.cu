@@ -226,8 +226,8 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     int rc = LSM_OK;
     if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->d_flag, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_flag, 0, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&ctx->d_pairs, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(ctx->d_pairs, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&ctx->d_pairs, 6 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_pairs, 0, 6 * sizeof(unsigned long long)) != cudaSuccess) {
         delete c;
         return LSM_E_CUDA;
     }
@@ -254,8 +254,8 @@ int lsm_destroy(lsm_ctx* c)
     cudaFree(c->c.d_flag);
     cudaFree(c->c.d_pairs);
     for (auto& e : c->c.prof_events) {
-        cudaEventDestroy(e.first);
-        cudaEventDestroy(e.second);
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
     }
     delete c;
     return LSM_OK;
@@ -276,23 +276,34 @@ int lsm_read_stats(lsm_ctx* c, lsm_ctx_stats* out, int reset)
     LSM_CUDA_TRY(ctx, cudaDeviceSynchronize());
     for (auto& e : ctx->prof_events) {
         float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) ctx->prof_ms += ms;
-        ctx->prof_launches++;
-        cudaEventDestroy(e.first);
-        cudaEventDestroy(e.second);
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) ctx->prof_ms[e.kind] += ms;
+        ctx->prof_launches[e.kind]++;
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
     }
     ctx->prof_events.clear();
-    unsigned long long pr[2] = {0, 0};
+    unsigned long long pr[6] = {0, 0, 0, 0, 0, 0};
     LSM_CUDA_TRY(ctx, cudaMemcpy(pr, ctx->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
     out->launches = ctx->launches.load();
-    out->pairs_near = (int64_t)pr[0];
-    out->pairs_far = (int64_t)pr[1];
-    out->pair_kernel_launches = ctx->prof_launches;
-    out->pair_kernel_ms = ctx->prof_ms;
+    out->pairs_near = out->pairs_far = 0;
+    out->pair_kernel_launches = 0;
+    out->pair_kernel_ms = 0.0;
+    for (int k = 0; k < 3; k++) {
+        out->kind_pairs_near[k] = (int64_t)pr[2 * k];
+        out->kind_pairs_far[k] = (int64_t)pr[2 * k + 1];
+        out->kind_launches[k] = ctx->prof_launches[k];
+        out->kind_ms[k] = ctx->prof_ms[k];
+        out->pairs_near += out->kind_pairs_near[k];
+        out->pairs_far += out->kind_pairs_far[k];
+        out->pair_kernel_launches += ctx->prof_launches[k];
+        out->pair_kernel_ms += ctx->prof_ms[k];
+    }
     if (reset) {
         LSM_CUDA_TRY(ctx, cudaMemset(ctx->d_pairs, 0, sizeof(pr)));
-        ctx->prof_ms = 0.0;
-        ctx->prof_launches = 0;
+        for (int k = 0; k < 3; k++) {
+            ctx->prof_ms[k] = 0.0;
+            ctx->prof_launches[k] = 0;
+        }
     }
     return LSM_OK;
 }

@@ -39,22 +39,21 @@
 #ifndef LSM_RSQRT_REFINE
 #define LSM_RSQRT_REFINE 1
 #endif
+#ifndef LSM_PACKED_F32X2
+#define LSM_PACKED_F32X2 1
+#endif
 
 namespace lsm {
 namespace {
 
 constexpr int kSer64 = 14;  // series terms, FP64, used for u^2 < 0.25
-constexpr int kSer32 = 11;  // series terms, FP32, used for u^2 < 0.5625
 constexpr double kUs64 = 0.25;
-constexpr float kUs32 = 0.5625f;
 constexpr double kTwoOverSqrtPi = 1.12837916709551257390;
 constexpr double kFourOverSqrtPi = 2.25675833419102514780;
 
 // Hs(u) = sum_m A_m w^m, Ks(u) = sum_m B_m w^m, w = u^2 (filled by the host)
 __constant__ double c_A64[kSer64];
 __constant__ double c_B64[kSer64];
-__constant__ float c_A32[kSer32];
-__constant__ float c_B32[kSer32];
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -133,11 +132,8 @@ __device__ __forceinline__ void radial64(double r2, double a, double sqrt2sig, d
     FK = a3 * a * a * K;
 }
 
-// FP32 radial factors.  Small u: the power series.  Otherwise the Laplace
-// part is separated from the smoothing correction, so that rounding of
-// erf(u) near 1 does not bias the result:
-//   g = 1 - G,  G(u) = erfc(u) + (2u/sqrt pi) e^{-u^2},
-//   a^3 Hs = (1 - G)/rho^3,   a^5 Ks = (3G - 3)/rho^5 + (4/sqrt pi) a^3 e^{-u^2}/rho^2.
+// One Newton step on the hardware estimate: the result is within about one
+// ulp and carries no systematic bias.
 __device__ __forceinline__ float rsqrt_refined(float r2)
 {
     // one Newton step on the hardware estimate: the result is within about
@@ -152,29 +148,40 @@ __device__ __forceinline__ float rsqrt_refined(float r2)
 #endif
 }
 
-__device__ __forceinline__ void radial32(float r2, float a, float& fH, float& FK)
+
+// Piecewise polynomial table of H(w) = g(u)/u^3, w = u^2 (see build_h_table):
+// interval k covers w in [k, k+1)/kHTabPerUnit; per interval three float4:
+// {c0h, c0l, c1h, c1l}, {c2h, c2l, c3, c4}, {c5, c6, 0, 0}, p(t) = sum c_j t^j,
+// t = w - centre.  Beyond kHTabWmax, H = 1/u^3 to 1e-14.
+constexpr int kHTabPerUnit = 16;
+constexpr int kHTabN = 520;                   // covers w < 32.5 (u < 5.70)
+constexpr float kHTabWmax = (float)kHTabN / kHTabPerUnit;
+__device__ float4 g_htab[kHTabN * 3];         // filled once per device by the host
+
+// FP32 radial factors from the table's leading parts: fH = a^3 H(w) and
+// FK = a^5 K with K = H'(u)/u = 2 dH/dw.  Depending on w alone, they avoid
+// the amplified rounding of u that the erfc form suffers where G is steep.
+__device__ __forceinline__ void radial_tab32(float r2, float a, const float4* __restrict__ tab, float& fH,
+                                             float& FK)
 {
-    const float w = r2 * a * a;
-    const float a3 = a * a * a;
-    if (w < kUs32) {
-        float H = c_A32[kSer32 - 1];
-        float K = c_B32[kSer32 - 1];
-#pragma unroll
-        for (int m = kSer32 - 2; m >= 0; m--) {
-            H = fmaf(H, w, c_A32[m]);
-            K = fmaf(K, w, c_B32[m]);
-        }
+    const float a2 = a * a;
+    const float w = r2 * a2;
+    if (w < kHTabWmax) {
+        const int k = min((int)(w * (float)kHTabPerUnit), kHTabN - 1);
+        const float t = w - ((float)k + 0.5f) * (1.0f / kHTabPerUnit);
+        const float4 c01 = tab[3 * k], c23 = tab[3 * k + 1], c45 = tab[3 * k + 2];
+        const float H = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(c45.y, t, c45.x), t, c23.w), t, c23.z), t, c23.x), t, c01.z),
+                             t, c01.x);
+        const float dH = fmaf(fmaf(fmaf(fmaf(fmaf(6.0f * c45.y, t, 5.0f * c45.x), t, 4.0f * c23.w), t,
+                                        3.0f * c23.z), t, 2.0f * c23.x), t, c01.z);
+        const float a3 = a2 * a;
         fH = a3 * H;
-        FK = a3 * a * a * K;
+        FK = 2.0f * a3 * a2 * dH;
     } else {
         const float ri = rsqrt_refined(r2);
-        const float u = r2 * ri * a;
-        const float e = expf(-w);
-        const float G = erfcf(u) + (float)kTwoOverSqrtPi * u * e;
         const float ri2 = ri * ri;
-        const float ri3 = ri2 * ri;
-        fH = fmaf(-G, ri3, ri3);
-        FK = fmaf(3.0f * G - 3.0f, ri3 * ri2, ri2 * ((float)kFourOverSqrtPi * a3 * e));
+        fH = ri2 * ri;
+        FK = -3.0f * fH * ri2;
     }
 }
 
@@ -185,6 +192,15 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
     const float err = (hi - (s - bp)) + (x - bp);
     hi = s;
     lo += err;
+}
+
+// Fold the low word back into the high word (Fast2Sum), so that the low word
+// never grows into a running FP32 sum of its own over many additions.
+__device__ __forceinline__ void renorm(float& hi, float& lo)
+{
+    const float s = hi + lo;
+    lo = lo - (s - hi);
+    hi = s;
 }
 
 __device__ __forceinline__ void two_sum_acc64(double& hi, double& lo, double x)
@@ -275,15 +291,134 @@ __device__ __forceinline__ void count_pairs(unsigned long long* dst, unsigned lo
     }
 }
 
+// ---------------------------------------------------------------- float-float arithmetic
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e)
+{
+    s = a - b;
+    const float bb = s - a;
+    e = (a - (s - bb)) - (b + bb);
+}
+
+
+// ff product of (ah, al) and (bh, bl)
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& h, float& l)
+{
+    h = ah * bh;
+    l = fmaf(ah, bh, -h) + fmaf(ah, bl, al * bh);
+}
+// ff sum (ah, al) + (bh, bl), renormalised
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& h, float& l)
+{
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    h = s + e;
+    l = e - (h - s);
+}
+
+
+// One source's Phi term for one target in float-float: the tile-local pair
+// difference r, |r|^2, the radial factor (far: 1/|r|^3 from the hardware
+// rsqrt plus a float-float Newton step; near: a^3 H(w) from the table),
+// nw . r and the product.  Also returns, rounded to FP32, the values the
+// gradient uses (r, |r|^2, nw . r) and, for far pairs, the rsqrt estimate.
+__device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const float4& yl, const float4& nl,
+                                        const float* qh, const float* ql, bool far,
+                                        const float4* __restrict__ tab, float& qhi, float& qlo, float& dxh,
+                                        float& dyh, float& dzh, float& rh, float& dh, float& r0)
+{
+    float dxl, dyl, dzl, e;
+    two_diff(y.x, qh[0], dxh, e);
+    dxl = e + (yl.x - ql[0]);
+    two_diff(y.y, qh[1], dyh, e);
+    dyl = e + (yl.y - ql[1]);
+    two_diff(y.z, qh[2], dzh, e);
+    dzl = e + (yl.z - ql[2]);
+    const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
+    float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
+    e0 = fmaf(2.0f * dxh, dxl, e0);
+    e1 = fmaf(2.0f * dyh, dyl, e1);
+    e2 = fmaf(2.0f * dzh, dzl, e2);
+    float s01, t01, t2;
+    two_sum(p0, p1, s01, t01);
+    two_sum(s01, p2, rh, t2);
+    const float rl = ((e0 + e1) + e2) + (t01 + t2);
+    float fHh, fHl;
+    float wh = 0.0f, aah = 0.0f, aal = 0.0f;
+    r0 = 0.0f;
+    if (!far) {
+        aah = y.w * y.w;
+        aal = fmaf(y.w, y.w, -aah) + 2.0f * y.w * yl.w;
+        wh = rh * aah;
+    }
+    if (!far && wh < kHTabWmax) {
+        const float wl = fmaf(rh, aah, -wh) + fmaf(rh, aal, rl * aah);
+        const int k = min((int)(wh * (float)kHTabPerUnit), kHTabN - 1);
+        const float wc = ((float)k + 0.5f) * (1.0f / kHTabPerUnit);
+        float th, te;
+        two_diff(wh, wc, th, te);
+        const float tl = te + wl;
+        const float4 c01 = tab[3 * k], c23 = tab[3 * k + 1], c45 = tab[3 * k + 2];
+        // tail in FP32, then three float-float Horner steps
+        const float q = fmaf(fmaf(fmaf(c45.y, th, c45.x), th, c23.w), th, c23.z);
+        float Hh, Hl, mh, ml;
+        ff_mul(th, tl, q, 0.0f, mh, ml);
+        ff_add(c23.x, c23.y, mh, ml, Hh, Hl);
+        ff_mul(th, tl, Hh, Hl, mh, ml);
+        ff_add(c01.z, c01.w, mh, ml, Hh, Hl);
+        ff_mul(th, tl, Hh, Hl, mh, ml);
+        ff_add(c01.x, c01.y, mh, ml, Hh, Hl);
+        float a3h, a3l;
+        ff_mul(aah, aal, y.w, yl.w, a3h, a3l);
+        ff_mul(a3h, a3l, Hh, Hl, fHh, fHl);
+    } else {
+        // 1/|r| = r0 (1 + delta/2), delta = 1 - |r|^2 r0^2; fH = 1/|r|^3
+        r0 = rsqrtf(rh);
+        const float a = r0 * r0, ae = fmaf(r0, r0, -a);
+        const float hh = rh * a;
+        float he = fmaf(rh, a, -hh);
+        he = fmaf(rh, ae, he);
+        he = fmaf(rl, a, he);
+        const float delta = (1.0f - hh) - he;
+        const float ril = 0.5f * r0 * delta;
+        const float q2l = fmaf(2.0f * r0, ril, ae);
+        fHh = a * r0;
+        fHl = fmaf(a, r0, -fHh) + fmaf(a, ril, q2l * r0);
+    }
+    const float d0 = n.x * dxh, d1 = n.y * dyh, d2 = n.z * dzh;
+    const float f0 = fmaf(n.x, dxh, -d0), f1 = fmaf(n.y, dyh, -d1), f2 = fmaf(n.z, dzh, -d2);
+    float sd, u1, u2;
+    two_sum(d0, d1, sd, u1);
+    two_sum(sd, d2, dh, u2);
+    const float dl = ((f0 + f1) + f2) + (u1 + u2) + fmaf(n.x, dxl, fmaf(n.y, dyl, n.z * dzl)) +
+                     fmaf(nl.x, dxh, fmaf(nl.y, dyh, nl.z * dzh));
+    ff_mul(dh, dl, fHh, fHl, qhi, qlo);
+    // FP32 values for the gradient: the pair difference with its low part
+    dxh += dxl;
+    dyh += dyl;
+    dzh += dzl;
+    rh += rl;
+    dh += dl;
+}
+
 // ---------------------------------------------------------------- mixed kernel
 template <int TPT>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __restrict__ spos,
+__global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __restrict__ spos,
                                                             const float4* __restrict__ snw,
-                                                            const float4* __restrict__ slo, EvalArgs A)
+                                                            const float4* __restrict__ slo,
+                                                            const float4* __restrict__ snwlo, EvalArgs A)
 {
     __shared__ __align__(128) float4 sh_pos[2][kTile];
     __shared__ __align__(128) float4 sh_nw[2][kTile];
     __shared__ __align__(128) float4 sh_lo[2][kTile];
+    __shared__ __align__(128) float4 sh_nl[2][kTile];
+    __shared__ __align__(16) float4 s_htab[kHTabN * 3];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float s_bb[6];
 
@@ -303,6 +438,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
         t1 = min(A.ntiles, t0 + A.tiles_per_split);
     }
 
+    for (int k = tid; k < kHTabN * 3; k += kEvalThreads) s_htab[k] = g_htab[k];
     float xh[TPT][3], xl[TPT][3];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int nvalid = 0;
@@ -340,10 +476,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
         const int cnt = (int)A.thi[t].w;
         const uint32_t bytes = (uint32_t)cnt * 16u;
         const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
-        mbar_expect_tx(&bar[b], (far ? 2u : 3u) * bytes);
+        mbar_expect_tx(&bar[b], (far ? 2u : 4u) * bytes);
         bulk_g2s(&sh_pos[b][0], spos + (size_t)t * kTile, bytes, &bar[b]);
         bulk_g2s(&sh_nw[b][0], snw + (size_t)t * kTile, bytes, &bar[b]);
-        if (!far) bulk_g2s(&sh_lo[b][0], slo + (size_t)t * kTile, bytes, &bar[b]);
+        if (!far) {
+            bulk_g2s(&sh_lo[b][0], slo + (size_t)t * kTile, bytes, &bar[b]);
+            bulk_g2s(&sh_nl[b][0], snwlo + (size_t)t * kTile, bytes, &bar[b]);
+        }
     };
     if (tid == 0 && t0 < t1) issue(t0, 0);
 
@@ -378,6 +517,59 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
             }
             // FP32 sums over chunks of kChunk sources, each folded into the
             // float-float accumulator
+#if LSM_PACKED_F32X2
+            if constexpr (TPT == 2) {
+                // the two targets of a thread ride in the two lanes of the packed
+                // FP32 instructions (fma/add/mul.f32x2), halving the issue slots
+                // of the pair arithmetic; x - y is carried (= -r)
+                const float2 qx = make_float2(xq[0][0], xq[1][0]);
+                const float2 qy = make_float2(xq[0][1], xq[1][1]);
+                const float2 qz = make_float2(xq[0][2], xq[1][2]);
+                const float2 one = make_float2(1.0f, 1.0f), half = make_float2(0.5f, 0.5f);
+                const float2 p3 = make_float2(3.0f, 3.0f), m1 = make_float2(-1.0f, -1.0f);
+                for (int c0 = 0; c0 < cnt; c0 += kChunk) {
+                    const int c1 = min(cnt, c0 + kChunk);
+                    float2 P0 = make_float2(0.0f, 0.0f), P1 = P0, P2 = P0, P3 = P0;
+#pragma unroll 4
+                    for (int s = c0; s < c1; s++) {
+                        const float4 y = sp[s];
+                        const float4 n = sn[s];
+                        const float2 ndx = __fadd2_rn(qx, make_float2(-y.x, -y.x));
+                        const float2 ndy = __fadd2_rn(qy, make_float2(-y.y, -y.y));
+                        const float2 ndz = __fadd2_rn(qz, make_float2(-y.z, -y.z));
+                        const float2 r2 = __ffma2_rn(ndx, ndx, __ffma2_rn(ndy, ndy, __fmul2_rn(ndz, ndz)));
+                        float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+#if LSM_RSQRT_REFINE
+                        const float2 t = __fmul2_rn(r2, ri);
+                        const float2 e = __ffma2_rn(t, __fmul2_rn(ri, m1), one);
+                        ri = __ffma2_rn(__fmul2_rn(ri, half), e, ri);
+#endif
+                        const float2 ri2 = __fmul2_rn(ri, ri);
+                        const float2 ri3 = __fmul2_rn(ri2, ri);
+                        const float2 nx = make_float2(n.x, n.x), ny = make_float2(n.y, n.y),
+                                     nz = make_float2(n.z, n.z);
+                        const float2 dneg = __ffma2_rn(nx, ndx, __ffma2_rn(ny, ndy, __fmul2_rn(nz, ndz)));
+                        const float2 qn = __fmul2_rn(dneg, ri3);          // -(nw . r)/|r|^3
+                        P0 = __fadd2_rn(P0, qn);                          // -Phi
+                        // grad = 3 q r / |r|^5 - nw/|r|^3 = (3 qn/|r|^2) (x - y) - nw/|r|^3
+                        const float2 tq = __fmul2_rn(qn, __fmul2_rn(ri2, p3));
+                        const float2 mnx = make_float2(-n.x, -n.x), mny = make_float2(-n.y, -n.y),
+                                     mnz = make_float2(-n.z, -n.z);
+                        P1 = __ffma2_rn(tq, ndx, __ffma2_rn(mnx, ri3, P1));
+                        P2 = __ffma2_rn(tq, ndy, __ffma2_rn(mny, ri3, P2));
+                        P3 = __ffma2_rn(tq, ndz, __ffma2_rn(mnz, ri3, P3));
+                    }
+                    two_sum_acc(acc_h[0][0], acc_l[0][0], -P0.x);
+                    two_sum_acc(acc_h[1][0], acc_l[1][0], -P0.y);
+                    two_sum_acc(acc_h[0][1], acc_l[0][1], P1.x);
+                    two_sum_acc(acc_h[1][1], acc_l[1][1], P1.y);
+                    two_sum_acc(acc_h[0][2], acc_l[0][2], P2.x);
+                    two_sum_acc(acc_h[1][2], acc_l[1][2], P2.y);
+                    two_sum_acc(acc_h[0][3], acc_l[0][3], P3.x);
+                    two_sum_acc(acc_h[1][3], acc_l[1][3], P3.y);
+                }
+            } else
+#endif
             for (int c0 = 0; c0 < cnt; c0 += kChunk) {
                 const int c1 = min(cnt, c0 + kChunk);
                 float p[TPT][4];
@@ -427,30 +619,55 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_mixed(const float4* __res
                 }
             }
             const float4* sl = sh_lo[b];
-            // near pairs carry the large terms: every pair is folded into the
-            // float-float accumulator
-#pragma unroll 2
+            const float4* snl = sh_nl[b];
+            // near pairs carry the large, often cancelling, terms: Phi in
+            // float-float (as the float-float kernel), folded into the
+            // accumulator pair by pair; the gradient in FP32 from the table
+            float cph[TPT], cpl[TPT], cg[TPT][3], cgl[TPT][3];   // this tile's sums, float-float
+#pragma unroll
+            for (int k = 0; k < TPT; k++) {
+                cph[k] = cpl[k] = 0.0f;
+                for (int c = 0; c < 3; c++) cg[k][c] = cgl[k][c] = 0.0f;
+            }
+#pragma unroll 1
             for (int s = 0; s < cnt; s++) {
                 const float4 y = sp[s];
                 const float4 n = sn[s];
                 const float4 yl = sl[s];
+                const float4 nl = snl[s];
 #pragma unroll
                 for (int k = 0; k < TPT; k++) {
-                    const float dx = (y.x - qh[k][0]) + (yl.x - ql[k][0]);
-                    const float dy = (y.y - qh[k][1]) + (yl.y - ql[k][1]);
-                    const float dz = (y.z - qh[k][2]) + (yl.z - ql[k][2]);
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
+                    ff_pair(y, n, yl, nl, qh[k], ql[k], false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
+                    float sph, tph;
+                    two_sum(cph[k], qh_, sph, tph);
+                    cph[k] = sph;
+                    cpl[k] += tph + ql_;
                     float fH, FK;
-                    radial32(r2, y.w, fH, FK);
-                    const float d = fmaf(n.x, dx, fmaf(n.y, dy, n.z * dz));
-                    const float tq = d * FK;
-                    two_sum_acc(acc_h[k][0], acc_l[k][0], d * fH);
-                    two_sum_acc(acc_h[k][1], acc_l[k][1], -fmaf(n.x, fH, tq * dx));
-                    two_sum_acc(acc_h[k][2], acc_l[k][2], -fmaf(n.y, fH, tq * dy));
-                    two_sum_acc(acc_h[k][3], acc_l[k][3], -fmaf(n.z, fH, tq * dz));
+                    radial_tab32(rh, y.w, s_htab, fH, FK);
+                    const float tq = dh * FK;
+                    two_sum_acc(cg[k][0], cgl[k][0], -fmaf(n.x, fH, tq * dxh));
+                    two_sum_acc(cg[k][1], cgl[k][1], -fmaf(n.y, fH, tq * dyh));
+                    two_sum_acc(cg[k][2], cgl[k][2], -fmaf(n.z, fH, tq * dzh));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < TPT; k++) {
+                float nh_, nl_;
+                ff_add(acc_h[k][0], acc_l[k][0], cph[k], cpl[k], nh_, nl_);
+                acc_h[k][0] = nh_;
+                acc_l[k][0] = nl_;
+                for (int c = 0; c < 3; c++) {
+                    ff_add(acc_h[k][c + 1], acc_l[k][c + 1], cg[k][c], cgl[k][c], nh_, nl_);
+                    acc_h[k][c + 1] = nh_;
+                    acc_l[k][c + 1] = nl_;
                 }
             }
         }
+#pragma unroll
+        for (int k = 0; k < TPT; k++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) renorm(acc_h[k][c], acc_l[k][c]);
         __syncthreads();
     }
     const int64_t plane = (int64_t)A.nt;
@@ -626,40 +843,6 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
 // the three leading coefficients in float-float); beyond kHTabWmax H equals
 // 1/u^3 to 1e-14.  grad Phi keeps mixed accuracy (FP32, compensated sums):
 // it only steers Newton.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e)
-{
-    s = a - b;
-    const float bb = s - a;
-    e = (a - (s - bb)) - (b + bb);
-}
-
-constexpr int kHTabPerUnit = 16;
-constexpr int kHTabN = 520;                   // covers w < 32.5 (u < 5.70)
-constexpr float kHTabWmax = (float)kHTabN / kHTabPerUnit;
-__device__ float4 g_htab[kHTabN * 3];         // filled once per device by the host
-
-// ff product of (ah, al) and (bh, bl)
-__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& h, float& l)
-{
-    h = ah * bh;
-    l = fmaf(ah, bh, -h) + fmaf(ah, bl, al * bh);
-}
-// ff sum (ah, al) + (bh, bl), renormalised
-__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& h, float& l)
-{
-    float s, e;
-    two_sum(ah, bh, s, e);
-    e += al + bl;
-    h = s + e;
-    l = e - (h - s);
-}
-
 constexpr int kFFStage = kTile * 64;  // bytes per stage: 4 float4 arrays
 constexpr int kMaxNearTiles = 768;    // near-tile list of one block (incremental mode)
 
@@ -798,89 +981,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         const float4* snl = sp + 3 * kTile;
         for (int c0 = 0; c0 < cnt; c0 += kChunk) {
             const int c1 = min(cnt, c0 + kChunk);
-            float g[3] = {0.0f, 0.0f, 0.0f};
+            float g[3] = {0.0f, 0.0f, 0.0f}, gn[3] = {0.0f, 0.0f, 0.0f};
             float cph = 0.0f, cpl = 0.0f;   // this chunk's Phi, float-float
 #pragma unroll 2
             for (int s = c0; s < c1; s++) {
                 const float4 y = sp[s], n = sn[s], yl = sl[s], nl = snl[s];
-                float dxh, dxl, dyh, dyl, dzh, dzl, e;
-                two_diff(y.x, qh[0], dxh, e);
-                dxl = e + (yl.x - ql[0]);
-                two_diff(y.y, qh[1], dyh, e);
-                dyl = e + (yl.y - ql[1]);
-                two_diff(y.z, qh[2], dzh, e);
-                dzl = e + (yl.z - ql[2]);
-                // |r|^2
-                const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
-                float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
-                e0 = fmaf(2.0f * dxh, dxl, e0);
-                e1 = fmaf(2.0f * dyh, dyl, e1);
-                e2 = fmaf(2.0f * dzh, dzl, e2);
-                float s01, t01, rh, t2;
-                two_sum(p0, p1, s01, t01);
-                two_sum(s01, p2, rh, t2);
-                const float rl = ((e0 + e1) + e2) + (t01 + t2);
-                // radial factor fH (float-float)
-                float fHh, fHl;
-                float wh = 0.0f, aah = 0.0f, aal = 0.0f;
-                if (!far) {
-                    aah = y.w * y.w;
-                    aal = fmaf(y.w, y.w, -aah) + 2.0f * y.w * yl.w;
-                    wh = rh * aah;
-                }
-                if (!far && wh < kHTabWmax) {
-                    const float wl = fmaf(rh, aah, -wh) + fmaf(rh, aal, rl * aah);
-                    const int k = min((int)(wh * (float)kHTabPerUnit), kHTabN - 1);
-                    const float wc = ((float)k + 0.5f) * (1.0f / kHTabPerUnit);
-                    float th, te;
-                    two_diff(wh, wc, th, te);
-                    const float tl = te + wl;
-                    const float4 c01 = s_htab[3 * k], c23 = s_htab[3 * k + 1], c45 = s_htab[3 * k + 2];
-                    // tail in FP32, then three float-float Horner steps
-                    const float q = fmaf(fmaf(fmaf(c45.y, th, c45.x), th, c23.w), th, c23.z);
-                    float Hh, Hl, mh, ml;
-                    ff_mul(th, tl, q, 0.0f, mh, ml);
-                    ff_add(c23.x, c23.y, mh, ml, Hh, Hl);
-                    ff_mul(th, tl, Hh, Hl, mh, ml);
-                    ff_add(c01.z, c01.w, mh, ml, Hh, Hl);
-                    ff_mul(th, tl, Hh, Hl, mh, ml);
-                    ff_add(c01.x, c01.y, mh, ml, Hh, Hl);
-                    // a^3 = a^2 a
-                    float a3h, a3l;
-                    ff_mul(aah, aal, y.w, yl.w, a3h, a3l);
-                    ff_mul(a3h, a3l, Hh, Hl, fHh, fHl);
-                } else {
-                    // 1/|r| = r0 (1 + delta/2), delta = 1 - |r|^2 r0^2; fH = 1/|r|^3
-                    const float r0 = rsqrtf(rh);
-                    const float a = r0 * r0, ae = fmaf(r0, r0, -a);
-                    const float hh = rh * a;
-                    float he = fmaf(rh, a, -hh);
-                    he = fmaf(rh, ae, he);
-                    he = fmaf(rl, a, he);
-                    const float delta = (1.0f - hh) - he;
-                    const float ril = 0.5f * r0 * delta;
-                    const float q2l = fmaf(2.0f * r0, ril, ae);
-                    fHh = a * r0;
-                    fHl = fmaf(a, r0, -fHh) + fmaf(a, ril, q2l * r0);
-                }
-                // nw . r
-                const float d0 = n.x * dxh, d1 = n.y * dyh, d2 = n.z * dzh;
-                const float f0 = fmaf(n.x, dxh, -d0), f1 = fmaf(n.y, dyh, -d1), f2 = fmaf(n.z, dzh, -d2);
-                float sd, u1, dh, u2;
-                two_sum(d0, d1, sd, u1);
-                two_sum(sd, d2, dh, u2);
-                const float dl = ((f0 + f1) + f2) + (u1 + u2) + fmaf(n.x, dxl, fmaf(n.y, dyl, n.z * dzl)) +
-                                 fmaf(nl.x, dxh, fmaf(nl.y, dyh, nl.z * dzh));
-                // Phi term
-                float qh_, ql_;
-                ff_mul(dh, dl, fHh, fHl, qh_, ql_);
+                float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
+                ff_pair(y, n, yl, nl, qh, ql, far, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
                 float sph, tph;
                 two_sum(cph, qh_, sph, tph);
                 cph = sph;
                 cpl += tph + ql_;
                 // grad from the high parts (FP32)
                 if (far) {
-                    const float ri = rsqrtf(rh);
+                    const float ri = r0;
                     const float ri2 = ri * ri;
                     const float ri3 = ri2 * ri;
                     const float tq = 3.0f * dh * ri3 * ri2;
@@ -889,24 +1003,32 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                     g[2] = fmaf(tq, dzh, fmaf(-n.z, ri3, g[2]));
                 } else {
                     float fH, FK;
-                    radial32(rh, y.w, fH, FK);
+                    radial_tab32(rh, y.w, s_htab, fH, FK);
                     const float tq = dh * FK;
-                    two_sum_acc(gh[0], gl[0], -fmaf(n.x, fH, tq * dxh));
-                    two_sum_acc(gh[1], gl[1], -fmaf(n.y, fH, tq * dyh));
-                    two_sum_acc(gh[2], gl[2], -fmaf(n.z, fH, tq * dzh));
+                    two_sum_acc(g[0], gn[0], -fmaf(n.x, fH, tq * dxh));
+                    two_sum_acc(g[1], gn[1], -fmaf(n.y, fH, tq * dyh));
+                    two_sum_acc(g[2], gn[2], -fmaf(n.z, fH, tq * dzh));
                 }
             }
             // fold the chunk into the running float-float sums, renormalised
             float nh_, nl_;
             if (far) {
 #pragma unroll
-                for (int c = 0; c < 3; c++) two_sum_acc(fgh[c], fgl[c], g[c]);
+                for (int c = 0; c < 3; c++) {
+                    two_sum_acc(fgh[c], fgl[c], g[c]);
+                    renorm(fgh[c], fgl[c]);
+                }
                 ff_add(fph, fpl, cph, cpl, nh_, nl_);
                 fph = nh_;
                 fpl = nl_;
             } else {
 #pragma unroll
-                for (int c = 0; c < 3; c++) two_sum_acc(gh[c], gl[c], g[c]);
+                for (int c = 0; c < 3; c++) {
+                    float ah, al;
+                    ff_add(gh[c], gl[c], g[c], gn[c], ah, al);
+                    gh[c] = ah;
+                    gl[c] = al;
+                }
                 ff_add(ph, pl, cph, cpl, nh_, nl_);
                 ph = nh_;
                 pl = nl_;
@@ -1039,15 +1161,8 @@ int upload_series_constants(Ctx* ctx)
         A[m] = kTwoOverSqrtPi * c[m + 1];
         B[m] = kTwoOverSqrtPi * c[m + 2] * (2.0 * (m + 2) - 2.0);
     }
-    float A32[kSer32], B32[kSer32];
-    for (int m = 0; m < kSer32; m++) {
-        A32[m] = (float)A[m];
-        B32[m] = (float)B[m];
-    }
     LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_A64, A, sizeof(double) * kSer64));
     LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_B64, B, sizeof(double) * kSer64));
-    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_A32, A32, sizeof(A32)));
-    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_B32, B32, sizeof(B32)));
     {
         std::vector<float4> tab(kHTabN * 3);
         build_h_table(tab.data());
@@ -1104,7 +1219,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     A.cut2 = (float)(cut * cut);
     A.out = part;
     A.flag = ctx->d_flag;
-    A.pairs = ctx->d_pairs;
+    A.pairs = ctx->d_pairs + 2 * (mixed ? 0 : (precision == LSM_FF ? 1 : 2));
     A.items = nullptr;
     A.n_items = nullptr;
     A.ff_mode = 0;
@@ -1123,7 +1238,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         LSM_CUDA_TRY(ctx, cudaEventRecord(ev0, st));
     }
     if (mixed) {
-        k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, A);
+        k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else if (ff) {
         k_eval_ff<<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else {
@@ -1132,7 +1247,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     LSM_LAUNCHED(ctx);
     if (ctx->profiling) {
         LSM_CUDA_TRY(ctx, cudaEventRecord(ev1, st));
-        ctx->prof_events.emplace_back(ev0, ev1);
+        ctx->prof_events.push_back(Ctx::ProfEvent{ev0, ev1, mixed ? 0 : (ff ? 1 : 2)});
     }
     if (nsplit > 1) {
         k_reduce_splits<<<(t.n + 255) / 256, 256, 0, st>>>(part, nsplit, t.n, res);
@@ -1163,14 +1278,14 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
     A.cut2 = (float)(cut * cut);
     A.out = res;
     A.flag = ctx->d_flag;
-    A.pairs = ctx->d_pairs;
+    A.pairs = ctx->d_pairs + 2 * (mixed ? 0 : (precision == LSM_FF ? 1 : 2));
     A.items = items;
     A.n_items = n_items;
     A.ff_mode = 0;
     A.far_io = nullptr;
     A.x_old = nullptr;
     if (mixed) {
-        k_eval_mixed<kTPT32><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, A);
+        k_eval_mixed<kTPT32><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
     } else if (precision == LSM_FF) {
         k_eval_ff<<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
     } else {
@@ -1298,7 +1413,7 @@ int eval_noalloc(Ctx* ctx, const Mesh* me, const double* x, int64_t n, double* p
     A.cut2 = (float)(cut * cut);
     A.out = nsplit > 1 ? part : R;
     A.flag = ctx->d_flag;
-    A.pairs = ctx->d_pairs;
+    A.pairs = ctx->d_pairs + 2 * (mixed ? 0 : (precision == LSM_FF ? 1 : 2));
     A.items = nullptr;
     A.n_items = nullptr;
     A.ff_mode = 0;
@@ -1306,7 +1421,7 @@ int eval_noalloc(Ctx* ctx, const Mesh* me, const double* x, int64_t n, double* p
     A.x_old = nullptr;
     dim3 grid(nblk, nsplit);
     if (mixed) {
-        k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, A);
+        k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else {
         k_eval_fp64<kTPT64><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
     }
