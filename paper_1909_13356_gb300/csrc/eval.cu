@@ -5,30 +5,32 @@
 // bounding box of a block of targets contributes through the Laplace double
 // layer (eq. kerapprox); every other tile contributes through the full
 // smoothed kernel (eq. kerpsi, and its gradient from eq. gradPhi with the
-// sign of the second term corrected), whose radial factors switch to a power
-// series for small u (eq. kerpsi_asymp, completed with the term eq.
-// kerpsi_asymp2 drops).  Nothing is dropped: a near tile evaluates the full
-// kernel for all of its pairs.
+// sign of the second term corrected).  Nothing is dropped: a near tile
+// evaluates the full kernel for all of its pairs.
 //
-// With nw' = nw / (4 pi), a = 1/(sqrt2 sigma), r = y - x, u = |r| a:
-//   phi  += (nw'.r) a^3 Hs(u)
-//   grad -= nw' a^3 Hs(u) + (nw'.r) a^5 Ks(u) r
-//   Hs(u) = g(u)/u^3,  Ks(u) = Hs'(u)/u = ((4/sqrt pi) e^{-u^2} - 3 Hs(u)) / u^2,
-//   g(u) = erf(u) - (2u/sqrt pi) e^{-u^2};
-// the Laplace limits are a^3 Hs -> 1/|r|^3 and a^5 Ks -> -3/|r|^5.
+// With nw' = nw / (4 pi), a = 1/(sqrt2 sigma), r = y - x, u = |r| a, w = u^2:
+//   phi  += (nw'.r) a^3 H(w)
+//   grad -= nw' a^3 H(w) + (nw'.r) a^5 K r,    K = H'(u)/u = 2 dH/dw
+//   H = g(u)/u^3, g(u) = erf(u) - (2u/sqrt pi) e^{-u^2};
+// the Laplace limits are a^3 H -> 1/|r|^3 and a^5 K -> -3/|r|^5.  The FP64
+// kernel evaluates H and K from their power series (small u, eq.
+// kerpsi_asymp completed with the term eq. kerpsi_asymp2 drops) or the
+// erf form; the FP32 and float-float kernels read H from a piecewise
+// polynomial table fitted at context creation.
 //
-// Layout: one CTA owns a block of kEvalThreads * TPT consecutive sorted
-// targets and walks a contiguous range of source tiles; each tile (kTile
-// nodes, pos and nw arrays) is staged into shared memory by the bulk-copy
-// engine (cp.async.bulk, completion on an mbarrier), double buffered.  A grid
-// y-dimension splits the tile range when there are too few target blocks to
-// fill the GPU; the partial sums are then reduced in a fixed order.
-//
-// Mixed precision: pair arithmetic in FP32 on tile-local coordinates (source
-// offsets from the tile centre, and the target offset formed from hi/lo
-// float parts of the FP64 target and of the centre), FP32 sums within a tile,
-// and a compensated (two-sum) float-float accumulator across tiles; results
-// are returned in FP64.
+// Three kernels share one layout.  A CTA owns a block of consecutive sorted
+// targets and walks a range of source tiles; each tile is staged into shared
+// memory by the bulk-copy engine (cp.async.bulk, completion on an mbarrier
+// with a bounded wait), double buffered.  A grid y-dimension splits the tile
+// range when there are too few target blocks to fill the GPU (partials are
+// reduced in a fixed order), or a table of work items (target range, tile
+// range) drives the grid for batches of meshes.
+//   k_eval_fp64   the FP64 reference path.
+//   k_eval_mixed  far tiles in FP32 on tile-local coordinates (two targets
+//                 per thread in packed f32x2 lanes), near tiles in
+//                 float-float; compensated, per-tile renormalised sums.
+//   k_eval_ff     Phi to FP64 accuracy on the FP32 pipes: every far and near
+//                 pair in float-float; grad Phi to mixed accuracy.
 #include <algorithm>
 #include <cmath>
 #include <mutex>

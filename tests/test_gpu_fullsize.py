@@ -1,0 +1,72 @@
+"""Full-size parity, in the launch configuration bench.py times.
+
+Graded torus, 30,720 triangles, Duffy 6x6 sources (1,105,920 nodes), 1e6
+targets within 3 sigma, order-8 chart nodes (1,105,920) to |Phi - 1/2| <
+1e-12: sampled outputs against the FP64 oracle computed one by one.
+Bumped icosphere, level 8 (1,310,720 triangles, 20,971,520 nodes): sampled
+outputs of a 1e5-target evaluation against the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lsm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1909_13356_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torus(lsm, oracle_mod):
+    w = synth.torus_c2(1_000_000)
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    src = oracle_mod.sources(m.verts, m.tris, m.sigma, 6, 0)
+    return w, ctx, mesh, src
+
+
+def test_torus_full_evaluation_sampled(lsm, oracle_mod, torus):
+    w, ctx, mesh, (y, nw, sg) = torus
+    m = w["mesh"]
+    x = torch.from_numpy(w["targets"]).cuda()
+    sel = np.random.default_rng(7).choice(len(w["targets"]), 64, replace=False)
+    po, go = oracle_mod.phi_grad(y, nw, sg, w["targets"][sel])
+    for prec, tol, gtol in ((lsm.MIXED, 1e-7, 1e-7), (lsm.FF, 1e-12, 1e-7)):
+        phi, grad = mesh.eval_phi_grad(x, prec)
+        p = phi.cpu().numpy()[sel]
+        g = grad.cpu().numpy()[sel]
+        assert np.abs(p - po).max() <= tol
+        assert np.abs(g - go).max() <= gtol / m.sigma.min()
+
+
+def test_torus_full_chart_solve_sampled(lsm, oracle_mod, torus):
+    w, ctx, mesh, (y, nw, sg) = torus
+    x, h, st, stats = mesh.solve_charts(order=8, tol=1e-12, precision=lsm.MIXED, device_out=True)
+    assert stats.n_nodes == 1_105_920 and stats.n_failed == 0
+    assert bool((st & 255 == 0).all())
+    sel = np.random.default_rng(8).choice(stats.n_nodes, 96, replace=False)
+    po, _ = oracle_mod.phi_grad(y, nw, sg, x.cpu().numpy()[sel])
+    assert np.abs(po - 0.5).max() < 1e-12
+
+
+def test_icosphere_full_evaluation_sampled(lsm, oracle_mod):
+    w = synth.icosphere_c3(n_targets=100_000)
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
+    assert mesh.info()["n_sources"] == 20_971_520
+    x = torch.from_numpy(w["targets"]).cuda()
+    phi, grad = mesh.eval_phi_grad(x, lsm.MIXED)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 4, 0)
+    sel = np.random.default_rng(9).choice(len(w["targets"]), 32, replace=False)
+    po, go = oracle_mod.phi_grad(y, nw, sg, w["targets"][sel])
+    assert np.abs(phi.cpu().numpy()[sel] - po).max() <= 1e-7
+    assert np.abs(grad.cpu().numpy()[sel] - go).max() <= 1e-7 / m.sigma.min()
