@@ -63,13 +63,34 @@ def parse():
     return ap.parse_args()
 
 
-def workload(args):
+def rank_seed(rank: int) -> int:
+    """Seed of the graded torus and its targets on one rank.  Every rank
+    solves its own independent problem (weak scaling, no data-path
+    collective); rank 0's is the single-GPU workload."""
+    return 2 + 1009 * rank
+
+
+def workload(args, rank: int = 0):
     import synth
+    seed = rank_seed(rank)
     if args.small:
-        w = synth.torus_c2(n_targets=min(args.targets, 50_000), nu=60, nv=16)
+        w = synth.torus_c2(n_targets=min(args.targets, 50_000), seed=seed, nu=60, nv=16)
     else:
-        w = synth.torus_c2(n_targets=args.targets)
+        w = synth.torus_c2(n_targets=args.targets, seed=seed)
     return w
+
+
+def reduce_over_ranks(dist, t_ms: float, units: int, device):
+    """Whole-job timing across ranks: the slowest rank's time and the units
+    all ranks processed.  With one process (dist None) this is the identity."""
+    if dist is None:
+        return t_ms, units
+    import torch
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(u.item()))
 
 
 class ClockSampler:
@@ -340,7 +361,7 @@ def main():
     if prec == lsm.FF and not args.no_charts:
         raise SystemExit("--precision ff evaluates only (add --no-charts)")
 
-    w = workload(args)
+    w = workload(args, rank)
     m = w["mesh"]
     ctx = lsm.Context(local)
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
@@ -391,13 +412,7 @@ def main():
     stats = ctx.read_stats(reset=True)
     launches = ctx.launch_count - launches0
     t_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-        u = torch.tensor([float(total_units)], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_units = int(u.item())
+    t_ms, total_units = reduce_over_ranks(dist, t_ms, total_units, dev)
     value = total_units / (t_ms / 1e3)
 
     # rooflines of the pair kernels, timed per launch by the library; the
@@ -469,6 +484,8 @@ def main():
             "config": {"workload": w["name"], "triangles": m.m, "sources": info["n_sources"],
                        "targets": nt, "chart_order": args.order, "chart_nodes": st.n_nodes if st else 0,
                        "newton_tol": args.tol, "precision": args.precision,
+                       "parallelism": (f"{world} ranks, one independent torus (own seed) each"
+                                       if world > 1 else "single GPU"),
                        "l2": "flushed (256 MB write) before each timed step"},
             "chart_nodes_per_s": st.n_converged / (t_ms / args.steps / 1e3) if st else None,
             "newton": {"iterations": st.iterations, "active_per_iter": st.active_per_iter,
