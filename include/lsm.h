@@ -98,7 +98,17 @@ typedef struct {
                               (1e-7, the mixed kernels' accuracy on Phi) is
                               met on mixed evaluations alone, with no FP64
                               steps */
-    int32_t reserved[8];
+    /* Far field of the mixed path on large meshes: a barycentric Lagrange
+     * treecode.  Source tiles are grouped by Morton order into a binary tree;
+     * a node of radius r whose box lies beyond the mixed cutoff from a target
+     * block, at distance >= r / tree_theta from the node's centre, acts on the
+     * block through (tree_degree + 1)^3 Chebyshev proxy points carrying its
+     * interpolated dipole weights. */
+    int32_t tree_degree;      /* Chebyshev degree p per axis (8; 1..12) */
+    float tree_theta;         /* opening parameter (0.5; (0, 1)) */
+    int32_t tree_min_sources; /* meshes with at least this many source nodes
+                                 use it (262,144); -1: never */
+    int32_t reserved[5];
 } lsm_options;
 
 /* Statistics of one chart solve. */

@@ -216,11 +216,22 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.cutoff_mixed = 6.5;
     ctx->opt.mixed_switch = 1e-6;
     ctx->opt.mixed_accept = 1e-7;
+    ctx->opt.tree_degree = 8;
+    ctx->opt.tree_theta = 0.5f;
+    ctx->opt.tree_min_sources = 262144;
     if (opt) {
+        if (opt->tree_degree < 0 || opt->tree_degree > kTreeMaxDegree || opt->tree_theta < 0.0f ||
+            opt->tree_theta >= 1.0f || opt->tree_min_sources < -1) {
+            delete c;
+            return LSM_E_INVALID_ARG;
+        }
         if (opt->mixed_accept > 0) ctx->opt.mixed_accept = opt->mixed_accept;
         if (opt->cutoff_fp64 > 0) ctx->opt.cutoff_fp64 = opt->cutoff_fp64;
         if (opt->cutoff_mixed > 0) ctx->opt.cutoff_mixed = opt->cutoff_mixed;
         if (opt->mixed_switch > 0) ctx->opt.mixed_switch = opt->mixed_switch;
+        if (opt->tree_degree > 0) ctx->opt.tree_degree = opt->tree_degree;
+        if (opt->tree_theta > 0.0f) ctx->opt.tree_theta = opt->tree_theta;
+        if (opt->tree_min_sources != 0) ctx->opt.tree_min_sources = opt->tree_min_sources;
     }
     DeviceGuard g(device);
     int rc = LSM_OK;
@@ -426,6 +437,8 @@ int lsm_mesh_free(lsm_mesh* mh)
     if (!mh) return LSM_E_INVALID_ARG;
     Mesh* me = &mh->m;
     DeviceGuard g(me->ctx ? me->ctx->device : 0);
+    tree_free(me->tree);
+    me->tree = nullptr;
     void* ps[] = {me->verts, me->tris, me->tri_sigma, me->tri_n, me->vpn, me->s64_pos, me->s64_nw,
                   me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, me->tile_lo, me->tile_hi, me->tile_chi, me->tile_clo};
     for (void* p : ps)

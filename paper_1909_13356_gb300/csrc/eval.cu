@@ -278,6 +278,14 @@ struct EvalArgs {
     double* far_io;
     const double* x_old;
     unsigned long long* pairs;  // [2] pairs evaluated in near / far tiles
+    // mixed kernel only: interaction lists of the treecode.  Block b walks the
+    // tile ids list[blist[b].x .. + blist[b].y); ids >= ntiles are proxy
+    // tiles (positions ppos, weights pnw; always far).  tlo .. tclo then
+    // cover source and proxy tiles.
+    const int* list = nullptr;
+    const int2* blist = nullptr;
+    const float4* ppos = nullptr;
+    const float4* pnw = nullptr;
 };
 
 // Block-wide sums of the pair counts, added once per CTA.
@@ -433,6 +441,14 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         tend = w.x + w.y;
         t0 = w.z;
         t1 = w.w;
+    } else if (A.list) {
+        // this split's part of the block's interaction list
+        base = blockIdx.x * (kEvalThreads * TPT);
+        tend = A.nt;
+        const int2 r = A.blist[blockIdx.x];
+        const int per = (r.y + (int)gridDim.y - 1) / (int)gridDim.y;
+        t0 = min(r.x + (int)blockIdx.y * per, r.x + r.y);
+        t1 = min(r.x + r.y, t0 + per);
     } else {
         base = blockIdx.x * (kEvalThreads * TPT);
         tend = A.nt;
@@ -473,39 +489,45 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         fence_mbar_init();
     }
     __syncthreads();
-    // thread 0 stages a tile; the low parts of the positions only for near tiles
+    // thread 0 stages a tile; the low parts of the positions only for near
+    // tiles.  Proxy tiles (ids >= ntiles, list mode only) are always far.
+    auto tile_at = [&](int j) { return A.list ? A.list[j] : j; };
     auto issue = [&](int t, int b) {
         const int cnt = (int)A.thi[t].w;
         const uint32_t bytes = (uint32_t)cnt * 16u;
-        const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+        const bool proxy = t >= A.ntiles;
+        const bool far = proxy || tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
         mbar_expect_tx(&bar[b], (far ? 2u : 4u) * bytes);
-        bulk_g2s(&sh_pos[b][0], spos + (size_t)t * kTile, bytes, &bar[b]);
-        bulk_g2s(&sh_nw[b][0], snw + (size_t)t * kTile, bytes, &bar[b]);
+        const float4* gp = proxy ? A.ppos + (size_t)(t - A.ntiles) * kTile : spos + (size_t)t * kTile;
+        const float4* gn = proxy ? A.pnw + (size_t)(t - A.ntiles) * kTile : snw + (size_t)t * kTile;
+        bulk_g2s(&sh_pos[b][0], gp, bytes, &bar[b]);
+        bulk_g2s(&sh_nw[b][0], gn, bytes, &bar[b]);
         if (!far) {
             bulk_g2s(&sh_lo[b][0], slo + (size_t)t * kTile, bytes, &bar[b]);
             bulk_g2s(&sh_nl[b][0], snwlo + (size_t)t * kTile, bytes, &bar[b]);
         }
     };
-    if (tid == 0 && t0 < t1) issue(t0, 0);
+    if (tid == 0 && t0 < t1) issue(tile_at(t0), 0);
 
     unsigned long long pairs_near = 0, pairs_far = 0;
-    for (int t = t0; t < t1; t++) {
-        const int it = t - t0;
+    for (int j = t0; j < t1; j++) {
+        const int it = j - t0;
         const int b = it & 1;
-        if (tid == 0 && t + 1 < t1) issue(t + 1, b ^ 1);
+        const int t = tile_at(j);
+        if (tid == 0 && j + 1 < t1) issue(tile_at(j + 1), b ^ 1);
         const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), kWaitLimit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(A.flag, kErrWaitTimeout);
                 // let any copy still in flight land before the CTA exits
-                if (t + 1 < t1) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
+                if (j + 1 < t1) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
             }
             break;
         }
         const float4 tl = A.tlo[t], th = A.thi[t];
         const float4 ch = A.tchi[t], cl = A.tclo[t];
         const int cnt = (int)A.thi[t].w;
-        const bool far = tile_is_far(s_bb, tl, th, A.cut2);
+        const bool far = t >= A.ntiles || tile_is_far(s_bb, tl, th, A.cut2);
         const float4* sp = sh_pos[b];
         const float4* sn = sh_nw[b];
         if (far) {
@@ -1204,6 +1226,20 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     nsplit = (ntiles + tps - 1) / tps;
 
     Scratch s(st);
+    // mixed path on a large mesh: the treecode's interaction lists
+    int* list = nullptr;
+    int2* blist = nullptr;
+    const bool use_tree = mixed && tree_wanted(ctx, me);
+    if (use_tree) {
+        int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st);
+        if (rc != LSM_OK) return rc;
+        int64_t total = 0;
+        rc = tree_lists(ctx, me, t, tpb, s, &list, &blist, &total, st);
+        if (rc != LSM_OK) return rc;
+        const int64_t avg = total / nblk;
+        nsplit = 1;
+        if (nblk < want) nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((want + nblk - 1) / nblk, avg / 4));
+    }
     double* part = res;
     if (nsplit > 1) LSM_CUDA_TRY(ctx, s.get(&part, (size_t)nsplit * 4 * t.n));
     EvalArgs A;
@@ -1231,6 +1267,17 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         A.ff_mode = inc->mode;
         A.far_io = inc->far_io;
         A.x_old = inc->x_old;
+    }
+    if (use_tree) {
+        const Tree* T = me->tree;
+        A.tlo = T->tile_lo;
+        A.thi = T->tile_hi;
+        A.tchi = T->tile_chi;
+        A.tclo = T->tile_clo;
+        A.list = list;
+        A.blist = blist;
+        A.ppos = T->p_pos;
+        A.pnw = T->p_nw;
     }
     dim3 grid(nblk, nsplit);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -23,6 +23,8 @@ namespace lsm {
 constexpr int kTile = 128;
 // Targets per thread block row of the pair kernels (threads * targets/thread).
 constexpr int kEvalThreads = 128;
+// Largest Chebyshev degree of the treecode's proxy grids.
+constexpr int kTreeMaxDegree = 12;
 
 // Last-error message, safe to set from several host threads.
 class ErrorText {
@@ -57,8 +59,11 @@ struct Ctx {
     int64_t prof_launches[3] = {0, 0, 0};
 };
 
+struct Tree;
+
 struct Mesh {
     Ctx* ctx = nullptr;
+    Tree* tree = nullptr;        // treecode far field, built on first use
     int64_t nv = 0, m = 0, ns = 0, ntiles = 0;
     int nq = 0;
     lsm_quad rule{4, 0};
@@ -211,6 +216,34 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
                int max_items, double* res, int precision, cudaStream_t st);
 int eval_noalloc(Ctx* ctx, const Mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
                  int precision, cudaStream_t st);
+
+// tree.cu
+// The treecode of a mesh: node boxes over Morton-ordered source tiles and the
+// proxy tiles (Chebyshev points with interpolated dipole weights) of the
+// nodes large enough to profit.  Tile ids below ntiles are source tiles,
+// the rest proxy tiles; tile_* cover both.
+struct Tree {
+    int degree = 0;
+    float theta = 0.0f;
+    int top = 0;                            // level of the root (level 0 = tiles)
+    int64_t lev_off[33] = {0};              // first node of each level
+    int64_t nnodes = 0;
+    int ntiles = 0, nptiles = 0;
+    float4* node_lo = nullptr;              // box, rounded down; w = sigma_max
+    float4* node_hi = nullptr;              // box, rounded up
+    int4* node_info = nullptr;              // first tile, tile count, first proxy tile or -1, proxy tiles
+    float4 *p_pos = nullptr, *p_nw = nullptr;   // proxies, kTile per proxy tile
+    float4 *tile_lo = nullptr, *tile_hi = nullptr, *tile_chi = nullptr, *tile_clo = nullptr;
+    size_t bytes = 0;
+};
+bool tree_wanted(const Ctx* ctx, const Mesh* me);
+int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st);
+void tree_free(Tree* t);
+// Interaction lists of sorted targets in blocks of tpb: for block b, the
+// tile ids list[blist[b].x .. + blist[b].y) in tree order; *total = the
+// summed list length.
+int tree_lists(Ctx* ctx, const Mesh* me, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
+               int64_t* total, cudaStream_t st);
 
 // newton.cu
 int solve_charts_device(Ctx* ctx, Mesh* mesh, int n_gl, double tol, int max_iter,

@@ -1,0 +1,653 @@
+// tree.cu -- far field of the mixed path on large meshes: a barycentric
+// Lagrange treecode over the Morton-ordered source tiles.
+//
+// Beyond the cutoff the smoothed kernel is the Laplace double layer (eq.
+// kerapprox, Sec. 4.4); the paper evaluates that part with an FMM.  Here the
+// tiles of consecutive Morton-sorted sources are the leaves of a binary tree
+// whose node (l, i) holds tiles [i 2^l, (i+1) 2^l) and their tight box.  For
+// a node C with box centre c and half-widths h, the double-layer kernel y ->
+// K(x, y) interpolated on the tensor Chebyshev grid s_k = c + h * cos(k pi/p)
+// (per axis) gives
+//     sum_j nw_j . K(x, y_j)  ~  sum_k Q_k . K(x, s_k),   Q_k = sum_j L_k(y_j) nw_j,
+// with L_k the tensor-product Lagrange basis of the grid in barycentric form.
+// The error falls like a power of (radius of C) / |x - c|, so a node acts
+// through its proxies (s_k, Q_k) on a block of targets when
+//     |c - block box| >= radius(C) / theta
+// and the node's box is beyond the cutoff from the block (every pair is a
+// pure double-layer pair).  Proxies are sources of the far-pair kernel like
+// any other: each node's proxies fill proxy tiles laid out as source tiles,
+// and a target block's interaction list (built per evaluation by a walk of
+// the tree) mixes source tiles and proxy tiles.  A node gets proxies only
+// when it holds at least twice as many sources as proxies.
+//
+// Steps: node boxes bottom-up (k_nodes_leaf, k_nodes_up); proxy assignment
+// on the host; P2M, the weights Q_k summed from the sources in chunks
+// (k_p2m, k_p2m_reduce); per evaluation, target block boxes
+// (k_block_boxes) and two walks (count, then write) of the tree per block
+// (k_tree_walk).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lsm_internal.cuh"
+
+namespace lsm {
+namespace {
+
+constexpr int kP2MThreads = 256;
+constexpr int kP2MChunkTiles = 256;      // source tiles per P2M work item
+constexpr int kMaxN = kTreeMaxDegree + 1; // grid points per axis at most
+constexpr int kLStride = 16;              // floats per (axis, source) row of basis values
+constexpr int kWalkThreads = 128;
+constexpr int kMaxLevels = 32;
+
+inline int blocks_of(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+__global__ void k_nodes_leaf(const float4* __restrict__ tlo, const float4* __restrict__ thi, int ntiles,
+                             float4* __restrict__ nlo, float4* __restrict__ nhi, int4* __restrict__ info)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntiles) return;
+    const float4 b = thi[i];
+    nlo[i] = tlo[i];
+    nhi[i] = make_float4(b.x, b.y, b.z, 0.0f);
+    info[i] = make_int4(i, 1, -1, 0);
+}
+
+// Node i of a level: the union of children 2i and 2i+1 of the level below.
+__global__ void k_nodes_up(const float4* __restrict__ clo, const float4* __restrict__ chi,
+                           const int4* __restrict__ cinfo, int nchild, float4* __restrict__ nlo,
+                           float4* __restrict__ nhi, int4* __restrict__ info, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = 2 * i, b = 2 * i + 1;
+    float4 l = clo[a], h = chi[a];
+    int4 f = cinfo[a];
+    if (b < nchild) {
+        const float4 l2 = clo[b], h2 = chi[b];
+        l = make_float4(fminf(l.x, l2.x), fminf(l.y, l2.y), fminf(l.z, l2.z), fmaxf(l.w, l2.w));
+        h = make_float4(fmaxf(h.x, h2.x), fmaxf(h.y, h2.y), fmaxf(h.z, h2.z), 0.0f);
+        f.y += cinfo[b].y;
+    }
+    nlo[i] = l;
+    nhi[i] = h;
+    info[i] = make_int4(f.x, f.y, -1, 0);
+}
+
+// Grid of one node: centre, half-widths and points per axis (one point on an
+// axis of zero extent).  Host and device compute it alike from the FP32 box.
+struct NodeGrid {
+    double c[3], h[3];
+    int n[3];
+};
+__host__ __device__ inline NodeGrid node_grid(float4 lo, float4 hi, int degree)
+{
+    NodeGrid g;
+    const float l[3] = {lo.x, lo.y, lo.z}, u[3] = {hi.x, hi.y, hi.z};
+    for (int a = 0; a < 3; a++) {
+        g.c[a] = 0.5 * ((double)l[a] + (double)u[a]);
+        g.h[a] = 0.5 * ((double)u[a] - (double)l[a]);
+        g.n[a] = g.h[a] > 0.0 ? degree + 1 : 1;
+    }
+    return g;
+}
+
+// Chebyshev points of the second kind on [-1, 1], in FP32.
+__device__ __forceinline__ float cheb_point(int k, int degree)
+{
+    return (float)cospi((double)k / (double)degree);
+}
+
+struct P2MArgs {
+    const double4_32a* pos;   // (x, y, z, a)
+    const double4_32a* nw;    // (nw / 4 pi, 0)
+    int64_t ns;
+    const float4* nlo;
+    const float4* nhi;
+    const int4* ninfo;
+    const int4* items;        // node, first tile, end tile, partial offset (in proxies) or -1
+    int degree;
+    float4* p_pos;
+    float4* p_nw;
+    double* partial;          // [proxies][3] per chunk
+};
+
+// One work item: the weights Q_k of one node summed over a run of its tiles.
+// Threads own a pair (k0, k1) of grid indices and every k2; with few pairs,
+// groups of threads split the sources of each tile and are summed at the end.
+__global__ void __launch_bounds__(kP2MThreads) k_p2m(P2MArgs A)
+{
+    __shared__ __align__(16) float sL[3][kTile][kLStride];
+    __shared__ __align__(16) float sN[kTile][4];
+    const int4 it = A.items[blockIdx.x];
+    const int node = it.x;
+    const float4 lo = A.nlo[node], hi = A.nhi[node];
+    const int4 info = A.ninfo[node];
+    const NodeGrid G = node_grid(lo, hi, A.degree);
+    const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+    const int pairs = n0 * n1;
+    const int tid = threadIdx.x;
+    const bool fits = (size_t)pairs * n2 * 3 * sizeof(double) <= sizeof(sL);
+    const int groups = fits ? max(1, min(3, kP2MThreads / pairs)) : 1;
+    const int g = tid / pairs, pr = tid - g * pairs;
+    const bool active = g < groups;
+    const int k0 = active ? pr / n1 : 0, k1 = active ? pr - (pr / n1) * n1 : 0;
+
+    float acc_h[kMaxN][3], acc_l[kMaxN][3];
+#pragma unroll
+    for (int k = 0; k < kMaxN; k++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc_h[k][c] = acc_l[k][c] = 0.0f;
+
+    for (int t = it.y; t < it.z; t++) {
+        if (tid < kTile) {
+            const int64_t i = (int64_t)t * kTile + tid;
+            if (i < A.ns) {
+                const double4_32a p = A.pos[i];
+                const double4_32a q = A.nw[i];
+                const double y[3] = {p.x, p.y, p.z};
+                for (int a = 0; a < 3; a++) {
+                    float* L = sL[a][tid];
+                    const int na = G.n[a];
+                    if (na == 1) {
+                        L[0] = 1.0f;
+                        continue;
+                    }
+                    const float xi = (float)((y[a] - G.c[a]) / G.h[a]);
+                    // barycentric weights (-1)^k, halved at the two ends
+                    int hit = -1;
+                    float sum = 0.0f;
+                    for (int k = 0; k < na; k++) {
+                        const float d = xi - cheb_point(k, na - 1);
+                        if (d == 0.0f) hit = k;
+                        float w = (k & 1) ? -1.0f : 1.0f;
+                        if (k == 0 || k == na - 1) w *= 0.5f;
+                        const float tk = d == 0.0f ? 0.0f : w / d;
+                        L[k] = tk;
+                        sum += tk;
+                    }
+                    if (hit >= 0) {
+                        for (int k = 0; k < na; k++) L[k] = k == hit ? 1.0f : 0.0f;
+                    } else {
+                        const float inv = 1.0f / sum;
+                        for (int k = 0; k < na; k++) L[k] *= inv;
+                    }
+                }
+                sN[tid][0] = (float)q.x;
+                sN[tid][1] = (float)q.y;
+                sN[tid][2] = (float)q.z;
+                sN[tid][3] = 0.0f;
+            } else {
+                for (int a = 0; a < 3; a++)
+                    for (int k = 0; k < G.n[a]; k++) sL[a][tid][k] = 0.0f;
+                sN[tid][0] = sN[tid][1] = sN[tid][2] = sN[tid][3] = 0.0f;
+            }
+        }
+        __syncthreads();
+        if (active) {
+            float ph[kMaxN][3];
+#pragma unroll
+            for (int k = 0; k < kMaxN; k++) ph[k][0] = ph[k][1] = ph[k][2] = 0.0f;
+            for (int s = g; s < kTile; s += groups) {
+                const float l01 = sL[0][s][k0] * sL[1][s][k1];
+                const float4 nv = *reinterpret_cast<const float4*>(sN[s]);
+                const float wx = nv.x * l01, wy = nv.y * l01, wz = nv.z * l01;
+                const float4* L2 = reinterpret_cast<const float4*>(sL[2][s]);
+#pragma unroll
+                for (int q = 0; q < (kMaxN + 3) / 4; q++) {
+                    if (4 * q >= n2) break;
+                    const float4 l4 = L2[q];
+                    const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int k2 = 4 * q + e;
+                        if (k2 < kMaxN) {
+                            ph[k2][0] = fmaf(lv[e], wx, ph[k2][0]);
+                            ph[k2][1] = fmaf(lv[e], wy, ph[k2][1]);
+                            ph[k2][2] = fmaf(lv[e], wz, ph[k2][2]);
+                        }
+                    }
+                }
+            }
+            // fold this tile's FP32 sums into the compensated accumulators
+#pragma unroll
+            for (int k = 0; k < kMaxN; k++) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float s = acc_h[k][c] + ph[k][c];
+                    const float bp = s - acc_h[k][c];
+                    acc_l[k][c] += (acc_h[k][c] - (s - bp)) + (ph[k][c] - bp);
+                    acc_h[k][c] = s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // sum the groups in order, group 0 writes
+    double* buf = reinterpret_cast<double*>(&sL[0][0][0]);
+    double Q[kMaxN][3];
+#pragma unroll
+    for (int k = 0; k < kMaxN; k++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) Q[k][c] = (double)acc_h[k][c] + (double)acc_l[k][c];
+    for (int gg = 1; gg < groups; gg++) {
+        if (g == gg) {
+            for (int k = 0; k < n2; k++)
+                for (int c = 0; c < 3; c++) buf[((size_t)pr * n2 + k) * 3 + c] = Q[k][c];
+        }
+        __syncthreads();
+        if (g == 0) {
+            for (int k = 0; k < n2; k++)
+                for (int c = 0; c < 3; c++) Q[k][c] += buf[((size_t)pr * n2 + k) * 3 + c];
+        }
+        __syncthreads();
+    }
+    if (g != 0 || !active) return;
+    const int64_t base = (int64_t)info.z * kTile;
+    const bool first_chunk = it.y == info.x;
+    for (int k2 = 0; k2 < n2; k2++) {
+        const int k = (k0 * n1 + k1) * n2 + k2;
+        if (it.w < 0) {
+            A.p_nw[base + k] = make_float4((float)Q[k2][0], (float)Q[k2][1], (float)Q[k2][2], 0.0f);
+        } else {
+            double* dst = A.partial + ((int64_t)it.w + k) * 3;
+            dst[0] = Q[k2][0];
+            dst[1] = Q[k2][1];
+            dst[2] = Q[k2][2];
+        }
+        if (first_chunk) {
+            const float s0 = n0 > 1 ? cheb_point(k0, n0 - 1) : 0.0f;
+            const float s1 = n1 > 1 ? cheb_point(k1, n1 - 1) : 0.0f;
+            const float s2 = n2 > 1 ? cheb_point(k2, n2 - 1) : 0.0f;
+            A.p_pos[base + k] = make_float4((float)(G.h[0] * (double)s0), (float)(G.h[1] * (double)s1),
+                                            (float)(G.h[2] * (double)s2), 0.0f);
+        }
+    }
+}
+
+// Nodes whose weights were summed in several chunks: add the chunks in order.
+// r = node, first partial offset, chunks, proxies.
+__global__ void k_p2m_reduce(const int4* __restrict__ red, const int4* __restrict__ ninfo,
+                             const double* __restrict__ partial, float4* __restrict__ p_nw)
+{
+    const int4 r = red[blockIdx.x];
+    const int64_t base = (int64_t)ninfo[r.x].z * kTile;
+    for (int k = threadIdx.x; k < r.w; k += blockDim.x) {
+        double q[3] = {0.0, 0.0, 0.0};
+        for (int ch = 0; ch < r.z; ch++) {
+            const double* src = partial + ((int64_t)r.y + (int64_t)ch * r.w + k) * 3;
+            q[0] += src[0];
+            q[1] += src[1];
+            q[2] += src[2];
+        }
+        p_nw[base + k] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.0f);
+    }
+}
+
+// Box of each block of tpb consecutive sorted targets, FP32 rounded outward
+// (the same box the pair kernels compute for the block).
+__global__ void __launch_bounds__(kEvalThreads) k_block_boxes(const double* __restrict__ x, int64_t ld, int n,
+                                                              int tpb, float4* __restrict__ blo,
+                                                              float4* __restrict__ bhi)
+{
+    __shared__ float part[6][kEvalThreads / 32];
+    const int b = blockIdx.x;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int j = threadIdx.x; j < tpb; j += kEvalThreads) {
+        const int64_t i = (int64_t)b * tpb + j;
+        if (i >= n) break;
+        for (int c = 0; c < 3; c++) {
+            const double v = x[c * ld + i];
+            lo[c] = fminf(lo[c], __double2float_rd(v));
+            hi[c] = fmaxf(hi[c], __double2float_ru(v));
+        }
+    }
+    for (int c = 0; c < 3; c++)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 3; c++) {
+            part[c][w] = lo[c];
+            part[3 + c][w] = hi[c];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 3; c++)
+            for (int k = 1; k < kEvalThreads / 32; k++) {
+                part[c][0] = fminf(part[c][0], part[c][k]);
+                part[3 + c][0] = fmaxf(part[3 + c][0], part[3 + c][k]);
+            }
+        blo[b] = make_float4(part[0][0], part[1][0], part[2][0], 0.0f);
+        bhi[b] = make_float4(part[3][0], part[4][0], part[5][0], 0.0f);
+    }
+}
+
+struct WalkArgs {
+    const float4* blo;
+    const float4* bhi;
+    int nblk;
+    const float4* nlo;
+    const float4* nhi;
+    const int4* info;
+    int64_t lev_off[kMaxLevels + 1];
+    int top;
+    int ntiles;
+    float theta2, cut2;
+    const uint32_t* off;   // pass 1: list offset of each block
+    uint32_t* cnt;         // pass 0: list length of each block
+    int* list;             // pass 1
+    int2* blist;           // pass 1: (offset, length)
+};
+
+// Depth-first walk of the tree for one target block (children in Morton
+// order, so the list is in a fixed order).  Pass 0 counts, pass 1 writes.
+__global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= A.nblk) return;
+    const float4 bl = A.blo[b], bh = A.bhi[b];
+    int stk[2 * kMaxLevels + 2];
+    int sp = 0;
+    stk[sp++] = A.top << 26;
+    uint32_t n = 0;
+    const uint32_t o = pass ? A.off[b] : 0u;
+    while (sp > 0) {
+        const int v = stk[--sp];
+        const int l = v >> 26, i = v & ((1 << 26) - 1);
+        const int64_t node = A.lev_off[l] + i;
+        const int4 f = A.info[node];
+        if (f.z >= 0) {
+            const float4 lo = A.nlo[node], hi = A.nhi[node];
+            const float gx = fmaxf(0.0f, fmaxf(lo.x - bh.x, bl.x - hi.x));
+            const float gy = fmaxf(0.0f, fmaxf(lo.y - bh.y, bl.y - hi.y));
+            const float gz = fmaxf(0.0f, fmaxf(lo.z - bh.z, bl.z - hi.z));
+            if (gx * gx + gy * gy + gz * gz > A.cut2 * lo.w * lo.w * 1.0001f) {
+                const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+                const float ex = hi.x - lo.x, ey = hi.y - lo.y, ez = hi.z - lo.z;
+                const float r2 = 0.25f * (ex * ex + ey * ey + ez * ez);
+                const float dx = fmaxf(0.0f, fmaxf(bl.x - cx, cx - bh.x));
+                const float dy = fmaxf(0.0f, fmaxf(bl.y - cy, cy - bh.y));
+                const float dz = fmaxf(0.0f, fmaxf(bl.z - cz, cz - bh.z));
+                if ((dx * dx + dy * dy + dz * dz) * A.theta2 >= r2 * 1.0001f) {
+                    if (pass)
+                        for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.ntiles + f.z + k;
+                    n += f.w;
+                    continue;
+                }
+            }
+        }
+        if (l == 0) {
+            if (pass) A.list[o + n] = i;
+            n++;
+            continue;
+        }
+        const int64_t nch = A.lev_off[l] - A.lev_off[l - 1];
+        if (2 * i + 1 < nch) stk[sp++] = ((l - 1) << 26) | (2 * i + 1);
+        stk[sp++] = ((l - 1) << 26) | (2 * i);
+    }
+    if (pass)
+        A.blist[b] = make_int2((int)o, (int)n);
+    else
+        A.cnt[b] = n;
+}
+
+}  // namespace
+
+bool tree_wanted(const Ctx* ctx, const Mesh* me)
+{
+    return ctx->opt.tree_min_sources >= 0 && me->ns >= ctx->opt.tree_min_sources && me->ntiles >= 8;
+}
+
+void tree_free(Tree* t)
+{
+    if (!t) return;
+    void* ps[] = {t->node_lo, t->node_hi, t->node_info, t->p_pos, t->p_nw, t->tile_lo, t->tile_hi, t->tile_chi,
+                  t->tile_clo};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete t;
+}
+
+int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st)
+{
+    const int degree = ctx->opt.tree_degree;
+    const float theta = ctx->opt.tree_theta;
+    if (me->tree && me->tree->degree == degree && me->tree->theta == theta) return LSM_OK;
+    tree_free(me->tree);
+    me->tree = nullptr;
+    Tree* T = new (std::nothrow) Tree();
+    if (!T) return LSM_E_OOM;
+    auto fail = [&](int rc) {
+        tree_free(T);
+        return rc;
+    };
+    auto alloc = [&](auto** p, size_t count) -> bool {
+        using E = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
+        if (cudaMalloc((void**)p, count * sizeof(E) + 16) != cudaSuccess) return false;
+        T->bytes += count * sizeof(E);
+        return true;
+    };
+    T->degree = degree;
+    T->theta = theta;
+    T->ntiles = (int)me->ntiles;
+    // levels: level l has ceil(ntiles / 2^l) nodes, up to a single root
+    int64_t n = me->ntiles;
+    int lev = 0;
+    T->lev_off[0] = 0;
+    while (true) {
+        T->lev_off[lev + 1] = T->lev_off[lev] + n;
+        if (n == 1 || lev == kMaxLevels - 1) break;
+        n = (n + 1) / 2;
+        lev++;
+    }
+    if (n != 1) {
+        ctx->err = "tree: too many source tiles";
+        return fail(LSM_E_INVALID_ARG);
+    }
+    T->top = lev;
+    T->nnodes = T->lev_off[lev + 1];
+    if (!alloc(&T->node_lo, T->nnodes) || !alloc(&T->node_hi, T->nnodes) || !alloc(&T->node_info, T->nnodes)) {
+        cudaGetLastError();
+        ctx->err = "tree: out of device memory";
+        return fail(LSM_E_OOM);
+    }
+    k_nodes_leaf<<<blocks_of(me->ntiles, 256), 256, 0, st>>>(me->tile_lo, me->tile_hi, (int)me->ntiles, T->node_lo,
+                                                               T->node_hi, T->node_info);
+    if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
+    ctx->launches++;
+    for (int l = 1; l <= T->top; l++) {
+        const int64_t c0 = T->lev_off[l - 1], nc = T->lev_off[l] - c0, o = T->lev_off[l],
+                      nn = T->lev_off[l + 1] - o;
+        k_nodes_up<<<blocks_of(nn, 256), 256, 0, st>>>(T->node_lo + c0, T->node_hi + c0, T->node_info + c0, (int)nc,
+                                                       T->node_lo + o, T->node_hi + o, T->node_info + o, (int)nn);
+        if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
+        ctx->launches++;
+    }
+    // proxy assignment on the host
+    std::vector<float4> hlo(T->nnodes), hhi(T->nnodes);
+    std::vector<int4> hinfo(T->nnodes);
+    if (cudaMemcpyAsync(hlo.data(), T->node_lo, sizeof(float4) * T->nnodes, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hhi.data(), T->node_hi, sizeof(float4) * T->nnodes, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hinfo.data(), T->node_info, sizeof(int4) * T->nnodes, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        ctx->err = "tree: copy of the node boxes failed";
+        return fail(LSM_E_CUDA);
+    }
+    std::vector<int4> items, reds;
+    std::vector<float4> ptlo, pthi, ptchi, ptclo;
+    int64_t nptiles = 0, npartial = 0;
+    for (int l = 1; l <= T->top; l++) {
+        for (int64_t node = T->lev_off[l]; node < T->lev_off[l + 1]; node++) {
+            int4& f = hinfo[node];
+            const int64_t s0 = (int64_t)f.x * kTile;
+            const int64_t s1 = std::min<int64_t>(me->ns, (int64_t)(f.x + f.y) * kTile);
+            const NodeGrid G = node_grid(hlo[node], hhi[node], degree);
+            const int64_t np = (int64_t)G.n[0] * G.n[1] * G.n[2];
+            if (2 * np > s1 - s0) continue;
+            const int npt = (int)((np + kTile - 1) / kTile);
+            f.z = (int)nptiles;
+            f.w = npt;
+            for (int j = 0; j < npt; j++) {
+                const int cnt = (int)std::min<int64_t>(kTile, np - (int64_t)j * kTile);
+                ptlo.push_back(hlo[node]);
+                pthi.push_back(make_float4(hhi[node].x, hhi[node].y, hhi[node].z, (float)cnt));
+                float ch[3], cl[3];
+                for (int a = 0; a < 3; a++) {
+                    ch[a] = (float)G.c[a];
+                    cl[a] = (float)(G.c[a] - (double)ch[a]);
+                }
+                ptchi.push_back(make_float4(ch[0], ch[1], ch[2], 0.0f));
+                ptclo.push_back(make_float4(cl[0], cl[1], cl[2], 0.0f));
+            }
+            nptiles += npt;
+            const int nch = (f.y + kP2MChunkTiles - 1) / kP2MChunkTiles;
+            if (nch == 1) {
+                items.push_back(make_int4((int)node, f.x, f.x + f.y, -1));
+            } else {
+                reds.push_back(make_int4((int)node, (int)npartial, nch, (int)np));
+                for (int c = 0; c < nch; c++) {
+                    const int t0 = f.x + c * kP2MChunkTiles, t1 = std::min(f.x + f.y, t0 + kP2MChunkTiles);
+                    items.push_back(make_int4((int)node, t0, t1, (int)(npartial + (int64_t)c * np)));
+                }
+                npartial += (int64_t)nch * np;
+            }
+            if (nptiles + me->ntiles >= (int64_t)1 << 30 || npartial >= (int64_t)1 << 30) {
+                ctx->err = "tree: too many proxies";
+                return fail(LSM_E_INVALID_ARG);
+            }
+        }
+    }
+    T->nptiles = (int)nptiles;
+    const int64_t nall = me->ntiles + nptiles;
+    if (!alloc(&T->tile_lo, nall) || !alloc(&T->tile_hi, nall) || !alloc(&T->tile_chi, nall) ||
+        !alloc(&T->tile_clo, nall) || !alloc(&T->p_pos, std::max<int64_t>(1, nptiles) * kTile) ||
+        !alloc(&T->p_nw, std::max<int64_t>(1, nptiles) * kTile)) {
+        cudaGetLastError();
+        ctx->err = "tree: out of device memory";
+        return fail(LSM_E_OOM);
+    }
+    const size_t b4 = sizeof(float4);
+    const size_t nt = (size_t)me->ntiles;
+    if (cudaMemcpyAsync(T->node_info, hinfo.data(), sizeof(int4) * T->nnodes, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(T->tile_lo, me->tile_lo, b4 * nt, cudaMemcpyDeviceToDevice, st) ||
+        cudaMemcpyAsync(T->tile_hi, me->tile_hi, b4 * nt, cudaMemcpyDeviceToDevice, st) ||
+        cudaMemcpyAsync(T->tile_chi, me->tile_chi, b4 * nt, cudaMemcpyDeviceToDevice, st) ||
+        cudaMemcpyAsync(T->tile_clo, me->tile_clo, b4 * nt, cudaMemcpyDeviceToDevice, st)) {
+        ctx->err = "tree: copy failed";
+        return fail(LSM_E_CUDA);
+    }
+    if (nptiles > 0 &&
+        (cudaMemcpyAsync(T->tile_lo + nt, ptlo.data(), b4 * nptiles, cudaMemcpyHostToDevice, st) ||
+         cudaMemcpyAsync(T->tile_hi + nt, pthi.data(), b4 * nptiles, cudaMemcpyHostToDevice, st) ||
+         cudaMemcpyAsync(T->tile_chi + nt, ptchi.data(), b4 * nptiles, cudaMemcpyHostToDevice, st) ||
+         cudaMemcpyAsync(T->tile_clo + nt, ptclo.data(), b4 * nptiles, cudaMemcpyHostToDevice, st))) {
+        ctx->err = "tree: copy failed";
+        return fail(LSM_E_CUDA);
+    }
+    if (!items.empty()) {
+        Scratch s(st);
+        int4 *d_items = nullptr, *d_reds = nullptr;
+        double* d_part = nullptr;
+        if (s.get(&d_items, items.size()) || s.get(&d_reds, std::max<size_t>(1, reds.size())) ||
+            s.get(&d_part, std::max<int64_t>(1, npartial) * 3)) {
+            ctx->err = "tree: out of device memory";
+            return fail(LSM_E_OOM);
+        }
+        if (cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st) ||
+            (!reds.empty() &&
+             cudaMemcpyAsync(d_reds, reds.data(), sizeof(int4) * reds.size(), cudaMemcpyHostToDevice, st))) {
+            ctx->err = "tree: copy failed";
+            return fail(LSM_E_CUDA);
+        }
+        P2MArgs P;
+        P.pos = me->s64_pos;
+        P.nw = me->s64_nw;
+        P.ns = me->ns;
+        P.nlo = T->node_lo;
+        P.nhi = T->node_hi;
+        P.ninfo = T->node_info;
+        P.items = d_items;
+        P.degree = degree;
+        P.p_pos = T->p_pos;
+        P.p_nw = T->p_nw;
+        P.partial = d_part;
+        k_p2m<<<(unsigned)items.size(), kP2MThreads, 0, st>>>(P);
+        if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
+        ctx->launches++;
+        if (!reds.empty()) {
+            k_p2m_reduce<<<(unsigned)reds.size(), 256, 0, st>>>(d_reds, T->node_info, d_part, T->p_nw);
+            if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
+            ctx->launches++;
+        }
+        // the host vectors and the scratch must outlive the copies
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            ctx->err = "tree: build failed";
+            return fail(LSM_E_CUDA);
+        }
+    } else if (cudaStreamSynchronize(st) != cudaSuccess) {
+        ctx->err = "tree: build failed";
+        return fail(LSM_E_CUDA);
+    }
+    me->tree = T;
+    me->bytes += T->bytes;
+    return LSM_OK;
+}
+
+int tree_lists(Ctx* ctx, const Mesh* me, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
+               int64_t* total_out, cudaStream_t st)
+{
+    const Tree* T = me->tree;
+    const int nblk = (t.n + tpb - 1) / tpb;
+    float4 *blo = nullptr, *bhi = nullptr;
+    uint32_t* cnt = nullptr;
+    LSM_CUDA_TRY(ctx, s.get(&blo, nblk));
+    LSM_CUDA_TRY(ctx, s.get(&bhi, nblk));
+    LSM_CUDA_TRY(ctx, s.get(&cnt, (size_t)nblk + 1));
+    LSM_CUDA_TRY(ctx, s.get(blist, nblk));
+    k_block_boxes<<<nblk, kEvalThreads, 0, st>>>(t.x, t.ld, t.n, tpb, blo, bhi);
+    LSM_LAUNCHED(ctx);
+    WalkArgs W;
+    W.blo = blo;
+    W.bhi = bhi;
+    W.nblk = nblk;
+    W.nlo = T->node_lo;
+    W.nhi = T->node_hi;
+    W.info = T->node_info;
+    for (int l = 0; l <= kMaxLevels; l++) W.lev_off[l] = l <= T->top + 1 ? T->lev_off[l] : 0;
+    W.top = T->top;
+    W.ntiles = T->ntiles;
+    W.theta2 = T->theta * T->theta;
+    W.cut2 = (float)(ctx->opt.cutoff_mixed * ctx->opt.cutoff_mixed);
+    W.off = cnt;
+    W.cnt = cnt;
+    W.list = nullptr;
+    W.blist = *blist;
+    k_tree_walk<<<blocks_of(nblk, kWalkThreads), kWalkThreads, 0, st>>>(W, 0);
+    LSM_LAUNCHED(ctx);
+    uint32_t* total = cnt + nblk;
+    int rc = scan_exclusive(ctx, cnt, nblk, total, st);
+    if (rc != LSM_OK) return rc;
+    uint32_t h_total = 0;
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(&h_total, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (h_total >= (1u << 31)) {
+        ctx->err = "tree: interaction lists too long";
+        return LSM_E_INVALID_ARG;
+    }
+    *total_out = h_total;
+    LSM_CUDA_TRY(ctx, s.get(list, std::max<uint32_t>(1u, h_total)));
+    W.list = *list;
+    k_tree_walk<<<blocks_of(nblk, kWalkThreads), kWalkThreads, 0, st>>>(W, 1);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
+}  // namespace lsm

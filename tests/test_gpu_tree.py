@@ -1,0 +1,162 @@
+"""GPU parity of the mixed path's treecode far field against the FP64 oracle.
+
+The treecode replaces far source tiles by Chebyshev proxies of their tree
+nodes; the sum it approximates is the oracle's direct sum over all pairs, so
+the bar is the mixed path's: |dPhi| <= 1e-7, |d grad Phi| <= 1e-7 / sigma_min.
+Meshes below the default size threshold are pushed onto the treecode with
+tree_min_sources=1.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-7
+
+
+@pytest.fixture(scope="module")
+def lsm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1909_13356_gb300 as m
+    m.load()
+    return m
+
+
+def _eval(lsm, ctx, mesh, x, prec=None):
+    phi, grad = mesh.eval_phi_grad(torch.from_numpy(x).cuda(), lsm.MIXED if prec is None else prec)
+    return phi.cpu().numpy(), grad.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def torus_case(lsm, oracle_mod):
+    # graded torus, 120 x 32 cells (7,680 triangles, 276,480 nodes), 6,000
+    # targets within 3 sigma
+    w = synth.torus_c2(6_000, seed=21, nu=120, nv=32)
+    m = w["mesh"]
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 6, 0)
+    phi_o, grad_o = oracle_mod.phi_grad(y, nw, sg, w["targets"])
+    return dict(w=w, phi=phi_o, grad=grad_o)
+
+
+def test_torus_tree_matches_oracle(lsm, torus_case):
+    w = torus_case["w"]
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    assert mesh.info()["n_sources"] >= 262_144     # above the default threshold
+    ctx.read_stats(reset=True)
+    phi, grad = _eval(lsm, ctx, mesh, w["targets"])
+    st_tree = ctx.read_stats(reset=True)
+    assert np.abs(phi - torus_case["phi"]).max() <= TOL32
+    assert np.abs(grad - torus_case["grad"]).max() <= TOL32 / m.sigma.min()
+    # the direct far field on the same inputs: same answer, more pairs
+    ctx_d = lsm.Context(0, tree_min_sources=-1)
+    mesh_d = ctx_d.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    ctx_d.read_stats(reset=True)
+    phi_d, grad_d = _eval(lsm, ctx_d, mesh_d, w["targets"])
+    st_dir = ctx_d.read_stats(reset=True)
+    assert np.abs(phi_d - torus_case["phi"]).max() <= TOL32
+    assert np.abs(phi - phi_d).max() <= TOL32
+    # near tiles are the same in both: the treecode only replaces far tiles
+    assert st_tree["pairs_near"] == st_dir["pairs_near"]
+    assert st_tree["pairs_far"] < st_dir["pairs_far"]
+
+
+def test_tree_dense_targets_against_direct(lsm):
+    """100,000 targets on the same torus (blocks of 256 targets are then
+    compact): the treecode against the direct far field, both on the GPU,
+    with far fewer pairs."""
+    w = synth.torus_c2(100_000, seed=21, nu=120, nv=32)
+    m = w["mesh"]
+    out = {}
+    for name, kw in (("tree", {}), ("direct", {"tree_min_sources": -1})):
+        ctx = lsm.Context(0, **kw)
+        mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+        ctx.read_stats(reset=True)
+        out[name] = _eval(lsm, ctx, mesh, w["targets"]) + (ctx.read_stats(reset=True),)
+    (pt, gt, st_t), (pd, gd, st_d) = out["tree"], out["direct"]
+    assert np.abs(pt - pd).max() <= TOL32
+    assert np.abs(gt - gd).max() <= TOL32 / m.sigma.min()
+    assert st_t["pairs_near"] + st_t["pairs_far"] < 0.5 * (st_d["pairs_near"] + st_d["pairs_far"])
+
+
+def test_tree_error_falls_with_degree(lsm, torus_case):
+    w = torus_case["w"]
+    m = w["mesh"]
+    errs = []
+    for deg in (3, 6, 10):
+        ctx = lsm.Context(0, tree_degree=deg, tree_theta=0.6)
+        mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+        phi, _ = _eval(lsm, ctx, mesh, w["targets"])
+        errs.append(np.abs(phi - torus_case["phi"]).max())
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] <= TOL32
+
+
+def test_tree_deterministic_and_reused(lsm, torus_case):
+    w = torus_case["w"]
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    n0 = ctx.launch_count
+    a = _eval(lsm, ctx, mesh, w["targets"])
+    n1 = ctx.launch_count
+    b = _eval(lsm, ctx, mesh, w["targets"])
+    n2 = ctx.launch_count
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # the tree (node boxes level by level, proxy weights) is built by the
+    # first call only
+    assert (n1 - n0) - (n2 - n1) >= 10
+
+
+def test_cube_flat_faces_tree(lsm, oracle_mod):
+    """Cube faces are planar, so node boxes have axes of zero extent (one
+    proxy point on such an axis).  Cube [-1,1]^3, 16 x 16 squares per face
+    (3,072 triangles, 49,152 nodes), sigma = 0.02, 50,000 targets uniform in
+    [-1.5,1.5]^3."""
+    m = synth.cube(1.0, 16)
+    m.sigma = np.full(m.m, 0.02)
+    x = synth.targets_uniform(50_000, -1.5, 1.5, synth.rng(31))
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 4, 0)
+    phi_o, grad_o = oracle_mod.phi_grad(y, nw, sg, x)
+    ctx = lsm.Context(0, tree_min_sources=1)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
+    ctx.read_stats(reset=True)
+    phi, grad = _eval(lsm, ctx, mesh, x)
+    st = ctx.read_stats(reset=True)
+    assert np.abs(phi - phi_o).max() <= TOL32
+    assert np.abs(grad - grad_o).max() <= TOL32 / m.sigma.min()
+    # volume targets make wide blocks: fewer nodes open, but proxies act
+    assert st["pairs_near"] + st["pairs_far"] < 0.9 * len(y) * len(x)
+
+
+def test_ragged_target_counts_tree(lsm, torus_case):
+    """Target counts that leave a partial block, a single target, and a block
+    count below the GPU's width (the interaction lists are split)."""
+    w = torus_case["w"]
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    for n in (1, 255, 257, 3001):
+        phi, grad = _eval(lsm, ctx, mesh, w["targets"][:n])
+        assert np.abs(phi - torus_case["phi"][:n]).max() <= TOL32
+        assert np.abs(grad - torus_case["grad"][:n]).max() <= TOL32 / m.sigma.min()
+
+
+def test_chart_solve_with_tree(lsm, oracle_mod):
+    """Mixed chart solve on a mesh that uses the treecode in its mixed sweeps:
+    the float-float sweeps still finish every node to the tolerance."""
+    w = synth.torus_c2(10, seed=22, nu=120, nv=32)
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    x, h, st, stats = mesh.solve_charts(order=8, tol=1e-10, precision=lsm.MIXED)
+    assert stats.n_failed == 0
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 6, 0)
+    sel = np.random.default_rng(3).choice(stats.n_nodes, 48, replace=False)
+    po, _ = oracle_mod.phi_grad(y, nw, sg, x[sel])
+    assert np.abs(po - 0.5).max() < 1e-10
