@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "ff"],
                     help="precision of the evaluation (ff: with --no-charts only)")
     ap.add_argument("--tol", type=float, default=1e-12)
-    ap.add_argument("--targets", type=int, default=1_000_000)
+    ap.add_argument("--targets", type=int, default=None,
+                    help="targets (torus: 1e6, icosphere: 2e7)")
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--small", action="store_true", help="small torus (quick check)")
     ap.add_argument("--workload", default="torus", choices=["torus", "ellipsoids", "serve", "icosphere"],
@@ -56,6 +57,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=5.0)
     ap.add_argument("--tmax", type=float, default=1e4)
+    ap.add_argument("--tree-degree", type=int, default=0, help="treecode degree (0: library default)")
+    ap.add_argument("--tree-theta", type=float, default=0.0, help="treecode opening parameter (0: default)")
     ap.add_argument("--no-charts", action="store_true", help="time the evaluation only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -74,9 +77,9 @@ def workload(args, rank: int = 0):
     import synth
     seed = rank_seed(rank)
     if args.small:
-        w = synth.torus_c2(n_targets=min(args.targets, 50_000), seed=seed, nu=60, nv=16)
+        w = synth.torus_c2(n_targets=min(args.targets or 50_000, 50_000), seed=seed, nu=60, nv=16)
     else:
-        w = synth.torus_c2(n_targets=args.targets, seed=seed)
+        w = synth.torus_c2(n_targets=args.targets or 1_000_000, seed=seed)
     return w
 
 
@@ -287,46 +290,87 @@ def bench_serve(args):
 
 def bench_icosphere(args):
     """Bumped icosphere, level 8 (1,310,720 triangles, Duffy 4x4 sources =
-    20,971,520 nodes): mixed-path Phi/grad-Phi on a 1e5-target subsample of
-    the targets within 3 sigma; error of the mixed path against the
-    float-float path on 1e4 of them and against the FP64 oracle on 64."""
+    20,971,520 nodes), 2e7 targets within 3 sigma: one mixed-path Phi/grad-Phi
+    evaluation per step (treecode far field).  Errors: the mixed path against
+    the float-float path (FP64-accurate, direct sum) on 1e5 targets and
+    against the FP64 oracle on a sample."""
     import torch
     import oracle
     import paper_1909_13356_gb300 as lsm
     import synth
-    w = synth.icosphere_c3(n_targets=100_000)
+    n = args.targets if args.targets else 20_000_000
+    w = synth.icosphere_c3(n_targets=n)
     m = w["mesh"]
-    ctx = lsm.Context(0)
+    ctx = lsm.Context(0, tree_degree=args.tree_degree, tree_theta=args.tree_theta)
     t0 = time.perf_counter()
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
+    torch.cuda.synchronize()
     t_up = time.perf_counter() - t0
     x = torch.from_numpy(w["targets"]).cuda()
-    for _ in range(max(1, args.warmup)):
-        mesh.eval_phi_grad(x[:2000], lsm.MIXED)
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    grad = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    # the autotuner picks the far field on windows of the targets (untimed);
+    # then the first call builds the chosen tree (node boxes, proxy weights)
+    t0 = time.perf_counter()
+    tune = mesh.autotune(x, err_budget=4e-8) if not (args.tree_degree or args.tree_theta) else None
+    t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mesh.eval_phi_grad(x[:4096], lsm.MIXED)
     torch.cuda.synchronize()
+    t_tree = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        mesh.eval_phi_grad(x, lsm.MIXED, phi=phi, grad=grad)
+    torch.cuda.synchronize()
+    ctx.read_stats(reset=True)
+    ctx.set_profiling(True)
+    l0 = ctx.launch_count
+    clk = ClockSampler(0)
+    clk.start()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(args.steps):
-        p32, g32 = mesh.eval_phi_grad(x, lsm.MIXED)
+        mesh.eval_phi_grad(x, lsm.MIXED, phi=phi, grad=grad)
     b.record()
     torch.cuda.synchronize()
+    clocks = clk.stop()
+    ctx.set_profiling(False)
+    stats = ctx.read_stats(reset=True)
+    launches = ctx.launch_count - l0
     ms = a.elapsed_time(b) / args.steps
-    pff, gff = mesh.eval_phi_grad(x[:10_000], lsm.FF)
-    err_ff = float((p32[:10_000] - pff).abs().max())
+    nref = min(n, 100_000)
+    pff, gff = mesh.eval_phi_grad(x[:nref], lsm.FF)
+    err_ff = float((phi[:nref] - pff).abs().max())
+    gerr_ff = float((grad[:nref] - gff).abs().max())
     y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, 4, 0)
-    xs = w["targets"][:64]
+    no = 256
+    xs = w["targets"][:no]
     po, _ = oracle.phi_grad(y, nw, sg, xs)
-    err_or = float(np.abs(p32[:64].cpu().numpy() - po).max())
-    err_ff_or = float(np.abs(pff[:64].cpu().numpy() - po).max())
+    err_or = float(np.abs(phi[:no].cpu().numpy() - po).max())
+    err_ff_or = float(np.abs(pff[:no].cpu().numpy() - po).max())
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    ms_k = stats["kind_ms"][0]
+    fl = stats["kind_pairs_far"][0] * FLOPS_FAR_PAIR + stats["kind_pairs_near"][0] * FLOPS_NEAR_PAIR
+    ach = fl / (ms_k / 1e3) / 1e12 if ms_k > 0 else None
     print(json.dumps({
-        "metric": "phi_grad_evals_per_s", "value": x.shape[0] / (ms / 1e3), "unit": "evals/s", "n_gpus": 1,
+        "metric": "phi_grad_evals_per_s", "value": n / (ms / 1e3), "unit": "evals/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
         "config": {"workload": w["name"], "triangles": m.m, "sources": mesh.info()["n_sources"],
-                   "targets": int(x.shape[0]), "precision": "mixed", "upload_s": t_up},
-        "pairs_per_s": x.shape[0] * mesh.info()["n_sources"] / (ms / 1e3),
-        "err_mixed_vs_ff_1e4": err_ff, "err_mixed_vs_oracle_64": err_or, "err_ff_vs_oracle_64": err_ff_or,
+                   "targets": n, "precision": "mixed",
+                   "far_field": ("autotuned" if tune else
+                                 f"treecode (degree {args.tree_degree or 'default'}, theta {args.tree_theta or 'default'})"),
+                   "upload_s": t_up, "tree_build_s": t_tree, "autotune_s": t_tune, "autotune": tune,
+                   "l2": "inputs (480 MB targets, 336 MB sources) larger than L2"},
+        "pairs_evaluated_per_step": (stats["kind_pairs_far"][0] + stats["kind_pairs_near"][0]) / args.steps,
+        "dense_equivalent_pairs_per_s": n * mesh.info()["n_sources"] / (ms / 1e3),
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": ach / fp32_peak if ach else None, "traffic": None, "kernel": "k_eval_mixed",
+                     "share_of_step": ms_k / (ms * args.steps)},
+        "clocks": clocks,
+        "err_mixed_vs_ff_1e5": err_ff, "grad_err_mixed_vs_ff_1e5": gerr_ff,
+        "err_mixed_vs_oracle_256": err_or, "err_ff_vs_oracle_256": err_ff_or,
     }))
 
 
@@ -363,11 +407,15 @@ def main():
 
     w = workload(args, rank)
     m = w["mesh"]
-    ctx = lsm.Context(local)
+    ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta)
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
     info = mesh.info()
     x_dev = torch.from_numpy(w["targets"]).to(dev)
     nt = x_dev.shape[0]
+    # far field of the mixed sweeps chosen by the autotuner (untimed)
+    tune = None
+    if prec == lsm.MIXED and not (args.tree_degree or args.tree_theta):
+        tune = mesh.autotune(x_dev, err_budget=4e-8)
     phi = torch.empty(nt, dtype=torch.float64, device=dev)
     grad = torch.empty((nt, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
@@ -483,7 +531,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": w["name"], "triangles": m.m, "sources": info["n_sources"],
                        "targets": nt, "chart_order": args.order, "chart_nodes": st.n_nodes if st else 0,
-                       "newton_tol": args.tol, "precision": args.precision,
+                       "newton_tol": args.tol, "precision": args.precision, "autotune": tune,
                        "parallelism": (f"{world} ranks, one independent torus (own seed) each"
                                        if world > 1 else "single GPU"),
                        "l2": "flushed (256 MB write) before each timed step"},

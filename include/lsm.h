@@ -105,7 +105,7 @@ typedef struct {
      * block through (tree_degree + 1)^3 Chebyshev proxy points carrying its
      * interpolated dipole weights. */
     int32_t tree_degree;      /* Chebyshev degree p per axis (8; 1..12) */
-    float tree_theta;         /* opening parameter (0.5; (0, 1)) */
+    float tree_theta;         /* opening parameter (0.4; (0, 1)) */
     int32_t tree_min_sources; /* meshes with at least this many source nodes
                                  use it (262,144); -1: never */
     int32_t reserved[5];
@@ -235,6 +235,36 @@ int lsm_eval_phi_grad(lsm_mesh* mesh, const double* x, int64_t n, double* phi, d
  */
 int lsm_eval_phi_grad_noalloc(lsm_mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
                               int precision, void* stream);
+
+/* Autotuner of the mixed path's far field (the paper has no counterpart:
+ * its FMM is run at a fixed precision, Sec. 4.4).  Chooses, for this mesh,
+ * between the direct tiled far field and the treecode, and the treecode's
+ * Chebyshev degree and opening parameter: the fastest candidate whose
+ * largest |Phi error| against the float-float path stays within err_budget.
+ *   x        [n][3] targets typical of the workload, host or device; up to
+ *            8 windows of 4,096 consecutive targets in Morton order (so with
+ *            the workload's density) are the sample
+ *   err_budget  bound on max |Phi_mixed - Phi_ff| over the sample (e.g.
+ *            5e-8, half the mixed path's 1e-7)
+ *   out      the choice and what was measured; may be NULL
+ * The choice is stored with the mesh and used by its later mixed
+ * evaluations and chart solves (it overrides the context's tree options).
+ * Cost: one float-float evaluation of the sample, and a tree build plus two
+ * mixed evaluations of it per candidate.  Synchronises `stream`.
+ * Errors: LSM_E_INVALID_ARG (n < 1, bad budget), LSM_E_OOM, LSM_E_CUDA. */
+typedef struct {
+    int32_t use_tree;         /* 0: the direct far field was chosen */
+    int32_t tree_degree;      /* chosen degree and opening parameter */
+    float tree_theta;
+    int32_t candidates;       /* candidates measured */
+    int64_t sample_targets;
+    double err_phi;           /* max |dPhi| of the choice on the sample */
+    double ms_sample;         /* its mixed-evaluation time on the sample */
+    double ms_direct;         /* the direct far field's time on the sample */
+    double err_direct;        /* and its error */
+} lsm_tune_result;
+int lsm_autotune(lsm_mesh* mesh, const double* x, int64_t n, double err_budget, lsm_tune_result* out,
+                 void* stream);
 
 /*
  * Chart nodes on Phi = 1/2 (Sec. 3.2): for each triangle j and each node

@@ -39,7 +39,7 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_read_stats", "lsm_mesh_upload", "lsm_mesh_free", "lsm_mesh_get_info", "lsm_eval_phi_grad",
            "lsm_eval_phi_grad_noalloc", "lsm_solve_charts", "lsm_batch_create", "lsm_batch_free",
            "lsm_batch_solve_charts", "lsm_server_create", "lsm_server_submit", "lsm_server_poll", "lsm_server_release",
-           "lsm_server_info", "lsm_server_destroy")
+           "lsm_server_info", "lsm_server_destroy", "lsm_autotune")
 
 
 class LsmError(RuntimeError):
@@ -93,6 +93,12 @@ class _Result(ctypes.Structure):
                 ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("stats", _Stats), ("x", ctypes.POINTER(ctypes.c_double)), ("h", ctypes.POINTER(ctypes.c_double)),
                 ("node_status", ctypes.POINTER(ctypes.c_int32))]
+
+
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("use_tree", ctypes.c_int32), ("tree_degree", ctypes.c_int32), ("tree_theta", ctypes.c_float),
+                ("candidates", ctypes.c_int32), ("sample_targets", ctypes.c_int64), ("err_phi", ctypes.c_double),
+                ("ms_sample", ctypes.c_double), ("ms_direct", ctypes.c_double), ("err_direct", ctypes.c_double)]
 
 
 class _ServerInfo(ctypes.Structure):
@@ -153,6 +159,7 @@ def load(build_if_needed: bool = True):
         L.lsm_batch_create.argtypes = [P, ctypes.POINTER(P), I32, P, ctypes.POINTER(P)]
         L.lsm_batch_free.argtypes = [P]
         L.lsm_batch_solve_charts.argtypes = [P, I32, D, I32, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
+        L.lsm_autotune.argtypes = [P, P, I64, D, ctypes.POINTER(_TuneResult), P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -297,6 +304,17 @@ class Mesh:
                                            _stream_handle(stream))
         self.ctx._check(rc)
         return phi, grad
+
+    def autotune(self, x, err_budget: float = 5e-8, stream=None) -> dict:
+        """Choose this mesh's mixed-path far field (direct, or the treecode's
+        degree and opening parameter) on a sample of the targets x [n, 3]
+        (lsm_autotune).  Returns the choice and the measured time and error."""
+        xs = _as(x, np.float64)
+        r = _TuneResult()
+        rc = self.ctx._L.lsm_autotune(self._h, _ptr(xs), int(xs.shape[0]), float(err_budget), ctypes.byref(r),
+                                      _stream_handle(stream))
+        self.ctx._check(rc)
+        return {k: getattr(r, k) for k, _ in _TuneResult._fields_}
 
     def solve_charts(self, order: int = 8, tol: float = 1e-12, max_iter: int = 20,
                      precision: int = FP64, device_out: bool = False, stream=None):

@@ -217,7 +217,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.mixed_switch = 1e-6;
     ctx->opt.mixed_accept = 1e-7;
     ctx->opt.tree_degree = 8;
-    ctx->opt.tree_theta = 0.5f;
+    ctx->opt.tree_theta = 0.4f;
     ctx->opt.tree_min_sources = 262144;
     if (opt) {
         if (opt->tree_degree < 0 || opt->tree_degree > kTreeMaxDegree || opt->tree_theta < 0.0f ||
@@ -505,6 +505,36 @@ int lsm_eval_phi_grad(lsm_mesh* mh, const double* x, int64_t n, double* phi, dou
         LSM_CUDA_TRY(ctx, cudaMemcpyAsync(grad, gd, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     if (!phi_dev || (grad && !grad_dev) || !is_device_ptr(x)) return check_flag(ctx, st);
     return LSM_OK;
+}
+
+int lsm_autotune(lsm_mesh* mh, const double* x, int64_t n, double err_budget, lsm_tune_result* out, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (n < 1 || n >= ((int64_t)1 << 31) || !x || !(err_budget > 0)) {
+        ctx->err = "autotune: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ni = (int)n;
+    Scratch s(st);
+    const double* xd;
+    int rc = to_device(ctx, s, x, 3 * (size_t)n, &xd, st);
+    if (rc) return rc;
+    uint32_t* perm;
+    double* T;
+    LSM_CUDA_TRY(ctx, s.get(&perm, n));
+    LSM_CUDA_TRY(ctx, s.get(&T, 3 * (size_t)n));
+    rc = morton_order_points(ctx, xd, 3, ni, perm, st);
+    if (rc) return rc;
+    k_gather_points<<<(ni + 255) / 256, 256, 0, st>>>(xd, perm, ni, T);
+    LSM_LAUNCHED(ctx);
+    Targets tg{T, n, ni};
+    rc = autotune_sorted(ctx, me, tg, err_budget, out, st);
+    if (rc) return rc;
+    return check_flag(ctx, st);
 }
 
 int lsm_solve_charts(lsm_mesh* mh, int order, double tol, int max_iter, int precision, double* x_out,

@@ -64,6 +64,11 @@ struct Tree;
 struct Mesh {
     Ctx* ctx = nullptr;
     Tree* tree = nullptr;        // treecode far field, built on first use
+    // far-field choice stored by the autotuner: -1 follow the context's
+    // options, 0 direct, 1 treecode with tune_degree / tune_theta
+    int tune_mode = -1;
+    int tune_degree = 0;
+    float tune_theta = 0.0f;
     int64_t nv = 0, m = 0, ns = 0, ntiles = 0;
     int nq = 0;
     lsm_quad rule{4, 0};
@@ -244,6 +249,9 @@ void tree_free(Tree* t);
 // summed list length.
 int tree_lists(Ctx* ctx, const Mesh* me, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
                int64_t* total, cudaStream_t st);
+
+// tune.cu: the autotuner on sorted SoA targets (lsm_autotune)
+int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tune_result* res, cudaStream_t st);
 
 // newton.cu
 int solve_charts_device(Ctx* ctx, Mesh* mesh, int n_gl, double tol, int max_iter,

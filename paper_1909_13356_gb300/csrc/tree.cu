@@ -400,7 +400,9 @@ __global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass
 
 bool tree_wanted(const Ctx* ctx, const Mesh* me)
 {
-    return ctx->opt.tree_min_sources >= 0 && me->ns >= ctx->opt.tree_min_sources && me->ntiles >= 8;
+    if (me->ntiles < 8) return false;
+    if (me->tune_mode >= 0) return me->tune_mode == 1;
+    return ctx->opt.tree_min_sources >= 0 && me->ns >= ctx->opt.tree_min_sources;
 }
 
 void tree_free(Tree* t)
@@ -415,9 +417,11 @@ void tree_free(Tree* t)
 
 int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st)
 {
-    const int degree = ctx->opt.tree_degree;
-    const float theta = ctx->opt.tree_theta;
+    const bool tuned = me->tune_mode == 1;
+    const int degree = tuned ? me->tune_degree : ctx->opt.tree_degree;
+    const float theta = tuned ? me->tune_theta : ctx->opt.tree_theta;
     if (me->tree && me->tree->degree == degree && me->tree->theta == theta) return LSM_OK;
+    if (me->tree) me->bytes -= me->tree->bytes;
     tree_free(me->tree);
     me->tree = nullptr;
     Tree* T = new (std::nothrow) Tree();

@@ -56,3 +56,17 @@ def test_create_without_device_fails_cleanly():
         pytest.skip("a GPU is present")
     with pytest.raises(lsm.LsmError):
         lsm.Context(0)
+
+
+def test_binding_declares_argument_types_for_every_export():
+    """Every entry point has ctypes argument types, so doubles and 64-bit
+    integers cross the boundary with the header's types."""
+    L = lsm.load()
+    for s in lsm.EXPORTS:
+        assert getattr(L, s).argtypes is not None, s
+
+
+def test_options_struct_matches_header_layout():
+    """The binding's lsm_options has the header's size (reserved words keep
+    the size fixed as fields are added)."""
+    assert ctypes.sizeof(lsm._Options) == 4 * 8 + 8 * 4
