@@ -108,7 +108,12 @@ typedef struct {
     float tree_theta;         /* opening parameter (0.4; (0, 1)) */
     int32_t tree_min_sources; /* meshes with at least this many source nodes
                                  use it (262,144); -1: never */
-    int32_t reserved[5];
+    /* The same for the float-float path (Phi to FP64 accuracy): proxies
+     * with float-float positions and weights computed in FP64. */
+    int32_t tree_ff_degree;      /* 13; 1..16 */
+    float tree_ff_theta;         /* 0.4 */
+    int32_t tree_ff_min_sources; /* 262,144; -1: never */
+    int32_t reserved[2];
 } lsm_options;
 
 /* Statistics of one chart solve. */

@@ -219,9 +219,14 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.tree_degree = 8;
     ctx->opt.tree_theta = 0.4f;
     ctx->opt.tree_min_sources = 262144;
+    ctx->opt.tree_ff_degree = 13;
+    ctx->opt.tree_ff_theta = 0.4f;
+    ctx->opt.tree_ff_min_sources = 262144;
     if (opt) {
-        if (opt->tree_degree < 0 || opt->tree_degree > kTreeMaxDegree || opt->tree_theta < 0.0f ||
-            opt->tree_theta >= 1.0f || opt->tree_min_sources < -1) {
+        if (opt->tree_degree < 0 || opt->tree_degree > 12 || opt->tree_theta < 0.0f ||
+            opt->tree_theta >= 1.0f || opt->tree_min_sources < -1 || opt->tree_ff_degree < 0 ||
+            opt->tree_ff_degree > kTreeMaxDegree || opt->tree_ff_theta < 0.0f || opt->tree_ff_theta >= 1.0f ||
+            opt->tree_ff_min_sources < -1) {
             delete c;
             return LSM_E_INVALID_ARG;
         }
@@ -232,6 +237,9 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
         if (opt->tree_degree > 0) ctx->opt.tree_degree = opt->tree_degree;
         if (opt->tree_theta > 0.0f) ctx->opt.tree_theta = opt->tree_theta;
         if (opt->tree_min_sources != 0) ctx->opt.tree_min_sources = opt->tree_min_sources;
+        if (opt->tree_ff_degree > 0) ctx->opt.tree_ff_degree = opt->tree_ff_degree;
+        if (opt->tree_ff_theta > 0.0f) ctx->opt.tree_ff_theta = opt->tree_ff_theta;
+        if (opt->tree_ff_min_sources != 0) ctx->opt.tree_ff_min_sources = opt->tree_ff_min_sources;
     }
     DeviceGuard g(device);
     int rc = LSM_OK;
@@ -439,6 +447,8 @@ int lsm_mesh_free(lsm_mesh* mh)
     DeviceGuard g(me->ctx ? me->ctx->device : 0);
     tree_free(me->tree);
     me->tree = nullptr;
+    tree_free(me->tree_ff);
+    me->tree_ff = nullptr;
     void* ps[] = {me->verts, me->tris, me->tri_sigma, me->tri_n, me->vpn, me->s64_pos, me->s64_nw,
                   me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, me->tile_lo, me->tile_hi, me->tile_chi, me->tile_clo};
     for (void* p : ps)

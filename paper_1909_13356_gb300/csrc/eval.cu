@@ -286,6 +286,8 @@ struct EvalArgs {
     const int2* blist = nullptr;
     const float4* ppos = nullptr;
     const float4* pnw = nullptr;
+    const float4* plo = nullptr;     // float-float kernel: proxy remainders
+    const float4* pnwlo = nullptr;
 };
 
 // Block-wide sums of the pair counts, added once per CTA.
@@ -891,6 +893,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         tend = w.x + w.y;
         t0 = w.z;
         t1 = w.w;
+    } else if (A.list) {
+        // this split's part of the block's interaction list (modes 0 and 1)
+        base = blockIdx.x * kEvalThreads;
+        tend = A.nt;
+        const int2 r = A.blist[blockIdx.x];
+        const int per = (r.y + (int)gridDim.y - 1) / (int)gridDim.y;
+        t0 = min(r.x + (int)blockIdx.y * per, r.x + r.y);
+        t1 = min(r.x + r.y, t0 + per);
     } else {
         base = blockIdx.x * kEvalThreads;
         tend = A.nt;
@@ -946,7 +956,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             nlist = t1 - t0;
         }
     }
-    auto tile_at = [&](int k) { return mode == 2 ? s_near[k] : t0 + k; };
+    auto tile_at = [&](int k) { return mode == 2 ? s_near[k] : (A.list ? A.list[t0 + k] : t0 + k); };
 
     float ph = 0.0f, pl = 0.0f;                                     // near Phi, float-float
     float gh[3] = {0.0f, 0.0f, 0.0f}, gl[3] = {0.0f, 0.0f, 0.0f};   // near grad, compensated FP32
@@ -963,11 +973,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         const int cnt = (int)A.thi[t].w;
         const uint32_t by = (uint32_t)cnt * 16u;
         mbar_expect_tx(&bar[b], 4u * by);
-        const size_t o = (size_t)t * kTile;
-        bulk_g2s(sh[b] + 0 * kTile * 16, spos + o, by, &bar[b]);
-        bulk_g2s(sh[b] + 1 * kTile * 16, snw + o, by, &bar[b]);
-        bulk_g2s(sh[b] + 2 * kTile * 16, slo + o, by, &bar[b]);
-        bulk_g2s(sh[b] + 3 * kTile * 16, snwlo + o, by, &bar[b]);
+        // proxy tiles (list mode, ids >= ntiles) come from the tree's arrays
+        const bool proxy = t >= A.ntiles;
+        const size_t o = (size_t)(proxy ? t - A.ntiles : t) * kTile;
+        bulk_g2s(sh[b] + 0 * kTile * 16, (proxy ? A.ppos : spos) + o, by, &bar[b]);
+        bulk_g2s(sh[b] + 1 * kTile * 16, (proxy ? A.pnw : snw) + o, by, &bar[b]);
+        bulk_g2s(sh[b] + 2 * kTile * 16, (proxy ? A.plo : slo) + o, by, &bar[b]);
+        bulk_g2s(sh[b] + 3 * kTile * 16, (proxy ? A.pnwlo : snwlo) + o, by, &bar[b]);
     };
     if (tid == 0 && nlist > 0) issue(tile_at(0), 0);
 
@@ -985,7 +997,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             break;
         }
         const int cnt = (int)A.thi[t].w;
-        const bool far = tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+        const bool far = t >= A.ntiles || tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
         if (far) pairs_far += valid ? cnt : 0;
         else pairs_near += valid ? cnt : 0;
         const float4 ch = A.tchi[t], cl = A.tclo[t];
@@ -1229,16 +1241,19 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     // mixed path on a large mesh: the treecode's interaction lists
     int* list = nullptr;
     int2* blist = nullptr;
-    const bool use_tree = mixed && tree_wanted(ctx, me);
+    // float-float: every mode but the near-only one (which lists near tiles itself)
+    const bool use_tree = mixed ? tree_wanted(ctx, me, false)
+                                : (ff && !(inc && inc->mode == 2) && tree_wanted(ctx, me, true));
     if (use_tree) {
-        int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st);
+        int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff);
         if (rc != LSM_OK) return rc;
         int64_t total = 0;
-        rc = tree_lists(ctx, me, t, tpb, s, &list, &blist, &total, st);
+        rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, s, &list, &blist, &total, st);
         if (rc != LSM_OK) return rc;
         const int64_t avg = total / nblk;
         nsplit = 1;
         if (nblk < want) nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((want + nblk - 1) / nblk, avg / 4));
+        if (ff && inc && inc->mode != 0) nsplit = 1;
     }
     double* part = res;
     if (nsplit > 1) LSM_CUDA_TRY(ctx, s.get(&part, (size_t)nsplit * 4 * t.n));
@@ -1269,7 +1284,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         A.x_old = inc->x_old;
     }
     if (use_tree) {
-        const Tree* T = me->tree;
+        const Tree* T = ff ? me->tree_ff : me->tree;
         A.tlo = T->tile_lo;
         A.thi = T->tile_hi;
         A.tchi = T->tile_chi;
@@ -1278,6 +1293,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         A.blist = blist;
         A.ppos = T->p_pos;
         A.pnw = T->p_nw;
+        A.plo = T->p_lo;
+        A.pnwlo = T->p_nwlo;
     }
     dim3 grid(nblk, nsplit);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

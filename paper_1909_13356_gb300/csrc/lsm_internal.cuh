@@ -24,7 +24,7 @@ constexpr int kTile = 128;
 // Targets per thread block row of the pair kernels (threads * targets/thread).
 constexpr int kEvalThreads = 128;
 // Largest Chebyshev degree of the treecode's proxy grids.
-constexpr int kTreeMaxDegree = 12;
+constexpr int kTreeMaxDegree = 16;
 
 // Last-error message, safe to set from several host threads.
 class ErrorText {
@@ -63,7 +63,8 @@ struct Tree;
 
 struct Mesh {
     Ctx* ctx = nullptr;
-    Tree* tree = nullptr;        // treecode far field, built on first use
+    Tree* tree = nullptr;        // treecode far field of the mixed path, built on first use
+    Tree* tree_ff = nullptr;     // and of the float-float path
     // far-field choice stored by the autotuner: -1 follow the context's
     // options, 0 direct, 1 treecode with tune_degree / tune_theta
     int tune_mode = -1;
@@ -228,6 +229,7 @@ int eval_noalloc(Ctx* ctx, const Mesh* mesh, const double* x, int64_t n, double*
 // nodes large enough to profit.  Tile ids below ntiles are source tiles,
 // the rest proxy tiles; tile_* cover both.
 struct Tree {
+    bool ff = false;                        // float-float proxies (FP64 weights split in two floats)
     int degree = 0;
     float theta = 0.0f;
     int top = 0;                            // level of the root (level 0 = tiles)
@@ -238,16 +240,17 @@ struct Tree {
     float4* node_hi = nullptr;              // box, rounded up
     int4* node_info = nullptr;              // first tile, tile count, first proxy tile or -1, proxy tiles
     float4 *p_pos = nullptr, *p_nw = nullptr;   // proxies, kTile per proxy tile
+    float4 *p_lo = nullptr, *p_nwlo = nullptr;  // float-float trees: remainders of both
     float4 *tile_lo = nullptr, *tile_hi = nullptr, *tile_chi = nullptr, *tile_clo = nullptr;
     size_t bytes = 0;
 };
-bool tree_wanted(const Ctx* ctx, const Mesh* me);
-int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st);
+bool tree_wanted(const Ctx* ctx, const Mesh* me, bool ff);
+int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff);
 void tree_free(Tree* t);
 // Interaction lists of sorted targets in blocks of tpb: for block b, the
 // tile ids list[blist[b].x .. + blist[b].y) in tree order; *total = the
 // summed list length.
-int tree_lists(Ctx* ctx, const Mesh* me, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
+int tree_lists(Ctx* ctx, const Tree* tree, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
                int64_t* total, cudaStream_t st);
 
 // tune.cu: the autotuner on sorted SoA targets (lsm_autotune)

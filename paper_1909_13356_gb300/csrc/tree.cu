@@ -36,8 +36,11 @@ namespace {
 
 constexpr int kP2MThreads = 256;
 constexpr int kP2MChunkTiles = 256;      // source tiles per P2M work item
-constexpr int kMaxN = kTreeMaxDegree + 1; // grid points per axis at most
+constexpr int kMaxDeg32 = 12;             // FP32 proxies (mixed path): degree at most
+constexpr int kMaxN = kMaxDeg32 + 1;      // grid points per axis at most
 constexpr int kLStride = 16;              // floats per (axis, source) row of basis values
+constexpr int kMaxN64 = kTreeMaxDegree + 1;
+constexpr int kP2M64Src = 64;             // sources staged per pass of the FP64 P2M
 constexpr int kWalkThreads = 128;
 constexpr int kMaxLevels = 32;
 
@@ -110,6 +113,8 @@ struct P2MArgs {
     int degree;
     float4* p_pos;
     float4* p_nw;
+    float4* p_lo;             // FP64 kernel: remainders of the positions
+    float4* p_nwlo;           // and of the weights
     double* partial;          // [proxies][3] per chunk
 };
 
@@ -267,10 +272,119 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(P2MArgs A)
     }
 }
 
+// Chebyshev points of the second kind in FP64 (the float-float proxies).
+__device__ __forceinline__ double cheb_point64(int k, int degree) { return cospi((double)k / (double)degree); }
+
+// FP64 P2M for the float-float proxies: thread k of grid row y owns proxy
+// 256 y + k of the item's node; its weight is summed in FP64 over the item's
+// tiles, 64 sources at a time (their basis values staged in shared memory).
+__global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
+{
+    __shared__ double sL[3][kP2M64Src][kMaxN64];
+    __shared__ double sN[kP2M64Src][3];
+    const int4 it = A.items[blockIdx.x];
+    const int node = it.x;
+    const float4 lo = A.nlo[node], hi = A.nhi[node];
+    const int4 info = A.ninfo[node];
+    const NodeGrid G = node_grid(lo, hi, A.degree);
+    const int n1 = G.n[1], n2 = G.n[2];
+    const int nprox = G.n[0] * n1 * n2;
+    if ((int)blockIdx.y * kP2MThreads >= nprox) return;   // whole CTA, before any barrier
+    const int tid = threadIdx.x;
+    const int k = blockIdx.y * kP2MThreads + tid;
+    const bool active = k < nprox;
+    const int k0 = active ? k / (n1 * n2) : 0;
+    const int k1 = active ? (k / n2) % n1 : 0;
+    const int k2 = active ? k % n2 : 0;
+    double q[3] = {0.0, 0.0, 0.0};
+    for (int t = it.y; t < it.z; t++) {
+        for (int half = 0; half < kTile / kP2M64Src; half++) {
+            if (tid < kP2M64Src) {
+                const int64_t i = (int64_t)t * kTile + half * kP2M64Src + tid;
+                if (i < A.ns) {
+                    const double4_32a p = A.pos[i];
+                    const double4_32a w = A.nw[i];
+                    const double y[3] = {p.x, p.y, p.z};
+                    for (int a = 0; a < 3; a++) {
+                        double* L = sL[a][tid];
+                        const int na = G.n[a];
+                        if (na == 1) {
+                            L[0] = 1.0;
+                            continue;
+                        }
+                        const double xi = (y[a] - G.c[a]) / G.h[a];
+                        int hit = -1;
+                        double sum = 0.0;
+                        for (int m = 0; m < na; m++) {
+                            const double d = xi - cheb_point64(m, na - 1);
+                            if (d == 0.0) hit = m;
+                            double wm = (m & 1) ? -1.0 : 1.0;
+                            if (m == 0 || m == na - 1) wm *= 0.5;
+                            const double tm = d == 0.0 ? 0.0 : wm / d;
+                            L[m] = tm;
+                            sum += tm;
+                        }
+                        if (hit >= 0) {
+                            for (int m = 0; m < na; m++) L[m] = m == hit ? 1.0 : 0.0;
+                        } else {
+                            const double inv = 1.0 / sum;
+                            for (int m = 0; m < na; m++) L[m] *= inv;
+                        }
+                    }
+                    sN[tid][0] = w.x;
+                    sN[tid][1] = w.y;
+                    sN[tid][2] = w.z;
+                } else {
+                    for (int a = 0; a < 3; a++)
+                        for (int m = 0; m < G.n[a]; m++) sL[a][tid][m] = 0.0;
+                    sN[tid][0] = sN[tid][1] = sN[tid][2] = 0.0;
+                }
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll 4
+                for (int s = 0; s < kP2M64Src; s++) {
+                    const double l = sL[0][s][k0] * sL[1][s][k1] * sL[2][s][k2];
+                    q[0] = fma(l, sN[s][0], q[0]);
+                    q[1] = fma(l, sN[s][1], q[1]);
+                    q[2] = fma(l, sN[s][2], q[2]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (!active) return;
+    const int64_t dst = (int64_t)info.z * kTile + k;
+    if (it.w < 0) {
+        const float h0 = (float)q[0], h1 = (float)q[1], h2 = (float)q[2];
+        A.p_nw[dst] = make_float4(h0, h1, h2, 0.0f);
+        A.p_nwlo[dst] = make_float4((float)(q[0] - (double)h0), (float)(q[1] - (double)h1),
+                                    (float)(q[2] - (double)h2), 0.0f);
+    } else {
+        double* o = A.partial + ((int64_t)it.w + k) * 3;
+        o[0] = q[0];
+        o[1] = q[1];
+        o[2] = q[2];
+    }
+    if (it.y == info.x) {
+        const double r[3] = {G.n[0] > 1 ? G.h[0] * cheb_point64(k0, G.n[0] - 1) : 0.0,
+                             n1 > 1 ? G.h[1] * cheb_point64(k1, n1 - 1) : 0.0,
+                             n2 > 1 ? G.h[2] * cheb_point64(k2, n2 - 1) : 0.0};
+        float rh[3], rl[3];
+        for (int a = 0; a < 3; a++) {
+            rh[a] = (float)r[a];
+            rl[a] = (float)(r[a] - (double)rh[a]);
+        }
+        A.p_pos[dst] = make_float4(rh[0], rh[1], rh[2], 0.0f);
+        A.p_lo[dst] = make_float4(rl[0], rl[1], rl[2], 0.0f);
+    }
+}
+
 // Nodes whose weights were summed in several chunks: add the chunks in order.
 // r = node, first partial offset, chunks, proxies.
 __global__ void k_p2m_reduce(const int4* __restrict__ red, const int4* __restrict__ ninfo,
-                             const double* __restrict__ partial, float4* __restrict__ p_nw)
+                             const double* __restrict__ partial, float4* __restrict__ p_nw,
+                             float4* __restrict__ p_nwlo)
 {
     const int4 r = red[blockIdx.x];
     const int64_t base = (int64_t)ninfo[r.x].z * kTile;
@@ -282,7 +396,11 @@ __global__ void k_p2m_reduce(const int4* __restrict__ red, const int4* __restric
             q[1] += src[1];
             q[2] += src[2];
         }
-        p_nw[base + k] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.0f);
+        const float h0 = (float)q[0], h1 = (float)q[1], h2 = (float)q[2];
+        p_nw[base + k] = make_float4(h0, h1, h2, 0.0f);
+        if (p_nwlo)
+            p_nwlo[base + k] = make_float4((float)(q[0] - (double)h0), (float)(q[1] - (double)h1),
+                                           (float)(q[2] - (double)h2), 0.0f);
     }
 }
 
@@ -398,9 +516,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass
 
 }  // namespace
 
-bool tree_wanted(const Ctx* ctx, const Mesh* me)
+bool tree_wanted(const Ctx* ctx, const Mesh* me, bool ff)
 {
     if (me->ntiles < 8) return false;
+    if (ff) return ctx->opt.tree_ff_min_sources >= 0 && me->ns >= ctx->opt.tree_ff_min_sources;
     if (me->tune_mode >= 0) return me->tune_mode == 1;
     return ctx->opt.tree_min_sources >= 0 && me->ns >= ctx->opt.tree_min_sources;
 }
@@ -408,24 +527,30 @@ bool tree_wanted(const Ctx* ctx, const Mesh* me)
 void tree_free(Tree* t)
 {
     if (!t) return;
-    void* ps[] = {t->node_lo, t->node_hi, t->node_info, t->p_pos, t->p_nw, t->tile_lo, t->tile_hi, t->tile_chi,
-                  t->tile_clo};
+    void* ps[] = {t->node_lo, t->node_hi, t->node_info, t->p_pos, t->p_nw, t->p_lo, t->p_nwlo, t->tile_lo,
+                  t->tile_hi, t->tile_chi, t->tile_clo};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete t;
 }
 
-int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st)
+int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
 {
-    const bool tuned = me->tune_mode == 1;
-    const int degree = tuned ? me->tune_degree : ctx->opt.tree_degree;
-    const float theta = tuned ? me->tune_theta : ctx->opt.tree_theta;
-    if (me->tree && me->tree->degree == degree && me->tree->theta == theta) return LSM_OK;
-    if (me->tree) me->bytes -= me->tree->bytes;
-    tree_free(me->tree);
-    me->tree = nullptr;
+    const bool tuned = !ff && me->tune_mode == 1;
+    const int degree = ff ? ctx->opt.tree_ff_degree : (tuned ? me->tune_degree : ctx->opt.tree_degree);
+    const float theta = ff ? ctx->opt.tree_ff_theta : (tuned ? me->tune_theta : ctx->opt.tree_theta);
+    Tree*& slot = ff ? me->tree_ff : me->tree;
+    if (slot && slot->degree == degree && slot->theta == theta) return LSM_OK;
+    if (!ff && degree > kMaxDeg32) {
+        ctx->err = "tree: the mixed path's degree is at most 12";
+        return LSM_E_INVALID_ARG;
+    }
+    if (slot) me->bytes -= slot->bytes;
+    tree_free(slot);
+    slot = nullptr;
     Tree* T = new (std::nothrow) Tree();
     if (!T) return LSM_E_OOM;
+    T->ff = ff;
     auto fail = [&](int rc) {
         tree_free(T);
         return rc;
@@ -533,7 +658,9 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st)
     const int64_t nall = me->ntiles + nptiles;
     if (!alloc(&T->tile_lo, nall) || !alloc(&T->tile_hi, nall) || !alloc(&T->tile_chi, nall) ||
         !alloc(&T->tile_clo, nall) || !alloc(&T->p_pos, std::max<int64_t>(1, nptiles) * kTile) ||
-        !alloc(&T->p_nw, std::max<int64_t>(1, nptiles) * kTile)) {
+        !alloc(&T->p_nw, std::max<int64_t>(1, nptiles) * kTile) ||
+        (ff && (!alloc(&T->p_lo, std::max<int64_t>(1, nptiles) * kTile) ||
+                !alloc(&T->p_nwlo, std::max<int64_t>(1, nptiles) * kTile)))) {
         cudaGetLastError();
         ctx->err = "tree: out of device memory";
         return fail(LSM_E_OOM);
@@ -582,12 +709,24 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st)
         P.degree = degree;
         P.p_pos = T->p_pos;
         P.p_nw = T->p_nw;
+        P.p_lo = T->p_lo;
+        P.p_nwlo = T->p_nwlo;
         P.partial = d_part;
-        k_p2m<<<(unsigned)items.size(), kP2MThreads, 0, st>>>(P);
+        if (ff) {
+            int64_t nmax = 0;
+            for (const int4& it : items) {
+                const NodeGrid G = node_grid(hlo[it.x], hhi[it.x], degree);
+                nmax = std::max<int64_t>(nmax, (int64_t)G.n[0] * G.n[1] * G.n[2]);
+            }
+            const dim3 grid((unsigned)items.size(), (unsigned)((nmax + kP2MThreads - 1) / kP2MThreads));
+            k_p2m64<<<grid, kP2MThreads, 0, st>>>(P);
+        } else {
+            k_p2m<<<(unsigned)items.size(), kP2MThreads, 0, st>>>(P);
+        }
         if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
         ctx->launches++;
         if (!reds.empty()) {
-            k_p2m_reduce<<<(unsigned)reds.size(), 256, 0, st>>>(d_reds, T->node_info, d_part, T->p_nw);
+            k_p2m_reduce<<<(unsigned)reds.size(), 256, 0, st>>>(d_reds, T->node_info, d_part, T->p_nw, T->p_nwlo);
             if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
             ctx->launches++;
         }
@@ -600,15 +739,14 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st)
         ctx->err = "tree: build failed";
         return fail(LSM_E_CUDA);
     }
-    me->tree = T;
+    slot = T;
     me->bytes += T->bytes;
     return LSM_OK;
 }
 
-int tree_lists(Ctx* ctx, const Mesh* me, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
+int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
                int64_t* total_out, cudaStream_t st)
 {
-    const Tree* T = me->tree;
     const int nblk = (t.n + tpb - 1) / tpb;
     float4 *blo = nullptr, *bhi = nullptr;
     uint32_t* cnt = nullptr;
@@ -629,7 +767,9 @@ int tree_lists(Ctx* ctx, const Mesh* me, const Targets& t, int tpb, Scratch& s, 
     W.top = T->top;
     W.ntiles = T->ntiles;
     W.theta2 = T->theta * T->theta;
-    W.cut2 = (float)(ctx->opt.cutoff_mixed * ctx->opt.cutoff_mixed);
+    // the near radius of the pair kernel that evaluates the lists
+    const double cut = T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed;
+    W.cut2 = (float)(cut * cut);
     W.off = cnt;
     W.cnt = cnt;
     W.list = nullptr;

@@ -143,7 +143,7 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
     me->tune_degree = c.degree;
     me->tune_theta = c.theta;
     if (c.mode == 1) {
-        rc = tree_ensure(ctx, me, st);
+        rc = tree_ensure(ctx, me, st, false);
         if (rc != LSM_OK) return rc;
     }
     if (res) {

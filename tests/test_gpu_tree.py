@@ -148,18 +148,19 @@ def test_ragged_target_counts_tree(lsm, torus_case):
 
 
 def test_chart_solve_with_tree(lsm, oracle_mod):
-    """Mixed chart solve on a mesh that uses the treecode in its mixed sweeps:
-    the float-float sweeps still finish every node to the tolerance."""
+    """Mixed chart solve on a mesh that uses the treecodes in its mixed sweeps
+    and in its float-float record sweep: every node to |Phi - 1/2| < 1e-12,
+    re-evaluated by the oracle."""
     w = synth.torus_c2(10, seed=22, nu=120, nv=32)
     m = w["mesh"]
     ctx = lsm.Context(0)
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
-    x, h, st, stats = mesh.solve_charts(order=8, tol=1e-10, precision=lsm.MIXED)
+    x, h, st, stats = mesh.solve_charts(order=8, tol=1e-12, precision=lsm.MIXED)
     assert stats.n_failed == 0
     y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 6, 0)
     sel = np.random.default_rng(3).choice(stats.n_nodes, 48, replace=False)
     po, _ = oracle_mod.phi_grad(y, nw, sg, x[sel])
-    assert np.abs(po - 0.5).max() < 1e-10
+    assert np.abs(po - 0.5).max() < 1e-12
 
 
 def test_autotune_choice_within_budget(lsm, oracle_mod):
@@ -193,3 +194,31 @@ def test_autotune_unreachable_budget(lsm, torus_case):
     assert r["err_phi"] > 1e-15
     phi, _ = _eval(lsm, ctx, mesh, w["targets"])
     assert np.abs(phi - torus_case["phi"]).max() <= TOL32
+
+
+def test_ff_tree_matches_oracle(lsm, torus_case):
+    """Float-float path with its treecode (degree 13, theta 0.4, FP64 proxy
+    weights): Phi to the FP64 bar."""
+    w = torus_case["w"]
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    phi, grad = _eval(lsm, ctx, mesh, w["targets"], lsm.FF)
+    assert np.abs(phi - torus_case["phi"]).max() <= 1e-12
+    assert np.abs(grad - torus_case["grad"]).max() <= TOL32 / m.sigma.min()
+
+
+def test_ff_tree_dense_against_direct(lsm):
+    w = synth.torus_c2(100_000, seed=21, nu=120, nv=32)
+    m = w["mesh"]
+    out = {}
+    for name, kw in (("tree", {}), ("direct", {"tree_ff_min_sources": -1})):
+        ctx = lsm.Context(0, **kw)
+        mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+        ctx.read_stats(reset=True)
+        out[name] = _eval(lsm, ctx, mesh, w["targets"], lsm.FF) + (ctx.read_stats(reset=True),)
+    (pt, gt, st_t), (pd, gd, st_d) = out["tree"], out["direct"]
+    assert np.abs(pt - pd).max() <= 5e-13
+    assert np.abs(gt - gd).max() <= TOL32 / m.sigma.min()
+    assert st_t["pairs_near"] == st_d["pairs_near"]
+    assert st_t["pairs_far"] < st_d["pairs_far"]
