@@ -51,6 +51,8 @@ def parse():
                     help="targets (torus: 1e6, icosphere: 2e7)")
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--small", action="store_true", help="small torus (quick check)")
+    ap.add_argument("--cells", default=None,
+                    help="torus cells NUxNV (default 240x64); e.g. 120x32 for a profiling case")
     ap.add_argument("--workload", default="torus", choices=["torus", "ellipsoids", "serve", "icosphere"],
                     help="torus: the default line; ellipsoids: 512 meshes in one batched, graph-captured "
                          "solve; serve: a Poisson request stream through the server")
@@ -78,6 +80,9 @@ def workload(args, rank: int = 0):
     seed = rank_seed(rank)
     if args.small:
         w = synth.torus_c2(n_targets=min(args.targets or 50_000, 50_000), seed=seed, nu=60, nv=16)
+    elif getattr(args, "cells", None):
+        nu, nv = (int(v) for v in args.cells.lower().split("x"))
+        w = synth.torus_c2(n_targets=args.targets or 1_000_000, seed=seed, nu=nu, nv=nv)
     else:
         w = synth.torus_c2(n_targets=args.targets or 1_000_000, seed=seed)
     return w

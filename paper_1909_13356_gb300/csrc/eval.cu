@@ -284,6 +284,7 @@ struct EvalArgs {
     // cover source and proxy tiles.
     const int* list = nullptr;
     const int2* blist = nullptr;
+    const int* border = nullptr;     // list mode: block of each CTA row (longest lists first)
     const float4* ppos = nullptr;
     const float4* pnw = nullptr;
     const float4* plo = nullptr;     // float-float kernel: proxy remainders
@@ -445,9 +446,10 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         t1 = w.w;
     } else if (A.list) {
         // this split's part of the block's interaction list
-        base = blockIdx.x * (kEvalThreads * TPT);
+        const int blk = A.border[blockIdx.x];
+        base = blk * (kEvalThreads * TPT);
         tend = A.nt;
-        const int2 r = A.blist[blockIdx.x];
+        const int2 r = A.blist[blk];
         const int per = (r.y + (int)gridDim.y - 1) / (int)gridDim.y;
         t0 = min(r.x + (int)blockIdx.y * per, r.x + r.y);
         t1 = min(r.x + r.y, t0 + per);
@@ -895,9 +897,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         t1 = w.w;
     } else if (A.list) {
         // this split's part of the block's interaction list (modes 0 and 1)
-        base = blockIdx.x * kEvalThreads;
+        const int blk = A.border[blockIdx.x];
+        base = blk * kEvalThreads;
         tend = A.nt;
-        const int2 r = A.blist[blockIdx.x];
+        const int2 r = A.blist[blk];
         const int per = (r.y + (int)gridDim.y - 1) / (int)gridDim.y;
         t0 = min(r.x + (int)blockIdx.y * per, r.x + r.y);
         t1 = min(r.x + r.y, t0 + per);
@@ -1241,6 +1244,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     // mixed path on a large mesh: the treecode's interaction lists
     int* list = nullptr;
     int2* blist = nullptr;
+    int* border = nullptr;
     // float-float: every mode but the near-only one (which lists near tiles itself)
     const bool use_tree = mixed ? tree_wanted(ctx, me, false)
                                 : (ff && !(inc && inc->mode == 2) && tree_wanted(ctx, me, true));
@@ -1248,7 +1252,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff);
         if (rc != LSM_OK) return rc;
         int64_t total = 0;
-        rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, s, &list, &blist, &total, st);
+        rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, s, &list, &blist, &border, &total, st);
         if (rc != LSM_OK) return rc;
         const int64_t avg = total / nblk;
         nsplit = 1;
@@ -1291,6 +1295,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         A.tclo = T->tile_clo;
         A.list = list;
         A.blist = blist;
+        A.border = border;
         A.ppos = T->p_pos;
         A.pnw = T->p_nw;
         A.plo = T->p_lo;

@@ -248,10 +248,11 @@ bool tree_wanted(const Ctx* ctx, const Mesh* me, bool ff);
 int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff);
 void tree_free(Tree* t);
 // Interaction lists of sorted targets in blocks of tpb: for block b, the
-// tile ids list[blist[b].x .. + blist[b].y) in tree order; *total = the
-// summed list length.
+// tile ids list[blist[b].x .. + blist[b].y) in tree order; order = the
+// blocks by decreasing list length (the launch order); *total = the summed
+// list length.
 int tree_lists(Ctx* ctx, const Tree* tree, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
-               int64_t* total, cudaStream_t st);
+               int** order, int64_t* total, cudaStream_t st);
 
 // tune.cu: the autotuner on sorted SoA targets (lsm_autotune)
 int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tune_result* res, cudaStream_t st);

@@ -514,6 +514,17 @@ __global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass
         A.cnt[b] = n;
 }
 
+// Sort keys that order blocks by decreasing list length (longest first),
+// block id as the value.
+__global__ void k_order_keys(const uint32_t* __restrict__ cnt, int n, uint32_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    keys[b] = 0xFFFFFFu - min(cnt[b], 0xFFFFFFu);
+    vals[b] = (uint32_t)b;
+}
+
 }  // namespace
 
 bool tree_wanted(const Ctx* ctx, const Mesh* me, bool ff)
@@ -745,7 +756,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
 }
 
 int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
-               int64_t* total_out, cudaStream_t st)
+               int** order, int64_t* total_out, cudaStream_t st)
 {
     const int nblk = (t.n + tpb - 1) / tpb;
     float4 *blo = nullptr, *bhi = nullptr;
@@ -776,6 +787,15 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, Scratch& s, i
     W.blist = *blist;
     k_tree_walk<<<blocks_of(nblk, kWalkThreads), kWalkThreads, 0, st>>>(W, 0);
     LSM_LAUNCHED(ctx);
+    // launch order: longest lists first, so that the last wave is short
+    uint32_t* keys = nullptr;
+    LSM_CUDA_TRY(ctx, s.get(&keys, nblk));
+    LSM_CUDA_TRY(ctx, s.get(order, nblk));
+    uint32_t* vals = reinterpret_cast<uint32_t*>(*order);
+    k_order_keys<<<blocks_of(nblk, 256), 256, 0, st>>>(cnt, nblk, keys, vals);
+    LSM_LAUNCHED(ctx);
+    int rc0 = radix_sort_pairs(ctx, keys, vals, nblk, 24, st);
+    if (rc0 != LSM_OK) return rc0;
     uint32_t* total = cnt + nblk;
     int rc = scan_exclusive(ctx, cnt, nblk, total, st);
     if (rc != LSM_OK) return rc;
