@@ -62,6 +62,9 @@ def _load():
             lib.or_chart_nodes.argtypes = [P, I64, P, P, P, ctypes.c_int, P, P, P, P, P]
             lib.or_solve_charts.argtypes = [I64, P, P, P, I64, P, P, P, ctypes.c_double,
                                             ctypes.c_int, P, P, P, P, P, ctypes.c_int]
+            lib.or_chart_frames.argtypes = [P, I64, P, P, ctypes.c_int, P, P, P, P, P, P, P]
+            lib.or_gauss_flux.argtypes = [I64, ctypes.c_int, P, P, P, P, P]
+            lib.or_gauss_flux.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -172,3 +175,34 @@ def solve_charts(y, nw, sig, x0, hdir, sloc, tol: float = 1e-12, max_iter: int =
                             float(tol), int(max_iter), _p(xo), _p(ho), _p(st), _p(it), _p(dh),
                             nthreads)
     return dict(x=xo, h=ho, status=st, iters=it, last_dh=dh)
+
+
+def chart_frames(verts, tris, h, grad, sigma=None, n: int = 6, uv=None):
+    """Local coordinates x_u, x_v and the area density |x_u x x_v| at the chart
+    nodes of the n x n Duffy chart rule (eq. u_vector, U_vector_2, v_vector,
+    v_vector_2, da), from the solved h and grad Phi at each node.  uv = (cu,
+    cv) replaces the rule's points (the same points on every triangle)."""
+    verts = _f64(verts)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    geo = geometry(verts, tris, sigma)
+    if uv is None:
+        cu, cv, _ = simplex_rule(n, 0)
+    else:
+        cu, cv = _f64(uv[0]), _f64(uv[1])
+    h, grad = _f64(h), _f64(grad)
+    m, npn = len(tris), len(cu)
+    assert h.shape == (m * npn,) and grad.shape == (m * npn, 3)
+    xu, xv, jac = np.empty((m * npn, 3)), np.empty((m * npn, 3)), np.empty(m * npn)
+    _load().or_chart_frames(_p(verts), m, _p(tris), _p(geo["vpn"]), npn, _p(cu), _p(cv), _p(h), _p(grad),
+                            _p(xu), _p(xv), _p(jac))
+    return xu, xv, jac
+
+
+def gauss_flux(x, grad, jac, x0, n: int = 6) -> float:
+    """Gauss flux error eps0 of the charts (Sec. 5) about the point x0, with
+    the n x n Duffy chart rule as quadrature on every triangle."""
+    _, _, cw = simplex_rule(n, 0)
+    x, grad, jac = _f64(x), _f64(grad), _f64(jac)
+    x0 = _f64(np.asarray(x0, dtype=np.float64).reshape(3))
+    assert len(x) % len(cw) == 0
+    return _load().or_gauss_flux(len(x), len(cw), _p(cw), _p(x), _p(grad), _p(jac), _p(x0))

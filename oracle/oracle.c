@@ -19,6 +19,9 @@
  *     the sign of the second term corrected; see below)
  *   - Newton on h: h <- h - (Phi(T + hH) - 1/2) / (H . grad Phi),  h0 = 0
  *                                                    (eq. newton, newtoneq)
+ *   - local coordinates x_u, x_v and da of the charts (eq. u_vector,
+ *     U_vector_2, v_vector, v_vector_2, da) and the Gauss flux error eps0
+ *     (Sec. 5)
  *
  * Notation.  r = y - x (source node minus target), rho = |r|,
  * a = 1/(sqrt(2) sigma), u = rho a,
@@ -401,4 +404,82 @@ void or_solve_charts(int64_t ns, const double* y, const double* nw, const double
         iters[i] = it;
         lastdh[i] = dh;
     }
+}
+
+/* Local coordinates of the chart nodes (Sec. 3.3): the chart is
+ * x(u,v) = T(u,v) + h(u,v) H(u,v)                               (eq. chart)
+ * with T_u = P2 - P1, T_v = P3 - P1 and, H being linear in (u,v),
+ * H_u = H2 - H1, H_v = H3 - H1.  x_u is tangent to the level set and grad Phi
+ * normal to it, so x_u . grad Phi = 0 gives
+ *   h_u = -((T_u + h H_u) . grad Phi) / (H . grad Phi)      (eq. U_vector_2)
+ *   x_u = T_u + h H_u + h_u H                                 (eq. u_vector)
+ * and the same in v (eq. v_vector, v_vector_2); the area element is
+ * da = |x_u x x_v| du dv                                         (eq. da).
+ * Node s = j * np + i sits at the rule point (cu[i], cv[i]) of triangle j;
+ * h [n] and grad [n][3] are the solved h and grad Phi at the node.
+ * Outputs: xu, xv [n][3], jac [n] = |x_u x x_v|. */
+void or_chart_frames(const double* verts, int64_t m, const int32_t* tris, const double* vpn,
+                     int np, const double* cu, const double* cv, const double* h,
+                     const double* grad, double* xu, double* xv, double* jac)
+{
+    for (int64_t j = 0; j < m; j++) {
+        const double* p1 = verts + 3 * (int64_t)tris[3*j+0];
+        const double* p2 = verts + 3 * (int64_t)tris[3*j+1];
+        const double* p3 = verts + 3 * (int64_t)tris[3*j+2];
+        const double* h1 = vpn + 3 * (int64_t)tris[3*j+0];
+        const double* h2 = vpn + 3 * (int64_t)tris[3*j+1];
+        const double* h3 = vpn + 3 * (int64_t)tris[3*j+2];
+        double tu[3], tv[3], hu[3], hv[3];
+        for (int c = 0; c < 3; c++) {
+            tu[c] = p2[c] - p1[c];
+            tv[c] = p3[c] - p1[c];
+            hu[c] = h2[c] - h1[c];
+            hv[c] = h3[c] - h1[c];
+        }
+        for (int i = 0; i < np; i++) {
+            const int64_t s = j * np + i;
+            const double* g = grad + 3*s;
+            double H[3], au[3], av[3];
+            for (int c = 0; c < 3; c++) {
+                H[c] = h1[c] + cu[i] * hu[c] + cv[i] * hv[c];
+                au[c] = tu[c] + h[s] * hu[c];
+                av[c] = tv[c] + h[s] * hv[c];
+            }
+            const double hg = dot3(H, g);
+            const double h_u = -dot3(au, g) / hg;
+            const double h_v = -dot3(av, g) / hg;
+            double a[3], b[3], n[3];
+            for (int c = 0; c < 3; c++) {
+                a[c] = au[c] + h_u * H[c];
+                b[c] = av[c] + h_v * H[c];
+                xu[3*s+c] = a[c];
+                xv[3*s+c] = b[c];
+            }
+            cross3(a, b, n);
+            jac[s] = norm3(n);
+        }
+    }
+}
+
+/* Gauss flux error of the charts (Sec. 5):
+ *   eps0 = 1 + integral over Gamma_1/2 of N_hat . grad_x 1/(4 pi |x0 - x|) da
+ * with grad_x 1/(4 pi |x0 - x|) = (x0 - x)/(4 pi |x0 - x|^3), the outward unit
+ * normal N_hat = -grad Phi/|grad Phi| (Phi falls from 1 inside to 0
+ * outside), and the chart rule as quadrature: node s = j * np + i carries
+ * cw[i] * jac[s] (the rule's weights sum to the reference triangle's 1/2).
+ * Zero for a closed surface around x0; 1 when x0 is outside. */
+double or_gauss_flux(int64_t n, int np, const double* cw, const double* x, const double* grad,
+                     const double* jac, const double* x0)
+{
+    double sum = 0.0;
+    for (int64_t s = 0; s < n; s++) {
+        const double* g = grad + 3*s;
+        const double gn = norm3(g);
+        double d[3];
+        for (int c = 0; c < 3; c++) d[c] = x0[c] - x[3*s+c];
+        const double r = norm3(d);
+        const double nd = -dot3(g, d) / gn;
+        sum += cw[s % np] * jac[s] * nd / (4.0 * M_PI * r * r * r);
+    }
+    return 1.0 + sum;
 }

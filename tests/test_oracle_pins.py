@@ -356,3 +356,112 @@ def test_newton_reports_nonconvergence(oracle_mod):
     out = oracle_mod.solve_charts(y, nw, sg, x0, hd, sl, tol=1e-14, max_iter=1)
     assert np.all((out["status"] & 255) == oracle_mod.ST_MAXITER)
     assert np.all(out["iters"] == 1)
+
+
+# ---------------------------------------------------------------- local coordinates and Gauss flux
+
+def _exact_sphere_charts(n):
+    """Unit sphere charted by radial projection of an icosphere's flat
+    triangles: positions, derivatives in (u, v) and |x_u x x_v| written out
+    from the projection x = T/|T| (no oracle code involved)."""
+    m = synth.icosphere(2)
+    V = m.verts / np.linalg.norm(m.verts, axis=1)[:, None]
+    cu, cv, _ = _rule(n)
+    P1, P2, P3 = V[m.tris[:, 0]], V[m.tris[:, 1]], V[m.tris[:, 2]]
+    Tu, Tv = P2 - P1, P3 - P1
+    T = P1[:, None, :] + cu[None, :, None] * Tu[:, None, :] + cv[None, :, None] * Tv[:, None, :]
+    nT = np.linalg.norm(T, axis=2)[..., None]
+    xu = Tu[:, None, :] / nT - T * np.sum(T * Tu[:, None, :], axis=2)[..., None] / nT ** 3
+    xv = Tv[:, None, :] / nT - T * np.sum(T * Tv[:, None, :], axis=2)[..., None] / nT ** 3
+    jac = np.linalg.norm(np.cross(xu, xv), axis=2)
+    return (T / nT).reshape(-1, 3), jac.ravel()
+
+
+def _rule(n):
+    """Duffy n x n rule on the reference triangle, written out with numpy's
+    Gauss-Legendre (u = xi (1 - eta), v = xi eta, w = w_xi w_eta xi)."""
+    g, wg = np.polynomial.legendre.leggauss(n)
+    g, wg = 0.5 * (g + 1), 0.5 * wg
+    xi, eta = np.meshgrid(g, g, indexing="ij")
+    wx, we = np.meshgrid(wg, wg, indexing="ij")
+    return (xi * (1 - eta)).ravel(), (xi * eta).ravel(), (wx * we * xi).ravel()
+
+
+def test_gauss_flux_exact_sphere(oracle_mod):
+    """Sec. 5: eps0 = 1 + flux of grad 1/(4 pi |x0 - x|) through a closed
+    surface is 0 for x0 inside and 1 outside; on an exactly charted sphere
+    the chart quadrature converges spectrally to those values."""
+    # the oracle's chart rule is the same Duffy rule (pinned above); check
+    # the point order used by the flux weights
+    u, v, w = oracle_mod.simplex_rule(8, 0)
+    cu, cv, cw = _rule(8)
+    assert np.allclose(u, cu) and np.allclose(v, cv) and np.allclose(w, cw)
+    errs = []
+    for n in (3, 5, 8):
+        x, jac = _exact_sphere_charts(n)
+        # outward normal is x; the oracle takes it as -grad Phi / |grad Phi|
+        e_in = [oracle_mod.gauss_flux(x, -x, jac, x0, n=n) for x0 in ((0.1, -0.2, 0.05), (0.0, 0.0, 0.0))]
+        e_out = oracle_mod.gauss_flux(x, -x, jac, (2.0, 0.3, 0.0), n=n)
+        errs.append(max(abs(e) for e in e_in))
+        assert abs(e_out - 1.0) < 1e-6
+    assert errs[0] > 1e3 * errs[1] and errs[1] > 1e3 * errs[2]
+    assert errs[2] < 1e-13
+
+
+@pytest.fixture(scope="module")
+def small_sphere_charts(oracle_mod):
+    """Icosphere level 1 (80 triangles), sigma by the workloads' rule, 4x4
+    sources; charts solved to 1e-14 at the rule points."""
+    m = synth.icosphere(1)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, None, 4, 0)
+    geo = oracle_mod.geometry(m.verts, m.tris, None)
+    return m, (y, nw, sg), geo
+
+
+def _solve_at(oracle_mod, m, src, geo, j, u, v):
+    """Chart point of triangle j at (u, v): Newton on h along H(u, v)."""
+    P = m.verts[m.tris[j]]
+    Hn = geo["vpn"][m.tris[j]]
+    x0 = P[0] + u * (P[1] - P[0]) + v * (P[2] - P[0])
+    H = Hn[0] + u * (Hn[1] - Hn[0]) + v * (Hn[2] - Hn[0])
+    r = oracle_mod.solve_charts(*src, x0[None], H[None], geo["sigma"][j:j + 1], tol=1e-14, max_iter=40)
+    assert r["status"][0] == 0
+    return r["x"][0], r["h"][0]
+
+
+def test_chart_frames_match_finite_differences(oracle_mod, small_sphere_charts):
+    """eq. u_vector / U_vector_2 (and v): x_u, x_v from the solved h and grad
+    Phi equal central differences of the solved chart x(u, v) = T + h H."""
+    m, src, geo = small_sphere_charts
+    d = 1e-4
+    for j, u, v in ((3, 0.2, 0.3), (41, 0.55, 0.1), (77, 0.1, 0.7)):
+        x, h = _solve_at(oracle_mod, m, src, geo, j, u, v)
+        _, g = oracle_mod.phi_grad(*src, x[None])
+        xu, xv, jac = oracle_mod.chart_frames(m.verts, m.tris, np.full(m.m, h), np.tile(g, (m.m, 1)),
+                                              uv=(np.array([u]), np.array([v])))
+        fu = (_solve_at(oracle_mod, m, src, geo, j, u + d, v)[0] - _solve_at(oracle_mod, m, src, geo, j, u - d, v)[0]) / (2 * d)
+        fv = (_solve_at(oracle_mod, m, src, geo, j, u, v + d)[0] - _solve_at(oracle_mod, m, src, geo, j, u, v - d)[0]) / (2 * d)
+        scale = np.linalg.norm(fu) + np.linalg.norm(fv)
+        assert np.abs(xu[j] - fu).max() < 1e-7 * scale
+        assert np.abs(xv[j] - fv).max() < 1e-7 * scale
+        assert abs(jac[j] - np.linalg.norm(np.cross(fu, fv))) < 1e-7 * scale ** 2
+        # the frame is tangent to the level set
+        assert abs(xu[j] @ g[0]) < 1e-9 * np.linalg.norm(xu[j]) * np.linalg.norm(g[0])
+
+
+def test_gauss_flux_of_solved_charts_converges(oracle_mod, small_sphere_charts):
+    """End to end: charts solved on the level set, their frames and the flux
+    about an interior point.  Adjacent charts meet exactly on shared edges,
+    so eps0 falls with the chart rule's order."""
+    m, src, geo = small_sphere_charts
+    out = []
+    for n in (3, 5, 7):
+        x0, hd, sl = oracle_mod.chart_nodes(m.verts, m.tris, None, n)
+        r = oracle_mod.solve_charts(*src, x0, hd, sl, tol=1e-14, max_iter=40)
+        assert (r["status"] == 0).all()
+        _, g = oracle_mod.phi_grad(*src, r["x"])
+        _, _, jac = oracle_mod.chart_frames(m.verts, m.tris, r["h"], g, n=n)
+        out.append(abs(oracle_mod.gauss_flux(r["x"], g, jac, (0.05, -0.1, 0.02), n=n)))
+    # measured: 1.4e-5, 4.7e-9, 9.9e-12
+    assert out[0] > 100 * out[1] and out[1] > 100 * out[2]
+    assert out[2] < 1e-10
