@@ -425,11 +425,14 @@ def main():
     grad = torch.empty((nt, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
+    last = {}
+
     def step():
         mesh.eval_phi_grad(x_dev, prec, phi=phi, grad=grad)
         if args.no_charts:
             return nt, None
-        _, _, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=prec, device_out=True)
+        xc, hc, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=prec, device_out=True)
+        last["x"], last["h"] = xc, hc
         return nt + sum(st.active_per_iter), st
 
     def barrier():
@@ -515,6 +518,17 @@ def main():
         e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": nt * 24,
                "d2h_bytes_per_step": nt * 32 + ncn * (24 + 8 + 4), "steps": e2e_steps}
 
+    # Gauss flux error of the last step's charts about the tube's centre line
+    # (untimed): grad Phi at the nodes from the float-float path, then the
+    # frames and the flux (Sec. 5)
+    eps0 = None
+    if "x" in last:
+        _, gc = mesh.eval_phi_grad(last["x"], lsm.FF)
+        _, _, jac = mesh.chart_frames(args.order, last["h"], gc)
+        eps0 = {"x0": [1.0, 0.0, 0.0], "value": mesh.gauss_flux(args.order, last["x"], gc, jac, (1.0, 0.0, 0.0)),
+                "grad": "float-float path"}
+        del gc, jac
+
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(w, args.cpu_seconds, w["rule"]["n"])
@@ -544,6 +558,7 @@ def main():
             "newton": {"iterations": st.iterations, "active_per_iter": st.active_per_iter,
                        "n_failed": st.n_failed, "eps_newton": st.eps_newton,
                        "max_residual": st.max_residual, "evals_fp64": st.evals_fp64} if st else None,
+            "gauss_flux_eps0": eps0,
             "gpu_launches": launches,
             "roofline": roofline,
             "roofline_kernels": kern,

@@ -241,6 +241,33 @@ int lsm_eval_phi_grad(lsm_mesh* mesh, const double* x, int64_t n, double* phi, d
 int lsm_eval_phi_grad_noalloc(lsm_mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
                               int precision, void* stream);
 
+/* Local coordinates of the solved charts (Sec. 3.3).  Chart j is
+ * x(u,v) = T^j(u,v) + h(u,v) H^j(u,v) (eq. chart); with grad Phi normal to the
+ * level set,
+ *   h_u = -((T_u + h H_u) . grad Phi) / (H . grad Phi)     (eq. U_vector_2)
+ *   x_u = T_u + h H_u + h_u H                                (eq. u_vector)
+ * and the same in v (eq. v_vector, v_vector_2); the area element is
+ * da = |x_u x x_v| du dv (eq. da).
+ *   order     the chart order given to lsm_solve_charts (rule n = order/2+2)
+ *   h         [N] solved h, nodes in lsm_solve_charts' order (N = M n^2)
+ *   grad      [N][3] grad Phi at the solved nodes (lsm_eval_phi_grad)
+ *   xu, xv    [N][3] out; jac [N] out: |x_u x x_v|
+ * Host or device pointers (outputs device-resident when device pointers are
+ * given).  A node with H . grad Phi = 0 gets non-finite values.
+ * Errors: LSM_E_INVALID_ARG, LSM_E_OOM, LSM_E_CUDA. */
+int lsm_chart_frames(lsm_mesh* mesh, int order, const double* h, const double* grad, double* xu, double* xv,
+                     double* jac, void* stream);
+/* Gauss flux error of the charts about an interior point x0 (Sec. 5):
+ *   eps0 = 1 + sum_nodes w_i jac N . (x0 - x)/(4 pi |x0 - x|^3),
+ * with N = -grad Phi/|grad Phi| the outward normal and the chart rule's
+ * weights w_i.  Zero for a closed surface around x0, one when x0 is outside.
+ *   x [N][3], grad [N][3], jac [N] as above (host or device); x0[3] host;
+ *   eps0 host out.  The sum is reduced in a fixed order (deterministic).
+ *   Synchronises `stream`.
+ * Errors: LSM_E_INVALID_ARG, LSM_E_OOM, LSM_E_CUDA. */
+int lsm_gauss_flux(lsm_mesh* mesh, int order, const double* x, const double* grad, const double* jac,
+                   const double* x0, double* eps0, void* stream);
+
 /* Autotuner of the mixed path's far field (the paper has no counterpart:
  * its FMM is run at a fixed precision, Sec. 4.4).  Chooses, for this mesh,
  * between the direct tiled far field and the treecode, and the treecode's

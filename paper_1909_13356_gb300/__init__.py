@@ -39,7 +39,7 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_read_stats", "lsm_mesh_upload", "lsm_mesh_free", "lsm_mesh_get_info", "lsm_eval_phi_grad",
            "lsm_eval_phi_grad_noalloc", "lsm_solve_charts", "lsm_batch_create", "lsm_batch_free",
            "lsm_batch_solve_charts", "lsm_server_create", "lsm_server_submit", "lsm_server_poll", "lsm_server_release",
-           "lsm_server_info", "lsm_server_destroy", "lsm_autotune")
+           "lsm_server_info", "lsm_server_destroy", "lsm_autotune", "lsm_chart_frames", "lsm_gauss_flux")
 
 
 class LsmError(RuntimeError):
@@ -162,6 +162,8 @@ def load(build_if_needed: bool = True):
         L.lsm_batch_free.argtypes = [P]
         L.lsm_batch_solve_charts.argtypes = [P, I32, D, I32, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
         L.lsm_autotune.argtypes = [P, P, I64, D, ctypes.POINTER(_TuneResult), P]
+        L.lsm_chart_frames.argtypes = [P, I32, P, P, P, P, P, P]
+        L.lsm_gauss_flux.argtypes = [P, I32, P, P, P, P, P, P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -320,6 +322,34 @@ class Mesh:
                                       _stream_handle(stream))
         self.ctx._check(rc)
         return {k: getattr(r, k) for k, _ in _TuneResult._fields_}
+
+    def chart_frames(self, order: int, h, grad, stream=None):
+        """Local coordinates x_u, x_v [N, 3] and |x_u x x_v| [N] of the solved
+        charts from their h [N] and grad Phi [N, 3] (lsm_chart_frames); torch
+        inputs give device-resident torch outputs."""
+        hs, gs = _as(h, np.float64), _as(grad, np.float64)
+        n = int(hs.shape[0])
+        if _is_torch(hs):
+            import torch
+            xu = torch.empty((n, 3), dtype=torch.float64, device=hs.device)
+            xv = torch.empty((n, 3), dtype=torch.float64, device=hs.device)
+            jac = torch.empty(n, dtype=torch.float64, device=hs.device)
+        else:
+            xu, xv, jac = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+        rc = self.ctx._L.lsm_chart_frames(self._h, int(order), _ptr(hs), _ptr(gs), _ptr(xu), _ptr(xv), _ptr(jac),
+                                          _stream_handle(stream))
+        self.ctx._check(rc)
+        return xu, xv, jac
+
+    def gauss_flux(self, order: int, x, grad, jac, x0, stream=None) -> float:
+        """Gauss flux error eps0 of the charts about x0 (lsm_gauss_flux)."""
+        xs, gs, js = _as(x, np.float64), _as(grad, np.float64), _as(jac, np.float64)
+        p0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float64).reshape(3))
+        out = ctypes.c_double()
+        rc = self.ctx._L.lsm_gauss_flux(self._h, int(order), _ptr(xs), _ptr(gs), _ptr(js), _ptr(p0),
+                                        ctypes.byref(out), _stream_handle(stream))
+        self.ctx._check(rc)
+        return out.value
 
     def solve_charts(self, order: int = 8, tol: float = 1e-12, max_iter: int = 20,
                      precision: int = FP64, device_out: bool = False, stream=None):

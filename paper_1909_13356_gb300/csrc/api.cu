@@ -547,6 +547,65 @@ int lsm_autotune(lsm_mesh* mh, const double* x, int64_t n, double err_budget, ls
     return check_flag(ctx, st);
 }
 
+int lsm_chart_frames(lsm_mesh* mh, int order, const double* h, const double* grad, double* xu, double* xv,
+                     double* jac, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (order < 0 || order > 40 || !h || !grad || !xu || !xv || !jac) {
+        ctx->err = "chart_frames: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_gl = order / 2 + 2;
+    const size_t N = (size_t)me->m * n_gl * n_gl;
+    Scratch s(st);
+    const double *hd, *gd;
+    int rc = to_device(ctx, s, h, N, &hd, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, grad, 3 * N, &gd, st);
+    if (rc) return rc;
+    double *a = xu, *b = xv, *c = jac;
+    const bool adev = is_device_ptr(xu), bdev = is_device_ptr(xv), cdev = is_device_ptr(jac);
+    if (!adev) LSM_CUDA_TRY(ctx, s.get(&a, 3 * N));
+    if (!bdev) LSM_CUDA_TRY(ctx, s.get(&b, 3 * N));
+    if (!cdev) LSM_CUDA_TRY(ctx, s.get(&c, N));
+    rc = chart_frames_dev(ctx, me, n_gl, hd, gd, a, b, c, st);
+    if (rc) return rc;
+    if (!adev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(xu, a, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+    if (!bdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(xv, b, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+    if (!cdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(jac, c, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    if (!adev || !bdev || !cdev) LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+int lsm_gauss_flux(lsm_mesh* mh, int order, const double* x, const double* grad, const double* jac,
+                   const double* x0, double* eps0, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (order < 0 || order > 40 || !x || !grad || !jac || !x0 || !eps0) {
+        ctx->err = "gauss_flux: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_gl = order / 2 + 2;
+    const size_t N = (size_t)me->m * n_gl * n_gl;
+    Scratch s(st);
+    const double *xd, *gd, *jd;
+    int rc = to_device(ctx, s, x, 3 * N, &xd, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, grad, 3 * N, &gd, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, jac, N, &jd, st);
+    if (rc) return rc;
+    return gauss_flux_dev(ctx, me, n_gl, xd, gd, jd, x0, eps0, st);
+}
+
 int lsm_solve_charts(lsm_mesh* mh, int order, double tol, int max_iter, int precision, double* x_out,
                      double* h_out, int32_t* status, lsm_solve_stats* stats, void* stream)
 {

@@ -1,0 +1,172 @@
+// frames.cu -- local coordinates of the solved charts and the Gauss flux
+// check of their closure (Sec. 3.3 and Sec. 5).
+//
+// Chart j is x(u,v) = T(u,v) + h(u,v) H(u,v) (eq. chart) over the flat
+// triangle T(u,v) = P1 + u (P2 - P1) + v (P3 - P1), with H interpolated
+// linearly from the vertex pseudonormals.  Newton gives h only at the rule
+// points; its derivatives follow from x_u being tangent to the level set and
+// grad Phi normal to it (x_u . grad Phi = 0):
+//   h_u = -((T_u + h H_u) . grad Phi) / (H . grad Phi)         (eq. U_vector_2)
+//   x_u = T_u + h H_u + h_u H                                    (eq. u_vector)
+// the same in v (eq. v_vector, v_vector_2), and da = |x_u x x_v| du dv
+// (eq. da).  The Gauss flux error
+//   eps0 = 1 + sum over chart nodes of w_i |x_u x x_v| N . (x0 - x) / (4 pi |x0 - x|^3),
+// N = -grad Phi / |grad Phi| the outward normal, is zero for a closed surface
+// around x0 (Sec. 5).  Both are elementwise FP64 work over the chart nodes;
+// the flux sum is reduced in a fixed order (per-block partials, then one
+// block), so it is deterministic.
+#include <vector>
+
+#include "lsm_internal.cuh"
+
+namespace lsm {
+namespace {
+
+constexpr int kFrameThreads = 256;
+constexpr double kFourPi = 12.566370614359172954;
+
+__global__ void k_chart_frames(const double* __restrict__ verts, const int32_t* __restrict__ tris,
+                               const double* __restrict__ vpn, int64_t m, int np, const double* __restrict__ rule,
+                               const double* __restrict__ h, const double* __restrict__ g, double* __restrict__ xu,
+                               double* __restrict__ xv, double* __restrict__ jac)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= m * np) return;
+    const int64_t j = s / np;
+    const int i = (int)(s - j * np);
+    const double u = rule[3 * i], v = rule[3 * i + 1];
+    const int a = tris[3 * j], b = tris[3 * j + 1], c = tris[3 * j + 2];
+    double tu[3], tv[3], H[3], hu[3], hv[3], gs[3];
+    for (int k = 0; k < 3; k++) {
+        const double p1 = verts[3 * a + k], n1 = vpn[3 * a + k];
+        tu[k] = verts[3 * b + k] - p1;
+        tv[k] = verts[3 * c + k] - p1;
+        hu[k] = vpn[3 * b + k] - n1;
+        hv[k] = vpn[3 * c + k] - n1;
+        H[k] = n1 + u * hu[k] + v * hv[k];
+        gs[k] = g[3 * s + k];
+    }
+    const double hs = h[s];
+    double au[3], av[3];
+    for (int k = 0; k < 3; k++) {
+        au[k] = tu[k] + hs * hu[k];
+        av[k] = tv[k] + hs * hv[k];
+    }
+    const double hg = H[0] * gs[0] + H[1] * gs[1] + H[2] * gs[2];
+    const double h_u = -(au[0] * gs[0] + au[1] * gs[1] + au[2] * gs[2]) / hg;
+    const double h_v = -(av[0] * gs[0] + av[1] * gs[1] + av[2] * gs[2]) / hg;
+    double x1[3], x2[3];
+    for (int k = 0; k < 3; k++) {
+        x1[k] = au[k] + h_u * H[k];
+        x2[k] = av[k] + h_v * H[k];
+        xu[3 * s + k] = x1[k];
+        xv[3 * s + k] = x2[k];
+    }
+    const double cx = x1[1] * x2[2] - x1[2] * x2[1];
+    const double cy = x1[2] * x2[0] - x1[0] * x2[2];
+    const double cz = x1[0] * x2[1] - x1[1] * x2[0];
+    jac[s] = sqrt(cx * cx + cy * cy + cz * cz);
+}
+
+// Per-block partial sums of the flux terms (block sums in a fixed tree order).
+__global__ void __launch_bounds__(kFrameThreads) k_flux_partial(const double* __restrict__ x,
+                                                                const double* __restrict__ g,
+                                                                const double* __restrict__ jac, int64_t n, int np,
+                                                                const double* __restrict__ rule, double x0, double y0,
+                                                                double z0, double* __restrict__ part)
+{
+    __shared__ double sw[kFrameThreads / 32];
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double t = 0.0;
+    if (s < n) {
+        const double dx = x0 - x[3 * s], dy = y0 - x[3 * s + 1], dz = z0 - x[3 * s + 2];
+        const double gx = g[3 * s], gy = g[3 * s + 1], gz = g[3 * s + 2];
+        const double gn = sqrt(gx * gx + gy * gy + gz * gz);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double r = sqrt(r2);
+        const double nd = -(gx * dx + gy * dy + gz * dz) / gn;
+        t = rule[3 * (s % np) + 2] * jac[s] * nd / (kFourPi * r2 * r);
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int k = 0; k < kFrameThreads / 32; k++) a += sw[k];
+        part[blockIdx.x] = a;
+    }
+}
+
+// One block: the partials in index order, then 1 + sum.
+__global__ void __launch_bounds__(kFrameThreads) k_flux_final(const double* __restrict__ part, int nb,
+                                                              double* __restrict__ out)
+{
+    __shared__ double sw[kFrameThreads];
+    double a = 0.0;
+    const int per = (nb + kFrameThreads - 1) / kFrameThreads;
+    const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+    for (int k = lo; k < hi; k++) a += part[k];
+    sw[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kFrameThreads; k++) t += sw[k];
+        *out = 1.0 + t;
+    }
+}
+
+int upload_rule(Ctx* ctx, Scratch& s, int n_gl, double** rule, cudaStream_t st)
+{
+    const int np = n_gl * n_gl;
+    std::vector<double> r(3 * (size_t)np);
+    simplex_rule_host(n_gl, 0, r.data());
+    LSM_CUDA_TRY(ctx, s.get(rule, r.size()));
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(*rule, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, st));
+    // the host vector must outlive the copy
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+}  // namespace
+
+int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const double* g, double* xu, double* xv,
+                     double* jac, cudaStream_t st)
+{
+    Scratch s(st);
+    double* rule = nullptr;
+    int rc = upload_rule(ctx, s, n_gl, &rule, st);
+    if (rc) return rc;
+    const int np = n_gl * n_gl;
+    const int64_t n = me->m * np;
+    if (n == 0) return LSM_OK;
+    k_chart_frames<<<(unsigned)((n + kFrameThreads - 1) / kFrameThreads), kFrameThreads, 0, st>>>(
+        me->verts, me->tris, me->vpn, me->m, np, rule, h, g, xu, xv, jac);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
+int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const double* g, const double* jac,
+                   const double* x0, double* eps0, cudaStream_t st)
+{
+    Scratch s(st);
+    double* rule = nullptr;
+    int rc = upload_rule(ctx, s, n_gl, &rule, st);
+    if (rc) return rc;
+    const int np = n_gl * n_gl;
+    const int64_t n = me->m * np;
+    const int nb = (int)((n + kFrameThreads - 1) / kFrameThreads);
+    double *part = nullptr, *out = nullptr;
+    LSM_CUDA_TRY(ctx, s.get(&part, std::max(1, nb)));
+    LSM_CUDA_TRY(ctx, s.get(&out, 1));
+    if (nb > 0) {
+        k_flux_partial<<<nb, kFrameThreads, 0, st>>>(x, g, jac, n, np, rule, x0[0], x0[1], x0[2], part);
+        LSM_LAUNCHED(ctx);
+    }
+    k_flux_final<<<1, kFrameThreads, 0, st>>>(part, nb, out);
+    LSM_LAUNCHED(ctx);
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(eps0, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+}  // namespace lsm

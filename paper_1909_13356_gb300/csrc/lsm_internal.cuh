@@ -254,6 +254,13 @@ void tree_free(Tree* t);
 int tree_lists(Ctx* ctx, const Tree* tree, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
                int** order, int64_t* total, cudaStream_t st);
 
+// frames.cu: chart local coordinates and the Gauss flux (lsm_chart_frames,
+// lsm_gauss_flux); all arrays on the device, nodes in solve order
+int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const double* g, double* xu, double* xv,
+                     double* jac, cudaStream_t st);
+int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const double* g, const double* jac,
+                   const double* x0, double* eps0, cudaStream_t st);
+
 // tune.cu: the autotuner on sorted SoA targets (lsm_autotune)
 int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tune_result* res, cudaStream_t st);
 
