@@ -65,6 +65,12 @@ def _load():
             lib.or_chart_frames.argtypes = [P, I64, P, P, ctypes.c_int, P, P, P, P, P, P, P]
             lib.or_gauss_flux.argtypes = [I64, ctypes.c_int, P, P, P, P, P]
             lib.or_gauss_flux.restype = ctypes.c_double
+            lib.or_sigma_sources.argtypes = [P, I64, P, ctypes.c_double, P, P]
+            lib.or_sigma_sources.restype = ctypes.c_double
+            lib.or_sigma_x.argtypes = [I64, P, P, ctypes.c_double, I64, P, P, P]
+            lib.or_phi_grad_sigx.argtypes = [I64, P, P, I64, P, P, P, P, P, ctypes.c_int]
+            lib.or_solve_charts_sigx.argtypes = [I64, P, P, I64, P, P, ctypes.c_double, I64, P, P, P,
+                                                 ctypes.c_double, ctypes.c_int, P, P, P, P, P, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -206,3 +212,57 @@ def gauss_flux(x, grad, jac, x0, n: int = 6) -> float:
     x0 = _f64(np.asarray(x0, dtype=np.float64).reshape(3))
     assert len(x) % len(cw) == 0
     return _load().or_gauss_flux(len(x), len(cw), _p(cw), _p(x), _p(grad), _p(jac), _p(x0))
+
+
+SIGMA_LAMBDA = 2.5
+
+
+def sigma0_default(dmax: float) -> float:
+    """sigma0 such that a centroid one diameter away has weight 1/2 (the
+    influence the paper states for its choice, Sec. 2.3)."""
+    return dmax / np.sqrt(2.0 * np.log(2.0))
+
+
+def sigma_sources(verts, tris, lam: float = SIGMA_LAMBDA):
+    """Centroids c_j, sigma_j = D_j / lambda (D_j: diameter of the smallest
+    enclosing ball) and max_j D_j (Sec. 2.3)."""
+    verts = _f64(verts)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    m = len(tris)
+    c, sj = np.empty((m, 3)), np.empty(m)
+    dmax = _load().or_sigma_sources(_p(verts), m, _p(tris), float(lam), _p(c), _p(sj))
+    return c, sj, dmax
+
+
+def sigma_x(c, sj, sigma0: float, x):
+    """sigma(x) and grad sigma(x) at targets x [n, 3] (eq. sigma2)."""
+    c, sj, x = _f64(c), _f64(sj), _f64(x)
+    n = len(x)
+    sig, gs = np.empty(n), np.empty((n, 3))
+    _load().or_sigma_x(len(c), _p(c), _p(sj), float(sigma0), n, _p(x), _p(sig), _p(gs))
+    return sig, gs
+
+
+def phi_grad_sigx(y, nw, x, sig, gsig, nthreads: int = 0):
+    """Phi and grad Phi with the targets' sigma (eq. kerpsi with sigma(x), eq.
+    gradPhi including the grad-sigma term, sign corrected)."""
+    y, nw, x, sig, gsig = _f64(y), _f64(nw), _f64(x), _f64(sig), _f64(gsig)
+    nt = len(x)
+    phi, grad = np.empty(nt), np.empty((nt, 3))
+    _load().or_phi_grad_sigx(len(y), _p(y), _p(nw), nt, _p(x), _p(sig), _p(gsig), _p(phi), _p(grad), nthreads)
+    return phi, grad
+
+
+def solve_charts_sigx(y, nw, c, sj, sigma0, x0, hdir, sloc, tol: float = 1e-12, max_iter: int = 20,
+                      nthreads: int = 0):
+    """Newton's method for h at each chart node (eq. newtoneq) with sigma(x)."""
+    y, nw, c, sj = _f64(y), _f64(nw), _f64(c), _f64(sj)
+    x0, hdir, sloc = _f64(x0), _f64(hdir), _f64(sloc)
+    n = len(x0)
+    xo, ho = np.empty((n, 3)), np.empty(n)
+    st, it = np.empty(n, dtype=np.int32), np.empty(n, dtype=np.int32)
+    dh = np.empty(n)
+    _load().or_solve_charts_sigx(len(y), _p(y), _p(nw), len(c), _p(c), _p(sj), float(sigma0), n, _p(x0), _p(hdir),
+                                 _p(sloc), float(tol), int(max_iter), _p(xo), _p(ho), _p(st), _p(it), _p(dh),
+                                 nthreads)
+    return dict(x=xo, h=ho, status=st, iters=it, last_dh=dh)

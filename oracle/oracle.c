@@ -22,6 +22,9 @@
  *   - local coordinates x_u, x_v and da of the charts (eq. u_vector,
  *     U_vector_2, v_vector, v_vector_2, da) and the Gauss flux error eps0
  *     (Sec. 5)
+ *   - the target-dependent width sigma(x), a Gaussian-weighted mean of
+ *     sigma_j = D_j / lambda over the triangle centroids (eq. sigma2), and
+ *     Phi, grad Phi with it (eq. gradPhi's third term, sign corrected)
  *
  * Notation.  r = y - x (source node minus target), rho = |r|,
  * a = 1/(sqrt(2) sigma), u = rho a,
@@ -482,4 +485,159 @@ double or_gauss_flux(int64_t n, int np, const double* cw, const double* x, const
         sum += cw[s % np] * jac[s] * nd / (4.0 * M_PI * r * r * r);
     }
     return 1.0 + sum;
+}
+
+/* ------------------------------------------------------------------ */
+/* Target-dependent smoothing width (Sec. 2.3, eq. sigma2).
+ * sigma_j = D_j / lambda with D_j the diameter of the smallest ball enclosing
+ * triangle j: the longest edge when the triangle is right or obtuse (the
+ * ball on that edge contains the third vertex), else twice the circumradius,
+ * 2R = abc / (2 area).  c_j is the centroid.  Outputs c [m][3], sj [m];
+ * returns max_j D_j. */
+double or_sigma_sources(const double* verts, int64_t m, const int32_t* tris, double lambda,
+                        double* c, double* sj)
+{
+    double dmax = 0.0;
+    for (int64_t j = 0; j < m; j++) {
+        const double* p[3] = {verts + 3 * (int64_t)tris[3*j+0], verts + 3 * (int64_t)tris[3*j+1],
+                              verts + 3 * (int64_t)tris[3*j+2]};
+        double e2[3], ab[3], ac[3], n[3];
+        for (int k = 0; k < 3; k++) {
+            const double* a = p[(k + 1) % 3];
+            const double* b = p[(k + 2) % 3];
+            double d[3] = {a[0] - b[0], a[1] - b[1], a[2] - b[2]};
+            e2[k] = dot3(d, d);             /* squared edge opposite vertex k */
+        }
+        for (int k = 0; k < 3; k++) {
+            ab[k] = p[1][k] - p[0][k];
+            ac[k] = p[2][k] - p[0][k];
+            c[3*j+k] = (p[0][k] + p[1][k] + p[2][k]) / 3.0;
+        }
+        cross3(ab, ac, n);
+        const double area = 0.5 * norm3(n);
+        int kl = 0;
+        if (e2[1] > e2[kl]) kl = 1;
+        if (e2[2] > e2[kl]) kl = 2;
+        double D;
+        if (e2[kl] >= e2[(kl + 1) % 3] + e2[(kl + 2) % 3]) {
+            D = sqrt(e2[kl]);
+        } else {
+            D = sqrt(e2[0]) * sqrt(e2[1]) * sqrt(e2[2]) / (2.0 * area);
+        }
+        sj[j] = D / lambda;
+        if (D > dmax) dmax = D;
+    }
+    return dmax;
+}
+
+/* sigma(x) = sum_j sigma_j e_j / sum_j e_j, e_j = exp(-|x - c_j|^2 / (2 sigma0^2))
+ * (eq. sigma2), and its gradient
+ *   grad sigma = (S1 sum_j e_j (x - c_j) - S0 sum_j sigma_j e_j (x - c_j)) / (sigma0^2 S0^2)
+ * with S0 = sum_j e_j, S1 = sum_j sigma_j e_j; direct sums over all M
+ * triangles.  gsig may be NULL. */
+static void sigma_x_one(int64_t m, const double* c, const double* sj, double sigma0, const double* x,
+                        double* sig, double* gsig)
+{
+    const double inv2s2 = 1.0 / (2.0 * sigma0 * sigma0);
+    double S0 = 0.0, S1 = 0.0, A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    for (int64_t j = 0; j < m; j++) {
+        double d[3] = {x[0] - c[3*j], x[1] - c[3*j+1], x[2] - c[3*j+2]};
+        const double e = exp(-dot3(d, d) * inv2s2);
+        S0 += e;
+        S1 += sj[j] * e;
+        for (int k = 0; k < 3; k++) {
+            A[k] += e * d[k];
+            B[k] += sj[j] * e * d[k];
+        }
+    }
+    *sig = S1 / S0;
+    if (gsig)
+        for (int k = 0; k < 3; k++) gsig[k] = (S1 * A[k] - S0 * B[k]) / (sigma0 * sigma0 * S0 * S0);
+}
+
+void or_sigma_x(int64_t m, const double* c, const double* sj, double sigma0, int64_t n, const double* x,
+                double* sig, double* gsig)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < n; t++) sigma_x_one(m, c, sj, sigma0, x + 3*t, sig + t, gsig ? gsig + 3*t : NULL);
+}
+
+/* Phi and grad Phi with the target's sigma: every pair of target t takes
+ * sigma = sig[t] (eq. kerpsi with sigma(x)), and grad Phi gains
+ * (dPhi/dsigma) grad sigma (eq. gradPhi, third term), with
+ *   d/dsigma [(nw . r) g(u) / (4 pi rho^3)] = -(nw . r) exp(-u^2) / (2 sqrt2 pi^(3/2) sigma^4),
+ * r = y - x, u = rho / (sqrt2 sigma).  (The paper prints this term with the
+ * opposite sign; differentiating g(u) = erf(u) - (2u/sqrt pi) exp(-u^2),
+ * g'(u) = (4 u^2 / sqrt pi) exp(-u^2), and u in sigma gives the minus.) */
+static void phi_grad_sigx_one(int64_t ns, const double* y, const double* nw, const double* x, double s,
+                              const double* gsig, double* phi, double* grad)
+{
+    const double cs = 1.0 / (2.0 * sqrt(2.0) * pow(M_PI, 1.5));
+    double p = 0.0, g[3] = {0.0, 0.0, 0.0}, dps = 0.0;
+    for (int64_t k = 0; k < ns; k++) {
+        or_pair(y + 3*k, nw + 3*k, s, x, &p, g);
+        double r[3] = {y[3*k] - x[0], y[3*k+1] - x[1], y[3*k+2] - x[2]};
+        const double u2 = dot3(r, r) / (2.0 * s * s);
+        dps -= dot3(nw + 3*k, r) * exp(-u2) * cs / (s * s * s * s);
+    }
+    *phi = p;
+    if (grad)
+        for (int c = 0; c < 3; c++) grad[c] = g[c] + dps * gsig[c];
+}
+
+void or_phi_grad_sigx(int64_t ns, const double* y, const double* nw, int64_t nt, const double* x,
+                      const double* sig, const double* gsig, double* phi, double* grad, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++)
+        phi_grad_sigx_one(ns, y, nw, x + 3*t, sig[t], gsig + 3*t, phi + t, grad ? grad + 3*t : NULL);
+}
+
+/* Newton's method for the charts with sigma(x): as or_solve_charts, with
+ * sigma(x) and grad sigma re-evaluated at every iterate. */
+void or_solve_charts_sigx(int64_t ns, const double* y, const double* nw, int64_t m, const double* c,
+                          const double* sj, double sigma0, int64_t n, const double* x0, const double* hdir,
+                          const double* sloc, double tol, int max_iter, double* xout, double* hout,
+                          int32_t* status, int32_t* iters, double* lastdh, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; i++) {
+        const double* H = hdir + 3*i;
+        double h = 0.0, dh = 0.0;
+        int st = OR_ST_MAXITER, clamped = 0, it = 0;
+        double x[3];
+        for (it = 0; it < max_iter; it++) {
+            for (int k = 0; k < 3; k++) x[k] = x0[3*i+k] + h * H[k];
+            double s, gs[3], p, g[3];
+            sigma_x_one(m, c, sj, sigma0, x, &s, gs);
+            phi_grad_sigx_one(ns, y, nw, x, s, gs, &p, g);
+            double res = p - 0.5;
+            if (!isfinite(res)) { st = OR_ST_NONFINITE; it++; break; }
+            if (fabs(res) < tol) { st = OR_ST_CONVERGED; it++; break; }
+            double d = dot3(H, g);
+            if (!isfinite(d)) { st = OR_ST_NONFINITE; it++; break; }
+            if (d == 0.0) { st = OR_ST_ZERODERIV; it++; break; }
+            double step = -res / d;
+            double lim = 4.0 * sloc[i];
+            if (step > lim) { step = lim; clamped = 1; }
+            if (step < -lim) { step = -lim; clamped = 1; }
+            h += step;
+            dh = fabs(step);
+        }
+        for (int k = 0; k < 3; k++) xout[3*i+k] = x0[3*i+k] + h * H[k];
+        hout[i] = h;
+        status[i] = st | (clamped ? 256 : 0);
+        iters[i] = it;
+        lastdh[i] = dh;
+    }
 }

@@ -465,3 +465,116 @@ def test_gauss_flux_of_solved_charts_converges(oracle_mod, small_sphere_charts):
     # measured: 1.4e-5, 4.7e-9, 9.9e-12
     assert out[0] > 100 * out[1] and out[1] > 100 * out[2]
     assert out[2] < 1e-10
+
+
+# ---------------------------------------------------------------- target-dependent sigma (eq. sigma2)
+
+def test_enclosing_ball_diameters(oracle_mod):
+    """D_j: longest edge for right and obtuse triangles, the circumdiameter
+    abc/(2 area) for acute ones (closed forms written out here)."""
+    P = np.array([[0, 0, 0], [1, 0, 0], [0.5, np.sqrt(3) / 2, 0],        # equilateral, side 1
+                  [0, 0, 1], [3, 0, 1], [0, 4, 1],                        # right, 3-4-5
+                  [0, 0, 2], [4, 0, 2], [1, 0.5, 2],                      # obtuse
+                  [0, 0, 3], [2, 0, 3], [0.8, 1.5, 3]], dtype=float)      # acute scalene
+    T = np.arange(12, dtype=np.int32).reshape(4, 3)
+    _, sj, dmax = oracle_mod.sigma_sources(P, T, lam=1.0)
+    a, b, c = np.linalg.norm(P[10] - P[9]), np.linalg.norm(P[11] - P[10]), np.linalg.norm(P[11] - P[9])
+    area = 0.5 * np.linalg.norm(np.cross(P[10] - P[9], P[11] - P[9]))
+    want = [2 / np.sqrt(3), 5.0, 4.0, a * b * c / (2 * area)]
+    assert np.allclose(sj, want, rtol=1e-14, atol=0)
+    assert dmax == max(want)
+
+
+def _graded_small():
+    m = synth.torus(1.0, 0.3, 24, 8, 8.0, 0.05, 7)
+    return m
+
+
+def test_sigma_x_constant_when_all_equal(oracle_mod):
+    m = synth.cube(1.0, 4)                    # every triangle right isosceles, legs 0.5
+    c, sj, dmax = oracle_mod.sigma_sources(m.verts, m.tris)
+    assert np.allclose(sj, 0.5 * np.sqrt(2) / 2.5, rtol=1e-15)
+    x = synth.targets_uniform(50, -1.5, 1.5, synth.rng(41))
+    s, gs = oracle_mod.sigma_x(c, sj, oracle_mod.sigma0_default(dmax), x)
+    assert np.allclose(s, sj[0], rtol=1e-14)
+    assert np.abs(gs).max() < 1e-12
+
+
+def test_sigma_x_gradient_finite_differences(oracle_mod):
+    m = _graded_small()
+    c, sj, dmax = oracle_mod.sigma_sources(m.verts, m.tris)
+    s0 = oracle_mod.sigma0_default(dmax)
+    x = synth.targets_near_surface(m, 20, synth.rng(42), 3.0)
+    _, gs = oracle_mod.sigma_x(c, sj, s0, x)
+    d = 1e-5
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = d
+        fd = (oracle_mod.sigma_x(c, sj, s0, x + e)[0] - oracle_mod.sigma_x(c, sj, s0, x - e)[0]) / (2 * d)
+        assert np.abs(fd - gs[:, k]).max() < 1e-8 * (np.abs(gs).max() + 1e-3)
+    # sigma varies on this graded mesh
+    assert np.ptp(sj) > 0.5 * sj.mean()
+
+
+def test_sigma_x_phi_reduces_to_constant_sigma(oracle_mod):
+    """With every sigma_j equal, sigma(x) is that constant and the sigma(x)
+    sum is the constant-sigma sum (pinned to the box's erf product above)."""
+    m = synth.cube(1.0, 4)
+    c, sj, dmax = oracle_mod.sigma_sources(m.verts, m.tris)
+    x = synth.targets_uniform(200, -1.5, 1.5, synth.rng(43))
+    s, gs = oracle_mod.sigma_x(c, sj, oracle_mod.sigma0_default(dmax), x)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, np.full(m.m, sj[0]), 4, 1)
+    p1, g1 = oracle_mod.phi_grad_sigx(y, nw, x, s, gs)
+    p0, g0 = oracle_mod.phi_grad(y, nw, sg, x)
+    assert np.abs(p1 - p0).max() < 1e-13
+    assert np.abs(g1 - g0).max() < 1e-11
+
+
+def test_sigma_x_grad_phi_finite_differences(oracle_mod):
+    """eq. gradPhi with sigma(x): its third term, (dPhi/dsigma) grad sigma
+    with the corrected sign, is needed to match central differences of Phi."""
+    m = _graded_small()
+    c, sj, dmax = oracle_mod.sigma_sources(m.verts, m.tris)
+    s0 = oracle_mod.sigma0_default(dmax)
+    y, nw, _ = oracle_mod.sources(m.verts, m.tris, None, 6, 0)
+    x = synth.targets_near_surface(m, 12, synth.rng(44), 2.0)
+
+    def phi_at(p):
+        s, gs = oracle_mod.sigma_x(c, sj, s0, p)
+        return oracle_mod.phi_grad_sigx(y, nw, p, s, gs)
+
+    _, g = phi_at(x)
+    s, gs = oracle_mod.sigma_x(c, sj, s0, x)
+    d = 1e-5
+    fd = np.empty_like(g)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = d
+        fd[:, k] = (phi_at(x + e)[0] - phi_at(x - e)[0]) / (2 * d)
+    scale = np.abs(g).max()
+    assert np.abs(fd - g).max() < 1e-7 * scale
+    # without the grad-sigma term (or with the printed sign) the match fails
+    dps = np.empty(len(x))
+    for t in range(len(x)):
+        r = y - x[t]
+        u2 = np.sum(r * r, axis=1) / (2 * s[t] ** 2)
+        dps[t] = -np.sum(np.sum(nw * r, axis=1) * np.exp(-u2)) / (2 * np.sqrt(2) * np.pi ** 1.5 * s[t] ** 4)
+    g_no = g - dps[:, None] * gs
+    g_flip = g - 2 * dps[:, None] * gs
+    assert np.abs(fd - g_no).max() > 100 * np.abs(fd - g).max()
+    assert np.abs(fd - g_flip).max() > 100 * np.abs(fd - g).max()
+
+
+def test_sigma_x_charts_converge(oracle_mod):
+    m = _graded_small()
+    c, sj, dmax = oracle_mod.sigma_sources(m.verts, m.tris)
+    s0 = oracle_mod.sigma0_default(dmax)
+    y, nw, _ = oracle_mod.sources(m.verts, m.tris, None, 6, 0)
+    x0, hd, _ = oracle_mod.chart_nodes(m.verts, m.tris, None, 4)
+    sel = np.arange(0, len(x0), 37)
+    sloc = np.repeat(sj, 16)[sel]
+    r = oracle_mod.solve_charts_sigx(y, nw, c, sj, s0, x0[sel], hd[sel], sloc, tol=1e-13, max_iter=30)
+    assert (r["status"] == 0).all()
+    s, gs = oracle_mod.sigma_x(c, sj, s0, r["x"])
+    p, _ = oracle_mod.phi_grad_sigx(y, nw, r["x"], s, gs)
+    assert np.abs(p - 0.5).max() < 1e-13
