@@ -192,6 +192,28 @@ int lsm_read_stats(lsm_ctx* ctx, lsm_ctx_stats* out, int reset);
 int lsm_mesh_upload(lsm_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris,
                     int64_t nt, const double* sigma, const lsm_quad* rule, void* stream,
                     lsm_mesh** out);
+/* Upload a mesh whose smoothing width depends on the target (Sec. 2.3,
+ * eq. sigma2): sigma(x) = sum_j sigma_j e_j / sum_j e_j with
+ * e_j = exp(-|x - c_j|^2 / (2 sigma0^2)), c_j the centroid of triangle j and
+ * sigma_j = D_j / lambda, D_j the diameter of the smallest ball enclosing it.
+ * Every evaluation then uses the target's sigma(x) for all of its pairs, and
+ * grad Phi gains (dPhi/dsigma) grad sigma (eq. gradPhi, third term, with the
+ * sign that differentiating eq. kerpsi in sigma gives).
+ *   lambda   0 selects 2.5 (the paper's choice)
+ *   sigma0   0 selects max_j D_j / sqrt(2 ln 2): a centroid one diameter away
+ *            weighs 1/2, the influence the paper describes for its choice
+ * Everything else as lsm_mesh_upload (sigma_j doubles as the per-triangle
+ * sigma of the Newton step clamp).  Batches and lsm_eval_phi_grad_noalloc
+ * reject such meshes.  Errors: as lsm_mesh_upload. */
+int lsm_mesh_upload_sigmax(lsm_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                           double lambda, double sigma0, const lsm_quad* rule, void* stream, lsm_mesh** out);
+/* sigma(x) [n] and grad sigma(x) [n][3] (may be NULL) at n targets of a mesh
+ * uploaded with lsm_mesh_upload_sigmax (eq. sigma2); pointers as in
+ * lsm_eval_phi_grad.  Errors: LSM_E_INVALID_ARG (also for other meshes),
+ * LSM_E_OOM, LSM_E_CUDA. */
+int lsm_eval_sigma(lsm_mesh* mesh, const double* x, int64_t n, double* sigma, double* gsigma, void* stream);
+/* sigma0 of a mesh uploaded with lsm_mesh_upload_sigmax (0 for others). */
+int lsm_mesh_get_sigma0(const lsm_mesh* mesh, double* sigma0);
 int lsm_mesh_free(lsm_mesh* mesh);
 int lsm_mesh_get_info(const lsm_mesh* mesh, lsm_mesh_info* out);
 

@@ -39,7 +39,8 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_read_stats", "lsm_mesh_upload", "lsm_mesh_free", "lsm_mesh_get_info", "lsm_eval_phi_grad",
            "lsm_eval_phi_grad_noalloc", "lsm_solve_charts", "lsm_batch_create", "lsm_batch_free",
            "lsm_batch_solve_charts", "lsm_server_create", "lsm_server_submit", "lsm_server_poll", "lsm_server_release",
-           "lsm_server_info", "lsm_server_destroy", "lsm_autotune", "lsm_chart_frames", "lsm_gauss_flux")
+           "lsm_server_info", "lsm_server_destroy", "lsm_autotune", "lsm_chart_frames", "lsm_gauss_flux",
+           "lsm_mesh_upload_sigmax", "lsm_mesh_get_sigma0", "lsm_eval_sigma")
 
 
 class LsmError(RuntimeError):
@@ -163,6 +164,9 @@ def load(build_if_needed: bool = True):
         L.lsm_batch_solve_charts.argtypes = [P, I32, D, I32, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
         L.lsm_autotune.argtypes = [P, P, I64, D, ctypes.POINTER(_TuneResult), P]
         L.lsm_chart_frames.argtypes = [P, I32, P, P, P, P, P, P]
+        L.lsm_mesh_upload_sigmax.argtypes = [P, P, I64, P, I64, D, D, ctypes.POINTER(_Quad), P, ctypes.POINTER(P)]
+        L.lsm_mesh_get_sigma0.argtypes = [P, ctypes.POINTER(D)]
+        L.lsm_eval_sigma.argtypes = [P, P, I64, P, P, P]
         L.lsm_gauss_flux.argtypes = [P, I32, P, P, P, P, P, P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
@@ -258,6 +262,11 @@ class Context:
     def upload(self, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0, stream=None) -> "Mesh":
         return Mesh(self, verts, tris, sigma, n_gl, subdiv, stream)
 
+    def upload_sigma_x(self, verts, tris, lam: float = 0.0, sigma0: float = 0.0, n_gl: int = 4, subdiv: int = 0,
+                       stream=None) -> "Mesh":
+        """A mesh with the target-dependent sigma(x) of eq. sigma2."""
+        return Mesh(self, verts, tris, None, n_gl, subdiv, stream, sigma_x=True, lam=lam, sigma0=sigma0)
+
     def close(self):
         if getattr(self, "_h", None):
             self._L.lsm_destroy(self._h)
@@ -274,18 +283,46 @@ class Mesh:
     """Resident device state of one skeleton triangulation (lsm_mesh_upload)."""
 
     def __init__(self, ctx: Context, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0,
-                 stream=None):
+                 stream=None, sigma_x: bool = False, lam: float = 0.0, sigma0: float = 0.0):
+        """sigma_x=True: target-dependent sigma(x) (lsm_mesh_upload_sigmax, with
+        lambda and sigma0, 0 for the defaults); else per-triangle sigma."""
         self.ctx = ctx
         v = _as(verts, np.float64)
         t = _as(tris, np.int32)
-        s = _as(sigma, np.float64) if sigma is not None else None
         q = _Quad(int(n_gl), int(subdiv))
         h = ctypes.c_void_p()
-        rc = ctx._L.lsm_mesh_upload(ctx._h, _ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]),
-                                    _ptr(s), ctypes.byref(q), _stream_handle(stream), ctypes.byref(h))
+        if sigma_x:
+            rc = ctx._L.lsm_mesh_upload_sigmax(ctx._h, _ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]),
+                                               float(lam), float(sigma0), ctypes.byref(q),
+                                               _stream_handle(stream), ctypes.byref(h))
+        else:
+            s = _as(sigma, np.float64) if sigma is not None else None
+            rc = ctx._L.lsm_mesh_upload(ctx._h, _ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]),
+                                        _ptr(s), ctypes.byref(q), _stream_handle(stream), ctypes.byref(h))
         ctx._check(rc)
         self._h = h
         self.n_triangles = int(t.shape[0])
+
+    def eval_sigma(self, x, stream=None):
+        """sigma(x) [n] and grad sigma [n, 3] of a sigma(x) mesh (lsm_eval_sigma)."""
+        xs = _as(x, np.float64)
+        n = int(xs.shape[0])
+        if _is_torch(xs):
+            import torch
+            sg = torch.empty(n, dtype=torch.float64, device=xs.device)
+            gs = torch.empty((n, 3), dtype=torch.float64, device=xs.device)
+        else:
+            sg, gs = np.empty(n), np.empty((n, 3))
+        rc = self.ctx._L.lsm_eval_sigma(self._h, _ptr(xs), n, _ptr(sg), _ptr(gs), _stream_handle(stream))
+        self.ctx._check(rc)
+        return sg, gs
+
+    @property
+    def sigma0(self) -> float:
+        """sigma0 of a sigma(x) mesh (0 otherwise)."""
+        out = ctypes.c_double()
+        self.ctx._check(self.ctx._L.lsm_mesh_get_sigma0(self._h, ctypes.byref(out)))
+        return out.value
 
     def info(self) -> dict:
         inf = _Info()

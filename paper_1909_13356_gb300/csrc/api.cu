@@ -440,6 +440,108 @@ int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* 
     return LSM_OK;
 }
 
+int lsm_mesh_upload_sigmax(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                           double lambda, double sigma0, const lsm_quad* rule, void* stream, lsm_mesh** out)
+{
+    if (!c || !out) return LSM_E_INVALID_ARG;
+    *out = nullptr;
+    Ctx* ctx = &c->c;
+    if (!verts || !tris || nv < 3 || nt < 4 || lambda < 0 || sigma0 < 0 || !std::isfinite(lambda) ||
+        !std::isfinite(sigma0)) {
+        ctx->err = "mesh_upload_sigmax: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    // sigma_j = D_j / lambda and the centroids, on the host
+    std::vector<double> hv, sj(nt), cen(3 * (size_t)nt);
+    std::vector<int32_t> ht;
+    const double* vp = verts;
+    const int32_t* tp = tris;
+    if (is_device_ptr(verts)) {
+        hv.resize(3 * (size_t)nv);
+        LSM_CUDA_TRY(ctx, cudaMemcpy(hv.data(), verts, sizeof(double) * 3 * nv, cudaMemcpyDeviceToHost));
+        vp = hv.data();
+    }
+    if (is_device_ptr(tris)) {
+        ht.resize(3 * (size_t)nt);
+        LSM_CUDA_TRY(ctx, cudaMemcpy(ht.data(), tris, sizeof(int32_t) * 3 * nt, cudaMemcpyDeviceToHost));
+        tp = ht.data();
+    }
+    for (int64_t k = 0; k < 3 * nt; k++)
+        if (tp[k] < 0 || tp[k] >= nv) {
+            ctx->err = "mesh_upload_sigmax: vertex index out of range";
+            return LSM_E_MESH;
+        }
+    const double lam = lambda > 0 ? lambda : 2.5;
+    const double dmax = sigma_sources_host(vp, tp, nt, lam, sj.data(), cen.data());
+    // default sigma0: a centroid one diameter away weighs 1/2
+    const double s0 = sigma0 > 0 ? sigma0 : dmax / std::sqrt(2.0 * std::log(2.0));
+    if (!(dmax > 0) || !(s0 > 0)) {
+        ctx->err = "mesh_upload_sigmax: degenerate triangles";
+        return LSM_E_MESH;
+    }
+    lsm_mesh* mh = nullptr;
+    int rc = lsm_mesh_upload(c, verts, nv, tris, nt, sj.data(), rule, stream, &mh);
+    if (rc != LSM_OK) return rc;
+    rc = sigma_attach(ctx, &mh->m, sj.data(), cen.data(), nt, s0, (cudaStream_t)stream);
+    if (rc != LSM_OK) {
+        lsm_mesh_free(mh);
+        return rc;
+    }
+    *out = mh;
+    return LSM_OK;
+}
+
+int lsm_eval_sigma(lsm_mesh* mh, const double* x, int64_t n, double* sigma, double* gsigma, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (n == 0) return LSM_OK;
+    if (!me->sigx || n < 0 || n >= ((int64_t)1 << 31) || !x || !sigma) {
+        ctx->err = "eval_sigma: bad arguments (or not a sigma(x) mesh)";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ni = (int)n;
+    Scratch s(st);
+    const double* xd;
+    int rc = to_device(ctx, s, x, 3 * (size_t)n, &xd, st);
+    if (rc) return rc;
+    uint32_t* perm;
+    double *T, *R;
+    LSM_CUDA_TRY(ctx, s.get(&perm, n));
+    LSM_CUDA_TRY(ctx, s.get(&T, 3 * (size_t)n));
+    LSM_CUDA_TRY(ctx, s.get(&R, 4 * (size_t)n));
+    rc = morton_order_points(ctx, xd, 3, ni, perm, st);
+    if (rc) return rc;
+    k_gather_points<<<(ni + 255) / 256, 256, 0, st>>>(xd, perm, ni, T);
+    LSM_LAUNCHED(ctx);
+    Targets tg{T, n, ni};
+    rc = sigma_x_eval(ctx, me, tg, R, R + n, st);
+    if (rc) return rc;
+    const bool sdev = is_device_ptr(sigma);
+    const bool gdev = gsigma && is_device_ptr(gsigma);
+    double* sd = sigma;
+    double* gd = gsigma;
+    if (!sdev) LSM_CUDA_TRY(ctx, s.get(&sd, n));
+    if (gsigma && !gdev) LSM_CUDA_TRY(ctx, s.get(&gd, 3 * (size_t)n));
+    k_scatter_results<<<(ni + 255) / 256, 256, 0, st>>>(R, perm, ni, sd, gd);
+    LSM_LAUNCHED(ctx);
+    if (!sdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(sigma, sd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (gsigma && !gdev)
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(gsigma, gd, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    return check_flag(ctx, st);
+}
+
+int lsm_mesh_get_sigma0(const lsm_mesh* mh, double* sigma0)
+{
+    if (!mh || !sigma0) return LSM_E_INVALID_ARG;
+    *sigma0 = mh->m.sigx ? mh->m.sigma0 : 0.0;
+    return LSM_OK;
+}
+
 int lsm_mesh_free(lsm_mesh* mh)
 {
     if (!mh) return LSM_E_INVALID_ARG;
@@ -449,6 +551,8 @@ int lsm_mesh_free(lsm_mesh* mh)
     me->tree = nullptr;
     tree_free(me->tree_ff);
     me->tree_ff = nullptr;
+    for (void* p : {(void*)me->cent, (void*)me->cent_lo, (void*)me->cent_hi})
+        if (p) cudaFree(p);
     void* ps[] = {me->verts, me->tris, me->tri_sigma, me->tri_n, me->vpn, me->s64_pos, me->s64_nw,
                   me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, me->tile_lo, me->tile_hi, me->tile_chi, me->tile_clo};
     for (void* p : ps)

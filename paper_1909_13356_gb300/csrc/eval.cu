@@ -103,6 +103,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 constexpr int kWaitLimit = 1 << 22;
+constexpr double kSqrt2 = 1.41421356237309505;
+// 1 / (2 sqrt2 pi^(3/2)): dPhi/dsigma = -(4 a^4 / (2 sqrt2 pi^(3/2))) sum (nw' . r) e^{-u^2} 4 pi
+// with nw' = nw / 4 pi and sigma = 1 / (sqrt2 a), i.e. -16 pi a^4 kSigC sum (nw' . r) e^{-w}
+constexpr double kSigC = 0.063493635934240970;
+constexpr double kFourPiD = 12.566370614359172954;
 constexpr int kChunk = 64;  // far-tile sources summed in FP32 before compensation
 constexpr int kErrWaitTimeout = 1;
 
@@ -246,6 +251,28 @@ __device__ __forceinline__ void block_bbox(float lo[3], float hi[3], float* s)
     __syncthreads();
 }
 
+// Block-wide max of one float, result in *dst (shared); all threads call.
+__device__ __forceinline__ void block_max1(float v, float* dst)
+{
+    __shared__ float part[kEvalThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = part[0];
+        for (int k = 1; k < kEvalThreads / 32; k++) m = fmaxf(m, part[k]);
+        *dst = m;
+    }
+    __syncthreads();
+}
+
+// The tile box with the near-field width replaced by the target block's
+// largest sigma (sigma(x) mode).
+__device__ __forceinline__ float4 with_sigma(float4 lo, float smax)
+{
+    return make_float4(lo.x, lo.y, lo.z, smax);
+}
+
 // True when every pair between the target block box and the source tile box
 // is at least cutoff * sigma_max(tile) apart (conservative in FP32).
 __device__ __forceinline__ bool tile_is_far(const float* bb, float4 lo, float4 hi, float cut2)
@@ -258,6 +285,9 @@ __device__ __forceinline__ bool tile_is_far(const float* bb, float4 lo, float4 h
 }
 
 struct EvalArgs {
+    // sigma(x) mode: the targets' sigma [nt] and grad sigma [3][nt] (sorted order)
+    const double* tsig = nullptr;
+    const double* tgsig = nullptr;
     const float4* tlo;
     const float4* thi;
     const float4* tchi;
@@ -421,7 +451,7 @@ __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const 
 }
 
 // ---------------------------------------------------------------- mixed kernel
-template <int TPT>
+template <int TPT, bool SIGX>
 __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __restrict__ spos,
                                                             const float4* __restrict__ snw,
                                                             const float4* __restrict__ slo,
@@ -434,6 +464,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
     __shared__ __align__(16) float4 s_htab[kHTabN * 3];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float s_bb[6];
+    __shared__ float s_smax;
 
     const int tid = threadIdx.x;
     int base, tend, t0, t1;
@@ -480,6 +511,26 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         nvalid += i < tend ? 1 : 0;
     }
     block_bbox(lo, hi, s_bb);
+    // sigma(x) mode: each target's a = 1/(sqrt2 sigma(x)) as a float pair, and
+    // the block's largest sigma for the near/far split
+    float ta_h[TPT], ta_l[TPT], dsum_h[TPT], dsum_l[TPT];
+#pragma unroll
+    for (int k = 0; k < TPT; k++) ta_h[k] = ta_l[k] = dsum_h[k] = dsum_l[k] = 0.0f;
+    if constexpr (SIGX) {
+        float smax = 0.0f;
+#pragma unroll
+        for (int k = 0; k < TPT; k++) {
+            const int i = base + k * kEvalThreads + tid;
+            if (i < tend) {
+                const double sg = A.tsig[i];
+                const double a = 1.0 / (kSqrt2 * sg);
+                ta_h[k] = (float)a;
+                ta_l[k] = (float)(a - (double)ta_h[k]);
+                smax = fmaxf(smax, __double2float_ru(sg));
+            }
+        }
+        block_max1(smax, &s_smax);
+    }
 
     float acc_h[TPT][4], acc_l[TPT][4];
 #pragma unroll
@@ -500,7 +551,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         const int cnt = (int)A.thi[t].w;
         const uint32_t bytes = (uint32_t)cnt * 16u;
         const bool proxy = t >= A.ntiles;
-        const bool far = proxy || tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+        const bool far = proxy || tile_is_far(s_bb, SIGX ? with_sigma(A.tlo[t], s_smax) : A.tlo[t], A.thi[t], A.cut2);
         mbar_expect_tx(&bar[b], (far ? 2u : 4u) * bytes);
         const float4* gp = proxy ? A.ppos + (size_t)(t - A.ntiles) * kTile : spos + (size_t)t * kTile;
         const float4* gn = proxy ? A.pnw + (size_t)(t - A.ntiles) * kTile : snw + (size_t)t * kTile;
@@ -531,7 +582,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         const float4 tl = A.tlo[t], th = A.thi[t];
         const float4 ch = A.tchi[t], cl = A.tclo[t];
         const int cnt = (int)A.thi[t].w;
-        const bool far = t >= A.ntiles || tile_is_far(s_bb, tl, th, A.cut2);
+        const bool far = t >= A.ntiles || tile_is_far(s_bb, SIGX ? with_sigma(tl, s_smax) : tl, th, A.cut2);
         const float4* sp = sh_pos[b];
         const float4* sn = sh_nw[b];
         if (far) {
@@ -657,6 +708,9 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                 cph[k] = cpl[k] = 0.0f;
                 for (int c = 0; c < 3; c++) cg[k][c] = cgl[k][c] = 0.0f;
             }
+            float cd[TPT];   // sigma(x) mode: this tile's sum of (nw . r) e^{-w}
+#pragma unroll
+            for (int k = 0; k < TPT; k++) cd[k] = 0.0f;
 #pragma unroll 1
             for (int s = 0; s < cnt; s++) {
                 const float4 y = sp[s];
@@ -665,18 +719,29 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                 const float4 nl = snl[s];
 #pragma unroll
                 for (int k = 0; k < TPT; k++) {
+                    // the pair's a: the source's, or the target's in sigma(x) mode
+                    const float4 ya = SIGX ? make_float4(y.x, y.y, y.z, ta_h[k]) : y;
+                    const float4 yla = SIGX ? make_float4(yl.x, yl.y, yl.z, ta_l[k]) : yl;
                     float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
-                    ff_pair(y, n, yl, nl, qh[k], ql[k], false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
+                    ff_pair(ya, n, yla, nl, qh[k], ql[k], false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
                     float sph, tph;
                     two_sum(cph[k], qh_, sph, tph);
                     cph[k] = sph;
                     cpl[k] += tph + ql_;
                     float fH, FK;
-                    radial_tab32(rh, y.w, s_htab, fH, FK);
+                    radial_tab32(rh, ya.w, s_htab, fH, FK);
                     const float tq = dh * FK;
                     two_sum_acc(cg[k][0], cgl[k][0], -fmaf(n.x, fH, tq * dxh));
                     two_sum_acc(cg[k][1], cgl[k][1], -fmaf(n.y, fH, tq * dyh));
                     two_sum_acc(cg[k][2], cgl[k][2], -fmaf(n.z, fH, tq * dzh));
+                    if constexpr (SIGX) cd[k] = fmaf(dh, expf(-rh * ya.w * ya.w), cd[k]);
+                }
+            }
+            if constexpr (SIGX) {
+#pragma unroll
+                for (int k = 0; k < TPT; k++) {
+                    two_sum_acc(dsum_h[k], dsum_l[k], cd[k]);
+                    renorm(dsum_h[k], dsum_l[k]);
                 }
             }
 #pragma unroll
@@ -704,15 +769,26 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
     for (int k = 0; k < TPT; k++) {
         const int i = base + k * kEvalThreads + tid;
         if (i < tend) {
+            double r[4];
 #pragma unroll
-            for (int c = 0; c < 4; c++) out[c * plane + i] = (double)acc_h[k][c] + (double)acc_l[k][c];
+            for (int c = 0; c < 4; c++) r[c] = (double)acc_h[k][c] + (double)acc_l[k][c];
+            if constexpr (SIGX) {
+                // grad Phi += (dPhi/dsigma) grad sigma (eq. gradPhi, third term)
+                const double a = (double)ta_h[k] + (double)ta_l[k];
+                const double a2 = a * a;
+                const double dps = -4.0 * kFourPiD * kSigC * a2 * a2 * ((double)dsum_h[k] + (double)dsum_l[k]);
+#pragma unroll
+                for (int c = 0; c < 3; c++) r[c + 1] += dps * A.tgsig[c * plane + i];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) out[c * plane + i] = r[c];
         }
     }
     count_pairs(A.pairs, pairs_near, pairs_far);
 }
 
 // ---------------------------------------------------------------- FP64 kernel
-template <int TPT>
+template <int TPT, bool SIGX>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* __restrict__ spos,
                                                            const double4_32a* __restrict__ snw, EvalArgs A)
 {
@@ -720,6 +796,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
     __shared__ __align__(128) double4_32a sh_nw[2][kTile];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float s_bb[6];
+    __shared__ float s_smax;
 
     const int tid = threadIdx.x;
     int base, tend, t0, t1;
@@ -753,6 +830,27 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
         }
     }
     block_bbox(lo, hi, s_bb);
+    // sigma(x) mode: each target's a = 1/(sqrt2 sigma(x)) and sqrt2 sigma(x)
+    double ta[TPT], ts2[TPT], dsum[TPT], dsuml[TPT];
+#pragma unroll
+    for (int k = 0; k < TPT; k++) ta[k] = ts2[k] = dsum[k] = dsuml[k] = 0.0;
+    if constexpr (SIGX) {
+        float smax = 0.0f;
+#pragma unroll
+        for (int k = 0; k < TPT; k++) {
+            const int i = base + k * kEvalThreads + tid;
+            if (i < tend) {
+                const double sg = A.tsig[i];
+                ts2[k] = kSqrt2 * sg;
+                ta[k] = 1.0 / ts2[k];
+                smax = fmaxf(smax, __double2float_ru(sg));
+            } else {
+                ts2[k] = 1.0;
+                ta[k] = 1.0;
+            }
+        }
+        block_max1(smax, &s_smax);
+    }
 
     double acc[TPT][4], accl[TPT][4];   // running sums, double-double
 #pragma unroll
@@ -793,7 +891,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
         }
         const float4 tl = A.tlo[t], th = A.thi[t];
         const int cnt = (int)A.thi[t].w;
-        const bool far = tile_is_far(s_bb, tl, th, A.cut2);
+        const bool far = tile_is_far(s_bb, SIGX ? with_sigma(tl, s_smax) : tl, th, A.cut2);
         const double4_32a* sp = sh_pos[b];
         const double4_32a* sn = sh_nw[b];
         if (far) pairs_far += (unsigned long long)cnt * nvalid;
@@ -823,6 +921,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
                 }
             }
         } else {
+            double pd[TPT];   // sigma(x) mode: this tile's sum of (nw . r) e^{-w}
+#pragma unroll
+            for (int k = 0; k < TPT; k++) pd[k] = 0.0;
             for (int s = 0; s < cnt; s++) {
                 const double4_32a y = sp[s];
                 const double4_32a n = sn[s];
@@ -831,14 +932,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
                     const double dx = y.x - x[k][0], dy = y.y - x[k][1], dz = y.z - x[k][2];
                     const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
                     double fH, FK;
-                    radial64(r2, y.w, n.w, fH, FK);
+                    // the pair's a and sqrt2 sigma: the source's, or the target's
+                    radial64(r2, SIGX ? ta[k] : y.w, SIGX ? ts2[k] : n.w, fH, FK);
                     const double d = fma(n.x, dx, fma(n.y, dy, n.z * dz));
                     p[k][0] = fma(d, fH, p[k][0]);
                     const double tq = d * FK;
                     p[k][1] -= fma(n.x, fH, tq * dx);
                     p[k][2] -= fma(n.y, fH, tq * dy);
                     p[k][3] -= fma(n.z, fH, tq * dz);
+                    if constexpr (SIGX) pd[k] = fma(d, exp(-r2 * ta[k] * ta[k]), pd[k]);
                 }
+            }
+            if constexpr (SIGX) {
+#pragma unroll
+                for (int k = 0; k < TPT; k++) two_sum_acc64(dsum[k], dsuml[k], pd[k]);
             }
         }
 #pragma unroll
@@ -853,8 +960,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
     for (int k = 0; k < TPT; k++) {
         const int i = base + k * kEvalThreads + tid;
         if (i < tend) {
+            double r[4];
 #pragma unroll
-            for (int c = 0; c < 4; c++) out[c * plane + i] = acc[k][c] + accl[k][c];
+            for (int c = 0; c < 4; c++) r[c] = acc[k][c] + accl[k][c];
+            if constexpr (SIGX) {
+                // grad Phi += (dPhi/dsigma) grad sigma (eq. gradPhi, third term)
+                const double a2 = ta[k] * ta[k];
+                const double dps = -4.0 * kFourPiD * kSigC * a2 * a2 * (dsum[k] + dsuml[k]);
+#pragma unroll
+                for (int c = 0; c < 3; c++) r[c + 1] += dps * A.tgsig[c * plane + i];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) out[c * plane + i] = r[c];
         }
     }
     count_pairs(A.pairs, pairs_near, pairs_far);
@@ -874,6 +991,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
 constexpr int kFFStage = kTile * 64;  // bytes per stage: 4 float4 arrays
 constexpr int kMaxNearTiles = 768;    // near-tile list of one block (incremental mode)
 
+template <bool SIGX>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     const float4* __restrict__ spos, const float4* __restrict__ snw, const float4* __restrict__ slo,
     const float4* __restrict__ snwlo, EvalArgs A)
@@ -885,6 +1003,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     __shared__ int s_near[kMaxNearTiles];
     __shared__ int s_warp[kEvalThreads / 32];
     __shared__ int s_nnear;
+    __shared__ float s_smax;
 
     const int tid = threadIdx.x;
     int base, tend, t0, t1;
@@ -928,6 +1047,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         }
     }
     block_bbox(lo, hi, s_bb);   // also orders the table fill before its first use
+    // sigma(x) mode: the target's a = 1/(sqrt2 sigma(x)) as a float pair, and
+    // the block's largest sigma for the near/far split
+    float ta_h = 0.0f, ta_l = 0.0f, dsum_h = 0.0f, dsum_l = 0.0f;
+    if constexpr (SIGX) {
+        float smax = 0.0f;
+        if (valid) {
+            const double sg = A.tsig[i];
+            const double a = 1.0 / (kSqrt2 * sg);
+            ta_h = (float)a;
+            ta_l = (float)(a - (double)ta_h);
+            smax = __double2float_ru(sg);
+        }
+        block_max1(smax, &s_smax);
+    }
 
     // incremental mode: the block's near tiles, in tile order
     int nlist = t1 - t0;
@@ -937,7 +1070,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         const int lane = tid & 31, wp = tid >> 5;
         for (int tb = t0; tb < t1; tb += kEvalThreads) {
             const int t = tb + tid;
-            const bool nr = t < t1 && !tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+            const bool nr = t < t1 && !tile_is_far(s_bb, SIGX ? with_sigma(A.tlo[t], s_smax) : A.tlo[t], A.thi[t], A.cut2);
             const unsigned bal = __ballot_sync(0xffffffffu, nr);
             if (lane == 0) s_warp[wp] = __popc(bal);
             __syncthreads();
@@ -1000,7 +1133,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             break;
         }
         const int cnt = (int)A.thi[t].w;
-        const bool far = t >= A.ntiles || tile_is_far(s_bb, A.tlo[t], A.thi[t], A.cut2);
+        const bool far =
+            t >= A.ntiles || tile_is_far(s_bb, SIGX ? with_sigma(A.tlo[t], s_smax) : A.tlo[t], A.thi[t], A.cut2);
         if (far) pairs_far += valid ? cnt : 0;
         else pairs_near += valid ? cnt : 0;
         const float4 ch = A.tchi[t], cl = A.tclo[t];
@@ -1022,9 +1156,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             const int c1 = min(cnt, c0 + kChunk);
             float g[3] = {0.0f, 0.0f, 0.0f}, gn[3] = {0.0f, 0.0f, 0.0f};
             float cph = 0.0f, cpl = 0.0f;   // this chunk's Phi, float-float
+            float cd = 0.0f;                // sigma(x) mode: sum of (nw . r) e^{-w}
 #pragma unroll 2
             for (int s = c0; s < c1; s++) {
-                const float4 y = sp[s], n = sn[s], yl = sl[s], nl = snl[s];
+                const float4 y0 = sp[s], n = sn[s], yl0 = sl[s], nl = snl[s];
+                // the pair's a: the source's, or the target's in sigma(x) mode
+                const float4 y = SIGX ? make_float4(y0.x, y0.y, y0.z, ta_h) : y0;
+                const float4 yl = SIGX ? make_float4(yl0.x, yl0.y, yl0.z, ta_l) : yl0;
                 float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
                 ff_pair(y, n, yl, nl, qh, ql, far, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
                 float sph, tph;
@@ -1047,6 +1185,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                     two_sum_acc(g[0], gn[0], -fmaf(n.x, fH, tq * dxh));
                     two_sum_acc(g[1], gn[1], -fmaf(n.y, fH, tq * dyh));
                     two_sum_acc(g[2], gn[2], -fmaf(n.z, fH, tq * dzh));
+                    if constexpr (SIGX) cd = fmaf(dh, expf(-rh * y.w * y.w), cd);
+                }
+            }
+            if constexpr (SIGX) {
+                if (!far) {
+                    two_sum_acc(dsum_h, dsum_l, cd);
+                    renorm(dsum_h, dsum_l);
                 }
             }
             // fold the chunk into the running float-float sums, renormalised
@@ -1100,6 +1245,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             }
             phi += fphi;
             for (int c = 0; c < 3; c++) gr[c] += fgr[c];
+        }
+        if constexpr (SIGX) {
+            // grad Phi += (dPhi/dsigma) grad sigma (eq. gradPhi, third term)
+            const double a = (double)ta_h + (double)ta_l;
+            const double a2 = a * a;
+            const double dps = -4.0 * kFourPiD * kSigC * a2 * a2 * ((double)dsum_h + (double)dsum_l);
+            for (int c = 0; c < 3; c++) gr[c] += dps * A.tgsig[c * plane + i];
         }
         out[i] = phi;
         for (int c = 0; c < 3; c++) out[(c + 1) * plane + i] = gr[c];
@@ -1241,6 +1393,14 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     nsplit = (ntiles + tps - 1) / tps;
 
     Scratch s(st);
+    // sigma(x) mode: sigma and grad sigma of the sorted targets
+    double *tsig = nullptr, *tgsig = nullptr;
+    if (me->sigx) {
+        LSM_CUDA_TRY(ctx, s.get(&tsig, (size_t)t.n));
+        LSM_CUDA_TRY(ctx, s.get(&tgsig, 3 * (size_t)t.n));
+        int rc = sigma_x_eval(ctx, me, t, tsig, tgsig, st);
+        if (rc != LSM_OK) return rc;
+    }
     // mixed path on a large mesh: the treecode's interaction lists
     int* list = nullptr;
     int2* blist = nullptr;
@@ -1252,7 +1412,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff);
         if (rc != LSM_OK) return rc;
         int64_t total = 0;
-        rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, s, &list, &blist, &border, &total, st);
+        rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, tsig, s, &list, &blist, &border, &total, st);
         if (rc != LSM_OK) return rc;
         const int64_t avg = total / nblk;
         nsplit = 1;
@@ -1301,6 +1461,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         A.plo = T->p_lo;
         A.pnwlo = T->p_nwlo;
     }
+    A.tsig = tsig;
+    A.tgsig = tgsig;
     dim3 grid(nblk, nsplit);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (ctx->profiling) {
@@ -1308,12 +1470,21 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         LSM_CUDA_TRY(ctx, cudaEventCreate(&ev1));
         LSM_CUDA_TRY(ctx, cudaEventRecord(ev0, st));
     }
-    if (mixed) {
-        k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
+    if (me->sigx) {
+        if (mixed)
+            k_eval_mixed<kTPT32, true><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
+                                                                      me->s32_nwlo, A);
+        else if (ff)
+            k_eval_ff<true><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
+        else
+            k_eval_fp64<kTPT64, true><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
+    } else if (mixed) {
+        k_eval_mixed<kTPT32, false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
+                                                                   me->s32_nwlo, A);
     } else if (ff) {
-        k_eval_ff<<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
+        k_eval_ff<false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else {
-        k_eval_fp64<kTPT64><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
+        k_eval_fp64<kTPT64, false><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
     }
     LSM_LAUNCHED(ctx);
     if (ctx->profiling) {
@@ -1356,11 +1527,12 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
     A.far_io = nullptr;
     A.x_old = nullptr;
     if (mixed) {
-        k_eval_mixed<kTPT32><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
+        k_eval_mixed<kTPT32, false><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo,
+                                                                        A);
     } else if (precision == LSM_FF) {
-        k_eval_ff<<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
+        k_eval_ff<false><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
     } else {
-        k_eval_fp64<kTPT64><<<max_items, kEvalThreads, 0, st>>>(v.s64_pos, v.s64_nw, A);
+        k_eval_fp64<kTPT64, false><<<max_items, kEvalThreads, 0, st>>>(v.s64_pos, v.s64_nw, A);
     }
     LSM_LAUNCHED(ctx);
     return LSM_OK;
@@ -1424,6 +1596,10 @@ int eval_noalloc(Ctx* ctx, const Mesh* me, const double* x, int64_t n, double* p
     }
     if (!x || !phi || (precision != LSM_FP64 && precision != LSM_MIXED)) {
         ctx->err = "eval_phi_grad_noalloc: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    if (me->sigx) {
+        ctx->err = "eval_phi_grad_noalloc: meshes with a target-dependent sigma are not supported";
         return LSM_E_INVALID_ARG;
     }
     if (!on_device(x) || !on_device(phi) || (grad && !on_device(grad))) {
@@ -1492,9 +1668,10 @@ int eval_noalloc(Ctx* ctx, const Mesh* me, const double* x, int64_t n, double* p
     A.x_old = nullptr;
     dim3 grid(nblk, nsplit);
     if (mixed) {
-        k_eval_mixed<kTPT32><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
+        k_eval_mixed<kTPT32, false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
+                                                                   me->s32_nwlo, A);
     } else {
-        k_eval_fp64<kTPT64><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
+        k_eval_fp64<kTPT64, false><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
     }
     LSM_LAUNCHED(ctx);
     if (nsplit > 1) {

@@ -65,6 +65,13 @@ struct Mesh {
     Ctx* ctx = nullptr;
     Tree* tree = nullptr;        // treecode far field of the mixed path, built on first use
     Tree* tree_ff = nullptr;     // and of the float-float path
+    // target-dependent sigma (eq. sigma2): centroids in Morton order (x, y, z,
+    // sigma_j), in tiles of kTile with outward-rounded boxes
+    bool sigx = false;
+    double sigma0 = 0.0;
+    int64_t ncent = 0, ncent_tiles = 0;
+    double4_32a* cent = nullptr;
+    float4 *cent_lo = nullptr, *cent_hi = nullptr;
     // far-field choice stored by the autotuner: -1 follow the context's
     // options, 0 direct, 1 treecode with tune_degree / tune_theta
     int tune_mode = -1;
@@ -251,8 +258,9 @@ void tree_free(Tree* t);
 // tile ids list[blist[b].x .. + blist[b].y) in tree order; order = the
 // blocks by decreasing list length (the launch order); *total = the summed
 // list length.
-int tree_lists(Ctx* ctx, const Tree* tree, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
-               int** order, int64_t* total, cudaStream_t st);
+// tsig: the targets' sigma in sigma(x) mode (the near width), else NULL.
+int tree_lists(Ctx* ctx, const Tree* tree, const Targets& t, int tpb, const double* tsig, Scratch& s, int** list,
+               int2** blist, int** order, int64_t* total, cudaStream_t st);
 
 // frames.cu: chart local coordinates and the Gauss flux (lsm_chart_frames,
 // lsm_gauss_flux); all arrays on the device, nodes in solve order
@@ -260,6 +268,14 @@ int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const 
                      double* jac, cudaStream_t st);
 int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const double* g, const double* jac,
                    const double* x0, double* eps0, cudaStream_t st);
+
+// sigma.cu: target-dependent sigma (eq. sigma2)
+double sigma_sources_host(const double* verts, const int32_t* tris, int64_t nt, double lambda, double* sj,
+                          double* cen);
+int sigma_attach(Ctx* ctx, Mesh* me, const double* sj, const double* cen, int64_t nt, double sigma0,
+                 cudaStream_t st);
+// sigma(x) [n] and grad sigma [3][n] (SoA) at sorted targets
+int sigma_x_eval(Ctx* ctx, const Mesh* me, const Targets& t, double* sig, double* gsig, cudaStream_t st);
 
 // tune.cu: the autotuner on sorted SoA targets (lsm_autotune)
 int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tune_result* res, cudaStream_t st);

@@ -407,12 +407,14 @@ __global__ void k_p2m_reduce(const int4* __restrict__ red, const int4* __restric
 // Box of each block of tpb consecutive sorted targets, FP32 rounded outward
 // (the same box the pair kernels compute for the block).
 __global__ void __launch_bounds__(kEvalThreads) k_block_boxes(const double* __restrict__ x, int64_t ld, int n,
-                                                              int tpb, float4* __restrict__ blo,
-                                                              float4* __restrict__ bhi)
+                                                              int tpb, const double* __restrict__ tsig,
+                                                              float4* __restrict__ blo, float4* __restrict__ bhi)
 {
     __shared__ float part[6][kEvalThreads / 32];
+    __shared__ float psig[kEvalThreads / 32];
     const int b = blockIdx.x;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float smax = 0.0f;   // sigma(x) mode: the block's largest target sigma
     for (int j = threadIdx.x; j < tpb; j += kEvalThreads) {
         const int64_t i = (int64_t)b * tpb + j;
         if (i >= n) break;
@@ -421,7 +423,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_block_boxes(const double* __re
             lo[c] = fminf(lo[c], __double2float_rd(v));
             hi[c] = fmaxf(hi[c], __double2float_ru(v));
         }
+        if (tsig) smax = fmaxf(smax, __double2float_ru(tsig[i]));
     }
+    for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    if ((threadIdx.x & 31) == 0) psig[threadIdx.x >> 5] = smax;
     for (int c = 0; c < 3; c++)
         for (int o = 16; o > 0; o >>= 1) {
             lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
@@ -440,7 +445,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_block_boxes(const double* __re
                 part[c][0] = fminf(part[c][0], part[c][k]);
                 part[3 + c][0] = fmaxf(part[3 + c][0], part[3 + c][k]);
             }
-        blo[b] = make_float4(part[0][0], part[1][0], part[2][0], 0.0f);
+        float sm = psig[0];
+        for (int k = 1; k < kEvalThreads / 32; k++) sm = fmaxf(sm, psig[k]);
+        blo[b] = make_float4(part[0][0], part[1][0], part[2][0], sm);
         bhi[b] = make_float4(part[3][0], part[4][0], part[5][0], 0.0f);
     }
 }
@@ -455,6 +462,7 @@ struct WalkArgs {
     int64_t lev_off[kMaxLevels + 1];
     int top;
     int ntiles;
+    int sigx;              // sigma(x) mode: the near width is the block's (blo.w)
     float theta2, cut2;
     const uint32_t* off;   // pass 1: list offset of each block
     uint32_t* cnt;         // pass 0: list length of each block
@@ -484,7 +492,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass
             const float gx = fmaxf(0.0f, fmaxf(lo.x - bh.x, bl.x - hi.x));
             const float gy = fmaxf(0.0f, fmaxf(lo.y - bh.y, bl.y - hi.y));
             const float gz = fmaxf(0.0f, fmaxf(lo.z - bh.z, bl.z - hi.z));
-            if (gx * gx + gy * gy + gz * gz > A.cut2 * lo.w * lo.w * 1.0001f) {
+            const float sw = A.sigx ? bl.w : lo.w;
+            if (gx * gx + gy * gy + gz * gz > A.cut2 * sw * sw * 1.0001f) {
                 const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
                 const float ex = hi.x - lo.x, ey = hi.y - lo.y, ez = hi.z - lo.z;
                 const float r2 = 0.25f * (ex * ex + ey * ey + ez * ez);
@@ -755,8 +764,8 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     return LSM_OK;
 }
 
-int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, Scratch& s, int** list, int2** blist,
-               int** order, int64_t* total_out, cudaStream_t st)
+int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double* tsig, Scratch& s, int** list,
+               int2** blist, int** order, int64_t* total_out, cudaStream_t st)
 {
     const int nblk = (t.n + tpb - 1) / tpb;
     float4 *blo = nullptr, *bhi = nullptr;
@@ -765,7 +774,7 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, Scratch& s, i
     LSM_CUDA_TRY(ctx, s.get(&bhi, nblk));
     LSM_CUDA_TRY(ctx, s.get(&cnt, (size_t)nblk + 1));
     LSM_CUDA_TRY(ctx, s.get(blist, nblk));
-    k_block_boxes<<<nblk, kEvalThreads, 0, st>>>(t.x, t.ld, t.n, tpb, blo, bhi);
+    k_block_boxes<<<nblk, kEvalThreads, 0, st>>>(t.x, t.ld, t.n, tpb, tsig, blo, bhi);
     LSM_LAUNCHED(ctx);
     WalkArgs W;
     W.blo = blo;
@@ -777,6 +786,7 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, Scratch& s, i
     for (int l = 0; l <= kMaxLevels; l++) W.lev_off[l] = l <= T->top + 1 ? T->lev_off[l] : 0;
     W.top = T->top;
     W.ntiles = T->ntiles;
+    W.sigx = tsig != nullptr;
     W.theta2 = T->theta * T->theta;
     // the near radius of the pair kernel that evaluates the lists
     const double cut = T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed;
