@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--tmax", type=float, default=1e4)
     ap.add_argument("--tree-degree", type=int, default=0, help="treecode degree (0: library default)")
     ap.add_argument("--tree-theta", type=float, default=0.0, help="treecode opening parameter (0: default)")
+    ap.add_argument("--sigma-x", action="store_true",
+                    help="target-dependent sigma(x) (eq. sigma2, lambda 2.5) instead of per-triangle sigma")
     ap.add_argument("--no-charts", action="store_true", help="time the evaluation only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -152,19 +154,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, seconds: float, rule_n: int):
-    """The FP64 oracle (direct sum, all pairs) on a target sample, all host cores."""
+def cpu_baseline(w, seconds: float, rule_n: int, sigma_x: bool = False):
+    """The FP64 oracle (direct sum, all pairs) on a target sample, all host
+    cores; with sigma_x, sigma(x) and its gradient are part of each evaluation."""
     import oracle
     m = w["mesh"]
-    y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, rule_n, 0)
+    if sigma_x:
+        c, sj, dmax = oracle.sigma_sources(m.verts, m.tris)
+        s0 = oracle.sigma0_default(dmax)
+        y, nw, _ = oracle.sources(m.verts, m.tris, sj, rule_n, 0)
+
+        def run(xx):
+            sg, gs = oracle.sigma_x(c, sj, s0, xx)
+            oracle.phi_grad_sigx(y, nw, xx, sg, gs)
+    else:
+        y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, rule_n, 0)
+
+        def run(xx):
+            oracle.phi_grad(y, nw, sg, xx)
     x = w["targets"]
     ncal = 8 * (os.cpu_count() or 1)
     t0 = time.perf_counter()
-    oracle.phi_grad(y, nw, sg, x[:ncal])
+    run(x[:ncal])
     dt = time.perf_counter() - t0
     n = int(max(ncal, min(len(x), ncal * seconds / max(dt, 1e-6))))
     t0 = time.perf_counter()
-    oracle.phi_grad(y, nw, sg, x[:n])
+    run(x[:n])
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{n} of {len(x)} targets, full FP64 direct sum over {len(y)} source nodes "
@@ -413,7 +428,10 @@ def main():
     w = workload(args, rank)
     m = w["mesh"]
     ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta)
-    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
+    if args.sigma_x:
+        mesh = ctx.upload_sigma_x(m.verts, m.tris, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
+    else:
+        mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
     info = mesh.info()
     x_dev = torch.from_numpy(w["targets"]).to(dev)
     nt = x_dev.shape[0]
@@ -531,7 +549,7 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        cpu = cpu_baseline(w, args.cpu_seconds, w["rule"]["n"])
+        cpu = cpu_baseline(w, args.cpu_seconds, w["rule"]["n"], args.sigma_x)
 
     if rank == 0:
         st = last_stats
@@ -551,6 +569,8 @@ def main():
             "config": {"workload": w["name"], "triangles": m.m, "sources": info["n_sources"],
                        "targets": nt, "chart_order": args.order, "chart_nodes": st.n_nodes if st else 0,
                        "newton_tol": args.tol, "precision": args.precision, "autotune": tune,
+                       "sigma": ("sigma(x), eq. sigma2: lambda 2.5, sigma0 = max D / sqrt(2 ln 2) = "
+                                 f"{mesh.sigma0:.5g}" if args.sigma_x else "per triangle, 0.5 sqrt(2 area)"),
                        "parallelism": (f"{world} ranks, one independent torus (own seed) each"
                                        if world > 1 else "single GPU"),
                        "l2": "flushed (256 MB write) before each timed step"},

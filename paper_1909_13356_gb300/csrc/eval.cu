@@ -1398,7 +1398,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     if (me->sigx) {
         LSM_CUDA_TRY(ctx, s.get(&tsig, (size_t)t.n));
         LSM_CUDA_TRY(ctx, s.get(&tgsig, 3 * (size_t)t.n));
-        int rc = sigma_x_eval(ctx, me, t, tsig, tgsig, st);
+        int rc = sigma_x_eval(ctx, me, t, tsig, tgsig, st, mixed);
         if (rc != LSM_OK) return rc;
     }
     // mixed path on a large mesh: the treecode's interaction lists

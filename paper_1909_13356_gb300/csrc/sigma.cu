@@ -11,8 +11,8 @@
 // the boxes, the squared distance U within which every target of the block
 // has a centroid (the least, over tiles, of the farthest block-to-tile
 // distance), then sums only tiles whose nearest distance is below
-// U + 75 sigma0^2: a skipped centroid weighs less than e^-37.5 of each
-// target's nearest one.  The weights are taken relative to exp(-U / 2
+// U + 2 T sigma0^2: a skipped centroid weighs less than e^-T of each target's
+// nearest one (T = 37.5 for the FP64-accurate paths, 20 for the mixed path).  The weights are taken relative to exp(-U / 2
 // sigma0^2) (a common factor that cancels in the ratio), so nothing
 // underflows however far the targets are.  FP64 throughout.
 #include <algorithm>
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kSigThreads) k_sigma_x(const double4_32a* __re
                                                          const float4* __restrict__ clo,
                                                          const float4* __restrict__ chi, int64_t ncent, int ntile,
                                                          const double* __restrict__ x, int64_t ld, int n,
-                                                         double sigma0, double* __restrict__ sig,
+                                                         double sigma0, double tail, double* __restrict__ sig,
                                                          double* __restrict__ gsig)
 {
     __shared__ double4_32a sc[kTile];
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kSigThreads) k_sigma_x(const double4_32a* __re
     __syncthreads();
     const double U = (double)s_u;
     const double inv2s2 = 1.0 / (2.0 * sigma0 * sigma0);
-    const float reach2 = (float)(U + 75.0 * sigma0 * sigma0) * 1.0001f;
+    const float reach2 = (float)(U + 2.0 * tail * sigma0 * sigma0) * 1.0001f;
     double S0 = 0.0, S1 = 0.0, A[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
     // candidate tiles kSigThreads at a time: each thread tests one, the
     // block compacts the list in tile order, then sums the listed tiles
@@ -256,12 +256,16 @@ int sigma_attach(Ctx* ctx, Mesh* me, const double* sj, const double* cen, int64_
     return LSM_OK;
 }
 
-int sigma_x_eval(Ctx* ctx, const Mesh* me, const Targets& t, double* sig, double* gsig, cudaStream_t st)
+int sigma_x_eval(Ctx* ctx, const Mesh* me, const Targets& t, double* sig, double* gsig, cudaStream_t st,
+                 bool mixed)
 {
     if (t.n <= 0) return LSM_OK;
     const int nb = (t.n + kSigThreads - 1) / kSigThreads;
+    // truncation: e^-20 (2e-9 relative) suffices for the mixed path's 1e-7,
+    // e^-37.5 (5e-17) for the FP64-accurate ones
+    const double tail = mixed ? 20.0 : 37.5;
     k_sigma_x<<<nb, kSigThreads, 0, st>>>(me->cent, me->cent_lo, me->cent_hi, me->ncent, (int)me->ncent_tiles, t.x,
-                                          t.ld, t.n, me->sigma0, sig, gsig);
+                                          t.ld, t.n, me->sigma0, tail, sig, gsig);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }
