@@ -71,6 +71,10 @@ def _load():
             lib.or_phi_grad_sigx.argtypes = [I64, P, P, I64, P, P, P, P, P, ctypes.c_int]
             lib.or_solve_charts_sigx.argtypes = [I64, P, P, I64, P, P, ctypes.c_double, I64, P, P, P,
                                                  ctypes.c_double, ctypes.c_int, P, P, P, P, P, ctypes.c_int]
+            lib.or_radial_G.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.or_radial_G.restype = ctypes.c_double
+            lib.or_phi_grad_hess.argtypes = [I64, P, P, P, I64, P, P, P, P, ctypes.c_int]
+            lib.or_chart_second.argtypes = [P, I64, P, P, ctypes.c_int, P, P, P, P, P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -266,3 +270,40 @@ def solve_charts_sigx(y, nw, c, sj, sigma0, x0, hdir, sloc, tol: float = 1e-12, 
                                  _p(sloc), float(tol), int(max_iter), _p(xo), _p(ho), _p(st), _p(it), _p(dh),
                                  nthreads)
     return dict(x=xo, h=ho, status=st, iters=it, last_dh=dh)
+
+
+def radial_G(rho: float, sigma: float) -> float:
+    """Third radial factor G = F'(rho)/rho of the pair kernel."""
+    return _load().or_radial_G(float(rho), float(sigma))
+
+
+def phi_grad_hess(y, nw, sig, x, nthreads: int = 0):
+    """Phi, grad Phi and the Hessian [n, 6] = (xx, xy, xz, yy, yz, zz) by
+    direct summation (per-triangle sigma)."""
+    y, nw, sig, x = _f64(y), _f64(nw), _f64(sig), _f64(x)
+    nt = len(x)
+    phi, grad, hess = np.empty(nt), np.empty((nt, 3)), np.empty((nt, 6))
+    _load().or_phi_grad_hess(len(y), _p(y), _p(nw), _p(sig), nt, _p(x), _p(phi), _p(grad), _p(hess), nthreads)
+    return phi, grad, hess
+
+
+def chart_second(verts, tris, h, grad, hess, sigma=None, n: int = 6, uv=None):
+    """Second derivatives x_uu, x_uv, x_vv [N, 3] of the solved charts and the
+    mean (sum of principal curvatures) and Gaussian curvatures [N] of the
+    level set at the nodes (eq. uu_vector and its analogues)."""
+    verts = _f64(verts)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    geo = geometry(verts, tris, sigma)
+    if uv is None:
+        cu, cv, _ = simplex_rule(n, 0)
+    else:
+        cu, cv = _f64(uv[0]), _f64(uv[1])
+    h, grad, hess = _f64(h), _f64(grad), _f64(hess)
+    m, npn = len(tris), len(cu)
+    N = m * npn
+    assert h.shape == (N,) and grad.shape == (N, 3) and hess.shape == (N, 6)
+    uu, uv_, vv = np.empty((N, 3)), np.empty((N, 3)), np.empty((N, 3))
+    km, kg = np.empty(N), np.empty(N)
+    _load().or_chart_second(_p(verts), m, _p(tris), _p(geo["vpn"]), npn, _p(cu), _p(cv), _p(h), _p(grad),
+                            _p(hess), _p(uu), _p(uv_), _p(vv), _p(km), _p(kg))
+    return uu, uv_, vv, km, kg

@@ -22,6 +22,8 @@
  *   - local coordinates x_u, x_v and da of the charts (eq. u_vector,
  *     U_vector_2, v_vector, v_vector_2, da) and the Gauss flux error eps0
  *     (Sec. 5)
+ *   - the Hessian of Phi and the charts' second derivatives and curvatures
+ *     (Sec. 3.3, eq. uu_vector, uu_vector_aux1, uu_vector_aux2)
  *   - the target-dependent width sigma(x), a Gaussian-weighted mean of
  *     sigma_j = D_j / lambda over the triangle centroids (eq. sigma2), and
  *     Phi, grad Phi with it (eq. gradPhi's third term, sign corrected)
@@ -639,5 +641,159 @@ void or_solve_charts_sigx(int64_t ns, const double* y, const double* nw, int64_t
         status[i] = st | (clamped ? 256 : 0);
         iters[i] = it;
         lastdh[i] = dh;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Second derivatives (Sec. 3.3, higher derivatives of the charts).
+ * Third radial factor G = F'(rho) / rho.  With k(u) = h'(u)/u as above,
+ * G = (k'(u)/u) a^7 / (4 pi):
+ *   series  k'(u)/u = (2/sqrt pi) sum_{k>=3} c_k (2k-2)(2k-4) u^{2k-6}
+ *   closed  k'(u)/u = 15 g / u^7 - (4/sqrt pi) e^{-u^2} (2/u^2 + 5/u^4)
+ * (g'(u) = (4/sqrt pi) u^2 e^{-u^2} differentiated through h = g/u^3).  The
+ * series is used below u = 1, where the closed form cancels. */
+double or_radial_G(double rho, double sig)
+{
+    const double a = 1.0 / (sqrt(2.0) * sig);
+    const double u = rho * a;
+    const double tsp = 2.0 / sqrt(OR_PI);
+    double kp;
+    if (u < 1.0) {
+        double s = 0.0, fact = 1.0, wp = 1.0;   /* wp = u^{2k-6} for k >= 3 */
+        for (int k = 1; k < 80; k++) {
+            fact *= k;
+            if (k < 3) continue;
+            const double ck = ((k & 1) ? 1.0 : -1.0) * (2.0 * k) / (fact * (2.0 * k + 1.0));
+            const double t = ck * (2.0 * k - 2.0) * (2.0 * k - 4.0) * wp;
+            s += t;
+            if (k > 6 && fabs(t) < 1e-18 * fabs(s)) break;
+            wp *= u * u;
+        }
+        kp = tsp * s;
+    } else {
+        const double e = exp(-u * u);
+        const double g = erf(u) - tsp * u * e;
+        const double u2 = u * u, u4 = u2 * u2;
+        kp = 15.0 * g / (u4 * u2 * u) - 2.0 * tsp * e * (2.0 / u2 + 5.0 / u4);
+    }
+    const double a2 = a * a;
+    return kp * a2 * a2 * a2 * a / (4.0 * OR_PI);
+}
+
+/* Phi, grad Phi and the Hessian of Phi (per-triangle sigma), direct sums.
+ * For one pair, with r = y - x, q = nw . r:
+ *   d2/dx_i dx_j [q f] = F (nw_i r_j + nw_j r_i + q delta_ij) + q G r_i r_j.
+ * hess [nt][6] = (xx, xy, xz, yy, yz, zz). */
+void or_phi_grad_hess(int64_t ns, const double* y, const double* nw, const double* sig, int64_t nt,
+                      const double* x, double* phi, double* grad, double* hess, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        double p = 0.0, g[3] = {0.0, 0.0, 0.0}, H[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t s = 0; s < ns; s++) {
+            const double* yy = y + 3*s;
+            const double* n = nw + 3*s;
+            double r[3] = {yy[0] - x[3*t], yy[1] - x[3*t+1], yy[2] - x[3*t+2]};
+            const double rho = norm3(r);
+            double f, F;
+            or_radial(rho, sig[s], &f, &F);
+            const double G = or_radial_G(rho, sig[s]);
+            const double q = dot3(n, r);
+            p += q * f;
+            for (int c = 0; c < 3; c++) g[c] -= n[c] * f + q * F * r[c];
+            int k = 0;
+            for (int i = 0; i < 3; i++)
+                for (int j = i; j < 3; j++)
+                    H[k++] += F * (n[i] * r[j] + n[j] * r[i] + (i == j ? q : 0.0)) + q * G * r[i] * r[j];
+        }
+        phi[t] = p;
+        for (int c = 0; c < 3; c++) grad[3*t+c] = g[c];
+        for (int c = 0; c < 6; c++) hess[6*t+c] = H[c];
+    }
+}
+
+/* Second derivatives of the charts and the curvatures of Gamma_1/2 at the
+ * chart nodes.  On a flat triangle T_uu = T_uv = T_vv = 0 and the linear H
+ * has no second derivatives, so (eq. uu_vector, read with the H_u factor on
+ * 2 h_u and h_uu on H, and its v and mixed analogues)
+ *   x_uu = 2 h_u H_u + h_uu H,  x_uv = h_u H_v + h_v H_u + h_uv H,  x_vv = 2 h_v H_v + h_vv H,
+ * and differentiating x_u . grad Phi(x) = 0 once more (eq. uu_vector_aux1,
+ * uu_vector_aux2):
+ *   h_uu = -(x_u^T Hess x_u + 2 h_u H_u . grad Phi) / (H . grad Phi)
+ *   h_uv = -(x_u^T Hess x_v + (h_u H_v + h_v H_u) . grad Phi) / (H . grad Phi)
+ *   h_vv = -(x_v^T Hess x_v + 2 h_v H_v . grad Phi) / (H . grad Phi).
+ * With N = -grad Phi/|grad Phi| (outward), E, F, G = x_u.x_u, x_u.x_v, x_v.x_v
+ * and L, M, Nn = x_uu.N, x_uv.N, x_vv.N:
+ *   kgauss = (L Nn - M^2) / (E G - F^2),
+ *   kmean  = -(E Nn - 2 F M + G L) / (E G - F^2)  (sum of the principal
+ *            curvatures, 2/R on a sphere of radius R).
+ * Inputs as or_chart_frames plus hess [n][6]; outputs xuu, xuv, xvv [n][3],
+ * kmean, kgauss [n]. */
+void or_chart_second(const double* verts, int64_t m, const int32_t* tris, const double* vpn, int np,
+                     const double* cu, const double* cv, const double* h, const double* grad, const double* hess,
+                     double* xuu, double* xuv, double* xvv, double* kmean, double* kgauss)
+{
+    for (int64_t j = 0; j < m; j++) {
+        const double* p1 = verts + 3 * (int64_t)tris[3*j+0];
+        const double* p2 = verts + 3 * (int64_t)tris[3*j+1];
+        const double* p3 = verts + 3 * (int64_t)tris[3*j+2];
+        const double* h1 = vpn + 3 * (int64_t)tris[3*j+0];
+        const double* h2 = vpn + 3 * (int64_t)tris[3*j+1];
+        const double* h3 = vpn + 3 * (int64_t)tris[3*j+2];
+        double tu[3], tv[3], hu[3], hv[3];
+        for (int c = 0; c < 3; c++) {
+            tu[c] = p2[c] - p1[c];
+            tv[c] = p3[c] - p1[c];
+            hu[c] = h2[c] - h1[c];
+            hv[c] = h3[c] - h1[c];
+        }
+        for (int i = 0; i < np; i++) {
+            const int64_t s = j * np + i;
+            const double* g = grad + 3*s;
+            const double* Hs = hess + 6*s;
+            const double S[3][3] = {{Hs[0], Hs[1], Hs[2]}, {Hs[1], Hs[3], Hs[4]}, {Hs[2], Hs[4], Hs[5]}};
+            double H[3], a[3], b[3];
+            for (int c = 0; c < 3; c++) H[c] = h1[c] + cu[i] * hu[c] + cv[i] * hv[c];
+            const double hg = dot3(H, g);
+            double au[3], av[3];
+            for (int c = 0; c < 3; c++) {
+                au[c] = tu[c] + h[s] * hu[c];
+                av[c] = tv[c] + h[s] * hv[c];
+            }
+            const double h_u = -dot3(au, g) / hg, h_v = -dot3(av, g) / hg;
+            for (int c = 0; c < 3; c++) {
+                a[c] = au[c] + h_u * H[c];
+                b[c] = av[c] + h_v * H[c];
+            }
+            double Sa[3], Sb[3];
+            for (int r = 0; r < 3; r++) {
+                Sa[r] = S[r][0] * a[0] + S[r][1] * a[1] + S[r][2] * a[2];
+                Sb[r] = S[r][0] * b[0] + S[r][1] * b[1] + S[r][2] * b[2];
+            }
+            const double huu = -(dot3(a, Sa) + 2.0 * h_u * dot3(hu, g)) / hg;
+            const double huv = -(dot3(a, Sb) + h_u * dot3(hv, g) + h_v * dot3(hu, g)) / hg;
+            const double hvv = -(dot3(b, Sb) + 2.0 * h_v * dot3(hv, g)) / hg;
+            double uu[3], uv[3], vv[3];
+            for (int c = 0; c < 3; c++) {
+                uu[c] = 2.0 * h_u * hu[c] + huu * H[c];
+                uv[c] = h_u * hv[c] + h_v * hu[c] + huv * H[c];
+                vv[c] = 2.0 * h_v * hv[c] + hvv * H[c];
+                xuu[3*s+c] = uu[c];
+                xuv[3*s+c] = uv[c];
+                xvv[3*s+c] = vv[c];
+            }
+            const double gn = norm3(g);
+            double N[3] = {-g[0] / gn, -g[1] / gn, -g[2] / gn};
+            const double E = dot3(a, a), F = dot3(a, b), G = dot3(b, b);
+            const double L = dot3(uu, N), M = dot3(uv, N), Nn = dot3(vv, N);
+            const double det = E * G - F * F;
+            kgauss[s] = (L * Nn - M * M) / det;
+            kmean[s] = -(E * Nn - 2.0 * F * M + G * L) / det;
+        }
     }
 }

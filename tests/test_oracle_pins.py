@@ -578,3 +578,122 @@ def test_sigma_x_charts_converge(oracle_mod):
     s, gs = oracle_mod.sigma_x(c, sj, s0, r["x"])
     p, _ = oracle_mod.phi_grad_sigx(y, nw, r["x"], s, gs)
     assert np.abs(p - 0.5).max() < 1e-13
+
+
+# ---------------------------------------------------------------- Hessian and curvatures
+
+def test_radial_G_is_derivative_of_F(oracle_mod):
+    """G = F'(rho)/rho on both branches (series below u = 1, closed form
+    above), and its Laplace limit 15/(4 pi rho^7)."""
+    s = 0.1
+    a = 1 / (np.sqrt(2) * s)
+    for u in (0.05, 0.3, 0.7, 0.99, 1.01, 1.5, 3.0, 6.0):
+        rho = u / a
+        d = 1e-5 * rho
+        F = lambda r: oracle_mod.radial(r, s)[1]
+        fd = (8 * (F(rho + d) - F(rho - d)) - (F(rho + 2 * d) - F(rho - 2 * d))) / (12 * d) / rho
+        G = oracle_mod.radial_G(rho, s)
+        assert abs(fd / G - 1) < 1e-8, (u, fd, G)
+    rho = 9.0 / a
+    assert abs(oracle_mod.radial_G(rho, s) * 4 * np.pi * rho ** 7 / 15 - 1) < 1e-14
+
+
+def test_hessian_box_closed_form(oracle_mod):
+    """Second derivatives of the box's erf product (P1 differentiated twice)."""
+    from scipy.special import erf as serf
+    m = synth.cube(1.0, 4)
+    sig = 0.1
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, np.full(m.m, sig), 8, 2)
+    x = synth.targets_uniform(20, -1.3, 1.3, synth.rng(61))
+    _, _, H = oracle_mod.phi_grad_hess(y, nw, sg, x)
+    A, c = 1.0, np.sqrt(2) * sig
+    ph = lambda t: 0.5 * (serf((A - t) / c) + serf((A + t) / c))
+    d1 = lambda t: (np.exp(-(A + t) ** 2 / (2 * sig ** 2)) - np.exp(-(A - t) ** 2 / (2 * sig ** 2))) / (
+        np.sqrt(2 * np.pi) * sig)
+    d2 = lambda t: (-(A - t) * np.exp(-(A - t) ** 2 / (2 * sig ** 2)) -
+                    (A + t) * np.exp(-(A + t) ** 2 / (2 * sig ** 2))) / (np.sqrt(2 * np.pi) * sig ** 3)
+    P = [ph(x[:, i]) for i in range(3)]
+    D1 = [d1(x[:, i]) for i in range(3)]
+    D2 = [d2(x[:, i]) for i in range(3)]
+    Hc = np.stack([D2[0] * P[1] * P[2], D1[0] * D1[1] * P[2], D1[0] * P[1] * D1[2],
+                   P[0] * D2[1] * P[2], P[0] * D1[1] * D1[2], P[0] * P[1] * D2[2]], 1)
+    assert np.abs(H - Hc).max() < 1e-11 * np.abs(Hc).max()
+
+
+def test_hessian_finite_differences_of_gradient(oracle_mod):
+    m = _graded_small()
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, None, 6, 0)
+    x = synth.targets_near_surface(m, 12, synth.rng(62), 2.0)
+    _, g, H = oracle_mod.phi_grad_hess(y, nw, sg, x)
+    _, g0 = oracle_mod.phi_grad(y, nw, sg, x)
+    assert np.abs(g - g0).max() < 1e-12 * np.abs(g0).max()
+    d = 1e-5
+    cols = []
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = d
+        cols.append((oracle_mod.phi_grad(y, nw, sg, x + e)[1] - oracle_mod.phi_grad(y, nw, sg, x - e)[1]) / (2 * d))
+    Hfd = np.stack([cols[0][:, 0], cols[1][:, 0], cols[2][:, 0], cols[1][:, 1], cols[2][:, 1], cols[2][:, 2]], 1)
+    assert np.abs(H - Hfd).max() < 1e-7 * np.abs(H).max()
+    # and the matrix FD is symmetric as the formula says
+    assert np.abs(cols[0][:, 1] - cols[1][:, 0]).max() < 1e-7 * np.abs(H).max()
+
+
+def test_chart_second_derivatives_match_finite_differences(oracle_mod, small_sphere_charts):
+    """eq. uu_vector (and its uv, vv analogues): x_uu, x_uv equal central
+    differences of the frames x_u of Newton-solved charts."""
+    m, src, geo = small_sphere_charts
+    y, nw, sg = src
+    d = 1e-4
+
+    def frame_at(j, u, v):
+        x, h = _solve_at(oracle_mod, m, src, geo, j, u, v)
+        _, g = oracle_mod.phi_grad(y, nw, sg, x[None])
+        xu, xv, _ = oracle_mod.chart_frames(m.verts, m.tris, np.full(m.m, h), np.tile(g, (m.m, 1)),
+                                            uv=(np.array([u]), np.array([v])))
+        return x, h, g[0], xu[j], xv[j]
+
+    for j, u, v in ((3, 0.2, 0.3), (41, 0.55, 0.1)):
+        x, h, g, _, _ = frame_at(j, u, v)
+        _, _, H = oracle_mod.phi_grad_hess(y, nw, sg, x[None])
+        uu, uv, vv, km, kg = oracle_mod.chart_second(m.verts, m.tris, np.full(m.m, h), np.tile(g, (m.m, 1)),
+                                                     np.tile(H[0], (m.m, 1)), uv=(np.array([u]), np.array([v])))
+        fuu = (frame_at(j, u + d, v)[3] - frame_at(j, u - d, v)[3]) / (2 * d)
+        fuv = (frame_at(j, u, v + d)[3] - frame_at(j, u, v - d)[3]) / (2 * d)
+        fvv = (frame_at(j, u, v + d)[4] - frame_at(j, u, v - d)[4]) / (2 * d)
+        scale = np.abs(fuu).max() + np.abs(fvv).max() + 1e-3
+        assert np.abs(uu[j] - fuu).max() < 1e-6 * scale
+        assert np.abs(uv[j] - fuv).max() < 1e-6 * scale
+        assert np.abs(vv[j] - fvv).max() < 1e-6 * scale
+        # the chart curvature equals the level set's, div(-grad Phi / |grad Phi|)
+        S = np.array([[H[0, 0], H[0, 1], H[0, 2]], [H[0, 1], H[0, 3], H[0, 4]], [H[0, 2], H[0, 4], H[0, 5]]])
+        gn = np.linalg.norm(g)
+        kdiv = -(np.trace(S) * gn ** 2 - g @ S @ g) / gn ** 3
+        assert abs(km[j] - kdiv) < 1e-9 * abs(kdiv)
+
+
+def _gauss_bonnet(oracle_mod, m, n, src):
+    y, nw, sg = src
+    x0, hd, sl = oracle_mod.chart_nodes(m.verts, m.tris, None, n)
+    r = oracle_mod.solve_charts(y, nw, sg, x0, hd, sl, tol=1e-14, max_iter=40)
+    assert (r["status"] == 0).all()
+    _, g, H = oracle_mod.phi_grad_hess(y, nw, sg, r["x"])
+    _, _, jac = oracle_mod.chart_frames(m.verts, m.tris, r["h"], g, n=n)
+    _, _, _, km, kg = oracle_mod.chart_second(m.verts, m.tris, r["h"], g, H, n=n)
+    _, _, cw = oracle_mod.simplex_rule(n, 0)
+    return float(np.sum(np.tile(cw, m.m) * jac * kg))
+
+
+def test_gauss_bonnet_sphere_and_torus(oracle_mod, small_sphere_charts):
+    """Gauss-Bonnet: the Gaussian curvature of the charts integrates to
+    2 pi chi, 4 pi on a sphere and 0 on a torus, with the chart rule's error
+    falling as its order grows."""
+    m, src, geo = small_sphere_charts
+    # measured: 2.0e-3, 6.7e-6, 5.5e-10 at n = 3, 5, 7
+    errs = [abs(_gauss_bonnet(oracle_mod, m, n, src) - 4 * np.pi) for n in (3, 5, 7)]
+    assert errs[0] > 10 * errs[1] and errs[1] > 10 * errs[2]
+    assert errs[2] < 1e-6
+    t = synth.torus(1.0, 0.4, 24, 10, 1.0, 0.0, 63)
+    st = oracle_mod.sources(t.verts, t.tris, None, 6, 0)
+    # measured: 2.9e-5 at n = 5, 2.8e-7 at n = 7
+    assert abs(_gauss_bonnet(oracle_mod, t, 7, st)) < 5e-6
