@@ -290,6 +290,30 @@ int lsm_chart_frames(lsm_mesh* mesh, int order, const double* h, const double* g
 int lsm_gauss_flux(lsm_mesh* mesh, int order, const double* x, const double* grad, const double* jac,
                    const double* x0, double* eps0, void* stream);
 
+/* The Hessian of Phi at n targets (Sec. 3.3: the charts' second derivatives
+ * need it, eq. uu_vector_aux1).  Per pair, with r = y - x, q = nw . r and
+ * the radial factors f, F = f'/rho, G = F'/rho of eq. kerpsi,
+ *   d2/dx_i dx_j [q f] = F (nw_i r_j + nw_j r_i + q delta_ij) + q G r_i r_j.
+ * Near tiles (within the FP64 cutoff) are summed in FP64, far tiles in FP32
+ * with compensated sums; direct far field.
+ *   x     [n][3] host or device;  hess [n][6] out: xx, xy, xz, yy, yz, zz.
+ * Meshes uploaded with lsm_mesh_upload_sigmax are rejected.
+ * Errors: LSM_E_INVALID_ARG, LSM_E_OOM, LSM_E_CUDA. */
+int lsm_eval_hessian(lsm_mesh* mesh, const double* x, int64_t n, double* hess, void* stream);
+/* Second derivatives of the solved charts and the curvatures of the level
+ * set at their nodes (Sec. 3.3).  On the flat skeleton triangles, with H
+ * linear, eq. uu_vector and its uv, vv analogues read
+ *   x_uu = 2 h_u H_u + h_uu H,  x_uv = h_u H_v + h_v H_u + h_uv H,  x_vv = 2 h_v H_v + h_vv H,
+ * with h_uu = -(x_u^T Hess x_u + 2 h_u H_u . grad Phi)/(H . grad Phi) and its
+ * analogues (eq. uu_vector_aux2).  With the outward normal -grad Phi/|grad Phi|
+ * and the two fundamental forms: kgauss = Gaussian curvature, kmean = the
+ * sum of the principal curvatures (2/R on a sphere of radius R).
+ *   h [N], grad [N][3], hess [N][6] at the solved nodes (lsm_solve_charts'
+ *   order); xuu, xuv, xvv [N][3], kmean, kgauss [N] out.  Host or device.
+ * Errors: LSM_E_INVALID_ARG, LSM_E_OOM, LSM_E_CUDA. */
+int lsm_chart_curvature(lsm_mesh* mesh, int order, const double* h, const double* grad, const double* hess,
+                        double* xuu, double* xuv, double* xvv, double* kmean, double* kgauss, void* stream);
+
 /* Autotuner of the mixed path's far field (the paper has no counterpart:
  * its FMM is run at a fixed precision, Sec. 4.4).  Chooses, for this mesh,
  * between the direct tiled far field and the treecode, and the treecode's

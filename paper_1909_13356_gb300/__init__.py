@@ -40,7 +40,8 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_eval_phi_grad_noalloc", "lsm_solve_charts", "lsm_batch_create", "lsm_batch_free",
            "lsm_batch_solve_charts", "lsm_server_create", "lsm_server_submit", "lsm_server_poll", "lsm_server_release",
            "lsm_server_info", "lsm_server_destroy", "lsm_autotune", "lsm_chart_frames", "lsm_gauss_flux",
-           "lsm_mesh_upload_sigmax", "lsm_mesh_get_sigma0", "lsm_eval_sigma")
+           "lsm_mesh_upload_sigmax", "lsm_mesh_get_sigma0", "lsm_eval_sigma", "lsm_eval_hessian",
+           "lsm_chart_curvature")
 
 
 class LsmError(RuntimeError):
@@ -167,6 +168,8 @@ def load(build_if_needed: bool = True):
         L.lsm_mesh_upload_sigmax.argtypes = [P, P, I64, P, I64, D, D, ctypes.POINTER(_Quad), P, ctypes.POINTER(P)]
         L.lsm_mesh_get_sigma0.argtypes = [P, ctypes.POINTER(D)]
         L.lsm_eval_sigma.argtypes = [P, P, I64, P, P, P]
+        L.lsm_eval_hessian.argtypes = [P, P, I64, P, P]
+        L.lsm_chart_curvature.argtypes = [P, I32, P, P, P, P, P, P, P, P, P]
         L.lsm_gauss_flux.argtypes = [P, I32, P, P, P, P, P, P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
@@ -377,6 +380,37 @@ class Mesh:
                                           _stream_handle(stream))
         self.ctx._check(rc)
         return xu, xv, jac
+
+    def eval_hessian(self, x, stream=None):
+        """Hessian of Phi [n, 6] = (xx, xy, xz, yy, yz, zz) at targets x [n, 3]
+        (lsm_eval_hessian)."""
+        xs = _as(x, np.float64)
+        n = int(xs.shape[0])
+        if _is_torch(xs):
+            import torch
+            hs = torch.empty((n, 6), dtype=torch.float64, device=xs.device)
+        else:
+            hs = np.empty((n, 6))
+        rc = self.ctx._L.lsm_eval_hessian(self._h, _ptr(xs), n, _ptr(hs), _stream_handle(stream))
+        self.ctx._check(rc)
+        return hs
+
+    def chart_curvature(self, order: int, h, grad, hess, stream=None):
+        """Second derivatives x_uu, x_uv, x_vv [N, 3] of the solved charts and the
+        mean (sum of principal curvatures) and Gaussian curvatures [N] at their
+        nodes (lsm_chart_curvature)."""
+        hs, gs, ss = _as(h, np.float64), _as(grad, np.float64), _as(hess, np.float64)
+        n = int(hs.shape[0])
+        if _is_torch(hs):
+            import torch
+            mk = lambda *sh: torch.empty(sh, dtype=torch.float64, device=hs.device)
+        else:
+            mk = lambda *sh: np.empty(sh)
+        uu, uv, vv, km, kg = mk(n, 3), mk(n, 3), mk(n, 3), mk(n), mk(n)
+        rc = self.ctx._L.lsm_chart_curvature(self._h, int(order), _ptr(hs), _ptr(gs), _ptr(ss), _ptr(uu), _ptr(uv),
+                                             _ptr(vv), _ptr(km), _ptr(kg), _stream_handle(stream))
+        self.ctx._check(rc)
+        return uu, uv, vv, km, kg
 
     def gauss_flux(self, order: int, x, grad, jac, x0, stream=None) -> float:
         """Gauss flux error eps0 of the charts about x0 (lsm_gauss_flux)."""

@@ -182,6 +182,16 @@ __global__ void k_scatter_results(const double* __restrict__ R, const uint32_t* 
     }
 }
 
+// res [6][n] in sorted order -> out [n][6] in the caller's order
+__global__ void k_scatter6(const double* __restrict__ R, const uint32_t* __restrict__ perm, int n,
+                           double* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = perm[i];
+    for (int c = 0; c < 6; c++) out[6 * o + c] = R[(int64_t)c * n + i];
+}
+
 int check_flag(Ctx* ctx, cudaStream_t st)
 {
     int h = 0;
@@ -682,6 +692,87 @@ int lsm_chart_frames(lsm_mesh* mh, int order, const double* h, const double* gra
     if (!bdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(xv, b, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
     if (!cdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(jac, c, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     if (!adev || !bdev || !cdev) LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+int lsm_eval_hessian(lsm_mesh* mh, const double* x, int64_t n, double* hess, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (n == 0) return LSM_OK;
+    if (n < 0 || n >= ((int64_t)1 << 31) || !x || !hess || me->sigx) {
+        ctx->err = "eval_hessian: bad arguments (meshes with sigma(x) are not supported)";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ni = (int)n;
+    Scratch s(st);
+    const double* xd;
+    int rc = to_device(ctx, s, x, 3 * (size_t)n, &xd, st);
+    if (rc) return rc;
+    uint32_t* perm;
+    double *T, *R;
+    LSM_CUDA_TRY(ctx, s.get(&perm, n));
+    LSM_CUDA_TRY(ctx, s.get(&T, 3 * (size_t)n));
+    LSM_CUDA_TRY(ctx, s.get(&R, 6 * (size_t)n));
+    rc = morton_order_points(ctx, xd, 3, ni, perm, st);
+    if (rc) return rc;
+    k_gather_points<<<(ni + 255) / 256, 256, 0, st>>>(xd, perm, ni, T);
+    LSM_LAUNCHED(ctx);
+    Targets tg{T, n, ni};
+    rc = hess_sorted(ctx, me, tg, R, st);
+    if (rc) return rc;
+    const bool hdev = is_device_ptr(hess);
+    double* hd = hess;
+    if (!hdev) LSM_CUDA_TRY(ctx, s.get(&hd, 6 * (size_t)n));
+    k_scatter6<<<(ni + 255) / 256, 256, 0, st>>>(R, perm, ni, hd);
+    LSM_LAUNCHED(ctx);
+    if (!hdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(hess, hd, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+    return check_flag(ctx, st);
+}
+
+int lsm_chart_curvature(lsm_mesh* mh, int order, const double* h, const double* grad, const double* hess,
+                        double* xuu, double* xuv, double* xvv, double* kmean, double* kgauss, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (order < 0 || order > 40 || !h || !grad || !hess || !xuu || !xuv || !xvv || !kmean || !kgauss) {
+        ctx->err = "chart_curvature: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_gl = order / 2 + 2;
+    const size_t N = (size_t)me->m * n_gl * n_gl;
+    Scratch s(st);
+    const double *hd, *gd, *sd;
+    int rc = to_device(ctx, s, h, N, &hd, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, grad, 3 * N, &gd, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, hess, 6 * N, &sd, st);
+    if (rc) return rc;
+    double* outs[5] = {xuu, xuv, xvv, kmean, kgauss};
+    const size_t cnt[5] = {3 * N, 3 * N, 3 * N, N, N};
+    double* dev[5];
+    bool isdev[5];
+    for (int k = 0; k < 5; k++) {
+        isdev[k] = is_device_ptr(outs[k]);
+        dev[k] = outs[k];
+        if (!isdev[k]) LSM_CUDA_TRY(ctx, s.get(&dev[k], cnt[k]));
+    }
+    rc = chart_second_dev(ctx, me, n_gl, hd, gd, sd, dev[0], dev[1], dev[2], dev[3], dev[4], st);
+    if (rc) return rc;
+    bool any_host = false;
+    for (int k = 0; k < 5; k++)
+        if (!isdev[k]) {
+            any_host = true;
+            LSM_CUDA_TRY(ctx, cudaMemcpyAsync(outs[k], dev[k], sizeof(double) * cnt[k], cudaMemcpyDeviceToHost, st));
+        }
+    if (any_host) LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     return LSM_OK;
 }
 

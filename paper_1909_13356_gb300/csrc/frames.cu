@@ -68,6 +68,80 @@ __global__ void k_chart_frames(const double* __restrict__ verts, const int32_t* 
     jac[s] = sqrt(cx * cx + cy * cy + cz * cz);
 }
 
+// Second derivatives of the charts and the curvatures of the level set at
+// the nodes.  On a flat triangle with linear H (eq. uu_vector and its uv, vv
+// analogues, T and H having no second derivatives):
+//   x_uu = 2 h_u H_u + h_uu H,  x_uv = h_u H_v + h_v H_u + h_uv H,  x_vv = 2 h_v H_v + h_vv H,
+// with h_uu, h_uv, h_vv from differentiating x_u . grad Phi = 0 once more
+// (eq. uu_vector_aux1, uu_vector_aux2):
+//   h_uu = -(x_u^T Hess x_u + 2 h_u H_u . grad Phi) / (H . grad Phi), etc.
+// Then with N = -grad Phi/|grad Phi| (outward) and the fundamental forms
+// E, F, G = x_u.x_u, x_u.x_v, x_v.x_v and L, M, Nn = x_uu.N, x_uv.N, x_vv.N:
+//   kgauss = (L Nn - M^2)/(EG - F^2),  kmean = -(E Nn - 2 F M + G L)/(EG - F^2)
+// (kmean the sum of the principal curvatures, 2/R on a sphere of radius R).
+__global__ void k_chart_second(const double* __restrict__ verts, const int32_t* __restrict__ tris,
+                               const double* __restrict__ vpn, int64_t m, int np, const double* __restrict__ rule,
+                               const double* __restrict__ h, const double* __restrict__ g,
+                               const double* __restrict__ hess, double* __restrict__ xuu, double* __restrict__ xuv,
+                               double* __restrict__ xvv, double* __restrict__ kmean, double* __restrict__ kgauss)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= m * np) return;
+    const int64_t j = s / np;
+    const int i = (int)(s - j * np);
+    const double u = rule[3 * i], v = rule[3 * i + 1];
+    const int ia = tris[3 * j], ib = tris[3 * j + 1], ic = tris[3 * j + 2];
+    double tu[3], tv[3], H[3], hu[3], hv[3], gs[3];
+    for (int k = 0; k < 3; k++) {
+        const double p1 = verts[3 * ia + k], n1 = vpn[3 * ia + k];
+        tu[k] = verts[3 * ib + k] - p1;
+        tv[k] = verts[3 * ic + k] - p1;
+        hu[k] = vpn[3 * ib + k] - n1;
+        hv[k] = vpn[3 * ic + k] - n1;
+        H[k] = n1 + u * hu[k] + v * hv[k];
+        gs[k] = g[3 * s + k];
+    }
+    const double* Hs = hess + 6 * s;
+    const double S[3][3] = {{Hs[0], Hs[1], Hs[2]}, {Hs[1], Hs[3], Hs[4]}, {Hs[2], Hs[4], Hs[5]}};
+    auto dot = [](const double* p, const double* q) { return p[0] * q[0] + p[1] * q[1] + p[2] * q[2]; };
+    const double hs = h[s];
+    const double hg = dot(H, gs);
+    double au[3], av[3], a[3], b[3];
+    for (int k = 0; k < 3; k++) {
+        au[k] = tu[k] + hs * hu[k];
+        av[k] = tv[k] + hs * hv[k];
+    }
+    const double h_u = -dot(au, gs) / hg, h_v = -dot(av, gs) / hg;
+    for (int k = 0; k < 3; k++) {
+        a[k] = au[k] + h_u * H[k];
+        b[k] = av[k] + h_v * H[k];
+    }
+    double Sa[3], Sb[3];
+    for (int r = 0; r < 3; r++) {
+        Sa[r] = S[r][0] * a[0] + S[r][1] * a[1] + S[r][2] * a[2];
+        Sb[r] = S[r][0] * b[0] + S[r][1] * b[1] + S[r][2] * b[2];
+    }
+    const double huu = -(dot(a, Sa) + 2.0 * h_u * dot(hu, gs)) / hg;
+    const double huv = -(dot(a, Sb) + h_u * dot(hv, gs) + h_v * dot(hu, gs)) / hg;
+    const double hvv = -(dot(b, Sb) + 2.0 * h_v * dot(hv, gs)) / hg;
+    double uu[3], uv[3], vv[3];
+    for (int k = 0; k < 3; k++) {
+        uu[k] = 2.0 * h_u * hu[k] + huu * H[k];
+        uv[k] = h_u * hv[k] + h_v * hu[k] + huv * H[k];
+        vv[k] = 2.0 * h_v * hv[k] + hvv * H[k];
+        xuu[3 * s + k] = uu[k];
+        xuv[3 * s + k] = uv[k];
+        xvv[3 * s + k] = vv[k];
+    }
+    const double gn = sqrt(dot(gs, gs));
+    const double N[3] = {-gs[0] / gn, -gs[1] / gn, -gs[2] / gn};
+    const double E = dot(a, a), F = dot(a, b), G = dot(b, b);
+    const double L = dot(uu, N), M = dot(uv, N), Nn = dot(vv, N);
+    const double det = E * G - F * F;
+    kgauss[s] = (L * Nn - M * M) / det;
+    kmean[s] = -(E * Nn - 2.0 * F * M + G * L) / det;
+}
+
 // Per-block partial sums of the flux terms (block sums in a fixed tree order).
 __global__ void __launch_bounds__(kFrameThreads) k_flux_partial(const double* __restrict__ x,
                                                                 const double* __restrict__ g,
@@ -141,6 +215,22 @@ int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const 
     if (n == 0) return LSM_OK;
     k_chart_frames<<<(unsigned)((n + kFrameThreads - 1) / kFrameThreads), kFrameThreads, 0, st>>>(
         me->verts, me->tris, me->vpn, me->m, np, rule, h, g, xu, xv, jac);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
+int chart_second_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const double* g, const double* hess,
+                     double* xuu, double* xuv, double* xvv, double* kmean, double* kgauss, cudaStream_t st)
+{
+    Scratch s(st);
+    double* rule = nullptr;
+    int rc = upload_rule(ctx, s, n_gl, &rule, st);
+    if (rc) return rc;
+    const int np = n_gl * n_gl;
+    const int64_t n = me->m * np;
+    if (n == 0) return LSM_OK;
+    k_chart_second<<<(unsigned)((n + kFrameThreads - 1) / kFrameThreads), kFrameThreads, 0, st>>>(
+        me->verts, me->tris, me->vpn, me->m, np, rule, h, g, hess, xuu, xuv, xvv, kmean, kgauss);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }

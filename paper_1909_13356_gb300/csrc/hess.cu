@@ -1,0 +1,294 @@
+// hess.cu -- the Hessian of Phi at targets (Sec. 3.3: second derivatives of
+// the charts need the Hessian of Phi, eq. uu_vector_aux1).
+//
+// For one pair, with r = y - x, q = nw . r and the radial factors
+// f = g(u)/(4 pi rho^3), F = f'(rho)/rho, G = F'(rho)/rho,
+//   d2/dx_i dx_j [q f] = F (nw_i r_j + nw_j r_i + q delta_ij) + q G r_i r_j.
+// With a = 1/(sqrt2 sigma), w = u^2 = rho^2 a^2, h(w) = g(u)/u^3 and
+// nw' = nw / 4 pi (the resident weights):
+//   f -> a^3 h,   F -> a^5 k,   G -> a^7 kp,
+//   k = h'(u)/u = 2 dh/dw,  kp = k'(u)/u = 2 dk/dw,
+// summed as power series in w below w = 1/4, else from the closed forms
+//   h = g/u^3,  k = (4/sqrt pi) e^-w / u^2 - 3 g / u^5,
+//   kp = 15 g / u^7 - (4/sqrt pi) e^-w (2/u^2 + 5/u^4);
+// beyond the cutoff they are the Laplace limits 1/rho^3, -3/rho^5, 15/rho^7.
+//
+// Near the level set the Hessian's curvature part is a small fraction of
+// its terms, which cancel: near tiles are summed in FP64.  Far tiles (the
+// Laplace double layer, no cancellation of note) are summed in FP32 on
+// tile-local coordinates with compensated accumulation.  The far field is
+// the direct tiled sum; a CTA owns 128 sorted targets and walks a range of
+// tiles (a grid row per split, partials reduced in a fixed order).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lsm_internal.cuh"
+
+namespace lsm {
+namespace {
+
+constexpr int kHessThreads = kTile;   // one target per thread, tiles staged by one load per thread
+constexpr int kHSer = 16;             // series terms for w < 1/4
+constexpr double kHSerW = 0.25;
+constexpr double kFourOverSqrtPiH = 2.25675833419102514780;
+constexpr double kTwoOverSqrtPiH = 1.12837916709551257390;
+
+__constant__ double c_hh[kHSer];    // h = sum c_hh[m] w^m
+__constant__ double c_hk[kHSer];    // k
+__constant__ double c_hkp[kHSer];   // kp
+
+__device__ __forceinline__ void radial3(double r2, double a, double& fH, double& FK, double& GK)
+{
+    const double w = r2 * a * a;
+    double h, k, kp;
+    if (w < kHSerW) {
+        h = c_hh[kHSer - 1];
+        k = c_hk[kHSer - 1];
+        kp = c_hkp[kHSer - 1];
+        for (int m = kHSer - 2; m >= 0; m--) {
+            h = fma(h, w, c_hh[m]);
+            k = fma(k, w, c_hk[m]);
+            kp = fma(kp, w, c_hkp[m]);
+        }
+    } else {
+        const double u = sqrt(w);
+        const double e = exp(-w);
+        const double g = erf(u) - kTwoOverSqrtPiH * u * e;
+        const double iu = 1.0 / u, iu2 = iu * iu;
+        h = g * iu2 * iu;
+        k = kFourOverSqrtPiH * e * iu2 - 3.0 * g * iu2 * iu2 * iu;
+        kp = 15.0 * g * iu2 * iu2 * iu2 * iu - kFourOverSqrtPiH * e * (2.0 * iu2 + 5.0 * iu2 * iu2);
+    }
+    const double a2 = a * a, a3 = a2 * a;
+    fH = a3 * h;
+    FK = a3 * a2 * k;
+    GK = a3 * a2 * a2 * kp;
+}
+
+__device__ __forceinline__ void tsum(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+
+struct HessArgs {
+    const float4* s32_pos;        // tile-local FP32 positions (far tiles)
+    const float4* s32_nw;
+    const double4_32a* s64_pos;   // FP64 (near tiles): (x, y, z, a)
+    const double4_32a* s64_nw;    // (nw / 4 pi, sqrt2 sigma)
+    const float4 *tlo, *thi, *tchi, *tclo;
+    int ntiles, tiles_per_split;
+    const double* tx;
+    int64_t ld;
+    int nt;
+    float cut2;
+    double* out;                  // [split][6][nt]
+};
+
+__global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
+{
+    __shared__ float4 sp[kTile], sn[kTile];
+    __shared__ double4_32a dp[kTile], dn[kTile];
+    __shared__ float part[6][kHessThreads / 32];
+    __shared__ float bb[6];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kHessThreads + tid;
+    const bool valid = i < A.nt;
+    const int t0 = blockIdx.y * A.tiles_per_split;
+    const int t1 = min(A.ntiles, t0 + A.tiles_per_split);
+
+    double x[3] = {0.0, 0.0, 0.0};
+    float xh[3], xl[3];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int c = 0; c < 3; c++) {
+        if (valid) {
+            x[c] = A.tx[c * A.ld + i];
+            lo[c] = __double2float_rd(x[c]);
+            hi[c] = __double2float_ru(x[c]);
+        }
+        xh[c] = (float)x[c];
+        xl[c] = (float)(x[c] - (double)xh[c]);
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    }
+    if ((tid & 31) == 0)
+        for (int c = 0; c < 3; c++) {
+            part[c][tid >> 5] = lo[c];
+            part[3 + c][tid >> 5] = hi[c];
+        }
+    __syncthreads();
+    if (tid == 0)
+        for (int c = 0; c < 3; c++) {
+            float L = part[c][0], H = part[3 + c][0];
+            for (int k = 1; k < kHessThreads / 32; k++) {
+                L = fminf(L, part[c][k]);
+                H = fmaxf(H, part[3 + c][k]);
+            }
+            bb[c] = L;
+            bb[3 + c] = H;
+        }
+    __syncthreads();
+
+    float fh[6], fl[6];   // far part, float-float
+    double nh[6];         // near part, FP64
+    for (int c = 0; c < 6; c++) {
+        fh[c] = fl[c] = 0.0f;
+        nh[c] = 0.0;
+    }
+    for (int t = t0; t < t1; t++) {
+        const float4 tl = A.tlo[t], th = A.thi[t];
+        const float gx = fmaxf(0.0f, fmaxf(tl.x - bb[3], bb[0] - th.x));
+        const float gy = fmaxf(0.0f, fmaxf(tl.y - bb[4], bb[1] - th.y));
+        const float gz = fmaxf(0.0f, fmaxf(tl.z - bb[5], bb[2] - th.z));
+        const bool far = gx * gx + gy * gy + gz * gz > A.cut2 * tl.w * tl.w * 1.0001f;
+        const int cnt = (int)th.w;
+        const int64_t j = (int64_t)t * kTile + tid;
+        if (tid < cnt) {
+            if (far) {
+                sp[tid] = A.s32_pos[j];
+                sn[tid] = A.s32_nw[j];
+            } else {
+                dp[tid] = A.s64_pos[j];
+                dn[tid] = A.s64_nw[j];
+            }
+        }
+        __syncthreads();
+        if (far) {
+            const float4 ch = A.tchi[t], cl = A.tclo[t];
+            // target in tile-local coordinates; r = y - x
+            const float qx = (xh[0] - ch.x) + (xl[0] - cl.x);
+            const float qy = (xh[1] - ch.y) + (xl[1] - cl.y);
+            const float qz = (xh[2] - ch.z) + (xl[2] - cl.z);
+            float p[6] = {0, 0, 0, 0, 0, 0};
+            for (int s = 0; s < cnt; s++) {
+                const float4 y = sp[s], n = sn[s];
+                const float r0 = y.x - qx, r1 = y.y - qy, r2c = y.z - qz;
+                const float r2 = fmaf(r0, r0, fmaf(r1, r1, r2c * r2c));
+                float ri = rsqrtf(r2);
+                ri = ri * fmaf(-0.5f * r2 * ri, ri, 1.5f);   // one Newton step for 1/sqrt
+                const float ri2 = ri * ri;
+                const float ri5 = ri2 * ri2 * ri;
+                const float q = fmaf(n.x, r0, fmaf(n.y, r1, n.z * r2c));
+                const float F = -3.0f * ri5;
+                const float qG = 15.0f * q * ri5 * ri2;
+                p[0] += F * (2.0f * n.x * r0 + q) + qG * r0 * r0;
+                p[1] += F * (n.x * r1 + n.y * r0) + qG * r0 * r1;
+                p[2] += F * (n.x * r2c + n.z * r0) + qG * r0 * r2c;
+                p[3] += F * (2.0f * n.y * r1 + q) + qG * r1 * r1;
+                p[4] += F * (n.y * r2c + n.z * r1) + qG * r1 * r2c;
+                p[5] += F * (2.0f * n.z * r2c + q) + qG * r2c * r2c;
+            }
+            for (int c = 0; c < 6; c++) tsum(fh[c], fl[c], p[c]);
+        } else {
+            double p[6] = {0, 0, 0, 0, 0, 0};
+            for (int s = 0; s < cnt; s++) {
+                const double4_32a y = dp[s], n = dn[s];
+                const double r0 = y.x - x[0], r1 = y.y - x[1], r2c = y.z - x[2];
+                const double r2 = fma(r0, r0, fma(r1, r1, r2c * r2c));
+                double fH, F, G;
+                radial3(r2, y.w, fH, F, G);
+                const double q = fma(n.x, r0, fma(n.y, r1, n.z * r2c));
+                const double qG = q * G;
+                p[0] += F * (2.0 * n.x * r0 + q) + qG * r0 * r0;
+                p[1] += F * (n.x * r1 + n.y * r0) + qG * r0 * r1;
+                p[2] += F * (n.x * r2c + n.z * r0) + qG * r0 * r2c;
+                p[3] += F * (2.0 * n.y * r1 + q) + qG * r1 * r1;
+                p[4] += F * (n.y * r2c + n.z * r1) + qG * r1 * r2c;
+                p[5] += F * (2.0 * n.z * r2c + q) + qG * r2c * r2c;
+            }
+            for (int c = 0; c < 6; c++) nh[c] += p[c];
+        }
+        __syncthreads();
+    }
+    if (valid) {
+        double* out = A.out + (int64_t)blockIdx.y * 6 * A.nt;
+        for (int c = 0; c < 6; c++) out[(int64_t)c * A.nt + i] = nh[c] + ((double)fh[c] + (double)fl[c]);
+    }
+}
+
+__global__ void k_reduce6(const double* __restrict__ part, int nsplit, int nt, double* __restrict__ res)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    for (int c = 0; c < 6; c++) {
+        double s = 0.0;
+        for (int k = 0; k < nsplit; k++) s += part[((int64_t)k * 6 + c) * nt + i];
+        res[(int64_t)c * nt + i] = s;
+    }
+}
+
+bool g_hess_consts[64] = {false};
+
+int hess_constants(Ctx* ctx)
+{
+    if (ctx->device >= 0 && ctx->device < 64 && g_hess_consts[ctx->device]) return LSM_OK;
+    // c_k = (-1)^{k+1} 2k / (k! (2k+1)); h = (2/sqrt pi) sum_{k>=1} c_k w^{k-1},
+    // k = 2 dh/dw, kp = 2 dk/dw
+    long double c[kHSer + 4];
+    long double fact = 1.0L;
+    for (int k = 1; k < kHSer + 4; k++) {
+        fact *= k;
+        c[k] = ((k & 1) ? 1.0L : -1.0L) * (2.0L * k) / (fact * (2.0L * k + 1.0L));
+    }
+    const long double tsp = 2.0L / sqrtl(3.14159265358979323846264338327950288L);
+    double hh[kHSer], hk[kHSer], hkp[kHSer];
+    for (int m = 0; m < kHSer; m++) {
+        hh[m] = (double)(tsp * c[m + 1]);
+        hk[m] = (double)(tsp * c[m + 2] * (2.0L * (m + 2) - 2.0L));
+        hkp[m] = (double)(tsp * c[m + 3] * (2.0L * (m + 3) - 2.0L) * (2.0L * (m + 3) - 4.0L));
+    }
+    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_hh, hh, sizeof(hh)));
+    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_hk, hk, sizeof(hk)));
+    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_hkp, hkp, sizeof(hkp)));
+    if (ctx->device >= 0 && ctx->device < 64) g_hess_consts[ctx->device] = true;
+    return LSM_OK;
+}
+
+}  // namespace
+
+int hess_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, cudaStream_t st)
+{
+    if (t.n <= 0) return LSM_OK;
+    int rc = hess_constants(ctx);
+    if (rc != LSM_OK) return rc;
+    const int nblk = (t.n + kHessThreads - 1) / kHessThreads;
+    const int ntiles = (int)me->ntiles;
+    const int want = ctx->num_sms * 8;
+    int nsplit = 1;
+    if (nblk < want) nsplit = std::min((want + nblk - 1) / nblk, std::max(1, ntiles / 4));
+    const int tps = (ntiles + nsplit - 1) / nsplit;
+    nsplit = (ntiles + tps - 1) / tps;
+    Scratch s(st);
+    double* part = res;
+    if (nsplit > 1) LSM_CUDA_TRY(ctx, s.get(&part, (size_t)nsplit * 6 * t.n));
+    HessArgs A;
+    A.s32_pos = me->s32_pos;
+    A.s32_nw = me->s32_nw;
+    A.s64_pos = me->s64_pos;
+    A.s64_nw = me->s64_nw;
+    A.tlo = me->tile_lo;
+    A.thi = me->tile_hi;
+    A.tchi = me->tile_chi;
+    A.tclo = me->tile_clo;
+    A.ntiles = ntiles;
+    A.tiles_per_split = tps;
+    A.tx = t.x;
+    A.ld = t.ld;
+    A.nt = t.n;
+    A.cut2 = (float)(ctx->opt.cutoff_fp64 * ctx->opt.cutoff_fp64);
+    A.out = part;
+    k_eval_hess<<<dim3(nblk, nsplit), kHessThreads, 0, st>>>(A);
+    LSM_LAUNCHED(ctx);
+    if (nsplit > 1) {
+        k_reduce6<<<(t.n + 255) / 256, 256, 0, st>>>(part, nsplit, t.n, res);
+        LSM_LAUNCHED(ctx);
+    }
+    return LSM_OK;
+}
+
+}  // namespace lsm

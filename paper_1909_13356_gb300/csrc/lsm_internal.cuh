@@ -269,6 +269,14 @@ int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const 
 int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const double* g, const double* jac,
                    const double* x0, double* eps0, cudaStream_t st);
 
+// hess.cu: the Hessian of Phi [6][n] (xx, xy, xz, yy, yz, zz) at sorted
+// targets (per-triangle sigma meshes)
+int hess_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, cudaStream_t st);
+// frames.cu: chart second derivatives and curvatures; device arrays, nodes in
+// solve order
+int chart_second_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const double* g, const double* hess,
+                     double* xuu, double* xuv, double* xvv, double* kmean, double* kgauss, cudaStream_t st);
+
 // sigma.cu: target-dependent sigma (eq. sigma2)
 double sigma_sources_host(const double* verts, const int32_t* tris, int64_t nt, double lambda, double* sj,
                           double* cen);
