@@ -75,6 +75,10 @@ def _load():
             lib.or_radial_G.restype = ctypes.c_double
             lib.or_phi_grad_hess.argtypes = [I64, P, P, P, I64, P, P, P, P, ctypes.c_int]
             lib.or_chart_second.argtypes = [P, I64, P, P, ctypes.c_int, P, P, P, P, P, P, P, P, P, P]
+            lib.or_chart_nodes_at.argtypes = [P, P, P, P, I64, P, P, P, P, P]
+            lib.or_chart_frames_at.argtypes = [P, P, P, I64, P, P, P, P, P, P, P]
+            lib.or_gauss_flux_w.argtypes = [I64, P, P, P, P, P]
+            lib.or_gauss_flux_w.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -307,3 +311,58 @@ def chart_second(verts, tris, h, grad, hess, sigma=None, n: int = 6, uv=None):
     _load().or_chart_second(_p(verts), m, _p(tris), _p(geo["vpn"]), npn, _p(cu), _p(cv), _p(h), _p(grad),
                             _p(hess), _p(uu), _p(uv_), _p(vv), _p(km), _p(kg))
     return uu, uv_, vv, km, kg
+
+
+def refined_nodes(m: int, n: int, levels):
+    """Chart nodes of triangles refined 1 -> 4 levels[j] times (Sec. 3.4): for
+    each triangle in order, the n x n Duffy rule composited over its 4^L
+    midpoint children, as parent coordinates (u, v) and weights (summing to
+    1/2 per triangle).  Returns tri [N], uv [N, 2], w [N]."""
+    levels = np.asarray(levels, dtype=np.int64)
+    assert levels.shape == (m,)
+    rules = {}
+    tri, uv, w = [], [], []
+    for j in range(m):
+        L = int(levels[j])
+        if L not in rules:
+            rules[L] = simplex_rule(n, L)
+        u, v, ww = rules[L]
+        tri.append(np.full(len(u), j, dtype=np.int32))
+        uv.append(np.stack([u, v], 1))
+        w.append(ww)
+    return np.concatenate(tri), np.concatenate(uv), np.concatenate(w)
+
+
+def chart_nodes_at(verts, tris, tri, uv, sigma=None):
+    """x0 = T(u, v), H(u, v) and sigma of the triangle at explicit nodes."""
+    verts = _f64(verts)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    geo = geometry(verts, tris, sigma)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    uv = _f64(uv)
+    n = len(tri)
+    x0, hd, sl = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+    _load().or_chart_nodes_at(_p(verts), _p(tris), _p(geo["vpn"]), _p(geo["sigma"]), n, _p(tri), _p(uv),
+                              _p(x0), _p(hd), _p(sl))
+    return x0, hd, sl
+
+
+def chart_frames_at(verts, tris, tri, uv, h, grad, sigma=None):
+    """chart_frames at explicit nodes (triangle, parent (u, v))."""
+    verts = _f64(verts)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    geo = geometry(verts, tris, sigma)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    uv, h, grad = _f64(uv), _f64(h), _f64(grad)
+    n = len(tri)
+    xu, xv, jac = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+    _load().or_chart_frames_at(_p(verts), _p(tris), _p(geo["vpn"]), n, _p(tri), _p(uv), _p(h), _p(grad),
+                               _p(xu), _p(xv), _p(jac))
+    return xu, xv, jac
+
+
+def gauss_flux_w(x, grad, jac, w, x0) -> float:
+    """Gauss flux error with a quadrature weight per node (Sec. 5)."""
+    x, grad, jac, w = _f64(x), _f64(grad), _f64(jac), _f64(w)
+    x0 = _f64(np.asarray(x0, dtype=np.float64).reshape(3))
+    return _load().or_gauss_flux_w(len(x), _p(w), _p(x), _p(grad), _p(jac), _p(x0))

@@ -22,6 +22,8 @@
  *   - local coordinates x_u, x_v and da of the charts (eq. u_vector,
  *     U_vector_2, v_vector, v_vector_2, da) and the Gauss flux error eps0
  *     (Sec. 5)
+ *   - refined charts: nodes of the 1 -> 4 midpoint children of a triangle in
+ *     the parent's chart map (Sec. 3.4)
  *   - the Hessian of Phi and the charts' second derivatives and curvatures
  *     (Sec. 3.3, eq. uu_vector, uu_vector_aux1, uu_vector_aux2)
  *   - the target-dependent width sigma(x), a Gaussian-weighted mean of
@@ -796,4 +798,64 @@ void or_chart_second(const double* verts, int64_t m, const int32_t* tris, const 
             kmean[s] = -(E * Nn - 2.0 * F * M + G * L) / det;
         }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Refinement (Sec. 3.4, surface refinement): a triangle split 1 -> 4 at its
+ * edge midpoints, any number of times, keeps the chart map of its parent:
+ * nodes of the children are points (u, v) of the parent's reference
+ * triangle, x0 = T(u, v) and H(u, v) linear in the parent's (u, v).  Since H
+ * is linear along every edge, a midpoint's H equals the mean of the edge's
+ * end values whichever neighbour is refined, so the pseudonormal field stays
+ * continuous across refined and unrefined neighbours.  Node s lies in
+ * triangle tri[s] at (uv[2s], uv[2s+1]). */
+void or_chart_nodes_at(const double* verts, const int32_t* tris, const double* vpn, const double* sigma,
+                       int64_t n, const int32_t* tri, const double* uv, double* x0, double* hdir, double* sloc)
+{
+    for (int64_t s = 0; s < n; s++) {
+        const int64_t j = tri[s];
+        const double u = uv[2*s], v = uv[2*s+1];
+        const double* p1 = verts + 3 * (int64_t)tris[3*j+0];
+        const double* p2 = verts + 3 * (int64_t)tris[3*j+1];
+        const double* p3 = verts + 3 * (int64_t)tris[3*j+2];
+        const double* h1 = vpn + 3 * (int64_t)tris[3*j+0];
+        const double* h2 = vpn + 3 * (int64_t)tris[3*j+1];
+        const double* h3 = vpn + 3 * (int64_t)tris[3*j+2];
+        for (int c = 0; c < 3; c++) {
+            x0[3*s+c] = p1[c] + u * (p2[c] - p1[c]) + v * (p3[c] - p1[c]);
+            hdir[3*s+c] = h1[c] + u * (h2[c] - h1[c]) + v * (h3[c] - h1[c]);
+        }
+        sloc[s] = sigma[j];
+    }
+}
+
+/* or_chart_frames at explicit nodes (triangle and parent (u, v) per node). */
+void or_chart_frames_at(const double* verts, const int32_t* tris, const double* vpn, int64_t n,
+                        const int32_t* tri, const double* uv, const double* h, const double* grad, double* xu,
+                        double* xv, double* jac)
+{
+    for (int64_t s = 0; s < n; s++) {
+        const int64_t j = tri[s];
+        /* one node of triangle j: reuse the rule form with a one-point rule */
+        or_chart_frames(verts, 1, tris + 3 * j, vpn, 1, uv + 2*s, uv + 2*s + 1, h + s, grad + 3*s,
+                        xu + 3*s, xv + 3*s, jac + s);
+    }
+}
+
+/* Gauss flux error with a quadrature weight per node (w[s] in the parent's
+ * reference triangle, as the chart rule's weights). */
+double or_gauss_flux_w(int64_t n, const double* w, const double* x, const double* grad, const double* jac,
+                       const double* x0)
+{
+    double sum = 0.0;
+    for (int64_t s = 0; s < n; s++) {
+        const double* g = grad + 3*s;
+        const double gn = norm3(g);
+        double d[3];
+        for (int c = 0; c < 3; c++) d[c] = x0[c] - x[3*s+c];
+        const double r = norm3(d);
+        const double nd = -dot3(g, d) / gn;
+        sum += w[s] * jac[s] * nd / (4.0 * M_PI * r * r * r);
+    }
+    return 1.0 + sum;
 }

@@ -697,3 +697,57 @@ def test_gauss_bonnet_sphere_and_torus(oracle_mod, small_sphere_charts):
     st = oracle_mod.sources(t.verts, t.tris, None, 6, 0)
     # measured: 2.9e-5 at n = 5, 2.8e-7 at n = 7
     assert abs(_gauss_bonnet(oracle_mod, t, 7, st)) < 5e-6
+
+
+# ---------------------------------------------------------------- refinement (Sec. 3.4)
+
+def _refined_eps(oracle_mod, m, src, n, levels):
+    y, nw, sg = src
+    tri, uv, w = oracle_mod.refined_nodes(m.m, n, levels)
+    assert np.allclose(np.bincount(tri, weights=w, minlength=m.m), 0.5, rtol=1e-13)
+    x0, hd, sl = oracle_mod.chart_nodes_at(m.verts, m.tris, tri, uv)
+    r = oracle_mod.solve_charts(y, nw, sg, x0, hd, sl, tol=1e-14, max_iter=40)
+    assert (r["status"] == 0).all()
+    _, g = oracle_mod.phi_grad(y, nw, sg, r["x"])
+    _, _, jac = oracle_mod.chart_frames_at(m.verts, m.tris, tri, uv, r["h"], g)
+    return oracle_mod.gauss_flux_w(r["x"], g, jac, w, (0.05, -0.1, 0.02))
+
+
+def test_refinement_converges_and_stays_closed(oracle_mod, small_sphere_charts):
+    """1 -> 4 refinement of every triangle shrinks the flux error about 2^(2n)
+    per level; refining a random subset (non-conforming) keeps the charts
+    closed: its error stays between the unrefined and refined ones."""
+    m, src, geo = small_sphere_charts
+    n = 3
+    e = [abs(_refined_eps(oracle_mod, m, src, n, np.full(m.m, L))) for L in (0, 1, 2)]
+    # measured: 1.4e-5, 1.8e-7, 2.6e-9
+    assert e[0] > 30 * e[1] and e[1] > 30 * e[2]
+    mix = np.random.default_rng(64).integers(0, 2, m.m)
+    em = abs(_refined_eps(oracle_mod, m, src, n, mix))
+    assert e[1] < em < e[0]
+
+
+def test_refined_midpoint_meets_unrefined_neighbour(oracle_mod, small_sphere_charts):
+    """The midpoint of an edge shared by a refined and an unrefined triangle:
+    the chart point solved from either triangle's map is the same (T and the
+    linear H agree along the shared edge)."""
+    m, src, geo = small_sphere_charts
+    y, nw, sg = src
+    T = m.tris
+    j = 5
+    a, b = T[j][0], T[j][1]
+    k = next(i for i in range(m.m) if i != j and a in T[i] and b in T[i])
+
+    def uv_of(i, p, q):
+        """parent (u, v) of the midpoint of edge (p, q) of triangle i"""
+        loc = [list(T[i]).index(p), list(T[i]).index(q)]
+        bary = np.zeros(3)
+        bary[loc] = 0.5
+        return np.array([[bary[1], bary[2]]])
+
+    xs = []
+    for i in (j, k):
+        x0, hd, sl = oracle_mod.chart_nodes_at(m.verts, m.tris, np.array([i]), uv_of(i, a, b))
+        r = oracle_mod.solve_charts(y, nw, sg, x0, hd, sl, tol=1e-15, max_iter=40)
+        xs.append(r["x"][0])
+    assert np.abs(xs[0] - xs[1]).max() < 1e-13
