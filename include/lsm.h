@@ -314,6 +314,34 @@ int lsm_eval_hessian(lsm_mesh* mesh, const double* x, int64_t n, double* hess, v
 int lsm_chart_curvature(lsm_mesh* mesh, int order, const double* h, const double* grad, const double* hess,
                         double* xuu, double* xuv, double* xvv, double* kmean, double* kgauss, void* stream);
 
+/* Refined charts (Sec. 3.4).  A skeleton triangle split 1 -> 4 at its edge
+ * midpoints, level times, keeps its parent's chart map: its nodes are the
+ * order's n x n Duffy rule composited over the 4^level children, given as
+ * points (u, v) of the parent's reference triangle with weights (1/2 per
+ * triangle in all).  H stays linear in the parent's (u, v), so the
+ * pseudonormal field, and with it the charts, stay continuous between
+ * refined and unrefined neighbours.
+ *   order     chart order (n = order/2 + 2);  m, level [m] in 0..4 (host)
+ *   tri [N], uvw [N][3] out (host): triangle and (u, v, weight) per node, in
+ *             triangle order; pass NULL for both to get only *n_out = N =
+ *             sum_j n^2 4^level_j.
+ * Errors: LSM_E_INVALID_ARG. */
+int lsm_refined_nodes(int order, int64_t m, const int32_t* level, int32_t* tri, double* uvw, int64_t* n_out);
+/* lsm_solve_charts at explicit nodes: node s in triangle tri[s] at parent
+ * coordinates (uvw[3s], uvw[3s+1]) (for instance from lsm_refined_nodes).
+ * Outputs and behaviour as lsm_solve_charts, in the given node order.
+ * Errors: LSM_E_INVALID_ARG (also a triangle index out of range), LSM_E_OOM,
+ * LSM_E_CUDA. */
+int lsm_solve_charts_nodes(lsm_mesh* mesh, int64_t n, const int32_t* tri, const double* uvw, double tol,
+                           int max_iter, int precision, double* x_out, double* h_out, int32_t* status_out,
+                           lsm_solve_stats* stats, void* stream);
+/* lsm_chart_frames and lsm_gauss_flux at explicit nodes; the flux weights
+ * are uvw[3s+2]. */
+int lsm_chart_frames_nodes(lsm_mesh* mesh, int64_t n, const int32_t* tri, const double* uvw, const double* h,
+                           const double* grad, double* xu, double* xv, double* jac, void* stream);
+int lsm_gauss_flux_nodes(lsm_mesh* mesh, int64_t n, const int32_t* tri, const double* uvw, const double* x,
+                         const double* grad, const double* jac, const double* x0, double* eps0, void* stream);
+
 /* Autotuner of the mixed path's far field (the paper has no counterpart:
  * its FMM is run at a fixed precision, Sec. 4.4).  Chooses, for this mesh,
  * between the direct tiled far field and the treecode, and the treecode's

@@ -41,7 +41,8 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_batch_solve_charts", "lsm_server_create", "lsm_server_submit", "lsm_server_poll", "lsm_server_release",
            "lsm_server_info", "lsm_server_destroy", "lsm_autotune", "lsm_chart_frames", "lsm_gauss_flux",
            "lsm_mesh_upload_sigmax", "lsm_mesh_get_sigma0", "lsm_eval_sigma", "lsm_eval_hessian",
-           "lsm_chart_curvature")
+           "lsm_chart_curvature", "lsm_refined_nodes", "lsm_solve_charts_nodes", "lsm_chart_frames_nodes",
+           "lsm_gauss_flux_nodes")
 
 
 class LsmError(RuntimeError):
@@ -170,6 +171,10 @@ def load(build_if_needed: bool = True):
         L.lsm_eval_sigma.argtypes = [P, P, I64, P, P, P]
         L.lsm_eval_hessian.argtypes = [P, P, I64, P, P]
         L.lsm_chart_curvature.argtypes = [P, I32, P, P, P, P, P, P, P, P, P]
+        L.lsm_refined_nodes.argtypes = [I32, I64, P, P, P, ctypes.POINTER(I64)]
+        L.lsm_solve_charts_nodes.argtypes = [P, I64, P, P, D, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
+        L.lsm_chart_frames_nodes.argtypes = [P, I64, P, P, P, P, P, P, P, P]
+        L.lsm_gauss_flux_nodes.argtypes = [P, I64, P, P, P, P, P, P, P, P]
         L.lsm_gauss_flux.argtypes = [P, I32, P, P, P, P, P, P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
@@ -216,6 +221,22 @@ def _as(a, dtype):
         td = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
         return a.to(td).contiguous()
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def refined_nodes(order: int, levels):
+    """Chart nodes of triangles refined 1 -> 4 levels[j] times (lsm_refined_nodes,
+    host only): (tri [N], uvw [N, 3]) in the parents' coordinates."""
+    L = load()
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    n = ctypes.c_int64()
+    rc = L.lsm_refined_nodes(int(order), int(lv.shape[0]), _ptr(lv), None, None, ctypes.byref(n))
+    if rc != 0:
+        raise LsmError(rc, "lsm_refined_nodes: bad order or levels (0..4)")
+    tri, uvw = np.empty(n.value, dtype=np.int32), np.empty((n.value, 3))
+    rc = L.lsm_refined_nodes(int(order), int(lv.shape[0]), _ptr(lv), _ptr(tri), _ptr(uvw), ctypes.byref(n))
+    if rc != 0:
+        raise LsmError(rc, "lsm_refined_nodes failed")
+    return tri, uvw
 
 
 class Context:
@@ -380,6 +401,39 @@ class Mesh:
                                           _stream_handle(stream))
         self.ctx._check(rc)
         return xu, xv, jac
+
+    def solve_charts_nodes(self, tri, uvw, tol: float = 1e-12, max_iter: int = 20, precision: int = FP64,
+                           stream=None):
+        """Charts at explicit nodes (lsm_solve_charts_nodes): (x, h, status, SolveStats)."""
+        t, u = _as(tri, np.int32), _as(uvw, np.float64)
+        n = int(t.shape[0])
+        x, h, st = np.empty((n, 3)), np.empty(n), np.empty(n, dtype=np.int32)
+        stats = _Stats()
+        rc = self.ctx._L.lsm_solve_charts_nodes(self._h, n, _ptr(t), _ptr(u), float(tol), int(max_iter),
+                                                int(precision), _ptr(x), _ptr(h), _ptr(st), ctypes.byref(stats),
+                                                _stream_handle(stream))
+        self.ctx._check(rc)
+        return x, h, st, _stats(stats)
+
+    def chart_frames_nodes(self, tri, uvw, h, grad, stream=None):
+        t, u = _as(tri, np.int32), _as(uvw, np.float64)
+        hs, gs = _as(h, np.float64), _as(grad, np.float64)
+        n = int(t.shape[0])
+        xu, xv, jac = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+        rc = self.ctx._L.lsm_chart_frames_nodes(self._h, n, _ptr(t), _ptr(u), _ptr(hs), _ptr(gs), _ptr(xu), _ptr(xv),
+                                                _ptr(jac), _stream_handle(stream))
+        self.ctx._check(rc)
+        return xu, xv, jac
+
+    def gauss_flux_nodes(self, tri, uvw, x, grad, jac, x0, stream=None) -> float:
+        t, u = _as(tri, np.int32), _as(uvw, np.float64)
+        xs, gs, js = _as(x, np.float64), _as(grad, np.float64), _as(jac, np.float64)
+        p0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float64).reshape(3))
+        out = ctypes.c_double()
+        rc = self.ctx._L.lsm_gauss_flux_nodes(self._h, int(t.shape[0]), _ptr(t), _ptr(u), _ptr(xs), _ptr(gs), _ptr(js),
+                                              _ptr(p0), ctypes.byref(out), _stream_handle(stream))
+        self.ctx._check(rc)
+        return out.value
 
     def eval_hessian(self, x, stream=None):
         """Hessian of Phi [n, 6] = (xx, xy, xz, yy, yz, zz) at targets x [n, 3]

@@ -801,6 +801,162 @@ int lsm_gauss_flux(lsm_mesh* mh, int order, const double* x, const double* grad,
     return gauss_flux_dev(ctx, me, n_gl, xd, gd, jd, x0, eps0, st);
 }
 
+int lsm_refined_nodes(int order, int64_t m, const int32_t* level, int32_t* tri, double* uvw, int64_t* n_out)
+{
+    if (order < 0 || order > 40 || m < 1 || !level || !n_out) return LSM_E_INVALID_ARG;
+    const int n_gl = order / 2 + 2;
+    int64_t n = 0;
+    for (int64_t j = 0; j < m; j++) {
+        if (level[j] < 0 || level[j] > 4) return LSM_E_INVALID_ARG;
+        n += (int64_t)n_gl * n_gl << (2 * level[j]);
+    }
+    *n_out = n;
+    if (!tri || !uvw) return LSM_OK;
+    std::vector<double> rules[5];
+    int64_t k = 0;
+    for (int64_t j = 0; j < m; j++) {
+        const int L = level[j];
+        if (rules[L].empty()) {
+            rules[L].resize(3 * ((size_t)n_gl * n_gl << (2 * L)));
+            simplex_rule_host(n_gl, L, rules[L].data());
+        }
+        const int64_t cnt = (int64_t)rules[L].size() / 3;
+        for (int64_t i = 0; i < cnt; i++, k++) {
+            tri[k] = (int32_t)j;
+            for (int c = 0; c < 3; c++) uvw[3 * k + c] = rules[L][3 * i + c];
+        }
+    }
+    return LSM_OK;
+}
+
+namespace {
+// Copy explicit nodes to the device and check their triangles.
+int node_spec(Ctx* ctx, Scratch& s, const Mesh* me, int64_t n, const int32_t* tri, const double* uvw, NodeSpec* out,
+              cudaStream_t st)
+{
+    if (n < 1 || n >= ((int64_t)1 << 31) || !tri || !uvw) {
+        ctx->err = "chart nodes: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    std::vector<int32_t> ht;
+    const int32_t* tp = tri;
+    if (is_device_ptr(tri)) {
+        ht.resize((size_t)n);
+        LSM_CUDA_TRY(ctx, cudaMemcpy(ht.data(), tri, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        tp = ht.data();
+    }
+    for (int64_t k = 0; k < n; k++)
+        if (tp[k] < 0 || tp[k] >= me->m) {
+            ctx->err = "chart nodes: triangle index out of range";
+            return LSM_E_INVALID_ARG;
+        }
+    const int32_t* td;
+    const double* ud;
+    int rc = to_device(ctx, s, tri, (size_t)n, &td, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, uvw, 3 * (size_t)n, &ud, st);
+    if (rc) return rc;
+    *out = NodeSpec{n, td, ud};
+    return LSM_OK;
+}
+}  // namespace
+
+int lsm_solve_charts_nodes(lsm_mesh* mh, int64_t n, const int32_t* tri, const double* uvw, double tol, int max_iter,
+                           int precision, double* x_out, double* h_out, int32_t* status, lsm_solve_stats* stats,
+                           void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (!(tol > 0) || max_iter < 1 || max_iter > 1000 || (precision != LSM_FP64 && precision != LSM_MIXED)) {
+        ctx->err = "solve_charts_nodes: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch s(st);
+    NodeSpec spec;
+    int rc = node_spec(ctx, s, me, n, tri, uvw, &spec, st);
+    if (rc) return rc;
+    double *xo = x_out, *ho = h_out;
+    int32_t* so = status;
+    const bool xdev = x_out && is_device_ptr(x_out);
+    const bool hdev = h_out && is_device_ptr(h_out);
+    const bool sdev = status && is_device_ptr(status);
+    if (!xdev) LSM_CUDA_TRY(ctx, s.get(&xo, 3 * (size_t)n));
+    if (!hdev) LSM_CUDA_TRY(ctx, s.get(&ho, (size_t)n));
+    if (!sdev) LSM_CUDA_TRY(ctx, s.get(&so, (size_t)n));
+    rc = solve_charts_device(ctx, me, 1, tol, max_iter, precision, xo, ho, so, stats, st, &spec);
+    if (rc) return rc;
+    if (x_out && !xdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(x_out, xo, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (h_out && !hdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(h_out, ho, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (status && !sdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(status, so, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    return check_flag(ctx, st);
+}
+
+int lsm_chart_frames_nodes(lsm_mesh* mh, int64_t n, const int32_t* tri, const double* uvw, const double* h,
+                           const double* grad, double* xu, double* xv, double* jac, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (!h || !grad || !xu || !xv || !jac) {
+        ctx->err = "chart_frames_nodes: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch s(st);
+    NodeSpec spec;
+    int rc = node_spec(ctx, s, me, n, tri, uvw, &spec, st);
+    if (rc) return rc;
+    const size_t N = (size_t)n;
+    const double *hd, *gd;
+    rc = to_device(ctx, s, h, N, &hd, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, grad, 3 * N, &gd, st);
+    if (rc) return rc;
+    double *a = xu, *b = xv, *c = jac;
+    const bool adev = is_device_ptr(xu), bdev = is_device_ptr(xv), cdev = is_device_ptr(jac);
+    if (!adev) LSM_CUDA_TRY(ctx, s.get(&a, 3 * N));
+    if (!bdev) LSM_CUDA_TRY(ctx, s.get(&b, 3 * N));
+    if (!cdev) LSM_CUDA_TRY(ctx, s.get(&c, N));
+    rc = chart_frames_dev(ctx, me, 1, hd, gd, a, b, c, st, &spec);
+    if (rc) return rc;
+    if (!adev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(xu, a, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+    if (!bdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(xv, b, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+    if (!cdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(jac, c, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+int lsm_gauss_flux_nodes(lsm_mesh* mh, int64_t n, const int32_t* tri, const double* uvw, const double* x,
+                         const double* grad, const double* jac, const double* x0, double* eps0, void* stream)
+{
+    if (!mh) return LSM_E_INVALID_ARG;
+    Mesh* me = &mh->m;
+    Ctx* ctx = me->ctx;
+    if (!x || !grad || !jac || !x0 || !eps0) {
+        ctx->err = "gauss_flux_nodes: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch s(st);
+    NodeSpec spec;
+    int rc = node_spec(ctx, s, me, n, tri, uvw, &spec, st);
+    if (rc) return rc;
+    const size_t N = (size_t)n;
+    const double *xd, *gd, *jd;
+    rc = to_device(ctx, s, x, 3 * N, &xd, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, grad, 3 * N, &gd, st);
+    if (rc) return rc;
+    rc = to_device(ctx, s, jac, N, &jd, st);
+    if (rc) return rc;
+    return gauss_flux_dev(ctx, me, 1, xd, gd, jd, x0, eps0, st, &spec);
+}
+
 int lsm_solve_charts(lsm_mesh* mh, int order, double tol, int max_iter, int precision, double* x_out,
                      double* h_out, int32_t* status, lsm_solve_stats* stats, void* stream)
 {

@@ -15,6 +15,7 @@
 // around x0 (Sec. 5).  Both are elementwise FP64 work over the chart nodes;
 // the flux sum is reduced in a fixed order (per-block partials, then one
 // block), so it is deterministic.
+#include <algorithm>
 #include <vector>
 
 #include "lsm_internal.cuh"
@@ -25,16 +26,36 @@ namespace {
 constexpr int kFrameThreads = 256;
 constexpr double kFourPi = 12.566370614359172954;
 
+// Triangle, parent (u, v) and weight of node s: from the rule shared by all
+// triangles (s = j np + i), or given per node (tri, uvw).
+__device__ __forceinline__ void node_of(int64_t s, int np, const double* rule, const int32_t* tri,
+                                        const double* uvw, int64_t& j, double& u, double& v, double& w)
+{
+    if (tri) {
+        j = tri[s];
+        u = uvw[3 * s];
+        v = uvw[3 * s + 1];
+        w = uvw[3 * s + 2];
+    } else {
+        j = s / np;
+        const int i = (int)(s - j * np);
+        u = rule[3 * i];
+        v = rule[3 * i + 1];
+        w = rule[3 * i + 2];
+    }
+}
+
 __global__ void k_chart_frames(const double* __restrict__ verts, const int32_t* __restrict__ tris,
-                               const double* __restrict__ vpn, int64_t m, int np, const double* __restrict__ rule,
+                               const double* __restrict__ vpn, int64_t n, int np, const double* __restrict__ rule,
+                               const int32_t* __restrict__ tri, const double* __restrict__ uvw,
                                const double* __restrict__ h, const double* __restrict__ g, double* __restrict__ xu,
                                double* __restrict__ xv, double* __restrict__ jac)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= m * np) return;
-    const int64_t j = s / np;
-    const int i = (int)(s - j * np);
-    const double u = rule[3 * i], v = rule[3 * i + 1];
+    if (s >= n) return;
+    int64_t j;
+    double u, v, wq;
+    node_of(s, np, rule, tri, uvw, j, u, v, wq);
     const int a = tris[3 * j], b = tris[3 * j + 1], c = tris[3 * j + 2];
     double tu[3], tv[3], H[3], hu[3], hv[3], gs[3];
     for (int k = 0; k < 3; k++) {
@@ -146,7 +167,8 @@ __global__ void k_chart_second(const double* __restrict__ verts, const int32_t* 
 __global__ void __launch_bounds__(kFrameThreads) k_flux_partial(const double* __restrict__ x,
                                                                 const double* __restrict__ g,
                                                                 const double* __restrict__ jac, int64_t n, int np,
-                                                                const double* __restrict__ rule, double x0, double y0,
+                                                                const double* __restrict__ rule,
+                                                                const double* __restrict__ uvw, double x0, double y0,
                                                                 double z0, double* __restrict__ part)
 {
     __shared__ double sw[kFrameThreads / 32];
@@ -159,7 +181,8 @@ __global__ void __launch_bounds__(kFrameThreads) k_flux_partial(const double* __
         const double r2 = dx * dx + dy * dy + dz * dz;
         const double r = sqrt(r2);
         const double nd = -(gx * dx + gy * dy + gz * dz) / gn;
-        t = rule[3 * (s % np) + 2] * jac[s] * nd / (kFourPi * r2 * r);
+        const double wq = uvw ? uvw[3 * s + 2] : rule[3 * (s % np) + 2];
+        t = wq * jac[s] * nd / (kFourPi * r2 * r);
     }
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = t;
@@ -204,17 +227,18 @@ int upload_rule(Ctx* ctx, Scratch& s, int n_gl, double** rule, cudaStream_t st)
 }  // namespace
 
 int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const double* g, double* xu, double* xv,
-                     double* jac, cudaStream_t st)
+                     double* jac, cudaStream_t st, const NodeSpec* spec)
 {
     Scratch s(st);
     double* rule = nullptr;
-    int rc = upload_rule(ctx, s, n_gl, &rule, st);
+    int rc = upload_rule(ctx, s, std::max(1, n_gl), &rule, st);
     if (rc) return rc;
     const int np = n_gl * n_gl;
-    const int64_t n = me->m * np;
+    const int64_t n = spec ? spec->n : me->m * np;
     if (n == 0) return LSM_OK;
     k_chart_frames<<<(unsigned)((n + kFrameThreads - 1) / kFrameThreads), kFrameThreads, 0, st>>>(
-        me->verts, me->tris, me->vpn, me->m, np, rule, h, g, xu, xv, jac);
+        me->verts, me->tris, me->vpn, n, np, rule, spec ? spec->tri : nullptr, spec ? spec->uvw : nullptr, h, g, xu,
+        xv, jac);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }
@@ -236,20 +260,21 @@ int chart_second_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const 
 }
 
 int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const double* g, const double* jac,
-                   const double* x0, double* eps0, cudaStream_t st)
+                   const double* x0, double* eps0, cudaStream_t st, const NodeSpec* spec)
 {
     Scratch s(st);
     double* rule = nullptr;
-    int rc = upload_rule(ctx, s, n_gl, &rule, st);
+    int rc = upload_rule(ctx, s, std::max(1, n_gl), &rule, st);
     if (rc) return rc;
     const int np = n_gl * n_gl;
-    const int64_t n = me->m * np;
+    const int64_t n = spec ? spec->n : me->m * np;
     const int nb = (int)((n + kFrameThreads - 1) / kFrameThreads);
     double *part = nullptr, *out = nullptr;
     LSM_CUDA_TRY(ctx, s.get(&part, std::max(1, nb)));
     LSM_CUDA_TRY(ctx, s.get(&out, 1));
     if (nb > 0) {
-        k_flux_partial<<<nb, kFrameThreads, 0, st>>>(x, g, jac, n, np, rule, x0[0], x0[1], x0[2], part);
+        k_flux_partial<<<nb, kFrameThreads, 0, st>>>(x, g, jac, n, np, rule, spec ? spec->uvw : nullptr, x0[0], x0[1],
+                                                     x0[2], part);
         LSM_LAUNCHED(ctx);
     }
     k_flux_final<<<1, kFrameThreads, 0, st>>>(part, nb, out);

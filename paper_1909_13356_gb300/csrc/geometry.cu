@@ -324,7 +324,38 @@ __global__ void k_chart_nodes(const double* __restrict__ verts, const int32_t* _
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Chart nodes given explicitly: node s in triangle tri[s] at parent
+// coordinates (uvw[3s], uvw[3s+1]) (refined charts keep their parent's map,
+// Sec. 3.4).
+__global__ void k_chart_nodes_at(const double* __restrict__ verts, const int32_t* __restrict__ tris,
+                                 const double* __restrict__ vpn, const double* __restrict__ tri_sigma, int64_t n,
+                                 const int32_t* __restrict__ tri, const double* __restrict__ uvw,
+                                 double* __restrict__ x0, double* __restrict__ hdir, double* __restrict__ sloc)
+{
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t j = tri[s];
+    const double u = uvw[3 * s], v = uvw[3 * s + 1];
+    const int ia = tris[3 * j], ib = tris[3 * j + 1], ic = tris[3 * j + 2];
+    for (int c = 0; c < 3; c++) {
+        const double p1 = verts[3 * ia + c], h1 = vpn[3 * ia + c];
+        x0[3 * s + c] = p1 + u * (verts[3 * ib + c] - p1) + v * (verts[3 * ic + c] - p1);
+        hdir[3 * s + c] = h1 + u * (vpn[3 * ib + c] - h1) + v * (vpn[3 * ic + c] - h1);
+    }
+    sloc[s] = tri_sigma[j];
+}
+
 }  // namespace
+
+int chart_nodes_at(Ctx* ctx, const Mesh* me, int64_t n, const int32_t* tri, const double* uvw, double* x0,
+                   double* hdir, double* sloc, cudaStream_t st)
+{
+    if (n <= 0) return LSM_OK;
+    k_chart_nodes_at<<<blocks_for(n, 256), 256, 0, st>>>(me->verts, me->tris, me->vpn, me->tri_sigma, n, tri, uvw,
+                                                         x0, hdir, sloc);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
 
 // Morton permutation of n points (AoS, `stride` doubles per point).
 int morton_order_points(Ctx* ctx, const double* pts, int stride, int n, uint32_t* perm,

@@ -180,6 +180,9 @@ int morton_order_points(Ctx* ctx, const double* pts, int stride, int n, uint32_t
                         cudaStream_t st);
 int chart_nodes_init(Ctx* ctx, const Mesh* mesh, const double* chart_rule_dev, int np,
                      double* x0, double* hdir, double* sloc, cudaStream_t st);
+// chart nodes at explicit (triangle, parent u, v) (device arrays)
+int chart_nodes_at(Ctx* ctx, const Mesh* mesh, int64_t n, const int32_t* tri, const double* uvw, double* x0,
+                   double* hdir, double* sloc, cudaStream_t st);
 int chart_nodes_raw(Ctx* ctx, const double* verts, const int32_t* tris, const double* vpn, const double* tri_sigma,
                     int64_t m, const double* chart_rule_dev, int np, double* x0, double* hdir, double* sloc,
                     cudaStream_t st);
@@ -204,6 +207,15 @@ inline SourceView view_of_batch(const Batch* b)
 }
 
 // eval.cu
+// Explicit chart nodes (device arrays): node s in triangle tri[s] at parent
+// coordinates uvw[3s], uvw[3s+1]; replaces the rule of order n_gl
+// (weight uvw[3s+2]).
+struct NodeSpec {
+    int64_t n;
+    const int32_t* tri;
+    const double* uvw;
+};
+
 struct Targets {
     const double* x;  // SoA: x[0..n), y = x + ld, z = x + 2 ld
     int64_t ld;
@@ -264,10 +276,11 @@ int tree_lists(Ctx* ctx, const Tree* tree, const Targets& t, int tpb, const doub
 
 // frames.cu: chart local coordinates and the Gauss flux (lsm_chart_frames,
 // lsm_gauss_flux); all arrays on the device, nodes in solve order
+// spec: explicit nodes (their parent u, v and weight in uvw) instead of the rule
 int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const double* g, double* xu, double* xv,
-                     double* jac, cudaStream_t st);
+                     double* jac, cudaStream_t st, const NodeSpec* spec = nullptr);
 int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const double* g, const double* jac,
-                   const double* x0, double* eps0, cudaStream_t st);
+                   const double* x0, double* eps0, cudaStream_t st, const NodeSpec* spec = nullptr);
 
 // hess.cu: the Hessian of Phi [6][n] (xx, xy, xz, yy, yz, zz) at sorted
 // targets (per-triangle sigma meshes)
@@ -292,7 +305,7 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
 // newton.cu
 int solve_charts_device(Ctx* ctx, Mesh* mesh, int n_gl, double tol, int max_iter,
                         int precision, double* x_out, double* h_out, int32_t* status_out,
-                        lsm_solve_stats* stats, cudaStream_t st);
+                        lsm_solve_stats* stats, cudaStream_t st, const NodeSpec* spec = nullptr);
 
 int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, int precision, int use_graph,
                        double* x_out, double* h_out, int32_t* status_out, lsm_solve_stats* stats,

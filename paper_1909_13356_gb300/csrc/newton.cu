@@ -244,10 +244,10 @@ inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, int precision,
                         double* x_out, double* h_out, int32_t* status_out, lsm_solve_stats* stats,
-                        cudaStream_t st)
+                        cudaStream_t st, const NodeSpec* spec)
 {
     const int np = n_gl * n_gl;
-    const int64_t N64 = me->m * (int64_t)np;
+    const int64_t N64 = spec ? spec->n : me->m * (int64_t)np;
     if (N64 >= (int64_t)1 << 31) {
         ctx->err = "too many chart nodes";
         return LSM_E_INVALID_ARG;
@@ -268,7 +268,8 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
     LSM_CUDA_TRY(ctx, s.get(&x0a, 3 * (size_t)N));
     LSM_CUDA_TRY(ctx, s.get(&hda, 3 * (size_t)N));
     LSM_CUDA_TRY(ctx, s.get(&sla, (size_t)N));
-    int rc = chart_nodes_init(ctx, me, rule_d, np, x0a, hda, sla, st);
+    int rc = spec ? chart_nodes_at(ctx, me, spec->n, spec->tri, spec->uvw, x0a, hda, sla, st)
+                  : chart_nodes_init(ctx, me, rule_d, np, x0a, hda, sla, st);
     if (rc) return rc;
     uint32_t* perm;
     LSM_CUDA_TRY(ctx, s.get(&perm, (size_t)N));

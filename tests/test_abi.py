@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_1909_13356_gb300 as lsm
@@ -70,3 +71,17 @@ def test_options_struct_matches_header_layout():
     """The binding's lsm_options has the header's size (reserved words keep
     the size fixed as fields are added)."""
     assert ctypes.sizeof(lsm._Options) == 4 * 8 + 8 * 4
+
+
+def test_refined_nodes_match_the_oracle_rule(oracle_mod):
+    """lsm_refined_nodes (host code of the library): per triangle the order's
+    Duffy rule composited over 4^level midpoint children, against the
+    oracle's composite rule."""
+    levels = np.array([0, 2, 1, 0, 3], dtype=np.int32)
+    tri, uvw = lsm.refined_nodes(8, levels)
+    otri, ouv, ow = oracle_mod.refined_nodes(len(levels), 6, levels)
+    assert np.array_equal(tri, otri)
+    assert np.allclose(uvw[:, :2], ouv, rtol=0, atol=1e-15)
+    assert np.allclose(uvw[:, 2], ow, rtol=1e-13, atol=0)
+    with pytest.raises(lsm.LsmError):
+        lsm.refined_nodes(8, np.array([5]))
