@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="small torus (quick check)")
     ap.add_argument("--cells", default=None,
                     help="torus cells NUxNV (default 240x64); e.g. 120x32 for a profiling case")
-    ap.add_argument("--workload", default="torus", choices=["torus", "ellipsoids", "serve", "icosphere"],
+    ap.add_argument("--workload", default="torus",
+                    choices=["torus", "ellipsoids", "serve", "icosphere", "geometry"],
                     help="torus: the default line; ellipsoids: 512 meshes in one batched, graph-captured "
                          "solve; serve: a Poisson request stream through the server")
     ap.add_argument("--requests", type=int, default=200)
@@ -395,6 +396,102 @@ def bench_icosphere(args):
     }))
 
 
+FLOPS_HESS_FAR = 60    # Hessian of the double layer per far pair (FP32; rsqrt not counted)
+FLOPS_HESS_NEAR = 90   # Hessian of the smoothed kernel per near pair (FP64; erf, exp not counted)
+
+
+def bench_geometry(args):
+    """Chart geometry on the graded torus: the charts are solved once (mixed,
+    order 8, to 1e-12) and grad Phi taken on the float-float path, untimed;
+    a step then evaluates the Hessian of Phi at every chart node, the frames,
+    second derivatives and curvatures, the Gauss flux and the Gauss-Bonnet
+    integral.  value = chart nodes per second."""
+    import torch
+    import paper_1909_13356_gb300 as lsm
+    w = workload(args, 0)
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
+    x, h, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=lsm.MIXED, device_out=True)
+    _, g = mesh.eval_phi_grad(x, lsm.FF)
+    n = int(h.shape[0])
+    wq = torch.from_numpy(np.tile(_duffy_weights(args.order // 2 + 2), m.m)).cuda()
+    out = {}
+
+    def step():
+        H = mesh.eval_hessian(x)
+        _, _, jac = mesh.chart_frames(args.order, h, g)
+        _, _, _, km, kg = mesh.chart_curvature(args.order, h, g, H)
+        out["eps0"] = mesh.gauss_flux(args.order, x, g, jac, (1.0, 0.0, 0.0))
+        out["gb"] = float((wq * jac * kg).sum())
+        out["km"] = (float(km.min()), float(km.max()))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.read_stats(reset=True)
+    ctx.set_profiling(True)
+    l0 = ctx.launch_count
+    clk = ClockSampler(0)
+    clk.start()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ctx.set_profiling(False)
+    stats = ctx.read_stats(reset=True)
+    ms = a.elapsed_time(b) / args.steps
+    ms_k = stats["kind_ms"][3]
+    far, near = stats["kind_pairs_far"][3], stats["kind_pairs_near"][3]
+    p32 = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    p64 = p32 / 64.0
+    f32 = far * FLOPS_HESS_FAR / (ms_k / 1e3) / 1e12
+    f64 = near * FLOPS_HESS_NEAR / (ms_k / 1e3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline_hessian(w, args.cpu_seconds, w["rule"]["n"], x.cpu().numpy())
+    print(json.dumps({
+        "metric": "chart_geometry_nodes_per_s", "value": n / (ms / 1e3), "unit": "chart nodes/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 near + f32 far", "data": "synthetic",
+        "config": {"workload": w["name"] + "_chart_geometry", "chart_order": args.order, "chart_nodes": n,
+                   "step": "Hessian at every node, frames, second derivatives, curvatures, Gauss flux, "
+                           "Gauss-Bonnet integral",
+                   "l2": "inputs larger than L2 (1.1e6 nodes x 13 doubles; 1.1e6 sources)"},
+        "gpu_launches": (ctx.launch_count - l0) // max(1, args.steps),
+        "roofline": {"bound": "alu", "kernel": "k_eval_hess", "achieved": f32 + f64, "unit": "TFLOP/s",
+                     "peak": None, "frac": f32 / p32 + f64 / p64, "traffic": None,
+                     "frac_fp32_far": f32 / p32, "frac_fp64_near": f64 / p64,
+                     "note": "far pairs on the FP32 pipe, near pairs on the FP64 pipe: frac is the sum of the two "
+                             "pipes' fractions",
+                     "pairs_far": far, "pairs_near": near, "share_of_step": ms_k / (ms * args.steps)},
+        "eps0": out["eps0"], "gauss_bonnet_integral_K": out["gb"], "mean_curvature_range": out["km"],
+        "clocks": clocks, "cpu_baseline": cpu,
+    }))
+
+
+def cpu_baseline_hessian(w, seconds, rule_n, nodes):
+    """The FP64 oracle's Phi, grad Phi and Hessian (direct sums) on a sample of
+    chart nodes, all host cores."""
+    import oracle
+    m = w["mesh"]
+    y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, rule_n, 0)
+    ncal = 4 * (os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    oracle.phi_grad_hess(y, nw, sg, nodes[:ncal])
+    dt = time.perf_counter() - t0
+    k = int(max(ncal, min(len(nodes), ncal * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.phi_grad_hess(y, nw, sg, nodes[:k])
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "chart nodes/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{k} of {len(nodes)} chart nodes, FP64 Phi, grad, Hessian by direct sums ({dt:.1f} s)"}
+
+
 def main():
     args = parse()
     if args.workload == "icosphere" and args.impl == "ours":
@@ -405,6 +502,9 @@ def main():
         return
     if args.workload == "serve" and args.impl == "ours":
         bench_serve(args)
+        return
+    if args.workload == "geometry" and args.impl == "ours":
+        bench_geometry(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

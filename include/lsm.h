@@ -162,11 +162,12 @@ typedef struct {
                                       profiling was on */
     double pair_kernel_ms;         /* their summed device time (CUDA events
                                       recorded on the launching stream) */
-    /* the same per pair kernel: [0] mixed, [1] float-float, [2] FP64 */
-    int64_t kind_pairs_near[3];
-    int64_t kind_pairs_far[3];
-    int64_t kind_launches[3];
-    double kind_ms[3];
+    /* the same per pair kernel: [0] mixed, [1] float-float, [2] FP64,
+       [3] the Hessian kernel (lsm_eval_hessian) */
+    int64_t kind_pairs_near[4];
+    int64_t kind_pairs_far[4];
+    int64_t kind_launches[4];
+    double kind_ms[4];
 } lsm_ctx_stats;
 
 /* Turn per-launch timing of the pair kernels on or off (off by default). */

@@ -75,9 +75,9 @@ class _Stats(ctypes.Structure):
 class _CtxStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("pairs_near", ctypes.c_int64),
                 ("pairs_far", ctypes.c_int64), ("pair_kernel_launches", ctypes.c_int64),
-                ("pair_kernel_ms", ctypes.c_double), ("kind_pairs_near", ctypes.c_int64 * 3),
-                ("kind_pairs_far", ctypes.c_int64 * 3), ("kind_launches", ctypes.c_int64 * 3),
-                ("kind_ms", ctypes.c_double * 3)]
+                ("pair_kernel_ms", ctypes.c_double), ("kind_pairs_near", ctypes.c_int64 * 4),
+                ("kind_pairs_far", ctypes.c_int64 * 4), ("kind_launches", ctypes.c_int64 * 4),
+                ("kind_ms", ctypes.c_double * 4)]
 
 
 class _Info(ctypes.Structure):

@@ -255,8 +255,8 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     int rc = LSM_OK;
     if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->d_flag, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_flag, 0, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&ctx->d_pairs, 6 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(ctx->d_pairs, 0, 6 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&ctx->d_pairs, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_pairs, 0, 8 * sizeof(unsigned long long)) != cudaSuccess) {
         delete c;
         return LSM_E_CUDA;
     }
@@ -311,13 +311,13 @@ int lsm_read_stats(lsm_ctx* c, lsm_ctx_stats* out, int reset)
         cudaEventDestroy(e.b);
     }
     ctx->prof_events.clear();
-    unsigned long long pr[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long pr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     LSM_CUDA_TRY(ctx, cudaMemcpy(pr, ctx->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
     out->launches = ctx->launches.load();
     out->pairs_near = out->pairs_far = 0;
     out->pair_kernel_launches = 0;
     out->pair_kernel_ms = 0.0;
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < 4; k++) {
         out->kind_pairs_near[k] = (int64_t)pr[2 * k];
         out->kind_pairs_far[k] = (int64_t)pr[2 * k + 1];
         out->kind_launches[k] = ctx->prof_launches[k];
@@ -329,7 +329,7 @@ int lsm_read_stats(lsm_ctx* c, lsm_ctx_stats* out, int reset)
     }
     if (reset) {
         LSM_CUDA_TRY(ctx, cudaMemset(ctx->d_pairs, 0, sizeof(pr)));
-        for (int k = 0; k < 3; k++) {
+        for (int k = 0; k < 4; k++) {
             ctx->prof_ms[k] = 0.0;
             ctx->prof_launches[k] = 0;
         }

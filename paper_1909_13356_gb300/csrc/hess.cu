@@ -86,6 +86,7 @@ struct HessArgs {
     int nt;
     float cut2;
     double* out;                  // [split][6][nt]
+    unsigned long long* pairs;    // [2] pairs in near / far tiles
 };
 
 __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
@@ -140,6 +141,7 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
         fh[c] = fl[c] = 0.0f;
         nh[c] = 0.0;
     }
+    unsigned long long pn = 0, pf = 0;
     for (int t = t0; t < t1; t++) {
         const float4 tl = A.tlo[t], th = A.thi[t];
         const float gx = fmaxf(0.0f, fmaxf(tl.x - bb[3], bb[0] - th.x));
@@ -147,6 +149,12 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
         const float gz = fmaxf(0.0f, fmaxf(tl.z - bb[5], bb[2] - th.z));
         const bool far = gx * gx + gy * gy + gz * gz > A.cut2 * tl.w * tl.w * 1.0001f;
         const int cnt = (int)th.w;
+        if (valid) {
+            if (far)
+                pf += cnt;
+            else
+                pn += cnt;
+        }
         const int64_t j = (int64_t)t * kTile + tid;
         if (tid < cnt) {
             if (far) {
@@ -208,6 +216,14 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
     if (valid) {
         double* out = A.out + (int64_t)blockIdx.y * 6 * A.nt;
         for (int c = 0; c < 6; c++) out[(int64_t)c * A.nt + i] = nh[c] + ((double)fh[c] + (double)fl[c]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        pn += __shfl_xor_sync(0xffffffffu, pn, o);
+        pf += __shfl_xor_sync(0xffffffffu, pf, o);
+    }
+    if ((tid & 31) == 0) {
+        if (pn) atomicAdd(A.pairs, pn);
+        if (pf) atomicAdd(A.pairs + 1, pf);
     }
 }
 
@@ -282,8 +298,19 @@ int hess_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, cudaStr
     A.nt = t.n;
     A.cut2 = (float)(ctx->opt.cutoff_fp64 * ctx->opt.cutoff_fp64);
     A.out = part;
+    A.pairs = ctx->d_pairs + 6;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (ctx->profiling) {
+        LSM_CUDA_TRY(ctx, cudaEventCreate(&ev0));
+        LSM_CUDA_TRY(ctx, cudaEventCreate(&ev1));
+        LSM_CUDA_TRY(ctx, cudaEventRecord(ev0, st));
+    }
     k_eval_hess<<<dim3(nblk, nsplit), kHessThreads, 0, st>>>(A);
     LSM_LAUNCHED(ctx);
+    if (ctx->profiling) {
+        LSM_CUDA_TRY(ctx, cudaEventRecord(ev1, st));
+        ctx->prof_events.push_back(Ctx::ProfEvent{ev0, ev1, 3});
+    }
     if (nsplit > 1) {
         k_reduce6<<<(t.n + 255) / 256, 256, 0, st>>>(part, nsplit, t.n, res);
         LSM_LAUNCHED(ctx);

@@ -48,15 +48,15 @@ struct Ctx {
     ErrorText err;
     std::atomic<int64_t> launches{0};
     int* d_flag = nullptr;   // device error word (bounded waits, bad sizes)
-    unsigned long long* d_pairs = nullptr;  // [3 kinds][2]: pairs in near / far tiles
+    unsigned long long* d_pairs = nullptr;  // [4 kinds][2]: pairs in near / far tiles
     bool profiling = false;
     struct ProfEvent {
         cudaEvent_t a, b;
         int kind;
     };
     std::vector<ProfEvent> prof_events;
-    double prof_ms[3] = {0.0, 0.0, 0.0};
-    int64_t prof_launches[3] = {0, 0, 0};
+    double prof_ms[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t prof_launches[4] = {0, 0, 0, 0};
 };
 
 struct Tree;
