@@ -1270,6 +1270,8 @@ __global__ void k_reduce_splits(const double* __restrict__ part, int nsplit, int
     for (int c = 0; c < 4; c++) res[(int64_t)c * nt + i] = s[c];
 }
 
+}  // namespace
+
 // H(w) = g(u)/u^3, w = u^2, in long double: the power series for w < 1,
 // the closed form with erfl/expl otherwise.
 long double h_of_w(long double w)
@@ -1292,40 +1294,50 @@ long double h_of_w(long double w)
     return g / (u * u * u);
 }
 
+// Monomial coefficients (about the interval's centre) of the degree-6
+// polynomial interpolating H at 7 Chebyshev points of interval k, which
+// covers w in [k, k+1)/per_unit; long double throughout.
+void h_interval_fit(int k, int per_unit, long double* cf)
+{
+    const int deg = 6;
+    const long double h = 0.5L / per_unit;
+    const long double wc = (k + 0.5L) / per_unit;
+    long double V[7][8];
+    for (int r = 0; r <= deg; r++) {
+        const long double t = h * cosl(3.14159265358979323846264338327950288L * (r + 0.5L) / (deg + 1));
+        long double tp = 1.0L;
+        for (int j = 0; j <= deg; j++) {
+            V[r][j] = tp;
+            tp *= t;
+        }
+        V[r][deg + 1] = h_of_w(wc + t);
+    }
+    // Gaussian elimination with partial pivoting
+    for (int c = 0; c <= deg; c++) {
+        int piv = c;
+        for (int r = c + 1; r <= deg; r++)
+            if (fabsl(V[r][c]) > fabsl(V[piv][c])) piv = r;
+        for (int j = 0; j <= deg + 1; j++) std::swap(V[c][j], V[piv][j]);
+        for (int r = 0; r <= deg; r++) {
+            if (r == c) continue;
+            const long double f = V[r][c] / V[c][c];
+            for (int j = c; j <= deg + 1; j++) V[r][j] -= f * V[c][j];
+        }
+    }
+    for (int j = 0; j <= deg; j++) cf[j] = V[j][deg + 1] / V[j][j];
+}
+
+namespace {
+
 // Piecewise polynomial table of H: interval k covers w in [k, k+1)/kHTabPerUnit,
 // p(t) = sum_j c_j t^j with t = w - centre, interpolating H at 7 Chebyshev
-// points (monomial coefficients by solving the Vandermonde system).
+// points (h_interval_fit).
 // Layout per interval: {c0h, c0l, c1h, c1l}, {c2h, c2l, c3, c4}, {c5, c6, 0, 0}.
 void build_h_table(float4* out)
 {
-    const int deg = 6;
-    const long double h = 0.5L / kHTabPerUnit;
     for (int k = 0; k < kHTabN; k++) {
-        const long double wc = (k + 0.5L) / kHTabPerUnit;
-        long double V[7][8];
-        for (int r = 0; r <= deg; r++) {
-            const long double t = h * cosl(3.14159265358979323846264338327950288L * (r + 0.5L) / (deg + 1));
-            long double tp = 1.0L;
-            for (int j = 0; j <= deg; j++) {
-                V[r][j] = tp;
-                tp *= t;
-            }
-            V[r][deg + 1] = h_of_w(wc + t);
-        }
-        // Gaussian elimination with partial pivoting
-        for (int c = 0; c <= deg; c++) {
-            int piv = c;
-            for (int r = c + 1; r <= deg; r++)
-                if (fabsl(V[r][c]) > fabsl(V[piv][c])) piv = r;
-            for (int j = 0; j <= deg + 1; j++) std::swap(V[c][j], V[piv][j]);
-            for (int r = 0; r <= deg; r++) {
-                if (r == c) continue;
-                const long double f = V[r][c] / V[c][c];
-                for (int j = c; j <= deg + 1; j++) V[r][j] -= f * V[c][j];
-            }
-        }
         long double cf[7];
-        for (int j = 0; j <= deg; j++) cf[j] = V[j][deg + 1] / V[j][j];
+        h_interval_fit(k, kHTabPerUnit, cf);
         auto hi = [](long double v) { return (float)v; };
         auto lo = [](long double v) { return (float)(v - (long double)(float)v); };
         out[3 * k + 0] = make_float4(hi(cf[0]), lo(cf[0]), hi(cf[1]), lo(cf[1]));

@@ -8,17 +8,18 @@
 // nw' = nw / 4 pi (the resident weights):
 //   f -> a^3 h,   F -> a^5 k,   G -> a^7 kp,
 //   k = h'(u)/u = 2 dh/dw,  kp = k'(u)/u = 2 dk/dw,
-// summed as power series in w below w = 1/4, else from the closed forms
-//   h = g/u^3,  k = (4/sqrt pi) e^-w / u^2 - 3 g / u^5,
-//   kp = 15 g / u^7 - (4/sqrt pi) e^-w (2/u^2 + 5/u^4);
-// beyond the cutoff they are the Laplace limits 1/rho^3, -3/rho^5, 15/rho^7.
+// read from a piecewise polynomial table of h in w (FP64); beyond the cutoff
+// they are the Laplace limits 1/rho^3, -3/rho^5, 15/rho^7.
 //
 // Near the level set the Hessian's curvature part is a small fraction of
 // its terms, which cancel: near tiles are summed in FP64.  Far tiles (the
 // Laplace double layer, no cancellation of note) are summed in FP32 on
-// tile-local coordinates with compensated accumulation.  The far field is
-// the direct tiled sum; a CTA owns 128 sorted targets and walks a range of
-// tiles (a grid row per split, partials reduced in a fixed order).
+// tile-local coordinates with compensated accumulation.  A CTA owns 128
+// sorted targets and walks a range of tiles (a grid row per split, partials
+// reduced in a fixed order): all tiles, or on a large mesh the interaction
+// list of the mixed path's treecode built for this kernel's near radius
+// (proxy tiles are far; x-derivatives of the interpolated kernel are the
+// interpolated derivatives).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -29,41 +30,39 @@ namespace lsm {
 namespace {
 
 constexpr int kHessThreads = kTile;   // one target per thread, tiles staged by one load per thread
-constexpr int kHSer = 16;             // series terms for w < 1/4
-constexpr double kHSerW = 0.25;
-constexpr double kFourOverSqrtPiH = 2.25675833419102514780;
-constexpr double kTwoOverSqrtPiH = 1.12837916709551257390;
+// FP64 table of h(w) = g(u)/u^3: interval k covers w in [k, k+1)/16 up to
+// w = 32.5, the degree-6 interpolant about the interval's centre (fitted in
+// long double at setup, 8 doubles per interval).  h, dh/dw and d2h/dw2 come
+// from the same polynomial: k = 2 dh/dw, kp = 4 d2h/dw2.  Beyond the table
+// (|r| > 8 sigma) the Laplace limits hold to about 1e-11 relative.
+constexpr int kH64PerUnit = 16;
+constexpr int kH64N = 520;
+constexpr double kH64Wmax = (double)kH64N / kH64PerUnit;
+__device__ double g_htab64[kH64N * 8];
 
-__constant__ double c_hh[kHSer];    // h = sum c_hh[m] w^m
-__constant__ double c_hk[kHSer];    // k
-__constant__ double c_hkp[kHSer];   // kp
-
-__device__ __forceinline__ void radial3(double r2, double a, double& fH, double& FK, double& GK)
+__device__ __forceinline__ void radial3(double r2, double a, const double* __restrict__ tab, double& fH,
+                                        double& FK, double& GK)
 {
     const double w = r2 * a * a;
-    double h, k, kp;
-    if (w < kHSerW) {
-        h = c_hh[kHSer - 1];
-        k = c_hk[kHSer - 1];
-        kp = c_hkp[kHSer - 1];
-        for (int m = kHSer - 2; m >= 0; m--) {
-            h = fma(h, w, c_hh[m]);
-            k = fma(k, w, c_hk[m]);
-            kp = fma(kp, w, c_hkp[m]);
-        }
+    if (w < kH64Wmax) {
+        const int k = min((int)(w * (double)kH64PerUnit), kH64N - 1);
+        const double t = w - ((double)k + 0.5) * (1.0 / kH64PerUnit);
+        const double* c = tab + 8 * k;
+        const double h = fma(fma(fma(fma(fma(fma(c[6], t, c[5]), t, c[4]), t, c[3]), t, c[2]), t, c[1]), t, c[0]);
+        const double d1 =
+            fma(fma(fma(fma(fma(6.0 * c[6], t, 5.0 * c[5]), t, 4.0 * c[4]), t, 3.0 * c[3]), t, 2.0 * c[2]), t, c[1]);
+        const double d2 = fma(fma(fma(fma(30.0 * c[6], t, 20.0 * c[5]), t, 12.0 * c[4]), t, 6.0 * c[3]), t, 2.0 * c[2]);
+        const double a2 = a * a, a3 = a2 * a;
+        fH = a3 * h;
+        FK = a3 * a2 * 2.0 * d1;
+        GK = a3 * a2 * a2 * 4.0 * d2;
     } else {
-        const double u = sqrt(w);
-        const double e = exp(-w);
-        const double g = erf(u) - kTwoOverSqrtPiH * u * e;
-        const double iu = 1.0 / u, iu2 = iu * iu;
-        h = g * iu2 * iu;
-        k = kFourOverSqrtPiH * e * iu2 - 3.0 * g * iu2 * iu2 * iu;
-        kp = 15.0 * g * iu2 * iu2 * iu2 * iu - kFourOverSqrtPiH * e * (2.0 * iu2 + 5.0 * iu2 * iu2);
+        const double ri = rsqrt(r2);
+        const double ri2 = ri * ri;
+        fH = ri2 * ri;
+        FK = -3.0 * fH * ri2;
+        GK = 15.0 * fH * ri2 * ri2;
     }
-    const double a2 = a * a, a3 = a2 * a;
-    fH = a3 * h;
-    FK = a3 * a2 * k;
-    GK = a3 * a2 * a2 * kp;
 }
 
 __device__ __forceinline__ void tsum(float& hi, float& lo, float x)
@@ -87,20 +86,38 @@ struct HessArgs {
     float cut2;
     double* out;                  // [split][6][nt]
     unsigned long long* pairs;    // [2] pairs in near / far tiles
+    // treecode lists (optional): block b walks list[blist[b].x .. + blist[b].y),
+    // launched in the order border; ids >= ntiles are proxy tiles (ppos, pnw)
+    const int* list;
+    const int2* blist;
+    const int* border;
+    const float4* ppos;
+    const float4* pnw;
 };
 
 __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
 {
     __shared__ float4 sp[kTile], sn[kTile];
     __shared__ double4_32a dp[kTile], dn[kTile];
+    __shared__ double s_tab[kH64N * 8];
     __shared__ float part[6][kHessThreads / 32];
     __shared__ float bb[6];
     const int tid = threadIdx.x;
-    const int i = blockIdx.x * kHessThreads + tid;
+    int blk = blockIdx.x, t0, t1;
+    if (A.list) {
+        blk = A.border[blockIdx.x];
+        const int2 r = A.blist[blk];
+        const int per = (r.y + (int)gridDim.y - 1) / (int)gridDim.y;
+        t0 = min(r.x + (int)blockIdx.y * per, r.x + r.y);
+        t1 = min(r.x + r.y, t0 + per);
+    } else {
+        t0 = blockIdx.y * A.tiles_per_split;
+        t1 = min(A.ntiles, t0 + A.tiles_per_split);
+    }
+    const int i = blk * kHessThreads + tid;
     const bool valid = i < A.nt;
-    const int t0 = blockIdx.y * A.tiles_per_split;
-    const int t1 = min(A.ntiles, t0 + A.tiles_per_split);
 
+    for (int k = tid; k < kH64N * 8; k += kHessThreads) s_tab[k] = g_htab64[k];
     double x[3] = {0.0, 0.0, 0.0};
     float xh[3], xl[3];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -142,12 +159,14 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
         nh[c] = 0.0;
     }
     unsigned long long pn = 0, pf = 0;
-    for (int t = t0; t < t1; t++) {
+    for (int jt = t0; jt < t1; jt++) {
+        const int t = A.list ? A.list[jt] : jt;
+        const bool proxy = t >= A.ntiles;
         const float4 tl = A.tlo[t], th = A.thi[t];
         const float gx = fmaxf(0.0f, fmaxf(tl.x - bb[3], bb[0] - th.x));
         const float gy = fmaxf(0.0f, fmaxf(tl.y - bb[4], bb[1] - th.y));
         const float gz = fmaxf(0.0f, fmaxf(tl.z - bb[5], bb[2] - th.z));
-        const bool far = gx * gx + gy * gy + gz * gz > A.cut2 * tl.w * tl.w * 1.0001f;
+        const bool far = proxy || gx * gx + gy * gy + gz * gz > A.cut2 * tl.w * tl.w * 1.0001f;
         const int cnt = (int)th.w;
         if (valid) {
             if (far)
@@ -155,9 +174,12 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
             else
                 pn += cnt;
         }
-        const int64_t j = (int64_t)t * kTile + tid;
+        const int64_t j = (int64_t)(proxy ? t - A.ntiles : t) * kTile + tid;
         if (tid < cnt) {
-            if (far) {
+            if (proxy) {
+                sp[tid] = A.ppos[j];
+                sn[tid] = A.pnw[j];
+            } else if (far) {
                 sp[tid] = A.s32_pos[j];
                 sn[tid] = A.s32_nw[j];
             } else {
@@ -199,7 +221,7 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
                 const double r0 = y.x - x[0], r1 = y.y - x[1], r2c = y.z - x[2];
                 const double r2 = fma(r0, r0, fma(r1, r1, r2c * r2c));
                 double fH, F, G;
-                radial3(r2, y.w, fH, F, G);
+                radial3(r2, y.w, s_tab, fH, F, G);
                 const double q = fma(n.x, r0, fma(n.y, r1, n.z * r2c));
                 const double qG = q * G;
                 p[0] += F * (2.0 * n.x * r0 + q) + qG * r0 * r0;
@@ -243,24 +265,13 @@ bool g_hess_consts[64] = {false};
 int hess_constants(Ctx* ctx)
 {
     if (ctx->device >= 0 && ctx->device < 64 && g_hess_consts[ctx->device]) return LSM_OK;
-    // c_k = (-1)^{k+1} 2k / (k! (2k+1)); h = (2/sqrt pi) sum_{k>=1} c_k w^{k-1},
-    // k = 2 dh/dw, kp = 2 dk/dw
-    long double c[kHSer + 4];
-    long double fact = 1.0L;
-    for (int k = 1; k < kHSer + 4; k++) {
-        fact *= k;
-        c[k] = ((k & 1) ? 1.0L : -1.0L) * (2.0L * k) / (fact * (2.0L * k + 1.0L));
+    std::vector<double> tab((size_t)kH64N * 8, 0.0);
+    for (int k = 0; k < kH64N; k++) {
+        long double cf[7];
+        h_interval_fit(k, kH64PerUnit, cf);
+        for (int j = 0; j < 7; j++) tab[8 * (size_t)k + j] = (double)cf[j];
     }
-    const long double tsp = 2.0L / sqrtl(3.14159265358979323846264338327950288L);
-    double hh[kHSer], hk[kHSer], hkp[kHSer];
-    for (int m = 0; m < kHSer; m++) {
-        hh[m] = (double)(tsp * c[m + 1]);
-        hk[m] = (double)(tsp * c[m + 2] * (2.0L * (m + 2) - 2.0L));
-        hkp[m] = (double)(tsp * c[m + 3] * (2.0L * (m + 3) - 2.0L) * (2.0L * (m + 3) - 4.0L));
-    }
-    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_hh, hh, sizeof(hh)));
-    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_hk, hk, sizeof(hk)));
-    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_hkp, hkp, sizeof(hkp)));
+    LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(g_htab64, tab.data(), sizeof(double) * tab.size()));
     if (ctx->device >= 0 && ctx->device < 64) g_hess_consts[ctx->device] = true;
     return LSM_OK;
 }
@@ -280,6 +291,21 @@ int hess_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, cudaStr
     const int tps = (ntiles + nsplit - 1) / nsplit;
     nsplit = (ntiles + tps - 1) / tps;
     Scratch s(st);
+    // a large mesh: the mixed path's treecode, walked for this kernel's radius
+    int *list = nullptr, *border = nullptr;
+    int2* blist = nullptr;
+    const bool use_tree = tree_wanted(ctx, me, false);
+    if (use_tree) {
+        rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, false);
+        if (rc != LSM_OK) return rc;
+        int64_t total = 0;
+        rc = tree_lists(ctx, me->tree, t, kHessThreads, nullptr, s, &list, &blist, &border, &total, st,
+                        ctx->opt.cutoff_fp64);
+        if (rc != LSM_OK) return rc;
+        nsplit = 1;
+        const int64_t avg = total / nblk;
+        if (nblk < want) nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((want + nblk - 1) / nblk, avg / 4));
+    }
     double* part = res;
     if (nsplit > 1) LSM_CUDA_TRY(ctx, s.get(&part, (size_t)nsplit * 6 * t.n));
     HessArgs A;
@@ -299,6 +325,22 @@ int hess_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, cudaStr
     A.cut2 = (float)(ctx->opt.cutoff_fp64 * ctx->opt.cutoff_fp64);
     A.out = part;
     A.pairs = ctx->d_pairs + 6;
+    A.list = nullptr;
+    A.blist = nullptr;
+    A.border = nullptr;
+    A.ppos = A.pnw = nullptr;
+    if (use_tree) {
+        const Tree* T = me->tree;
+        A.tlo = T->tile_lo;
+        A.thi = T->tile_hi;
+        A.tchi = T->tile_chi;
+        A.tclo = T->tile_clo;
+        A.list = list;
+        A.blist = blist;
+        A.border = border;
+        A.ppos = T->p_pos;
+        A.pnw = T->p_nw;
+    }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (ctx->profiling) {
         LSM_CUDA_TRY(ctx, cudaEventCreate(&ev0));

@@ -271,8 +271,10 @@ void tree_free(Tree* t);
 // blocks by decreasing list length (the launch order); *total = the summed
 // list length.
 // tsig: the targets' sigma in sigma(x) mode (the near width), else NULL.
+// cut_override > 0: the near radius (in sigma) of the kernel that evaluates
+// the lists, when it is not the tree's own path's.
 int tree_lists(Ctx* ctx, const Tree* tree, const Targets& t, int tpb, const double* tsig, Scratch& s, int** list,
-               int2** blist, int** order, int64_t* total, cudaStream_t st);
+               int2** blist, int** order, int64_t* total, cudaStream_t st, double cut_override = 0.0);
 
 // frames.cu: chart local coordinates and the Gauss flux (lsm_chart_frames,
 // lsm_gauss_flux); all arrays on the device, nodes in solve order
@@ -281,6 +283,12 @@ int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const 
                      double* jac, cudaStream_t st, const NodeSpec* spec = nullptr);
 int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const double* g, const double* jac,
                    const double* x0, double* eps0, cudaStream_t st, const NodeSpec* spec = nullptr);
+
+// eval.cu: H(w) = g(u)/u^3 in long double, and the degree-6 interpolant of H
+// on interval k of width 1/per_unit in w (monomial coefficients about its
+// centre)
+long double h_of_w(long double w);
+void h_interval_fit(int k, int per_unit, long double* cf);
 
 // hess.cu: the Hessian of Phi [6][n] (xx, xy, xz, yy, yz, zz) at sorted
 // targets (per-triangle sigma meshes)

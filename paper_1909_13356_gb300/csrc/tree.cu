@@ -765,7 +765,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
 }
 
 int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double* tsig, Scratch& s, int** list,
-               int2** blist, int** order, int64_t* total_out, cudaStream_t st)
+               int2** blist, int** order, int64_t* total_out, cudaStream_t st, double cut_override)
 {
     const int nblk = (t.n + tpb - 1) / tpb;
     float4 *blo = nullptr, *bhi = nullptr;
@@ -789,7 +789,7 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double*
     W.sigx = tsig != nullptr;
     W.theta2 = T->theta * T->theta;
     // the near radius of the pair kernel that evaluates the lists
-    const double cut = T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed;
+    const double cut = cut_override > 0 ? cut_override : (T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed);
     W.cut2 = (float)(cut * cut);
     W.off = cnt;
     W.cnt = cnt;

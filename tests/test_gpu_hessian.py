@@ -96,3 +96,27 @@ def test_hessian_rejects_sigma_x_mesh(lsm):
     mesh = ctx.upload_sigma_x(m.verts, m.tris, n_gl=3)
     with pytest.raises(lsm.LsmError):
         mesh.eval_hessian(np.zeros((3, 3)))
+
+
+def test_hessian_with_treecode(lsm, oracle_mod):
+    """A mesh above the treecode threshold (graded torus 120 x 32, 276,480
+    nodes): the Hessian over the treecode's lists (far pairs through the
+    proxies) against the direct sum on the GPU and the oracle on a sample of
+    50,000 dense targets; fewer far pairs."""
+    m = synth.torus(1.0, 0.3, 120, 32, 20.0, 0.05, 73)
+    x = synth.targets_near_surface(m, 50_000, synth.rng(74), 3.0)
+    out = {}
+    for name, kw in (("tree", {}), ("direct", {"tree_min_sources": -1})):
+        ctx = lsm.Context(0, **kw)
+        mesh = ctx.upload(m.verts, m.tris, None, n_gl=6)
+        ctx.read_stats(reset=True)
+        out[name] = (mesh.eval_hessian(x), ctx.read_stats(reset=True))
+    (Ht, st_t), (Hd, st_d) = out["tree"], out["direct"]
+    scale = np.abs(Hd).max()
+    assert np.abs(Ht - Hd).max() <= 1e-7 * scale
+    assert st_t["kind_pairs_near"][3] == st_d["kind_pairs_near"][3]
+    assert st_t["kind_pairs_far"][3] < 0.5 * st_d["kind_pairs_far"][3]
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, None, 6, 0)
+    sel = np.random.default_rng(75).choice(len(x), 100, replace=False)
+    _, _, Ho = oracle_mod.phi_grad_hess(y, nw, sg, x[sel])
+    assert np.abs(Ht[sel] - Ho).max() <= 1e-7 * scale
