@@ -66,6 +66,8 @@ def parse():
                     help="target-dependent sigma(x) (eq. sigma2, lambda 2.5) instead of per-triangle sigma")
     ap.add_argument("--no-charts", action="store_true", help="time the evaluation only")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-geometry", action="store_true",
+                    help="skip the untimed Gauss flux and Gauss-Bonnet checks after the step (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -641,7 +643,7 @@ def main():
     # (untimed): grad Phi at the nodes from the float-float path, then the
     # frames and the flux (Sec. 5)
     eps0 = None
-    if "x" in last:
+    if "x" in last and not args.no_geometry:
         _, gc = mesh.eval_phi_grad(last["x"], lsm.FF)
         _, _, jac = mesh.chart_frames(args.order, last["h"], gc)
         eps0 = {"x0": [1.0, 0.0, 0.0], "value": mesh.gauss_flux(args.order, last["x"], gc, jac, (1.0, 0.0, 0.0)),

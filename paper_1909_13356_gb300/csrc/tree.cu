@@ -275,9 +275,11 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(P2MArgs A)
 // Chebyshev points of the second kind in FP64 (the float-float proxies).
 __device__ __forceinline__ double cheb_point64(int k, int degree) { return cospi((double)k / (double)degree); }
 
-// FP64 P2M for the float-float proxies: thread k of grid row y owns proxy
-// 256 y + k of the item's node; its weight is summed in FP64 over the item's
-// tiles, 64 sources at a time (their basis values staged in shared memory).
+// FP64 P2M for the float-float proxies: thread k of grid row y owns the grid
+// pair (k0, k1) = 256 y + k of the item's node and all its k2 points, so the
+// tensor factor L0 L1 nw is formed once per source and each proxy costs three
+// FP64 FMAs per source.  Summed over the item's tiles, 64 sources at a time
+// (their basis values staged in shared memory).
 __global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
 {
     __shared__ double sL[3][kP2M64Src][kMaxN64];
@@ -288,15 +290,16 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
     const int4 info = A.ninfo[node];
     const NodeGrid G = node_grid(lo, hi, A.degree);
     const int n1 = G.n[1], n2 = G.n[2];
-    const int nprox = G.n[0] * n1 * n2;
-    if ((int)blockIdx.y * kP2MThreads >= nprox) return;   // whole CTA, before any barrier
+    const int npair = G.n[0] * n1;
+    if ((int)blockIdx.y * kP2MThreads >= npair) return;   // whole CTA, before any barrier
     const int tid = threadIdx.x;
-    const int k = blockIdx.y * kP2MThreads + tid;
-    const bool active = k < nprox;
-    const int k0 = active ? k / (n1 * n2) : 0;
-    const int k1 = active ? (k / n2) % n1 : 0;
-    const int k2 = active ? k % n2 : 0;
-    double q[3] = {0.0, 0.0, 0.0};
+    const int pr = blockIdx.y * kP2MThreads + tid;
+    const bool active = pr < npair;
+    const int k0 = active ? pr / n1 : 0;
+    const int k1 = active ? pr % n1 : 0;
+    double q[kMaxN64][3];
+#pragma unroll
+    for (int m = 0; m < kMaxN64; m++) q[m][0] = q[m][1] = q[m][2] = 0.0;
     for (int t = it.y; t < it.z; t++) {
         for (int half = 0; half < kTile / kP2M64Src; half++) {
             if (tid < kP2M64Src) {
@@ -342,41 +345,52 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
             }
             __syncthreads();
             if (active) {
-#pragma unroll 4
                 for (int s = 0; s < kP2M64Src; s++) {
-                    const double l = sL[0][s][k0] * sL[1][s][k1] * sL[2][s][k2];
-                    q[0] = fma(l, sN[s][0], q[0]);
-                    q[1] = fma(l, sN[s][1], q[1]);
-                    q[2] = fma(l, sN[s][2], q[2]);
+                    const double l01 = sL[0][s][k0] * sL[1][s][k1];
+                    const double wx = l01 * sN[s][0], wy = l01 * sN[s][1], wz = l01 * sN[s][2];
+#pragma unroll
+                    for (int m = 0; m < kMaxN64; m++) {
+                        if (m < n2) {
+                            const double l2 = sL[2][s][m];
+                            q[m][0] = fma(l2, wx, q[m][0]);
+                            q[m][1] = fma(l2, wy, q[m][1]);
+                            q[m][2] = fma(l2, wz, q[m][2]);
+                        }
+                    }
                 }
             }
             __syncthreads();
         }
     }
     if (!active) return;
-    const int64_t dst = (int64_t)info.z * kTile + k;
-    if (it.w < 0) {
-        const float h0 = (float)q[0], h1 = (float)q[1], h2 = (float)q[2];
-        A.p_nw[dst] = make_float4(h0, h1, h2, 0.0f);
-        A.p_nwlo[dst] = make_float4((float)(q[0] - (double)h0), (float)(q[1] - (double)h1),
-                                    (float)(q[2] - (double)h2), 0.0f);
-    } else {
-        double* o = A.partial + ((int64_t)it.w + k) * 3;
-        o[0] = q[0];
-        o[1] = q[1];
-        o[2] = q[2];
-    }
-    if (it.y == info.x) {
-        const double r[3] = {G.n[0] > 1 ? G.h[0] * cheb_point64(k0, G.n[0] - 1) : 0.0,
-                             n1 > 1 ? G.h[1] * cheb_point64(k1, n1 - 1) : 0.0,
-                             n2 > 1 ? G.h[2] * cheb_point64(k2, n2 - 1) : 0.0};
-        float rh[3], rl[3];
-        for (int a = 0; a < 3; a++) {
-            rh[a] = (float)r[a];
-            rl[a] = (float)(r[a] - (double)rh[a]);
+#pragma unroll
+    for (int k2 = 0; k2 < kMaxN64; k2++) {
+        if (k2 >= n2) break;
+        const int k = pr * n2 + k2;   // (k0 n1 + k1) n2 + k2
+        const int64_t dst = (int64_t)info.z * kTile + k;
+        if (it.w < 0) {
+            const float h0 = (float)q[k2][0], h1 = (float)q[k2][1], h2 = (float)q[k2][2];
+            A.p_nw[dst] = make_float4(h0, h1, h2, 0.0f);
+            A.p_nwlo[dst] = make_float4((float)(q[k2][0] - (double)h0), (float)(q[k2][1] - (double)h1),
+                                        (float)(q[k2][2] - (double)h2), 0.0f);
+        } else {
+            double* o = A.partial + ((int64_t)it.w + k) * 3;
+            o[0] = q[k2][0];
+            o[1] = q[k2][1];
+            o[2] = q[k2][2];
         }
-        A.p_pos[dst] = make_float4(rh[0], rh[1], rh[2], 0.0f);
-        A.p_lo[dst] = make_float4(rl[0], rl[1], rl[2], 0.0f);
+        if (it.y == info.x) {
+            const double r[3] = {G.n[0] > 1 ? G.h[0] * cheb_point64(k0, G.n[0] - 1) : 0.0,
+                                 n1 > 1 ? G.h[1] * cheb_point64(k1, n1 - 1) : 0.0,
+                                 n2 > 1 ? G.h[2] * cheb_point64(k2, n2 - 1) : 0.0};
+            float rh[3], rl[3];
+            for (int a = 0; a < 3; a++) {
+                rh[a] = (float)r[a];
+                rl[a] = (float)(r[a] - (double)rh[a]);
+            }
+            A.p_pos[dst] = make_float4(rh[0], rh[1], rh[2], 0.0f);
+            A.p_lo[dst] = make_float4(rl[0], rl[1], rl[2], 0.0f);
+        }
     }
 }
 
@@ -733,10 +747,10 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         P.p_nwlo = T->p_nwlo;
         P.partial = d_part;
         if (ff) {
-            int64_t nmax = 0;
+            int64_t nmax = 0;   // grid pairs (k0, k1) per node at most
             for (const int4& it : items) {
                 const NodeGrid G = node_grid(hlo[it.x], hhi[it.x], degree);
-                nmax = std::max<int64_t>(nmax, (int64_t)G.n[0] * G.n[1] * G.n[2]);
+                nmax = std::max<int64_t>(nmax, (int64_t)G.n[0] * G.n[1]);
             }
             const dim3 grid((unsigned)items.size(), (unsigned)((nmax + kP2MThreads - 1) / kP2MThreads));
             k_p2m64<<<grid, kP2MThreads, 0, st>>>(P);
