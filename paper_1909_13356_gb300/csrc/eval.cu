@@ -307,6 +307,7 @@ struct EvalArgs {
     int ff_mode;
     double* far_io;
     const double* x_old;
+    float* bb_io = nullptr;   // [block][8]: block box recorded in mode 1, reused in mode 2
     unsigned long long* pairs;  // [2] pairs evaluated in near / far tiles
     // mixed kernel only: interaction lists of the treecode.  Block b walks the
     // tile ids list[blist[b].x .. + blist[b].y); ids >= ntiles are proxy
@@ -1061,6 +1062,23 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         }
         block_max1(smax, &s_smax);
     }
+    // incremental modes: the record call stores the block's box, the
+    // near-only call reuses it (the same near/far split in both)
+    if (A.bb_io && mode != 0) {
+        // the block's own slot: list mode launches blocks in another order
+        const int64_t bslot = A.list ? (int64_t)(base / kEvalThreads) : (int64_t)blockIdx.x;
+        float* io = A.bb_io + 8 * bslot;
+        if (tid == 0) {
+            if (mode == 1) {
+                for (int c = 0; c < 6; c++) io[c] = s_bb[c];
+                io[6] = SIGX ? s_smax : 0.0f;
+            } else {
+                for (int c = 0; c < 6; c++) s_bb[c] = io[c];
+                if (SIGX) s_smax = io[6];
+            }
+        }
+        __syncthreads();
+    }
 
     // incremental mode: the block's near tiles, in tile order
     int nlist = t1 - t0;
@@ -1458,6 +1476,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         A.ff_mode = inc->mode;
         A.far_io = inc->far_io;
         A.x_old = inc->x_old;
+        A.bb_io = inc->bb_io;
     }
     if (use_tree) {
         const Tree* T = ff ? me->tree_ff : me->tree;
@@ -1513,7 +1532,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
 int eval_item_targets(int precision) { return kEvalThreads * (precision == LSM_MIXED ? kTPT32 : kTPT64); }
 
 int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* items, const int* n_items,
-               int max_items, double* res, int precision, cudaStream_t st)
+               int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc)
 {
     if (max_items <= 0) return LSM_OK;
     EvalArgs A;
@@ -1538,6 +1557,12 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
     A.ff_mode = 0;
     A.far_io = nullptr;
     A.x_old = nullptr;
+    if (precision == LSM_FF && inc) {
+        A.ff_mode = inc->mode;
+        A.far_io = inc->far_io;
+        A.x_old = inc->x_old;
+        A.bb_io = inc->bb_io;
+    }
     if (mixed) {
         k_eval_mixed<kTPT32, false><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo,
                                                                         A);

@@ -143,13 +143,14 @@ struct Batch {
 // ---------------------------------------------------------------- scratch
 // Stream-ordered scratch allocation for one call.
 struct Scratch {
+    static constexpr int kMax = 64;
     cudaStream_t st;
-    void* ptrs[32];
+    void* ptrs[kMax];
     int n = 0;
     explicit Scratch(cudaStream_t s) : st(s) {}
     template <class T>
     cudaError_t get(T** p, size_t count) {
-        if (n >= 32) return cudaErrorMemoryAllocation;
+        if (n >= kMax) return cudaErrorMemoryAllocation;
         void* q = nullptr;
         cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 16, st);
         if (e != cudaSuccess) return e;
@@ -226,10 +227,14 @@ int eval_init_constants(Ctx* ctx);
 // far-tile part of Phi and grad Phi into far_io [4][n]; mode 2 then
 // evaluates only the near tiles and adds the recorded far part moved to the
 // new positions along its gradient (x_old = the targets of the mode 1 call).
+// bb_io [grid blocks][8]: mode 1 stores each block's box (and its largest
+// sigma in sigma(x) mode), mode 2 reuses it, so both calls split near and far
+// tiles identically however little the targets moved.
 struct FFIncremental {
     int mode;
     double* far_io;
     const double* x_old;
+    float* bb_io = nullptr;
 };
 int eval_sorted(Ctx* ctx, const Mesh* mesh, const Targets& t, double* res, int precision,
                 cudaStream_t st, const FFIncremental* inc = nullptr);
@@ -238,7 +243,7 @@ int eval_sorted(Ctx* ctx, const Mesh* mesh, const Targets& t, double* res, int p
 // items is read on the device from *n_items, the grid covers max_items.
 int eval_item_targets(int precision);
 int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* items, const int* n_items,
-               int max_items, double* res, int precision, cudaStream_t st);
+               int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc = nullptr);
 int eval_noalloc(Ctx* ctx, const Mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
                  int precision, cudaStream_t st);
 

@@ -321,11 +321,13 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
     // them are ~1e-8 sigma, where the far part is linear to ~1e-14
     int32_t* Lrec = nullptr;
     double *Trec = nullptr, *Rfar = nullptr;
+    float* BBrec = nullptr;   // block boxes of the record sweep (kEvalThreads targets per block)
     int nrec = 0, ff_stage = 0;
     if (mixed) {
         LSM_CUDA_TRY(ctx, s.get(&Lrec, (size_t)N));
         LSM_CUDA_TRY(ctx, s.get(&Trec, 3 * (size_t)N));
         LSM_CUDA_TRY(ctx, s.get(&Rfar, 4 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&BBrec, 8 * ((size_t)N / kEvalThreads + 2)));
     }
     int iter = 0;
     for (; iter < max_iter && nact > 0; iter++) {
@@ -342,7 +344,7 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
                 k_gather_targets<<<nb(nl), 256, 0, st>>>(L, nl, S, T);
                 LSM_LAUNCHED(ctx);
                 Targets tg{T, nl, nl};
-                FFIncremental inc{2, Rfar, Trec};
+                FFIncremental inc{2, Rfar, Trec, BBrec};
                 rc = eval_sorted(ctx, me, tg, R, LSM_FF, st, &inc);
                 if (rc) return rc;
                 k_newton_update<<<nb(nl), 256, 0, st>>>(L, nl, R, S, 0, accept_mixed, tol, ctx->opt.mixed_switch,
@@ -367,7 +369,7 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
             Targets tg{T, nl, nl};
             if (mixed && m == 1) {
                 // recording float-float sweep
-                FFIncremental inc{1, Rfar, nullptr};
+                FFIncremental inc{1, Rfar, nullptr, BBrec};
                 rc = eval_sorted(ctx, me, tg, R, LSM_FF, st, &inc);
                 if (rc) return rc;
                 LSM_CUDA_TRY(ctx, cudaMemcpyAsync(Lrec, L, sizeof(int32_t) * nl, cudaMemcpyDeviceToDevice, st));
@@ -457,8 +459,28 @@ __global__ void k_gather_mesh(const int32_t* __restrict__ tri_mesh, int np, int 
     if (k < n) mesh_of_sorted[k] = tri_mesh[perm[k] / np];
 }
 
+// Float-float sweeps of a mixed batch solve come in pairs, as in the
+// single-mesh solve: the first (stage 1) evaluates its node list fully and
+// records each node's far-tile part; the second (stage 2) re-evaluates the
+// same list (same items, so the same near/far split) over near tiles only and
+// adds the recorded far part moved along its gradient.
+__global__ void k_copy_record(const int32_t* __restrict__ L, const int* __restrict__ nL, int32_t* __restrict__ Lrec,
+                              int* __restrict__ n_rec, const double* __restrict__ T, double* __restrict__ Trec, int N)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = *nL;
+    if (k == 0) *n_rec = n;
+    if (k >= n) return;
+    Lrec[k] = L[k];
+    for (int c = 0; c < 3; c++) Trec[(int64_t)c * N + k] = T[(int64_t)c * N + k];
+}
+
 struct BatchSweep {
     int N, nmesh, max_items_mixed, max_items_other;
+    int32_t* Lrec;     // float-float record: node list, its length, targets, far part, block boxes
+    int* n_rec;
+    double *Trec, *Rfar;
+    float* BBrec;
     int32_t *flags, *lst, *node_mesh;
     int *n_lst, *n_items, *sweep_counter, *hist;
     double *T, *R;
@@ -473,14 +495,18 @@ struct BatchSweep {
 };
 
 int batch_sweep(Ctx* ctx, const BatchSweep& B, const int32_t* act, const int* n_act, int32_t* act_out,
-                int* n_act_out, cudaStream_t st)
+                int* n_act_out, cudaStream_t st, int ff_stage)
 {
     int rc;
     for (int m = B.mixed ? 0 : 1; m <= 1; m++) {
         const int prec = m == 0 ? LSM_MIXED : (B.mixed ? LSM_FF : LSM_FP64);
         const int32_t* L = act;
         const int* nL = n_act;
-        if (B.mixed) {
+        const bool verify = B.mixed && m == 1 && ff_stage == 2;
+        if (verify) {
+            L = B.Lrec;
+            nL = B.n_rec;
+        } else if (B.mixed) {
             k_list_mode_flags<<<nb(B.N), 256, 0, st>>>(act, n_act, B.S.mode, B.flags);
             LSM_LAUNCHED(ctx);
             rc = compact_flags_dev(ctx, B.flags, m, act, n_act, B.N, B.lst, B.n_lst, B.bc, st);
@@ -495,9 +521,15 @@ int batch_sweep(Ctx* ctx, const BatchSweep& B, const int32_t* act, const int* n_
                          st);
         if (rc) return rc;
         Targets tg{B.T, B.N, B.N};
+        FFIncremental inc{verify ? 2 : 1, B.Rfar, verify ? B.Trec : nullptr, B.BBrec};
+        const bool ffpair = B.mixed && m == 1;
         rc = eval_items(ctx, B.view, tg, B.items, B.n_items, prec == LSM_MIXED ? B.max_items_mixed : B.max_items_other,
-                        B.R, prec, st);
+                        B.R, prec, st, ffpair ? &inc : nullptr);
         if (rc) return rc;
+        if (ffpair && !verify) {
+            k_copy_record<<<nb(B.N), 256, 0, st>>>(L, nL, B.Lrec, B.n_rec, B.T, B.Trec, B.N);
+            LSM_LAUNCHED(ctx);
+        }
         k_newton_update_dev<<<nb(B.N), 256, 0, st>>>(L, nL, B.R, B.N, B.S, m == 0 ? 1 : 0, B.accept_mixed, B.tol, B.sw,
                                                      B.max_iter);
         LSM_LAUNCHED(ctx);
@@ -622,6 +654,11 @@ int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, i
         B.n_items = cnts + 3;
         B.sweep_counter = cnts + 4;
         B.hist = cnts + 5;
+        B.n_rec = cnts + 37;
+        LSM_CUDA_TRY(ctx, s.get(&B.Lrec, (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&B.Trec, 3 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&B.Rfar, 4 * (size_t)N));
+        LSM_CUDA_TRY(ctx, s.get(&B.BBrec, 8 * (size_t)B.max_items_other));
         // identity active list
         LSM_CUDA_TRY(ctx, cudaMemsetAsync(B.flags, 0, sizeof(int32_t) * N, st));
         rc = compact_flags(ctx, B.flags, 0, nullptr, N, actA, n_actA, st);
@@ -640,8 +677,9 @@ int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, i
             cudaGraphExec_t exec = nullptr;
             const int64_t l0 = ctx->launches;
             LSM_CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc1 = batch_sweep(ctx, B, actA, n_actA, actB, n_actB, st);
-            int rc2 = rc1 ? rc1 : batch_sweep(ctx, B, actB, n_actB, actA, n_actA, st);
+            // sweep 1 records the float-float far parts, sweep 2 verifies
+            int rc1 = batch_sweep(ctx, B, actA, n_actA, actB, n_actB, st, 1);
+            int rc2 = rc1 ? rc1 : batch_sweep(ctx, B, actB, n_actB, actA, n_actA, st, 2);
             cudaError_t ce = cudaStreamEndCapture(st, &graph);
             if (rc2 || ce != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
@@ -672,7 +710,7 @@ int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, i
             int32_t *a = actA, *c = actB;
             int *na = n_actA, *nc = n_actB;
             while (sweeps < max_iter) {
-                rc = batch_sweep(ctx, B, a, na, c, nc, st);
+                rc = batch_sweep(ctx, B, a, na, c, nc, st, (sweeps & 1) ? 2 : 1);
                 if (rc) return rc;
                 sweeps++;
                 LSM_CUDA_TRY(ctx, cudaMemcpyAsync(hcount, nc, sizeof(int), cudaMemcpyDeviceToHost, st));
