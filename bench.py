@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--tmax", type=float, default=1e4)
     ap.add_argument("--tree-degree", type=int, default=0, help="treecode degree (0: library default)")
     ap.add_argument("--tree-theta", type=float, default=0.0, help="treecode opening parameter (0: default)")
+    ap.add_argument("--tree-grid", type=int, default=0,
+                    help="proxy grids: 1 per-axis point counts (default), 2 full (degree + 1)^3")
     ap.add_argument("--sigma-x", action="store_true",
                     help="target-dependent sigma(x) (eq. sigma2, lambda 2.5) instead of per-triangle sigma")
     ap.add_argument("--no-charts", action="store_true", help="time the evaluation only")
@@ -239,7 +241,7 @@ def bench_ellipsoids(args):
     import paper_1909_13356_gb300 as lsm
     import synth
     w = synth.ellipsoid_batch_c4()
-    ctx = lsm.Context(0)
+    ctx = lsm.Context(0, tree_grid=args.tree_grid)
     meshes = [ctx.upload(m.verts, m.tris, m.sigma, n_gl=4) for m in w["meshes"]]
     batch = lsm.Batch(ctx, meshes)
     tol = 1e-10
@@ -283,7 +285,7 @@ def bench_serve(args):
     from synth.workloads import make_request_mesh
     reqs = synth.serve_stream_c5(nreq=args.requests, rate=args.rate, tmax=args.tmax)
     meshes = [make_request_mesh(r) for r in reqs]
-    ctx = lsm.Context(0)
+    ctx = lsm.Context(0, tree_grid=args.tree_grid)
     # warm the kernels once
     m0 = meshes[0]
     wm = ctx.upload(m0.verts, m0.tris, m0.sigma, n_gl=4)
@@ -332,7 +334,7 @@ def bench_icosphere(args):
     n = args.targets if args.targets else 20_000_000
     w = synth.icosphere_c3(n_targets=n)
     m = w["mesh"]
-    ctx = lsm.Context(0, tree_degree=args.tree_degree, tree_theta=args.tree_theta)
+    ctx = lsm.Context(0, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid)
     t0 = time.perf_counter()
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
     torch.cuda.synchronize()
@@ -412,7 +414,7 @@ def bench_geometry(args):
     import paper_1909_13356_gb300 as lsm
     w = workload(args, 0)
     m = w["mesh"]
-    ctx = lsm.Context(0)
+    ctx = lsm.Context(0, tree_grid=args.tree_grid)
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
     x, h, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=lsm.MIXED, device_out=True)
     _, g = mesh.eval_phi_grad(x, lsm.FF)
@@ -530,7 +532,7 @@ def main():
 
     w = workload(args, rank)
     m = w["mesh"]
-    ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta)
+    ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid)
     if args.sigma_x:
         mesh = ctx.upload_sigma_x(m.verts, m.tris, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
     else:

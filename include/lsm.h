@@ -93,7 +93,9 @@ typedef struct {
     double cutoff_mixed;   /* same for the mixed path (6.5: neglected
                               relative term 4e-9 < FP32 rounding) */
     double mixed_switch;   /* mixed Newton: a node moves to FP64 steps once
-                              |Phi - 1/2| < mixed_switch (1e-6) */
+                              |Phi - 1/2| < mixed_switch (1e-4; the mixed step
+                              then lands near 1e-8, and one accurate step
+                              below 1e-12) */
     double mixed_accept;   /* mixed Newton: a tolerance >= mixed_accept
                               (1e-7, the mixed kernels' accuracy on Phi) is
                               met on mixed evaluations alone, with no FP64
@@ -102,18 +104,23 @@ typedef struct {
      * treecode.  Source tiles are grouped by Morton order into a binary tree;
      * a node of radius r whose box lies beyond the mixed cutoff from a target
      * block, at distance >= r / tree_theta from the node's centre, acts on the
-     * block through (tree_degree + 1)^3 Chebyshev proxy points carrying its
-     * interpolated dipole weights. */
+     * block through a tensor grid of Chebyshev proxy points carrying its
+     * interpolated dipole weights: tree_degree + 1 points on the box's widest
+     * axis, and on each narrower axis the fewest points whose interpolation
+     * error bound is 1/32 of the widest axis's (tree_grid). */
     int32_t tree_degree;      /* Chebyshev degree p per axis (8; 1..12) */
     float tree_theta;         /* opening parameter (0.4; (0, 1)) */
     int32_t tree_min_sources; /* meshes with at least this many source nodes
                                  use it (262,144); -1: never */
     /* The same for the float-float path (Phi to FP64 accuracy): proxies
      * with float-float positions and weights computed in FP64. */
-    int32_t tree_ff_degree;      /* 13; 1..16 */
+    int32_t tree_ff_degree;      /* 14; 1..16 */
     float tree_ff_theta;         /* 0.4 */
     int32_t tree_ff_min_sources; /* 262,144; -1: never */
-    int32_t reserved[2];
+    int32_t tree_grid;           /* proxy grids of both treecodes: 0 or 1 per-axis
+                                    point counts (default), 2 (degree + 1)^3 on
+                                    every node */
+    int32_t reserved;
 } lsm_options;
 
 /* Statistics of one chart solve. */

@@ -224,19 +224,20 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->device = device;
     ctx->opt.cutoff_fp64 = 8.0;
     ctx->opt.cutoff_mixed = 6.5;
-    ctx->opt.mixed_switch = 1e-6;
+    ctx->opt.mixed_switch = 1e-4;
     ctx->opt.mixed_accept = 1e-7;
     ctx->opt.tree_degree = 8;
     ctx->opt.tree_theta = 0.4f;
     ctx->opt.tree_min_sources = 262144;
-    ctx->opt.tree_ff_degree = 13;
+    ctx->opt.tree_ff_degree = 14;
     ctx->opt.tree_ff_theta = 0.4f;
     ctx->opt.tree_ff_min_sources = 262144;
+    ctx->opt.tree_grid = 1;
     if (opt) {
         if (opt->tree_degree < 0 || opt->tree_degree > 12 || opt->tree_theta < 0.0f ||
             opt->tree_theta >= 1.0f || opt->tree_min_sources < -1 || opt->tree_ff_degree < 0 ||
             opt->tree_ff_degree > kTreeMaxDegree || opt->tree_ff_theta < 0.0f || opt->tree_ff_theta >= 1.0f ||
-            opt->tree_ff_min_sources < -1) {
+            opt->tree_ff_min_sources < -1 || opt->tree_grid < 0 || opt->tree_grid > 2) {
             delete c;
             return LSM_E_INVALID_ARG;
         }
@@ -250,6 +251,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
         if (opt->tree_ff_degree > 0) ctx->opt.tree_ff_degree = opt->tree_ff_degree;
         if (opt->tree_ff_theta > 0.0f) ctx->opt.tree_ff_theta = opt->tree_ff_theta;
         if (opt->tree_ff_min_sources != 0) ctx->opt.tree_ff_min_sources = opt->tree_ff_min_sources;
+        if (opt->tree_grid > 0) ctx->opt.tree_grid = opt->tree_grid;
     }
     DeviceGuard g(device);
     int rc = LSM_OK;
@@ -282,6 +284,7 @@ int lsm_destroy(lsm_ctx* c)
     DeviceGuard g(c->c.device);
     cudaFree(c->c.d_flag);
     cudaFree(c->c.d_pairs);
+    for (int32_t* p : c->c.host_free) cudaFreeHost(p);
     for (auto& e : c->c.prof_events) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);

@@ -57,6 +57,35 @@ struct Ctx {
     std::vector<ProfEvent> prof_events;
     double prof_ms[4] = {0.0, 0.0, 0.0, 0.0};
     int64_t prof_launches[4] = {0, 0, 0, 0};
+    // pinned host blocks of kHostWords int32 for counts read back by the
+    // solves; several solves may run at once on one context (server slots),
+    // so each takes its own block and returns it (freed at lsm_destroy)
+    static constexpr int kHostWords = 64;
+    std::mutex host_mu;
+    std::vector<int32_t*> host_free;
+};
+
+// A pinned block from the context's pool, returned to it on scope exit.
+struct HostWords {
+    Ctx* ctx;
+    int32_t* p = nullptr;
+    explicit HostWords(Ctx* c) : ctx(c) {}
+    cudaError_t get() {
+        {
+            std::lock_guard<std::mutex> lk(ctx->host_mu);
+            if (!ctx->host_free.empty()) {
+                p = ctx->host_free.back();
+                ctx->host_free.pop_back();
+                return cudaSuccess;
+            }
+        }
+        return cudaMallocHost(&p, sizeof(int32_t) * Ctx::kHostWords);
+    }
+    ~HostWords() {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(ctx->host_mu);
+        ctx->host_free.push_back(p);
+    }
 };
 
 struct Tree;
@@ -256,6 +285,7 @@ struct Tree {
     bool ff = false;                        // float-float proxies (FP64 weights split in two floats)
     int degree = 0;
     float theta = 0.0f;
+    int grid = 1;                           // 1 per-axis point counts, 2 full (degree + 1)^3 grids
     int top = 0;                            // level of the root (level 0 = tiles)
     int64_t lev_off[33] = {0};              // first node of each level
     int64_t nnodes = 0;

@@ -301,12 +301,9 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
     LSM_CUDA_TRY(ctx, s.get(&dcount, 4));
     LSM_CUDA_TRY(ctx, s.get(&T, 3 * (size_t)N));
     LSM_CUDA_TRY(ctx, s.get(&R, 4 * (size_t)N));
-    int32_t* hcount = nullptr;
-    LSM_CUDA_TRY(ctx, cudaMallocHost(&hcount, sizeof(int32_t) * 4));
-    struct PinnedFree {
-        int32_t* p;
-        ~PinnedFree() { cudaFreeHost(p); }
-    } pf{hcount};
+    HostWords hw(ctx);
+    LSM_CUDA_TRY(ctx, hw.get());
+    int32_t* hcount = hw.p;
 
     // identity active list
     LSM_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, sizeof(int32_t) * N, st));
@@ -664,12 +661,9 @@ int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, i
         rc = compact_flags(ctx, B.flags, 0, nullptr, N, actA, n_actA, st);
         if (rc) return rc;
 
-        int32_t* hcount = nullptr;
-        LSM_CUDA_TRY(ctx, cudaMallocHost(&hcount, sizeof(int32_t) * 40));
-        struct PinnedFree {
-            int32_t* p;
-            ~PinnedFree() { cudaFreeHost(p); }
-        } pf{hcount};
+        HostWords hw(ctx);
+        LSM_CUDA_TRY(ctx, hw.get());
+        int32_t* hcount = hw.p;   // 40 words: the batch counters
 
         int sweeps = 0;
         if (use_graph) {

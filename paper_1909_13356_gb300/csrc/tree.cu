@@ -20,6 +20,18 @@
 // the tree) mixes source tiles and proxy tiles.  A node gets proxies only
 // when it holds at least twice as many sources as proxies.
 //
+// Points per axis.  Along axis a of half-width h_a the kernel, as a function
+// of y_a alone, has its singularities at distance >= d = (1/theta - 1) r from
+// the box (r its radius; the opening rule keeps |x - c| >= r / theta), so its
+// degree-p Chebyshev interpolant errs like rho(d / h_a)^-p, rho(q) = q +
+// sqrt(q^2 - 1), the Bernstein ellipse through the nearest singularity (a
+// real one in the worst case).  The widest axis keeps the degree; a narrower
+// axis gets the smallest degree whose bound is 1/32 of the widest axis's
+// (the tensor interpolant's error sums the axes' errors, each amplified by
+// the other axes' Lebesgue constants, about 2.7 each at these degrees).
+// Boxes of surface patches are thin across the surface, so most nodes need
+// few points on that axis.
+//
 // Steps: node boxes bottom-up (k_nodes_leaf, k_nodes_up); proxy assignment
 // on the host; P2M, the weights Q_k summed from the sources in chunks
 // (k_p2m, k_p2m_reduce); per evaluation, target block boxes
@@ -78,22 +90,55 @@ __global__ void k_nodes_up(const float4* __restrict__ clo, const float4* __restr
     info[i] = make_int4(f.x, f.y, -1, 0);
 }
 
-// Grid of one node: centre, half-widths and points per axis (one point on an
-// axis of zero extent).  Host and device compute it alike from the FP32 box.
+// Grid of one node: centre and half-widths from the FP32 box (host and
+// device compute them alike), and points per axis chosen on the host once
+// (grid_counts) and passed to the device.
 struct NodeGrid {
     double c[3], h[3];
     int n[3];
 };
-__host__ __device__ inline NodeGrid node_grid(float4 lo, float4 hi, int degree)
+__host__ __device__ inline NodeGrid node_grid(float4 lo, float4 hi, int4 counts)
 {
     NodeGrid g;
     const float l[3] = {lo.x, lo.y, lo.z}, u[3] = {hi.x, hi.y, hi.z};
+    const int n[3] = {counts.x, counts.y, counts.z};
     for (int a = 0; a < 3; a++) {
         g.c[a] = 0.5 * ((double)l[a] + (double)u[a]);
         g.h[a] = 0.5 * ((double)u[a] - (double)l[a]);
-        g.n[a] = g.h[a] > 0.0 ? degree + 1 : 1;
+        g.n[a] = n[a];
     }
     return g;
+}
+
+// Points per axis of a node's grid (host only): one on an axis of zero
+// extent; grid 2: degree + 1 on every other axis; grid 1: degree + 1 on the
+// widest axis and the bound above on the others.
+int4 grid_counts(float4 lo, float4 hi, int degree, float theta, int grid)
+{
+    const float l[3] = {lo.x, lo.y, lo.z}, u[3] = {hi.x, hi.y, hi.z};
+    double h[3], hmax = 0.0, r2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        h[a] = 0.5 * ((double)u[a] - (double)l[a]);
+        hmax = std::max(hmax, h[a]);
+        r2 += h[a] * h[a];
+    }
+    int n[3];
+    const double d = (1.0 / (double)theta - 1.0) * std::sqrt(r2);
+    auto log_rho = [](double q) { return std::log(q + std::sqrt(q * q - 1.0)); };
+    // the bound needs the widest axis's ellipse to exist (d > h_max)
+    const bool per_axis = grid != 2 && hmax > 0.0 && d > 1.05 * hmax;
+    const double target = per_axis ? degree * log_rho(d / hmax) + std::log(32.0) : 0.0;
+    for (int a = 0; a < 3; a++) {
+        if (!(h[a] > 0.0)) {
+            n[a] = 1;
+        } else if (!per_axis || h[a] == hmax) {
+            n[a] = degree + 1;
+        } else {
+            const int p = (int)std::ceil(target / log_rho(d / h[a]) - 1e-9);
+            n[a] = std::min(degree, std::max(1, p)) + 1;
+        }
+    }
+    return make_int4(n[0], n[1], n[2], 0);
 }
 
 // Chebyshev points of the second kind on [-1, 1], in FP32.
@@ -110,7 +155,7 @@ struct P2MArgs {
     const float4* nhi;
     const int4* ninfo;
     const int4* items;        // node, first tile, end tile, partial offset (in proxies) or -1
-    int degree;
+    const int4* ngrid;        // points per axis of each node's grid
     float4* p_pos;
     float4* p_nw;
     float4* p_lo;             // FP64 kernel: remainders of the positions
@@ -129,7 +174,7 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(P2MArgs A)
     const int node = it.x;
     const float4 lo = A.nlo[node], hi = A.nhi[node];
     const int4 info = A.ninfo[node];
-    const NodeGrid G = node_grid(lo, hi, A.degree);
+    const NodeGrid G = node_grid(lo, hi, A.ngrid[node]);
     const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
     const int pairs = n0 * n1;
     const int tid = threadIdx.x;
@@ -288,7 +333,7 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
     const int node = it.x;
     const float4 lo = A.nlo[node], hi = A.nhi[node];
     const int4 info = A.ninfo[node];
-    const NodeGrid G = node_grid(lo, hi, A.degree);
+    const NodeGrid G = node_grid(lo, hi, A.ngrid[node]);
     const int n1 = G.n[1], n2 = G.n[2];
     const int npair = G.n[0] * n1;
     if ((int)blockIdx.y * kP2MThreads >= npair) return;   // whole CTA, before any barrier
@@ -573,8 +618,9 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     const bool tuned = !ff && me->tune_mode == 1;
     const int degree = ff ? ctx->opt.tree_ff_degree : (tuned ? me->tune_degree : ctx->opt.tree_degree);
     const float theta = ff ? ctx->opt.tree_ff_theta : (tuned ? me->tune_theta : ctx->opt.tree_theta);
+    const int grid = ctx->opt.tree_grid;
     Tree*& slot = ff ? me->tree_ff : me->tree;
-    if (slot && slot->degree == degree && slot->theta == theta) return LSM_OK;
+    if (slot && slot->degree == degree && slot->theta == theta && slot->grid == grid) return LSM_OK;
     if (!ff && degree > kMaxDeg32) {
         ctx->err = "tree: the mixed path's degree is at most 12";
         return LSM_E_INVALID_ARG;
@@ -597,6 +643,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     };
     T->degree = degree;
     T->theta = theta;
+    T->grid = grid;
     T->ntiles = (int)me->ntiles;
     // levels: level l has ceil(ntiles / 2^l) nodes, up to a single root
     int64_t n = me->ntiles;
@@ -645,6 +692,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         return fail(LSM_E_CUDA);
     }
     std::vector<int4> items, reds;
+    std::vector<int4> hgrid(T->nnodes, make_int4(1, 1, 1, 0));
     std::vector<float4> ptlo, pthi, ptchi, ptclo;
     int64_t nptiles = 0, npartial = 0;
     for (int l = 1; l <= T->top; l++) {
@@ -652,9 +700,11 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
             int4& f = hinfo[node];
             const int64_t s0 = (int64_t)f.x * kTile;
             const int64_t s1 = std::min<int64_t>(me->ns, (int64_t)(f.x + f.y) * kTile);
-            const NodeGrid G = node_grid(hlo[node], hhi[node], degree);
+            const int4 gn = grid_counts(hlo[node], hhi[node], degree, theta, grid);
+            const NodeGrid G = node_grid(hlo[node], hhi[node], gn);
             const int64_t np = (int64_t)G.n[0] * G.n[1] * G.n[2];
             if (2 * np > s1 - s0) continue;
+            hgrid[node] = gn;
             const int npt = (int)((np + kTile - 1) / kTile);
             f.z = (int)nptiles;
             f.w = npt;
@@ -719,14 +769,15 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     }
     if (!items.empty()) {
         Scratch s(st);
-        int4 *d_items = nullptr, *d_reds = nullptr;
+        int4 *d_items = nullptr, *d_reds = nullptr, *d_grid = nullptr;
         double* d_part = nullptr;
         if (s.get(&d_items, items.size()) || s.get(&d_reds, std::max<size_t>(1, reds.size())) ||
-            s.get(&d_part, std::max<int64_t>(1, npartial) * 3)) {
+            s.get(&d_part, std::max<int64_t>(1, npartial) * 3) || s.get(&d_grid, (size_t)T->nnodes)) {
             ctx->err = "tree: out of device memory";
             return fail(LSM_E_OOM);
         }
         if (cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(d_grid, hgrid.data(), sizeof(int4) * hgrid.size(), cudaMemcpyHostToDevice, st) ||
             (!reds.empty() &&
              cudaMemcpyAsync(d_reds, reds.data(), sizeof(int4) * reds.size(), cudaMemcpyHostToDevice, st))) {
             ctx->err = "tree: copy failed";
@@ -740,7 +791,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         P.nhi = T->node_hi;
         P.ninfo = T->node_info;
         P.items = d_items;
-        P.degree = degree;
+        P.ngrid = d_grid;
         P.p_pos = T->p_pos;
         P.p_nw = T->p_nw;
         P.p_lo = T->p_lo;
@@ -748,10 +799,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         P.partial = d_part;
         if (ff) {
             int64_t nmax = 0;   // grid pairs (k0, k1) per node at most
-            for (const int4& it : items) {
-                const NodeGrid G = node_grid(hlo[it.x], hhi[it.x], degree);
-                nmax = std::max<int64_t>(nmax, (int64_t)G.n[0] * G.n[1]);
-            }
+            for (const int4& it : items) nmax = std::max<int64_t>(nmax, (int64_t)hgrid[it.x].x * hgrid[it.x].y);
             const dim3 grid((unsigned)items.size(), (unsigned)((nmax + kP2MThreads - 1) / kP2MThreads));
             k_p2m64<<<grid, kP2MThreads, 0, st>>>(P);
         } else {

@@ -85,3 +85,15 @@ def test_refined_nodes_match_the_oracle_rule(oracle_mod):
     assert np.allclose(uvw[:, 2], ow, rtol=1e-13, atol=0)
     with pytest.raises(lsm.LsmError):
         lsm.refined_nodes(8, np.array([5]))
+
+
+def test_out_of_range_options_are_rejected_before_any_device_call():
+    """lsm_create checks its options first: an out-of-range treecode option
+    returns LSM_E_INVALID_ARG (-1), with or without a GPU."""
+    L = lsm.load()
+    for field, value in (("tree_grid", 3), ("tree_grid", -1), ("tree_degree", 13), ("tree_theta", 1.0),
+                         ("tree_ff_degree", 17), ("tree_min_sources", -2)):
+        opt = lsm._Options()
+        setattr(opt, field, value)
+        h = ctypes.c_void_p()
+        assert L.lsm_create(ctypes.byref(h), 0, ctypes.byref(opt)) == -1, field
