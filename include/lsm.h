@@ -102,24 +102,31 @@ typedef struct {
                               steps */
     /* Far field of the mixed path on large meshes: a barycentric Lagrange
      * treecode.  Source tiles are grouped by Morton order into a binary tree;
-     * a node of radius r whose box lies beyond the mixed cutoff from a target
-     * block, at distance >= r / tree_theta from the node's centre, acts on the
-     * block through a tensor grid of Chebyshev proxy points carrying its
-     * interpolated dipole weights: tree_degree + 1 points on the box's widest
-     * axis, and on each narrower axis the fewest points whose interpolation
-     * error bound is 1/32 of the widest axis's (tree_grid). */
+     * a node whose box lies beyond the mixed cutoff from a target block acts
+     * on the block through a tensor grid of Chebyshev proxy points carrying
+     * its interpolated dipole weights.  The grid lies along the principal
+     * axes of the node's sources: degree p points on the widest axis, fewer
+     * on narrower ones; p is the largest of tree_degree, tree_degree - 2, ...
+     * whose grid has at most 2/3 as many points as the node has sources.
+     * Opening rule: every target at distance >= r + q_p h_max from the box's
+     * centre (r its radius, h_max its largest half-width), with q_p chosen so
+     * that the interpolation error bound equals that of the classic rule
+     * |x - c| >= r / tree_theta on a cube at tree_degree (tree_grid 1).
+     * tree_grid 2: axis-aligned boxes, (tree_degree + 1)^3 points, the
+     * classic rule. */
     int32_t tree_degree;      /* Chebyshev degree p per axis (8; 1..12) */
-    float tree_theta;         /* opening parameter (0.4; (0, 1)) */
+    float tree_theta;         /* opening parameter (0.45; (0, 1)) */
     int32_t tree_min_sources; /* meshes with at least this many source nodes
                                  use it (262,144); -1: never */
     /* The same for the float-float path (Phi to FP64 accuracy): proxies
      * with float-float positions and weights computed in FP64. */
     int32_t tree_ff_degree;      /* 14; 1..16 */
-    float tree_ff_theta;         /* 0.4 */
+    float tree_ff_theta;         /* 0.45 */
     int32_t tree_ff_min_sources; /* 262,144; -1: never */
-    int32_t tree_grid;           /* proxy grids of both treecodes: 0 or 1 per-axis
-                                    point counts (default), 2 (degree + 1)^3 on
-                                    every node */
+    int32_t tree_grid;           /* proxy grids of both treecodes: 0 or 1
+                                    oriented per-axis grids and a degree ladder
+                                    (default), 2 (degree + 1)^3 axis-aligned
+                                    grids of one degree */
     int32_t reserved;
 } lsm_options;
 

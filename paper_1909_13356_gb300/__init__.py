@@ -249,8 +249,9 @@ class Context:
         """Zero selects a default.  tree_*: the treecode far field of the mixed
         path (Chebyshev degree, opening parameter, and the source count from
         which a mesh uses it; tree_min_sources=-1 turns it off); tree_ff_*: the
-        same for the float-float path.  tree_grid: 1 per-axis proxy grids (the
-        default), 2 the full (degree + 1)^3 grid on every node."""
+        same for the float-float path.  tree_grid: 1 oriented per-axis proxy
+        grids with a degree ladder (the default), 2 full (degree + 1)^3
+        axis-aligned grids of one degree."""
         self._L = load()
         opt = _Options(cutoff_fp64, cutoff_mixed, mixed_switch, mixed_accept, int(tree_degree),
                        float(tree_theta), int(tree_min_sources), int(tree_ff_degree), float(tree_ff_theta),

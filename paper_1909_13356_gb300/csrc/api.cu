@@ -227,10 +227,10 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.mixed_switch = 1e-4;
     ctx->opt.mixed_accept = 1e-7;
     ctx->opt.tree_degree = 8;
-    ctx->opt.tree_theta = 0.4f;
+    ctx->opt.tree_theta = 0.45f;
     ctx->opt.tree_min_sources = 262144;
     ctx->opt.tree_ff_degree = 14;
-    ctx->opt.tree_ff_theta = 0.4f;
+    ctx->opt.tree_ff_theta = 0.45f;
     ctx->opt.tree_ff_min_sources = 262144;
     ctx->opt.tree_grid = 1;
     if (opt) {

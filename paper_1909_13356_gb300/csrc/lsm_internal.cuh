@@ -285,7 +285,7 @@ struct Tree {
     bool ff = false;                        // float-float proxies (FP64 weights split in two floats)
     int degree = 0;
     float theta = 0.0f;
-    int grid = 1;                           // 1 per-axis point counts, 2 full (degree + 1)^3 grids
+    int grid = 1;                           // 1 oriented per-axis grids and a degree ladder, 2 full (degree + 1)^3 grids
     int top = 0;                            // level of the root (level 0 = tiles)
     int64_t lev_off[33] = {0};              // first node of each level
     int64_t nnodes = 0;
@@ -293,6 +293,7 @@ struct Tree {
     float4* node_lo = nullptr;              // box, rounded down; w = sigma_max
     float4* node_hi = nullptr;              // box, rounded up
     int4* node_info = nullptr;              // first tile, tile count, first proxy tile or -1, proxy tiles
+    float4* node_acc = nullptr;             // proxy nodes: frame centre, (radius / theta_n)^2
     float4 *p_pos = nullptr, *p_nw = nullptr;   // proxies, kTile per proxy tile
     float4 *p_lo = nullptr, *p_nwlo = nullptr;  // float-float trees: remainders of both
     float4 *tile_lo = nullptr, *tile_hi = nullptr, *tile_chi = nullptr, *tile_clo = nullptr;

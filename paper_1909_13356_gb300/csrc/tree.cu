@@ -20,23 +20,41 @@
 // the tree) mixes source tiles and proxy tiles.  A node gets proxies only
 // when it holds at least twice as many sources as proxies.
 //
-// Points per axis.  Along axis a of half-width h_a the kernel, as a function
-// of y_a alone, has its singularities at distance >= d = (1/theta - 1) r from
-// the box (r its radius; the opening rule keeps |x - c| >= r / theta), so its
-// degree-p Chebyshev interpolant errs like rho(d / h_a)^-p, rho(q) = q +
-// sqrt(q^2 - 1), the Bernstein ellipse through the nearest singularity (a
-// real one in the worst case).  The widest axis keeps the degree; a narrower
-// axis gets the smallest degree whose bound is 1/32 of the widest axis's
-// (the tensor interpolant's error sums the axes' errors, each amplified by
-// the other axes' Lebesgue constants, about 2.7 each at these degrees).
-// Boxes of surface patches are thin across the surface, so most nodes need
-// few points on that axis.
+// Oriented grids.  A node's grid lies in its own frame: the principal axes
+// of its sources (mean, covariance, Jacobi eigenvectors) with the extents of
+// the sources along them.  Surface patches are thin across the surface in
+// that frame, whatever their tilt against the coordinate axes.
 //
-// Steps: node boxes bottom-up (k_nodes_leaf, k_nodes_up); proxy assignment
-// on the host; P2M, the weights Q_k summed from the sources in chunks
-// (k_p2m, k_p2m_reduce); per evaluation, target block boxes
-// (k_block_boxes) and two walks (count, then write) of the tree per block
-// (k_tree_walk).
+// Opening rule and points per axis.  As a function of one coordinate along
+// axis a (half-width h_a), the kernel has its singularities at distance >= d
+// from the node's box when every target is at distance >= d from it; its
+// degree-p Chebyshev interpolant then errs like rho(d / h_a)^-p, rho(q) = q +
+// sqrt(q^2 - 1) = exp(acosh q), the Bernstein ellipse through the nearest
+// singularity (a real one in the worst case).  The widest axis sets the
+// error, so a node of degree p acts on a block of targets when
+//     |x - c| >= r + q_p h_max,   q_p = cosh(C / p),
+// (c, r the centre and radius of the box) for every target x of the block:
+// then d >= q_p h_max and the error is ~exp(-C) whatever the box's shape.
+// C = p_top acosh(sqrt3 (1/theta - 1)) is the bound of the classic rule
+// |x - c| >= r / theta on a cube, so (p_top, theta) keep their meaning.  A
+// narrower axis gets the smallest degree whose bound is 1/32 of the widest
+// axis's (the tensor interpolant's error sums the axes' errors, each
+// amplified by the other axes' Lebesgue constants, about 2.7 each).
+//
+// Degree ladder.  A node acts through proxies only when it holds 1.5 times
+// as many sources as proxies, which at the top degree excludes every small
+// node.  So each node takes the largest degree of the ladder p, p - 2, ...
+// that it can carry; with the same C, lower degrees act only from farther
+// away (larger q_p).
+// tree_grid 2 keeps the first design (axis-aligned boxes, (p+1)^3 points,
+// one degree, sources >= 2 proxies, |x - c| >= r / theta) through the same
+// code with identity frames.
+//
+// Steps: node boxes bottom-up (k_nodes_leaf, k_nodes_up); node frames
+// (k_node_frames); grids and proxy assignment on the host; P2M, the weights
+// Q_k summed from the sources in chunks (k_p2m, k_p2m64, k_p2m_reduce); per
+// evaluation, target block boxes (k_block_boxes) and two walks (count, then
+// write) of the tree per block (k_tree_walk).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -90,55 +108,180 @@ __global__ void k_nodes_up(const float4* __restrict__ clo, const float4* __restr
     info[i] = make_int4(f.x, f.y, -1, 0);
 }
 
-// Grid of one node: centre and half-widths from the FP32 box (host and
-// device compute them alike), and points per axis chosen on the host once
-// (grid_counts) and passed to the device.
-struct NodeGrid {
-    double c[3], h[3];
-    int n[3];
+// Oriented box of a node: centre, orthonormal axes (rows) and half-widths.
+struct NodeFrame {
+    double c[3];
+    double e[3][3];
+    double h[3];
 };
-__host__ __device__ inline NodeGrid node_grid(float4 lo, float4 hi, int4 counts)
+
+// Bound exponent C of (degree, theta): the classic rule on a cube (host).
+double tree_bound(int degree, double theta)
 {
-    NodeGrid g;
-    const float l[3] = {lo.x, lo.y, lo.z}, u[3] = {hi.x, hi.y, hi.z};
-    const int n[3] = {counts.x, counts.y, counts.z};
-    for (int a = 0; a < 3; a++) {
-        g.c[a] = 0.5 * ((double)l[a] + (double)u[a]);
-        g.h[a] = 0.5 * ((double)u[a] - (double)l[a]);
-        g.n[a] = n[a];
-    }
-    return g;
+    const double q = std::max(1.05, std::sqrt(3.0) * (1.0 / theta - 1.0));
+    return degree * std::acosh(q);
 }
 
-// Points per axis of a node's grid (host only): one on an axis of zero
-// extent; grid 2: degree + 1 on every other axis; grid 1: degree + 1 on the
-// widest axis and the bound above on the others.
-int4 grid_counts(float4 lo, float4 hi, int degree, float theta, int grid)
+// Points per axis of a node's grid of degree p (host only), from its
+// half-widths: one on an axis of zero extent; grid 2: p + 1 on every other
+// axis; grid 1: p + 1 on the widest axis, and on the others the fewest
+// whose bound, at d = q_p h_max, is 1/32 of the widest axis's.
+int4 grid_counts(const double h[3], int p, double C, int grid)
 {
-    const float l[3] = {lo.x, lo.y, lo.z}, u[3] = {hi.x, hi.y, hi.z};
-    double h[3], hmax = 0.0, r2 = 0.0;
-    for (int a = 0; a < 3; a++) {
-        h[a] = 0.5 * ((double)u[a] - (double)l[a]);
-        hmax = std::max(hmax, h[a]);
-        r2 += h[a] * h[a];
-    }
+    double hmax = 0.0;
+    for (int a = 0; a < 3; a++) hmax = std::max(hmax, h[a]);
+    const double d = std::cosh(C / p) * hmax;
     int n[3];
-    const double d = (1.0 / (double)theta - 1.0) * std::sqrt(r2);
-    auto log_rho = [](double q) { return std::log(q + std::sqrt(q * q - 1.0)); };
-    // the bound needs the widest axis's ellipse to exist (d > h_max)
-    const bool per_axis = grid != 2 && hmax > 0.0 && d > 1.05 * hmax;
-    const double target = per_axis ? degree * log_rho(d / hmax) + std::log(32.0) : 0.0;
     for (int a = 0; a < 3; a++) {
         if (!(h[a] > 0.0)) {
             n[a] = 1;
-        } else if (!per_axis || h[a] == hmax) {
-            n[a] = degree + 1;
+        } else if (grid == 2 || h[a] == hmax) {
+            n[a] = p + 1;
         } else {
-            const int p = (int)std::ceil(target / log_rho(d / h[a]) - 1e-9);
-            n[a] = std::min(degree, std::max(1, p)) + 1;
+            const int pa = (int)std::ceil((C + std::log(32.0)) / std::acosh(d / h[a]) - 1e-9);
+            n[a] = std::min(p, std::max(1, pa)) + 1;
         }
     }
     return make_int4(n[0], n[1], n[2], 0);
+}
+
+// Sum of K doubles over a block of kFrameThreads threads, returned to every
+// thread (fixed order: warp shuffles, then the warps in order).
+constexpr int kFrameThreads = 256;
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* sm)
+{
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < K; k++) sm[w * K + k] = v[k];
+    __syncthreads();
+    for (int k = 0; k < K; k++) {
+        double t = 0.0;
+        for (int j = 0; j < kFrameThreads / 32; j++) t += sm[j * K + k];
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+// Eigenvectors of a symmetric 3x3 matrix by cyclic Jacobi rotations: the
+// columns of v.  The rotations keep v orthonormal, so any stopping point
+// gives a valid frame.
+__device__ void jacobi3(double a[3][3], double v[3][3])
+{
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) v[i][j] = i == j ? 1.0 : 0.0;
+    const double scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
+    for (int sweep = 0; sweep < 16; sweep++) {
+        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+        if (!(off > 1e-18 * scale)) break;
+        for (int r = 0; r < 3; r++) {
+            const int p = r == 2 ? 1 : 0, q = r == 0 ? 1 : 2;
+            const double apq = a[p][q];
+            if (apq == 0.0) continue;
+            const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
+            const double t = fabs(th) > 1e150 ? 0.5 / th : (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+            a[p][p] -= t * apq;
+            a[q][q] += t * apq;
+            a[p][q] = a[q][p] = 0.0;
+            const int k = 3 - p - q;
+            const double akp = a[k][p], akq = a[k][q];
+            a[k][p] = a[p][k] = c * akp - sn * akq;
+            a[k][q] = a[q][k] = sn * akp + c * akq;
+            for (int i = 0; i < 3; i++) {
+                const double vip = v[i][p], viq = v[i][q];
+                v[i][p] = c * vip - sn * viq;
+                v[i][q] = sn * vip + c * viq;
+            }
+        }
+    }
+}
+
+// Frame of each node of levels >= 1 (one CTA per node, nodes node0 ...):
+// mean and covariance of its sources in FP64, principal axes, and the
+// extents of the sources along them.  Half-widths below 1e-9 of the box's
+// radius are raised to it, so that the coordinates of the P2M basis stay in
+// [-1, 1] up to rounding.
+__global__ void __launch_bounds__(kFrameThreads) k_node_frames(const double4_32a* __restrict__ pos, int64_t ns,
+                                                               const int4* __restrict__ info, int64_t node0,
+                                                               NodeFrame* __restrict__ fr)
+{
+    __shared__ double sm[(kFrameThreads / 32) * 6];
+    __shared__ double s_e[3][3];
+    const int64_t node = node0 + blockIdx.x;
+    const int4 f = info[node];
+    const int64_t s0 = (int64_t)f.x * kTile, s1 = min(ns, (int64_t)(f.x + f.y) * kTile);
+    const double cnt = (double)max((int64_t)1, s1 - s0);
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += kFrameThreads) {
+        const double4_32a p = pos[i];
+        m[0] += p.x;
+        m[1] += p.y;
+        m[2] += p.z;
+    }
+    block_sum<3>(m, sm);
+    for (int k = 0; k < 3; k++) m[k] /= cnt;
+    double cv[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += kFrameThreads) {
+        const double4_32a p = pos[i];
+        const double d0 = p.x - m[0], d1 = p.y - m[1], d2 = p.z - m[2];
+        cv[0] += d0 * d0;
+        cv[1] += d0 * d1;
+        cv[2] += d0 * d2;
+        cv[3] += d1 * d1;
+        cv[4] += d1 * d2;
+        cv[5] += d2 * d2;
+    }
+    block_sum<6>(cv, sm);
+    if (threadIdx.x == 0) {
+        double a[3][3] = {{cv[0], cv[1], cv[2]}, {cv[1], cv[3], cv[4]}, {cv[2], cv[4], cv[5]}}, v[3][3];
+        jacobi3(a, v);
+        for (int ax = 0; ax < 3; ax++)
+            for (int c = 0; c < 3; c++) s_e[ax][c] = v[c][ax];
+    }
+    __syncthreads();
+    double e[3][3];
+    for (int ax = 0; ax < 3; ax++)
+        for (int c = 0; c < 3; c++) e[ax][c] = s_e[ax][c];
+    double ext[6] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY};   // max, then -min
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += kFrameThreads) {
+        const double4_32a p = pos[i];
+        const double d[3] = {p.x - m[0], p.y - m[1], p.z - m[2]};
+        for (int ax = 0; ax < 3; ax++) {
+            const double t = d[0] * e[ax][0] + d[1] * e[ax][1] + d[2] * e[ax][2];
+            ext[ax] = fmax(ext[ax], t);
+            ext[3 + ax] = fmax(ext[3 + ax], -t);
+        }
+    }
+    for (int k = 0; k < 6; k++)
+        for (int o = 16; o > 0; o >>= 1) ext[k] = fmax(ext[k], __shfl_xor_sync(0xffffffffu, ext[k], o));
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 6; k++) sm[w * 6 + k] = ext[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; k++)
+            for (int j = 1; j < kFrameThreads / 32; j++) ext[k] = fmax(ext[k], sm[j * 6 + k]);
+        NodeFrame F;
+        double r2 = 0.0;
+        for (int ax = 0; ax < 3; ax++) {
+            const double hi = ext[ax], lo = -ext[3 + ax];
+            F.h[ax] = 0.5 * (hi - lo);
+            r2 += F.h[ax] * F.h[ax];
+            const double mid = 0.5 * (hi + lo);
+            for (int c = 0; c < 3; c++) F.e[ax][c] = e[ax][c];
+            m[0] += mid * e[ax][0];
+            m[1] += mid * e[ax][1];
+            m[2] += mid * e[ax][2];
+        }
+        const double hmin = 1e-9 * sqrt(r2);
+        for (int ax = 0; ax < 3; ax++) F.h[ax] = fmax(F.h[ax], hmin);
+        for (int c = 0; c < 3; c++) F.c[c] = m[c];
+        fr[node] = F;
+    }
 }
 
 // Chebyshev points of the second kind on [-1, 1], in FP32.
@@ -151,8 +294,7 @@ struct P2MArgs {
     const double4_32a* pos;   // (x, y, z, a)
     const double4_32a* nw;    // (nw / 4 pi, 0)
     int64_t ns;
-    const float4* nlo;
-    const float4* nhi;
+    const NodeFrame* fr;      // each node's oriented box
     const int4* ninfo;
     const int4* items;        // node, first tile, end tile, partial offset (in proxies) or -1
     const int4* ngrid;        // points per axis of each node's grid
@@ -172,10 +314,11 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(P2MArgs A)
     __shared__ __align__(16) float sN[kTile][4];
     const int4 it = A.items[blockIdx.x];
     const int node = it.x;
-    const float4 lo = A.nlo[node], hi = A.nhi[node];
     const int4 info = A.ninfo[node];
-    const NodeGrid G = node_grid(lo, hi, A.ngrid[node]);
-    const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+    const NodeFrame& F = A.fr[node];
+    const int4 gn = A.ngrid[node];
+    const int Gn[3] = {gn.x, gn.y, gn.z};
+    const int n0 = gn.x, n1 = gn.y, n2 = gn.z;
     const int pairs = n0 * n1;
     const int tid = threadIdx.x;
     const bool fits = (size_t)pairs * n2 * 3 * sizeof(double) <= sizeof(sL);
@@ -196,15 +339,16 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(P2MArgs A)
             if (i < A.ns) {
                 const double4_32a p = A.pos[i];
                 const double4_32a q = A.nw[i];
-                const double y[3] = {p.x, p.y, p.z};
+                const double d[3] = {p.x - F.c[0], p.y - F.c[1], p.z - F.c[2]};
                 for (int a = 0; a < 3; a++) {
                     float* L = sL[a][tid];
-                    const int na = G.n[a];
+                    const int na = Gn[a];
                     if (na == 1) {
                         L[0] = 1.0f;
                         continue;
                     }
-                    const float xi = (float)((y[a] - G.c[a]) / G.h[a]);
+                    const double pr = d[0] * F.e[a][0] + d[1] * F.e[a][1] + d[2] * F.e[a][2];
+                    const float xi = (float)(pr / F.h[a]);
                     // barycentric weights (-1)^k, halved at the two ends
                     int hit = -1;
                     float sum = 0.0f;
@@ -230,7 +374,7 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(P2MArgs A)
                 sN[tid][3] = 0.0f;
             } else {
                 for (int a = 0; a < 3; a++)
-                    for (int k = 0; k < G.n[a]; k++) sL[a][tid][k] = 0.0f;
+                    for (int k = 0; k < Gn[a]; k++) sL[a][tid][k] = 0.0f;
                 sN[tid][0] = sN[tid][1] = sN[tid][2] = sN[tid][3] = 0.0f;
             }
         }
@@ -308,11 +452,13 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(P2MArgs A)
             dst[2] = Q[k2][2];
         }
         if (first_chunk) {
-            const float s0 = n0 > 1 ? cheb_point(k0, n0 - 1) : 0.0f;
-            const float s1 = n1 > 1 ? cheb_point(k1, n1 - 1) : 0.0f;
-            const float s2 = n2 > 1 ? cheb_point(k2, n2 - 1) : 0.0f;
-            A.p_pos[base + k] = make_float4((float)(G.h[0] * (double)s0), (float)(G.h[1] * (double)s1),
-                                            (float)(G.h[2] * (double)s2), 0.0f);
+            // the grid point's offset from the frame's centre
+            const double t0 = F.h[0] * (double)(n0 > 1 ? cheb_point(k0, n0 - 1) : 0.0f);
+            const double t1 = F.h[1] * (double)(n1 > 1 ? cheb_point(k1, n1 - 1) : 0.0f);
+            const double t2 = F.h[2] * (double)(n2 > 1 ? cheb_point(k2, n2 - 1) : 0.0f);
+            float o[3];
+            for (int c = 0; c < 3; c++) o[c] = (float)(t0 * F.e[0][c] + t1 * F.e[1][c] + t2 * F.e[2][c]);
+            A.p_pos[base + k] = make_float4(o[0], o[1], o[2], 0.0f);
         }
     }
 }
@@ -331,11 +477,12 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
     __shared__ double sN[kP2M64Src][3];
     const int4 it = A.items[blockIdx.x];
     const int node = it.x;
-    const float4 lo = A.nlo[node], hi = A.nhi[node];
     const int4 info = A.ninfo[node];
-    const NodeGrid G = node_grid(lo, hi, A.ngrid[node]);
-    const int n1 = G.n[1], n2 = G.n[2];
-    const int npair = G.n[0] * n1;
+    const NodeFrame& F = A.fr[node];
+    const int4 gn = A.ngrid[node];
+    const int Gn[3] = {gn.x, gn.y, gn.z};
+    const int n1 = gn.y, n2 = gn.z;
+    const int npair = gn.x * n1;
     if ((int)blockIdx.y * kP2MThreads >= npair) return;   // whole CTA, before any barrier
     const int tid = threadIdx.x;
     const int pr = blockIdx.y * kP2MThreads + tid;
@@ -352,15 +499,15 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
                 if (i < A.ns) {
                     const double4_32a p = A.pos[i];
                     const double4_32a w = A.nw[i];
-                    const double y[3] = {p.x, p.y, p.z};
+                    const double d[3] = {p.x - F.c[0], p.y - F.c[1], p.z - F.c[2]};
                     for (int a = 0; a < 3; a++) {
                         double* L = sL[a][tid];
-                        const int na = G.n[a];
+                        const int na = Gn[a];
                         if (na == 1) {
                             L[0] = 1.0;
                             continue;
                         }
-                        const double xi = (y[a] - G.c[a]) / G.h[a];
+                        const double xi = (d[0] * F.e[a][0] + d[1] * F.e[a][1] + d[2] * F.e[a][2]) / F.h[a];
                         int hit = -1;
                         double sum = 0.0;
                         for (int m = 0; m < na; m++) {
@@ -384,7 +531,7 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
                     sN[tid][2] = w.z;
                 } else {
                     for (int a = 0; a < 3; a++)
-                        for (int m = 0; m < G.n[a]; m++) sL[a][tid][m] = 0.0;
+                        for (int m = 0; m < Gn[a]; m++) sL[a][tid][m] = 0.0;
                     sN[tid][0] = sN[tid][1] = sN[tid][2] = 0.0;
                 }
             }
@@ -425,13 +572,15 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m64(P2MArgs A)
             o[2] = q[k2][2];
         }
         if (it.y == info.x) {
-            const double r[3] = {G.n[0] > 1 ? G.h[0] * cheb_point64(k0, G.n[0] - 1) : 0.0,
-                                 n1 > 1 ? G.h[1] * cheb_point64(k1, n1 - 1) : 0.0,
-                                 n2 > 1 ? G.h[2] * cheb_point64(k2, n2 - 1) : 0.0};
+            // the grid point's offset from the frame's centre
+            const double t[3] = {Gn[0] > 1 ? F.h[0] * cheb_point64(k0, Gn[0] - 1) : 0.0,
+                                 n1 > 1 ? F.h[1] * cheb_point64(k1, n1 - 1) : 0.0,
+                                 n2 > 1 ? F.h[2] * cheb_point64(k2, n2 - 1) : 0.0};
             float rh[3], rl[3];
             for (int a = 0; a < 3; a++) {
-                rh[a] = (float)r[a];
-                rl[a] = (float)(r[a] - (double)rh[a]);
+                const double r = t[0] * F.e[0][a] + t[1] * F.e[1][a] + t[2] * F.e[2][a];
+                rh[a] = (float)r;
+                rl[a] = (float)(r - (double)rh[a]);
             }
             A.p_pos[dst] = make_float4(rh[0], rh[1], rh[2], 0.0f);
             A.p_lo[dst] = make_float4(rl[0], rl[1], rl[2], 0.0f);
@@ -517,12 +666,13 @@ struct WalkArgs {
     int nblk;
     const float4* nlo;
     const float4* nhi;
+    const float4* acc;     // proxy nodes: centre of the frame, (radius / theta_n)^2
     const int4* info;
     int64_t lev_off[kMaxLevels + 1];
     int top;
     int ntiles;
     int sigx;              // sigma(x) mode: the near width is the block's (blo.w)
-    float theta2, cut2;
+    float cut2;
     const uint32_t* off;   // pass 1: list offset of each block
     uint32_t* cnt;         // pass 0: list length of each block
     int* list;             // pass 1
@@ -553,13 +703,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass
             const float gz = fmaxf(0.0f, fmaxf(lo.z - bh.z, bl.z - hi.z));
             const float sw = A.sigx ? bl.w : lo.w;
             if (gx * gx + gy * gy + gz * gz > A.cut2 * sw * sw * 1.0001f) {
-                const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
-                const float ex = hi.x - lo.x, ey = hi.y - lo.y, ez = hi.z - lo.z;
-                const float r2 = 0.25f * (ex * ex + ey * ey + ez * ez);
-                const float dx = fmaxf(0.0f, fmaxf(bl.x - cx, cx - bh.x));
-                const float dy = fmaxf(0.0f, fmaxf(bl.y - cy, cy - bh.y));
-                const float dz = fmaxf(0.0f, fmaxf(bl.z - cz, cz - bh.z));
-                if ((dx * dx + dy * dy + dz * dz) * A.theta2 >= r2 * 1.0001f) {
+                // opening rule: the block at distance >= radius / theta_n
+                // from the centre of the node's frame
+                const float4 ac = A.acc[node];
+                const float dx = fmaxf(0.0f, fmaxf(bl.x - ac.x, ac.x - bh.x));
+                const float dy = fmaxf(0.0f, fmaxf(bl.y - ac.y, ac.y - bh.y));
+                const float dz = fmaxf(0.0f, fmaxf(bl.z - ac.z, ac.z - bh.z));
+                if (dx * dx + dy * dy + dz * dz >= ac.w * 1.0001f) {
                     if (pass)
                         for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.ntiles + f.z + k;
                     n += f.w;
@@ -606,7 +756,7 @@ bool tree_wanted(const Ctx* ctx, const Mesh* me, bool ff)
 void tree_free(Tree* t)
 {
     if (!t) return;
-    void* ps[] = {t->node_lo, t->node_hi, t->node_info, t->p_pos, t->p_nw, t->p_lo, t->p_nwlo, t->tile_lo,
+    void* ps[] = {t->node_lo, t->node_hi, t->node_info, t->node_acc, t->p_pos, t->p_nw, t->p_lo, t->p_nwlo, t->tile_lo,
                   t->tile_hi, t->tile_chi, t->tile_clo};
     for (void* p : ps)
         if (p) cudaFree(p);
@@ -661,7 +811,8 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     }
     T->top = lev;
     T->nnodes = T->lev_off[lev + 1];
-    if (!alloc(&T->node_lo, T->nnodes) || !alloc(&T->node_hi, T->nnodes) || !alloc(&T->node_info, T->nnodes)) {
+    if (!alloc(&T->node_lo, T->nnodes) || !alloc(&T->node_hi, T->nnodes) || !alloc(&T->node_info, T->nnodes) ||
+        !alloc(&T->node_acc, T->nnodes)) {
         cudaGetLastError();
         ctx->err = "tree: out of device memory";
         return fail(LSM_E_OOM);
@@ -678,7 +829,28 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
         ctx->launches++;
     }
-    // proxy assignment on the host
+    // node frames: principal axes on the device (grid 1), or the axis-aligned
+    // boxes (grid 2, filled on the host below)
+    Scratch sb(st);
+    NodeFrame* d_fr = nullptr;
+    const int64_t n_inner = T->nnodes - T->lev_off[1];
+    if (sb.get(&d_fr, (size_t)T->nnodes)) {
+        ctx->err = "tree: out of device memory";
+        return fail(LSM_E_OOM);
+    }
+    std::vector<NodeFrame> hfr(T->nnodes);
+    if (grid != 2 && n_inner > 0) {
+        k_node_frames<<<(unsigned)n_inner, kFrameThreads, 0, st>>>(me->s64_pos, me->ns, T->node_info, T->lev_off[1],
+                                                                  d_fr);
+        if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
+        ctx->launches++;
+        if (cudaMemcpyAsync(hfr.data() + T->lev_off[1], d_fr + T->lev_off[1], sizeof(NodeFrame) * n_inner,
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            ctx->err = "tree: copy of the node frames failed";
+            return fail(LSM_E_CUDA);
+        }
+    }
+    // grids and proxy assignment on the host
     std::vector<float4> hlo(T->nnodes), hhi(T->nnodes);
     std::vector<int4> hinfo(T->nnodes);
     if (cudaMemcpyAsync(hlo.data(), T->node_lo, sizeof(float4) * T->nnodes, cudaMemcpyDeviceToHost, st) !=
@@ -691,20 +863,54 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         ctx->err = "tree: copy of the node boxes failed";
         return fail(LSM_E_CUDA);
     }
+    if (grid == 2) {
+        for (int64_t node = T->lev_off[1]; node < T->nnodes; node++) {
+            NodeFrame& F = hfr[node];
+            const float l[3] = {hlo[node].x, hlo[node].y, hlo[node].z}, u[3] = {hhi[node].x, hhi[node].y, hhi[node].z};
+            for (int a = 0; a < 3; a++) {
+                F.c[a] = 0.5 * ((double)l[a] + (double)u[a]);
+                F.h[a] = 0.5 * ((double)u[a] - (double)l[a]);
+                for (int c = 0; c < 3; c++) F.e[a][c] = a == c ? 1.0 : 0.0;
+            }
+        }
+    }
+    // the degree ladder; grid 2: one degree
+    const double C = tree_bound(degree, theta);
+    std::vector<int> ladder;
+    for (int p = degree; p >= (grid == 2 ? degree : std::max(3, degree / 2 - 1)); p -= 2) ladder.push_back(p);
     std::vector<int4> items, reds;
     std::vector<int4> hgrid(T->nnodes, make_int4(1, 1, 1, 0));
+    std::vector<float4> hacc(T->nnodes, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
     std::vector<float4> ptlo, pthi, ptchi, ptclo;
     int64_t nptiles = 0, npartial = 0;
     for (int l = 1; l <= T->top; l++) {
         for (int64_t node = T->lev_off[l]; node < T->lev_off[l + 1]; node++) {
             int4& f = hinfo[node];
+            const NodeFrame& F = hfr[node];
             const int64_t s0 = (int64_t)f.x * kTile;
             const int64_t s1 = std::min<int64_t>(me->ns, (int64_t)(f.x + f.y) * kTile);
-            const int4 gn = grid_counts(hlo[node], hhi[node], degree, theta, grid);
-            const NodeGrid G = node_grid(hlo[node], hhi[node], gn);
-            const int64_t np = (int64_t)G.n[0] * G.n[1] * G.n[2];
-            if (2 * np > s1 - s0) continue;
+            // the largest ladder degree whose grid the node can carry: sources
+            // >= 1.5 x proxies (grid 2: >= 2 x)
+            int4 gn = make_int4(1, 1, 1, 0);
+            int64_t np = 0;
+            int pn = 0;
+            for (int p : ladder) {
+                const int4 g = grid_counts(F.h, p, C, grid);
+                const int64_t n3 = (int64_t)g.x * g.y * g.z;
+                if (grid == 2 ? 2 * n3 <= s1 - s0 : 3 * n3 <= 2 * (s1 - s0)) {
+                    gn = g;
+                    np = n3;
+                    pn = p;
+                    break;
+                }
+            }
+            if (np == 0) continue;
             hgrid[node] = gn;
+            // the opening radius
+            const double r = std::sqrt(F.h[0] * F.h[0] + F.h[1] * F.h[1] + F.h[2] * F.h[2]);
+            const double hmax = std::max(F.h[0], std::max(F.h[1], F.h[2]));
+            const double R = grid == 2 ? r / theta : r + std::cosh(C / pn) * hmax;
+            hacc[node] = make_float4((float)F.c[0], (float)F.c[1], (float)F.c[2], (float)(R * R));
             const int npt = (int)((np + kTile - 1) / kTile);
             f.z = (int)nptiles;
             f.w = npt;
@@ -714,8 +920,8 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
                 pthi.push_back(make_float4(hhi[node].x, hhi[node].y, hhi[node].z, (float)cnt));
                 float ch[3], cl[3];
                 for (int a = 0; a < 3; a++) {
-                    ch[a] = (float)G.c[a];
-                    cl[a] = (float)(G.c[a] - (double)ch[a]);
+                    ch[a] = (float)F.c[a];
+                    cl[a] = (float)(F.c[a] - (double)ch[a]);
                 }
                 ptchi.push_back(make_float4(ch[0], ch[1], ch[2], 0.0f));
                 ptclo.push_back(make_float4(cl[0], cl[1], cl[2], 0.0f));
@@ -737,6 +943,11 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
                 return fail(LSM_E_INVALID_ARG);
             }
         }
+    }
+    if (cudaMemcpyAsync(T->node_acc, hacc.data(), sizeof(float4) * T->nnodes, cudaMemcpyHostToDevice, st) ||
+        (grid == 2 && cudaMemcpyAsync(d_fr, hfr.data(), sizeof(NodeFrame) * T->nnodes, cudaMemcpyHostToDevice, st))) {
+        ctx->err = "tree: copy failed";
+        return fail(LSM_E_CUDA);
     }
     T->nptiles = (int)nptiles;
     const int64_t nall = me->ntiles + nptiles;
@@ -787,8 +998,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         P.pos = me->s64_pos;
         P.nw = me->s64_nw;
         P.ns = me->ns;
-        P.nlo = T->node_lo;
-        P.nhi = T->node_hi;
+        P.fr = d_fr;
         P.ninfo = T->node_info;
         P.items = d_items;
         P.ngrid = d_grid;
@@ -844,12 +1054,12 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double*
     W.nblk = nblk;
     W.nlo = T->node_lo;
     W.nhi = T->node_hi;
+    W.acc = T->node_acc;
     W.info = T->node_info;
     for (int l = 0; l <= kMaxLevels; l++) W.lev_off[l] = l <= T->top + 1 ? T->lev_off[l] : 0;
     W.top = T->top;
     W.ntiles = T->ntiles;
     W.sigx = tsig != nullptr;
-    W.theta2 = T->theta * T->theta;
     // the near radius of the pair kernel that evaluates the lists
     const double cut = cut_override > 0 ? cut_override : (T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed);
     W.cut2 = (float)(cut * cut);

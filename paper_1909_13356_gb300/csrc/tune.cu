@@ -31,8 +31,8 @@ struct Candidate {
     float theta;
 };
 const Candidate kCandidates[] = {
-    {0, 0, 0.0f},    {1, 4, 0.25f},  {1, 5, 0.3f},  {1, 6, 0.3f},  {1, 6, 0.35f},
-    {1, 7, 0.35f},   {1, 7, 0.4f},   {1, 8, 0.4f},  {1, 8, 0.5f},  {1, 10, 0.5f},
+    {0, 0, 0.0f},    {1, 5, 0.35f},  {1, 6, 0.4f},  {1, 6, 0.45f},  {1, 7, 0.4f},
+    {1, 7, 0.45f},   {1, 7, 0.5f},   {1, 8, 0.45f}, {1, 8, 0.5f},   {1, 10, 0.55f},
 };
 
 // max |a - b| over n entries, as the bit pattern of a non-negative double

@@ -47,6 +47,31 @@ def test_torus_full_evaluation_sampled(lsm, oracle_mod, torus):
         assert np.abs(g - go).max() <= gtol / m.sigma.min()
 
 
+def test_torus_oriented_trees_against_first_design(lsm, oracle_mod, torus):
+    """The default trees (oriented per-axis grids, degree ladder, shape-aware
+    opening rule) against the first design (axis-aligned (p+1)^3 grids, one
+    degree, |x - c| >= r / theta; mixed (8, 0.4), float-float (13, 0.4)) on
+    the full torus: both within the bars on sampled targets, and the default
+    evaluates fewer far pairs in both paths."""
+    w, ctx, mesh, (y, nw, sg) = torus
+    m = w["mesh"]
+    x = torch.from_numpy(w["targets"]).cuda()
+    sel = np.random.default_rng(17).choice(len(w["targets"]), 64, replace=False)
+    po, _ = oracle_mod.phi_grad(y, nw, sg, w["targets"][sel])
+    ctx_old = lsm.Context(0, tree_grid=2, tree_degree=8, tree_theta=0.4, tree_ff_degree=13, tree_ff_theta=0.4)
+    mesh_old = ctx_old.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    far = {}
+    for name, c, me in (("new", ctx, mesh), ("old", ctx_old, mesh_old)):
+        for prec, tol in ((lsm.MIXED, 1e-7), (lsm.FF, 1e-12)):
+            me.eval_phi_grad(x[:4096], prec)   # builds the tree
+            c.read_stats(reset=True)
+            phi, _ = me.eval_phi_grad(x, prec)
+            far[name, prec] = c.read_stats(reset=True)["pairs_far"]
+            assert np.abs(phi.cpu().numpy()[sel] - po).max() <= tol, (name, prec)
+    assert far["new", lsm.MIXED] < far["old", lsm.MIXED], far
+    assert far["new", lsm.FF] < 0.85 * far["old", lsm.FF], far
+
+
 def test_torus_full_chart_solve_sampled(lsm, oracle_mod, torus):
     w, ctx, mesh, (y, nw, sg) = torus
     x, h, st, stats = mesh.solve_charts(order=8, tol=1e-12, precision=lsm.MIXED, device_out=True)
