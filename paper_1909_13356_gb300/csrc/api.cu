@@ -392,8 +392,7 @@ int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* 
     me->m = nt;
     me->nq = nq;
     me->rule = q;
-    me->ns = ns;
-    me->ntiles = (ns + kTile - 1) / kTile;
+    me->ns = ns;   // tiles (and the padded source arrays) are laid out by build_mesh_device
     auto fail = [&](int rc) {
         lsm_mesh_free(mh);
         return rc;
@@ -405,12 +404,8 @@ int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* 
         me->bytes += bytes;
         return true;
     };
-    const size_t ntl = (size_t)me->ntiles;
     if (!alloc(&me->verts, 3 * nv) || !alloc(&me->tris, 3 * nt) || !alloc(&me->tri_sigma, nt) ||
-        !alloc(&me->tri_n, 3 * nt) || !alloc(&me->vpn, 3 * nv) || !alloc(&me->s64_pos, ns) ||
-        !alloc(&me->s64_nw, ns) || !alloc(&me->s32_pos, ns) || !alloc(&me->s32_nw, ns) || !alloc(&me->s32_lo, ns) || !alloc(&me->s32_nwlo, ns) ||
-        !alloc(&me->tile_lo, ntl) || !alloc(&me->tile_hi, ntl) || !alloc(&me->tile_chi, ntl) ||
-        !alloc(&me->tile_clo, ntl)) {
+        !alloc(&me->tri_n, 3 * nt) || !alloc(&me->vpn, 3 * nv)) {
         cudaGetLastError();
         ctx->err = "mesh_upload: out of device memory";
         return fail(LSM_E_OOM);

@@ -72,12 +72,12 @@ int batch_build(Ctx* ctx, Batch* b, lsm_mesh* const* meshes, int n, cudaStream_t
         LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->vpn + 3 * voff[i], me->vpn, sizeof(double) * 3 * me->nv, dd, st));
         LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->tris + 3 * toff[i], me->tris, sizeof(int32_t) * 3 * me->m, dd, st));
         LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->tri_sigma + toff[i], me->tri_sigma, sizeof(double) * me->m, dd, st));
-        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s32_pos + so, me->s32_pos, sizeof(float4) * me->ns, dd, st));
-        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s32_nw + so, me->s32_nw, sizeof(float4) * me->ns, dd, st));
-        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s32_lo + so, me->s32_lo, sizeof(float4) * me->ns, dd, st));
-        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s32_nwlo + so, me->s32_nwlo, sizeof(float4) * me->ns, dd, st));
-        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s64_pos + so, me->s64_pos, sizeof(double4_32a) * me->ns, dd, st));
-        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s64_nw + so, me->s64_nw, sizeof(double4_32a) * me->ns, dd, st));
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s32_pos + so, me->s32_pos, sizeof(float4) * me->ntiles * kTile, dd, st));
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s32_nw + so, me->s32_nw, sizeof(float4) * me->ntiles * kTile, dd, st));
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s32_lo + so, me->s32_lo, sizeof(float4) * me->ntiles * kTile, dd, st));
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s32_nwlo + so, me->s32_nwlo, sizeof(float4) * me->ntiles * kTile, dd, st));
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s64_pos + so, me->s64_pos, sizeof(double4_32a) * me->ntiles * kTile, dd, st));
+        LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->s64_nw + so, me->s64_nw, sizeof(double4_32a) * me->ntiles * kTile, dd, st));
         LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->tile_lo + tileoff[i], me->tile_lo, sizeof(float4) * me->ntiles, dd, st));
         LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->tile_hi + tileoff[i], me->tile_hi, sizeof(float4) * me->ntiles, dd, st));
         LSM_CUDA_TRY(ctx, cudaMemcpyAsync(b->tile_chi + tileoff[i], me->tile_chi, sizeof(float4) * me->ntiles, dd, st));

@@ -158,8 +158,8 @@ __device__ __forceinline__ float rsqrt_refined(float r2)
 
 // Piecewise polynomial table of H(w) = g(u)/u^3, w = u^2 (see build_h_table):
 // interval k covers w in [k, k+1)/kHTabPerUnit; per interval three float4:
-// {c0h, c0l, c1h, c1l}, {c2h, c2l, c3, c4}, {c5, c6, 0, 0}, p(t) = sum c_j t^j,
-// t = w - centre.  Beyond kHTabWmax, H = 1/u^3 to 1e-14.
+// {c0h, c0l, c1h, c1l}, {c2h, c2l, c3h, c3l}, {c4h, c4l, c5, c6}, p(t) =
+// sum c_j t^j, t = w - centre.  Beyond kHTabWmax, H = 1/u^3 to 1e-14.
 constexpr int kHTabPerUnit = 16;
 constexpr int kHTabN = 520;                   // covers w < 32.5 (u < 5.70)
 constexpr float kHTabWmax = (float)kHTabN / kHTabPerUnit;
@@ -177,9 +177,9 @@ __device__ __forceinline__ void radial_tab32(float r2, float a, const float4* __
         const int k = min((int)(w * (float)kHTabPerUnit), kHTabN - 1);
         const float t = w - ((float)k + 0.5f) * (1.0f / kHTabPerUnit);
         const float4 c01 = tab[3 * k], c23 = tab[3 * k + 1], c45 = tab[3 * k + 2];
-        const float H = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(c45.y, t, c45.x), t, c23.w), t, c23.z), t, c23.x), t, c01.z),
+        const float H = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(c45.w, t, c45.z), t, c45.x), t, c23.z), t, c23.x), t, c01.z),
                              t, c01.x);
-        const float dH = fmaf(fmaf(fmaf(fmaf(fmaf(6.0f * c45.y, t, 5.0f * c45.x), t, 4.0f * c23.w), t,
+        const float dH = fmaf(fmaf(fmaf(fmaf(fmaf(6.0f * c45.w, t, 5.0f * c45.z), t, 4.0f * c45.x), t,
                                         3.0f * c23.z), t, 2.0f * c23.x), t, c01.z);
         const float a3 = a2 * a;
         fH = a3 * H;
@@ -372,6 +372,10 @@ __device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, f
 // rsqrt plus a float-float Newton step; near: a^3 H(w) from the table),
 // nw . r and the product.  Also returns, rounded to FP32, the values the
 // gradient uses (r, |r|^2, nw . r) and, for far pairs, the rsqrt estimate.
+// FULL: the table's c0..c4 in float-float Horner steps (H to ~1e-15; the
+// FP32 c3 t^3 term alone errs by 4e-12 of H near w = 1, |t| <= 1/32); else
+// c0..c2 (the mixed path's near Phi, to ~1e-11 of H).
+template <bool FULL>
 __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const float4& yl, const float4& nl,
                                         const float* qh, const float* ql, bool far,
                                         const float4* __restrict__ tab, float& qhi, float& qlo, float& dxh,
@@ -409,10 +413,19 @@ __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const 
         two_diff(wh, wc, th, te);
         const float tl = te + wl;
         const float4 c01 = tab[3 * k], c23 = tab[3 * k + 1], c45 = tab[3 * k + 2];
-        // tail in FP32, then three float-float Horner steps
-        const float q = fmaf(fmaf(fmaf(c45.y, th, c45.x), th, c23.w), th, c23.z);
+        // tail in FP32, then float-float Horner steps
         float Hh, Hl, mh, ml;
-        ff_mul(th, tl, q, 0.0f, mh, ml);
+        if (FULL) {
+            const float q = fmaf(c45.w, th, c45.z);
+            ff_mul(th, tl, q, 0.0f, mh, ml);
+            ff_add(c45.x, c45.y, mh, ml, Hh, Hl);
+            ff_mul(th, tl, Hh, Hl, mh, ml);
+            ff_add(c23.z, c23.w, mh, ml, Hh, Hl);
+            ff_mul(th, tl, Hh, Hl, mh, ml);
+        } else {
+            const float q = fmaf(fmaf(fmaf(c45.w, th, c45.z), th, c45.x), th, c23.z);
+            ff_mul(th, tl, q, 0.0f, mh, ml);
+        }
         ff_add(c23.x, c23.y, mh, ml, Hh, Hl);
         ff_mul(th, tl, Hh, Hl, mh, ml);
         ff_add(c01.z, c01.w, mh, ml, Hh, Hl);
@@ -422,7 +435,10 @@ __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const 
         ff_mul(aah, aal, y.w, yl.w, a3h, a3l);
         ff_mul(a3h, a3l, Hh, Hl, fHh, fHl);
     } else {
-        // 1/|r| = r0 (1 + delta/2), delta = 1 - |r|^2 r0^2; fH = 1/|r|^3
+        // 1/|r| = r0 (1 - delta)^-1/2 = r0 (1 + delta/2 + 3 delta^2/8 + ...),
+        // delta = 1 - |r|^2 r0^2 (~5e-7 from the hardware estimate); fH =
+        // 1/|r|^3.  The delta^2 term is ~1e-13 of 1/|r| and of one sign for
+        // every pair, so dropping it biases the whole far sum
         r0 = rsqrtf(rh);
         const float a = r0 * r0, ae = fmaf(r0, r0, -a);
         const float hh = rh * a;
@@ -430,7 +446,7 @@ __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const 
         he = fmaf(rh, ae, he);
         he = fmaf(rl, a, he);
         const float delta = (1.0f - hh) - he;
-        const float ril = 0.5f * r0 * delta;
+        const float ril = r0 * delta * fmaf(0.375f, delta, 0.5f);
         const float q2l = fmaf(2.0f * r0, ril, ae);
         fHh = a * r0;
         fHl = fmaf(a, r0, -fHh) + fmaf(a, ril, q2l * r0);
@@ -724,7 +740,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                     const float4 ya = SIGX ? make_float4(y.x, y.y, y.z, ta_h[k]) : y;
                     const float4 yla = SIGX ? make_float4(yl.x, yl.y, yl.z, ta_l[k]) : yl;
                     float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
-                    ff_pair(ya, n, yla, nl, qh[k], ql[k], false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
+                    ff_pair<false>(ya, n, yla, nl, qh[k], ql[k], false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
                     float sph, tph;
                     two_sum(cph[k], qh_, sph, tph);
                     cph[k] = sph;
@@ -986,7 +1002,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
 // tiles use the Laplace factor 1/|r|^3.  Near pairs use a^3 H(w), w = u^2,
 // H = g(u)/u^3, read from a piecewise polynomial table (kHTabPerUnit
 // intervals per unit of w up to kHTabWmax, degree 6 in the local variable,
-// the three leading coefficients in float-float); beyond kHTabWmax H equals
+// the five leading coefficients in float-float); beyond kHTabWmax H equals
 // 1/u^3 to 1e-14.  grad Phi keeps mixed accuracy (FP32, compensated sums):
 // it only steers Newton.
 constexpr int kFFStage = kTile * 64;  // bytes per stage: 4 float4 arrays
@@ -1005,6 +1021,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     __shared__ int s_warp[kEvalThreads / 32];
     __shared__ int s_nnear;
     __shared__ float s_smax;
+    __shared__ float4 s_dref[2][2];   // per stage: tile centre - block reference, float pair
 
     const int tid = threadIdx.x;
     int base, tend, t0, t1;
@@ -1035,13 +1052,19 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     for (int k = tid; k < kHTabN * 3; k += kEvalThreads) s_htab[k] = g_htab[k];
     int mode = A.ff_mode;
 
+    // the target relative to the block's first target, as a float pair: a
+    // float pair of the absolute position would carry only ~48 bits of |x|,
+    // an error that grad Phi (~1/sigma) turns into ~1e-13 of Phi
+    double bref[3];
     float xh[3], xl[3];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const double v = valid ? A.tx[c * A.ld + i] : 0.0;
-        xh[c] = __double2float_rn(v);
-        xl[c] = __double2float_rn(v - (double)xh[c]);
+        bref[c] = A.tx[c * A.ld + base];
+        const double v = valid ? A.tx[c * A.ld + i] : bref[c];
+        const double xb = v - bref[c];
+        xh[c] = __double2float_rn(xb);
+        xl[c] = __double2float_rn(xb - (double)xh[c]);
         if (valid) {
             lo[c] = __double2float_rd(v);
             hi[c] = __double2float_ru(v);
@@ -1126,6 +1149,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     auto issue = [&](int t, int b) {
         const int cnt = (int)A.thi[t].w;
         const uint32_t by = (uint32_t)cnt * 16u;
+        // the tile's centre relative to the block reference, in FP64 (read
+        // by every thread after the stage's barrier)
+        const float4 ch = A.tchi[t], cl = A.tclo[t];
+        const double d0 = ((double)ch.x - bref[0]) + (double)cl.x, d1 = ((double)ch.y - bref[1]) + (double)cl.y,
+                     d2 = ((double)ch.z - bref[2]) + (double)cl.z;
+        const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
+        s_dref[b][0] = make_float4(h0, h1, h2, 0.0f);
+        s_dref[b][1] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1), (float)(d2 - (double)h2), 0.0f);
         mbar_expect_tx(&bar[b], 4u * by);
         // proxy tiles (list mode, ids >= ntiles) come from the tree's arrays
         const bool proxy = t >= A.ntiles;
@@ -1155,7 +1186,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             t >= A.ntiles || tile_is_far(s_bb, SIGX ? with_sigma(A.tlo[t], s_smax) : A.tlo[t], A.thi[t], A.cut2);
         if (far) pairs_far += valid ? cnt : 0;
         else pairs_near += valid ? cnt : 0;
-        const float4 ch = A.tchi[t], cl = A.tclo[t];
+        const float4 ch = s_dref[b][0], cl = s_dref[b][1];
         const float cc[3] = {ch.x, ch.y, ch.z}, cc2[3] = {cl.x, cl.y, cl.z};
         float qh[3], ql[3];
 #pragma unroll
@@ -1182,7 +1213,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                 const float4 y = SIGX ? make_float4(y0.x, y0.y, y0.z, ta_h) : y0;
                 const float4 yl = SIGX ? make_float4(yl0.x, yl0.y, yl0.z, ta_l) : yl0;
                 float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
-                ff_pair(y, n, yl, nl, qh, ql, far, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
+                ff_pair<true>(y, n, yl, nl, qh, ql, far, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
                 float sph, tph;
                 two_sum(cph, qh_, sph, tph);
                 cph = sph;
@@ -1350,7 +1381,7 @@ namespace {
 // Piecewise polynomial table of H: interval k covers w in [k, k+1)/kHTabPerUnit,
 // p(t) = sum_j c_j t^j with t = w - centre, interpolating H at 7 Chebyshev
 // points (h_interval_fit).
-// Layout per interval: {c0h, c0l, c1h, c1l}, {c2h, c2l, c3, c4}, {c5, c6, 0, 0}.
+// Layout per interval: {c0h, c0l, c1h, c1l}, {c2h, c2l, c3h, c3l}, {c4h, c4l, c5, c6}.
 void build_h_table(float4* out)
 {
     for (int k = 0; k < kHTabN; k++) {
@@ -1359,8 +1390,8 @@ void build_h_table(float4* out)
         auto hi = [](long double v) { return (float)v; };
         auto lo = [](long double v) { return (float)(v - (long double)(float)v); };
         out[3 * k + 0] = make_float4(hi(cf[0]), lo(cf[0]), hi(cf[1]), lo(cf[1]));
-        out[3 * k + 1] = make_float4(hi(cf[2]), lo(cf[2]), (float)cf[3], (float)cf[4]);
-        out[3 * k + 2] = make_float4((float)cf[5], (float)cf[6], 0.0f, 0.0f);
+        out[3 * k + 1] = make_float4(hi(cf[2]), lo(cf[2]), hi(cf[3]), lo(cf[3]));
+        out[3 * k + 2] = make_float4(hi(cf[4]), lo(cf[4]), (float)cf[5], (float)cf[6]);
     }
 }
 

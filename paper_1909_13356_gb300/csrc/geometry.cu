@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <type_traits>
+
 #include "lsm_internal.cuh"
 
 namespace lsm {
@@ -219,10 +221,71 @@ __global__ void k_gather_sources(const double4_32a* __restrict__ pin, const doub
     nout[i] = nin[k];
 }
 
+// Segments of the Morton-ordered sources: a new one starts where two
+// consecutive sources lie farther apart than kSegJump times the larger of
+// their sigmas.  Tiles never straddle a segment boundary, so a tile does not
+// span a jump of the curve (a tile of sources from two far parts of the
+// surface would be near too many targets, and its sources' float-pair
+// offsets from the tile's centre would lose absolute precision).
+constexpr double kSegJump = 8.0;
+__global__ void k_seg_flags(const double4_32a* __restrict__ p, int n, uint32_t* __restrict__ flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t f = 1;
+    if (i > 0) {
+        const double4_32a a = p[i], b = p[i - 1];
+        const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        // a = 1/(sqrt2 sigma): the larger sigma has the smaller a
+        const double s = 1.0 / (1.41421356237309505 * fmin(a.w, b.w));
+        f = dx * dx + dy * dy + dz * dz > kSegJump * kSegJump * s * s ? 1u : 0u;
+    }
+    flags[i] = f;
+}
+// First source of each segment (sid: exclusive scan of the flags).
+__global__ void k_seg_starts(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ sid, int n,
+                             uint32_t* __restrict__ starts)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flags[i]) starts[sid[i]] = (uint32_t)i;
+}
+// Tiles of each segment.
+__global__ void k_seg_tiles(const uint32_t* __restrict__ starts, int nseg, int n, uint32_t* __restrict__ ntile)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const uint32_t len = (s + 1 < nseg ? starts[s + 1] : (uint32_t)n) - starts[s];
+    ntile[s] = (len + kTile - 1) / kTile;
+}
+// Each source to its slot: tile tbase[segment] + local / kTile, slot local %
+// kTile; the first source of a tile writes the tile's count.
+__global__ void k_seg_scatter(const double4_32a* __restrict__ pin, const double4_32a* __restrict__ nin,
+                              const uint32_t* __restrict__ flags, const uint32_t* __restrict__ sid,
+                              const uint32_t* __restrict__ starts, const uint32_t* __restrict__ tbase, int nseg,
+                              int n, double4_32a* __restrict__ pout, double4_32a* __restrict__ nout,
+                              int* __restrict__ tcnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int seg = (int)(sid[i] + flags[i]) - 1;
+    const uint32_t local = (uint32_t)i - starts[seg];
+    const uint32_t tile = tbase[seg] + local / kTile, slot = local % kTile;
+    const int64_t dst = (int64_t)tile * kTile + slot;
+    pout[dst] = pin[i];
+    nout[dst] = nin[i];
+    if (slot == 0) {
+        const uint32_t len = (seg + 1 < nseg ? starts[seg + 1] : (uint32_t)n) - starts[seg];
+        tcnt[tile] = (int)min((uint32_t)kTile, len - local);
+    }
+}
+
 // One block per tile: bounding box (outward-rounded to FP32), sigma_max,
 // centre (split in two floats) and the FP32 tile-local copies of its nodes.
+// Slots past the tile's count become padding: a copy of the tile's first
+// node with zero weight (every kernel stops at the count; the tree's P2M and
+// node frames read whole tiles, where zero weight adds nothing).
 __global__ void __launch_bounds__(kTile) k_tile_meta(
-    const double4_32a* __restrict__ pos, const double4_32a* __restrict__ nw, int ns,
+    double4_32a* __restrict__ pos, double4_32a* __restrict__ nw, const int* __restrict__ tcnt,
     float4* __restrict__ s32p, float4* __restrict__ s32n, float4* __restrict__ s32l,
     float4* __restrict__ s32nl, float4* __restrict__ tlo,
     float4* __restrict__ thi, float4* __restrict__ tchi, float4* __restrict__ tclo)
@@ -230,7 +293,8 @@ __global__ void __launch_bounds__(kTile) k_tile_meta(
     __shared__ double red[7][kTile / 32];
     const int t = blockIdx.x;
     const int i = t * kTile + threadIdx.x;
-    const bool ok = i < ns;
+    const int tc = tcnt[t];
+    const bool ok = (int)threadIdx.x < tc;
     double4_32a p = ok ? pos[i] : make_double4_32a(0, 0, 0, 0);
     double lo[3], hi[3], sg;
     if (ok) {
@@ -269,21 +333,25 @@ __global__ void __launch_bounds__(kTile) k_tile_meta(
         }
     }
     for (int k = 0; k < kTile / 32; k++) S = fmax(S, red[6][k]);
+    // the centre is the float pair (ch, cl) itself, exactly: sources are
+    // stored relative to it and the kernels rebuild it from the two floats
+    // (a centre off by the pair's rounding, ~2^-48 |C|, shifts every source
+    // of the tile alike, ~1e-13 of Phi through grad Phi ~ 1/sigma)
     double C[3];
-    float ch[3];
+    float ch[3], cl[3];
     for (int c = 0; c < 3; c++) {
-        C[c] = 0.5 * (L[c] + Hh[c]);
-        ch[c] = __double2float_rn(C[c]);
+        const double mid = 0.5 * (L[c] + Hh[c]);
+        ch[c] = __double2float_rn(mid);
+        cl[c] = __double2float_rn(mid - (double)ch[c]);
+        C[c] = (double)ch[c] + (double)cl[c];
     }
     if (threadIdx.x == 0) {
         tlo[t] = make_float4(__double2float_rd(L[0]), __double2float_rd(L[1]), __double2float_rd(L[2]),
                              __double2float_ru(S));
-        const int cnt = min(kTile, ns - t * kTile);
         thi[t] = make_float4(__double2float_ru(Hh[0]), __double2float_ru(Hh[1]), __double2float_ru(Hh[2]),
-                             (float)cnt);
+                             (float)tc);
         tchi[t] = make_float4(ch[0], ch[1], ch[2], 0.0f);
-        tclo[t] = make_float4(__double2float_rn(C[0] - (double)ch[0]), __double2float_rn(C[1] - (double)ch[1]),
-                              __double2float_rn(C[2] - (double)ch[2]), 0.0f);
+        tclo[t] = make_float4(cl[0], cl[1], cl[2], 0.0f);
     }
     if (ok) {
         const double4_32a q = nw[i];
@@ -297,6 +365,19 @@ __global__ void __launch_bounds__(kTile) k_tile_meta(
         s32n[i] = make_float4(nx, ny, nz, __double2float_rn(q.w));
         s32nl[i] = make_float4(__double2float_rn(q.x - (double)nx), __double2float_rn(q.y - (double)ny),
                                __double2float_rn(q.z - (double)nz), 0.0f);
+    } else {
+        // padding slot: the tile's first node with zero weight
+        const double4_32a f = pos[(int64_t)t * kTile];
+        pos[i] = f;
+        nw[i] = make_double4_32a(0, 0, 0, 0);
+        const double lx = f.x - C[0], ly = f.y - C[1], lz = f.z - C[2];
+        const float hx = __double2float_rn(lx), hy = __double2float_rn(ly), hz = __double2float_rn(lz);
+        const float ah = __double2float_rn(f.w);
+        s32p[i] = make_float4(hx, hy, hz, ah);
+        s32l[i] = make_float4(__double2float_rn(lx - (double)hx), __double2float_rn(ly - (double)hy),
+                              __double2float_rn(lz - (double)hz), __double2float_rn(f.w - (double)ah));
+        s32n[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s32nl[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
 
@@ -416,11 +497,65 @@ int build_mesh_device(Ctx* ctx, Mesh* me, const double* sigma_in_dev, const doub
     LSM_LAUNCHED(ctx);
     int rc = morton_order_points(ctx, reinterpret_cast<const double*>(p0), 4, ns, perm, st);
     if (rc != LSM_OK) return rc;
-    k_gather_sources<<<blocks_for(ns, 256), 256, 0, st>>>(p0, n0, perm, ns, me->s64_pos, me->s64_nw);
+    double4_32a *p1, *n1;
+    LSM_CUDA_TRY(ctx, s.get(&p1, ns));
+    LSM_CUDA_TRY(ctx, s.get(&n1, ns));
+    k_gather_sources<<<blocks_for(ns, 256), 256, 0, st>>>(p0, n0, perm, ns, p1, n1);
     LSM_LAUNCHED(ctx);
-    k_tile_meta<<<(unsigned)me->ntiles, kTile, 0, st>>>(me->s64_pos, me->s64_nw, ns, me->s32_pos,
-                                                        me->s32_nw, me->s32_lo, me->s32_nwlo, me->tile_lo, me->tile_hi,
-                                                        me->tile_chi, me->tile_clo);
+
+    // segments at jumps of the Morton curve, then tiles within segments
+    uint32_t *flags, *sid, *cnt2;
+    LSM_CUDA_TRY(ctx, s.get(&flags, ns));
+    LSM_CUDA_TRY(ctx, s.get(&sid, ns));
+    LSM_CUDA_TRY(ctx, s.get(&cnt2, 2));
+    k_seg_flags<<<blocks_for(ns, 256), 256, 0, st>>>(p1, ns, flags);
+    LSM_LAUNCHED(ctx);
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(sid, flags, sizeof(uint32_t) * ns, cudaMemcpyDeviceToDevice, st));
+    rc = scan_exclusive(ctx, sid, ns, cnt2, st);
+    if (rc != LSM_OK) return rc;
+    uint32_t nseg = 0;
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(&nseg, cnt2, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    uint32_t *starts, *tbase;
+    LSM_CUDA_TRY(ctx, s.get(&starts, nseg));
+    LSM_CUDA_TRY(ctx, s.get(&tbase, nseg));
+    k_seg_starts<<<blocks_for(ns, 256), 256, 0, st>>>(flags, sid, ns, starts);
+    LSM_LAUNCHED(ctx);
+    k_seg_tiles<<<blocks_for(nseg, 256), 256, 0, st>>>(starts, (int)nseg, ns, tbase);
+    LSM_LAUNCHED(ctx);
+    rc = scan_exclusive(ctx, tbase, nseg, cnt2 + 1, st);
+    if (rc != LSM_OK) return rc;
+    uint32_t ntiles = 0;
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(&ntiles, cnt2 + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if ((int64_t)ntiles * kTile >= ((int64_t)1 << 31)) {
+        ctx->err = "mesh_upload: too many source tiles";
+        return LSM_E_INVALID_ARG;
+    }
+    me->ntiles = ntiles;
+    const size_t nsl = (size_t)ntiles * kTile, ntl = ntiles;
+    auto alloc = [&](auto** p, size_t count) -> bool {
+        using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
+        if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) return false;
+        me->bytes += count * sizeof(T);
+        return true;
+    };
+    if (!alloc(&me->s64_pos, nsl) || !alloc(&me->s64_nw, nsl) || !alloc(&me->s32_pos, nsl) ||
+        !alloc(&me->s32_nw, nsl) || !alloc(&me->s32_lo, nsl) || !alloc(&me->s32_nwlo, nsl) ||
+        !alloc(&me->tile_lo, ntl) || !alloc(&me->tile_hi, ntl) || !alloc(&me->tile_chi, ntl) ||
+        !alloc(&me->tile_clo, ntl)) {
+        cudaGetLastError();
+        ctx->err = "mesh_upload: out of device memory";
+        return LSM_E_OOM;
+    }
+    int* tcnt;
+    LSM_CUDA_TRY(ctx, s.get(&tcnt, ntl));
+    k_seg_scatter<<<blocks_for(ns, 256), 256, 0, st>>>(p1, n1, flags, sid, starts, tbase, (int)nseg, ns,
+                                                      me->s64_pos, me->s64_nw, tcnt);
+    LSM_LAUNCHED(ctx);
+    k_tile_meta<<<(unsigned)ntiles, kTile, 0, st>>>(me->s64_pos, me->s64_nw, tcnt, me->s32_pos, me->s32_nw,
+                                                    me->s32_lo, me->s32_nwlo, me->tile_lo, me->tile_hi,
+                                                    me->tile_chi, me->tile_clo);
     LSM_LAUNCHED(ctx);
     LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     return LSM_OK;

@@ -293,7 +293,7 @@ __device__ __forceinline__ float cheb_point(int k, int degree)
 struct P2MArgs {
     const double4_32a* pos;   // (x, y, z, a)
     const double4_32a* nw;    // (nw / 4 pi, 0)
-    int64_t ns;
+    int64_t ns;               // source slots (tiles x kTile)
     const NodeFrame* fr;      // each node's oriented box
     const int4* ninfo;
     const int4* items;        // node, first tile, end tile, partial offset (in proxies) or -1
@@ -840,7 +840,8 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     }
     std::vector<NodeFrame> hfr(T->nnodes);
     if (grid != 2 && n_inner > 0) {
-        k_node_frames<<<(unsigned)n_inner, kFrameThreads, 0, st>>>(me->s64_pos, me->ns, T->node_info, T->lev_off[1],
+        k_node_frames<<<(unsigned)n_inner, kFrameThreads, 0, st>>>(me->s64_pos, me->ntiles * kTile, T->node_info,
+                                                                  T->lev_off[1],
                                                                   d_fr);
         if (cudaGetLastError() != cudaSuccess) return fail(LSM_E_CUDA);
         ctx->launches++;
@@ -886,9 +887,9 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     for (int l = 1; l <= T->top; l++) {
         for (int64_t node = T->lev_off[l]; node < T->lev_off[l + 1]; node++) {
             int4& f = hinfo[node];
-            const NodeFrame& F = hfr[node];
+            NodeFrame& F = hfr[node];
             const int64_t s0 = (int64_t)f.x * kTile;
-            const int64_t s1 = std::min<int64_t>(me->ns, (int64_t)(f.x + f.y) * kTile);
+            const int64_t s1 = (int64_t)(f.x + f.y) * kTile;   // slots, padding included
             // the largest ladder degree whose grid the node can carry: sources
             // >= 1.5 x proxies (grid 2: >= 2 x)
             int4 gn = make_int4(1, 1, 1, 0);
@@ -906,6 +907,13 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
             }
             if (np == 0) continue;
             hgrid[node] = gn;
+            // the frame's centre becomes its float pair exactly: the proxies
+            // are placed relative to it and the kernels rebuild it from the
+            // two floats of the proxy tiles
+            for (int a = 0; a < 3; a++) {
+                const float h = (float)F.c[a];
+                F.c[a] = (double)h + (double)(float)(F.c[a] - (double)h);
+            }
             // the opening radius
             const double r = std::sqrt(F.h[0] * F.h[0] + F.h[1] * F.h[1] + F.h[2] * F.h[2]);
             const double hmax = std::max(F.h[0], std::max(F.h[1], F.h[2]));
@@ -945,7 +953,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         }
     }
     if (cudaMemcpyAsync(T->node_acc, hacc.data(), sizeof(float4) * T->nnodes, cudaMemcpyHostToDevice, st) ||
-        (grid == 2 && cudaMemcpyAsync(d_fr, hfr.data(), sizeof(NodeFrame) * T->nnodes, cudaMemcpyHostToDevice, st))) {
+        cudaMemcpyAsync(d_fr, hfr.data(), sizeof(NodeFrame) * T->nnodes, cudaMemcpyHostToDevice, st)) {
         ctx->err = "tree: copy failed";
         return fail(LSM_E_CUDA);
     }
@@ -997,7 +1005,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         P2MArgs P;
         P.pos = me->s64_pos;
         P.nw = me->s64_nw;
-        P.ns = me->ns;
+        P.ns = me->ntiles * kTile;   // slots: padding has zero weight
         P.fr = d_fr;
         P.ninfo = T->node_info;
         P.items = d_items;

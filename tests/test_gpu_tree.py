@@ -114,8 +114,9 @@ def test_tree_deterministic_and_reused(lsm, torus_case):
 
 
 def test_cube_flat_faces_tree(lsm, oracle_mod):
-    """Cube faces are planar, so node boxes have axes of zero extent (one
-    proxy point on such an axis).  Cube [-1,1]^3, 16 x 16 squares per face
+    """Cube faces are planar: oriented node boxes of one face have a zero
+    extent across it (raised to 1e-9 of the radius, two points).  Cube
+    [-1,1]^3, 16 x 16 squares per face
     (3,072 triangles, 49,152 nodes), sigma = 0.02, 50,000 targets uniform in
     [-1.5,1.5]^3."""
     m = synth.cube(1.0, 16)
@@ -130,8 +131,9 @@ def test_cube_flat_faces_tree(lsm, oracle_mod):
     st = ctx.read_stats(reset=True)
     assert np.abs(phi - phi_o).max() <= TOL32
     assert np.abs(grad - grad_o).max() <= TOL32 / m.sigma.min()
-    # volume targets make wide blocks: fewer nodes open, but proxies act
-    assert st["pairs_near"] + st["pairs_far"] < 0.9 * len(y) * len(x)
+    # volume targets make wide blocks that few nodes may act on, but proxies
+    # act (fewer pairs than the direct sum)
+    assert st["pairs_near"] + st["pairs_far"] < len(y) * len(x)
 
 
 def test_ragged_target_counts_tree(lsm, torus_case):
