@@ -394,16 +394,22 @@ void or_solve_charts(int64_t ns, const double* y, const double* nw, const double
                 or_pair(y + 3*s, nw + 3*s, sig[s], x, &p, g);
             double res = p - 0.5;
             if (!isfinite(res)) { st = OR_ST_NONFINITE; it++; break; }
-            if (fabs(res) < tol) { st = OR_ST_CONVERGED; it++; break; }
+            const int done = fabs(res) < tol;
             double d = dot3(H, g);
-            if (!isfinite(d)) { st = OR_ST_NONFINITE; it++; break; }
-            if (d == 0.0) { st = OR_ST_ZERODERIV; it++; break; }
+            if (!isfinite(d) || d == 0.0) {
+                st = done ? OR_ST_CONVERGED : (isfinite(d) ? OR_ST_ZERODERIV : OR_ST_NONFINITE);
+                it++;
+                break;
+            }
+            /* the update of eq. newtoneq is applied before the stopping test
+               (Sec. 5), also on the sweep that meets the tolerance */
             double step = -res / d;
             double lim = 4.0 * sloc[i];
             if (step > lim) { step = lim; clamped = 1; }
             if (step < -lim) { step = -lim; clamped = 1; }
             h += step;
             dh = fabs(step);
+            if (done) { st = OR_ST_CONVERGED; it++; break; }
         }
         for (int c = 0; c < 3; c++) xout[3*i+c] = x0[3*i+c] + h * H[c];
         hout[i] = h;
@@ -627,16 +633,22 @@ void or_solve_charts_sigx(int64_t ns, const double* y, const double* nw, int64_t
             phi_grad_sigx_one(ns, y, nw, x, s, gs, &p, g);
             double res = p - 0.5;
             if (!isfinite(res)) { st = OR_ST_NONFINITE; it++; break; }
-            if (fabs(res) < tol) { st = OR_ST_CONVERGED; it++; break; }
+            const int done = fabs(res) < tol;
             double d = dot3(H, g);
-            if (!isfinite(d)) { st = OR_ST_NONFINITE; it++; break; }
-            if (d == 0.0) { st = OR_ST_ZERODERIV; it++; break; }
+            if (!isfinite(d) || d == 0.0) {
+                st = done ? OR_ST_CONVERGED : (isfinite(d) ? OR_ST_ZERODERIV : OR_ST_NONFINITE);
+                it++;
+                break;
+            }
+            /* the update of eq. newtoneq is applied before the stopping test
+               (Sec. 5), also on the sweep that meets the tolerance */
             double step = -res / d;
             double lim = 4.0 * sloc[i];
             if (step > lim) { step = lim; clamped = 1; }
             if (step < -lim) { step = -lim; clamped = 1; }
             h += step;
             dh = fabs(step);
+            if (done) { st = OR_ST_CONVERGED; it++; break; }
         }
         for (int k = 0; k < 3; k++) xout[3*i+k] = x0[3*i+k] + h * H[k];
         hout[i] = h;

@@ -99,18 +99,14 @@ __device__ __forceinline__ void newton_update_one(int i, int k, int64_t p, const
         S.st[i] = LSM_NODE_NONFINITE;
         return;
     }
-    if ((!mixed_eval || accept_mixed) && fabs(r) < tol) {
-        S.st[i] = LSM_NODE_CONVERGED;
-        return;
-    }
-    if (mixed_eval && !accept_mixed && fabs(r) < sw) S.mode[i] = 1;
+    // the tolerance is met on this evaluation; its update is still applied
+    // (eq. newtoneq: each update precedes the stopping test, Sec. 5), so the
+    // returned h lies closer to the root than the residual reported
+    const bool done = (!mixed_eval || accept_mixed) && fabs(r) < tol;
+    if (!done && mixed_eval && !accept_mixed && fabs(r) < sw) S.mode[i] = 1;
     const double d = S.hd[i] * R[p + k] + S.hd[S.n + i] * R[2 * p + k] + S.hd[2 * S.n + i] * R[3 * p + k];
-    if (!isfinite(d)) {
-        S.st[i] = LSM_NODE_NONFINITE;
-        return;
-    }
-    if (d == 0.0) {
-        S.st[i] = LSM_NODE_ZERODERIV;
+    if (!isfinite(d) || d == 0.0) {
+        S.st[i] = done ? LSM_NODE_CONVERGED : (isfinite(d) ? LSM_NODE_ZERODERIV : LSM_NODE_NONFINITE);
         return;
     }
     double step = -r / d;
@@ -121,7 +117,8 @@ __device__ __forceinline__ void newton_update_one(int i, int k, int64_t p, const
     }
     S.h[i] += step;
     S.dh[i] = fabs(step);
-    if (it >= max_iter) S.st[i] = LSM_NODE_MAXITER;
+    if (done) S.st[i] = LSM_NODE_CONVERGED;
+    else if (it >= max_iter) S.st[i] = LSM_NODE_MAXITER;
 }
 
 __global__ void k_newton_update(const int32_t* __restrict__ list, int n, const double* __restrict__ R,

@@ -2,7 +2,8 @@
 
 Graded torus, 30,720 triangles, Duffy 6x6 sources (1,105,920 nodes), 1e6
 targets within 3 sigma, order-8 chart nodes (1,105,920) to |Phi - 1/2| <
-1e-12: sampled outputs against the FP64 oracle computed one by one.
+1e-12: seeded samples of 10,000 targets and 10,000 chart nodes against the
+FP64 oracle computed one by one.
 Bumped icosphere, level 8 (1,310,720 triangles, 20,971,520 nodes): sampled
 outputs of a 1e5-target evaluation against the oracle.
 """
@@ -37,7 +38,7 @@ def test_torus_full_evaluation_sampled(lsm, oracle_mod, torus):
     w, ctx, mesh, (y, nw, sg) = torus
     m = w["mesh"]
     x = torch.from_numpy(w["targets"]).cuda()
-    sel = np.random.default_rng(7).choice(len(w["targets"]), 64, replace=False)
+    sel = np.random.default_rng(7).choice(len(w["targets"]), 10_000, replace=False)
     po, go = oracle_mod.phi_grad(y, nw, sg, w["targets"][sel])
     for prec, tol, gtol in ((lsm.MIXED, 1e-7, 1e-7), (lsm.FF, 1e-12, 1e-7)):
         phi, grad = mesh.eval_phi_grad(x, prec)
@@ -98,7 +99,7 @@ def test_torus_full_chart_solve_sampled(lsm, oracle_mod, torus):
     x, h, st, stats = mesh.solve_charts(order=8, tol=1e-12, precision=lsm.MIXED, device_out=True)
     assert stats.n_nodes == 1_105_920 and stats.n_failed == 0
     assert bool((st & 255 == 0).all())
-    sel = np.random.default_rng(8).choice(stats.n_nodes, 96, replace=False)
+    sel = np.random.default_rng(8).choice(stats.n_nodes, 10_000, replace=False)
     po, _ = oracle_mod.phi_grad(y, nw, sg, x.cpu().numpy()[sel])
     assert np.abs(po - 0.5).max() < 1e-12
 
