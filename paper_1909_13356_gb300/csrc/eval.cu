@@ -36,6 +36,8 @@
 #include <mutex>
 #include <vector>
 
+#include <type_traits>
+
 #include "lsm_internal.cuh"
 
 #ifndef LSM_RSQRT_REFINE
@@ -1206,37 +1208,46 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             float g[3] = {0.0f, 0.0f, 0.0f}, gn[3] = {0.0f, 0.0f, 0.0f};
             float cph = 0.0f, cpl = 0.0f;   // this chunk's Phi, float-float
             float cd = 0.0f;                // sigma(x) mode: sum of (nw . r) e^{-w}
+            // the pair loop, compiled once for far tiles and once for near
+            // ones (far is uniform over the tile)
+            auto pairs = [&](auto far_c) {
+                constexpr bool FAR = decltype(far_c)::value;
 #pragma unroll 2
-            for (int s = c0; s < c1; s++) {
-                const float4 y0 = sp[s], n = sn[s], yl0 = sl[s], nl = snl[s];
-                // the pair's a: the source's, or the target's in sigma(x) mode
-                const float4 y = SIGX ? make_float4(y0.x, y0.y, y0.z, ta_h) : y0;
-                const float4 yl = SIGX ? make_float4(yl0.x, yl0.y, yl0.z, ta_l) : yl0;
-                float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
-                ff_pair<true>(y, n, yl, nl, qh, ql, far, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
-                float sph, tph;
-                two_sum(cph, qh_, sph, tph);
-                cph = sph;
-                cpl += tph + ql_;
-                // grad from the high parts (FP32)
-                if (far) {
-                    const float ri = r0;
-                    const float ri2 = ri * ri;
-                    const float ri3 = ri2 * ri;
-                    const float tq = 3.0f * dh * ri3 * ri2;
-                    g[0] = fmaf(tq, dxh, fmaf(-n.x, ri3, g[0]));
-                    g[1] = fmaf(tq, dyh, fmaf(-n.y, ri3, g[1]));
-                    g[2] = fmaf(tq, dzh, fmaf(-n.z, ri3, g[2]));
-                } else {
-                    float fH, FK;
-                    radial_tab32(rh, y.w, s_htab, fH, FK);
-                    const float tq = dh * FK;
-                    two_sum_acc(g[0], gn[0], -fmaf(n.x, fH, tq * dxh));
-                    two_sum_acc(g[1], gn[1], -fmaf(n.y, fH, tq * dyh));
-                    two_sum_acc(g[2], gn[2], -fmaf(n.z, fH, tq * dzh));
-                    if constexpr (SIGX) cd = fmaf(dh, expf(-rh * y.w * y.w), cd);
+                for (int s = c0; s < c1; s++) {
+                    const float4 y0 = sp[s], n = sn[s], yl0 = sl[s], nl = snl[s];
+                    // the pair's a: the source's, or the target's in sigma(x) mode
+                    const float4 y = SIGX ? make_float4(y0.x, y0.y, y0.z, ta_h) : y0;
+                    const float4 yl = SIGX ? make_float4(yl0.x, yl0.y, yl0.z, ta_l) : yl0;
+                    float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
+                    ff_pair<true>(y, n, yl, nl, qh, ql, FAR, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
+                    float sph, tph;
+                    two_sum(cph, qh_, sph, tph);
+                    cph = sph;
+                    cpl += tph + ql_;
+                    // grad from the high parts (FP32)
+                    if constexpr (FAR) {
+                        const float ri = r0;
+                        const float ri2 = ri * ri;
+                        const float ri3 = ri2 * ri;
+                        const float tq = 3.0f * dh * ri3 * ri2;
+                        g[0] = fmaf(tq, dxh, fmaf(-n.x, ri3, g[0]));
+                        g[1] = fmaf(tq, dyh, fmaf(-n.y, ri3, g[1]));
+                        g[2] = fmaf(tq, dzh, fmaf(-n.z, ri3, g[2]));
+                    } else {
+                        float fH, FK;
+                        radial_tab32(rh, y.w, s_htab, fH, FK);
+                        const float tq = dh * FK;
+                        two_sum_acc(g[0], gn[0], -fmaf(n.x, fH, tq * dxh));
+                        two_sum_acc(g[1], gn[1], -fmaf(n.y, fH, tq * dyh));
+                        two_sum_acc(g[2], gn[2], -fmaf(n.z, fH, tq * dzh));
+                        if constexpr (SIGX) cd = fmaf(dh, expf(-rh * y.w * y.w), cd);
+                    }
                 }
-            }
+            };
+            if (far)
+                pairs(std::true_type{});
+            else
+                pairs(std::false_type{});
             if constexpr (SIGX) {
                 if (!far) {
                     two_sum_acc(dsum_h, dsum_l, cd);
