@@ -150,7 +150,8 @@ typedef struct {
     int64_t n_vertices;
     int64_t n_triangles;
     int64_t n_sources;        /* n_triangles * nodes per triangle */
-    int64_t n_tiles;          /* source tiles of the tiled kernels */
+    int64_t n_tiles;          /* source tiles of the tiled kernels: runs of at most 128
+                                 Morton-ordered nodes, cut where the curve jumps */
     int64_t device_bytes;     /* device memory held by the mesh */
     double sigma_min, sigma_max;
 } lsm_mesh_info;
