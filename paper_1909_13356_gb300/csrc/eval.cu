@@ -1212,7 +1212,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             // ones (far is uniform over the tile)
             auto pairs = [&](auto far_c) {
                 constexpr bool FAR = decltype(far_c)::value;
-#pragma unroll 2
+#pragma unroll 4
                 for (int s = c0; s < c1; s++) {
                     const float4 y0 = sp[s], n = sn[s], yl0 = sl[s], nl = snl[s];
                     // the pair's a: the source's, or the target's in sigma(x) mode
