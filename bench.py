@@ -384,7 +384,7 @@ def bench_icosphere(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
         "config": {"workload": w["name"], "triangles": m.m, "sources": mesh.info()["n_sources"],
-                   "targets": n, "precision": "mixed",
+                   "targets": n, "precision": "mixed", "cutoff_sigma": {"mixed": 6.5},
                    "far_field": ("autotuned" if tune else
                                  f"treecode (degree {args.tree_degree or 'default'}, theta {args.tree_theta or 'default'})"),
                    "upload_s": t_up, "tree_build_s": t_tree, "autotune_s": t_tune, "autotune": tune,
@@ -686,6 +686,9 @@ def main():
             "config": {"workload": w["name"], "triangles": m.m, "sources": info["n_sources"],
                        "targets": nt, "chart_order": args.order, "chart_nodes": st.n_nodes if st else 0,
                        "newton_tol": args.tol, "precision": args.precision, "autotune": tune,
+                       # the library's default near-field cutoffs (lsm_options), unchanged here: the
+                       # mixed one meets erfc(c/sqrt2) + c sqrt(2/pi) e^(-c^2/2) <= 1e-8 (3.6e-9 at 6.5)
+                       "cutoff_sigma": {"fp64_and_float_float": 8.0, "mixed": 6.5},
                        "sigma": ("sigma(x), eq. sigma2: lambda 2.5, sigma0 = max D / sqrt(2 ln 2) = "
                                  f"{mesh.sigma0:.5g}" if args.sigma_x else "per triangle, 0.5 sqrt(2 area)"),
                        "parallelism": (f"{world} ranks, one independent torus (own seed) each"
