@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -31,9 +32,6 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 SMSPs x 32)
-NUM_SMS = 152
-SM_MAX_MHZ = 2070.0
 FLOPS_FAR_PAIR = 31              # Laplace double layer, Phi + grad (1 rsqrt not counted)
 FLOPS_NEAR_PAIR = 60             # full smoothed kernel, Phi + grad (erfc, exp, rsqrt not counted)
 
@@ -72,6 +70,12 @@ def parse():
                     help="skip the untimed Gauss flux and Gauss-Bonnet checks after the step (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--fp64-check", type=int, default=0,
+                    help="icosphere: also compare with the FP64 direct sum on this many targets")
+    ap.add_argument("--no-paths", action="store_true",
+                    help="skip the float-float and FP64 path legs after the timed region")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several ranks: an independent torus per rank instead of one problem split")
     return ap.parse_args()
 
 
@@ -85,9 +89,10 @@ def _duffy_weights(n: int) -> np.ndarray:
 
 
 def rank_seed(rank: int) -> int:
-    """Seed of the graded torus and its targets on one rank.  Every rank
-    solves its own independent problem (weak scaling, no data-path
-    collective); rank 0's is the single-GPU workload."""
+    """Seed of the graded torus and its targets on one rank with --replicas:
+    every rank then solves its own independent problem (weak scaling, no
+    data-path collective); rank 0's is the single-GPU workload.  Without
+    --replicas all ranks share rank 0's problem, split into Morton ranges."""
     return 2 + 1009 * rank
 
 
@@ -127,11 +132,11 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"lsm_clocks{index}_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
@@ -141,6 +146,10 @@ class ClockSampler:
 
     def stop(self):
         if self.p is None:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
             return None
         self.p.terminate()
         try:
@@ -162,15 +171,22 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, seconds: float, rule_n: int, sigma_x: bool = False):
+def cpu_baseline(w, seconds: float, rule_n: int, sigma_x: bool = False, check=None):
     """The FP64 oracle (direct sum, all pairs) on a target sample, all host
-    cores; with sigma_x, sigma(x) and its gradient are part of each evaluation."""
+    cores; with sigma_x, sigma(x) and its gradient are part of each evaluation.
+    `check`: further targets at which the oracle's Phi is returned too (the
+    precision paths' errors are measured there).  Returns (baseline, Phi at
+    check or None)."""
     import oracle
     m = w["mesh"]
     if sigma_x:
@@ -180,12 +196,12 @@ def cpu_baseline(w, seconds: float, rule_n: int, sigma_x: bool = False):
 
         def run(xx):
             sg, gs = oracle.sigma_x(c, sj, s0, xx)
-            oracle.phi_grad_sigx(y, nw, xx, sg, gs)
+            return oracle.phi_grad_sigx(y, nw, xx, sg, gs)
     else:
         y, nw, sg = oracle.sources(m.verts, m.tris, m.sigma, rule_n, 0)
 
         def run(xx):
-            oracle.phi_grad(y, nw, sg, xx)
+            return oracle.phi_grad(y, nw, sg, xx)
     x = w["targets"]
     ncal = 8 * (os.cpu_count() or 1)
     t0 = time.perf_counter()
@@ -195,9 +211,10 @@ def cpu_baseline(w, seconds: float, rule_n: int, sigma_x: bool = False):
     t0 = time.perf_counter()
     run(x[:n])
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} of {len(x)} targets, full FP64 direct sum over {len(y)} source nodes "
-                      f"({dt:.1f} s)"}
+    phi_check = run(np.ascontiguousarray(check))[0] if check is not None and len(check) else None
+    return ({"value": n / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"{n} of {len(x)} targets, full FP64 direct sum over {len(y)} source nodes "
+                       f"({dt:.1f} s)"}, phi_check)
 
 
 def run_reference(args, rank, world):
@@ -375,7 +392,16 @@ def bench_icosphere(args):
     pff, gff = mesh.eval_phi_grad(x[:nref], lsm.FF)
     err_ff = float((phi[:nref] - pff).abs().max())
     gerr_ff = float((grad[:nref] - gff).abs().max())
-    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peaks = ctx.measure_peaks()
+    fp32_peak = _peak_fp32(peaks)
+    # the mixed path against the FP64 direct sum (the reference path) on a
+    # coherent sample of the targets (--fp64-check targets; untimed)
+    err_fp64 = None
+    if args.fp64_check:
+        sel = torch.from_numpy(_coherent_sample(w["targets"], 4, max(256, args.fp64_check // 4))).cuda()
+        p64, g64 = mesh.eval_phi_grad(x[sel], lsm.FP64)
+        err_fp64 = {"targets": int(sel.shape[0]), "err_phi": float((phi[sel] - p64).abs().max()),
+                    "err_grad": float((grad[sel] - g64).abs().max())}
     ms_k = stats["kind_ms"][0]
     fl = stats["kind_pairs_far"][0] * FLOPS_FAR_PAIR + stats["kind_pairs_near"][0] * FLOPS_NEAR_PAIR
     ach = fl / (ms_k / 1e3) / 1e12 if ms_k > 0 else None
@@ -394,7 +420,9 @@ def bench_icosphere(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": ach / fp32_peak if ach else None, "traffic": None, "kernel": "k_eval_mixed",
-                     "share_of_step": ms_k / (ms * args.steps)},
+                     "share_of_step": ms_k / (ms * args.steps),
+                     "peak_source": "measured on this GPU by lsm_measure_peaks: max(FFMA, packed FFMA2)"},
+        "peaks": peaks, "err_mixed_vs_fp64_direct": err_fp64,
         "clocks": clocks,
         "err_mixed_vs_ff_1e5": err_ff, "grad_err_mixed_vs_ff_1e5": gerr_ff,
     }))
@@ -451,8 +479,9 @@ def bench_geometry(args):
     ms = a.elapsed_time(b) / args.steps
     ms_k = stats["kind_ms"][3]
     far, near = stats["kind_pairs_far"][3], stats["kind_pairs_near"][3]
-    p32 = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    p64 = p32 / 64.0
+    peaks = ctx.measure_peaks()
+    p32 = _peak_fp32(peaks)
+    p64 = peaks["dfma_tflops"]
     f32 = far * FLOPS_HESS_FAR / (ms_k / 1e3) / 1e12
     f64 = near * FLOPS_HESS_NEAR / (ms_k / 1e3) / 1e12
     cpu = None
@@ -469,7 +498,7 @@ def bench_geometry(args):
         "gpu_launches": (ctx.launch_count - l0) // max(1, args.steps),
         "roofline": {"bound": "alu", "kernel": "k_eval_hess", "achieved": f32 + f64, "unit": "TFLOP/s",
                      "peak": None, "frac": f32 / p32 + f64 / p64, "traffic": None,
-                     "frac_fp32_far": f32 / p32, "frac_fp64_near": f64 / p64,
+                     "frac_fp32_far": f32 / p32, "frac_fp64_near": f64 / p64, "peaks": peaks,
                      "note": "far pairs on the FP32 pipe, near pairs on the FP64 pipe: frac is the sum of the two "
                              "pipes' fractions",
                      "pairs_far": far, "pairs_near": near, "share_of_step": ms_k / (ms * args.steps)},
@@ -496,6 +525,50 @@ def cpu_baseline_hessian(w, seconds, rule_n, nodes):
             "sample": f"{k} of {len(nodes)} chart nodes, FP64 Phi, grad, Hessian by direct sums ({dt:.1f} s)"}
 
 
+def _peak_fp32(peaks):
+    return max(peaks["ffma_tflops"], peaks["ffma2_tflops"])
+
+
+def _kernel_rooflines(stats, peaks, step_ms_total, kinds=(0, 1, 2)):
+    """Rooflines of the pair kernels timed per launch by the library: counted
+    algorithmic flops (FLOPS_FAR_PAIR per far pair, FLOPS_NEAR_PAIR per near
+    pair) over the kernel's CUDA-event time, against the FP32 (mixed,
+    float-float) or FP64 (FP64 path) FMA throughput measured on this GPU by
+    lsm_measure_peaks; one special-function rsqrt per pair against the
+    measured rsqrt rate."""
+    names = ["k_eval_mixed", "k_eval_ff", "k_eval_fp64"]
+    kern = {}
+    for k in kinds:
+        ms_k = stats["kind_ms"][k]
+        if ms_k <= 0:
+            continue
+        far, near = stats["kind_pairs_far"][k], stats["kind_pairs_near"][k]
+        fl = far * FLOPS_FAR_PAIR + near * FLOPS_NEAR_PAIR
+        pk = _peak_fp32(peaks) if k < 2 else peaks["dfma_tflops"]
+        ach = fl / (ms_k / 1e3) / 1e12
+        kern[names[k]] = {
+            "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "traffic": None, "launches": stats["kind_launches"][k],
+            "avg_launch_ms": ms_k / max(1, stats["kind_launches"][k]),
+            "pairs_far": far, "pairs_near": near,
+            "share_of_step": ms_k / step_ms_total if step_ms_total else None,
+            "mufu_rsqrt_util": (far + near) / (ms_k / 1e3) / (peaks["rsqrt_gops"] * 1e9),
+            "peak_source": ("measured on this GPU by lsm_measure_peaks: max(FFMA, packed FFMA2) throughput"
+                            if k < 2 else "measured on this GPU by lsm_measure_peaks: DFMA throughput"),
+        }
+    return kern
+
+
+def _coherent_sample(points, n_chunks: int, chunk: int):
+    """Indices of n_chunks contiguous runs of `chunk` points, equally spaced in
+    the points' Morton order: spatially compact blocks, as the full set's."""
+    from paper_1909_13356_gb300 import shard
+    order = np.argsort(shard.morton_keys(points), kind="stable")
+    n = len(order)
+    starts = [int((n - chunk) * (k + 0.5) / n_chunks) // 256 * 256 for k in range(n_chunks)]
+    return np.concatenate([order[s0:s0 + chunk] for s0 in starts])
+
+
 def main():
     args = parse()
     if args.workload == "icosphere" and args.impl == "ours":
@@ -519,6 +592,7 @@ def main():
 
     import torch
     import paper_1909_13356_gb300 as lsm
+    from paper_1909_13356_gb300 import shard
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -529,16 +603,33 @@ def main():
     prec = {"mixed": lsm.MIXED, "fp64": lsm.FP64, "ff": lsm.FF}[args.precision]
     if prec == lsm.FF and not args.no_charts:
         raise SystemExit("--precision ff evaluates only (add --no-charts)")
+    # one problem split into Morton ranges across ranks (mesh replicated), or
+    # with --replicas an independent problem per rank
+    sharded = world > 1 and not args.replicas
 
-    w = workload(args, rank)
+    w = workload(args, rank if args.replicas else 0)
     m = w["mesh"]
     ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid)
+    # the pipes' measured throughput (roofline denominators), clocks sampled around the probe
+    pclk = ClockSampler(local)
+    pclk.start()
+    peaks = ctx.measure_peaks()
+    peaks["clocks"] = pclk.stop()
     if args.sigma_x:
         mesh = ctx.upload_sigma_x(m.verts, m.tris, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
     else:
         mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
     info = mesh.info()
-    x_dev = torch.from_numpy(w["targets"]).to(dev)
+    targets = w["targets"]
+    tri_all, uvw_all = lsm.refined_nodes(args.order, np.zeros(m.m, dtype=np.int32))
+    x0_all = shard.chart_node_positions(m.verts, m.tris, tri_all, uvw_all)
+    if sharded:
+        idx_t = shard.morton_ranges(targets, world)[rank]
+        idx_c = shard.morton_ranges(x0_all, world)[rank]
+        targets = targets[idx_t]
+        tri_d = torch.from_numpy(tri_all[idx_c]).to(dev)
+        uvw_d = torch.from_numpy(uvw_all[idx_c]).to(dev)
+    x_dev = torch.from_numpy(targets).to(dev)
     nt = x_dev.shape[0]
     # far field of the mixed sweeps chosen by the autotuner (untimed)
     tune = None
@@ -549,14 +640,27 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     last = {}
+    eval_ms = []
+
+    def solve():
+        if sharded:
+            return mesh.solve_charts_nodes(tri_d, uvw_d, tol=args.tol, precision=prec, device_out=True)
+        return mesh.solve_charts(order=args.order, tol=args.tol, precision=prec, device_out=True)
 
     def step():
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        ea.record()
         mesh.eval_phi_grad(x_dev, prec, phi=phi, grad=grad)
+        eb.record()
+        last["eval_events"] = (ea, eb)
         if args.no_charts:
             return nt, None
-        xc, hc, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=prec, device_out=True)
+        xc, hc, _, st = solve()
         last["x"], last["h"] = xc, hc
-        return nt + sum(st.active_per_iter), st
+        # full Phi + grad Phi evaluations: the near-only verification sweeps,
+        # which reuse the far part recorded by the sweep before, are not counted
+        return nt + st.evals_fp32 + st.evals_fp64 - st.evals_near_only, st
 
     def barrier():
         torch.cuda.synchronize()
@@ -584,6 +688,7 @@ def main():
         b.record()
         torch.cuda.synchronize()
         step_ms.append(a.elapsed_time(b))
+        eval_ms.append(last["eval_events"][0].elapsed_time(last["eval_events"][1]))
         total_units += units
     barrier()
     clocks = clk.stop()
@@ -593,59 +698,112 @@ def main():
     t_ms = sum(step_ms)
     t_ms, total_units = reduce_over_ranks(dist, t_ms, total_units, dev)
     value = total_units / (t_ms / 1e3)
-
-    # rooflines of the pair kernels, timed per launch by the library; the
-    # dominant one (largest device time in the timed region) is "roofline"
-    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    names = ["k_eval_mixed", "k_eval_ff", "k_eval_fp64"]
-    kern = {}
-    for k in range(3):
-        ms_k = stats["kind_ms"][k]
-        if ms_k <= 0:
-            continue
-        fl = stats["kind_pairs_far"][k] * FLOPS_FAR_PAIR + stats["kind_pairs_near"][k] * FLOPS_NEAR_PAIR
-        pk = fp32_peak if k < 2 else fp32_peak / 64.0
-        ach = fl / (ms_k / 1e3) / 1e12
-        kern[names[k]] = {
-            "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-            "traffic": None, "launches": stats["kind_launches"][k],
-            "avg_launch_ms": ms_k / max(1, stats["kind_launches"][k]),
-            "pairs_far": stats["kind_pairs_far"][k], "pairs_near": stats["kind_pairs_near"][k],
-            "share_of_step": ms_k / sum(step_ms) if step_ms else None,
-            "peak_source": ("FP32 FMA lanes: 152 SM x 128 x 2 flops x 2070 MHz" if k < 2 else
-                            "FP32 FMA peak / 64 (GB300 FP64 rate)"),
-        }
+    kern = _kernel_rooflines(stats, peaks, sum(step_ms))
     dom = max(kern, key=lambda n: kern[n]["avg_launch_ms"] * kern[n]["launches"]) if kern else None
     roofline = dict(kern[dom], kernel=dom) if dom else None
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end through the C ABI with pinned host buffers: the same number
+    # of steps as the device timing, after one warm-up step of the buffers
     e2e = None
-    if not args.no_e2e and rank == 0:
-        xh = torch.from_numpy(w["targets"]).pin_memory()
+    if not args.no_e2e:
+        xh = torch.from_numpy(targets).pin_memory()
         ph = torch.empty(nt, dtype=torch.float64).pin_memory()
         gh = torch.empty((nt, 3), dtype=torch.float64).pin_memory()
-        units = 0
-        e2e_steps = 1
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ncn = 0
-        for _ in range(e2e_steps):
+        if sharded:
+            tri_h, uvw_h = tri_all[idx_c], uvw_all[idx_c]
+
+        def e2e_step():
             mesh.eval_phi_grad(xh, prec, phi=ph, grad=gh)
-            units += nt
-            if not args.no_charts:
+            if args.no_charts:
+                return nt, 0
+            if sharded:
+                _, _, _, st = mesh.solve_charts_nodes(tri_h, uvw_h, tol=args.tol, precision=prec)
+            else:
                 _, _, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=prec)
-                units += sum(st.active_per_iter)
-                ncn = st.n_nodes
+            return nt + st.evals_fp32 + st.evals_fp64 - st.evals_near_only, st.n_nodes
+
+        e2e_step()
+        barrier()
+        units = 0
+        ncn = 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            u, ncn = e2e_step()
+            units += u
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": nt * 24,
-               "d2h_bytes_per_step": nt * 32 + ncn * (24 + 8 + 4), "steps": e2e_steps}
+        dt_ms = (time.perf_counter() - t0) * 1e3
+        dt_ms, units = reduce_over_ranks(dist, dt_ms, units, dev)
+        e2e = {"value": units / (dt_ms / 1e3), "unit": "evals/s", "h2d_bytes_per_step": nt * 24 +
+               (ncn * (4 + 24) if sharded else 0),
+               "d2h_bytes_per_step": nt * 32 + ncn * (24 + 8 + 4), "steps": args.steps}
+
+    # The same inputs on the three precision paths (untimed by the step, each
+    # with CUDA events): the float-float evaluation at every target (Phi to
+    # FP64 accuracy), the FP64 direct sum on a spatially coherent sample of
+    # the targets (its cost is linear in the targets: extrapolated), and the
+    # FP64 chart solve on a coherent sample of the chart nodes.
+    paths = None
+    fp64_kern = None
+    if not args.no_charts and not args.sigma_x and prec == lsm.MIXED and not args.no_paths:
+        def timed(fn):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            r = fn()
+            b.record()
+            torch.cuda.synchronize()
+            return r, a.elapsed_time(b)
+
+        (pff, gff), ms_ff = timed(lambda: mesh.eval_phi_grad(x_dev, lsm.FF))
+        sel = _coherent_sample(targets, 4, 4096)
+        xs = x_dev[torch.from_numpy(sel).to(dev)]
+        ctx.read_stats(reset=True)
+        ctx.set_profiling(True)
+        (p64, _), ms_64 = timed(lambda: mesh.eval_phi_grad(xs, lsm.FP64))
+        ctx.set_profiling(False)
+        fp64_kern = _kernel_rooflines(ctx.read_stats(reset=True), peaks, ms_64, kinds=(2,)).get("k_eval_fp64")
+        if sharded:
+            node_pts, tri_src, uvw_src = x0_all[idx_c], tri_all[idx_c], uvw_all[idx_c]
+        else:
+            node_pts, tri_src, uvw_src = x0_all, tri_all, uvw_all
+        csel = _coherent_sample(node_pts, 4, 4096)
+        (xc64, _, st64, s64), ms_s64 = timed(lambda: mesh.solve_charts_nodes(
+            tri_src[csel], uvw_src[csel], tol=args.tol, precision=lsm.FP64, device_out=True))
+        e_mx = nt / (statistics.median(eval_ms) / 1e3)
+        e_ff = nt / (ms_ff / 1e3)
+        e_64 = len(sel) / (ms_64 / 1e3)
+        nodes_mx = last_stats.n_converged / (statistics.median(step_ms) / 1e3 - statistics.median(eval_ms) / 1e3)
+        nodes_64 = s64.n_converged / (ms_s64 / 1e3)
+        if not sharded:
+            dx = float((xc64 - last["x"][torch.from_numpy(csel).to(dev)]).abs().max())
+        else:
+            dx = None
+        paths = {
+            "mixed": {"evals_per_s": e_mx, "targets": nt, "tol_phi": 1e-7,
+                      "ms": statistics.median(eval_ms)},
+            "float_float": {"evals_per_s": e_ff, "targets": nt, "tol_phi": 1e-12, "ms": ms_ff},
+            "fp64": {"evals_per_s": e_64, "targets_timed": len(sel), "extrapolated": True, "ms": ms_64,
+                     "sample": "4 runs of 4096 consecutive targets in Morton order, equally spaced; the "
+                               "direct sum's cost per target does not depend on the other targets"},
+            "speedup_float_float_vs_fp64": e_ff / e_64,
+            "speedup_mixed_vs_fp64": e_mx / e_64,
+            "chart_solve": {
+                "mixed_then_float_float_nodes_per_s": nodes_mx,
+                "fp64_nodes_per_s": nodes_64, "fp64_nodes_timed": len(csel), "fp64_extrapolated": True,
+                "fp64_sweeps": s64.iterations, "fp64_max_residual": s64.max_residual,
+                "mixed_max_residual": last_stats.max_residual,
+                "max_node_position_difference": dx, "tol": args.tol,
+                "speedup": nodes_mx / nodes_64,
+            },
+        }
+        last["err_check"] = (sel[::32], pff, p64)
 
     # Gauss flux error of the last step's charts about the tube's centre line
     # (untimed): grad Phi at the nodes from the float-float path, then the
     # frames and the flux (Sec. 5)
     eps0 = None
-    if "x" in last and not args.no_geometry:
+    if "x" in last and not args.no_geometry and not sharded:
         _, gc = mesh.eval_phi_grad(last["x"], lsm.FF)
         _, _, jac = mesh.chart_frames(args.order, last["h"], gc)
         eps0 = {"x0": [1.0, 0.0, 0.0], "value": mesh.gauss_flux(args.order, last["x"], gc, jac, (1.0, 0.0, 0.0)),
@@ -666,7 +824,19 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        cpu = cpu_baseline(w, args.cpu_seconds, w["rule"]["n"], args.sigma_x)
+        check = None
+        if "err_check" in last:
+            csel_t, pff, p64 = last["err_check"]
+            check = targets[csel_t]
+        cpu, phi_check = cpu_baseline(w, args.cpu_seconds, w["rule"]["n"], args.sigma_x, check)
+        if paths is not None and phi_check is not None:
+            # errors of the three paths against the oracle at the same targets
+            csel_t, pff, p64 = last["err_check"]
+            idx = torch.from_numpy(csel_t).to(dev)
+            paths["mixed"]["err_phi_vs_oracle"] = float(np.abs(phi[idx].cpu().numpy() - phi_check).max())
+            paths["float_float"]["err_phi_vs_oracle"] = float(np.abs(pff[idx].cpu().numpy() - phi_check).max())
+            paths["fp64"]["err_phi_vs_oracle"] = float(np.abs(p64[::32].cpu().numpy() - phi_check).max())
+            paths["err_sample"] = f"{len(csel_t)} targets (every 32nd of the FP64 sample), oracle FP64 direct sum"
 
     if rank == 0:
         st = last_stats
@@ -679,29 +849,38 @@ def main():
             "warmup": args.warmup,
             "ms_per_step": t_ms / args.steps,
             "higher_is_better": True,
-            "scaling": "weak",
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None,
             "dtype": {lsm.MIXED: "f32+ff", lsm.FF: "ff", lsm.FP64: "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": w["name"], "triangles": m.m, "sources": info["n_sources"],
-                       "targets": nt, "chart_order": args.order, "chart_nodes": st.n_nodes if st else 0,
+                       "targets": len(w["targets"]), "chart_order": args.order,
+                       "chart_nodes": len(tri_all) if not args.no_charts else 0,
                        "newton_tol": args.tol, "precision": args.precision, "autotune": tune,
                        # the library's default near-field cutoffs (lsm_options), unchanged here: the
                        # mixed one meets erfc(c/sqrt2) + c sqrt(2/pi) e^(-c^2/2) <= 1e-8 (3.6e-9 at 6.5)
                        "cutoff_sigma": {"fp64_and_float_float": 8.0, "mixed": 6.5},
                        "sigma": ("sigma(x), eq. sigma2: lambda 2.5, sigma0 = max D / sqrt(2 ln 2) = "
                                  f"{mesh.sigma0:.5g}" if args.sigma_x else "per triangle, 0.5 sqrt(2 area)"),
-                       "parallelism": (f"{world} ranks, one independent torus (own seed) each"
-                                       if world > 1 else "single GPU"),
+                       "parallelism": (f"{world} ranks, targets and chart nodes in Morton ranges, mesh replicated"
+                                       if sharded else
+                                       (f"{world} ranks, one independent torus (own seed) each"
+                                        if world > 1 else "single GPU")),
                        "l2": "flushed (256 MB write) before each timed step"},
-            "chart_nodes_per_s": st.n_converged / (t_ms / args.steps / 1e3) if st else None,
+            "units_per_step": ({"targets_mixed": nt, "newton_mixed": st.evals_fp32,
+                                "newton_float_float_full": st.evals_fp64 - st.evals_near_only,
+                                "newton_float_float_near_only_not_counted": st.evals_near_only}
+                               if st else {"targets": nt}),
+            "chart_nodes_per_s": st.n_converged * world / (t_ms / args.steps / 1e3) if st else None,
             "newton": {"iterations": st.iterations, "active_per_iter": st.active_per_iter,
                        "n_failed": st.n_failed, "eps_newton": st.eps_newton,
                        "max_residual": st.max_residual, "evals_fp64": st.evals_fp64} if st else None,
+            "precision_paths": paths,
             "gauss_flux_eps0": eps0,
             "gpu_launches": launches,
             "roofline": roofline,
-            "roofline_kernels": kern,
+            "roofline_kernels": dict(kern, **({"k_eval_fp64": fp64_kern} if fp64_kern else {})),
+            "peaks": peaks,
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,

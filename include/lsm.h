@@ -14,8 +14,14 @@
  *
  * Conventions for every entry point:
  *   - Return value: LSM_OK (0) or a negative lsm_status; no exceptions cross
- *     the ABI.  lsm_last_error(ctx) returns a message for the last failure
- *     on that context (thread-unsafe, owned by the context).
+ *     the ABI.  lsm_last_error(ctx) returns the message of the calling
+ *     thread's last failed call on that context.
+ *   - Every wait of a pair kernel on its staged source tile is bounded.  A
+ *     wait that runs out sets the calling thread's device error word of the
+ *     context and the targets of the thread blocks that gave up get NaN
+ *     results.  Synchronous calls return LSM_E_TIMEOUT for it; calls left
+ *     asynchronous (device pointers) report it at lsm_check_error or at the
+ *     thread's next synchronous call.
  *   - Handles are opaque.  Device state belongs to the library until the
  *     matching *_free / lsm_destroy.
  *   - Array arguments may be host or device pointers (detected with
@@ -60,9 +66,10 @@ typedef enum {
     LSM_MIXED = 1,  /* FP32 pair kernels, compensated per-tile accumulation,
                        FP64 results; Newton finishes with LSM_FF steps when
                        the tolerance asks for more than FP32 gives */
-    LSM_FF = 2      /* Phi to FP64 accuracy on the FP32 pipes: far tiles in
+    LSM_FF = 2      /* Phi to FP64 accuracy on the FP32 pipes: every pair in
                        float-float arithmetic (about 44 significant bits),
-                       near tiles in FP64; grad Phi to mixed accuracy */
+                       the near pairs' radial factor from a float-float
+                       table; grad Phi to mixed accuracy */
 } lsm_precision;
 
 /* Per-node status of the chart solve (low byte); bit 8 set when a Newton
@@ -141,8 +148,12 @@ typedef struct {
     double max_residual;      /* max |Phi - 1/2| at the converged nodes' last
                                  evaluation */
     int64_t evals_fp32;       /* target evaluations done by the mixed kernels */
-    int64_t evals_fp64;       /* target evaluations done by FP64 kernels */
+    int64_t evals_fp64;       /* target evaluations done by FP64-accurate kernels
+                                 (LSM_FP64, or the float-float steps of LSM_MIXED) */
     int32_t active_per_iter[32];
+    int64_t evals_near_only;  /* of evals_fp64: float-float verification sweeps that
+                                 re-evaluate only the near tiles and reuse the far
+                                 part recorded by the sweep before */
 } lsm_solve_stats;
 
 /* Counts describing an uploaded mesh. */
@@ -161,10 +172,23 @@ typedef struct {
 int lsm_create(lsm_ctx** out, int device, const lsm_options* opt);
 /* Destroy a context; every mesh created from it must be freed first. */
 int lsm_destroy(lsm_ctx* ctx);
-/* Message of the last failed call on ctx (never NULL). */
+/* Message of the calling thread's last failed call on ctx ("" if none;
+ * never NULL).  The string belongs to the calling thread and stays valid
+ * until its next lsm_last_error call. */
 const char* lsm_last_error(const lsm_ctx* ctx);
 /* Number of kernel launches the library issued on this context so far. */
 int64_t lsm_launch_count(const lsm_ctx* ctx);
+/* Synchronise `stream`, then read and clear the calling thread's device
+ * error word of ctx: LSM_E_TIMEOUT if a pair kernel launched by this thread
+ * since the last check gave up on a bounded wait (its targets hold NaN),
+ * else LSM_OK.  Errors: LSM_E_INVALID_ARG, LSM_E_CUDA. */
+int lsm_check_error(lsm_ctx* ctx, void* stream);
+/* Test hook, off by default: with enable != 0 every pair kernel launched on
+ * ctx arms its first stage's barrier without issuing the copy and waits
+ * with a short limit, so that the wait runs out with nothing in flight and
+ * the call reports LSM_E_TIMEOUT.  Used to test the failure path; never
+ * needed otherwise. */
+int lsm_test_inject_wait_timeout(lsm_ctx* ctx, int enable);
 
 /* Work counters of a context, for roofline accounting. */
 typedef struct {
@@ -184,6 +208,23 @@ typedef struct {
     int64_t kind_launches[4];
     double kind_ms[4];
 } lsm_ctx_stats;
+
+/* Measured throughput of the arithmetic the pair kernels run on (their
+ * roofline denominators; the kernels are ALU-bound, not HBM- or tensor-
+ * bound): one probe kernel per instruction kind, eight independent
+ * dependency chains per thread at full occupancy on every SM, timed with
+ * CUDA events on `stream`, best of three launches after a warm-up.  Takes
+ * well under a second.  Synchronises `stream`.
+ * Errors: LSM_E_INVALID_ARG, LSM_E_CUDA. */
+typedef struct {
+    double ffma_tflops;    /* FP32 fma.rn.f32, 2 flops each */
+    double ffma2_tflops;   /* packed fma.rn.f32x2, 4 flops each */
+    double dfma_tflops;    /* FP64 fma.rn.f64, 2 flops each */
+    double rsqrt_gops;     /* rsqrt.approx.f32 per second (special-function unit) */
+    double ex2_gops;       /* ex2.approx.ftz.f32 per second (special-function unit) */
+    double ms[5];          /* the probes' best launch times, in the order above */
+} lsm_peaks;
+int lsm_measure_peaks(lsm_ctx* ctx, lsm_peaks* out, void* stream);
 
 /* Turn per-launch timing of the pair kernels on or off (off by default). */
 int lsm_set_profiling(lsm_ctx* ctx, int enable);
@@ -256,11 +297,16 @@ int lsm_eval_phi_grad(lsm_mesh* mesh, const double* x, int64_t n, double* phi, d
  * device memory is already reserved in full by another allocator (a
  * framework's caching pool), so that a further cudaMalloc would fail.
  *
- * It computes what lsm_eval_phi_grad computes, with the same kernels and
- * tolerances, but it does not sort the targets (they are evaluated in the
- * caller's order) and it takes its scratch from one fixed device array of
- * 8 MiB inside the library, which every GPU that loads the library holds
- * until the process exits.
+ * It computes what lsm_eval_phi_grad computes at precision LSM_FP64 or
+ * LSM_MIXED, with the same kernels and tolerances (LSM_FF, which needs the
+ * treecode's scratch, returns LSM_E_INVALID_ARG), but it does not sort the
+ * targets and takes its scratch from one fixed device array of 8 MiB inside
+ * the library, which every GPU that loads the library holds until the
+ * process exits.  Targets are evaluated in the caller's order: a thread
+ * block of consecutive targets decides near and far source tiles from the
+ * box around its targets, so targets scattered over the surface put most
+ * pairs on the slower near-field path; callers that can should pass targets
+ * in a spatially coherent order.
  *   x     double[n][3], device pointer
  *   phi   double[n], device pointer
  *   grad  double[n][3], device pointer, or NULL
@@ -268,7 +314,8 @@ int lsm_eval_phi_grad(lsm_mesh* mesh, const double* x, int64_t n, double* phi, d
  *         message naming the limit.  Host pointers also return
  *         LSM_E_INVALID_ARG.
  * Asynchronous on `stream`.  It calls no cudaMalloc, cudaFree or other
- * allocating routine.  The first call on a device looks up the array's
+ * allocating routine.  A bounded wait that runs out leaves NaN in the
+ * targets concerned and sets the error word that lsm_check_error reads.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  Every call on a device shares the
  * one array and leaves its contents behind for the next call; the kernels
@@ -470,6 +517,7 @@ typedef struct {
     const double* x;         /* [n_nodes][3], server-owned */
     const double* h;         /* [n_nodes] */
     const int32_t* node_status;
+    const char* error;       /* the failed request's own message ("" if ok), server-owned */
 } lsm_result;
 
 typedef struct {

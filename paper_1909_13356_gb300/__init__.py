@@ -42,7 +42,7 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_server_info", "lsm_server_destroy", "lsm_autotune", "lsm_chart_frames", "lsm_gauss_flux",
            "lsm_mesh_upload_sigmax", "lsm_mesh_get_sigma0", "lsm_eval_sigma", "lsm_eval_hessian",
            "lsm_chart_curvature", "lsm_refined_nodes", "lsm_solve_charts_nodes", "lsm_chart_frames_nodes",
-           "lsm_gauss_flux_nodes")
+           "lsm_gauss_flux_nodes", "lsm_check_error", "lsm_test_inject_wait_timeout", "lsm_measure_peaks")
 
 
 class LsmError(RuntimeError):
@@ -69,7 +69,7 @@ class _Stats(ctypes.Structure):
                 ("n_converged", ctypes.c_int32), ("n_failed", ctypes.c_int32),
                 ("eps_newton", ctypes.c_double), ("max_residual", ctypes.c_double),
                 ("evals_fp32", ctypes.c_int64), ("evals_fp64", ctypes.c_int64),
-                ("active_per_iter", ctypes.c_int32 * 32)]
+                ("active_per_iter", ctypes.c_int32 * 32), ("evals_near_only", ctypes.c_int64)]
 
 
 class _CtxStats(ctypes.Structure):
@@ -97,7 +97,13 @@ class _Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("t_submit_ms", ctypes.c_double),
                 ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("stats", _Stats), ("x", ctypes.POINTER(ctypes.c_double)), ("h", ctypes.POINTER(ctypes.c_double)),
-                ("node_status", ctypes.POINTER(ctypes.c_int32))]
+                ("node_status", ctypes.POINTER(ctypes.c_int32)), ("error", ctypes.c_char_p)]
+
+
+class _Peaks(ctypes.Structure):
+    _fields_ = [("ffma_tflops", ctypes.c_double), ("ffma2_tflops", ctypes.c_double),
+                ("dfma_tflops", ctypes.c_double), ("rsqrt_gops", ctypes.c_double), ("ex2_gops", ctypes.c_double),
+                ("ms", ctypes.c_double * 5)]
 
 
 class _TuneResult(ctypes.Structure):
@@ -123,6 +129,7 @@ class SolveStats:
     evals_fp32: int
     evals_fp64: int
     active_per_iter: list
+    evals_near_only: int = 0
 
 
 _lock = threading.Lock()
@@ -176,6 +183,9 @@ def load(build_if_needed: bool = True):
         L.lsm_chart_frames_nodes.argtypes = [P, I64, P, P, P, P, P, P, P, P]
         L.lsm_gauss_flux_nodes.argtypes = [P, I64, P, P, P, P, P, P, P, P]
         L.lsm_gauss_flux.argtypes = [P, I32, P, P, P, P, P, P]
+        L.lsm_check_error.argtypes = [P, P]
+        L.lsm_test_inject_wait_timeout.argtypes = [P, I32]
+        L.lsm_measure_peaks.argtypes = [P, ctypes.POINTER(_Peaks), P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -283,6 +293,25 @@ class Context:
         for k, _ in _CtxStats._fields_:
             v = getattr(st, k)
             out[k] = list(v) if k.startswith("kind_") else v
+        return out
+
+    def check_error(self, stream=None):
+        """Raise LsmError (TIMEOUT) if a pair kernel this thread launched gave
+        up on a bounded wait since the last check (lsm_check_error)."""
+        self._check(self._L.lsm_check_error(self._h, _stream_handle(stream)))
+
+    def inject_wait_timeout(self, enable: bool = True):
+        """Test hook (lsm_test_inject_wait_timeout): pair kernels arm their
+        first stage without a copy, so that their bounded wait runs out."""
+        self._check(self._L.lsm_test_inject_wait_timeout(self._h, 1 if enable else 0))
+
+    def measure_peaks(self, stream=None) -> dict:
+        """Measured FP32 (scalar and packed), FP64 FMA and special-function
+        throughput of this GPU (lsm_measure_peaks)."""
+        p = _Peaks()
+        self._check(self._L.lsm_measure_peaks(self._h, ctypes.byref(p), _stream_handle(stream)))
+        out = {k: getattr(p, k) for k, _ in _Peaks._fields_ if k != "ms"}
+        out["ms"] = list(p.ms)
         return out
 
     def upload(self, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0, stream=None) -> "Mesh":
@@ -405,11 +434,19 @@ class Mesh:
         return xu, xv, jac
 
     def solve_charts_nodes(self, tri, uvw, tol: float = 1e-12, max_iter: int = 20, precision: int = FP64,
-                           stream=None):
-        """Charts at explicit nodes (lsm_solve_charts_nodes): (x, h, status, SolveStats)."""
+                           device_out: bool = False, stream=None):
+        """Charts at explicit nodes (lsm_solve_charts_nodes): (x, h, status, SolveStats);
+        with device_out the outputs are CUDA tensors on the mesh's device."""
         t, u = _as(tri, np.int32), _as(uvw, np.float64)
         n = int(t.shape[0])
-        x, h, st = np.empty((n, 3)), np.empty(n), np.empty(n, dtype=np.int32)
+        if device_out:
+            import torch
+            dev = torch.device("cuda", self.ctx.device)
+            x = torch.empty((n, 3), dtype=torch.float64, device=dev)
+            h = torch.empty(n, dtype=torch.float64, device=dev)
+            st = torch.empty(n, dtype=torch.int32, device=dev)
+        else:
+            x, h, st = np.empty((n, 3)), np.empty(n), np.empty(n, dtype=np.int32)
         stats = _Stats()
         rc = self.ctx._L.lsm_solve_charts_nodes(self._h, n, _ptr(t), _ptr(u), float(tol), int(max_iter),
                                                 int(precision), _ptr(x), _ptr(h), _ptr(st), ctypes.byref(stats),
@@ -497,10 +534,7 @@ class Mesh:
                                           _ptr(x), _ptr(h), _ptr(st), ctypes.byref(stats),
                                           _stream_handle(stream))
         self.ctx._check(rc)
-        s = SolveStats(stats.iterations, stats.n_nodes, stats.n_converged, stats.n_failed,
-                       stats.eps_newton, stats.max_residual, stats.evals_fp32, stats.evals_fp64,
-                       list(stats.active_per_iter)[:max(stats.iterations, 0)])
-        return x, h, st, s
+        return x, h, st, _stats(stats)
 
     def free(self):
         if getattr(self, "_h", None):
@@ -516,7 +550,8 @@ class Mesh:
 
 def _stats(st: "_Stats") -> SolveStats:
     return SolveStats(st.iterations, st.n_nodes, st.n_converged, st.n_failed, st.eps_newton, st.max_residual,
-                      st.evals_fp32, st.evals_fp64, list(st.active_per_iter)[:max(min(st.iterations, 32), 0)])
+                      st.evals_fp32, st.evals_fp64, list(st.active_per_iter)[:max(min(st.iterations, 32), 0)],
+                      st.evals_near_only)
 
 
 class Batch:
@@ -594,7 +629,8 @@ class Server:
         self.ctx._check(rc)
         n = int(r.n_nodes)
         out = {"status": int(r.status), "n_nodes": n, "t_submit_ms": r.t_submit_ms, "t_start_ms": r.t_start_ms,
-               "t_done_ms": r.t_done_ms, "device_bytes": int(r.device_bytes), "stats": _stats(r.stats)}
+               "t_done_ms": r.t_done_ms, "device_bytes": int(r.device_bytes), "stats": _stats(r.stats),
+               "error": (r.error or b"").decode(errors="replace")}
         if r.status == 0 and n > 0:
             out["x"] = np.ctypeslib.as_array(r.x, shape=(n, 3)).copy()
             out["h"] = np.ctypeslib.as_array(r.h, shape=(n,)).copy()

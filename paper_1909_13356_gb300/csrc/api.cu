@@ -195,11 +195,14 @@ __global__ void k_scatter6(const double* __restrict__ R, const uint32_t* __restr
 int check_flag(Ctx* ctx, cudaStream_t st)
 {
     int h = 0;
-    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int* f = flag_word(ctx);
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(&h, f, sizeof(int), cudaMemcpyDeviceToHost, st));
     LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     if (h != 0) {
-        ctx->err = "device wait limit reached in a pair kernel (error word " + std::to_string(h) + ")";
-        cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st);
+        ctx->err = "device wait limit reached in a pair kernel (error word " + std::to_string(h) +
+                   "); the targets of the blocks that gave up hold NaN";
+        LSM_CUDA_TRY(ctx, cudaMemsetAsync(f, 0, sizeof(int), st));
+        LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
         return LSM_E_TIMEOUT;
     }
     return LSM_OK;
@@ -347,6 +350,20 @@ const char* lsm_last_error(const lsm_ctx* c)
 }
 
 int64_t lsm_launch_count(const lsm_ctx* c) { return c ? c->c.launches.load() : -1; }
+
+int lsm_check_error(lsm_ctx* c, void* stream)
+{
+    if (!c) return LSM_E_INVALID_ARG;
+    DeviceGuard g(c->c.device);
+    return check_flag(&c->c, (cudaStream_t)stream);
+}
+
+int lsm_test_inject_wait_timeout(lsm_ctx* c, int enable)
+{
+    if (!c) return LSM_E_INVALID_ARG;
+    c->c.test_nocopy = enable != 0;
+    return LSM_OK;
+}
 
 int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     const double* sigma, const lsm_quad* rule, void* stream, lsm_mesh** out)

@@ -105,6 +105,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 constexpr int kWaitLimit = 1 << 22;
+constexpr int kTestWaitLimit = 1 << 10;   // the test hook's short limit (nothing is in flight then)
 constexpr double kSqrt2 = 1.41421356237309505;
 // 1 / (2 sqrt2 pi^(3/2)): dPhi/dsigma = -(4 a^4 / (2 sqrt2 pi^(3/2))) sum (nw' . r) e^{-u^2} 4 pi
 // with nw' = nw / 4 pi and sigma = 1 / (sqrt2 a), i.e. -16 pi a^4 kSigC sum (nw' . r) e^{-w}
@@ -301,6 +302,11 @@ struct EvalArgs {
     float cut2;
     double* out;       // [split][4][nt] (phi, gx, gy, gz) when splitting, else [4][nt]
     int* flag;
+    // bounded waits: polls before a stage counts as lost; test_nocopy != 0
+    // (test hook) arms the first stage's barrier without issuing its copy,
+    // so that the wait runs out with nothing in flight
+    int wait_limit = 1 << 22;
+    int test_nocopy = 0;
     const int4* items; // optional work items (first target, count, first tile, end tile)
     const int* n_items;
     // float-float kernel only: 0 plain; 1 record the far-tile part into
@@ -336,6 +342,19 @@ __device__ __forceinline__ void count_pairs(unsigned long long* dst, unsigned lo
         if (f) atomicAdd(dst + 1, f);
     }
 }
+
+// A stage's copy did not complete within the wait limit: record the error in
+// the device word and wait (bounded again) for both stages, the lost one and
+// the prefetched next one (when `next` was issued), so that no bulk copy is
+// still writing into shared memory when the CTA exits.  Called by thread 0.
+__device__ __forceinline__ void give_up(const EvalArgs& A, uint64_t* bar, int b, int it, bool next)
+{
+    atomicOr(A.flag, kErrWaitTimeout);
+    mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), A.wait_limit);
+    if (next) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), A.wait_limit);
+}
+// Targets of a CTA that gave up get NaN results.
+constexpr double kNaN = __builtin_nan("");
 
 // ---------------------------------------------------------------- float-float arithmetic
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
@@ -566,12 +585,13 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
     // thread 0 stages a tile; the low parts of the positions only for near
     // tiles.  Proxy tiles (ids >= ntiles, list mode only) are always far.
     auto tile_at = [&](int j) { return A.list ? A.list[j] : j; };
-    auto issue = [&](int t, int b) {
+    auto issue = [&](int t, int b, bool arm_only) {
         const int cnt = (int)A.thi[t].w;
         const uint32_t bytes = (uint32_t)cnt * 16u;
         const bool proxy = t >= A.ntiles;
         const bool far = proxy || tile_is_far(s_bb, SIGX ? with_sigma(A.tlo[t], s_smax) : A.tlo[t], A.thi[t], A.cut2);
         mbar_expect_tx(&bar[b], (far ? 2u : 4u) * bytes);
+        if (arm_only) return;
         const float4* gp = proxy ? A.ppos + (size_t)(t - A.ntiles) * kTile : spos + (size_t)t * kTile;
         const float4* gn = proxy ? A.pnw + (size_t)(t - A.ntiles) * kTile : snw + (size_t)t * kTile;
         bulk_g2s(&sh_pos[b][0], gp, bytes, &bar[b]);
@@ -581,21 +601,19 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
             bulk_g2s(&sh_nl[b][0], snwlo + (size_t)t * kTile, bytes, &bar[b]);
         }
     };
-    if (tid == 0 && t0 < t1) issue(tile_at(t0), 0);
+    if (tid == 0 && t0 < t1) issue(tile_at(t0), 0, A.test_nocopy != 0);
 
     unsigned long long pairs_near = 0, pairs_far = 0;
+    bool failed = false;
     for (int j = t0; j < t1; j++) {
         const int it = j - t0;
         const int b = it & 1;
         const int t = tile_at(j);
-        if (tid == 0 && j + 1 < t1) issue(tile_at(j + 1), b ^ 1);
-        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), kWaitLimit);
+        if (tid == 0 && j + 1 < t1) issue(tile_at(j + 1), b ^ 1, false);
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), A.wait_limit);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(A.flag, kErrWaitTimeout);
-                // let any copy still in flight land before the CTA exits
-                if (j + 1 < t1) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
-            }
+            if (tid == 0) give_up(A, bar, b, it, j + 1 < t1);
+            failed = true;
             break;
         }
         const float4 tl = A.tlo[t], th = A.thi[t];
@@ -790,7 +808,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         if (i < tend) {
             double r[4];
 #pragma unroll
-            for (int c = 0; c < 4; c++) r[c] = (double)acc_h[k][c] + (double)acc_l[k][c];
+            for (int c = 0; c < 4; c++) r[c] = failed ? kNaN : (double)acc_h[k][c] + (double)acc_l[k][c];
             if constexpr (SIGX) {
                 // grad Phi += (dPhi/dsigma) grad sigma (eq. gradPhi, third term)
                 const double a = (double)ta_h[k] + (double)ta_l[k];
@@ -887,25 +905,25 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int t, int b) {
+    auto issue = [&](int t, int b, bool arm_only) {
         const int cnt = (int)A.thi[t].w;
         const uint32_t bytes = (uint32_t)cnt * 32u;
         mbar_expect_tx(&bar[b], 2u * bytes);
+        if (arm_only) return;
         bulk_g2s(&sh_pos[b][0], spos + (size_t)t * kTile, bytes, &bar[b]);
         bulk_g2s(&sh_nw[b][0], snw + (size_t)t * kTile, bytes, &bar[b]);
     };
-    if (tid == 0 && t0 < t1) issue(t0, 0);
+    if (tid == 0 && t0 < t1) issue(t0, 0, A.test_nocopy != 0);
 
+    bool failed = false;
     for (int t = t0; t < t1; t++) {
         const int it = t - t0;
         const int b = it & 1;
-        if (tid == 0 && t + 1 < t1) issue(t + 1, b ^ 1);
-        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), kWaitLimit);
+        if (tid == 0 && t + 1 < t1) issue(t + 1, b ^ 1, false);
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), A.wait_limit);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(A.flag, kErrWaitTimeout);
-                if (t + 1 < t1) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
-            }
+            if (tid == 0) give_up(A, bar, b, it, t + 1 < t1);
+            failed = true;
             break;
         }
         const float4 tl = A.tlo[t], th = A.thi[t];
@@ -981,7 +999,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
         if (i < tend) {
             double r[4];
 #pragma unroll
-            for (int c = 0; c < 4; c++) r[c] = acc[k][c] + accl[k][c];
+            for (int c = 0; c < 4; c++) r[c] = failed ? kNaN : acc[k][c] + accl[k][c];
             if constexpr (SIGX) {
                 // grad Phi += (dPhi/dsigma) grad sigma (eq. gradPhi, third term)
                 const double a2 = ta[k] * ta[k];
@@ -1148,7 +1166,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int t, int b) {
+    auto issue = [&](int t, int b, bool arm_only) {
         const int cnt = (int)A.thi[t].w;
         const uint32_t by = (uint32_t)cnt * 16u;
         // the tile's centre relative to the block reference, in FP64 (read
@@ -1160,6 +1178,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         s_dref[b][0] = make_float4(h0, h1, h2, 0.0f);
         s_dref[b][1] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1), (float)(d2 - (double)h2), 0.0f);
         mbar_expect_tx(&bar[b], 4u * by);
+        if (arm_only) return;
         // proxy tiles (list mode, ids >= ntiles) come from the tree's arrays
         const bool proxy = t >= A.ntiles;
         const size_t o = (size_t)(proxy ? t - A.ntiles : t) * kTile;
@@ -1168,19 +1187,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         bulk_g2s(sh[b] + 2 * kTile * 16, (proxy ? A.plo : slo) + o, by, &bar[b]);
         bulk_g2s(sh[b] + 3 * kTile * 16, (proxy ? A.pnwlo : snwlo) + o, by, &bar[b]);
     };
-    if (tid == 0 && nlist > 0) issue(tile_at(0), 0);
+    if (tid == 0 && nlist > 0) issue(tile_at(0), 0, A.test_nocopy != 0);
 
     unsigned long long pairs_near = 0, pairs_far = 0;
+    bool failed = false;
     for (int it = 0; it < nlist; it++) {
         const int t = tile_at(it);
         const int b = it & 1;
-        if (tid == 0 && it + 1 < nlist) issue(tile_at(it + 1), b ^ 1);
-        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), kWaitLimit);
+        if (tid == 0 && it + 1 < nlist) issue(tile_at(it + 1), b ^ 1, false);
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), A.wait_limit);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(A.flag, kErrWaitTimeout);
-                if (it + 1 < nlist) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
-            }
+            if (tid == 0) give_up(A, bar, b, it, it + 1 < nlist);
+            failed = true;
             break;
         }
         const int cnt = (int)A.thi[t].w;
@@ -1289,7 +1307,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         const double fphi = (double)fph + (double)fpl;
         double fgr[3];
         for (int c = 0; c < 3; c++) fgr[c] = (double)fgh[c] + (double)fgl[c];
-        if (mode == 2) {
+        if (failed) {
+            // a stage was lost: no partial sums leave the CTA
+            phi = kNaN;
+            for (int c = 0; c < 3; c++) gr[c] = kNaN;
+        } else if (mode == 2) {
             // recorded far part, moved to x along its gradient
             double fp = A.far_io[i];
             for (int c = 0; c < 3; c++) {
@@ -1507,7 +1529,9 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     const double cut = mixed ? ctx->opt.cutoff_mixed : ctx->opt.cutoff_fp64;
     A.cut2 = (float)(cut * cut);
     A.out = part;
-    A.flag = ctx->d_flag;
+    A.flag = flag_word(ctx);
+    A.test_nocopy = ctx->test_nocopy ? 1 : 0;
+    A.wait_limit = ctx->test_nocopy ? kTestWaitLimit : kWaitLimit;
     A.pairs = ctx->d_pairs + 2 * (mixed ? 0 : (precision == LSM_FF ? 1 : 2));
     A.items = nullptr;
     A.n_items = nullptr;
@@ -1592,7 +1616,9 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
     const double cut = mixed ? ctx->opt.cutoff_mixed : ctx->opt.cutoff_fp64;
     A.cut2 = (float)(cut * cut);
     A.out = res;
-    A.flag = ctx->d_flag;
+    A.flag = flag_word(ctx);
+    A.test_nocopy = ctx->test_nocopy ? 1 : 0;
+    A.wait_limit = ctx->test_nocopy ? kTestWaitLimit : kWaitLimit;
     A.pairs = ctx->d_pairs + 2 * (mixed ? 0 : (precision == LSM_FF ? 1 : 2));
     A.items = items;
     A.n_items = n_items;
@@ -1738,7 +1764,9 @@ int eval_noalloc(Ctx* ctx, const Mesh* me, const double* x, int64_t n, double* p
     const double cut = mixed ? ctx->opt.cutoff_mixed : ctx->opt.cutoff_fp64;
     A.cut2 = (float)(cut * cut);
     A.out = nsplit > 1 ? part : R;
-    A.flag = ctx->d_flag;
+    A.flag = flag_word(ctx);
+    A.test_nocopy = ctx->test_nocopy ? 1 : 0;
+    A.wait_limit = ctx->test_nocopy ? kTestWaitLimit : kWaitLimit;
     A.pairs = ctx->d_pairs + 2 * (mixed ? 0 : (precision == LSM_FF ? 1 : 2));
     A.items = nullptr;
     A.n_items = nullptr;

@@ -6,7 +6,9 @@
 #include <cstdint>
 #include <cstdio>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <utility>
 #include <vector>
@@ -26,19 +28,29 @@ constexpr int kEvalThreads = 128;
 // Largest Chebyshev degree of the treecode's proxy grids.
 constexpr int kTreeMaxDegree = 16;
 
-// Last-error message, safe to set from several host threads.
+// Last-error messages of a context, one per host thread: a call records its
+// message for the thread that made it, so that threads sharing a context
+// (the server's worker slots) never read each other's messages.  c_str()
+// returns a copy taken under the lock, owned by the calling thread and valid
+// until its next c_str() call.
 class ErrorText {
 public:
     ErrorText& operator=(const std::string& s) {
         std::lock_guard<std::mutex> lk(mu_);
-        text_ = s;
+        text_[std::this_thread::get_id()] = s;
         return *this;
     }
-    const char* c_str() const { return text_.c_str(); }
+    const char* c_str() const {
+        thread_local std::string copy;
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = text_.find(std::this_thread::get_id());
+        copy = it == text_.end() ? std::string() : it->second;
+        return copy.c_str();
+    }
 
 private:
-    std::mutex mu_;
-    std::string text_;
+    mutable std::mutex mu_;
+    std::map<std::thread::id, std::string> text_;
 };
 
 struct Ctx {
@@ -47,7 +59,8 @@ struct Ctx {
     lsm_options opt{};
     ErrorText err;
     std::atomic<int64_t> launches{0};
-    int* d_flag = nullptr;   // device error word (bounded waits, bad sizes)
+    int* d_flag = nullptr;   // device error word (bounded waits); see flag_word()
+    bool test_nocopy = false;  // test hook: pair kernels arm their first stage without copying
     unsigned long long* d_pairs = nullptr;  // [4 kinds][2]: pairs in near / far tiles
     bool profiling = false;
     struct ProfEvent {
@@ -63,6 +76,30 @@ struct Ctx {
     static constexpr int kHostWords = 64;
     std::mutex host_mu;
     std::vector<int32_t*> host_free;
+};
+
+// Device error word of the calling thread: a thread that installed its own
+// word for this context (FlagScope) gets that one, every other thread the
+// context's.  Kernels launched by the thread set it; check_flag reads it.
+struct FlagOverride {
+    const Ctx* ctx = nullptr;
+    int* flag = nullptr;
+};
+inline FlagOverride& flag_override()
+{
+    thread_local FlagOverride f;
+    return f;
+}
+inline int* flag_word(Ctx* ctx)
+{
+    const FlagOverride& f = flag_override();
+    return f.ctx == ctx && f.flag ? f.flag : ctx->d_flag;
+}
+// Installs `flag` as the calling thread's error word of ctx for its lifetime.
+struct FlagScope {
+    FlagOverride saved;
+    FlagScope(const Ctx* ctx, int* flag) : saved(flag_override()) { flag_override() = FlagOverride{ctx, flag}; }
+    ~FlagScope() { flag_override() = saved; }
 };
 
 // A pinned block from the context's pool, returned to it on scope exit.

@@ -345,6 +345,7 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
                                                          max_iter);
                 LSM_LAUNCHED(ctx);
                 S0.evals_fp64 += nl;
+                S0.evals_near_only += nl;
                 continue;
             }
             if (mixed) {

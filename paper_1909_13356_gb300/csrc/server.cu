@@ -95,6 +95,7 @@ void run_job(lsm_server* sv, cudaStream_t st, Job& j)
         rc = lsm_solve_charts(mesh, j.order, j.tol, j.max_iter, j.precision, j.x.data(), j.h.data(),
                               j.node_status.data(), &j.stats, st);
     }
+    // the message this worker thread's own failing call recorded
     if (rc != LSM_OK) j.err = lsm_last_error(sv->ctx);
     if (mesh) lsm_mesh_free(mesh);
     j.status = rc;
@@ -105,6 +106,15 @@ void worker(lsm_server* sv)
     cudaSetDevice(sv->ctx->c.device);
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+    // this slot's own device error word: a wait that runs out in one request
+    // is charged to that request, not to whichever slot checks the word first
+    // (the messages are per thread already)
+    int* wflag = nullptr;
+    if (cudaMalloc(&wflag, sizeof(int)) != cudaSuccess || cudaMemset(wflag, 0, sizeof(int)) != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return;
+    }
+    FlagScope scope(&sv->ctx->c, wflag);
     for (;;) {
         std::shared_ptr<Job> job;
         {
@@ -144,6 +154,7 @@ void worker(lsm_server* sv)
         sv->cv_work.notify_all();
     }
     cudaStreamDestroy(st);
+    cudaFree(wflag);
 }
 
 }  // namespace
@@ -218,6 +229,7 @@ int lsm_server_poll(lsm_server* sv, int64_t ticket, int wait, lsm_result* out)
     out->x = j->x.empty() ? nullptr : j->x.data();
     out->h = j->h.empty() ? nullptr : j->h.data();
     out->node_status = j->node_status.empty() ? nullptr : j->node_status.data();
+    out->error = j->err.c_str();
     return LSM_OK;
 }
 

@@ -4,8 +4,9 @@ Graded torus, 30,720 triangles, Duffy 6x6 sources (1,105,920 nodes), 1e6
 targets within 3 sigma, order-8 chart nodes (1,105,920) to |Phi - 1/2| <
 1e-12: seeded samples of 10,000 targets and 10,000 chart nodes against the
 FP64 oracle computed one by one.
-Bumped icosphere, level 8 (1,310,720 triangles, 20,971,520 nodes): sampled
-outputs of a 1e5-target evaluation against the oracle.
+Bumped icosphere, level 8 (1,310,720 triangles, 20,971,520 nodes): a
+1e5-target evaluation against the float-float path at every target, the FP64
+direct sum on 10,240 targets and the oracle on 1,000.
 """
 import numpy as np
 import pytest
@@ -105,6 +106,13 @@ def test_torus_full_chart_solve_sampled(lsm, oracle_mod, torus):
 
 
 def test_icosphere_full_evaluation_sampled(lsm, oracle_mod):
+    """The 2.1e7-node bumped icosphere, mixed path with its treecode at 1e5
+    targets, against: the float-float path at all 1e5 targets, the FP64
+    direct sum on 10,240 targets (four runs of 2,560 consecutive targets in
+    Morton order, so that its blocks are as compact as the full set's), and
+    the FP64 oracle on 1,000 targets.  The float-float path is also held to
+    the FP64 direct sum there (1e-12)."""
+    from paper_1909_13356_gb300 import shard
     w = synth.icosphere_c3(n_targets=100_000)
     m = w["mesh"]
     ctx = lsm.Context(0)
@@ -112,8 +120,20 @@ def test_icosphere_full_evaluation_sampled(lsm, oracle_mod):
     assert mesh.info()["n_sources"] == 20_971_520
     x = torch.from_numpy(w["targets"]).cuda()
     phi, grad = mesh.eval_phi_grad(x, lsm.MIXED)
+    pff, gff = mesh.eval_phi_grad(x, lsm.FF)
+    assert (phi - pff).abs().max().item() <= 1e-7
+    assert (grad - gff).abs().max().item() <= 1e-7 / m.sigma.min()
+    order = np.argsort(shard.morton_keys(w["targets"]), kind="stable")
+    starts = [k * 25_000 + 256 for k in range(4)]
+    sel = np.concatenate([order[s0:s0 + 2560] for s0 in starts])
+    sel_d = torch.from_numpy(sel).cuda()
+    p64, g64 = mesh.eval_phi_grad(x[sel_d], lsm.FP64)
+    assert (phi[sel_d] - p64).abs().max().item() <= 1e-7
+    assert (grad[sel_d] - g64).abs().max().item() <= 1e-7 / m.sigma.min()
+    assert (pff[sel_d] - p64).abs().max().item() <= 1e-12
     y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 4, 0)
-    sel = np.random.default_rng(9).choice(len(w["targets"]), 32, replace=False)
-    po, go = oracle_mod.phi_grad(y, nw, sg, w["targets"][sel])
-    assert np.abs(phi.cpu().numpy()[sel] - po).max() <= 1e-7
-    assert np.abs(grad.cpu().numpy()[sel] - go).max() <= 1e-7 / m.sigma.min()
+    so = np.random.default_rng(9).choice(len(w["targets"]), 1000, replace=False)
+    po, go = oracle_mod.phi_grad(y, nw, sg, w["targets"][so])
+    assert np.abs(phi.cpu().numpy()[so] - po).max() <= 1e-7
+    assert np.abs(grad.cpu().numpy()[so] - go).max() <= 1e-7 / m.sigma.min()
+    assert np.abs(pff.cpu().numpy()[so] - po).max() <= 1e-12

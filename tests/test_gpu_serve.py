@@ -69,6 +69,36 @@ def test_failing_request_is_isolated(setup):
     t_ok2 = srv.submit(ms[2].verts, ms[2].tris, ms[2].sigma, n_gl=4, order=8, tol=1e-10)
     r_bad = srv.result(t_bad)
     assert r_bad["status"] == -4
-    _check(srv.result(t_ok), alone[0])
-    _check(srv.result(t_ok2), alone[2])
+    assert "edge" in r_bad["error"] or "closed" in r_bad["error"] or "mesh" in r_bad["error"], r_bad["error"]
+    for t, ref in ((t_ok, alone[0]), (t_ok2, alone[2])):
+        r = srv.result(t)
+        _check(r, ref)
+        assert r["error"] == ""
     srv.close()
+
+
+def test_failing_requests_keep_their_own_messages(setup):
+    """Two kinds of failure running next to good requests on several slots:
+    each failed request reports its own message, the good ones none."""
+    lsm, ctx, ms, alone = setup
+    srv = lsm.Server(ctx, slots=3)
+    bad = synth.cube(1.0, 2)
+    flipped = bad.tris[:, ::-1].copy()        # inward orientation: negative volume
+    tickets = []
+    for k in range(3):
+        tickets.append(("ok", k, srv.submit(ms[k].verts, ms[k].tris, ms[k].sigma, n_gl=4, order=8, tol=1e-10)))
+        tickets.append(("open", k, srv.submit(bad.verts, bad.tris[:-1], None, order=8)))
+        tickets.append(("flip", k, srv.submit(bad.verts, flipped, None, order=8)))
+    msgs = {}
+    for kind, k, t in tickets:
+        r = srv.result(t)
+        if kind == "ok":
+            _check(r, alone[k])
+            assert r["error"] == ""
+        else:
+            assert r["status"] == -4 and r["error"]
+            msgs.setdefault(kind, set()).add(r["error"])
+    srv.close()
+    # every request of a kind got that kind's message, and the kinds differ
+    assert len(msgs["open"]) == 1 and len(msgs["flip"]) == 1
+    assert msgs["open"] != msgs["flip"]

@@ -6,7 +6,8 @@ whose device memory another allocator has already reserved in full.  For them
 the library evaluates Phi and grad Phi with its scratch in one fixed 8 MiB
 device array.  This file checks, through the C ABI, that it returns what
 lsm_eval_phi_grad returns (within the tolerances of the other GPU tests) on
-two calls in a row, and that it refuses sizes beyond its limit.  It builds
+calls in a row, that the last of them matches the oracle, that it refuses
+sizes beyond its limit, and that a bounded wait that runs out is reported.  It builds
 its own context and mesh, so it runs the same alone or after the other tests.
 """
 import ctypes
@@ -46,10 +47,14 @@ def _noalloc(L, mesh, x, prec):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-7)])
-def test_noalloc_matches_eval_on_two_calls(setup, prec, tol):
+def test_noalloc_matches_eval_on_two_calls(setup, oracle_mod, prec, tol):
+    """Calls in a row of growing, then shrinking size: the shared array keeps
+    the previous call's contents, and the split planes move with n, so a
+    smaller call after the largest would read stale partials if any element
+    were read before being written."""
     lsm, L, ctx, m, mesh = setup
     smin = m.sigma.min()
-    for call, (n, seed) in enumerate(((3001, 40), (MAX_TARGETS, 41))):
+    for call, (n, seed) in enumerate(((3001, 40), (MAX_TARGETS, 41), (777, 42))):
         x = torch.from_numpy(synth.targets_near_surface(m, n, synth.rng(seed), 3.0)).cuda()
         rc, phi, grad = _noalloc(L, mesh, x, prec)
         assert rc == 0, ctx._L.lsm_last_error(ctx._h)
@@ -60,6 +65,37 @@ def test_noalloc_matches_eval_on_two_calls(setup, prec, tol):
         eg = (grad - ref_grad).abs().max().item()
         assert ep <= tol, (call, ep)
         assert eg <= tol / smin, (call, eg)
+    # the last call against the FP64 oracle on a subset of its targets
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 3, 0)
+    xs = x[:96].cpu().numpy()
+    phi_o, grad_o = oracle_mod.phi_grad(y, nw, sg, xs)
+    assert np.abs(phi[:96].cpu().numpy() - phi_o).max() <= tol
+    assert np.abs(grad[:96].cpu().numpy() - grad_o).max() <= tol / smin
+    ctx.check_error()   # no bounded wait ran out
+
+
+def test_noalloc_reports_a_lost_stage(setup):
+    """A wait that runs out (test hook: the first stage is armed without a
+    copy) leaves NaN in the targets concerned and is reported by
+    lsm_check_error; the next call is clean."""
+    lsm, L, ctx, m, mesh = setup
+    x = torch.from_numpy(synth.targets_near_surface(m, 500, synth.rng(43), 3.0)).cuda()
+    ctx.inject_wait_timeout(True)
+    try:
+        rc, phi, _ = _noalloc(L, mesh, x, 1)
+        assert rc == 0   # asynchronous: reported below
+        torch.cuda.synchronize()
+        assert torch.isnan(phi).all()
+        with pytest.raises(lsm.LsmError) as e:
+            ctx.check_error()
+        assert e.value.code == -6
+    finally:
+        ctx.inject_wait_timeout(False)
+    rc, phi, _ = _noalloc(L, mesh, x, 1)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert torch.isfinite(phi).all()
+    ctx.check_error()
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(setup):
