@@ -79,6 +79,10 @@ def _load():
             lib.or_chart_frames_at.argtypes = [P, P, P, I64, P, P, P, P, P, P, P]
             lib.or_gauss_flux_w.argtypes = [I64, P, P, P, P, P]
             lib.or_gauss_flux_w.restype = ctypes.c_double
+            lib.or_geometry_quad.argtypes = [I64, P, I64, P, P, ctypes.c_int, P, P, P, P, P]
+            lib.or_sources_quad.argtypes = [P, I64, P, P, ctypes.c_int, P, P, P, P, P, P]
+            lib.or_chart_nodes_quad_at.argtypes = [P, P, P, P, I64, P, P, P, P, P]
+            lib.or_chart_frames_quad_at.argtypes = [P, P, P, I64, P, P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -366,3 +370,66 @@ def gauss_flux_w(x, grad, jac, w, x0) -> float:
     x, grad, jac, w = _f64(x), _f64(grad), _f64(jac), _f64(w)
     x0 = _f64(np.asarray(x0, dtype=np.float64).reshape(3))
     return _load().or_gauss_flux_w(len(x), _p(w), _p(x), _p(grad), _p(jac), _p(x0))
+
+
+# ---------------------------------------------------------------- quadratic patches
+def geometry_quad(verts, tris6, sigma=None, n: int = 4, subdiv: int = 0):
+    """sigma_j (0.5 sqrt(2 area_j), the curved patch's area by the n x n
+    rule, or the given sigma) and the corner vertex pseudonormals of a mesh of
+    6-node quadratic patches (corners P1..P3, then the nodes of edges 1-2,
+    2-3, 3-1)."""
+    verts = _f64(verts)
+    tris6 = np.ascontiguousarray(tris6, dtype=np.int32)
+    nv, m = len(verts), len(tris6)
+    ru, rv, rw = simplex_rule(n, subdiv)
+    sig = np.empty(m)
+    vpn = np.empty((nv, 3))
+    sig_in = _f64(sigma) if sigma is not None else None
+    rc = _load().or_geometry_quad(nv, _p(verts), m, _p(tris6), _p(sig_in) if sig_in is not None else None,
+                                  len(ru), _p(ru), _p(rv), _p(rw), _p(sig), _p(vpn))
+    if rc != 0:
+        raise ValueError("a corner vertex has zero total angle")
+    return dict(sigma=sig, vpn=vpn)
+
+
+def sources_quad(verts, tris6, sigma=None, n: int = 4, subdiv: int = 0):
+    """Source nodes on quadratic patches: y = T(u_k, v_k), nw = w_k (T_u x T_v)."""
+    verts = _f64(verts)
+    tris6 = np.ascontiguousarray(tris6, dtype=np.int32)
+    geo = geometry_quad(verts, tris6, sigma, n, subdiv)
+    ru, rv, rw = simplex_rule(n, subdiv)
+    m, nq = len(tris6), len(ru)
+    y, nw, sg = np.empty((m * nq, 3)), np.empty((m * nq, 3)), np.empty(m * nq)
+    _load().or_sources_quad(_p(verts), m, _p(tris6), _p(geo["sigma"]), nq, _p(ru), _p(rv), _p(rw), _p(y),
+                            _p(nw), _p(sg))
+    return y, nw, sg
+
+
+def chart_nodes_quad_at(verts, tris6, tri, uv, sigma=None, n: int = 4, subdiv: int = 0):
+    """x0 = T(u, v) on the quadratic patch, H(u, v) linear in its corner
+    pseudonormals, and sigma of the patch (sigma by the n x n source rule's
+    area when not given)."""
+    verts = _f64(verts)
+    tris6 = np.ascontiguousarray(tris6, dtype=np.int32)
+    geo = geometry_quad(verts, tris6, sigma, n, subdiv)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    uv = _f64(uv)
+    k = len(tri)
+    x0, hd, sl = np.empty((k, 3)), np.empty((k, 3)), np.empty(k)
+    _load().or_chart_nodes_quad_at(_p(verts), _p(tris6), _p(geo["vpn"]), _p(geo["sigma"]), k, _p(tri), _p(uv),
+                                   _p(x0), _p(hd), _p(sl))
+    return x0, hd, sl
+
+
+def chart_frames_quad_at(verts, tris6, tri, uv, h, grad, n: int = 4, subdiv: int = 0):
+    """x_u, x_v and |x_u x x_v| of charts on quadratic patches at explicit nodes."""
+    verts = _f64(verts)
+    tris6 = np.ascontiguousarray(tris6, dtype=np.int32)
+    geo = geometry_quad(verts, tris6, None, n, subdiv)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    uv, h, grad = _f64(uv), _f64(h), _f64(grad)
+    k = len(tri)
+    xu, xv, jac = np.empty((k, 3)), np.empty((k, 3)), np.empty(k)
+    _load().or_chart_frames_quad_at(_p(verts), _p(tris6), _p(geo["vpn"]), k, _p(tri), _p(uv), _p(h), _p(grad),
+                                    _p(xu), _p(xv), _p(jac))
+    return xu, xv, jac

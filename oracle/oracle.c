@@ -871,3 +871,176 @@ double or_gauss_flux_w(int64_t n, const double* w, const double* x, const double
     }
     return 1.0 + sum;
 }
+
+/* ------------------------------------------------------------------ */
+/* Quadratic (curved) skeleton patches (Sec. 5, quadratic skeletons): each
+ * patch is the 6-node curvilinear triangle through its corners P1, P2, P3
+ * and one node on each edge, P4 (edge P1-P2), P5 (edge P2-P3), P6 (edge
+ * P3-P1):
+ *   T(u,v) = sum_k N_k(u,v) P_k  with L1 = 1 - u - v, L2 = u, L3 = v and
+ *   N1 = L1 (2 L1 - 1), N2 = L2 (2 L2 - 1), N3 = L3 (2 L3 - 1),
+ *   N4 = 4 L1 L2,       N5 = 4 L2 L3,       N6 = 4 L3 L1,
+ * the standard second-order Lagrange basis on T0.  With the edge nodes at
+ * the edge midpoints the map is the flat chart of eq. tparam.  Everything
+ * else follows the flat construction with the patch's own tangents: the
+ * normal N(u,v) = T_u x T_v now varies over the patch, a source node
+ * carries nw = w N(u_k, v_k), a corner's vertex angle is the angle between
+ * the tangents of its two edges there, the vertex pseudonormal is the
+ * angle-weighted mean of the corner unit normals (eq. mkvertexpn), and H is
+ * linear in (u, v) between the three corner pseudonormals (eq. mkpseudovec),
+ * which the paper describes as analogous to the flat case.  Neighbouring
+ * patches share an edge's three nodes, so T, and with it the charts, stay
+ * continuous across edges.  tris6 [m][6] holds P1..P6's vertex indices. */
+static void quad_map(const double* verts, const int32_t* t6, double u, double v, double* T, double* Tu,
+                     double* Tv)
+{
+    const double L1 = 1.0 - u - v, L2 = u, L3 = v;
+    const double N[6] = {L1 * (2.0*L1 - 1.0), L2 * (2.0*L2 - 1.0), L3 * (2.0*L3 - 1.0),
+                         4.0 * L1 * L2, 4.0 * L2 * L3, 4.0 * L3 * L1};
+    /* d/du: dL1 = -1, dL2 = 1, dL3 = 0;  d/dv: dL1 = -1, dL2 = 0, dL3 = 1 */
+    const double Nu[6] = {-(4.0*L1 - 1.0), 4.0*L2 - 1.0, 0.0, 4.0 * (L1 - L2), 4.0 * L3, -4.0 * L3};
+    const double Nv[6] = {-(4.0*L1 - 1.0), 0.0, 4.0*L3 - 1.0, -4.0 * L2, 4.0 * L2, 4.0 * (L1 - L3)};
+    for (int c = 0; c < 3; c++) {
+        T[c] = Tu[c] = Tv[c] = 0.0;
+        for (int k = 0; k < 6; k++) {
+            const double p = verts[3 * (int64_t)t6[k] + c];
+            T[c] += N[k] * p;
+            Tu[c] += Nu[k] * p;
+            Tv[c] += Nv[k] * p;
+        }
+    }
+}
+
+/* Geometry of quadratic patches: sigma_j = 0.5 sqrt(2 area_j) (or sigma_in),
+ * area_j = sum_k w_k |N(u_k, v_k)| with the given rule on the patch, and the
+ * vertex pseudonormals (eq. mkvertexpn) from the corners' unit normals and
+ * vertex angles.  At the corners (0,0), (1,0), (0,1) the two edges leave
+ * along (T_u, T_v), (T_v - T_u, -T_u) and (-T_v, T_u - T_v).
+ * Returns 0, or -1 when a vertex has zero total angle. */
+int or_geometry_quad(int64_t nv, const double* verts, int64_t m, const int32_t* tris6, const double* sigma_in,
+                     int nq, const double* ru, const double* rv, const double* rw, double* sigma, double* vpn)
+{
+    double* asum = (double*)calloc((size_t)nv, sizeof(double));
+    memset(vpn, 0, sizeof(double) * 3 * (size_t)nv);
+    static const double cuv[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+    for (int64_t j = 0; j < m; j++) {
+        const int32_t* t6 = tris6 + 6 * j;
+        double area = 0.0;
+        for (int k = 0; k < nq; k++) {
+            double T[3], Tu[3], Tv[3], n[3];
+            quad_map(verts, t6, ru[k], rv[k], T, Tu, Tv);
+            cross3(Tu, Tv, n);
+            area += rw[k] * norm3(n);
+        }
+        sigma[j] = sigma_in ? sigma_in[j] : 0.5 * sqrt(2.0 * area);
+        for (int c = 0; c < 3; c++) {
+            double T[3], Tu[3], Tv[3], n[3], e1[3], e2[3], x[3];
+            quad_map(verts, t6, cuv[c][0], cuv[c][1], T, Tu, Tv);
+            cross3(Tu, Tv, n);
+            const double nn = norm3(n);
+            for (int d = 0; d < 3; d++) {
+                if (c == 0) { e1[d] = Tu[d]; e2[d] = Tv[d]; }
+                else if (c == 1) { e1[d] = Tv[d] - Tu[d]; e2[d] = -Tu[d]; }
+                else { e1[d] = -Tv[d]; e2[d] = Tu[d] - Tv[d]; }
+            }
+            cross3(e1, e2, x);
+            const double th = atan2(norm3(x), dot3(e1, e2));
+            const int64_t vi = t6[c];
+            asum[vi] += th;
+            for (int d = 0; d < 3; d++) vpn[3*vi+d] += th * n[d] / nn;
+        }
+    }
+    int bad = 0;
+    for (int64_t i = 0; i < nv; i++) {
+        if (asum[i] > 0) {
+            for (int k = 0; k < 3; k++) vpn[3*i+k] /= asum[i];
+        }
+    }
+    /* only corner vertices carry pseudonormals; edge nodes keep zero */
+    for (int64_t j = 0; j < m; j++)
+        for (int c = 0; c < 3; c++)
+            if (!(asum[tris6[6*j+c]] > 0)) bad = 1;
+    free(asum);
+    return bad ? -1 : 0;
+}
+
+/* Source nodes on quadratic patches (eq. discrete_int on the curved
+ * skeleton): y = T(u_k, v_k), nw = w_k N(u_k, v_k) (the area element is in
+ * |N|), sig = sigma_j.  Triangle-major, then rule order. */
+void or_sources_quad(const double* verts, int64_t m, const int32_t* tris6, const double* sigma, int nq,
+                     const double* ru, const double* rv, const double* rw, double* y, double* nw, double* sig)
+{
+    for (int64_t j = 0; j < m; j++) {
+        for (int k = 0; k < nq; k++) {
+            const int64_t s = j * nq + k;
+            double T[3], Tu[3], Tv[3], n[3];
+            quad_map(verts, tris6 + 6 * j, ru[k], rv[k], T, Tu, Tv);
+            cross3(Tu, Tv, n);
+            for (int c = 0; c < 3; c++) {
+                y[3*s+c] = T[c];
+                nw[3*s+c] = rw[k] * n[c];
+            }
+            sig[s] = sigma[j];
+        }
+    }
+}
+
+/* Chart nodes on quadratic patches at explicit (triangle, u, v):
+ * x0 = T(u, v), H linear in the corner pseudonormals (eq. mkpseudovec). */
+void or_chart_nodes_quad_at(const double* verts, const int32_t* tris6, const double* vpn, const double* sigma,
+                            int64_t n, const int32_t* tri, const double* uv, double* x0, double* hdir,
+                            double* sloc)
+{
+    for (int64_t s = 0; s < n; s++) {
+        const int64_t j = tri[s];
+        const double u = uv[2*s], v = uv[2*s+1];
+        double T[3], Tu[3], Tv[3];
+        quad_map(verts, tris6 + 6 * j, u, v, T, Tu, Tv);
+        const double* h1 = vpn + 3 * (int64_t)tris6[6*j+0];
+        const double* h2 = vpn + 3 * (int64_t)tris6[6*j+1];
+        const double* h3 = vpn + 3 * (int64_t)tris6[6*j+2];
+        for (int c = 0; c < 3; c++) {
+            x0[3*s+c] = T[c];
+            hdir[3*s+c] = h1[c] + u * (h2[c] - h1[c]) + v * (h3[c] - h1[c]);
+        }
+        sloc[s] = sigma[j];
+    }
+}
+
+/* Local coordinates of charts on quadratic patches (eq. u_vector,
+ * U_vector_2, v_vector, v_vector_2, da) with the patch's tangents at the
+ * node: h_u = -((T_u + h H_u) . grad Phi)/(H . grad Phi), x_u = T_u + h H_u
+ * + h_u H, and the same in v; jac = |x_u x x_v|. */
+void or_chart_frames_quad_at(const double* verts, const int32_t* tris6, const double* vpn, int64_t n,
+                             const int32_t* tri, const double* uv, const double* h, const double* grad,
+                             double* xu, double* xv, double* jac)
+{
+    for (int64_t s = 0; s < n; s++) {
+        const int64_t j = tri[s];
+        const double u = uv[2*s], v = uv[2*s+1];
+        double T[3], Tu[3], Tv[3];
+        quad_map(verts, tris6 + 6 * j, u, v, T, Tu, Tv);
+        const double* h1 = vpn + 3 * (int64_t)tris6[6*j+0];
+        const double* h2 = vpn + 3 * (int64_t)tris6[6*j+1];
+        const double* h3 = vpn + 3 * (int64_t)tris6[6*j+2];
+        const double* g = grad + 3*s;
+        double H[3], au[3], av[3];
+        for (int c = 0; c < 3; c++) {
+            H[c] = h1[c] + u * (h2[c] - h1[c]) + v * (h3[c] - h1[c]);
+            au[c] = Tu[c] + h[s] * (h2[c] - h1[c]);
+            av[c] = Tv[c] + h[s] * (h3[c] - h1[c]);
+        }
+        const double hg = dot3(H, g);
+        const double h_u = -dot3(au, g) / hg;
+        const double h_v = -dot3(av, g) / hg;
+        double a[3], b[3], nn[3];
+        for (int c = 0; c < 3; c++) {
+            a[c] = au[c] + h_u * H[c];
+            b[c] = av[c] + h_v * H[c];
+            xu[3*s+c] = a[c];
+            xv[3*s+c] = b[c];
+        }
+        cross3(a, b, nn);
+        jac[s] = norm3(nn);
+    }
+}

@@ -17,6 +17,10 @@ varied size (ellipsoids).
 """
 from .meshes import (  # noqa: F401
     Mesh,
+    QuadMesh,
+    quadratic_from_flat,
+    quadratic_icosphere,
+    quadratic_torus,
     cube,
     torus,
     icosphere,

@@ -254,3 +254,93 @@ def targets_near_surface(mesh: Mesh, n: int, g: np.random.Generator, width: floa
     nn /= np.linalg.norm(nn, axis=1, keepdims=True)
     off = g.uniform(-width, width, size=n) * sig[j]
     return p1 + b1[:, None] * (p2 - p1) + b2[:, None] * (p3 - p1) + off[:, None] * nn
+
+
+# ---------------------------------------------------------------- quadratic patches
+@dataclass
+class QuadMesh:
+    """A closed surface of 6-node quadratic (curvilinear) triangles.
+
+    verts: float64 [nv, 3]; tris6: int32 [m, 6], the corners P1, P2, P3
+    (counter-clockwise seen from outside) then the nodes on the edges P1-P2,
+    P2-P3, P3-P1; neighbouring patches share an edge's node.  sigma: float64
+    [m] or None."""
+
+    verts: np.ndarray
+    tris6: np.ndarray
+    sigma: np.ndarray | None = None
+    name: str = ""
+
+    @property
+    def nv(self) -> int:
+        return int(self.verts.shape[0])
+
+    @property
+    def m(self) -> int:
+        return int(self.tris6.shape[0])
+
+
+def quadratic_from_flat(mesh: Mesh, t: float = 0.5, project=None, name: str = "") -> QuadMesh:
+    """Quadratic patches on a flat mesh's triangles: one node per edge at
+    P_a + t (P_b - P_a), a < b the edge's vertex indices (so both patches on
+    an edge share the node), optionally mapped by `project` (for instance onto
+    the surface the flat mesh approximates).  t = 0.5 without projection gives
+    the flat mesh itself; t != 0.5 keeps every patch flat but parametrised
+    non-affinely (valid for 1/4 < t < 3/4)."""
+    v, f = mesh.verts, mesh.tris
+    nv = len(v)
+    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+    lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
+    key = lo.astype(np.int64) * (nv + 1) + hi
+    uk, inv = np.unique(key, return_inverse=True)
+    a, b = uk // (nv + 1), uk % (nv + 1)
+    mid = v[a] + t * (v[b] - v[a])
+    if project is not None:
+        mid = project(mid)
+    m = len(f)
+    t6 = np.stack([f[:, 0], f[:, 1], f[:, 2], nv + inv[:m], nv + inv[m:2 * m], nv + inv[2 * m:]], 1)
+    return QuadMesh(np.concatenate([v, mid]), t6.astype(np.int32), None, name or f"quadratic_{mesh.name}")
+
+
+def quadratic_icosphere(level: int) -> QuadMesh:
+    """Unit sphere from quadratic patches: the icosphere's triangles with
+    their edge nodes at the normalised edge midpoints (every node on the
+    sphere)."""
+    return quadratic_from_flat(icosphere(level), 0.5, lambda p: p / np.linalg.norm(p, axis=1, keepdims=True),
+                               f"quadratic_icosphere_l{level}")
+
+
+def quadratic_torus(R: float = 1.0, r: float = 0.3, nu: int = 24, nv: int = 8) -> QuadMesh:
+    """Torus of radii (R, r) from quadratic patches: a uniform (u, v) grid of
+    nu x nv cells split into triangles, every node (corners and the edge
+    nodes at the parameter midpoints) on the exact torus."""
+    def on_torus(U, V):
+        A = R + r * np.cos(V)
+        return np.stack([A * np.cos(U), A * np.sin(U), r * np.sin(V)], axis=-1)
+
+    uu = np.arange(nu) / nu * 2.0 * np.pi
+    vv = np.arange(nv) / nv * 2.0 * np.pi
+    U, V = np.meshgrid(uu, vv, indexing="ij")
+    P = on_torus(U, V).reshape(-1, 3)
+    idx = np.arange(nu * nv).reshape(nu, nv)
+    idx = np.concatenate([idx, idx[:1]], axis=0)
+    idx = np.concatenate([idx, idx[:, :1]], axis=1)
+    f = _grid_tris(idx)
+    # parameter coordinates of every corner (unwrapped per triangle) give the
+    # edge nodes' parameter midpoints
+    iu, iv = np.divmod(np.arange(nu * nv), nv)
+    fu, fv = iu[f].astype(np.float64), iv[f].astype(np.float64)
+    for c in range(1, 3):   # unwrap the periodic seams relative to the first corner
+        fu[:, c] += np.where(fu[:, c] - fu[:, 0] < -nu / 2, nu, 0) - np.where(fu[:, c] - fu[:, 0] > nu / 2, nu, 0)
+        fv[:, c] += np.where(fv[:, c] - fv[:, 0] < -nv / 2, nv, 0) - np.where(fv[:, c] - fv[:, 0] > nv / 2, nv, 0)
+    nvert = len(P)
+    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+    eu = np.concatenate([fu[:, [0, 1]], fu[:, [1, 2]], fu[:, [2, 0]]]).mean(1)
+    ev = np.concatenate([fv[:, [0, 1]], fv[:, [1, 2]], fv[:, [2, 0]]]).mean(1)
+    lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
+    key = lo.astype(np.int64) * (nvert + 1) + hi
+    uk, first, inv = np.unique(key, return_index=True, return_inverse=True)
+    mid = on_torus(eu[first] / nu * 2.0 * np.pi, ev[first] / nv * 2.0 * np.pi)
+    m = len(f)
+    t6 = np.stack([f[:, 0], f[:, 1], f[:, 2], nvert + inv[:m], nvert + inv[m:2 * m], nvert + inv[2 * m:]], 1)
+    return QuadMesh(np.concatenate([P, mid]), t6.astype(np.int32), None, f"quadratic_torus_{nu}x{nv}")

@@ -751,3 +751,142 @@ def test_refined_midpoint_meets_unrefined_neighbour(oracle_mod, small_sphere_cha
         r = oracle_mod.solve_charts(y, nw, sg, x0, hd, sl, tol=1e-15, max_iter=40)
         xs.append(r["x"][0])
     assert np.abs(xs[0] - xs[1]).max() < 1e-13
+
+
+# ---------------------------------------------------------------- quadratic (curved) skeletons
+def test_quadratic_with_straight_edges_is_the_flat_mesh(oracle_mod):
+    """6-node patches whose edge nodes sit at the edge midpoints are the flat
+    triangles (the quadratic basis reproduces the affine map of eq. tparam):
+    sources, sigma rule, pseudonormals, chart nodes and frames all equal the
+    flat oracle's."""
+    m = synth.cube(1.0, 2)
+    q = synth.quadratic_from_flat(m, 0.5)
+    sig = np.linspace(0.15, 0.25, m.m)
+    y, nw, sg = oracle_mod.sources(m.verts, m.tris, sig, 4, 1)
+    yq, nwq, sgq = oracle_mod.sources_quad(q.verts, q.tris6, sig, 4, 1)
+    assert np.abs(yq - y).max() < 1e-15 and np.abs(nwq - nw).max() < 1e-15 and np.array_equal(sgq, sg)
+    geo = oracle_mod.geometry(m.verts, m.tris, None)
+    gq = oracle_mod.geometry_quad(q.verts, q.tris6, None, 4, 1)
+    assert np.abs(gq["sigma"] - geo["sigma"]).max() < 1e-15
+    assert np.abs(gq["vpn"][:m.nv] - geo["vpn"]).max() < 1e-15
+    tri, uv, w = oracle_mod.refined_nodes(m.m, 3, np.zeros(m.m))
+    a = oracle_mod.chart_nodes_at(m.verts, m.tris, tri, uv)
+    b = oracle_mod.chart_nodes_quad_at(q.verts, q.tris6, tri, uv)
+    for p, r in zip(a, b):
+        assert np.abs(p - r).max() < 1e-15
+    g = np.random.default_rng(5)
+    h, grad = g.normal(size=len(tri)) * 0.1, g.normal(size=(len(tri), 3))
+    fa = oracle_mod.chart_frames_at(m.verts, m.tris, tri, uv, h, grad)
+    fb = oracle_mod.chart_frames_quad_at(q.verts, q.tris6, tri, uv, h, grad)
+    for p, r in zip(fa, fb):
+        assert np.abs(p - r).max() < 1e-13
+
+
+def test_quadratic_reparametrised_cube_is_the_box(oracle_mod):
+    """The cube's flat faces with a non-affine parametrisation: every edge node
+    at 0.4 of its edge, so T_u, T_v and |N| vary over each patch.  The surface
+    is still the cube, so the discrete sum converges to the box's erf product
+    (P1) as the rule is refined; the corner tangents keep the edges'
+    directions, so the pseudonormals equal the flat cube's; and (1/3) sum
+    nw . y is the cube's volume."""
+    m = synth.cube(1.0, 4)
+    q = synth.quadratic_from_flat(m, 0.4)
+    s = 0.1
+    x = synth.cube_c1(300)["targets"]
+    ex = box_phi(x, 1.0, s)
+    errs = []
+    for n, sd in ((4, 1), (8, 1), (8, 2)):
+        y, nw, sg = oracle_mod.sources_quad(q.verts, q.tris6, np.full(m.m, s), n, sd)
+        phi, gr = oracle_mod.phi_grad(y, nw, sg, x)
+        errs.append(np.abs(phi - ex).max())
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-11
+    assert np.abs(gr - box_grad(x, 1.0, s)).max() < 1e-9
+    assert abs((nw * y).sum() / 3.0 - 8.0) < 1e-13
+    geo = oracle_mod.geometry(m.verts, m.tris, None)
+    gq = oracle_mod.geometry_quad(q.verts, q.tris6, None, 4, 0)
+    assert np.abs(gq["vpn"][:m.nv] - geo["vpn"]).max() < 1e-14
+
+
+def test_quadratic_sphere_converges_faster_than_flat(oracle_mod):
+    """Quadratic patches with every node on the unit sphere: the enclosed
+    volume (1/3) sum nw . y and the constant-sigma sum at points near the
+    surface (against the ball's closed form, P4) converge at a higher order in
+    the edge length than the flat icosphere's (second order)."""
+    s = 0.15
+    rr = np.array([0.8, 0.95, 1.0, 1.05])
+    x = np.stack([rr / math.sqrt(3)] * 3, axis=1)
+    vq, vf, bq, bf = [], [], [], []
+    for level in (1, 2, 3):
+        q = synth.quadratic_icosphere(level)
+        y, nw, sg = oracle_mod.sources_quad(q.verts, q.tris6, np.full(q.m, s), 6, 0)
+        vq.append(abs((nw * y).sum() / 3.0 - 4.0 * math.pi / 3.0))
+        bq.append(np.abs(oracle_mod.phi_grad(y, nw, sg, x)[0] - _ball_phi(rr, 1.0, s)).max())
+        f = synth.icosphere(level)
+        y, nw, sg = oracle_mod.sources(f.verts, f.tris, np.full(f.m, s), 6, 0)
+        vf.append(abs((nw * y).sum() / 3.0 - 4.0 * math.pi / 3.0))
+        bf.append(np.abs(oracle_mod.phi_grad(y, nw, sg, x)[0] - _ball_phi(rr, 1.0, s)).max())
+    for e in (vf, bf):   # flat: second order
+        assert 3.0 < e[0] / e[1] < 5.0 and 3.0 < e[1] / e[2] < 5.0
+    for e in (vq, bq):   # quadratic: at least third order, and far smaller
+        assert e[0] / e[1] > 7.0 and e[1] / e[2] > 7.0
+    assert vq[2] < 0.05 * vf[2] and bq[2] < 0.05 * bf[2]
+
+
+def _quad_solve_at(oracle_mod, q, src, tri, uv, tol=1e-14):
+    x0, hd, sl = oracle_mod.chart_nodes_quad_at(q.verts, q.tris6, tri, uv)
+    r = oracle_mod.solve_charts(*src, x0, hd, sl, tol=tol, max_iter=40)
+    assert (r["status"] == 0).all()
+    return r
+
+
+def test_quadratic_chart_frames_match_finite_differences(oracle_mod):
+    """eq. u_vector / U_vector_2 on a curved patch (T_u, T_v vary with u, v):
+    x_u, x_v equal central differences of the solved chart x(u, v)."""
+    q = synth.quadratic_icosphere(1)
+    src = oracle_mod.sources_quad(q.verts, q.tris6, None, 4, 0)
+    d = 1e-4
+    for j, u, v in ((3, 0.2, 0.3), (41, 0.55, 0.1), (77, 0.1, 0.7)):
+        tri = np.array([j] * 5, dtype=np.int32)
+        uv = np.array([[u, v], [u + d, v], [u - d, v], [u, v + d], [u, v - d]])
+        r = _quad_solve_at(oracle_mod, q, src, tri, uv)
+        _, g = oracle_mod.phi_grad(*src, r["x"][:1])
+        xu, xv, jac = oracle_mod.chart_frames_quad_at(q.verts, q.tris6, tri[:1], uv[:1], r["h"][:1], g)
+        fu = (r["x"][1] - r["x"][2]) / (2 * d)
+        fv = (r["x"][3] - r["x"][4]) / (2 * d)
+        scale = np.linalg.norm(fu) + np.linalg.norm(fv)
+        assert np.abs(xu[0] - fu).max() < 1e-7 * scale
+        assert np.abs(xv[0] - fv).max() < 1e-7 * scale
+        assert abs(jac[0] - np.linalg.norm(np.cross(fu, fv))) < 1e-7 * scale ** 2
+
+
+def test_quadratic_charts_close_and_flux_converges(oracle_mod):
+    """Charts on quadratic patches: the node at an edge's midpoint solved from
+    either neighbouring patch is the same point (T and the linear H agree on
+    the shared curved edge), and the Gauss flux error eps0 falls with the
+    chart order."""
+    q = synth.quadratic_icosphere(1)
+    src = oracle_mod.sources_quad(q.verts, q.tris6, None, 4, 0)
+    T = q.tris6
+    j = 5
+    a, b = T[j][0], T[j][1]
+    k = next(i for i in range(q.m) if i != j and a in T[i][:3] and b in T[i][:3])
+
+    def uv_of(i, p, r):
+        loc = [list(T[i][:3]).index(p), list(T[i][:3]).index(r)]
+        bary = np.zeros(3)
+        bary[loc] = 0.5
+        return np.array([[bary[1], bary[2]]])
+
+    xs = [_quad_solve_at(oracle_mod, q, src, np.array([i], dtype=np.int32), uv_of(i, a, b), 1e-15)["x"][0]
+          for i in (j, k)]
+    assert np.abs(xs[0] - xs[1]).max() < 1e-13
+    out = []
+    for n in (3, 5, 7):
+        tri, uv, w = oracle_mod.refined_nodes(q.m, n, np.zeros(q.m))
+        r = _quad_solve_at(oracle_mod, q, src, tri, uv)
+        _, g = oracle_mod.phi_grad(*src, r["x"])
+        _, _, jac = oracle_mod.chart_frames_quad_at(q.verts, q.tris6, tri, uv, r["h"], g)
+        out.append(abs(oracle_mod.gauss_flux_w(r["x"], g, jac, w, (0.05, -0.1, 0.02))))
+    assert out[0] > 100 * out[1] and out[1] > 100 * out[2]
+    assert out[2] < 1e-10
