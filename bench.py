@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=5.0)
     ap.add_argument("--tmax", type=float, default=1e4)
+    ap.add_argument("--serve-seconds", type=float, default=0.0,
+                    help="serve: cut the stream at this wall time (cancel what is still queued)")
     ap.add_argument("--tree-degree", type=int, default=0, help="treecode degree (0: library default)")
     ap.add_argument("--tree-theta", type=float, default=0.0, help="treecode opening parameter (0: default)")
     ap.add_argument("--tree-grid", type=int, default=0,
@@ -296,46 +298,88 @@ def bench_ellipsoids(args):
 def bench_serve(args):
     """A Poisson stream of mesh requests (ellipsoid, graded torus, bumped
     icosphere; triangles log-uniform in [1e3, tmax]), order-8 charts to 1e-10,
-    submitted at their arrival times to the continuous-batching server."""
+    submitted at their arrival times to the continuous-batching server.
+
+    Meshes come from a pool of templates (per generator, 24 sizes spread
+    log-uniformly over the range), each request taking its generator's
+    template nearest its size: building thousands of meshes of up to 5e5
+    triangles on the host would otherwise pace the stream.  With
+    --serve-seconds the stream is cut at that wall time: requests still
+    queued then are cancelled and the running ones finish; latencies are those
+    of the completed requests, and a queue that grows over the run is
+    reported as unstable, with the completion rate as the capacity."""
     import paper_1909_13356_gb300 as lsm
     import synth
     from synth.workloads import make_request_mesh
     reqs = synth.serve_stream_c5(nreq=args.requests, rate=args.rate, tmax=args.tmax)
-    meshes = [make_request_mesh(r) for r in reqs]
+    sizes = np.exp(np.linspace(np.log(1e3), np.log(args.tmax), 24))
+    templates = {}
+
+    def mesh_of(r):
+        k = int(np.argmin(np.abs(np.log(sizes) - np.log(r["T"]))))
+        key = (r["kind"], k)
+        if key not in templates:
+            templates[key] = make_request_mesh(dict(kind=r["kind"], T=int(sizes[k]), seed=1000 * r["kind"] + k))
+        return templates[key]
+
     ctx = lsm.Context(0, tree_grid=args.tree_grid)
     # warm the kernels once
-    m0 = meshes[0]
+    m0 = mesh_of(reqs[0])
     wm = ctx.upload(m0.verts, m0.tris, m0.sigma, n_gl=4)
     wm.solve_charts(order=8, tol=1e-10, precision=lsm.MIXED)
     wm.free()
+    for r in reqs:            # build the templates before the clock starts
+        mesh_of(r)
     srv = lsm.Server(ctx, slots=4)
     t_start = time.perf_counter()
     tickets = []
-    max_queue = 0
-    for r, m in zip(reqs, meshes):
+    queue_trace = []
+    lag = []
+    cut = args.serve_seconds if args.serve_seconds > 0 else float("inf")
+    for r in reqs:
         delay = r["arrival"] - (time.perf_counter() - t_start)
         if delay > 0:
             time.sleep(delay)
+        now = time.perf_counter() - t_start
+        if now > cut:
+            break
+        m = mesh_of(r)
         tickets.append(srv.submit(m.verts, m.tris, m.sigma, n_gl=4, order=8, tol=1e-10))
-        max_queue = max(max_queue, srv.info()["queued"])
+        lag.append(now - r["arrival"])
+        queue_trace.append((now, srv.info()["queued"]))
+    # past the cut: stop admitting, cancel what still waits, let the rest finish
+    while time.perf_counter() - t_start < min(cut, reqs[-1]["arrival"] + 1.0) and cut < float("inf"):
+        time.sleep(0.05)
+        queue_trace.append((time.perf_counter() - t_start, srv.info()["queued"]))
+    n_cancel = sum(1 for t in tickets if srv.cancel(t)) if cut < float("inf") else 0
     res = [srv.result(t) for t in tickets]
     wall = time.perf_counter() - t_start
     info = srv.info()
     srv.close()
-    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in res])
-    nodes = sum(r["stats"].n_converged for r in res if r["status"] == 0)
+    done = [r for r in res if r["status"] == 0]
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in done]) if done else np.array([np.nan])
+    nodes = sum(r["stats"].n_converged for r in done)
+    t_last_done = max((r["t_done_ms"] for r in done), default=0.0) / 1e3
     half = len(lat) // 2
+    q = np.array([v for _, v in queue_trace]) if queue_trace else np.zeros(1)
+    growing = bool(len(q) > 4 and q[-len(q) // 4:].mean() > 2.0 * max(1.0, q[:len(q) // 4].mean()))
+    stable = (not growing and n_cancel == 0 and
+              bool(np.median(lat[half:]) < 2.0 * np.median(lat[:half]) + 1000.0))
     print(json.dumps({
         "metric": "serve_latency_p50_ms", "value": float(np.percentile(lat, 50)), "unit": "ms", "n_gpus": 1,
-        "steps": len(res), "warmup": 1, "ms_per_step": wall * 1e3 / len(res), "higher_is_better": False,
+        "steps": len(done), "warmup": 1, "ms_per_step": wall * 1e3 / max(1, len(done)), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
-        "config": {"workload": "serve_stream", "requests": len(res), "rate_per_s": args.rate,
-                   "triangles": [1000, args.tmax], "order": 8, "tol": 1e-10, "slots": 4},
+        "config": {"workload": "serve_stream", "requests_in_stream": len(reqs), "requests_submitted": len(tickets),
+                   "rate_per_s": args.rate, "triangles": [1000, args.tmax], "order": 8, "tol": 1e-10, "slots": 4,
+                   "cut_s": args.serve_seconds or None, "mesh_templates": len(templates)},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "chart_nodes_per_s": nodes / wall, "failed": sum(r["status"] != 0 for r in res),
-        "max_queued": max_queue, "max_running": info["max_running"],
-        "peak_device_bytes": info["peak_in_use_bytes"],
-        "stable": bool(np.median(lat[half:]) < 2.0 * np.median(lat[:half]) + 1000.0),
+        "completed": len(done), "cancelled": n_cancel,
+        "failed": sum(r["status"] not in (0, -7) for r in res),
+        "chart_nodes_per_s": nodes / max(t_last_done, 1e-9),
+        "capacity_requests_per_s": len(done) / max(t_last_done, 1e-9),
+        "submission_lag_s_max": float(max(lag)) if lag else None,
+        "max_queued": int(q.max()), "queue_growing": growing, "max_running": info["max_running"],
+        "peak_device_bytes": info["peak_in_use_bytes"], "stable": stable,
     }))
 
 

@@ -58,6 +58,7 @@ typedef enum {
     LSM_E_MESH = -4,          /* not watertight / not conforming / orientation */
     LSM_E_NOT_CONVERGED = -5, /* reserved: per-node failures go to status arrays */
     LSM_E_TIMEOUT = -6,
+    LSM_E_CANCELLED = -7,     /* lsm_server_cancel took the request off the queue */
     LSM_PENDING = 1           /* lsm_server_poll: the request has not finished */
 } lsm_status;
 
@@ -529,6 +530,10 @@ typedef struct {
 int lsm_server_create(lsm_ctx* ctx, int slots, int64_t hbm_budget_bytes, lsm_server** out);
 int lsm_server_submit(lsm_server* server, const lsm_request* request, int64_t* ticket);
 int lsm_server_poll(lsm_server* server, int64_t ticket, int wait, lsm_result* out);
+/* Take a request that is still queued off the queue: its result is then
+ * final with status LSM_E_CANCELLED.  Returns LSM_OK, or LSM_E_INVALID_ARG
+ * for an unknown ticket or a request that has already started. */
+int lsm_server_cancel(lsm_server* server, int64_t ticket);
 int lsm_server_release(lsm_server* server, int64_t ticket);
 int lsm_server_info(lsm_server* server, lsm_server_info_t* out);
 int lsm_server_destroy(lsm_server* server);

@@ -32,7 +32,8 @@ NODE_ZERODERIV = 2
 NODE_NONFINITE = 3
 NODE_CLAMPED_BIT = 256
 
-_ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVERGED", -6: "TIMEOUT"}
+_ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVERGED", -6: "TIMEOUT",
+           -7: "CANCELLED"}
 
 # every symbol include/lsm.h declares
 EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "lsm_set_profiling",
@@ -42,7 +43,8 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_server_info", "lsm_server_destroy", "lsm_autotune", "lsm_chart_frames", "lsm_gauss_flux",
            "lsm_mesh_upload_sigmax", "lsm_mesh_get_sigma0", "lsm_eval_sigma", "lsm_eval_hessian",
            "lsm_chart_curvature", "lsm_refined_nodes", "lsm_solve_charts_nodes", "lsm_chart_frames_nodes",
-           "lsm_gauss_flux_nodes", "lsm_check_error", "lsm_test_inject_wait_timeout", "lsm_measure_peaks")
+           "lsm_gauss_flux_nodes", "lsm_check_error", "lsm_test_inject_wait_timeout", "lsm_measure_peaks",
+           "lsm_server_cancel")
 
 
 class LsmError(RuntimeError):
@@ -166,6 +168,7 @@ def load(build_if_needed: bool = True):
         L.lsm_server_submit.argtypes = [P, ctypes.POINTER(_Request), ctypes.POINTER(I64)]
         L.lsm_server_poll.argtypes = [P, I64, I32, ctypes.POINTER(_Result)]
         L.lsm_server_release.argtypes = [P, I64]
+        L.lsm_server_cancel.argtypes = [P, I64]
         L.lsm_server_info.argtypes = [P, ctypes.POINTER(_ServerInfo)]
         L.lsm_server_destroy.argtypes = [P]
         L.lsm_batch_create.argtypes = [P, ctypes.POINTER(P), I32, P, ctypes.POINTER(P)]
@@ -638,6 +641,11 @@ class Server:
         if release:
             self.ctx._L.lsm_server_release(self._h, int(ticket))
         return out
+
+    def cancel(self, ticket: int) -> bool:
+        """Take a still-queued request off the queue (lsm_server_cancel);
+        False when it has already started or finished."""
+        return self.ctx._L.lsm_server_cancel(self._h, int(ticket)) == 0
 
     def info(self) -> dict:
         inf = _ServerInfo()

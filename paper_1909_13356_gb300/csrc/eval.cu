@@ -488,6 +488,58 @@ __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const 
     dh += dl;
 }
 
+// One source's far-tile Phi term for one target in float-float (the far
+// branch of ff_pair, with fewer instructions): the tile-local pair
+// difference r and |r|^2 as float pairs, then 1/|r|^3 from the hardware
+// estimate r0 = rsqrt(|r|^2) and its relative defect
+//   delta = 1 - |r|^2 r0^2 = (1 - t r0) - (t_err + |r|^2_lo r0) r0,
+// with t + t_err = |r|^2_hi r0 exactly (an FMA), as
+//   1/|r|^3 = r0^3 (1 - delta)^(-3/2) = r0^3 (1 + 3/2 delta + 15/8 delta^2),
+// r0^3 a float pair (r0^2 is exact in two floats); the next term, 35/16
+// delta^3 ~ 1e-20, is below float-float precision.  nw . r in float-float,
+// and the product.  Returns for the gradient, in FP32, the high parts of r
+// and nw . r, r0^2 and r0^3 (the gradient keeps mixed accuracy).
+__device__ __forceinline__ void ff_far_pair(const float4& y, const float4& n, const float4& yl, const float4& nl,
+                                            const float* qh, const float* ql, float& qhi, float& qlo, float& dxh,
+                                            float& dyh, float& dzh, float& dh, float& ri2, float& ri3)
+{
+    float dxl, dyl, dzl, e;
+    two_diff(y.x, qh[0], dxh, e);
+    dxl = e + (yl.x - ql[0]);
+    two_diff(y.y, qh[1], dyh, e);
+    dyl = e + (yl.y - ql[1]);
+    two_diff(y.z, qh[2], dzh, e);
+    dzl = e + (yl.z - ql[2]);
+    const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
+    float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
+    e0 = fmaf(2.0f * dxh, dxl, e0);
+    e1 = fmaf(2.0f * dyh, dyl, e1);
+    e2 = fmaf(2.0f * dzh, dzl, e2);
+    float s01, t01, t2, rh;
+    two_sum(p0, p1, s01, t01);
+    two_sum(s01, p2, rh, t2);
+    const float rl = ((e0 + e1) + e2) + (t01 + t2);
+    const float r0 = rsqrtf(rh);
+    const float t = rh * r0;
+    const float te = fmaf(rh, r0, -t);
+    const float u = fmaf(rl, r0, te);
+    const float delta = fmaf(-u, r0, fmaf(-t, r0, 1.0f));
+    const float a = r0 * r0, ae = fmaf(r0, r0, -a);
+    const float fHh = a * r0;
+    const float c3l = fmaf(ae, r0, fmaf(a, r0, -fHh));
+    const float fHl = fmaf(fHh, delta * fmaf(1.875f, delta, 1.5f), c3l);
+    const float d0 = n.x * dxh, d1 = n.y * dyh, d2 = n.z * dzh;
+    const float f0 = fmaf(n.x, dxh, -d0), f1 = fmaf(n.y, dyh, -d1), f2 = fmaf(n.z, dzh, -d2);
+    float sd, u1, u2;
+    two_sum(d0, d1, sd, u1);
+    two_sum(sd, d2, dh, u2);
+    const float dl = fmaf(n.x, dxl, fmaf(n.y, dyl, fmaf(n.z, dzl, fmaf(nl.x, dxh, fmaf(nl.y, dyh,
+                     fmaf(nl.z, dzh, ((f0 + f1) + f2) + (u1 + u2)))))));
+    ff_mul(dh, dl, fHh, fHl, qhi, qlo);
+    ri2 = a;
+    ri3 = fHh;
+}
+
 // ---------------------------------------------------------------- mixed kernel
 template <int TPT, bool SIGX>
 __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __restrict__ spos,
@@ -1236,22 +1288,26 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                     // the pair's a: the source's, or the target's in sigma(x) mode
                     const float4 y = SIGX ? make_float4(y0.x, y0.y, y0.z, ta_h) : y0;
                     const float4 yl = SIGX ? make_float4(yl0.x, yl0.y, yl0.z, ta_l) : yl0;
-                    float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
-                    ff_pair<true>(y, n, yl, nl, qh, ql, FAR, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
-                    float sph, tph;
-                    two_sum(cph, qh_, sph, tph);
-                    cph = sph;
-                    cpl += tph + ql_;
-                    // grad from the high parts (FP32)
+                    float qh_, ql_, dxh, dyh, dzh, rh, dh;
                     if constexpr (FAR) {
-                        const float ri = r0;
-                        const float ri2 = ri * ri;
-                        const float ri3 = ri2 * ri;
+                        float ri2, ri3;
+                        ff_far_pair(y, n, yl, nl, qh, ql, qh_, ql_, dxh, dyh, dzh, dh, ri2, ri3);
+                        float sph, tph;
+                        two_sum(cph, qh_, sph, tph);
+                        cph = sph;
+                        cpl += tph + ql_;
+                        // grad from the high parts (FP32)
                         const float tq = 3.0f * dh * ri3 * ri2;
                         g[0] = fmaf(tq, dxh, fmaf(-n.x, ri3, g[0]));
                         g[1] = fmaf(tq, dyh, fmaf(-n.y, ri3, g[1]));
                         g[2] = fmaf(tq, dzh, fmaf(-n.z, ri3, g[2]));
                     } else {
+                        float r0;
+                        ff_pair<true>(y, n, yl, nl, qh, ql, false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
+                        float sph, tph;
+                        two_sum(cph, qh_, sph, tph);
+                        cph = sph;
+                        cpl += tph + ql_;
                         float fH, FK;
                         radial_tab32(rh, y.w, s_htab, fH, FK);
                         const float tq = dh * FK;

@@ -11,6 +11,7 @@
 // the caller releases them.
 #include <chrono>
 #include <condition_variable>
+#include <algorithm>
 #include <deque>
 #include <map>
 #include <memory>
@@ -230,6 +231,33 @@ int lsm_server_poll(lsm_server* sv, int64_t ticket, int wait, lsm_result* out)
     out->h = j->h.empty() ? nullptr : j->h.data();
     out->node_status = j->node_status.empty() ? nullptr : j->node_status.data();
     out->error = j->err.c_str();
+    return LSM_OK;
+}
+
+int lsm_server_cancel(lsm_server* sv, int64_t ticket)
+{
+    if (!sv) return LSM_E_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->jobs.find(ticket);
+        if (it == sv->jobs.end()) return LSM_E_INVALID_ARG;
+        auto q = std::find(sv->queue.begin(), sv->queue.end(), it->second);
+        if (q == sv->queue.end()) return LSM_E_INVALID_ARG;   // already started or finished
+        Job& j = **q;
+        sv->queue.erase(q);
+        j.status = LSM_E_CANCELLED;
+        j.err = "cancelled while queued";
+        j.t_start = j.t_done = ms_since(sv);
+        j.done = true;
+        j.verts.clear();
+        j.verts.shrink_to_fit();
+        j.tris.clear();
+        j.tris.shrink_to_fit();
+        j.sigma.clear();
+        j.sigma.shrink_to_fit();
+    }
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
     return LSM_OK;
 }
 

@@ -102,3 +102,22 @@ def test_failing_requests_keep_their_own_messages(setup):
     # every request of a kind got that kind's message, and the kinds differ
     assert len(msgs["open"]) == 1 and len(msgs["flip"]) == 1
     assert msgs["open"] != msgs["flip"]
+
+
+def test_cancel_takes_queued_requests_off_the_queue(setup):
+    """With one slot the later requests wait in the queue; cancelling them
+    finalises them as cancelled, the others still run, and a request that has
+    already finished cannot be cancelled."""
+    lsm, ctx, ms, alone = setup
+    srv = lsm.Server(ctx, slots=1)
+    tickets = [srv.submit(m.verts, m.tris, m.sigma, n_gl=4, order=8, tol=1e-10) for m in ms[:4]]
+    cancelled = [t for t in tickets[2:] if srv.cancel(t)]
+    assert cancelled, "the last requests should still have been queued"
+    for k, t in enumerate(tickets):
+        r = srv.result(t, release=False)
+        if t in cancelled:
+            assert r["status"] == -7 and "cancel" in r["error"]
+        else:
+            _check(r, alone[k])
+            assert not srv.cancel(t)
+    srv.close()
