@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fp64-check", type=int, default=0,
                     help="icosphere: also compare with the FP64 direct sum on this many targets")
+    ap.add_argument("--no-tune", action="store_true", help="ellipsoids: skip the batch autotuner")
     ap.add_argument("--no-paths", action="store_true",
                     help="skip the float-float and FP64 path legs after the timed region")
     ap.add_argument("--replicas", action="store_true",
@@ -264,15 +265,24 @@ def bench_ellipsoids(args):
     meshes = [ctx.upload(m.verts, m.tris, m.sigma, n_gl=4) for m in w["meshes"]]
     batch = lsm.Batch(ctx, meshes)
     tol = 1e-10
+    t0 = time.perf_counter()
+    tune = batch.autotune(order=6, err_budget=4e-8) if not args.no_tune else None
+    t_tune = time.perf_counter() - t0
     for _ in range(args.warmup):
         batch.solve_charts(order=6, tol=tol, precision=lsm.MIXED, use_graph=True, device_out=True)
     torch.cuda.synchronize()
     l0 = ctx.launch_count
-    t0 = time.perf_counter()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(0)
+    clk.start()
+    a.record()
     for _ in range(args.steps):
         x, h, st, stats = batch.solve_charts(order=6, tol=tol, precision=lsm.MIXED, use_graph=True, device_out=True)
+    b.record()
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / args.steps
+    clocks = clk.stop()
+    dt = a.elapsed_time(b) / 1e3 / args.steps
     launches = (ctx.launch_count - l0) // args.steps
     # the same work mesh by mesh, for comparison
     t1 = time.perf_counter()
@@ -291,6 +301,9 @@ def bench_ellipsoids(args):
         "newton": {"sweeps": stats.iterations, "active_per_iter": stats.active_per_iter,
                    "n_failed": stats.n_failed, "max_residual": stats.max_residual},
         "gpu_launches_per_step": launches,
+        "graph_replays_per_step": (stats.iterations + 1) // 2,
+        "autotune": tune, "autotune_s": t_tune,
+        "clocks": clocks,
         "unbatched": {"seconds": dt_alone, "nodes_per_s": n_alone / dt_alone},
     }))
 

@@ -265,6 +265,26 @@ int lsm_mesh_upload(lsm_ctx* ctx, const double* verts, int64_t nv, const int32_t
  * reject such meshes.  Errors: as lsm_mesh_upload. */
 int lsm_mesh_upload_sigmax(lsm_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                            double lambda, double sigma0, const lsm_quad* rule, void* stream, lsm_mesh** out);
+/* Upload a skeleton of quadratic (6-node curvilinear) patches (Sec. 5,
+ * quadratic skeletons).  Patch j is the second-order Lagrange interpolant
+ * T^j(u,v) on the standard simplex through its corners P1, P2, P3
+ * (counter-clockwise seen from outside) and one node on each edge: P4 on
+ * P1-P2, P5 on P2-P3, P6 on P3-P1.  Everything else is built as for flat
+ * triangles with the patch's own tangents T_u, T_v and normal
+ * N(u,v) = T_u x T_v: source nodes y = T(u_k, v_k) with nw = w_k N(u_k, v_k);
+ * sigma_j = 0.5 sqrt(2 area_j) with the curved area (or the given sigma);
+ * vertex pseudonormals (eq. mkvertexpn) from the corners' unit normals and
+ * the angles between their two edges' tangents; H^j linear in (u, v) between
+ * the corner pseudonormals (eq. mkpseudovec); charts x = T^j + h H^j.
+ *   verts  double[nv][3]: corners and edge nodes
+ *   tris6  int32[nt][6] (P1, P2, P3, P4, P5, P6); the two patches on an edge
+ *          share its edge node
+ * Charts, frames and the Gauss flux (lsm_solve_charts*, lsm_chart_frames*,
+ * lsm_gauss_flux*), Phi, grad Phi and the Hessian work as for flat meshes;
+ * batches and lsm_chart_curvature reject such meshes.  Errors: as
+ * lsm_mesh_upload (LSM_E_MESH also for inconsistent edge nodes). */
+int lsm_mesh_upload_quadratic(lsm_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris6, int64_t nt,
+                              const double* sigma, const lsm_quad* rule, void* stream, lsm_mesh** out);
 /* sigma(x) [n] and grad sigma(x) [n][3] (may be NULL) at n targets of a mesh
  * uploaded with lsm_mesh_upload_sigmax (eq. sigma2); pointers as in
  * lsm_eval_phi_grad.  Errors: LSM_E_INVALID_ARG (also for other meshes),
@@ -419,6 +439,11 @@ int lsm_gauss_flux_nodes(lsm_mesh* mesh, int64_t n, const int32_t* tri, const do
  *   out      the choice and what was measured; may be NULL
  * The choice is stored with the mesh and used by its later mixed
  * evaluations and chart solves (it overrides the context's tree options).
+ * With that far field it then chooses the mixed kernel's near-field radius
+ * (6.4, 6.5 or 7 sigma: those where the smoothed kernel differs from the
+ * Laplace double layer by at most 1e-8 relative, Sec. 4.4) and its target
+ * tile (128 or 256 targets per thread block), again the fastest within the
+ * budget.
  * Cost: one float-float evaluation of the sample, and a tree build plus two
  * mixed evaluations of it per candidate.  Synchronises `stream`.
  * Errors: LSM_E_INVALID_ARG (n < 1, bad budget), LSM_E_OOM, LSM_E_CUDA. */
@@ -432,6 +457,9 @@ typedef struct {
     double ms_sample;         /* its mixed-evaluation time on the sample */
     double ms_direct;         /* the direct far field's time on the sample */
     double err_direct;        /* and its error */
+    double cutoff;            /* chosen near-field radius of the mixed kernel, in sigma */
+    int32_t targets_per_block;/* chosen target tile of the mixed kernel (128 or 256) */
+    int32_t reserved;
 } lsm_tune_result;
 int lsm_autotune(lsm_mesh* mesh, const double* x, int64_t n, double err_budget, lsm_tune_result* out,
                  void* stream);
@@ -477,6 +505,20 @@ int lsm_batch_free(lsm_batch* batch);
  */
 int lsm_batch_solve_charts(lsm_batch* batch, int order, double tol, int max_iter, int precision, int use_graph,
                            double* x_out, double* h_out, int32_t* status, lsm_solve_stats* stats, void* stream);
+
+/*
+ * Autotuner of a batch (this library's addition, as lsm_autotune): chooses
+ * the mixed kernel's near-field radius (6.4, 6.5 or 7 sigma, as
+ * lsm_autotune) and target tile (128 or 256 targets per thread block) for the
+ * batch's later lsm_batch_solve_charts calls: the fastest within err_budget
+ * of the float-float evaluation, measured on the chart nodes' starting
+ * points of every stride-th mesh (about 64 meshes), in the work items the
+ * batched solve uses.  Batches use the direct far field, so there is no
+ * treecode to tune.  `out` (may be NULL) reports the choice: use_tree = 0,
+ * cutoff, targets_per_block, err_phi and ms_sample of the choice, ms_direct
+ * and err_direct of the default settings.  Synchronises `stream`.
+ * Errors: LSM_E_INVALID_ARG, LSM_E_OOM, LSM_E_CUDA. */
+int lsm_batch_autotune(lsm_batch* batch, int order, double err_budget, lsm_tune_result* out, void* stream);
 
 /*
  * Serving: a continuous-batching request server over one context (the paper

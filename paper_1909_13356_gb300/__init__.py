@@ -44,7 +44,8 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_mesh_upload_sigmax", "lsm_mesh_get_sigma0", "lsm_eval_sigma", "lsm_eval_hessian",
            "lsm_chart_curvature", "lsm_refined_nodes", "lsm_solve_charts_nodes", "lsm_chart_frames_nodes",
            "lsm_gauss_flux_nodes", "lsm_check_error", "lsm_test_inject_wait_timeout", "lsm_measure_peaks",
-           "lsm_server_cancel")
+           "lsm_server_cancel", "lsm_batch_autotune",
+           "lsm_mesh_upload_quadratic")
 
 
 class LsmError(RuntimeError):
@@ -111,7 +112,8 @@ class _Peaks(ctypes.Structure):
 class _TuneResult(ctypes.Structure):
     _fields_ = [("use_tree", ctypes.c_int32), ("tree_degree", ctypes.c_int32), ("tree_theta", ctypes.c_float),
                 ("candidates", ctypes.c_int32), ("sample_targets", ctypes.c_int64), ("err_phi", ctypes.c_double),
-                ("ms_sample", ctypes.c_double), ("ms_direct", ctypes.c_double), ("err_direct", ctypes.c_double)]
+                ("ms_sample", ctypes.c_double), ("ms_direct", ctypes.c_double), ("err_direct", ctypes.c_double),
+                ("cutoff", ctypes.c_double), ("targets_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _ServerInfo(ctypes.Structure):
@@ -175,7 +177,9 @@ def load(build_if_needed: bool = True):
         L.lsm_batch_free.argtypes = [P]
         L.lsm_batch_solve_charts.argtypes = [P, I32, D, I32, I32, I32, P, P, P, ctypes.POINTER(_Stats), P]
         L.lsm_autotune.argtypes = [P, P, I64, D, ctypes.POINTER(_TuneResult), P]
+        L.lsm_batch_autotune.argtypes = [P, I32, D, ctypes.POINTER(_TuneResult), P]
         L.lsm_chart_frames.argtypes = [P, I32, P, P, P, P, P, P]
+        L.lsm_mesh_upload_quadratic.argtypes = [P, P, I64, P, I64, P, ctypes.POINTER(_Quad), P, ctypes.POINTER(P)]
         L.lsm_mesh_upload_sigmax.argtypes = [P, P, I64, P, I64, D, D, ctypes.POINTER(_Quad), P, ctypes.POINTER(P)]
         L.lsm_mesh_get_sigma0.argtypes = [P, ctypes.POINTER(D)]
         L.lsm_eval_sigma.argtypes = [P, P, I64, P, P, P]
@@ -320,6 +324,13 @@ class Context:
     def upload(self, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0, stream=None) -> "Mesh":
         return Mesh(self, verts, tris, sigma, n_gl, subdiv, stream)
 
+    def upload_quadratic(self, verts, tris6, sigma=None, n_gl: int = 4, subdiv: int = 0, stream=None) -> "Mesh":
+        """A skeleton of 6-node quadratic patches (lsm_mesh_upload_quadratic)."""
+        t = _as(tris6, np.int32)
+        if t.ndim != 2 or t.shape[1] != 6:
+            raise ValueError("tris6 must be [m, 6]")
+        return Mesh(self, verts, t, sigma, n_gl, subdiv, stream)
+
     def upload_sigma_x(self, verts, tris, lam: float = 0.0, sigma0: float = 0.0, n_gl: int = 4, subdiv: int = 0,
                        stream=None) -> "Mesh":
         """A mesh with the target-dependent sigma(x) of eq. sigma2."""
@@ -343,7 +354,8 @@ class Mesh:
     def __init__(self, ctx: Context, verts, tris, sigma=None, n_gl: int = 4, subdiv: int = 0,
                  stream=None, sigma_x: bool = False, lam: float = 0.0, sigma0: float = 0.0):
         """sigma_x=True: target-dependent sigma(x) (lsm_mesh_upload_sigmax, with
-        lambda and sigma0, 0 for the defaults); else per-triangle sigma."""
+        lambda and sigma0, 0 for the defaults); else per-triangle sigma.
+        tris [m, 6]: quadratic patches (lsm_mesh_upload_quadratic)."""
         self.ctx = ctx
         v = _as(verts, np.float64)
         t = _as(tris, np.int32)
@@ -353,6 +365,10 @@ class Mesh:
             rc = ctx._L.lsm_mesh_upload_sigmax(ctx._h, _ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]),
                                                float(lam), float(sigma0), ctypes.byref(q),
                                                _stream_handle(stream), ctypes.byref(h))
+        elif t.shape[1] == 6:
+            s = _as(sigma, np.float64) if sigma is not None else None
+            rc = ctx._L.lsm_mesh_upload_quadratic(ctx._h, _ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]),
+                                                  _ptr(s), ctypes.byref(q), _stream_handle(stream), ctypes.byref(h))
         else:
             s = _as(sigma, np.float64) if sigma is not None else None
             rc = ctx._L.lsm_mesh_upload(ctx._h, _ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]),
@@ -409,14 +425,15 @@ class Mesh:
 
     def autotune(self, x, err_budget: float = 5e-8, stream=None) -> dict:
         """Choose this mesh's mixed-path far field (direct, or the treecode's
-        degree and opening parameter) on a sample of the targets x [n, 3]
-        (lsm_autotune).  Returns the choice and the measured time and error."""
+        degree and opening parameter), then its near-field radius and target
+        tile, on a sample of the targets x [n, 3] (lsm_autotune).  Returns the
+        choice and the measured time and error."""
         xs = _as(x, np.float64)
         r = _TuneResult()
         rc = self.ctx._L.lsm_autotune(self._h, _ptr(xs), int(xs.shape[0]), float(err_budget), ctypes.byref(r),
                                       _stream_handle(stream))
         self.ctx._check(rc)
-        return {k: getattr(r, k) for k, _ in _TuneResult._fields_}
+        return {k: getattr(r, k) for k, _ in _TuneResult._fields_ if k != "reserved"}
 
     def chart_frames(self, order: int, h, grad, stream=None):
         """Local coordinates x_u, x_v [N, 3] and |x_u x x_v| [N] of the solved
@@ -588,6 +605,14 @@ class Batch:
                                                 ctypes.byref(stats), _stream_handle(stream))
         self.ctx._check(rc)
         return x, h, st, _stats(stats)
+
+    def autotune(self, order: int = 6, err_budget: float = 5e-8, stream=None) -> dict:
+        """Mixed-kernel near-field radius and target tile for this batch
+        (lsm_batch_autotune), measured on a sample of its meshes' nodes."""
+        r = _TuneResult()
+        self.ctx._check(self.ctx._L.lsm_batch_autotune(self._h, int(order), float(err_budget), ctypes.byref(r),
+                                                        _stream_handle(stream)))
+        return {k: getattr(r, k) for k, _ in _TuneResult._fields_ if k != "reserved"}
 
     def free(self):
         if getattr(self, "_h", None):

@@ -208,6 +208,131 @@ int check_flag(Ctx* ctx, cudaStream_t st)
     return LSM_OK;
 }
 
+// Edge nodes of quadratic patches: in range, never a patch corner, every
+// vertex a corner or an edge node, and the two patches on an edge sharing
+// its node (directed edge (a, b) and its reverse carry the same node).
+bool check_edge_nodes(const int32_t* t6, int64_t m, int64_t nv, std::string& why)
+{
+    std::vector<uint8_t> role((size_t)nv, 0);   // 1 corner, 2 edge node
+    for (int64_t j = 0; j < m; j++)
+        for (int k = 0; k < 3; k++) role[t6[6 * j + k]] |= 1;
+    std::vector<std::pair<uint64_t, int32_t>> e;
+    e.reserve(3 * (size_t)m);
+    for (int64_t j = 0; j < m; j++) {
+        for (int k = 0; k < 3; k++) {
+            const int32_t a = t6[6 * j + k], b = t6[6 * j + (k + 1) % 3], mid = t6[6 * j + 3 + k];
+            if (mid < 0 || mid >= nv) {
+                why = "edge node index out of range";
+                return false;
+            }
+            role[mid] |= 2;
+            e.push_back({(uint64_t)a * (uint64_t)nv + (uint64_t)b, mid});
+        }
+    }
+    for (int64_t i = 0; i < nv; i++) {
+        if (role[i] == 3) {
+            why = "a vertex is both a patch corner and an edge node";
+            return false;
+        }
+        if (role[i] == 0) {
+            why = "vertex not used by any patch";
+            return false;
+        }
+    }
+    std::sort(e.begin(), e.end());
+    for (const auto& d : e) {
+        const uint64_t a = d.first / (uint64_t)nv, b = d.first % (uint64_t)nv;
+        auto it = std::lower_bound(e.begin(), e.end(), std::make_pair(b * (uint64_t)nv + a, INT32_MIN));
+        if (it == e.end() || it->first != b * (uint64_t)nv + a || it->second != d.second) {
+            why = "the two patches on an edge do not share its edge node";
+            return false;
+        }
+    }
+    return true;
+}
+
+// Upload after the topology checks: tris holds the triangles' (or patches')
+// corners, tris6 (host, or null for flat triangles) the quadratic patches.
+int upload_common(Ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tris6,
+                  const double* sigma, const lsm_quad* rule, cudaStream_t st, lsm_mesh** out)
+{
+    lsm_quad q = rule ? *rule : lsm_quad{4, 0};
+    if (q.n_gl < 1 || q.n_gl > 32 || q.subdiv < 0 || q.subdiv > 5) {
+        ctx->err = "mesh_upload: rule needs 1 <= n_gl <= 32 and 0 <= subdiv <= 5";
+        return LSM_E_INVALID_ARG;
+    }
+    const int nq = q.n_gl * q.n_gl * (1 << (2 * q.subdiv));
+    const int64_t ns = nt * (int64_t)nq;
+    if (ns >= ((int64_t)1 << 31) - kTile || nv >= ((int64_t)1 << 31)) {
+        ctx->err = "mesh_upload: too many source nodes (limit 2^31)";
+        return LSM_E_INVALID_ARG;
+    }
+    lsm_mesh* mh = new (std::nothrow) lsm_mesh();
+    if (!mh) return LSM_E_OOM;
+    Mesh* me = &mh->m;
+    me->ctx = ctx;
+    me->nv = nv;
+    me->m = nt;
+    me->nq = nq;
+    me->rule = q;
+    me->ns = ns;   // tiles (and the padded source arrays) are laid out by build_mesh_device
+    auto fail = [&](int rc) {
+        lsm_mesh_free(mh);
+        return rc;
+    };
+    auto alloc = [&](auto** p, size_t count) -> bool {
+        using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
+        const size_t bytes = count * sizeof(T);
+        if (cudaMalloc((void**)p, bytes) != cudaSuccess) return false;
+        me->bytes += bytes;
+        return true;
+    };
+    if (!alloc(&me->verts, 3 * nv) || !alloc(&me->tris, 3 * nt) || !alloc(&me->tri_sigma, nt) ||
+        !alloc(&me->tri_n, 3 * nt) || !alloc(&me->vpn, 3 * nv) || (tris6 && !alloc(&me->tris6, 6 * nt))) {
+        cudaGetLastError();
+        ctx->err = "mesh_upload: out of device memory";
+        return fail(LSM_E_OOM);
+    }
+    const cudaMemcpyKind kv = is_device_ptr(verts) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kt = is_device_ptr(tris) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(me->verts, verts, sizeof(double) * 3 * nv, kv, st) != cudaSuccess ||
+        cudaMemcpyAsync(me->tris, tris, sizeof(int32_t) * 3 * nt, kt, st) != cudaSuccess ||
+        (tris6 && cudaMemcpyAsync(me->tris6, tris6, sizeof(int32_t) * 6 * nt, cudaMemcpyHostToDevice, st) !=
+                      cudaSuccess)) {
+        ctx->err = "mesh_upload: copy failed";
+        return fail(LSM_E_CUDA);
+    }
+    int rc;
+    {
+        Scratch s(st);
+        const double* sig_d = nullptr;
+        rc = to_device(ctx, s, sigma, (size_t)nt, &sig_d, st);
+        if (rc) return fail(rc);
+        std::vector<double> rh((size_t)nq * 3);
+        simplex_rule_host(q.n_gl, q.subdiv, rh.data());
+        double* rd;
+        if (s.get(&rd, rh.size()) != cudaSuccess ||
+            cudaMemcpyAsync(rd, rh.data(), sizeof(double) * rh.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            ctx->err = "mesh_upload: rule upload failed";
+            return fail(LSM_E_CUDA);
+        }
+        double red[8];
+        rc = build_mesh_device(ctx, me, sig_d, rd, red, st);
+        if (rc == LSM_E_MESH) {
+            ctx->err = red[3] > 0 ? "mesh_upload: zero-area triangle or sigma <= 0"
+                     : red[4] > 0 ? "mesh_upload: vertex not used by any triangle"
+                                  : "mesh_upload: signed volume <= 0 (triangles must be counter-clockwise seen from outside)";
+        }
+        if (rc) return fail(rc);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        ctx->err = "mesh_upload: stream failed";
+        return fail(LSM_E_CUDA);
+    }
+    *out = mh;
+    return LSM_OK;
+}
+
 }  // namespace
 }  // namespace lsm
 
@@ -375,19 +500,7 @@ int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* 
         ctx->err = "mesh_upload: need at least 3 vertices and 4 triangles";
         return LSM_E_INVALID_ARG;
     }
-    lsm_quad q = rule ? *rule : lsm_quad{4, 0};
-    if (q.n_gl < 1 || q.n_gl > 32 || q.subdiv < 0 || q.subdiv > 5) {
-        ctx->err = "mesh_upload: rule needs 1 <= n_gl <= 32 and 0 <= subdiv <= 5";
-        return LSM_E_INVALID_ARG;
-    }
-    const int nq = q.n_gl * q.n_gl * (1 << (2 * q.subdiv));
-    const int64_t ns = nt * (int64_t)nq;
-    if (ns >= ((int64_t)1 << 31) - kTile || nv >= ((int64_t)1 << 31)) {
-        ctx->err = "mesh_upload: too many source nodes (limit 2^31)";
-        return LSM_E_INVALID_ARG;
-    }
     DeviceGuard g(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
     // topology on the host
     std::vector<int32_t> htris;
     const int32_t* tp = tris;
@@ -401,68 +514,36 @@ int lsm_mesh_upload(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* 
         ctx->err = "mesh_upload: " + why;
         return LSM_E_MESH;
     }
-    lsm_mesh* mh = new (std::nothrow) lsm_mesh();
-    if (!mh) return LSM_E_OOM;
-    Mesh* me = &mh->m;
-    me->ctx = ctx;
-    me->nv = nv;
-    me->m = nt;
-    me->nq = nq;
-    me->rule = q;
-    me->ns = ns;   // tiles (and the padded source arrays) are laid out by build_mesh_device
-    auto fail = [&](int rc) {
-        lsm_mesh_free(mh);
-        return rc;
-    };
-    auto alloc = [&](auto** p, size_t count) -> bool {
-        using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
-        const size_t bytes = count * sizeof(T);
-        if (cudaMalloc((void**)p, bytes) != cudaSuccess) return false;
-        me->bytes += bytes;
-        return true;
-    };
-    if (!alloc(&me->verts, 3 * nv) || !alloc(&me->tris, 3 * nt) || !alloc(&me->tri_sigma, nt) ||
-        !alloc(&me->tri_n, 3 * nt) || !alloc(&me->vpn, 3 * nv)) {
-        cudaGetLastError();
-        ctx->err = "mesh_upload: out of device memory";
-        return fail(LSM_E_OOM);
+    return upload_common(ctx, verts, nv, tris, nt, nullptr, sigma, rule, (cudaStream_t)stream, out);
+}
+
+int lsm_mesh_upload_quadratic(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* tris6, int64_t nt,
+                              const double* sigma, const lsm_quad* rule, void* stream, lsm_mesh** out)
+{
+    if (!c || !out) return LSM_E_INVALID_ARG;
+    *out = nullptr;
+    Ctx* ctx = &c->c;
+    if (!verts || !tris6 || nv < 6 || nt < 4) {
+        ctx->err = "mesh_upload_quadratic: need at least 6 vertices and 4 patches";
+        return LSM_E_INVALID_ARG;
     }
-    const cudaMemcpyKind kv = is_device_ptr(verts) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const cudaMemcpyKind kt = is_device_ptr(tris) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (cudaMemcpyAsync(me->verts, verts, sizeof(double) * 3 * nv, kv, st) != cudaSuccess ||
-        cudaMemcpyAsync(me->tris, tris, sizeof(int32_t) * 3 * nt, kt, st) != cudaSuccess) {
-        ctx->err = "mesh_upload: copy failed";
-        return fail(LSM_E_CUDA);
+    DeviceGuard g(ctx->device);
+    std::vector<int32_t> h6;
+    const int32_t* t6 = tris6;
+    if (is_device_ptr(tris6)) {
+        h6.resize(6 * (size_t)nt);
+        LSM_CUDA_TRY(ctx, cudaMemcpy(h6.data(), tris6, sizeof(int32_t) * 6 * nt, cudaMemcpyDeviceToHost));
+        t6 = h6.data();
     }
-    int rc;
-    {
-        Scratch s(st);
-        const double* sig_d = nullptr;
-        rc = to_device(ctx, s, sigma, (size_t)nt, &sig_d, st);
-        if (rc) return fail(rc);
-        std::vector<double> rh((size_t)nq * 3);
-        simplex_rule_host(q.n_gl, q.subdiv, rh.data());
-        double* rd;
-        if (s.get(&rd, rh.size()) != cudaSuccess ||
-            cudaMemcpyAsync(rd, rh.data(), sizeof(double) * rh.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
-            ctx->err = "mesh_upload: rule upload failed";
-            return fail(LSM_E_CUDA);
-        }
-        double red[8];
-        rc = build_mesh_device(ctx, me, sig_d, rd, red, st);
-        if (rc == LSM_E_MESH) {
-            ctx->err = red[3] > 0 ? "mesh_upload: zero-area triangle or sigma <= 0"
-                     : red[4] > 0 ? "mesh_upload: vertex not used by any triangle"
-                                  : "mesh_upload: signed volume <= 0 (triangles must be counter-clockwise seen from outside)";
-        }
-        if (rc) return fail(rc);
+    std::vector<int32_t> corners(3 * (size_t)nt);
+    for (int64_t j = 0; j < nt; j++)
+        for (int k = 0; k < 3; k++) corners[3 * j + k] = t6[6 * j + k];
+    std::string why;
+    if (!check_topology(corners.data(), nt, nv, why) || !check_edge_nodes(t6, nt, nv, why)) {
+        ctx->err = "mesh_upload_quadratic: " + why;
+        return LSM_E_MESH;
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) {
-        ctx->err = "mesh_upload: stream failed";
-        return fail(LSM_E_CUDA);
-    }
-    *out = mh;
-    return LSM_OK;
+    return upload_common(ctx, verts, nv, corners.data(), nt, t6, sigma, rule, (cudaStream_t)stream, out);
 }
 
 int lsm_mesh_upload_sigmax(lsm_ctx* c, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
@@ -578,7 +659,7 @@ int lsm_mesh_free(lsm_mesh* mh)
     me->tree_ff = nullptr;
     for (void* p : {(void*)me->cent, (void*)me->cent_lo, (void*)me->cent_hi})
         if (p) cudaFree(p);
-    void* ps[] = {me->verts, me->tris, me->tri_sigma, me->tri_n, me->vpn, me->s64_pos, me->s64_nw,
+    void* ps[] = {me->verts, me->tris, me->tris6, me->tri_sigma, me->tri_n, me->vpn, me->s64_pos, me->s64_nw,
                   me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, me->tile_lo, me->tile_hi, me->tile_chi, me->tile_clo};
     for (void* p : ps)
         if (p) cudaFree(p);
@@ -756,6 +837,10 @@ int lsm_chart_curvature(lsm_mesh* mh, int order, const double* h, const double* 
     Ctx* ctx = me->ctx;
     if (order < 0 || order > 40 || !h || !grad || !hess || !xuu || !xuv || !xvv || !kmean || !kgauss) {
         ctx->err = "chart_curvature: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    if (me->tris6) {
+        ctx->err = "chart_curvature: the flat-triangle form of eq. uu_vector; quadratic patches are not supported";
         return LSM_E_INVALID_ARG;
     }
     DeviceGuard g(ctx->device);
@@ -1075,6 +1160,22 @@ int lsm_batch_solve_charts(lsm_batch* bh, int order, double tol, int max_iter, i
     if (x_out && !xdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(x_out, xo, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
     if (h_out && !hdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(h_out, ho, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     if (status && !sdev) LSM_CUDA_TRY(ctx, cudaMemcpyAsync(status, so, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+    return check_flag(ctx, st);
+}
+
+int lsm_batch_autotune(lsm_batch* bh, int order, double err_budget, lsm_tune_result* out, void* stream)
+{
+    if (!bh) return LSM_E_INVALID_ARG;
+    Batch* b = &bh->b;
+    Ctx* ctx = b->ctx;
+    if (order < 0 || order > 40 || !(err_budget > 0)) {
+        ctx->err = "batch_autotune: bad arguments";
+        return LSM_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = batch_autotune(ctx, b, order / 2 + 2, err_budget, out, st);
+    if (rc) return rc;
     return check_flag(ctx, st);
 }
 

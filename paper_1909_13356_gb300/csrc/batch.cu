@@ -33,6 +33,10 @@ int batch_build(Ctx* ctx, Batch* b, lsm_mesh* const* meshes, int n, cudaStream_t
             ctx->err = "batch: meshes with a target-dependent sigma are solved one by one";
             return LSM_E_INVALID_ARG;
         }
+        if (me->tris6) {
+            ctx->err = "batch: meshes of quadratic patches are solved one by one";
+            return LSM_E_INVALID_ARG;
+        }
         voff[i + 1] = voff[i] + me->nv;
         toff[i + 1] = toff[i] + me->m;
         tileoff[i + 1] = tileoff[i] + me->ntiles;

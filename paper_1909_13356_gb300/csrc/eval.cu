@@ -1523,6 +1523,9 @@ constexpr int kTPT64 = 1;
 
 int eval_init_constants(Ctx* ctx) { return upload_series_constants(ctx); }
 
+int mixed_tpt(const Mesh* me) { return me->tune_tpt == 1 && !me->sigx ? 1 : kTPT32; }
+double mixed_cut(const Ctx* ctx, const Mesh* me) { return me->tune_cut > 0.0 ? me->tune_cut : ctx->opt.cutoff_mixed; }
+
 // Phi and grad at n sorted targets (SoA x with stride ld) into res [4][n]
 // (phi, then the three gradient components).
 int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int precision, cudaStream_t st,
@@ -1531,7 +1534,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     if (t.n <= 0) return LSM_OK;
     const bool mixed = precision == LSM_MIXED;
     const bool ff = precision == LSM_FF;
-    const int tpb = kEvalThreads * (mixed ? kTPT32 : kTPT64);
+    const int tpt = mixed ? mixed_tpt(me) : kTPT64;
+    const int tpb = kEvalThreads * tpt;
     const int nblk = (t.n + tpb - 1) / tpb;
     const int ntiles = (int)me->ntiles;
     // split the tile range so that the grid covers the GPU a few times over
@@ -1562,7 +1566,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff);
         if (rc != LSM_OK) return rc;
         int64_t total = 0;
-        rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, tsig, s, &list, &blist, &border, &total, st);
+        rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, tsig, s, &list, &blist, &border, &total, st,
+                        mixed ? mixed_cut(ctx, me) : 0.0);
         if (rc != LSM_OK) return rc;
         const int64_t avg = total / nblk;
         nsplit = 1;
@@ -1582,7 +1587,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     A.tx = t.x;
     A.ld = t.ld;
     A.nt = t.n;
-    const double cut = mixed ? ctx->opt.cutoff_mixed : ctx->opt.cutoff_fp64;
+    const double cut = mixed ? mixed_cut(ctx, me) : ctx->opt.cutoff_fp64;
     A.cut2 = (float)(cut * cut);
     A.out = part;
     A.flag = flag_word(ctx);
@@ -1631,6 +1636,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
             k_eval_ff<true><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
         else
             k_eval_fp64<kTPT64, true><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
+    } else if (mixed && tpt == 1) {
+        k_eval_mixed<1, false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else if (mixed) {
         k_eval_mixed<kTPT32, false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
                                                                    me->s32_nwlo, A);
@@ -1651,10 +1658,14 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     return LSM_OK;
 }
 
-int eval_item_targets(int precision) { return kEvalThreads * (precision == LSM_MIXED ? kTPT32 : kTPT64); }
+int eval_item_targets(int precision, int tpt)
+{
+    return kEvalThreads * (precision == LSM_MIXED ? (tpt == 1 ? 1 : kTPT32) : kTPT64);
+}
 
 int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* items, const int* n_items,
-               int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc)
+               int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc, int tpt,
+               double cut_mixed)
 {
     if (max_items <= 0) return LSM_OK;
     EvalArgs A;
@@ -1669,7 +1680,7 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
     A.ld = t.ld;
     A.nt = t.n;
     const bool mixed = precision == LSM_MIXED;
-    const double cut = mixed ? ctx->opt.cutoff_mixed : ctx->opt.cutoff_fp64;
+    const double cut = mixed ? (cut_mixed > 0.0 ? cut_mixed : ctx->opt.cutoff_mixed) : ctx->opt.cutoff_fp64;
     A.cut2 = (float)(cut * cut);
     A.out = res;
     A.flag = flag_word(ctx);
@@ -1687,7 +1698,9 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
         A.x_old = inc->x_old;
         A.bb_io = inc->bb_io;
     }
-    if (mixed) {
+    if (mixed && tpt == 1) {
+        k_eval_mixed<1, false><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
+    } else if (mixed) {
         k_eval_mixed<kTPT32, false><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo,
                                                                         A);
     } else if (precision == LSM_FF) {

@@ -1,9 +1,9 @@
 // frames.cu -- local coordinates of the solved charts and the Gauss flux
 // check of their closure (Sec. 3.3 and Sec. 5).
 //
-// Chart j is x(u,v) = T(u,v) + h(u,v) H(u,v) (eq. chart) over the flat
-// triangle T(u,v) = P1 + u (P2 - P1) + v (P3 - P1), with H interpolated
-// linearly from the vertex pseudonormals.  Newton gives h only at the rule
+// Chart j is x(u,v) = T(u,v) + h(u,v) H(u,v) (eq. chart) over the skeleton
+// patch T(u,v) (the flat triangle of eq. tparam, or a quadratic patch), with
+// H interpolated linearly from the vertex pseudonormals.  Newton gives h only at the rule
 // points; its derivatives follow from x_u being tangent to the level set and
 // grad Phi normal to it (x_u . grad Phi = 0):
 //   h_u = -((T_u + h H_u) . grad Phi) / (H . grad Phi)         (eq. U_vector_2)
@@ -46,10 +46,11 @@ __device__ __forceinline__ void node_of(int64_t s, int np, const double* rule, c
 }
 
 __global__ void k_chart_frames(const double* __restrict__ verts, const int32_t* __restrict__ tris,
-                               const double* __restrict__ vpn, int64_t n, int np, const double* __restrict__ rule,
-                               const int32_t* __restrict__ tri, const double* __restrict__ uvw,
-                               const double* __restrict__ h, const double* __restrict__ g, double* __restrict__ xu,
-                               double* __restrict__ xv, double* __restrict__ jac)
+                               const int32_t* __restrict__ tris6, const double* __restrict__ vpn, int64_t n, int np,
+                               const double* __restrict__ rule, const int32_t* __restrict__ tri,
+                               const double* __restrict__ uvw, const double* __restrict__ h,
+                               const double* __restrict__ g, double* __restrict__ xu, double* __restrict__ xv,
+                               double* __restrict__ jac)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -57,11 +58,10 @@ __global__ void k_chart_frames(const double* __restrict__ verts, const int32_t* 
     double u, v, wq;
     node_of(s, np, rule, tri, uvw, j, u, v, wq);
     const int a = tris[3 * j], b = tris[3 * j + 1], c = tris[3 * j + 2];
-    double tu[3], tv[3], H[3], hu[3], hv[3], gs[3];
+    double T[3], tu[3], tv[3], H[3], hu[3], hv[3], gs[3];
+    patch_map(verts, tris, tris6, j, u, v, T, tu, tv);   // the patch's tangents at the node
     for (int k = 0; k < 3; k++) {
-        const double p1 = verts[3 * a + k], n1 = vpn[3 * a + k];
-        tu[k] = verts[3 * b + k] - p1;
-        tv[k] = verts[3 * c + k] - p1;
+        const double n1 = vpn[3 * a + k];
         hu[k] = vpn[3 * b + k] - n1;
         hv[k] = vpn[3 * c + k] - n1;
         H[k] = n1 + u * hu[k] + v * hv[k];
@@ -237,8 +237,8 @@ int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const 
     const int64_t n = spec ? spec->n : me->m * np;
     if (n == 0) return LSM_OK;
     k_chart_frames<<<(unsigned)((n + kFrameThreads - 1) / kFrameThreads), kFrameThreads, 0, st>>>(
-        me->verts, me->tris, me->vpn, n, np, rule, spec ? spec->tri : nullptr, spec ? spec->uvw : nullptr, h, g, xu,
-        xv, jac);
+        me->verts, me->tris, me->tris6, me->vpn, n, np, rule, spec ? spec->tri : nullptr, spec ? spec->uvw : nullptr, h,
+        g, xu, xv, jac);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }

@@ -94,8 +94,11 @@ __global__ void k_tri_geometry(const double* __restrict__ verts, const int32_t* 
     }
 }
 
+// edge_nodes != 0 (quadratic patches): vertices that are no patch's corner
+// are edge nodes and carry no pseudonormal (the host checked that every
+// vertex is a corner or an edge node)
 __global__ void k_vertex_pn(const double* __restrict__ vacc, int64_t nv, double* __restrict__ vpn,
-                            double* __restrict__ red)
+                            double* __restrict__ red, int edge_nodes)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nv) return;
@@ -106,7 +109,7 @@ __global__ void k_vertex_pn(const double* __restrict__ vacc, int64_t nv, double*
         vpn[3 * i + 2] = vacc[4 * i + 2] / A;
     } else {
         vpn[3 * i] = vpn[3 * i + 1] = vpn[3 * i + 2] = 0.0;
-        atomicAdd(red + 4, 1.0);  // unreferenced vertex
+        if (!edge_nodes) atomicAdd(red + 4, 1.0);  // unreferenced vertex
     }
 }
 
@@ -132,6 +135,104 @@ __global__ void k_sources(const double* __restrict__ verts, const int32_t* __res
     const double q = w / (4.0 * kPi);
     pos[s] = make_double4_32a(y[0], y[1], y[2], 1.0 / (sqrt(2.0) * sg));
     nw[s] = make_double4_32a(q * tri_n[3 * j], q * tri_n[3 * j + 1], q * tri_n[3 * j + 2], sqrt(2.0) * sg);
+}
+
+// Quadratic patches: the same per-triangle state as k_tri_geometry, with the
+// patch's own tangents.  sigma_j = 0.5 sqrt(2 area_j) (or the given one),
+// area_j = sum_k w_k |N(u_k, v_k)| over the source rule; the signed volume
+// sum_k w_k T . N / 3 by the same rule; each corner adds its vertex angle
+// (between the tangents of its two edges there) and its unit normal to the
+// vertex sums of eq. mkvertexpn.  tri_n holds N at the patch centroid.
+__global__ void k_tri_geometry_quad(const double* __restrict__ verts, const int32_t* __restrict__ tris6,
+                                    int64_t m, const double* __restrict__ sigma_in, const double* __restrict__ rule,
+                                    int nq, double* __restrict__ tri_n, double* __restrict__ tri_sigma,
+                                    double* __restrict__ vacc, double* __restrict__ red)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double vol = 0.0;
+    double smin = 1e300, smax = -1e300, bad = 0.0;
+    if (j < m) {
+        double area = 0.0;
+        for (int k = 0; k < nq; k++) {
+            double T[3], Tu[3], Tv[3];
+            patch_map(verts, nullptr, tris6, j, rule[3 * k], rule[3 * k + 1], T, Tu, Tv);
+            const double nx = Tu[1] * Tv[2] - Tu[2] * Tv[1], ny = Tu[2] * Tv[0] - Tu[0] * Tv[2],
+                         nz = Tu[0] * Tv[1] - Tu[1] * Tv[0];
+            const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+            if (!(nn > 0.0)) bad = 1.0;
+            area += rule[3 * k + 2] * nn;
+            vol += rule[3 * k + 2] * (T[0] * nx + T[1] * ny + T[2] * nz) / 3.0;
+        }
+        {
+            double T[3], Tu[3], Tv[3];
+            patch_map(verts, nullptr, tris6, j, 1.0 / 3.0, 1.0 / 3.0, T, Tu, Tv);
+            tri_n[3 * j] = Tu[1] * Tv[2] - Tu[2] * Tv[1];
+            tri_n[3 * j + 1] = Tu[2] * Tv[0] - Tu[0] * Tv[2];
+            tri_n[3 * j + 2] = Tu[0] * Tv[1] - Tu[1] * Tv[0];
+        }
+        const double sg = sigma_in ? sigma_in[j] : 0.5 * sqrt(2.0 * area);
+        tri_sigma[j] = sg;
+        smin = sg;
+        smax = sg;
+        if (!(sg > 0.0)) bad = 1.0;
+        const double cu[3] = {0.0, 1.0, 0.0}, cv[3] = {0.0, 0.0, 1.0};
+        for (int c = 0; c < 3; c++) {
+            double T[3], Tu[3], Tv[3], e1[3], e2[3];
+            patch_map(verts, nullptr, tris6, j, cu[c], cv[c], T, Tu, Tv);
+            for (int k = 0; k < 3; k++) {
+                // the two edges leaving the corner: (u, v) along (1,0),(0,1) at P1;
+                // (-1,1),(-1,0) at P2; (0,-1),(1,-1) at P3
+                e1[k] = c == 0 ? Tu[k] : (c == 1 ? Tv[k] - Tu[k] : -Tv[k]);
+                e2[k] = c == 0 ? Tv[k] : (c == 1 ? -Tu[k] : Tu[k] - Tv[k]);
+            }
+            const double nx = Tu[1] * Tv[2] - Tu[2] * Tv[1], ny = Tu[2] * Tv[0] - Tu[0] * Tv[2],
+                         nz = Tu[0] * Tv[1] - Tu[1] * Tv[0];
+            const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+            if (!(nn > 0.0)) {
+                bad = 1.0;
+                continue;
+            }
+            const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                         cz = e1[0] * e2[1] - e1[1] * e2[0];
+            const double th = atan2(sqrt(cx * cx + cy * cy + cz * cz), e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2]);
+            double* a = vacc + 4 * (int64_t)tris6[6 * j + c];
+            atomicAdd(a + 0, th * nx / nn);
+            atomicAdd(a + 1, th * ny / nn);
+            atomicAdd(a + 2, th * nz / nn);
+            atomicAdd(a + 3, th);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        vol += __shfl_down_sync(0xffffffffu, vol, o);
+        smin = fmin(smin, __shfl_down_sync(0xffffffffu, smin, o));
+        smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, o));
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(red + 0, vol);
+        atomicMin(reinterpret_cast<long long*>(red + 1), ordered_bits(smin));
+        atomicMax(reinterpret_cast<long long*>(red + 2), ordered_bits(smax));
+        if (bad > 0) atomicAdd(red + 3, bad);
+    }
+}
+
+// Source nodes on quadratic patches: y = T(u, v), nw = w N(u, v) / (4 pi)
+// (the area element is in |N|), a = 1/(sqrt2 sigma_j).
+__global__ void k_sources_quad(const double* __restrict__ verts, const int32_t* __restrict__ tris6,
+                               const double* __restrict__ tri_sigma, int64_t m, const double* __restrict__ rule,
+                               int nq, double4_32a* __restrict__ pos, double4_32a* __restrict__ nw)
+{
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= m * nq) return;
+    const int64_t j = s / nq;
+    const int k = (int)(s - j * nq);
+    double T[3], Tu[3], Tv[3];
+    patch_map(verts, nullptr, tris6, j, rule[3 * k], rule[3 * k + 1], T, Tu, Tv);
+    const double sg = tri_sigma[j];
+    const double q = rule[3 * k + 2] / (4.0 * kPi);
+    pos[s] = make_double4_32a(T[0], T[1], T[2], 1.0 / (sqrt(2.0) * sg));
+    nw[s] = make_double4_32a(q * (Tu[1] * Tv[2] - Tu[2] * Tv[1]), q * (Tu[2] * Tv[0] - Tu[0] * Tv[2]),
+                             q * (Tu[0] * Tv[1] - Tu[1] * Tv[0]), sqrt(2.0) * sg);
 }
 
 // ordered(+DBL_MAX) for the minima, ordered(-DBL_MAX) for the maxima
@@ -384,9 +485,9 @@ __global__ void __launch_bounds__(kTile) k_tile_meta(
 // Chart nodes (Sec. 3.2): x0 = T^j(u_i, v_i), H = H^j(u_i, v_i) (eq. mkpseudovec),
 // sloc = sigma_j.  Triangle-major, then rule order.  x0, hdir AoS [n][3].
 __global__ void k_chart_nodes(const double* __restrict__ verts, const int32_t* __restrict__ tris,
-                              const double* __restrict__ vpn, const double* __restrict__ tri_sigma,
-                              int64_t m, const double* __restrict__ rule, int np,
-                              double* __restrict__ x0, double* __restrict__ hdir,
+                              const int32_t* __restrict__ tris6, const double* __restrict__ vpn,
+                              const double* __restrict__ tri_sigma, int64_t m, const double* __restrict__ rule,
+                              int np, double* __restrict__ x0, double* __restrict__ hdir,
                               double* __restrict__ sloc)
 {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -395,9 +496,11 @@ __global__ void k_chart_nodes(const double* __restrict__ verts, const int32_t* _
     const int k = (int)(s - j * np);
     const double u = rule[3 * k], v = rule[3 * k + 1];
     const int ia = tris[3 * j], ib = tris[3 * j + 1], ic = tris[3 * j + 2];
+    double T[3], Tu[3], Tv[3];
+    patch_map(verts, tris, tris6, j, u, v, T, Tu, Tv);
     for (int c = 0; c < 3; c++) {
-        const double p1 = verts[3 * ia + c], h1 = vpn[3 * ia + c];
-        x0[3 * s + c] = p1 + u * (verts[3 * ib + c] - p1) + v * (verts[3 * ic + c] - p1);
+        const double h1 = vpn[3 * ia + c];
+        x0[3 * s + c] = T[c];
         hdir[3 * s + c] = h1 + u * (vpn[3 * ib + c] - h1) + v * (vpn[3 * ic + c] - h1);
     }
     sloc[s] = tri_sigma[j];
@@ -409,18 +512,21 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // coordinates (uvw[3s], uvw[3s+1]) (refined charts keep their parent's map,
 // Sec. 3.4).
 __global__ void k_chart_nodes_at(const double* __restrict__ verts, const int32_t* __restrict__ tris,
-                                 const double* __restrict__ vpn, const double* __restrict__ tri_sigma, int64_t n,
-                                 const int32_t* __restrict__ tri, const double* __restrict__ uvw,
-                                 double* __restrict__ x0, double* __restrict__ hdir, double* __restrict__ sloc)
+                                 const int32_t* __restrict__ tris6, const double* __restrict__ vpn,
+                                 const double* __restrict__ tri_sigma, int64_t n, const int32_t* __restrict__ tri,
+                                 const double* __restrict__ uvw, double* __restrict__ x0,
+                                 double* __restrict__ hdir, double* __restrict__ sloc)
 {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t j = tri[s];
     const double u = uvw[3 * s], v = uvw[3 * s + 1];
     const int ia = tris[3 * j], ib = tris[3 * j + 1], ic = tris[3 * j + 2];
+    double T[3], Tu[3], Tv[3];
+    patch_map(verts, tris, tris6, j, u, v, T, Tu, Tv);
     for (int c = 0; c < 3; c++) {
-        const double p1 = verts[3 * ia + c], h1 = vpn[3 * ia + c];
-        x0[3 * s + c] = p1 + u * (verts[3 * ib + c] - p1) + v * (verts[3 * ic + c] - p1);
+        const double h1 = vpn[3 * ia + c];
+        x0[3 * s + c] = T[c];
         hdir[3 * s + c] = h1 + u * (vpn[3 * ib + c] - h1) + v * (vpn[3 * ic + c] - h1);
     }
     sloc[s] = tri_sigma[j];
@@ -432,8 +538,8 @@ int chart_nodes_at(Ctx* ctx, const Mesh* me, int64_t n, const int32_t* tri, cons
                    double* hdir, double* sloc, cudaStream_t st)
 {
     if (n <= 0) return LSM_OK;
-    k_chart_nodes_at<<<blocks_for(n, 256), 256, 0, st>>>(me->verts, me->tris, me->vpn, me->tri_sigma, n, tri, uvw,
-                                                         x0, hdir, sloc);
+    k_chart_nodes_at<<<blocks_for(n, 256), 256, 0, st>>>(me->verts, me->tris, me->tris6, me->vpn, me->tri_sigma, n,
+                                                         tri, uvw, x0, hdir, sloc);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }
@@ -468,10 +574,15 @@ int build_mesh_device(Ctx* ctx, Mesh* me, const double* sigma_in_dev, const doub
     LSM_CUDA_TRY(ctx, cudaMemsetAsync(vacc, 0, sizeof(double) * 4 * me->nv, st));
     k_red_init<<<1, 32, 0, st>>>(red);
     LSM_LAUNCHED(ctx);
-    k_tri_geometry<<<blocks_for(me->m, 256), 256, 0, st>>>(me->verts, me->tris, me->m, sigma_in_dev,
-                                                         me->tri_n, me->tri_sigma, vacc, red);
+    if (me->tris6)
+        k_tri_geometry_quad<<<blocks_for(me->m, 256), 256, 0, st>>>(me->verts, me->tris6, me->m, sigma_in_dev,
+                                                                  rule_dev, me->nq, me->tri_n, me->tri_sigma, vacc,
+                                                                  red);
+    else
+        k_tri_geometry<<<blocks_for(me->m, 256), 256, 0, st>>>(me->verts, me->tris, me->m, sigma_in_dev,
+                                                             me->tri_n, me->tri_sigma, vacc, red);
     LSM_LAUNCHED(ctx);
-    k_vertex_pn<<<blocks_for(me->nv, 256), 256, 0, st>>>(vacc, me->nv, me->vpn, red);
+    k_vertex_pn<<<blocks_for(me->nv, 256), 256, 0, st>>>(vacc, me->nv, me->vpn, red, me->tris6 ? 1 : 0);
     LSM_LAUNCHED(ctx);
     LSM_CUDA_TRY(ctx, cudaMemcpyAsync(host_red, red, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
     LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -492,8 +603,12 @@ int build_mesh_device(Ctx* ctx, Mesh* me, const double* sigma_in_dev, const doub
     LSM_CUDA_TRY(ctx, s.get(&p0, ns));
     LSM_CUDA_TRY(ctx, s.get(&n0, ns));
     LSM_CUDA_TRY(ctx, s.get(&perm, ns));
-    k_sources<<<blocks_for(ns, 256), 256, 0, st>>>(me->verts, me->tris, me->tri_n, me->tri_sigma, me->m,
-                                                  rule_dev, me->nq, p0, n0);
+    if (me->tris6)
+        k_sources_quad<<<blocks_for(ns, 256), 256, 0, st>>>(me->verts, me->tris6, me->tri_sigma, me->m, rule_dev,
+                                                           me->nq, p0, n0);
+    else
+        k_sources<<<blocks_for(ns, 256), 256, 0, st>>>(me->verts, me->tris, me->tri_n, me->tri_sigma, me->m,
+                                                      rule_dev, me->nq, p0, n0);
     LSM_LAUNCHED(ctx);
     int rc = morton_order_points(ctx, reinterpret_cast<const double*>(p0), 4, ns, perm, st);
     if (rc != LSM_OK) return rc;
@@ -565,7 +680,7 @@ int chart_nodes_init(Ctx* ctx, const Mesh* me, const double* chart_rule_dev, int
                      double* hdir, double* sloc, cudaStream_t st)
 {
     const int64_t n = me->m * np;
-    k_chart_nodes<<<blocks_for(n, 256), 256, 0, st>>>(me->verts, me->tris, me->vpn, me->tri_sigma, me->m,
+    k_chart_nodes<<<blocks_for(n, 256), 256, 0, st>>>(me->verts, me->tris, me->tris6, me->vpn, me->tri_sigma, me->m,
                                                     chart_rule_dev, np, x0, hdir, sloc);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
@@ -576,8 +691,8 @@ int chart_nodes_raw(Ctx* ctx, const double* verts, const int32_t* tris, const do
                     cudaStream_t st)
 {
     const int64_t n = m * np;
-    k_chart_nodes<<<blocks_for(n, 256), 256, 0, st>>>(verts, tris, vpn, tri_sigma, m, chart_rule_dev, np, x0, hdir,
-                                                    sloc);
+    k_chart_nodes<<<blocks_for(n, 256), 256, 0, st>>>(verts, tris, nullptr, vpn, tri_sigma, m, chart_rule_dev, np, x0,
+                                                    hdir, sloc);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }

@@ -143,6 +143,10 @@ struct Mesh {
     int tune_mode = -1;
     int tune_degree = 0;
     float tune_theta = 0.0f;
+    // and its near-field radius (in sigma) and targets per thread of the
+    // mixed kernel (0: the context's cutoff_mixed, two targets per thread)
+    double tune_cut = 0.0;
+    int tune_tpt = 0;
     int64_t nv = 0, m = 0, ns = 0, ntiles = 0;
     int nq = 0;
     lsm_quad rule{4, 0};
@@ -154,6 +158,10 @@ struct Mesh {
     double* tri_sigma = nullptr; // [m]
     double* tri_n = nullptr;     // [m][3] N = T_u x T_v (not normalised)
     double* vpn = nullptr;       // [nv][3] vertex pseudonormals
+    // quadratic skeletons (Sec. 5, quadratic skeletons): [m][6] patch nodes,
+    // the corners (also in tris) then the nodes of edges 1-2, 2-3, 3-1;
+    // nullptr for flat triangles
+    int32_t* tris6 = nullptr;
     // sources in Morton order
     double4_32a* s64_pos = nullptr;  // (x, y, z, a = 1/(sqrt2 sigma))
     double4_32a* s64_nw = nullptr;   // (nw / 4 pi, 0)
@@ -184,7 +192,46 @@ struct Batch {
     float4 *tile_lo = nullptr, *tile_hi = nullptr, *tile_chi = nullptr, *tile_clo = nullptr;
     int2* mesh_tiles = nullptr;  // [nmesh] (first tile, end tile)
     std::vector<int64_t> tri_off;  // host [nmesh + 1]
+    // mixed kernel settings chosen by lsm_batch_autotune (0: defaults)
+    double cut_mixed = 0.0;
+    int tpt = 0;
 };
+
+// ---------------------------------------------------------------- patch map
+// T(u,v), T_u and T_v of skeleton triangle j.  Flat triangles (tris6 null):
+// T = P1 + u (P2 - P1) + v (P3 - P1) (eq. tparam).  Quadratic patches: the
+// second-order Lagrange interpolant through the corners P1, P2, P3 and the
+// edge nodes P4 (edge 1-2), P5 (2-3), P6 (3-1), written in monomials,
+//   T = P1 + u A + v B + u^2 C + u v D + v^2 E,
+//   A = 4 P4 - 3 P1 - P2,  B = 4 P6 - 3 P1 - P3,  C = 2 (P1 + P2 - 2 P4),
+//   D = 4 (P1 - P4 + P5 - P6),  E = 2 (P1 + P3 - 2 P6),
+// which reduces to the flat map when the edge nodes are the midpoints.
+__device__ __forceinline__ void patch_map(const double* __restrict__ verts, const int32_t* __restrict__ tris,
+                                          const int32_t* __restrict__ tris6, int64_t j, double u, double v,
+                                          double T[3], double Tu[3], double Tv[3])
+{
+    if (!tris6) {
+        const int64_t a = tris[3 * j], b = tris[3 * j + 1], c = tris[3 * j + 2];
+        for (int k = 0; k < 3; k++) {
+            const double p1 = verts[3 * a + k];
+            Tu[k] = verts[3 * b + k] - p1;
+            Tv[k] = verts[3 * c + k] - p1;
+            T[k] = p1 + u * Tu[k] + v * Tv[k];
+        }
+        return;
+    }
+    const int32_t* q = tris6 + 6 * j;
+    for (int k = 0; k < 3; k++) {
+        const double p1 = verts[3 * (int64_t)q[0] + k], p2 = verts[3 * (int64_t)q[1] + k],
+                     p3 = verts[3 * (int64_t)q[2] + k], p4 = verts[3 * (int64_t)q[3] + k],
+                     p5 = verts[3 * (int64_t)q[4] + k], p6 = verts[3 * (int64_t)q[5] + k];
+        const double A = 4.0 * p4 - 3.0 * p1 - p2, B = 4.0 * p6 - 3.0 * p1 - p3;
+        const double C = 2.0 * (p1 + p2 - 2.0 * p4), D = 4.0 * (p1 - p4 + p5 - p6), E = 2.0 * (p1 + p3 - 2.0 * p6);
+        T[k] = p1 + u * (A + u * C + v * D) + v * (B + v * E);
+        Tu[k] = A + 2.0 * u * C + v * D;
+        Tv[k] = B + u * D + 2.0 * v * E;
+    }
+}
 
 // ---------------------------------------------------------------- errors
 #define LSM_CUDA_TRY(ctx, call)                                                   \
@@ -307,9 +354,15 @@ int eval_sorted(Ctx* ctx, const Mesh* mesh, const Targets& t, double* res, int p
 // Targets grouped by work items (int4: first target, count, first tile, end
 // tile; at most eval_item_targets(precision) targets each); the number of
 // items is read on the device from *n_items, the grid covers max_items.
-int eval_item_targets(int precision);
+// tpt: targets per thread of the mixed kernel (1 or 2; 0 the default 2);
+// cut: its near-field radius in sigma (0: the context's cutoff_mixed)
+int eval_item_targets(int precision, int tpt = 0);
 int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* items, const int* n_items,
-               int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc = nullptr);
+               int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc = nullptr,
+               int tpt = 0, double cut = 0.0);
+// the mixed kernel's settings for a mesh: its autotuned ones, else the defaults
+int mixed_tpt(const Mesh* me);
+double mixed_cut(const Ctx* ctx, const Mesh* me);
 int eval_noalloc(Ctx* ctx, const Mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
                  int precision, cudaStream_t st);
 
@@ -382,6 +435,8 @@ int sigma_x_eval(Ctx* ctx, const Mesh* me, const Targets& t, double* sig, double
 
 // tune.cu: the autotuner on sorted SoA targets (lsm_autotune)
 int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tune_result* res, cudaStream_t st);
+// the batch's mixed-kernel radius and target tile (lsm_batch_autotune)
+int batch_autotune(Ctx* ctx, Batch* b, int n_gl, double budget, lsm_tune_result* res, cudaStream_t st);
 
 // newton.cu
 int solve_charts_device(Ctx* ctx, Mesh* mesh, int n_gl, double tol, int max_iter,

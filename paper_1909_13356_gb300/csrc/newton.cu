@@ -487,6 +487,8 @@ struct BatchSweep {
     bool mixed;
     int accept_mixed, max_iter;
     double tol, sw;
+    int tpt;          // mixed kernel: targets per thread (0: default)
+    double cut;       // mixed kernel: near-field radius in sigma (0: default)
 };
 
 int batch_sweep(Ctx* ctx, const BatchSweep& B, const int32_t* act, const int* n_act, int32_t* act_out,
@@ -511,7 +513,7 @@ int batch_sweep(Ctx* ctx, const BatchSweep& B, const int32_t* act, const int* n_
         }
         k_gather_targets_dev<<<nb(B.N), 256, 0, st>>>(L, nL, B.S, B.T, B.N);
         LSM_LAUNCHED(ctx);
-        const int bs = eval_item_targets(prec);
+        const int bs = eval_item_targets(prec, B.tpt);
         rc = build_items(ctx, L, nL, B.N, B.node_mesh, B.mesh_tiles, B.nmesh, bs, B.cnt, B.nblk, B.items, B.n_items,
                          st);
         if (rc) return rc;
@@ -519,7 +521,7 @@ int batch_sweep(Ctx* ctx, const BatchSweep& B, const int32_t* act, const int* n_
         FFIncremental inc{verify ? 2 : 1, B.Rfar, verify ? B.Trec : nullptr, B.BBrec};
         const bool ffpair = B.mixed && m == 1;
         rc = eval_items(ctx, B.view, tg, B.items, B.n_items, prec == LSM_MIXED ? B.max_items_mixed : B.max_items_other,
-                        B.R, prec, st, ffpair ? &inc : nullptr);
+                        B.R, prec, st, ffpair ? &inc : nullptr, B.tpt, B.cut);
         if (rc) return rc;
         if (ffpair && !verify) {
             k_copy_record<<<nb(B.N), 256, 0, st>>>(L, nL, B.Lrec, B.n_rec, B.T, B.Trec, B.N);
@@ -602,7 +604,10 @@ int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, i
         BatchSweep B;
         B.N = N;
         B.nmesh = b->nmesh;
-        B.max_items_mixed = (N + eval_item_targets(LSM_MIXED) - 1) / eval_item_targets(LSM_MIXED) + b->nmesh;
+        B.tpt = b->tpt;
+        B.cut = b->cut_mixed;
+        B.max_items_mixed = (N + eval_item_targets(LSM_MIXED, B.tpt) - 1) / eval_item_targets(LSM_MIXED, B.tpt) +
+                            b->nmesh;
         B.max_items_other = (N + eval_item_targets(LSM_FP64) - 1) / eval_item_targets(LSM_FP64) + b->nmesh;
         B.mesh_tiles = b->mesh_tiles;
         B.view = view_of_batch(b);

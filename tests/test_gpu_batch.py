@@ -52,3 +52,25 @@ def test_batch_residual_against_oracle(setup, oracle_mod):
         assert np.abs(phi - 0.5).max() < 1e-11
         o += n
     b.free()
+
+
+def test_batch_autotune_then_solve(setup):
+    """lsm_batch_autotune picks the mixed kernel's near-field radius (within
+    the mixed bound) and target tile on a sample of the batch's meshes; the
+    batched solve with that choice still gives each mesh its own result."""
+    lsm, ctx, ms, meshes = setup
+    b = lsm.Batch(ctx, meshes)
+    r = b.autotune(order=6, err_budget=5e-8)
+    assert r["use_tree"] == 0 and r["candidates"] == 6
+    assert min(abs(r["cutoff"] - c) for c in (6.4, 6.5, 7.0)) < 1e-12
+    assert r["targets_per_block"] in (128, 256)
+    assert r["err_phi"] <= 5e-8 and r["sample_targets"] == sum(m.m for m in ms) * 25
+    x, h, st, stats = b.solve_charts(order=6, tol=1e-10, precision=lsm.MIXED, use_graph=True)
+    assert np.all(st & 255 == 0)
+    o = 0
+    for mesh in meshes:
+        xa, ha, sa, _ = mesh.solve_charts(order=6, tol=1e-10, precision=lsm.MIXED)
+        n = len(ha)
+        assert np.abs(x[o:o + n] - xa).max() < 1e-9
+        o += n
+    b.free()

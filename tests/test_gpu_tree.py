@@ -177,6 +177,9 @@ def test_autotune_choice_within_budget(lsm, oracle_mod):
     assert r["candidates"] >= 5 and r["sample_targets"] == 8 * 4096
     assert r["err_phi"] <= 5e-8
     assert r["ms_sample"] <= r["ms_direct"] * 1.05
+    # second stage: the near-field radius (within the mixed bound) and the target tile
+    assert min(abs(r["cutoff"] - c) for c in (6.4, 6.5, 7.0)) < 1e-12
+    assert r["targets_per_block"] in (128, 256)
     phi, grad = _eval(lsm, ctx, mesh, w["targets"])
     y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 6, 0)
     sel = np.random.default_rng(5).choice(len(w["targets"]), 400, replace=False)
