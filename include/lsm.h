@@ -171,7 +171,9 @@ typedef struct {
 /* Create a context on CUDA device `device`.  Allocates no large memory.
  * Errors: LSM_E_INVALID_ARG (bad device or options), LSM_E_CUDA. */
 int lsm_create(lsm_ctx** out, int device, const lsm_options* opt);
-/* Destroy a context; every mesh created from it must be freed first. */
+/* Destroy a context.  Servers, batches and meshes made from it that are
+ * still alive are destroyed first (their handles become invalid), so that
+ * none is ever used after its context. */
 int lsm_destroy(lsm_ctx* ctx);
 /* Message of the calling thread's last failed call on ctx ("" if none;
  * never NULL).  The string belongs to the calling thread and stays valid

@@ -558,7 +558,9 @@ class Mesh:
 
     def free(self):
         if getattr(self, "_h", None):
-            self.ctx._L.lsm_mesh_free(self._h)
+            # a closed context has freed its meshes already (lsm_destroy)
+            if getattr(self.ctx, "_h", None):
+                self.ctx._L.lsm_mesh_free(self._h)
             self._h = None
 
     def __del__(self):
@@ -616,7 +618,8 @@ class Batch:
 
     def free(self):
         if getattr(self, "_h", None):
-            self.ctx._L.lsm_batch_free(self._h)
+            if getattr(self.ctx, "_h", None):
+                self.ctx._L.lsm_batch_free(self._h)
             self._h = None
 
     def __del__(self):
@@ -679,7 +682,8 @@ class Server:
 
     def close(self):
         if getattr(self, "_h", None):
-            self.ctx._L.lsm_server_destroy(self._h)
+            if getattr(self.ctx, "_h", None):
+                self.ctx._L.lsm_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -80,16 +80,36 @@ void simplex_rule_host(int n, int subdiv, double* uvw)
 
 namespace {
 
+// Makes `dev` current for the scope of a call.  A failure here is left to
+// the call's own checks, but its error is cleared, so that it cannot surface
+// later as the error of an unrelated launch.
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            if (cudaSetDevice(dev) != cudaSuccess) cudaGetLastError();
+        } else {
+            prev = -1;
+            cudaGetLastError();
+        }
     }
     ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
+        if (prev >= 0 && cudaSetDevice(prev) != cudaSuccess) cudaGetLastError();
     }
 };
+
+template <class H>
+void reg_add(Ctx* ctx, std::set<H*>& set, H* h)
+{
+    std::lock_guard<std::mutex> lk(ctx->reg_mu);
+    set.insert(h);
+}
+template <class H>
+void reg_remove(Ctx* ctx, std::set<H*>& set, H* h)
+{
+    std::lock_guard<std::mutex> lk(ctx->reg_mu);
+    set.erase(h);
+}
 
 bool is_device_ptr(const void* p)
 {
@@ -329,6 +349,7 @@ int upload_common(Ctx* ctx, const double* verts, int64_t nv, const int32_t* tris
         ctx->err = "mesh_upload: stream failed";
         return fail(LSM_E_CUDA);
     }
+    reg_add(ctx, ctx->meshes, mh);
     *out = mh;
     return LSM_OK;
 }
@@ -410,6 +431,20 @@ int lsm_destroy(lsm_ctx* c)
 {
     if (!c) return LSM_E_INVALID_ARG;
     DeviceGuard g(c->c.device);
+    // what the caller did not free: servers first (their workers use meshes
+    // of their own), then batches, then meshes
+    std::vector<lsm_server*> sv;
+    std::vector<lsm_batch*> bt;
+    std::vector<lsm_mesh*> ms;
+    {
+        std::lock_guard<std::mutex> lk(c->c.reg_mu);
+        sv.assign(c->c.servers.begin(), c->c.servers.end());
+        bt.assign(c->c.batches.begin(), c->c.batches.end());
+        ms.assign(c->c.meshes.begin(), c->c.meshes.end());
+    }
+    for (lsm_server* s : sv) lsm_server_destroy(s);
+    for (lsm_batch* b : bt) lsm_batch_free(b);
+    for (lsm_mesh* m : ms) lsm_mesh_free(m);
     cudaFree(c->c.d_flag);
     cudaFree(c->c.d_pairs);
     for (int32_t* p : c->c.host_free) cudaFreeHost(p);
@@ -652,6 +687,7 @@ int lsm_mesh_free(lsm_mesh* mh)
 {
     if (!mh) return LSM_E_INVALID_ARG;
     Mesh* me = &mh->m;
+    if (me->ctx) reg_remove(me->ctx, me->ctx->meshes, mh);
     DeviceGuard g(me->ctx ? me->ctx->device : 0);
     tree_free(me->tree);
     me->tree = nullptr;
@@ -1118,6 +1154,7 @@ int lsm_batch_create(lsm_ctx* c, lsm_mesh* const* meshes, int n, void* stream, l
         delete bh;
         return rc;
     }
+    reg_add(ctx, ctx->batches, bh);
     *out = bh;
     return LSM_OK;
 }
@@ -1125,6 +1162,7 @@ int lsm_batch_create(lsm_ctx* c, lsm_mesh* const* meshes, int n, void* stream, l
 int lsm_batch_free(lsm_batch* bh)
 {
     if (!bh) return LSM_E_INVALID_ARG;
+    if (bh->b.ctx) reg_remove(bh->b.ctx, bh->b.ctx->batches, bh);
     DeviceGuard g(bh->b.ctx ? bh->b.ctx->device : 0);
     batch_release(&bh->b);
     delete bh;

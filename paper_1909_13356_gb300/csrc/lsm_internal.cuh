@@ -8,6 +8,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <string>
 #include <utility>
@@ -16,6 +17,8 @@
 #include "lsm.h"
 
 struct lsm_mesh;
+struct lsm_batch;
+struct lsm_server;
 
 namespace lsm {
 
@@ -76,6 +79,12 @@ struct Ctx {
     static constexpr int kHostWords = 64;
     std::mutex host_mu;
     std::vector<int32_t*> host_free;
+    // handles made from this context and not yet freed; lsm_destroy frees
+    // them, so that none outlives the context it points to
+    std::mutex reg_mu;
+    std::set<lsm_mesh*> meshes;
+    std::set<lsm_batch*> batches;
+    std::set<lsm_server*> servers;
 };
 
 // Device error word of the calling thread: a thread that installed its own

@@ -181,6 +181,10 @@ int lsm_server_create(lsm_ctx* ctx, int slots, int64_t hbm_budget_bytes, lsm_ser
     sv->budget = hbm_budget_bytes;
     sv->t0 = Clock::now();
     for (int i = 0; i < slots; i++) sv->workers.emplace_back(worker, sv);
+    {
+        std::lock_guard<std::mutex> lk(ctx->c.reg_mu);
+        ctx->c.servers.insert(sv);
+    }
     *out = sv;
     return LSM_OK;
 }
@@ -288,6 +292,10 @@ int lsm_server_info(lsm_server* sv, lsm_server_info_t* out)
 int lsm_server_destroy(lsm_server* sv)
 {
     if (!sv) return LSM_E_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->ctx->c.reg_mu);
+        sv->ctx->c.servers.erase(sv);
+    }
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stopping = true;

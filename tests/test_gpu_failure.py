@@ -71,3 +71,26 @@ def test_timeout_in_chart_solve(setup):
     xc, h, st, stats = mesh.solve_charts(order=4, tol=1e-12, precision=lsm.MIXED)
     assert np.all(st & 255 == 0)
     assert np.array_equal(xc, ref[0])
+
+
+def test_context_closed_before_its_meshes(setup):
+    """Objects freed in any order (as a garbage collector may do with cycles):
+    closing a context first frees its meshes, batches and servers; freeing
+    them afterwards is a no-op, and later calls on a new context see no error
+    left behind."""
+    lsm, _, m, _, x = setup
+    ctx2 = lsm.Context(0)
+    mesh2 = ctx2.upload(m.verts, m.tris, m.sigma, n_gl=3)
+    b2 = lsm.Batch(ctx2, [mesh2])
+    srv = lsm.Server(ctx2, slots=2)
+    ctx2.close()
+    mesh2.free()
+    b2.free()
+    srv.close()
+    ctx3 = lsm.Context(0)
+    mesh3 = ctx3.upload(m.verts, m.tris, m.sigma, n_gl=3)
+    phi, _ = mesh3.eval_phi_grad(x[:500], lsm.MIXED)
+    assert np.isfinite(phi).all()
+    ctx3.check_error()
+    mesh3.free()
+    ctx3.close()
