@@ -135,7 +135,13 @@ typedef struct {
                                     oriented per-axis grids and a degree ladder
                                     (default), 2 (degree + 1)^3 axis-aligned
                                     grids of one degree */
-    int32_t reserved;
+    /* Target clusters of the float-float treecode: runs of this many
+     * Morton-sorted targets (a multiple of 128) get an oriented box with a
+     * tensor Chebyshev grid (degree tree_ff_degree on the widest axis); a
+     * node far enough from a cluster (the opening rule from the targets'
+     * side, with the same error bound) acts on the grid's points, and the
+     * targets interpolate its field from them.  0 selects 2048; -1: off. */
+    int32_t tree_ff_cluster;
 } lsm_options;
 
 /* Statistics of one chart solve. */

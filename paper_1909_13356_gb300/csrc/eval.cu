@@ -1562,12 +1562,20 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     // float-float: every mode but the near-only one (which lists near tiles itself)
     const bool use_tree = mixed ? tree_wanted(ctx, me, false)
                                 : (ff && !(inc && inc->mode == 2) && tree_wanted(ctx, me, true));
+    // float-float treecode: target clusters take the nodes far from them
+    ClusterPlan cp;
+    const int tpc = ctx->opt.tree_ff_cluster;
+    const bool clusters = use_tree && ff && !me->sigx && tpc > 0 && t.n >= 2 * tpc;
     if (use_tree) {
         int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff);
         if (rc != LSM_OK) return rc;
+        if (clusters) {
+            rc = cluster_setup(ctx, me->tree_ff, t, tpc, s, &cp, st);
+            if (rc != LSM_OK) return rc;
+        }
         int64_t total = 0;
         rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, tsig, s, &list, &blist, &border, &total, st,
-                        mixed ? mixed_cut(ctx, me) : 0.0);
+                        mixed ? mixed_cut(ctx, me) : 0.0, clusters ? &cp : nullptr);
         if (rc != LSM_OK) return rc;
         const int64_t avg = total / nblk;
         nsplit = 1;
@@ -1647,6 +1655,26 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         k_eval_fp64<kTPT64, false><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
     }
     LSM_LAUNCHED(ctx);
+    double* rg = nullptr;
+    if (clusters && cp.ngblk > 0) {
+        // the clusters' grid points against the nodes their clusters took:
+        // the same kernel in list mode, every pair far
+        LSM_CUDA_TRY(ctx, s.get(&rg, 4 * (size_t)cp.ng));
+        EvalArgs G = A;
+        G.tx = cp.gx;
+        G.ld = cp.ng;
+        G.nt = (int)cp.ng;
+        G.out = rg;
+        G.list = cp.list;
+        G.blist = cp.gblist;
+        G.border = cp.gorder;
+        G.ff_mode = 0;
+        G.far_io = nullptr;
+        G.x_old = nullptr;
+        G.bb_io = nullptr;
+        k_eval_ff<false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, G);
+        LSM_LAUNCHED(ctx);
+    }
     if (ctx->profiling) {
         LSM_CUDA_TRY(ctx, cudaEventRecord(ev1, st));
         ctx->prof_events.push_back(Ctx::ProfEvent{ev0, ev1, mixed ? 0 : (ff ? 1 : 2)});
@@ -1654,6 +1682,10 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     if (nsplit > 1) {
         k_reduce_splits<<<(t.n + 255) / 256, 256, 0, st>>>(part, nsplit, t.n, res);
         LSM_LAUNCHED(ctx);
+    }
+    if (rg) {
+        int rc = cluster_l2p(ctx, cp, t, rg, res, (inc && inc->mode == 1) ? inc->far_io : nullptr, st);
+        if (rc != LSM_OK) return rc;
     }
     return LSM_OK;
 }

@@ -393,6 +393,7 @@ struct Tree {
     float4* node_hi = nullptr;              // box, rounded up
     int4* node_info = nullptr;              // first tile, tile count, first proxy tile or -1, proxy tiles
     float4* node_acc = nullptr;             // proxy nodes: frame centre, (radius / theta_n)^2
+    float* node_r = nullptr;                // proxy nodes: radius of the frame box, rounded up
     float4 *p_pos = nullptr, *p_nw = nullptr;   // proxies, kTile per proxy tile
     float4 *p_lo = nullptr, *p_nwlo = nullptr;  // float-float trees: remainders of both
     float4 *tile_lo = nullptr, *tile_hi = nullptr, *tile_chi = nullptr, *tile_clo = nullptr;
@@ -408,8 +409,36 @@ void tree_free(Tree* t);
 // tsig: the targets' sigma in sigma(x) mode (the near width), else NULL.
 // cut_override > 0: the near radius (in sigma) of the kernel that evaluates
 // the lists, when it is not the tree's own path's.
+// Target clusters of one evaluation (float-float treecode): runs of `tpc`
+// consecutive sorted targets, each with an oriented box and a tensor
+// Chebyshev grid on it.  A source node far enough from a cluster acts on the
+// cluster's grid points (through its proxies), and the cluster's targets
+// interpolate that field from the grid (cluster_l2p); the targets' own
+// block lists skip such nodes.  Device arrays in the caller's Scratch.
+struct ClusterPlan {
+    int tpc = 0;                 // targets per cluster (0: no clusters)
+    int ncl = 0;
+    float4 *box_lo = nullptr, *box_hi = nullptr;   // outward box of each cluster's oriented box
+    float4* cacc = nullptr;      // frame centre, (r + q h_max)^2: the target-side opening radius
+    double* frame = nullptr;     // [ncl][16]: centre (3), axes (9, rows), half-widths (3), unused
+    int4* counts = nullptr;      // grid points per axis; w = first grid point (padded to kEvalThreads)
+    int64_t ng = 0;              // grid points, padded
+    double* gx = nullptr;        // grid points, SoA [3][ng]
+    int* list = nullptr;         // proxy tiles acting on each cluster's grid
+    int2* gblist = nullptr;      // per block of grid points: its cluster's (offset, length) in list
+    int* gorder = nullptr;       // grid blocks in launch order
+    int ngblk = 0;
+    int64_t total = 0;           // summed length of the clusters' lists
+};
+int cluster_setup(Ctx* ctx, const Tree* tree, const Targets& t, int tpc, Scratch& s, ClusterPlan* plan,
+                  cudaStream_t st);
+// Adds the clusters' interpolated far field to res [4][n] (and to far_io [4][n]
+// when not null) from the grid values rg [4][ng].
+int cluster_l2p(Ctx* ctx, const ClusterPlan& plan, const Targets& t, const double* rg, double* res,
+                double* far_io, cudaStream_t st);
 int tree_lists(Ctx* ctx, const Tree* tree, const Targets& t, int tpb, const double* tsig, Scratch& s, int** list,
-               int2** blist, int** order, int64_t* total, cudaStream_t st, double cut_override = 0.0);
+               int2** blist, int** order, int64_t* total, cudaStream_t st, double cut_override = 0.0,
+               const ClusterPlan* clusters = nullptr);
 
 // frames.cu: chart local coordinates and the Gauss flux (lsm_chart_frames,
 // lsm_gauss_flux); all arrays on the device, nodes in solve order

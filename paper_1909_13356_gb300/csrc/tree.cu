@@ -677,7 +677,39 @@ struct WalkArgs {
     uint32_t* cnt;         // pass 0: list length of each block
     int* list;             // pass 1
     int2* blist;           // pass 1: (offset, length)
+    // target clusters: a node that block b's cluster (b / bpc) takes is left
+    // to the cluster's grid (bpc 0: no clusters)
+    int bpc = 0;
+    const float4* c_lo = nullptr;
+    const float4* c_hi = nullptr;
+    const float4* c_acc = nullptr;
+    const float* nr = nullptr;   // node radii
 };
+
+// True when cluster c takes node `node` (which has proxies): the node's box is
+// beyond the near radius from the cluster's box, the cluster's box satisfies
+// the node's opening rule (its proxies represent it there: source side), and
+// every point of the node's frame box is at least the cluster's opening radius
+// r_C + q h_C from the cluster's centre (the node's field is smooth enough over
+// the cluster's box for its grid: target side).  FP32 with a 1e-4 margin.
+__device__ __forceinline__ bool cluster_takes(const WalkArgs& A, int64_t node, int c)
+{
+    const float4 bl = A.c_lo[c], bh = A.c_hi[c];
+    const float4 lo = A.nlo[node], hi = A.nhi[node];
+    const float gx = fmaxf(0.0f, fmaxf(lo.x - bh.x, bl.x - hi.x));
+    const float gy = fmaxf(0.0f, fmaxf(lo.y - bh.y, bl.y - hi.y));
+    const float gz = fmaxf(0.0f, fmaxf(lo.z - bh.z, bl.z - hi.z));
+    if (!(gx * gx + gy * gy + gz * gz > A.cut2 * lo.w * lo.w * 1.0001f)) return false;
+    const float4 ac = A.acc[node];
+    const float dx = fmaxf(0.0f, fmaxf(bl.x - ac.x, ac.x - bh.x));
+    const float dy = fmaxf(0.0f, fmaxf(bl.y - ac.y, ac.y - bh.y));
+    const float dz = fmaxf(0.0f, fmaxf(bl.z - ac.z, ac.z - bh.z));
+    if (!(dx * dx + dy * dy + dz * dz >= ac.w * 1.0001f)) return false;
+    const float4 cc = A.c_acc[c];
+    const float ex = ac.x - cc.x, ey = ac.y - cc.y, ez = ac.z - cc.z;
+    const float d = sqrtf(ex * ex + ey * ey + ez * ez) - A.nr[node];
+    return d > 0.0f && d * d >= cc.w * 1.0001f;
+}
 
 // Depth-first walk of the tree for one target block (children in Morton
 // order, so the list is in a fixed order).  Pass 0 counts, pass 1 writes.
@@ -696,6 +728,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass
         const int l = v >> 26, i = v & ((1 << 26) - 1);
         const int64_t node = A.lev_off[l] + i;
         const int4 f = A.info[node];
+        if (f.z >= 0 && A.bpc > 0 && cluster_takes(A, node, b / A.bpc)) continue;   // the cluster's grid has it
         if (f.z >= 0) {
             const float4 lo = A.nlo[node], hi = A.nhi[node];
             const float gx = fmaxf(0.0f, fmaxf(lo.x - bh.x, bl.x - hi.x));
@@ -743,6 +776,260 @@ __global__ void k_order_keys(const uint32_t* __restrict__ cnt, int n, uint32_t* 
     vals[b] = (uint32_t)b;
 }
 
+// ---------------------------------------------------------------- target clusters
+// A run of tpc consecutive Morton-sorted targets (a cluster) gets its own
+// oriented box: the principal axes of its targets (FP64 mean and covariance,
+// Jacobi eigenvectors) and their extents along them, and a tensor Chebyshev
+// grid (second kind) on that box with per-axis counts chosen as for the
+// source nodes' proxies (the widest axis p + 1 points).  A node far enough
+// from the cluster acts on the grid's points instead of on the targets:
+// the field of its proxies is smooth over the cluster's box, and its
+// degree-p interpolant errs like exp(-C) when the node is at least
+// r + q_p h_max from the box's centre (q_p = cosh(C / p), the same bound as
+// the source side).  The targets then interpolate the grid's values
+// (barycentric Lagrange form, FP64).
+
+__device__ int4 grid_counts_dev(const double h[3], int p, double C)
+{
+    double hmax = 0.0;
+    for (int a = 0; a < 3; a++) hmax = fmax(hmax, h[a]);
+    const double d = cosh(C / p) * hmax;
+    int n[3];
+    for (int a = 0; a < 3; a++) {
+        if (!(h[a] > 0.0)) {
+            n[a] = 1;
+        } else if (h[a] == hmax) {
+            n[a] = p + 1;
+        } else {
+            const int pa = (int)ceil((C + log(32.0)) / acosh(d / h[a]) - 1e-9);
+            n[a] = min(p, max(1, pa)) + 1;
+        }
+    }
+    return make_int4(n[0], n[1], n[2], 0);
+}
+
+// One CTA per cluster: frame (centre, axes as rows, half-widths) into
+// frame[16 c ...], grid counts, the outward box of the oriented box, and the
+// centre with the squared opening radius (r + q_p h_max)^2.
+__global__ void __launch_bounds__(kFrameThreads) k_cluster_frames(const double* __restrict__ x, int64_t ld, int n,
+                                                                  int tpc, double C, int p, double* __restrict__ frame,
+                                                                  int4* __restrict__ counts, float4* __restrict__ clo,
+                                                                  float4* __restrict__ chi, float4* __restrict__ cacc)
+{
+    __shared__ double sm[(kFrameThreads / 32) * 6];
+    __shared__ double s_e[3][3];
+    const int c = blockIdx.x;
+    const int64_t i0 = (int64_t)c * tpc, i1 = min((int64_t)n, i0 + tpc);
+    const double cnt = (double)max((int64_t)1, i1 - i0);
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kFrameThreads)
+        for (int k = 0; k < 3; k++) m[k] += x[k * ld + i];
+    block_sum<3>(m, sm);
+    for (int k = 0; k < 3; k++) m[k] /= cnt;
+    double cv[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kFrameThreads) {
+        const double d0 = x[i] - m[0], d1 = x[ld + i] - m[1], d2 = x[2 * ld + i] - m[2];
+        cv[0] += d0 * d0;
+        cv[1] += d0 * d1;
+        cv[2] += d0 * d2;
+        cv[3] += d1 * d1;
+        cv[4] += d1 * d2;
+        cv[5] += d2 * d2;
+    }
+    block_sum<6>(cv, sm);
+    if (threadIdx.x == 0) {
+        double a[3][3] = {{cv[0], cv[1], cv[2]}, {cv[1], cv[3], cv[4]}, {cv[2], cv[4], cv[5]}}, v[3][3];
+        jacobi3(a, v);
+        for (int ax = 0; ax < 3; ax++)
+            for (int k = 0; k < 3; k++) s_e[ax][k] = v[k][ax];
+    }
+    __syncthreads();
+    double e[3][3];
+    for (int ax = 0; ax < 3; ax++)
+        for (int k = 0; k < 3; k++) e[ax][k] = s_e[ax][k];
+    double ext[6] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kFrameThreads) {
+        const double d[3] = {x[i] - m[0], x[ld + i] - m[1], x[2 * ld + i] - m[2]};
+        for (int ax = 0; ax < 3; ax++) {
+            const double t = d[0] * e[ax][0] + d[1] * e[ax][1] + d[2] * e[ax][2];
+            ext[ax] = fmax(ext[ax], t);
+            ext[3 + ax] = fmax(ext[3 + ax], -t);
+        }
+    }
+    for (int k = 0; k < 6; k++)
+        for (int o = 16; o > 0; o >>= 1) ext[k] = fmax(ext[k], __shfl_xor_sync(0xffffffffu, ext[k], o));
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 6; k++) sm[w * 6 + k] = ext[k];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < 6; k++)
+        for (int j = 1; j < kFrameThreads / 32; j++) ext[k] = fmax(ext[k], sm[j * 6 + k]);
+    double h[3], r2 = 0.0;
+    for (int ax = 0; ax < 3; ax++) {
+        const double hi = ext[ax], lo = -ext[3 + ax];
+        h[ax] = 0.5 * (hi - lo);
+        r2 += h[ax] * h[ax];
+        const double mid = 0.5 * (hi + lo);
+        for (int k = 0; k < 3; k++) m[k] += mid * e[ax][k];
+    }
+    // a small floor keeps the local coordinates of a flat cluster in [-1, 1]
+    const double hmin = 1e-9 * sqrt(r2) + 1e-300;
+    double hmax = 0.0;
+    for (int ax = 0; ax < 3; ax++) {
+        h[ax] = fmax(h[ax], hmin);
+        hmax = fmax(hmax, h[ax]);
+    }
+    double* F = frame + 16 * (int64_t)c;
+    for (int k = 0; k < 3; k++) F[k] = m[k];
+    for (int ax = 0; ax < 3; ax++)
+        for (int k = 0; k < 3; k++) F[3 + 3 * ax + k] = e[ax][k];
+    for (int ax = 0; ax < 3; ax++) F[12 + ax] = h[ax];
+    F[15] = 0.0;
+    counts[c] = grid_counts_dev(h, p, C);
+    float lo[3], hi[3];
+    for (int k = 0; k < 3; k++) {
+        double ext_k = 0.0;
+        for (int ax = 0; ax < 3; ax++) ext_k += h[ax] * fabs(e[ax][k]);
+        lo[k] = __double2float_rd(m[k] - ext_k * (1.0 + 1e-12));
+        hi[k] = __double2float_ru(m[k] + ext_k * (1.0 + 1e-12));
+    }
+    clo[c] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    chi[c] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+    const double R = sqrt(r2) + cosh(C / p) * hmax;
+    cacc[c] = make_float4((float)m[0], (float)m[1], (float)m[2], __double2float_ru(R * R));
+}
+
+// Grid points of every cluster (one CTA per cluster), SoA with stride ng:
+// point g = (k0 n1 + k1) n2 + k2 at centre + sum_a h_a cos(k_a pi / (n_a - 1)) e_a;
+// the slots up to the next multiple of kEvalThreads repeat the first point.
+__global__ void k_cluster_points(const double* __restrict__ frame, const int4* __restrict__ counts, int64_t ng,
+                                 double* __restrict__ gx)
+{
+    const int c = blockIdx.x;
+    const double* F = frame + 16 * (int64_t)c;
+    const int4 nc = counts[c];
+    const int np = nc.x * nc.y * nc.z;
+    const int npad = (np + kEvalThreads - 1) / kEvalThreads * kEvalThreads;
+    for (int g = threadIdx.x; g < npad; g += blockDim.x) {
+        const int q = g < np ? g : 0;
+        const int k[3] = {q / (nc.y * nc.z), (q / nc.z) % nc.y, q % nc.z};
+        const int na[3] = {nc.x, nc.y, nc.z};
+        double pt[3] = {F[0], F[1], F[2]};
+        for (int ax = 0; ax < 3; ax++) {
+            const double t = na[ax] > 1 ? cospi((double)k[ax] / (double)(na[ax] - 1)) : 0.0;
+            for (int j = 0; j < 3; j++) pt[j] += F[12 + ax] * t * F[3 + 3 * ax + j];
+        }
+        for (int j = 0; j < 3; j++) gx[j * ng + nc.w + g] = pt[j];
+    }
+}
+
+struct ClusterWalkArgs {
+    WalkArgs W;            // the tree and the cluster boxes (W.c_lo, ...)
+    int ncl;
+    const uint32_t* off;   // pass 1: list offset of each cluster
+    uint32_t* cnt;         // pass 0: list length of each cluster
+    int* list;
+    int2* clist;           // pass 1: (offset, length)
+};
+
+// Depth-first walk per cluster: the proxy tiles of the nodes the cluster
+// takes (cluster_takes), in the same order as the block walk would meet them.
+__global__ void __launch_bounds__(kWalkThreads) k_cluster_walk(ClusterWalkArgs A, int pass)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= A.ncl) return;
+    int stk[2 * kMaxLevels + 2];
+    int sp = 0;
+    stk[sp++] = A.W.top << 26;
+    uint32_t n = 0;
+    const uint32_t o = pass ? A.off[c] : 0u;
+    while (sp > 0) {
+        const int v = stk[--sp];
+        const int l = v >> 26, i = v & ((1 << 26) - 1);
+        const int64_t node = A.W.lev_off[l] + i;
+        const int4 f = A.W.info[node];
+        if (f.z >= 0 && cluster_takes(A.W, node, c)) {
+            if (pass)
+                for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.W.ntiles + f.z + k;
+            n += f.w;
+            continue;
+        }
+        if (l == 0) continue;
+        const int64_t nch = A.W.lev_off[l] - A.W.lev_off[l - 1];
+        if (2 * i + 1 < nch) stk[sp++] = ((l - 1) << 26) | (2 * i + 1);
+        stk[sp++] = ((l - 1) << 26) | (2 * i);
+    }
+    if (pass)
+        A.clist[c] = make_int2((int)o, (int)n);
+    else
+        A.cnt[c] = n;
+}
+
+// Each block of grid points takes its cluster's list; launch order as given.
+__global__ void k_grid_blocks(const int* __restrict__ gb_cluster, int ngblk, const int2* __restrict__ clist,
+                              int2* __restrict__ gblist, int* __restrict__ gorder)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngblk) return;
+    gblist[g] = clist[gb_cluster[g]];
+    gorder[g] = g;
+}
+
+// The targets' share of their clusters' far field: tensor Lagrange
+// interpolation (barycentric form on the Chebyshev points of the second kind)
+// of the grid values, Phi in FP64, the gradient likewise; added to res [4][n]
+// and, when recording, far_io [4][n].
+__global__ void k_cluster_l2p(const double* __restrict__ x, int64_t ld, int n, int tpc,
+                              const double* __restrict__ frame, const int4* __restrict__ counts,
+                              const double* __restrict__ rg, int64_t ng, double* __restrict__ res,
+                              double* __restrict__ far_io)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = i / tpc;
+    const double* F = frame + 16 * (int64_t)c;
+    const int4 nc = counts[c];
+    const int na[3] = {nc.x, nc.y, nc.z};
+    const double d[3] = {x[i] - F[0], x[ld + i] - F[1], x[2 * ld + i] - F[2]};
+    double L[3][kMaxN64];
+    for (int ax = 0; ax < 3; ax++) {
+        const int m = na[ax];
+        if (m == 1) {
+            L[ax][0] = 1.0;
+            continue;
+        }
+        double xi = (d[0] * F[3 + 3 * ax] + d[1] * F[4 + 3 * ax] + d[2] * F[5 + 3 * ax]) / F[12 + ax];
+        xi = fmin(1.0, fmax(-1.0, xi));
+        int hit = -1;
+        double den = 0.0;
+        for (int k = 0; k < m; k++) {
+            const double t = cospi((double)k / (double)(m - 1));
+            const double wk = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == m - 1) ? 0.5 : 1.0);
+            if (xi == t) hit = k;
+            L[ax][k] = wk / (xi - t);
+            den += L[ax][k];
+        }
+        for (int k = 0; k < m; k++) L[ax][k] = hit >= 0 ? (k == hit ? 1.0 : 0.0) : L[ax][k] / den;
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t base = nc.w;
+    for (int k0 = 0; k0 < na[0]; k0++) {
+        double s1[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k1 = 0; k1 < na[1]; k1++) {
+            double s2[4] = {0.0, 0.0, 0.0, 0.0};
+            const int64_t g0 = base + ((int64_t)k0 * na[1] + k1) * na[2];
+            for (int k2 = 0; k2 < na[2]; k2++)
+                for (int f = 0; f < 4; f++) s2[f] = fma(L[2][k2], rg[f * ng + g0 + k2], s2[f]);
+            for (int f = 0; f < 4; f++) s1[f] = fma(L[1][k1], s2[f], s1[f]);
+        }
+        for (int f = 0; f < 4; f++) acc[f] = fma(L[0][k0], s1[f], acc[f]);
+    }
+    for (int f = 0; f < 4; f++) res[(int64_t)f * n + i] += acc[f];
+    if (far_io)
+        for (int f = 0; f < 4; f++) far_io[(int64_t)f * n + i] += acc[f];
+}
+
 }  // namespace
 
 bool tree_wanted(const Ctx* ctx, const Mesh* me, bool ff)
@@ -756,7 +1043,8 @@ bool tree_wanted(const Ctx* ctx, const Mesh* me, bool ff)
 void tree_free(Tree* t)
 {
     if (!t) return;
-    void* ps[] = {t->node_lo, t->node_hi, t->node_info, t->node_acc, t->p_pos, t->p_nw, t->p_lo, t->p_nwlo, t->tile_lo,
+    void* ps[] = {t->node_lo, t->node_hi, t->node_info, t->node_acc, t->node_r, t->p_pos, t->p_nw, t->p_lo, t->p_nwlo,
+                  t->tile_lo,
                   t->tile_hi, t->tile_chi, t->tile_clo};
     for (void* p : ps)
         if (p) cudaFree(p);
@@ -812,7 +1100,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     T->top = lev;
     T->nnodes = T->lev_off[lev + 1];
     if (!alloc(&T->node_lo, T->nnodes) || !alloc(&T->node_hi, T->nnodes) || !alloc(&T->node_info, T->nnodes) ||
-        !alloc(&T->node_acc, T->nnodes)) {
+        !alloc(&T->node_acc, T->nnodes) || !alloc(&T->node_r, T->nnodes)) {
         cudaGetLastError();
         ctx->err = "tree: out of device memory";
         return fail(LSM_E_OOM);
@@ -882,6 +1170,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     std::vector<int4> items, reds;
     std::vector<int4> hgrid(T->nnodes, make_int4(1, 1, 1, 0));
     std::vector<float4> hacc(T->nnodes, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+    std::vector<float> hrad(T->nnodes, 0.0f);
     std::vector<float4> ptlo, pthi, ptchi, ptclo;
     int64_t nptiles = 0, npartial = 0;
     for (int l = 1; l <= T->top; l++) {
@@ -919,6 +1208,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
             const double hmax = std::max(F.h[0], std::max(F.h[1], F.h[2]));
             const double R = grid == 2 ? r / theta : r + std::cosh(C / pn) * hmax;
             hacc[node] = make_float4((float)F.c[0], (float)F.c[1], (float)F.c[2], (float)(R * R));
+            hrad[node] = std::nextafter((float)r, INFINITY);
             const int npt = (int)((np + kTile - 1) / kTile);
             f.z = (int)nptiles;
             f.w = npt;
@@ -953,6 +1243,7 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
         }
     }
     if (cudaMemcpyAsync(T->node_acc, hacc.data(), sizeof(float4) * T->nnodes, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(T->node_r, hrad.data(), sizeof(float) * T->nnodes, cudaMemcpyHostToDevice, st) ||
         cudaMemcpyAsync(d_fr, hfr.data(), sizeof(NodeFrame) * T->nnodes, cudaMemcpyHostToDevice, st)) {
         ctx->err = "tree: copy failed";
         return fail(LSM_E_CUDA);
@@ -1044,8 +1335,114 @@ int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
     return LSM_OK;
 }
 
+static void fill_walk_tree(WalkArgs& W, const Tree* T, double cut)
+{
+    W.nlo = T->node_lo;
+    W.nhi = T->node_hi;
+    W.acc = T->node_acc;
+    W.info = T->node_info;
+    W.nr = T->node_r;
+    for (int l = 0; l <= kMaxLevels; l++) W.lev_off[l] = l <= T->top + 1 ? T->lev_off[l] : 0;
+    W.top = T->top;
+    W.ntiles = T->ntiles;
+    W.cut2 = (float)(cut * cut);
+}
+
+int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, Scratch& s, ClusterPlan* P, cudaStream_t st)
+{
+    ClusterPlan& cp = *P;
+    cp.tpc = tpc;
+    cp.ncl = (t.n + tpc - 1) / tpc;
+    const int ncl = cp.ncl;
+    LSM_CUDA_TRY(ctx, s.get(&cp.box_lo, ncl));
+    LSM_CUDA_TRY(ctx, s.get(&cp.box_hi, ncl));
+    LSM_CUDA_TRY(ctx, s.get(&cp.cacc, ncl));
+    LSM_CUDA_TRY(ctx, s.get(&cp.frame, 16 * (size_t)ncl));
+    LSM_CUDA_TRY(ctx, s.get(&cp.counts, ncl));
+    const double C = tree_bound(T->degree, T->theta);
+    k_cluster_frames<<<ncl, kFrameThreads, 0, st>>>(t.x, t.ld, t.n, tpc, C, T->degree, cp.frame, cp.counts, cp.box_lo,
+                                                    cp.box_hi, cp.cacc);
+    LSM_LAUNCHED(ctx);
+    // grid offsets on the host: each cluster's points start on a block boundary
+    std::vector<int4> hc(ncl);
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), cp.counts, sizeof(int4) * ncl, cudaMemcpyDeviceToHost, st));
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    std::vector<int> gb_cluster;
+    int64_t ng = 0;
+    for (int c = 0; c < ncl; c++) {
+        const int64_t np = (int64_t)hc[c].x * hc[c].y * hc[c].z;
+        const int64_t nb = (np + kEvalThreads - 1) / kEvalThreads;
+        hc[c].w = (int)ng;
+        for (int64_t b = 0; b < nb; b++) gb_cluster.push_back(c);
+        ng += nb * kEvalThreads;
+    }
+    if (ng >= ((int64_t)1 << 31)) {
+        ctx->err = "tree: too many cluster grid points";
+        return LSM_E_INVALID_ARG;
+    }
+    cp.ng = ng;
+    cp.ngblk = (int)gb_cluster.size();
+    int* d_gbc;
+    LSM_CUDA_TRY(ctx, s.get(&d_gbc, gb_cluster.size()));
+    LSM_CUDA_TRY(ctx, s.get(&cp.gx, 3 * (size_t)ng));
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(cp.counts, hc.data(), sizeof(int4) * ncl, cudaMemcpyHostToDevice, st));
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(d_gbc, gb_cluster.data(), sizeof(int) * gb_cluster.size(),
+                                      cudaMemcpyHostToDevice, st));
+    k_cluster_points<<<ncl, 128, 0, st>>>(cp.frame, cp.counts, ng, cp.gx);
+    LSM_LAUNCHED(ctx);
+    // the clusters' lists: count, scan, write
+    ClusterWalkArgs A;
+    fill_walk_tree(A.W, T, T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed);
+    A.W.c_lo = cp.box_lo;
+    A.W.c_hi = cp.box_hi;
+    A.W.c_acc = cp.cacc;
+    A.ncl = ncl;
+    uint32_t* cnt;
+    LSM_CUDA_TRY(ctx, s.get(&cnt, (size_t)ncl + 1));
+    int2* clist;
+    LSM_CUDA_TRY(ctx, s.get(&clist, ncl));
+    A.off = cnt;
+    A.cnt = cnt;
+    A.list = nullptr;
+    A.clist = clist;
+    k_cluster_walk<<<blocks_of(ncl, kWalkThreads), kWalkThreads, 0, st>>>(A, 0);
+    LSM_LAUNCHED(ctx);
+    int rc = scan_exclusive(ctx, cnt, ncl, cnt + ncl, st);
+    if (rc != LSM_OK) return rc;
+    uint32_t h_total = 0;
+    LSM_CUDA_TRY(ctx, cudaMemcpyAsync(&h_total, cnt + ncl, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (h_total >= (1u << 31)) {
+        ctx->err = "tree: cluster lists too long";
+        return LSM_E_INVALID_ARG;
+    }
+    cp.total = h_total;
+    LSM_CUDA_TRY(ctx, s.get(&cp.list, std::max<uint32_t>(1u, h_total)));
+    A.list = cp.list;
+    k_cluster_walk<<<blocks_of(ncl, kWalkThreads), kWalkThreads, 0, st>>>(A, 1);
+    LSM_LAUNCHED(ctx);
+    LSM_CUDA_TRY(ctx, s.get(&cp.gblist, std::max(1, cp.ngblk)));
+    LSM_CUDA_TRY(ctx, s.get(&cp.gorder, std::max(1, cp.ngblk)));
+    if (cp.ngblk > 0) {
+        k_grid_blocks<<<blocks_of(cp.ngblk, 256), 256, 0, st>>>(d_gbc, cp.ngblk, clist, cp.gblist, cp.gorder);
+        LSM_LAUNCHED(ctx);
+    }
+    return LSM_OK;
+}
+
+int cluster_l2p(Ctx* ctx, const ClusterPlan& cp, const Targets& t, const double* rg, double* res, double* far_io,
+                cudaStream_t st)
+{
+    if (t.n <= 0 || cp.ncl <= 0) return LSM_OK;
+    k_cluster_l2p<<<blocks_of(t.n, 128), 128, 0, st>>>(t.x, t.ld, t.n, cp.tpc, cp.frame, cp.counts, rg, cp.ng, res,
+                                                      far_io);
+    LSM_LAUNCHED(ctx);
+    return LSM_OK;
+}
+
 int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double* tsig, Scratch& s, int** list,
-               int2** blist, int** order, int64_t* total_out, cudaStream_t st, double cut_override)
+               int2** blist, int** order, int64_t* total_out, cudaStream_t st, double cut_override,
+               const ClusterPlan* clusters)
 {
     const int nblk = (t.n + tpb - 1) / tpb;
     float4 *blo = nullptr, *bhi = nullptr;
@@ -1068,9 +1465,16 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double*
     W.top = T->top;
     W.ntiles = T->ntiles;
     W.sigx = tsig != nullptr;
+    W.nr = T->node_r;
     // the near radius of the pair kernel that evaluates the lists
     const double cut = cut_override > 0 ? cut_override : (T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed);
     W.cut2 = (float)(cut * cut);
+    if (clusters && clusters->tpc > 0) {
+        W.bpc = clusters->tpc / tpb;
+        W.c_lo = clusters->box_lo;
+        W.c_hi = clusters->box_hi;
+        W.c_acc = clusters->cacc;
+    }
     W.off = cnt;
     W.cnt = cnt;
     W.list = nullptr;
