@@ -429,6 +429,9 @@ struct ClusterPlan {
     int* gorder = nullptr;       // grid blocks in launch order
     int ngblk = 0;
     int64_t total = 0;           // summed length of the clusters' lists
+    float4 *blo = nullptr, *bhi = nullptr;   // the target blocks' boxes (kEvalThreads targets each)
+    uint32_t* cbits = nullptr;   // [ncl][cwords]: bit `node` set when the cluster took the node
+    int64_t cwords = 0;
 };
 int cluster_setup(Ctx* ctx, const Tree* tree, const Targets& t, int tpc, Scratch& s, ClusterPlan* plan,
                   cudaStream_t st);

@@ -677,14 +677,34 @@ struct WalkArgs {
     uint32_t* cnt;         // pass 0: list length of each block
     int* list;             // pass 1
     int2* blist;           // pass 1: (offset, length)
-    // target clusters: a node that block b's cluster (b / bpc) takes is left
-    // to the cluster's grid (bpc 0: no clusters)
+    // target clusters: the nodes block b's cluster (b / bpc) took, a bitmap
+    // of cwords words per cluster over the tree's nodes, are left to the
+    // cluster's grid (bpc 0: no clusters)
     int bpc = 0;
-    const float4* c_lo = nullptr;
+    const uint32_t* cbits = nullptr;
+    int64_t cwords = 0;
+    const float4* c_lo = nullptr;   // cluster walk: the clusters' boxes
     const float4* c_hi = nullptr;
     const float4* c_acc = nullptr;
-    const float* nr = nullptr;   // node radii
+    const float* nr = nullptr;      // node radii
 };
+
+// The block rule: node `node` (with proxies) acts on a target box through its
+// proxies when its box is beyond the near radius from the target box (sigma
+// sw) and the target box satisfies its opening rule.
+__device__ __forceinline__ bool box_takes(const WalkArgs& A, int64_t node, float4 bl, float4 bh, float sw)
+{
+    const float4 lo = A.nlo[node], hi = A.nhi[node];
+    const float gx = fmaxf(0.0f, fmaxf(lo.x - bh.x, bl.x - hi.x));
+    const float gy = fmaxf(0.0f, fmaxf(lo.y - bh.y, bl.y - hi.y));
+    const float gz = fmaxf(0.0f, fmaxf(lo.z - bh.z, bl.z - hi.z));
+    if (!(gx * gx + gy * gy + gz * gz > A.cut2 * sw * sw * 1.0001f)) return false;
+    const float4 ac = A.acc[node];
+    const float dx = fmaxf(0.0f, fmaxf(bl.x - ac.x, ac.x - bh.x));
+    const float dy = fmaxf(0.0f, fmaxf(bl.y - ac.y, ac.y - bh.y));
+    const float dz = fmaxf(0.0f, fmaxf(bl.z - ac.z, ac.z - bh.z));
+    return dx * dx + dy * dy + dz * dz >= ac.w * 1.0001f;
+}
 
 // True when cluster c takes node `node` (which has proxies): the node's box is
 // beyond the near radius from the cluster's box, the cluster's box satisfies
@@ -694,17 +714,8 @@ struct WalkArgs {
 // the cluster's box for its grid: target side).  FP32 with a 1e-4 margin.
 __device__ __forceinline__ bool cluster_takes(const WalkArgs& A, int64_t node, int c)
 {
-    const float4 bl = A.c_lo[c], bh = A.c_hi[c];
-    const float4 lo = A.nlo[node], hi = A.nhi[node];
-    const float gx = fmaxf(0.0f, fmaxf(lo.x - bh.x, bl.x - hi.x));
-    const float gy = fmaxf(0.0f, fmaxf(lo.y - bh.y, bl.y - hi.y));
-    const float gz = fmaxf(0.0f, fmaxf(lo.z - bh.z, bl.z - hi.z));
-    if (!(gx * gx + gy * gy + gz * gz > A.cut2 * lo.w * lo.w * 1.0001f)) return false;
+    if (!box_takes(A, node, A.c_lo[c], A.c_hi[c], A.nlo[node].w)) return false;
     const float4 ac = A.acc[node];
-    const float dx = fmaxf(0.0f, fmaxf(bl.x - ac.x, ac.x - bh.x));
-    const float dy = fmaxf(0.0f, fmaxf(bl.y - ac.y, ac.y - bh.y));
-    const float dz = fmaxf(0.0f, fmaxf(bl.z - ac.z, ac.z - bh.z));
-    if (!(dx * dx + dy * dy + dz * dz >= ac.w * 1.0001f)) return false;
     const float4 cc = A.c_acc[c];
     const float ex = ac.x - cc.x, ey = ac.y - cc.y, ez = ac.z - cc.z;
     const float d = sqrtf(ex * ex + ey * ey + ez * ez) - A.nr[node];
@@ -728,26 +739,16 @@ __global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass
         const int l = v >> 26, i = v & ((1 << 26) - 1);
         const int64_t node = A.lev_off[l] + i;
         const int4 f = A.info[node];
-        if (f.z >= 0 && A.bpc > 0 && cluster_takes(A, node, b / A.bpc)) continue;   // the cluster's grid has it
         if (f.z >= 0) {
-            const float4 lo = A.nlo[node], hi = A.nhi[node];
-            const float gx = fmaxf(0.0f, fmaxf(lo.x - bh.x, bl.x - hi.x));
-            const float gy = fmaxf(0.0f, fmaxf(lo.y - bh.y, bl.y - hi.y));
-            const float gz = fmaxf(0.0f, fmaxf(lo.z - bh.z, bl.z - hi.z));
-            const float sw = A.sigx ? bl.w : lo.w;
-            if (gx * gx + gy * gy + gz * gz > A.cut2 * sw * sw * 1.0001f) {
-                // opening rule: the block at distance >= radius / theta_n
-                // from the centre of the node's frame
-                const float4 ac = A.acc[node];
-                const float dx = fmaxf(0.0f, fmaxf(bl.x - ac.x, ac.x - bh.x));
-                const float dy = fmaxf(0.0f, fmaxf(bl.y - ac.y, ac.y - bh.y));
-                const float dz = fmaxf(0.0f, fmaxf(bl.z - ac.z, ac.z - bh.z));
-                if (dx * dx + dy * dy + dz * dz >= ac.w * 1.0001f) {
-                    if (pass)
-                        for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.ntiles + f.z + k;
-                    n += f.w;
-                    continue;
-                }
+            // the cluster's grid has it
+            if (A.bpc > 0 && ((A.cbits[(int64_t)(b / A.bpc) * A.cwords + (node >> 5)] >> (node & 31)) & 1u)) continue;
+            // opening rule: the block at distance >= the node's opening radius
+            // from the centre of its frame
+            if (box_takes(A, node, bl, bh, A.sigx ? bl.w : A.nlo[node].w)) {
+                if (pass)
+                    for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.ntiles + f.z + k;
+                n += f.w;
+                continue;
             }
         }
         if (l == 0) {
@@ -927,14 +928,21 @@ __global__ void k_cluster_points(const double* __restrict__ frame, const int4* _
 struct ClusterWalkArgs {
     WalkArgs W;            // the tree and the cluster boxes (W.c_lo, ...)
     int ncl;
+    int nblk, bpc;         // target blocks, blocks per cluster
+    const float4* blo;     // the blocks' boxes
+    const float4* bhi;
+    uint32_t* cbits;       // pass 1: the bitmap of taken nodes (zeroed)
     const uint32_t* off;   // pass 1: list offset of each cluster
     uint32_t* cnt;         // pass 0: list length of each cluster
     int* list;
     int2* clist;           // pass 1: (offset, length)
 };
 
-// Depth-first walk per cluster: the proxy tiles of the nodes the cluster
-// takes (cluster_takes), in the same order as the block walk would meet them.
+// Depth-first walk per cluster: the nodes the cluster takes (cluster_takes)
+// and their proxy tiles.  The walk does not go below a node that one of the
+// cluster's blocks takes itself (the block rule), so every node the cluster
+// takes is reached by all of its blocks' walks, which skip it (the bitmap):
+// every (target, node) interaction is counted once.
 __global__ void __launch_bounds__(kWalkThreads) k_cluster_walk(ClusterWalkArgs A, int pass)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -944,16 +952,25 @@ __global__ void __launch_bounds__(kWalkThreads) k_cluster_walk(ClusterWalkArgs A
     stk[sp++] = A.W.top << 26;
     uint32_t n = 0;
     const uint32_t o = pass ? A.off[c] : 0u;
+    const int b0 = c * A.bpc, b1 = min(A.nblk, b0 + A.bpc);
     while (sp > 0) {
         const int v = stk[--sp];
         const int l = v >> 26, i = v & ((1 << 26) - 1);
         const int64_t node = A.W.lev_off[l] + i;
         const int4 f = A.W.info[node];
-        if (f.z >= 0 && cluster_takes(A.W, node, c)) {
-            if (pass)
-                for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.W.ntiles + f.z + k;
-            n += f.w;
-            continue;
+        if (f.z >= 0) {
+            if (cluster_takes(A.W, node, c)) {
+                if (pass) {
+                    for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.W.ntiles + f.z + k;
+                    A.cbits[(int64_t)c * A.W.cwords + (node >> 5)] |= 1u << (node & 31);
+                }
+                n += f.w;
+                continue;
+            }
+            bool some_block = false;
+            for (int b = b0; b < b1 && !some_block; b++)
+                some_block = box_takes(A.W, node, A.blo[b], A.bhi[b], A.W.nlo[node].w);
+            if (some_block) continue;
         }
         if (l == 0) continue;
         const int64_t nch = A.W.lev_off[l] - A.W.lev_off[l - 1];
@@ -1390,13 +1407,29 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, Scratch& s
                                       cudaMemcpyHostToDevice, st));
     k_cluster_points<<<ncl, 128, 0, st>>>(cp.frame, cp.counts, ng, cp.gx);
     LSM_LAUNCHED(ctx);
+    // the target blocks' boxes (as the block walk sees them) and the bitmap
+    const int tpb = kEvalThreads;
+    const int nblk = (t.n + tpb - 1) / tpb;
+    LSM_CUDA_TRY(ctx, s.get(&cp.blo, nblk));
+    LSM_CUDA_TRY(ctx, s.get(&cp.bhi, nblk));
+    k_block_boxes<<<nblk, kEvalThreads, 0, st>>>(t.x, t.ld, t.n, tpb, nullptr, cp.blo, cp.bhi);
+    LSM_LAUNCHED(ctx);
+    cp.cwords = (T->nnodes + 31) / 32;
+    LSM_CUDA_TRY(ctx, s.get(&cp.cbits, (size_t)cp.cwords * ncl));
+    LSM_CUDA_TRY(ctx, cudaMemsetAsync(cp.cbits, 0, sizeof(uint32_t) * (size_t)cp.cwords * ncl, st));
     // the clusters' lists: count, scan, write
     ClusterWalkArgs A;
     fill_walk_tree(A.W, T, T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed);
     A.W.c_lo = cp.box_lo;
     A.W.c_hi = cp.box_hi;
     A.W.c_acc = cp.cacc;
+    A.W.cwords = cp.cwords;
     A.ncl = ncl;
+    A.nblk = nblk;
+    A.bpc = tpc / tpb;
+    A.blo = cp.blo;
+    A.bhi = cp.bhi;
+    A.cbits = cp.cbits;
     uint32_t* cnt;
     LSM_CUDA_TRY(ctx, s.get(&cnt, (size_t)ncl + 1));
     int2* clist;
@@ -1471,9 +1504,8 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double*
     W.cut2 = (float)(cut * cut);
     if (clusters && clusters->tpc > 0) {
         W.bpc = clusters->tpc / tpb;
-        W.c_lo = clusters->box_lo;
-        W.c_hi = clusters->box_hi;
-        W.c_acc = clusters->cacc;
+        W.cbits = clusters->cbits;
+        W.cwords = clusters->cwords;
     }
     W.off = cnt;
     W.cnt = cnt;
