@@ -140,7 +140,7 @@ typedef struct {
      * tensor Chebyshev grid (degree tree_ff_degree on the widest axis); a
      * node far enough from a cluster (the opening rule from the targets'
      * side, with the same error bound) acts on the grid's points, and the
-     * targets interpolate its field from them.  0 selects 2048; -1: off. */
+     * targets interpolate its field from them.  0 selects 4096; -1: off. */
     int32_t tree_ff_cluster;
 } lsm_options;
 
