@@ -168,33 +168,6 @@ constexpr int kHTabN = 520;                   // covers w < 32.5 (u < 5.70)
 constexpr float kHTabWmax = (float)kHTabN / kHTabPerUnit;
 __device__ float4 g_htab[kHTabN * 3];         // filled once per device by the host
 
-// FP32 radial factors from the table's leading parts: fH = a^3 H(w) and
-// FK = a^5 K with K = H'(u)/u = 2 dH/dw.  Depending on w alone, they avoid
-// the amplified rounding of u that the erfc form suffers where G is steep.
-__device__ __forceinline__ void radial_tab32(float r2, float a, const float4* __restrict__ tab, float& fH,
-                                             float& FK)
-{
-    const float a2 = a * a;
-    const float w = r2 * a2;
-    if (w < kHTabWmax) {
-        const int k = min((int)(w * (float)kHTabPerUnit), kHTabN - 1);
-        const float t = w - ((float)k + 0.5f) * (1.0f / kHTabPerUnit);
-        const float4 c01 = tab[3 * k], c23 = tab[3 * k + 1], c45 = tab[3 * k + 2];
-        const float H = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(c45.w, t, c45.z), t, c45.x), t, c23.z), t, c23.x), t, c01.z),
-                             t, c01.x);
-        const float dH = fmaf(fmaf(fmaf(fmaf(fmaf(6.0f * c45.w, t, 5.0f * c45.z), t, 4.0f * c45.x), t,
-                                        3.0f * c23.z), t, 2.0f * c23.x), t, c01.z);
-        const float a3 = a2 * a;
-        fH = a3 * H;
-        FK = 2.0f * a3 * a2 * dH;
-    } else {
-        const float ri = rsqrt_refined(r2);
-        const float ri2 = ri * ri;
-        fH = ri2 * ri;
-        FK = -3.0f * fH * ri2;
-    }
-}
-
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
 {
     const float s = hi + x;
@@ -396,11 +369,15 @@ __device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, f
 // FULL: the table's c0..c4 in float-float Horner steps (H to ~1e-15; the
 // FP32 c3 t^3 term alone errs by 4e-12 of H near w = 1, |t| <= 1/32); else
 // c0..c2 (the mixed path's near Phi, to ~1e-11 of H).
+// Also returns the FP32 radial factors of the gradient, fH = a^3 H(w) and
+// FK = a^5 K = 2 a^5 dH/dw, from the same table interval (or the Laplace
+// limits beyond the table), so that the caller need not look them up again.
 template <bool FULL>
 __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const float4& yl, const float4& nl,
                                         const float* qh, const float* ql, bool far,
                                         const float4* __restrict__ tab, float& qhi, float& qlo, float& dxh,
-                                        float& dyh, float& dzh, float& rh, float& dh, float& r0)
+                                        float& dyh, float& dzh, float& rh, float& dh, float& r0, float& gfH,
+                                        float& gFK)
 {
     float dxl, dyl, dzl, e;
     two_diff(y.x, qh[0], dxh, e);
@@ -455,6 +432,10 @@ __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const 
         float a3h, a3l;
         ff_mul(aah, aal, y.w, yl.w, a3h, a3l);
         ff_mul(a3h, a3l, Hh, Hl, fHh, fHl);
+        const float dH = fmaf(fmaf(fmaf(fmaf(fmaf(6.0f * c45.w, th, 5.0f * c45.z), th, 4.0f * c45.x), th,
+                                        3.0f * c23.z), th, 2.0f * c23.x), th, c01.z);
+        gfH = fHh;
+        gFK = 2.0f * a3h * aah * dH;
     } else {
         // 1/|r| = r0 (1 - delta)^-1/2 = r0 (1 + delta/2 + 3 delta^2/8 + ...),
         // delta = 1 - |r|^2 r0^2 (~5e-7 from the hardware estimate); fH =
@@ -471,6 +452,8 @@ __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const 
         const float q2l = fmaf(2.0f * r0, ril, ae);
         fHh = a * r0;
         fHl = fmaf(a, r0, -fHh) + fmaf(a, ril, q2l * r0);
+        gfH = fHh;
+        gFK = -3.0f * fHh * a;
     }
     const float d0 = n.x * dxh, d1 = n.y * dyh, d2 = n.z * dzh;
     const float f0 = fmaf(n.x, dxh, -d0), f1 = fmaf(n.y, dyh, -d1), f2 = fmaf(n.z, dzh, -d2);
@@ -811,14 +794,13 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                     // the pair's a: the source's, or the target's in sigma(x) mode
                     const float4 ya = SIGX ? make_float4(y.x, y.y, y.z, ta_h[k]) : y;
                     const float4 yla = SIGX ? make_float4(yl.x, yl.y, yl.z, ta_l[k]) : yl;
-                    float qh_, ql_, dxh, dyh, dzh, rh, dh, r0;
-                    ff_pair<false>(ya, n, yla, nl, qh[k], ql[k], false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
+                    float qh_, ql_, dxh, dyh, dzh, rh, dh, r0, fH, FK;
+                    ff_pair<false>(ya, n, yla, nl, qh[k], ql[k], false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0,
+                                   fH, FK);
                     float sph, tph;
                     two_sum(cph[k], qh_, sph, tph);
                     cph[k] = sph;
                     cpl[k] += tph + ql_;
-                    float fH, FK;
-                    radial_tab32(rh, ya.w, s_htab, fH, FK);
                     const float tq = dh * FK;
                     two_sum_acc(cg[k][0], cgl[k][0], -fmaf(n.x, fH, tq * dxh));
                     two_sum_acc(cg[k][1], cgl[k][1], -fmaf(n.y, fH, tq * dyh));
@@ -1302,14 +1284,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                         g[1] = fmaf(tq, dyh, fmaf(-n.y, ri3, g[1]));
                         g[2] = fmaf(tq, dzh, fmaf(-n.z, ri3, g[2]));
                     } else {
-                        float r0;
-                        ff_pair<true>(y, n, yl, nl, qh, ql, false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0);
+                        float r0, fH, FK;
+                        ff_pair<true>(y, n, yl, nl, qh, ql, false, s_htab, qh_, ql_, dxh, dyh, dzh, rh, dh, r0, fH,
+                                      FK);
                         float sph, tph;
                         two_sum(cph, qh_, sph, tph);
                         cph = sph;
                         cpl += tph + ql_;
-                        float fH, FK;
-                        radial_tab32(rh, y.w, s_htab, fH, FK);
                         const float tq = dh * FK;
                         two_sum_acc(g[0], gn[0], -fmaf(n.x, fH, tq * dxh));
                         two_sum_acc(g[1], gn[1], -fmaf(n.y, fH, tq * dyh));
