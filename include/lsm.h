@@ -434,6 +434,34 @@ int lsm_chart_frames_nodes(lsm_mesh* mesh, int64_t n, const int32_t* tri, const 
 int lsm_gauss_flux_nodes(lsm_mesh* mesh, int64_t n, const int32_t* tri, const double* uvw, const double* x,
                          const double* grad, const double* jac, const double* x0, double* eps0, void* stream);
 
+/* Per-triangle Gauss flux (Sec. 5, the quantity of lsm_gauss_flux split by
+ * skeleton triangle): out[j] = sum over the nodes s of triangle j of
+ * uvw[3s+2] jac[s] N . (x0 - x[s]) / (4 pi |x0 - x[s]|^3), N = -grad Phi/|grad Phi|.
+ * Nodes must be grouped by triangle in increasing triangle order (as
+ * lsm_refined_nodes lists them); a triangle with no node gets 0.
+ *   n, tri [n], uvw [n][3], x [n][3], grad [n][3], jac [n]: host or device;
+ *   x0[3] host; out [m] host or device (m = the mesh's triangles).
+ * Synchronises `stream`.  Errors: LSM_E_INVALID_ARG, LSM_E_CUDA. */
+int lsm_flux_per_triangle(lsm_mesh* mesh, int64_t n, const int32_t* tri, const double* uvw, const double* x,
+                          const double* grad, const double* jac, const double* x0, double* out, void* stream);
+/* A posteriori refinement of the charts (Sec. 3.4: refinement where standard
+ * a posteriori estimates from adaptive integration ask for it).  For each
+ * triangle at level L (1 -> 4 midpoint splits, the children keeping the
+ * parent's chart map, lsm_refined_nodes) the Gauss flux integral about the
+ * interior point x0 over its charts is compared with the same integral one
+ * level finer; where they differ by more than flux_tol the triangle is
+ * refined and tested again one level further, up to max_level (0..4).  Each
+ * test solves the charts (mixed precision finished in float-float, to
+ * newton_tol) at the nodes concerned.
+ *   order      chart order (rule n = order/2 + 2)
+ *   level_out  [m] host: the level of each triangle
+ *   rounds_out host, may be NULL: refinement rounds run
+ * Synchronises `stream`.  Errors: LSM_E_INVALID_ARG, LSM_E_OOM, LSM_E_CUDA,
+ * LSM_E_NOT_CONVERGED (chart nodes that did not converge; level_out is still
+ * filled), LSM_E_TIMEOUT. */
+int lsm_refine_adaptive(lsm_mesh* mesh, int order, double newton_tol, double flux_tol, int max_level,
+                        const double* x0, int32_t* level_out, int* rounds_out, void* stream);
+
 /* Autotuner of the mixed path's far field (the paper has no counterpart:
  * its FMM is run at a fixed precision, Sec. 4.4).  Chooses, for this mesh,
  * between the direct tiled far field and the treecode, and the treecode's

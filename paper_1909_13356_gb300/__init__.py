@@ -45,7 +45,7 @@ EXPORTS = ("lsm_create", "lsm_destroy", "lsm_last_error", "lsm_launch_count", "l
            "lsm_chart_curvature", "lsm_refined_nodes", "lsm_solve_charts_nodes", "lsm_chart_frames_nodes",
            "lsm_gauss_flux_nodes", "lsm_check_error", "lsm_test_inject_wait_timeout", "lsm_measure_peaks",
            "lsm_server_cancel", "lsm_batch_autotune",
-           "lsm_mesh_upload_quadratic")
+           "lsm_mesh_upload_quadratic", "lsm_flux_per_triangle", "lsm_refine_adaptive")
 
 
 class LsmError(RuntimeError):
@@ -190,6 +190,8 @@ def load(build_if_needed: bool = True):
         L.lsm_chart_frames_nodes.argtypes = [P, I64, P, P, P, P, P, P, P, P]
         L.lsm_gauss_flux_nodes.argtypes = [P, I64, P, P, P, P, P, P, P, P]
         L.lsm_gauss_flux.argtypes = [P, I32, P, P, P, P, P, P]
+        L.lsm_flux_per_triangle.argtypes = [P, I64, P, P, P, P, P, P, P, P]
+        L.lsm_refine_adaptive.argtypes = [P, I32, D, D, I32, P, P, ctypes.POINTER(ctypes.c_int), P]
         L.lsm_check_error.argtypes = [P, P]
         L.lsm_test_inject_wait_timeout.argtypes = [P, I32]
         L.lsm_measure_peaks.argtypes = [P, ctypes.POINTER(_Peaks), P]
@@ -495,6 +497,29 @@ class Mesh:
                                               _ptr(p0), ctypes.byref(out), _stream_handle(stream))
         self.ctx._check(rc)
         return out.value
+
+    def flux_per_triangle(self, tri, uvw, x, grad, jac, x0, stream=None):
+        """Gauss flux split by skeleton triangle (lsm_flux_per_triangle), host [m]."""
+        t, u = _as(tri, np.int32), _as(uvw, np.float64)
+        xs, gs, js = _as(x, np.float64), _as(grad, np.float64), _as(jac, np.float64)
+        p0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(3)
+        out = np.empty(self.n_triangles)
+        rc = self.ctx._L.lsm_flux_per_triangle(self._h, int(t.shape[0]), _ptr(t), _ptr(u), _ptr(xs), _ptr(gs),
+                                               _ptr(js), _ptr(p0), _ptr(out), _stream_handle(stream))
+        self.ctx._check(rc)
+        return out
+
+    def refine_adaptive(self, order: int, flux_tol: float, max_level: int, x0, newton_tol: float = 1e-12,
+                        stream=None):
+        """Per-triangle refinement levels from the a posteriori flux estimate
+        (lsm_refine_adaptive): (levels [m], rounds)."""
+        p0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(3)
+        lv = np.zeros(self.n_triangles, dtype=np.int32)
+        rounds = ctypes.c_int()
+        rc = self.ctx._L.lsm_refine_adaptive(self._h, int(order), float(newton_tol), float(flux_tol), int(max_level),
+                                             _ptr(p0), _ptr(lv), ctypes.byref(rounds), _stream_handle(stream))
+        self.ctx._check(rc)
+        return lv, int(rounds.value)
 
     def eval_hessian(self, x, stream=None):
         """Hessian of Phi [n, 6] = (xx, xy, xz, yy, yz, zz) at targets x [n, 3]

@@ -212,6 +212,8 @@ __global__ void k_scatter6(const double* __restrict__ R, const uint32_t* __restr
     for (int c = 0; c < 6; c++) out[6 * o + c] = R[(int64_t)c * n + i];
 }
 
+}  // namespace
+
 int check_flag(Ctx* ctx, cudaStream_t st)
 {
     int h = 0;
@@ -227,6 +229,8 @@ int check_flag(Ctx* ctx, cudaStream_t st)
     }
     return LSM_OK;
 }
+
+namespace {
 
 // Edge nodes of quadratic patches: in range, never a patch corner, every
 // vertex a corner or an edge node, and the two patches on an edge sharing

@@ -163,6 +163,34 @@ __global__ void k_chart_second(const double* __restrict__ verts, const int32_t* 
     kmean[s] = -(E * Nn - 2.0 * F * M + G * L) / det;
 }
 
+// One node's term of the Gauss flux about x0: w jac N . (x0 - x) / (4 pi |x0 - x|^3),
+// N = -grad Phi / |grad Phi|.
+__device__ __forceinline__ double flux_term(const double* __restrict__ x, const double* __restrict__ g,
+                                            const double* __restrict__ jac, int64_t s, double wq, double x0, double y0,
+                                            double z0)
+{
+    const double dx = x0 - x[3 * s], dy = y0 - x[3 * s + 1], dz = z0 - x[3 * s + 2];
+    const double gx = g[3 * s], gy = g[3 * s + 1], gz = g[3 * s + 2];
+    const double gn = sqrt(gx * gx + gy * gy + gz * gz);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double r = sqrt(r2);
+    const double nd = -(gx * dx + gy * dy + gz * dz) / gn;
+    return wq * jac[s] * nd / (kFourPi * r2 * r);
+}
+
+// Per-triangle sums of the flux terms: triangle j's nodes are [off[j], off[j+1])
+// (nodes grouped by triangle), summed in node order by one thread.
+__global__ void k_flux_tri(const double* __restrict__ x, const double* __restrict__ g, const double* __restrict__ jac,
+                           const double* __restrict__ uvw, const int64_t* __restrict__ off, int64_t m, double x0,
+                           double y0, double z0, double* __restrict__ out)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double a = 0.0;
+    for (int64_t s = off[j]; s < off[j + 1]; s++) a += flux_term(x, g, jac, s, uvw[3 * s + 2], x0, y0, z0);
+    out[j] = a;
+}
+
 // Per-block partial sums of the flux terms (block sums in a fixed tree order).
 __global__ void __launch_bounds__(kFrameThreads) k_flux_partial(const double* __restrict__ x,
                                                                 const double* __restrict__ g,
@@ -174,16 +202,7 @@ __global__ void __launch_bounds__(kFrameThreads) k_flux_partial(const double* __
     __shared__ double sw[kFrameThreads / 32];
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double t = 0.0;
-    if (s < n) {
-        const double dx = x0 - x[3 * s], dy = y0 - x[3 * s + 1], dz = z0 - x[3 * s + 2];
-        const double gx = g[3 * s], gy = g[3 * s + 1], gz = g[3 * s + 2];
-        const double gn = sqrt(gx * gx + gy * gy + gz * gz);
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        const double r = sqrt(r2);
-        const double nd = -(gx * dx + gy * dy + gz * dz) / gn;
-        const double wq = uvw ? uvw[3 * s + 2] : rule[3 * (s % np) + 2];
-        t = wq * jac[s] * nd / (kFourPi * r2 * r);
-    }
+    if (s < n) t = flux_term(x, g, jac, s, uvw ? uvw[3 * s + 2] : rule[3 * (s % np) + 2], x0, y0, z0);
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = t;
     __syncthreads();
@@ -281,6 +300,15 @@ int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const do
     LSM_LAUNCHED(ctx);
     LSM_CUDA_TRY(ctx, cudaMemcpyAsync(eps0, out, sizeof(double), cudaMemcpyDeviceToHost, st));
     LSM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+int flux_per_triangle_dev(Ctx* ctx, int64_t m, const int64_t* off, const double* x, const double* g, const double* jac,
+                          const double* uvw, const double* x0, double* out, cudaStream_t st)
+{
+    if (m <= 0) return LSM_OK;
+    k_flux_tri<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(x, g, jac, uvw, off, m, x0[0], x0[1], x0[2], out);
+    LSM_LAUNCHED(ctx);
     return LSM_OK;
 }
 

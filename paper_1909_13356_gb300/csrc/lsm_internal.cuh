@@ -450,6 +450,10 @@ int chart_frames_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* h, const 
                      double* jac, cudaStream_t st, const NodeSpec* spec = nullptr);
 int gauss_flux_dev(Ctx* ctx, const Mesh* me, int n_gl, const double* x, const double* g, const double* jac,
                    const double* x0, double* eps0, cudaStream_t st, const NodeSpec* spec = nullptr);
+// per-triangle sums of the Gauss flux terms (device arrays; nodes grouped by
+// triangle, triangle j's nodes [off[j], off[j+1]), weights uvw[3s+2]); x0 host
+int flux_per_triangle_dev(Ctx* ctx, int64_t m, const int64_t* off, const double* x, const double* g, const double* jac,
+                          const double* uvw, const double* x0, double* out, cudaStream_t st);
 
 // eval.cu: H(w) = g(u)/u^3 in long double, and the degree-6 interpolant of H
 // on interval k of width 1/per_unit in w (monomial coefficients about its
@@ -495,6 +499,9 @@ int build_items(Ctx* ctx, const int32_t* list, const int* n_list, int n_max, con
 
 // host helpers (api.cu)
 void simplex_rule_host(int n, int subdiv, double* uvw);  // [cnt][3]
+// synchronise st, read and clear the calling thread's device error word:
+// LSM_E_TIMEOUT when a bounded wait ran out
+int check_flag(Ctx* ctx, cudaStream_t st);
 
 }  // namespace lsm
 

@@ -84,3 +84,49 @@ def test_refined_nodes_reject_bad_triangles(lsm, refined):
     bad[3] = m.m
     with pytest.raises(lsm.LsmError):
         mesh.solve_charts_nodes(bad, uvw)
+
+
+def test_flux_per_triangle_matches_oracle(lsm, oracle_mod, refined):
+    """The Gauss flux split by skeleton triangle (on refined, non-conforming
+    node sets) against the oracle's flux over each triangle's nodes, and the
+    total against lsm_gauss_flux_nodes."""
+    m, levels, tri, uvw, ctx, mesh, (y, nw, sg) = refined
+    x, h, st, stats = mesh.solve_charts_nodes(tri, uvw, tol=1e-13, precision=lsm.FP64)
+    _, g = mesh.eval_phi_grad(x, lsm.FP64)
+    _, _, jac = mesh.chart_frames_nodes(tri, uvw, h, g)
+    x0 = (0.05, -0.1, 0.02)
+    per = mesh.flux_per_triangle(tri, uvw, x, g, jac, x0)
+    for j in range(m.m):
+        sel = tri == j
+        ref = oracle_mod.gauss_flux_w(x[sel], g[sel], jac[sel], uvw[sel, 2], x0) - 1.0
+        assert abs(per[j] - ref) < 1e-14
+    tot = mesh.gauss_flux_nodes(tri, uvw, x, g, jac, x0)
+    assert abs((1.0 + per.sum()) - tot) < 1e-13
+
+
+def test_adaptive_refinement_driver(lsm):
+    """lsm_refine_adaptive on a sphere with sharp Gaussian bumps: the flux
+    estimate refines the triangles near the bumps; the charts at the chosen
+    levels close the Gauss flux far better than the unrefined charts, with
+    fewer nodes than refining everything to the same maximum level."""
+    m = synth.bumped_icosphere(2, 12, 7)
+    ctx = lsm.Context(0)
+    mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
+    x0 = (0.03, -0.02, 0.05)
+    levels, rounds = mesh.refine_adaptive(order=4, flux_tol=1e-6, max_level=2, x0=x0)
+    assert rounds >= 1 and levels.min() >= 0 and levels.max() <= 2
+    assert 0 < (levels > 0).sum() < m.m            # some triangles refined, not all
+
+    def eps(lv):
+        tri, uvw = lsm.refined_nodes(4, lv)
+        x, h, st, stats = mesh.solve_charts_nodes(tri, uvw, tol=1e-12, precision=lsm.MIXED)
+        assert stats.n_failed == 0
+        _, g = mesh.eval_phi_grad(x, lsm.FF)
+        _, _, jac = mesh.chart_frames_nodes(tri, uvw, h, g)
+        return abs(mesh.gauss_flux_nodes(tri, uvw, x, g, jac, x0)), len(tri)
+
+    e0, n0 = eps(np.zeros(m.m, dtype=np.int32))
+    ea, na = eps(levels.astype(np.int32))
+    e2, n2 = eps(np.full(m.m, 2, dtype=np.int32))
+    assert ea < 0.1 * e0, (e0, ea, e2)
+    assert na < n2
