@@ -142,6 +142,11 @@ typedef struct {
      * side, with the same error bound) acts on the grid's points, and the
      * targets interpolate its field from them.  0 selects 4096; -1: off. */
     int32_t tree_ff_cluster;
+    /* The same for the mixed path's treecode (degree tree_degree grids on
+     * clusters of this many targets, a multiple of 256).  0 selects 4096;
+     * -1: off. */
+    int32_t tree_cluster;
+    int32_t reserved;
 } lsm_options;
 
 /* Statistics of one chart solve. */

@@ -64,7 +64,8 @@ class _Options(ctypes.Structure):
                 ("tree_degree", ctypes.c_int32), ("tree_theta", ctypes.c_float),
                 ("tree_min_sources", ctypes.c_int32), ("tree_ff_degree", ctypes.c_int32),
                 ("tree_ff_theta", ctypes.c_float), ("tree_ff_min_sources", ctypes.c_int32),
-                ("tree_grid", ctypes.c_int32), ("tree_ff_cluster", ctypes.c_int32)]
+                ("tree_grid", ctypes.c_int32), ("tree_ff_cluster", ctypes.c_int32), ("tree_cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -265,18 +266,19 @@ class Context:
                  mixed_switch: float = 0.0, mixed_accept: float = 0.0, tree_degree: int = 0,
                  tree_theta: float = 0.0, tree_min_sources: int = 0, tree_ff_degree: int = 0,
                  tree_ff_theta: float = 0.0, tree_ff_min_sources: int = 0, tree_grid: int = 0,
-                 tree_ff_cluster: int = 0):
+                 tree_ff_cluster: int = 0, tree_cluster: int = 0):
         """Zero selects a default.  tree_*: the treecode far field of the mixed
         path (Chebyshev degree, opening parameter, and the source count from
         which a mesh uses it; tree_min_sources=-1 turns it off); tree_ff_*: the
         same for the float-float path.  tree_grid: 1 oriented per-axis proxy
         grids with a degree ladder (the default), 2 full (degree + 1)^3
         axis-aligned grids of one degree.  tree_ff_cluster: targets per target
-        cluster of the float-float treecode (0: 4096, -1: off)."""
+        cluster of the float-float treecode (0: 4096, -1: off); tree_cluster:
+        the same for the mixed treecode."""
         self._L = load()
         opt = _Options(cutoff_fp64, cutoff_mixed, mixed_switch, mixed_accept, int(tree_degree),
                        float(tree_theta), int(tree_min_sources), int(tree_ff_degree), float(tree_ff_theta),
-                       int(tree_ff_min_sources), int(tree_grid), int(tree_ff_cluster))
+                       int(tree_ff_min_sources), int(tree_grid), int(tree_ff_cluster), int(tree_cluster), 0)
         h = ctypes.c_void_p()
         rc = self._L.lsm_create(ctypes.byref(h), int(device), ctypes.byref(opt))
         if rc != 0:

@@ -387,12 +387,15 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.tree_ff_min_sources = 262144;
     ctx->opt.tree_grid = 1;
     ctx->opt.tree_ff_cluster = 4096;
+    ctx->opt.tree_cluster = 4096;
     if (opt) {
         if (opt->tree_degree < 0 || opt->tree_degree > 12 || opt->tree_theta < 0.0f ||
             opt->tree_theta >= 1.0f || opt->tree_min_sources < -1 || opt->tree_ff_degree < 0 ||
             opt->tree_ff_degree > kTreeMaxDegree || opt->tree_ff_theta < 0.0f || opt->tree_ff_theta >= 1.0f ||
             opt->tree_ff_min_sources < -1 || opt->tree_grid < 0 || opt->tree_grid > 2 || opt->tree_ff_cluster < -1 ||
-            opt->tree_ff_cluster > (1 << 20) || (opt->tree_ff_cluster > 0 && opt->tree_ff_cluster % kEvalThreads)) {
+            opt->tree_ff_cluster > (1 << 20) || (opt->tree_ff_cluster > 0 && opt->tree_ff_cluster % kEvalThreads) ||
+            opt->tree_cluster < -1 || opt->tree_cluster > (1 << 20) ||
+            (opt->tree_cluster > 0 && opt->tree_cluster % (2 * kEvalThreads))) {
             delete c;
             return LSM_E_INVALID_ARG;
         }
@@ -408,6 +411,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
         if (opt->tree_ff_min_sources != 0) ctx->opt.tree_ff_min_sources = opt->tree_ff_min_sources;
         if (opt->tree_grid > 0) ctx->opt.tree_grid = opt->tree_grid;
         if (opt->tree_ff_cluster != 0) ctx->opt.tree_ff_cluster = opt->tree_ff_cluster > 0 ? opt->tree_ff_cluster : 0;
+        if (opt->tree_cluster != 0) ctx->opt.tree_cluster = opt->tree_cluster > 0 ? opt->tree_cluster : 0;
     }
     DeviceGuard g(device);
     int rc = LSM_OK;

@@ -1543,15 +1543,16 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     // float-float: every mode but the near-only one (which lists near tiles itself)
     const bool use_tree = mixed ? tree_wanted(ctx, me, false)
                                 : (ff && !(inc && inc->mode == 2) && tree_wanted(ctx, me, true));
-    // float-float treecode: target clusters take the nodes far from them
+    // treecodes: target clusters take the nodes far from them (tpc a multiple of the block)
     ClusterPlan cp;
-    const int tpc = ctx->opt.tree_ff_cluster;
-    const bool clusters = use_tree && ff && !me->sigx && tpc > 0 && t.n >= 2 * tpc;
+    const int tpc = (ff ? ctx->opt.tree_ff_cluster : ctx->opt.tree_cluster) / tpb * tpb;
+    const bool clusters = use_tree && (ff || mixed) && !me->sigx && tpc > 0 && t.n >= 2 * tpc;
     if (use_tree) {
         int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff);
         if (rc != LSM_OK) return rc;
         if (clusters) {
-            rc = cluster_setup(ctx, me->tree_ff, t, tpc, s, &cp, st);
+            rc = cluster_setup(ctx, ff ? me->tree_ff : me->tree, t, tpc, tpb, ff ? ctx->opt.cutoff_fp64 : mixed_cut(ctx, me),
+                               s, &cp, st);
             if (rc != LSM_OK) return rc;
         }
         int64_t total = 0;
@@ -1653,7 +1654,14 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         G.far_io = nullptr;
         G.x_old = nullptr;
         G.bb_io = nullptr;
-        k_eval_ff<false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, G);
+        if (ff)
+            k_eval_ff<false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, G);
+        else if (tpt == 1)
+            k_eval_mixed<1, false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
+                                                                     me->s32_nwlo, G);
+        else
+            k_eval_mixed<kTPT32, false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
+                                                                          me->s32_nwlo, G);
         LSM_LAUNCHED(ctx);
     }
     if (ctx->profiling) {

@@ -421,7 +421,7 @@ struct ClusterPlan {
     float4 *box_lo = nullptr, *box_hi = nullptr;   // outward box of each cluster's oriented box
     float4* cacc = nullptr;      // frame centre, (r + q h_max)^2: the target-side opening radius
     double* frame = nullptr;     // [ncl][16]: centre (3), axes (9, rows), half-widths (3), unused
-    int4* counts = nullptr;      // grid points per axis; w = first grid point (padded to kEvalThreads)
+    int4* counts = nullptr;      // grid points per axis; w = first grid point (padded to a block)
     int64_t ng = 0;              // grid points, padded
     double* gx = nullptr;        // grid points, SoA [3][ng]
     int* list = nullptr;         // proxy tiles acting on each cluster's grid
@@ -429,12 +429,14 @@ struct ClusterPlan {
     int* gorder = nullptr;       // grid blocks in launch order
     int ngblk = 0;
     int64_t total = 0;           // summed length of the clusters' lists
-    float4 *blo = nullptr, *bhi = nullptr;   // the target blocks' boxes (kEvalThreads targets each)
+    float4 *blo = nullptr, *bhi = nullptr;   // the target blocks' boxes
     uint32_t* cbits = nullptr;   // [ncl][cwords]: bit `node` set when the cluster took the node
     int64_t cwords = 0;
 };
-int cluster_setup(Ctx* ctx, const Tree* tree, const Targets& t, int tpc, Scratch& s, ClusterPlan* plan,
-                  cudaStream_t st);
+// tpb: targets per block of the pair kernel that evaluates the lists (and
+// the grid points); cut: its near radius in sigma
+int cluster_setup(Ctx* ctx, const Tree* tree, const Targets& t, int tpc, int tpb, double cut, Scratch& s,
+                  ClusterPlan* plan, cudaStream_t st);
 // Adds the clusters' interpolated far field to res [4][n] (and to far_io [4][n]
 // when not null) from the grid values rg [4][ng].
 int cluster_l2p(Ctx* ctx, const ClusterPlan& plan, const Targets& t, const double* rg, double* res,

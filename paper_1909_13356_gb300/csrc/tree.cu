@@ -903,15 +903,16 @@ __global__ void __launch_bounds__(kFrameThreads) k_cluster_frames(const double* 
 
 // Grid points of every cluster (one CTA per cluster), SoA with stride ng:
 // point g = (k0 n1 + k1) n2 + k2 at centre + sum_a h_a cos(k_a pi / (n_a - 1)) e_a;
-// the slots up to the next multiple of kEvalThreads repeat the first point.
+// the slots up to the next multiple of the pair kernel's block (tpb) repeat
+// the first point.
 __global__ void k_cluster_points(const double* __restrict__ frame, const int4* __restrict__ counts, int64_t ng,
-                                 double* __restrict__ gx)
+                                 int tpb, double* __restrict__ gx)
 {
     const int c = blockIdx.x;
     const double* F = frame + 16 * (int64_t)c;
     const int4 nc = counts[c];
     const int np = nc.x * nc.y * nc.z;
-    const int npad = (np + kEvalThreads - 1) / kEvalThreads * kEvalThreads;
+    const int npad = (np + tpb - 1) / tpb * tpb;
     for (int g = threadIdx.x; g < npad; g += blockDim.x) {
         const int q = g < np ? g : 0;
         const int k[3] = {q / (nc.y * nc.z), (q / nc.z) % nc.y, q % nc.z};
@@ -1365,7 +1366,8 @@ static void fill_walk_tree(WalkArgs& W, const Tree* T, double cut)
     W.cut2 = (float)(cut * cut);
 }
 
-int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, Scratch& s, ClusterPlan* P, cudaStream_t st)
+int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, int tpb, double cut, Scratch& s,
+                  ClusterPlan* P, cudaStream_t st)
 {
     ClusterPlan& cp = *P;
     cp.tpc = tpc;
@@ -1388,10 +1390,10 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, Scratch& s
     int64_t ng = 0;
     for (int c = 0; c < ncl; c++) {
         const int64_t np = (int64_t)hc[c].x * hc[c].y * hc[c].z;
-        const int64_t nb = (np + kEvalThreads - 1) / kEvalThreads;
+        const int64_t nb = (np + tpb - 1) / tpb;
         hc[c].w = (int)ng;
         for (int64_t b = 0; b < nb; b++) gb_cluster.push_back(c);
-        ng += nb * kEvalThreads;
+        ng += nb * tpb;
     }
     if (ng >= ((int64_t)1 << 31)) {
         ctx->err = "tree: too many cluster grid points";
@@ -1405,10 +1407,9 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, Scratch& s
     LSM_CUDA_TRY(ctx, cudaMemcpyAsync(cp.counts, hc.data(), sizeof(int4) * ncl, cudaMemcpyHostToDevice, st));
     LSM_CUDA_TRY(ctx, cudaMemcpyAsync(d_gbc, gb_cluster.data(), sizeof(int) * gb_cluster.size(),
                                       cudaMemcpyHostToDevice, st));
-    k_cluster_points<<<ncl, 128, 0, st>>>(cp.frame, cp.counts, ng, cp.gx);
+    k_cluster_points<<<ncl, 128, 0, st>>>(cp.frame, cp.counts, ng, tpb, cp.gx);
     LSM_LAUNCHED(ctx);
     // the target blocks' boxes (as the block walk sees them) and the bitmap
-    const int tpb = kEvalThreads;
     const int nblk = (t.n + tpb - 1) / tpb;
     LSM_CUDA_TRY(ctx, s.get(&cp.blo, nblk));
     LSM_CUDA_TRY(ctx, s.get(&cp.bhi, nblk));
@@ -1419,7 +1420,7 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, Scratch& s
     LSM_CUDA_TRY(ctx, cudaMemsetAsync(cp.cbits, 0, sizeof(uint32_t) * (size_t)cp.cwords * ncl, st));
     // the clusters' lists: count, scan, write
     ClusterWalkArgs A;
-    fill_walk_tree(A.W, T, T->ff ? ctx->opt.cutoff_fp64 : ctx->opt.cutoff_mixed);
+    fill_walk_tree(A.W, T, cut);
     A.W.c_lo = cp.box_lo;
     A.W.c_hi = cp.box_hi;
     A.W.c_acc = cp.cacc;
