@@ -143,8 +143,9 @@ typedef struct {
      * targets interpolate its field from them.  0 selects 4096; -1: off. */
     int32_t tree_ff_cluster;
     /* The same for the mixed path's treecode (degree tree_degree grids on
-     * clusters of this many targets, a multiple of 256).  0 selects 4096;
-     * -1: off. */
+     * clusters of this many targets, a multiple of 256).  0 or -1: off (the
+     * default: on the graded torus at 10^6 targets it cut the mixed kernel's
+     * far pairs by 20 % but the whole evaluation by only 2 %). */
     int32_t tree_cluster;
     int32_t reserved;
 } lsm_options;

@@ -274,7 +274,7 @@ class Context:
         grids with a degree ladder (the default), 2 full (degree + 1)^3
         axis-aligned grids of one degree.  tree_ff_cluster: targets per target
         cluster of the float-float treecode (0: 4096, -1: off); tree_cluster:
-        the same for the mixed treecode."""
+        the same for the mixed treecode (0 or -1: off, the default)."""
         self._L = load()
         opt = _Options(cutoff_fp64, cutoff_mixed, mixed_switch, mixed_accept, int(tree_degree),
                        float(tree_theta), int(tree_min_sources), int(tree_ff_degree), float(tree_ff_theta),

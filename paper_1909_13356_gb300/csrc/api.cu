@@ -387,7 +387,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.tree_ff_min_sources = 262144;
     ctx->opt.tree_grid = 1;
     ctx->opt.tree_ff_cluster = 4096;
-    ctx->opt.tree_cluster = 4096;
+    ctx->opt.tree_cluster = 0;   // off: at 10^6 targets it saves 2% of a mixed evaluation
     if (opt) {
         if (opt->tree_degree < 0 || opt->tree_degree > 12 || opt->tree_theta < 0.0f ||
             opt->tree_theta >= 1.0f || opt->tree_min_sources < -1 || opt->tree_ff_degree < 0 ||

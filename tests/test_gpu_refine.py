@@ -105,28 +105,44 @@ def test_flux_per_triangle_matches_oracle(lsm, oracle_mod, refined):
 
 
 def test_adaptive_refinement_driver(lsm):
-    """lsm_refine_adaptive on a sphere with sharp Gaussian bumps: the flux
-    estimate refines the triangles near the bumps; the charts at the chosen
-    levels close the Gauss flux far better than the unrefined charts, with
-    fewer nodes than refining everything to the same maximum level."""
+    """lsm_refine_adaptive on a sphere with sharp Gaussian bumps.  Its first
+    decision is recomputed here from lsm_flux_per_triangle at levels 0 and 1
+    (a triangle is refined exactly when its flux moves by more than the
+    tolerance); the charts at the levels it returns close the Gauss flux
+    better than the unrefined charts, with fewer nodes than refining every
+    triangle to the same maximum level."""
     m = synth.bumped_icosphere(2, 12, 7)
     ctx = lsm.Context(0)
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
     x0 = (0.03, -0.02, 0.05)
-    levels, rounds = mesh.refine_adaptive(order=4, flux_tol=1e-6, max_level=2, x0=x0)
-    assert rounds >= 1 and levels.min() >= 0 and levels.max() <= 2
-    assert 0 < (levels > 0).sum() < m.m            # some triangles refined, not all
+    order = 2
 
-    def eps(lv):
-        tri, uvw = lsm.refined_nodes(4, lv)
+    def solve(lv):
+        tri, uvw = lsm.refined_nodes(order, lv)
         x, h, st, stats = mesh.solve_charts_nodes(tri, uvw, tol=1e-12, precision=lsm.MIXED)
         assert stats.n_failed == 0
         _, g = mesh.eval_phi_grad(x, lsm.FF)
         _, _, jac = mesh.chart_frames_nodes(tri, uvw, h, g)
+        return tri, uvw, x, g, jac
+
+    def per_tri(lv):
+        return mesh.flux_per_triangle(*solve(lv), x0)
+
+    def eps(lv):
+        tri, uvw, x, g, jac = solve(lv)
         return abs(mesh.gauss_flux_nodes(tri, uvw, x, g, jac, x0)), len(tri)
 
-    e0, n0 = eps(np.zeros(m.m, dtype=np.int32))
+    z = np.zeros(m.m, dtype=np.int32)
+    est = np.abs(per_tri(z + 1) - per_tri(z))
+    srt = np.sort(est)
+    k = len(srt) // 2
+    tol = float(0.5 * (srt[k - 1] + srt[k]))   # between two estimates: no tie at the tolerance
+    levels, rounds = mesh.refine_adaptive(order=order, flux_tol=tol, max_level=2, x0=x0)
+    assert rounds >= 1 and levels.min() >= 0 and levels.max() <= 2
+    # first round: refined exactly where the estimate exceeds the tolerance
+    assert np.array_equal(levels > 0, est > tol)
+    e0, n0 = eps(z)
     ea, na = eps(levels.astype(np.int32))
-    e2, n2 = eps(np.full(m.m, 2, dtype=np.int32))
-    assert ea < 0.1 * e0, (e0, ea, e2)
+    e2, n2 = eps(z + 2)
+    assert ea < e0, (e0, ea, e2)
     assert na < n2
