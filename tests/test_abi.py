@@ -68,9 +68,17 @@ def test_binding_declares_argument_types_for_every_export():
 
 
 def test_options_struct_matches_header_layout():
-    """The binding's lsm_options has the header's size (reserved words keep
-    the size fixed as fields are added)."""
-    assert ctypes.sizeof(lsm._Options) == 4 * 8 + 8 * 4
+    """The binding's lsm_options has the header's fields, in the header's
+    order and with the header's types (read from include/lsm.h)."""
+    with open(HEADER) as f:
+        text = f.read()
+    end = text.index("} lsm_options;")
+    body = text[text.rindex("typedef struct {", 0, end):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(double|float|int32_t)\s+(\w+)\s*;", body)
+    ctypes_of = {"double": ctypes.c_double, "float": ctypes.c_float, "int32_t": ctypes.c_int32}
+    assert [(n, ctypes_of[t]) for t, n in fields] == list(lsm._Options._fields_)
+    assert ctypes.sizeof(lsm._Options) == sum(ctypes.sizeof(ctypes_of[t]) for t, _ in fields)
 
 
 def test_refined_nodes_match_the_oracle_rule(oracle_mod):
