@@ -62,6 +62,8 @@ def parse():
                     help="serve: cut the stream at this wall time (cancel what is still queued)")
     ap.add_argument("--tree-degree", type=int, default=0, help="treecode degree (0: library default)")
     ap.add_argument("--tree-theta", type=float, default=0.0, help="treecode opening parameter (0: default)")
+    ap.add_argument("--ff-block", type=int, default=0,
+                    help="targets per CTA of the float-float kernel (64 or 128; 0: library default)")
     ap.add_argument("--tree-grid", type=int, default=0,
                     help="proxy grids: 1 per-axis point counts (default), 2 full (degree + 1)^3")
     ap.add_argument("--sigma-x", action="store_true",
@@ -262,7 +264,7 @@ def bench_ellipsoids(args):
     import paper_1909_13356_gb300 as lsm
     import synth
     w = synth.ellipsoid_batch_c4()
-    ctx = lsm.Context(0, tree_grid=args.tree_grid)
+    ctx = lsm.Context(0, tree_grid=args.tree_grid, ff_block=args.ff_block)
     meshes = [ctx.upload(m.verts, m.tris, m.sigma, n_gl=4) for m in w["meshes"]]
     batch = lsm.Batch(ctx, meshes)
     tol = 1e-10
@@ -336,7 +338,7 @@ def bench_serve(args):
             templates[key] = make_request_mesh(dict(kind=r["kind"], T=int(sizes[k]), seed=1000 * r["kind"] + k))
         return templates[key]
 
-    ctx = lsm.Context(0, tree_grid=args.tree_grid)
+    ctx = lsm.Context(0, tree_grid=args.tree_grid, ff_block=args.ff_block)
     # warm the kernels once
     m0 = mesh_of(reqs[0])
     wm = ctx.upload(m0.verts, m0.tris, m0.sigma, n_gl=4)
@@ -409,7 +411,8 @@ def bench_icosphere(args):
     n = args.targets if args.targets else 20_000_000
     w = synth.icosphere_c3(n_targets=n)
     m = w["mesh"]
-    ctx = lsm.Context(0, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid)
+    ctx = lsm.Context(0, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid,
+                      ff_block=args.ff_block)
     t0 = time.perf_counter()
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
     torch.cuda.synchronize()
@@ -500,7 +503,7 @@ def bench_geometry(args):
     import paper_1909_13356_gb300 as lsm
     w = workload(args, 0)
     m = w["mesh"]
-    ctx = lsm.Context(0, tree_grid=args.tree_grid)
+    ctx = lsm.Context(0, tree_grid=args.tree_grid, ff_block=args.ff_block)
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=w["rule"]["n"], subdiv=w["rule"]["subdiv"])
     x, h, _, st = mesh.solve_charts(order=args.order, tol=args.tol, precision=lsm.MIXED, device_out=True)
     _, g = mesh.eval_phi_grad(x, lsm.FF)
@@ -667,7 +670,8 @@ def main():
 
     w = workload(args, rank if args.replicas else 0)
     m = w["mesh"]
-    ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid)
+    ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid,
+                      ff_block=args.ff_block)
     # the pipes' measured throughput (roofline denominators), clocks sampled around the probe
     pclk = ClockSampler(local)
     pclk.start()
@@ -915,9 +919,12 @@ def main():
                        "targets": len(w["targets"]), "chart_order": args.order,
                        "chart_nodes": len(tri_all) if not args.no_charts else 0,
                        "newton_tol": args.tol, "precision": args.precision, "autotune": tune,
-                       # the library's default near-field cutoffs (lsm_options), unchanged here: the
-                       # mixed one meets erfc(c/sqrt2) + c sqrt(2/pi) e^(-c^2/2) <= 1e-8 (3.6e-9 at 6.5)
-                       "cutoff_sigma": {"fp64_and_float_float": 8.0, "mixed": 6.5},
+                       # near-field cutoffs: the library's FP64 one; the mixed one as the autotuner
+                       # chose it (candidates meeting erfc(c/sqrt2) + c sqrt(2/pi) e^(-c^2/2) <= 1e-8),
+                       # else the default 6.5
+                       "cutoff_sigma": {"fp64_and_float_float": 8.0,
+                                        "mixed": (tune or {}).get("cutoff", 6.5) or 6.5},
+                       "ff_targets_per_cta": args.ff_block or 64,
                        "sigma": ("sigma(x), eq. sigma2: lambda 2.5, sigma0 = max D / sqrt(2 ln 2) = "
                                  f"{mesh.sigma0:.5g}" if args.sigma_x else "per triangle, 0.5 sqrt(2 area)"),
                        "parallelism": (f"{world} ranks, targets and chart nodes in Morton ranges, mesh replicated"

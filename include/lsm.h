@@ -147,7 +147,12 @@ typedef struct {
      * default: on the graded torus at 10^6 targets it cut the mixed kernel's
      * far pairs by 20 % but the whole evaluation by only 2 %). */
     int32_t tree_cluster;
-    int32_t reserved;
+    /* Targets per CTA of the float-float kernel (64 or 128; 0 selects 64):
+     * the near/far split and the treecode's lists are per CTA, so a smaller
+     * target box means fewer pairs per target, at the price of more CTAs
+     * streaming each source tile.  The target-dependent sigma(x) mode and
+     * batches always use 128. */
+    int32_t ff_block;
 } lsm_options;
 
 /* Statistics of one chart solve. */

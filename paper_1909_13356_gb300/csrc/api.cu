@@ -388,6 +388,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.tree_grid = 1;
     ctx->opt.tree_ff_cluster = 4096;
     ctx->opt.tree_cluster = 0;   // off: at 10^6 targets it saves 2% of a mixed evaluation
+    ctx->opt.ff_block = 64;
     if (opt) {
         if (opt->tree_degree < 0 || opt->tree_degree > 12 || opt->tree_theta < 0.0f ||
             opt->tree_theta >= 1.0f || opt->tree_min_sources < -1 || opt->tree_ff_degree < 0 ||
@@ -395,7 +396,8 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
             opt->tree_ff_min_sources < -1 || opt->tree_grid < 0 || opt->tree_grid > 2 || opt->tree_ff_cluster < -1 ||
             opt->tree_ff_cluster > (1 << 20) || (opt->tree_ff_cluster > 0 && opt->tree_ff_cluster % kEvalThreads) ||
             opt->tree_cluster < -1 || opt->tree_cluster > (1 << 20) ||
-            (opt->tree_cluster > 0 && opt->tree_cluster % (2 * kEvalThreads))) {
+            (opt->tree_cluster > 0 && opt->tree_cluster % (2 * kEvalThreads)) ||
+            (opt->ff_block != 0 && opt->ff_block != 64 && opt->ff_block != 128)) {
             delete c;
             return LSM_E_INVALID_ARG;
         }
@@ -412,6 +414,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
         if (opt->tree_grid > 0) ctx->opt.tree_grid = opt->tree_grid;
         if (opt->tree_ff_cluster != 0) ctx->opt.tree_ff_cluster = opt->tree_ff_cluster > 0 ? opt->tree_ff_cluster : 0;
         if (opt->tree_cluster != 0) ctx->opt.tree_cluster = opt->tree_cluster > 0 ? opt->tree_cluster : 0;
+        if (opt->ff_block != 0) ctx->opt.ff_block = opt->ff_block;
     }
     DeviceGuard g(device);
     int rc = LSM_OK;

@@ -283,8 +283,9 @@ struct EvalArgs {
     const int4* items; // optional work items (first target, count, first tile, end tile)
     const int* n_items;
     // float-float kernel only: 0 plain; 1 record the far-tile part into
-    // far_io [4][nt]; 2 evaluate near tiles only and add the recorded far part
-    // moved to x by its gradient (x_old: SoA targets of the record call)
+    // far_io ([split][4][nt] like out); 2 evaluate near tiles only, split 0
+    // adding the recorded far part ([4][nt]) moved to x by its gradient
+    // (x_old: SoA targets of the record call)
     int ff_mode;
     double* far_io;
     const double* x_old;
@@ -719,6 +720,52 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                     two_sum_acc(acc_h[0][3], acc_l[0][3], P3.x);
                     two_sum_acc(acc_h[1][3], acc_l[1][3], P3.y);
                 }
+            } else if constexpr (TPT == 1) {
+                // one target per thread: two consecutive sources ride in the
+                // two lanes (an odd tail pairs the last source with a zero
+                // weight), and the lanes are added before each chunk's fold
+                const float2 qx = make_float2(xq[0][0], xq[0][0]);
+                const float2 qy = make_float2(xq[0][1], xq[0][1]);
+                const float2 qz = make_float2(xq[0][2], xq[0][2]);
+                const float2 one = make_float2(1.0f, 1.0f), half = make_float2(0.5f, 0.5f);
+                const float2 p3 = make_float2(3.0f, 3.0f), m1 = make_float2(-1.0f, -1.0f);
+                for (int c0 = 0; c0 < cnt; c0 += kChunk) {
+                    const int c1 = min(cnt, c0 + kChunk);
+                    float2 P0 = make_float2(0.0f, 0.0f), P1 = P0, P2 = P0, P3 = P0;
+                    auto step = [&](const float4& ya, const float4& yb, const float4& na, const float4& nb) {
+                        const float2 ndx = __fadd2_rn(qx, make_float2(-ya.x, -yb.x));
+                        const float2 ndy = __fadd2_rn(qy, make_float2(-ya.y, -yb.y));
+                        const float2 ndz = __fadd2_rn(qz, make_float2(-ya.z, -yb.z));
+                        const float2 r2 = __ffma2_rn(ndx, ndx, __ffma2_rn(ndy, ndy, __fmul2_rn(ndz, ndz)));
+                        float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+#if LSM_RSQRT_REFINE
+                        const float2 t = __fmul2_rn(r2, ri);
+                        const float2 e = __ffma2_rn(t, __fmul2_rn(ri, m1), one);
+                        ri = __ffma2_rn(__fmul2_rn(ri, half), e, ri);
+#endif
+                        const float2 ri2 = __fmul2_rn(ri, ri);
+                        const float2 ri3 = __fmul2_rn(ri2, ri);
+                        const float2 nx = make_float2(na.x, nb.x), ny = make_float2(na.y, nb.y),
+                                     nz = make_float2(na.z, nb.z);
+                        const float2 dneg = __ffma2_rn(nx, ndx, __ffma2_rn(ny, ndy, __fmul2_rn(nz, ndz)));
+                        const float2 qn = __fmul2_rn(dneg, ri3);          // -(nw . r)/|r|^3
+                        P0 = __fadd2_rn(P0, qn);                          // -Phi
+                        const float2 tq = __fmul2_rn(qn, __fmul2_rn(ri2, p3));
+                        const float2 mnx = make_float2(-na.x, -nb.x), mny = make_float2(-na.y, -nb.y),
+                                     mnz = make_float2(-na.z, -nb.z);
+                        P1 = __ffma2_rn(tq, ndx, __ffma2_rn(mnx, ri3, P1));
+                        P2 = __ffma2_rn(tq, ndy, __ffma2_rn(mny, ri3, P2));
+                        P3 = __ffma2_rn(tq, ndz, __ffma2_rn(mnz, ri3, P3));
+                    };
+                    int s = c0;
+#pragma unroll 2
+                    for (; s + 1 < c1; s += 2) step(sp[s], sp[s + 1], sn[s], sn[s + 1]);
+                    if (s < c1) step(sp[s], sp[s], sn[s], make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+                    two_sum_acc(acc_h[0][0], acc_l[0][0], -(P0.x + P0.y));
+                    two_sum_acc(acc_h[0][1], acc_l[0][1], P1.x + P1.y);
+                    two_sum_acc(acc_h[0][2], acc_l[0][2], P2.x + P2.y);
+                    two_sum_acc(acc_h[0][3], acc_l[0][3], P3.x + P3.y);
+                }
             } else
 #endif
             for (int c0 = 0; c0 < cnt; c0 += kChunk) {
@@ -1062,7 +1109,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(const double4_32a* _
 constexpr int kFFStage = kTile * 64;  // bytes per stage: 4 float4 arrays
 constexpr int kMaxNearTiles = 768;    // near-tile list of one block (incremental mode)
 
-template <bool SIGX>
+template <bool SIGX, int TPB = kEvalThreads>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     const float4* __restrict__ spos, const float4* __restrict__ snw, const float4* __restrict__ slo,
     const float4* __restrict__ snwlo, EvalArgs A)
@@ -1089,19 +1136,23 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     } else if (A.list) {
         // this split's part of the block's interaction list (modes 0 and 1)
         const int blk = A.border[blockIdx.x];
-        base = blk * kEvalThreads;
+        base = blk * TPB;
         tend = A.nt;
         const int2 r = A.blist[blk];
         const int per = (r.y + (int)gridDim.y - 1) / (int)gridDim.y;
         t0 = min(r.x + (int)blockIdx.y * per, r.x + r.y);
         t1 = min(r.x + r.y, t0 + per);
     } else {
-        base = blockIdx.x * kEvalThreads;
+        base = blockIdx.x * TPB;
         tend = A.nt;
         t0 = blockIdx.y * A.tiles_per_split;
         t1 = min(A.ntiles, t0 + A.tiles_per_split);
     }
-    const int i = base + tid;
+    // SPL threads share each target, each taking every SPL-th source of a tile
+    constexpr int SPL = kEvalThreads / TPB;
+    static_assert(SPL == 1 || SPL == 2, "64 or 128 targets per CTA");
+    const int lane = SPL == 1 ? 0 : tid / TPB;
+    const int i = base + (SPL == 1 ? tid : tid % TPB);
     const bool valid = i < tend;
     for (int k = tid; k < kHTabN * 3; k += kEvalThreads) s_htab[k] = g_htab[k];
     int mode = A.ff_mode;
@@ -1143,7 +1194,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     // near-only call reuses it (the same near/far split in both)
     if (A.bb_io && mode != 0) {
         // the block's own slot: list mode launches blocks in another order
-        const int64_t bslot = A.list ? (int64_t)(base / kEvalThreads) : (int64_t)blockIdx.x;
+        const int64_t bslot = A.list ? (int64_t)(base / TPB) : (int64_t)blockIdx.x;
         float* io = A.bb_io + 8 * bslot;
         if (tid == 0) {
             if (mode == 1) {
@@ -1159,6 +1210,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
 
     // incremental mode: the block's near tiles, in tile order
     int nlist = t1 - t0;
+    bool scan = false;
     if (mode == 2) {
         if (tid == 0) s_nnear = 0;
         __syncthreads();
@@ -1182,12 +1234,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             __syncthreads();
         }
         nlist = s_nnear;
-        if (nlist > kMaxNearTiles) {   // too many to list: evaluate everything
-            mode = 0;
+        if (nlist > kMaxNearTiles) {   // too many to list: walk the whole range, skipping far tiles' pairs
+            scan = true;
             nlist = t1 - t0;
         }
     }
-    auto tile_at = [&](int k) { return mode == 2 ? s_near[k] : (A.list ? A.list[t0 + k] : t0 + k); };
+    auto tile_at = [&](int k) {
+        return mode == 2 && !scan ? s_near[k] : (A.list ? A.list[t0 + k] : t0 + k);
+    };
 
     float ph = 0.0f, pl = 0.0f;                                     // near Phi, float-float
     float gh[3] = {0.0f, 0.0f, 0.0f}, gl[3] = {0.0f, 0.0f, 0.0f};   // near grad, compensated FP32
@@ -1238,8 +1292,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         const int cnt = (int)A.thi[t].w;
         const bool far =
             t >= A.ntiles || tile_is_far(s_bb, SIGX ? with_sigma(A.tlo[t], s_smax) : A.tlo[t], A.thi[t], A.cut2);
-        if (far) pairs_far += valid ? cnt : 0;
-        else pairs_near += valid ? cnt : 0;
+        if (scan && far) {   // near-only call walking its whole range: the far part is the recorded one
+            __syncthreads();
+            continue;
+        }
+        if (far) pairs_far += valid && lane == 0 ? cnt : 0;
+        else pairs_near += valid && lane == 0 ? cnt : 0;
         const float4 ch = s_dref[b][0], cl = s_dref[b][1];
         const float cc[3] = {ch.x, ch.y, ch.z}, cc2[3] = {cl.x, cl.y, cl.z};
         float qh[3], ql[3];
@@ -1265,7 +1323,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             auto pairs = [&](auto far_c) {
                 constexpr bool FAR = decltype(far_c)::value;
 #pragma unroll 4
-                for (int s = c0; s < c1; s++) {
+                for (int s = c0 + lane; s < c1; s += SPL) {
                     const float4 y0 = sp[s], n = sn[s], yl0 = sl[s], nl = snl[s];
                     // the pair's a: the source's, or the target's in sigma(x) mode
                     const float4 y = SIGX ? make_float4(y0.x, y0.y, y0.z, ta_h) : y0;
@@ -1335,7 +1393,50 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         }
         __syncthreads();
     }
-    if (valid) {
+    if constexpr (SPL == 2) {
+        // the second lane's partial sums join the first's, through the stage
+        // buffers (idle: every copy has been waited for unless a stage was lost)
+        if (!failed) {
+            float* xch = reinterpret_cast<float*>(sh[0]);
+            const int k = tid % TPB;
+            if (lane == 1) {
+                float v[18] = {ph, pl, fph, fpl, dsum_h, dsum_l};
+                for (int c = 0; c < 3; c++) {
+                    v[6 + c] = gh[c];
+                    v[9 + c] = gl[c];
+                    v[12 + c] = fgh[c];
+                    v[15 + c] = fgl[c];
+                }
+#pragma unroll
+                for (int q = 0; q < 18; q++) xch[q * TPB + k] = v[q];
+            }
+            __syncthreads();
+            if (lane == 0) {
+                float v[18];
+#pragma unroll
+                for (int q = 0; q < 18; q++) v[q] = xch[q * TPB + k];
+                float nh_, nl_;
+                ff_add(ph, pl, v[0], v[1], nh_, nl_);
+                ph = nh_;
+                pl = nl_;
+                ff_add(fph, fpl, v[2], v[3], nh_, nl_);
+                fph = nh_;
+                fpl = nl_;
+                ff_add(dsum_h, dsum_l, v[4], v[5], nh_, nl_);
+                dsum_h = nh_;
+                dsum_l = nl_;
+                for (int c = 0; c < 3; c++) {
+                    ff_add(gh[c], gl[c], v[6 + c], v[9 + c], nh_, nl_);
+                    gh[c] = nh_;
+                    gl[c] = nl_;
+                    ff_add(fgh[c], fgl[c], v[12 + c], v[15 + c], nh_, nl_);
+                    fgh[c] = nh_;
+                    fgl[c] = nl_;
+                }
+            }
+        }
+    }
+    if (valid && lane == 0) {
         const int64_t plane = (int64_t)A.nt;
         double* out = A.out + (int64_t)blockIdx.y * 4 * plane;
         double phi = (double)ph + (double)pl;
@@ -1349,18 +1450,21 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             phi = kNaN;
             for (int c = 0; c < 3; c++) gr[c] = kNaN;
         } else if (mode == 2) {
-            // recorded far part, moved to x along its gradient
-            double fp = A.far_io[i];
-            for (int c = 0; c < 3; c++) {
-                const double g0 = A.far_io[(c + 1) * plane + i];
-                fp += g0 * (A.tx[c * A.ld + i] - A.x_old[c * A.ld + i]);
-                gr[c] += g0;
+            // recorded far part, moved to x along its gradient (once, by split 0)
+            if (blockIdx.y == 0) {
+                double fp = A.far_io[i];
+                for (int c = 0; c < 3; c++) {
+                    const double g0 = A.far_io[(c + 1) * plane + i];
+                    fp += g0 * (A.tx[c * A.ld + i] - A.x_old[c * A.ld + i]);
+                    gr[c] += g0;
+                }
+                phi += fp;
             }
-            phi += fp;
         } else {
             if (mode == 1) {
-                A.far_io[i] = fphi;
-                for (int c = 0; c < 3; c++) A.far_io[(c + 1) * plane + i] = fgr[c];
+                double* fo = A.far_io + (int64_t)blockIdx.y * 4 * plane;
+                fo[i] = fphi;
+                for (int c = 0; c < 3; c++) fo[(c + 1) * plane + i] = fgr[c];
             }
             phi += fphi;
             for (int c = 0; c < 3; c++) gr[c] += fgr[c];
@@ -1516,14 +1620,15 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     const bool mixed = precision == LSM_MIXED;
     const bool ff = precision == LSM_FF;
     const int tpt = mixed ? mixed_tpt(me) : kTPT64;
-    const int tpb = kEvalThreads * tpt;
+    // float-float CTAs of 64 targets (the option's default) outside sigma(x) mode
+    const bool ff64 = ff && !me->sigx && ctx->opt.ff_block == 64;
+    const int tpb = ff64 ? 64 : kEvalThreads * tpt;
     const int nblk = (t.n + tpb - 1) / tpb;
     const int ntiles = (int)me->ntiles;
     // split the tile range so that the grid covers the GPU a few times over
     const int want = ctx->num_sms * 16;
     int nsplit = 1;
     if (nblk < want) nsplit = std::min((want + nblk - 1) / nblk, std::max(1, ntiles / 4));
-    if (ff && inc && inc->mode != 0) nsplit = 1;   // the recorded far part is per target, not per split
     const int tps = (ntiles + nsplit - 1) / nsplit;
     nsplit = (ntiles + tps - 1) / tps;
 
@@ -1562,10 +1667,13 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         const int64_t avg = total / nblk;
         nsplit = 1;
         if (nblk < want) nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((want + nblk - 1) / nblk, avg / 4));
-        if (ff && inc && inc->mode != 0) nsplit = 1;
     }
     double* part = res;
     if (nsplit > 1) LSM_CUDA_TRY(ctx, s.get(&part, (size_t)nsplit * 4 * t.n));
+    // a split record call keeps one far part per split, summed like the results
+    const bool split_far = ff && inc && inc->mode == 1 && nsplit > 1;
+    double* far_part = nullptr;
+    if (split_far) LSM_CUDA_TRY(ctx, s.get(&far_part, (size_t)nsplit * 4 * t.n));
     EvalArgs A;
     A.tlo = me->tile_lo;
     A.thi = me->tile_hi;
@@ -1591,7 +1699,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     A.x_old = nullptr;
     if (ff && inc) {
         A.ff_mode = inc->mode;
-        A.far_io = inc->far_io;
+        A.far_io = split_far ? far_part : inc->far_io;
         A.x_old = inc->x_old;
         A.bb_io = inc->bb_io;
     }
@@ -1631,6 +1739,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     } else if (mixed) {
         k_eval_mixed<kTPT32, false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
                                                                    me->s32_nwlo, A);
+    } else if (ff64) {
+        k_eval_ff<false, 64><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else if (ff) {
         k_eval_ff<false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else {
@@ -1654,7 +1764,9 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         G.far_io = nullptr;
         G.x_old = nullptr;
         G.bb_io = nullptr;
-        if (ff)
+        if (ff64)
+            k_eval_ff<false, 64><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, G);
+        else if (ff)
             k_eval_ff<false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, G);
         else if (tpt == 1)
             k_eval_mixed<1, false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
@@ -1670,6 +1782,10 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     }
     if (nsplit > 1) {
         k_reduce_splits<<<(t.n + 255) / 256, 256, 0, st>>>(part, nsplit, t.n, res);
+        LSM_LAUNCHED(ctx);
+    }
+    if (split_far) {
+        k_reduce_splits<<<(t.n + 255) / 256, 256, 0, st>>>(far_part, nsplit, t.n, inc->far_io);
         LSM_LAUNCHED(ctx);
     }
     if (rg) {

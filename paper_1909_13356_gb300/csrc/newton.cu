@@ -315,13 +315,13 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
     // them are ~1e-8 sigma, where the far part is linear to ~1e-14
     int32_t* Lrec = nullptr;
     double *Trec = nullptr, *Rfar = nullptr;
-    float* BBrec = nullptr;   // block boxes of the record sweep (kEvalThreads targets per block)
+    float* BBrec = nullptr;   // block boxes of the record sweep (64 or more targets per block)
     int nrec = 0, ff_stage = 0;
     if (mixed) {
         LSM_CUDA_TRY(ctx, s.get(&Lrec, (size_t)N));
         LSM_CUDA_TRY(ctx, s.get(&Trec, 3 * (size_t)N));
         LSM_CUDA_TRY(ctx, s.get(&Rfar, 4 * (size_t)N));
-        LSM_CUDA_TRY(ctx, s.get(&BBrec, 8 * ((size_t)N / kEvalThreads + 2)));
+        LSM_CUDA_TRY(ctx, s.get(&BBrec, 8 * ((size_t)N / 64 + 2)));
     }
     int iter = 0;
     for (; iter < max_iter && nact > 0; iter++) {

@@ -722,48 +722,112 @@ __device__ __forceinline__ bool cluster_takes(const WalkArgs& A, int64_t node, i
     return d > 0.0f && d * d >= cc.w * 1.0001f;
 }
 
-// Depth-first walk of the tree for one target block (children in Morton
-// order, so the list is in a fixed order).  Pass 0 counts, pass 1 writes.
-__global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass)
+// A warp walks the tree for one target box.  Each round pops up to 32 entries
+// from the top of the warp's stack (shared memory), one per lane; a lane's
+// node is either emitted (its proxy tiles, or its tile at the leaf level),
+// skipped, or opened (its children pushed).  Emitted tiles and pushed
+// children are placed by warp prefix sums in lane order, so the walk and its
+// list are the same on every call (pass 0 counts, pass 1 writes).  A round
+// pops at most kWalkSoft - sp entries, so a round never takes the stack past
+// kWalkSoft; at kWalkSoft and above it pops one entry, a plain depth-first
+// step, which adds at most one entry per level below the popped node: the
+// stack stays within kWalkSoft + kMaxLevels + 1 <= kWalkStack.
+constexpr int kWalkSoft = 216;
+constexpr int kWalkStack = 256;
+static_assert(kWalkSoft + kMaxLevels + 1 <= kWalkStack, "walk stack bound");
+enum WalkAct { kSkip = 0, kEmitProxies = 1, kEmitLeaf = 2, kOpen = 3 };
+
+template <class Decide>
+__device__ __forceinline__ uint32_t warp_walk(const WalkArgs& A, int* stk, int* list, uint32_t o, int pass,
+                                              Decide&& decide)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= A.nblk) return;
-    const float4 bl = A.blo[b], bh = A.bhi[b];
-    int stk[2 * kMaxLevels + 2];
-    int sp = 0;
-    stk[sp++] = A.top << 26;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) stk[0] = A.top << 26;
+    __syncwarp();
+    int sp = 1;
     uint32_t n = 0;
-    const uint32_t o = pass ? A.off[b] : 0u;
     while (sp > 0) {
-        const int v = stk[--sp];
-        const int l = v >> 26, i = v & ((1 << 26) - 1);
-        const int64_t node = A.lev_off[l] + i;
-        const int4 f = A.info[node];
-        if (f.z >= 0) {
-            // the cluster's grid has it
-            if (A.bpc > 0 && ((A.cbits[(int64_t)(b / A.bpc) * A.cwords + (node >> 5)] >> (node & 31)) & 1u)) continue;
-            // opening rule: the block at distance >= the node's opening radius
-            // from the centre of its frame
-            if (box_takes(A, node, bl, bh, A.sigx ? bl.w : A.nlo[node].w)) {
-                if (pass)
-                    for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.ntiles + f.z + k;
-                n += f.w;
-                continue;
+        const int k = min(32, min(sp, max(1, kWalkSoft - sp)));
+        int nent = 0, nchild = 0, l = 0, i = 0, act = kSkip;
+        int4 f = make_int4(0, 0, -1, 0);
+        if (lane < k) {
+            const int v = stk[sp - 1 - lane];
+            l = v >> 26;
+            i = v & ((1 << 26) - 1);
+            const int64_t node = A.lev_off[l] + i;
+            f = A.info[node];
+            act = decide(node, l, f);
+            if (act == kEmitProxies) {
+                nent = f.w;
+            } else if (act == kEmitLeaf) {
+                nent = 1;
+            } else if (act == kOpen) {
+                const int64_t nch = A.lev_off[l] - A.lev_off[l - 1];
+                nchild = 2 * i + 1 < nch ? 2 : 1;
             }
         }
-        if (l == 0) {
-            if (pass) A.list[o + n] = i;
-            n++;
-            continue;
+        __syncwarp();   // every popped entry is read before children overwrite it
+        int pe = nent, pc = nchild;   // inclusive prefix sums over the lanes
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, pe, d), b = __shfl_up_sync(0xffffffffu, pc, d);
+            if (lane >= d) {
+                pe += a;
+                pc += b;
+            }
         }
-        const int64_t nch = A.lev_off[l] - A.lev_off[l - 1];
-        if (2 * i + 1 < nch) stk[sp++] = ((l - 1) << 26) | (2 * i + 1);
-        stk[sp++] = ((l - 1) << 26) | (2 * i);
+        const int tot_e = __shfl_sync(0xffffffffu, pe, 31), tot_c = __shfl_sync(0xffffffffu, pc, 31);
+        if (pass && nent) {
+            int* dst = list + o + n + (pe - nent);
+            if (act == kEmitLeaf) dst[0] = i;
+            else
+                for (int q = 0; q < nent; q++) dst[q] = A.ntiles + f.z + q;
+        }
+        if (nchild) {
+            // the odd child below the even one, as a depth-first walk pushes them
+            int* dst = stk + (sp - k) + (pc - nchild);
+            if (nchild == 2) {
+                dst[0] = ((l - 1) << 26) | (2 * i + 1);
+                dst[1] = ((l - 1) << 26) | (2 * i);
+            } else {
+                dst[0] = ((l - 1) << 26) | (2 * i);
+            }
+        }
+        __syncwarp();
+        sp = sp - k + tot_c;
+        n += (uint32_t)tot_e;
     }
-    if (pass)
-        A.blist[b] = make_int2((int)o, (int)n);
-    else
-        A.cnt[b] = n;
+    return n;
+}
+
+// The interaction list of each target block, one warp per block: a node with
+// proxies that the block's cluster took (bitmap) is skipped, one that the
+// block rule accepts is emitted, and the walk descends to the leaf tiles
+// otherwise.
+__global__ void __launch_bounds__(kWalkThreads) k_tree_walk(WalkArgs A, int pass)
+{
+    __shared__ int s_stk[kWalkThreads / 32][kWalkStack];
+    const int b = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (b >= A.nblk) return;   // whole warps
+    const float4 bl = A.blo[b], bh = A.bhi[b];
+    const uint32_t o = pass ? A.off[b] : 0u;
+    const uint32_t n = warp_walk(A, s_stk[threadIdx.x >> 5], A.list, o, pass, [&](int64_t node, int l, int4 f) {
+        if (f.z >= 0) {
+            // the cluster's grid has it
+            if (A.bpc > 0 && ((A.cbits[(int64_t)(b / A.bpc) * A.cwords + (node >> 5)] >> (node & 31)) & 1u))
+                return (int)kSkip;
+            // opening rule: the block at distance >= the node's opening radius
+            // from the centre of its frame
+            if (box_takes(A, node, bl, bh, A.sigx ? bl.w : A.nlo[node].w)) return (int)kEmitProxies;
+        }
+        return l == 0 ? (int)kEmitLeaf : (int)kOpen;
+    });
+    if ((threadIdx.x & 31) == 0) {
+        if (pass)
+            A.blist[b] = make_int2((int)o, (int)n);
+        else
+            A.cnt[b] = n;
+    }
 }
 
 // Sort keys that order blocks by decreasing list length (longest first),
@@ -946,42 +1010,28 @@ struct ClusterWalkArgs {
 // every (target, node) interaction is counted once.
 __global__ void __launch_bounds__(kWalkThreads) k_cluster_walk(ClusterWalkArgs A, int pass)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= A.ncl) return;
-    int stk[2 * kMaxLevels + 2];
-    int sp = 0;
-    stk[sp++] = A.W.top << 26;
-    uint32_t n = 0;
+    __shared__ int s_stk[kWalkThreads / 32][kWalkStack];
+    const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (c >= A.ncl) return;   // whole warps
     const uint32_t o = pass ? A.off[c] : 0u;
     const int b0 = c * A.bpc, b1 = min(A.nblk, b0 + A.bpc);
-    while (sp > 0) {
-        const int v = stk[--sp];
-        const int l = v >> 26, i = v & ((1 << 26) - 1);
-        const int64_t node = A.W.lev_off[l] + i;
-        const int4 f = A.W.info[node];
+    const uint32_t n = warp_walk(A.W, s_stk[threadIdx.x >> 5], A.list, o, pass, [&](int64_t node, int l, int4 f) {
         if (f.z >= 0) {
             if (cluster_takes(A.W, node, c)) {
-                if (pass) {
-                    for (int k = 0; k < f.w; k++) A.list[o + n + k] = A.W.ntiles + f.z + k;
-                    A.cbits[(int64_t)c * A.W.cwords + (node >> 5)] |= 1u << (node & 31);
-                }
-                n += f.w;
-                continue;
+                if (pass) atomicOr(&A.cbits[(int64_t)c * A.W.cwords + (node >> 5)], 1u << (node & 31));
+                return (int)kEmitProxies;
             }
-            bool some_block = false;
-            for (int b = b0; b < b1 && !some_block; b++)
-                some_block = box_takes(A.W, node, A.blo[b], A.bhi[b], A.W.nlo[node].w);
-            if (some_block) continue;
+            for (int b = b0; b < b1; b++)
+                if (box_takes(A.W, node, A.blo[b], A.bhi[b], A.W.nlo[node].w)) return (int)kSkip;
         }
-        if (l == 0) continue;
-        const int64_t nch = A.W.lev_off[l] - A.W.lev_off[l - 1];
-        if (2 * i + 1 < nch) stk[sp++] = ((l - 1) << 26) | (2 * i + 1);
-        stk[sp++] = ((l - 1) << 26) | (2 * i);
+        return l == 0 ? (int)kSkip : (int)kOpen;
+    });
+    if ((threadIdx.x & 31) == 0) {
+        if (pass)
+            A.clist[c] = make_int2((int)o, (int)n);
+        else
+            A.cnt[c] = n;
     }
-    if (pass)
-        A.clist[c] = make_int2((int)o, (int)n);
-    else
-        A.cnt[c] = n;
 }
 
 // Each block of grid points takes its cluster's list; launch order as given.
@@ -1439,7 +1489,7 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, int tpb, d
     A.cnt = cnt;
     A.list = nullptr;
     A.clist = clist;
-    k_cluster_walk<<<blocks_of(ncl, kWalkThreads), kWalkThreads, 0, st>>>(A, 0);
+    k_cluster_walk<<<blocks_of((int64_t)ncl * 32, kWalkThreads), kWalkThreads, 0, st>>>(A, 0);
     LSM_LAUNCHED(ctx);
     int rc = scan_exclusive(ctx, cnt, ncl, cnt + ncl, st);
     if (rc != LSM_OK) return rc;
@@ -1453,7 +1503,7 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, int tpb, d
     cp.total = h_total;
     LSM_CUDA_TRY(ctx, s.get(&cp.list, std::max<uint32_t>(1u, h_total)));
     A.list = cp.list;
-    k_cluster_walk<<<blocks_of(ncl, kWalkThreads), kWalkThreads, 0, st>>>(A, 1);
+    k_cluster_walk<<<blocks_of((int64_t)ncl * 32, kWalkThreads), kWalkThreads, 0, st>>>(A, 1);
     LSM_LAUNCHED(ctx);
     LSM_CUDA_TRY(ctx, s.get(&cp.gblist, std::max(1, cp.ngblk)));
     LSM_CUDA_TRY(ctx, s.get(&cp.gorder, std::max(1, cp.ngblk)));
@@ -1512,7 +1562,7 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double*
     W.cnt = cnt;
     W.list = nullptr;
     W.blist = *blist;
-    k_tree_walk<<<blocks_of(nblk, kWalkThreads), kWalkThreads, 0, st>>>(W, 0);
+    k_tree_walk<<<blocks_of((int64_t)nblk * 32, kWalkThreads), kWalkThreads, 0, st>>>(W, 0);
     LSM_LAUNCHED(ctx);
     // launch order: longest lists first, so that the last wave is short
     uint32_t* keys = nullptr;
@@ -1536,7 +1586,7 @@ int tree_lists(Ctx* ctx, const Tree* T, const Targets& t, int tpb, const double*
     *total_out = h_total;
     LSM_CUDA_TRY(ctx, s.get(list, std::max<uint32_t>(1u, h_total)));
     W.list = *list;
-    k_tree_walk<<<blocks_of(nblk, kWalkThreads), kWalkThreads, 0, st>>>(W, 1);
+    k_tree_walk<<<blocks_of((int64_t)nblk * 32, kWalkThreads), kWalkThreads, 0, st>>>(W, 1);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }

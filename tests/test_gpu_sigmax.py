@@ -56,18 +56,21 @@ def test_phi_grad_sigma_x_matches_oracle(lsm, graded, prec, tphi, tgrad):
 
 def test_sigma_x_equal_widths_reduce_to_constant(lsm):
     """Cube: every triangle has the same D_j, so sigma(x) is constant and the
-    results equal the per-triangle mesh's with that sigma."""
+    results equal the per-triangle mesh's with that sigma.  The float-float
+    kernel's gradient is FP32 with compensated sums (it only steers Newton),
+    and the two meshes run it on differently sized target blocks, so its bar
+    is the mixed one."""
     m = synth.cube(1.0, 4)
     ctx = lsm.Context(0)
     mx = ctx.upload_sigma_x(m.verts, m.tris, n_gl=4, subdiv=1)
     sig = 0.5 * np.sqrt(2) / 2.5
     mc = ctx.upload(m.verts, m.tris, np.full(m.m, sig), n_gl=4, subdiv=1)
     x = synth.targets_uniform(2000, -1.5, 1.5, synth.rng(53))
-    for prec, tol in ((lsm.FP64, 1e-13), (lsm.FF, 1e-13), (lsm.MIXED, 5e-8)):
+    for prec, tol, gtol in ((lsm.FP64, 1e-13, 1e-11), (lsm.FF, 1e-13, 1e-7), (lsm.MIXED, 5e-8, 5e-6)):
         p1, g1 = mx.eval_phi_grad(x, prec)
         p0, g0 = mc.eval_phi_grad(x, prec)
         assert np.abs(p1 - p0).max() <= tol
-        assert np.abs(g1 - g0).max() <= tol * 100 / sig
+        assert np.abs(g1 - g0).max() <= gtol / sig
 
 
 def test_sigma_x_chart_solve(lsm, oracle_mod, graded):

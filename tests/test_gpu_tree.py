@@ -229,6 +229,29 @@ def test_ff_tree_dense_against_direct(lsm):
     assert st_t["pairs_far"] < st_d["pairs_far"]
 
 
+def test_ff_block_sizes(lsm, torus_case):
+    """The float-float kernel with 64 targets per CTA (two threads per target,
+    the default) and with 128: both within the FP64 bar of the oracle, within
+    5e-13 of each other, and the smaller target boxes evaluate fewer pairs."""
+    w = torus_case["w"]
+    m = w["mesh"]
+    out = {}
+    for blk in (64, 128):
+        ctx = lsm.Context(0, ff_block=blk)
+        mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+        _eval(lsm, ctx, mesh, w["targets"][:4096], lsm.FF)    # builds the tree
+        ctx.read_stats(reset=True)
+        phi, grad = _eval(lsm, ctx, mesh, w["targets"], lsm.FF)
+        st = ctx.read_stats(reset=True)
+        assert np.abs(phi - torus_case["phi"]).max() <= 1e-12, blk
+        assert np.abs(grad - torus_case["grad"]).max() <= TOL32 / m.sigma.min(), blk
+        out[blk] = (phi, st["pairs_near"] + st["pairs_far"])
+    assert np.abs(out[64][0] - out[128][0]).max() <= 5e-13
+    assert out[64][1] < out[128][1], (out[64][1], out[128][1])
+    with pytest.raises(lsm.LsmError):
+        lsm.Context(0, ff_block=96)
+
+
 def test_oriented_grids_and_full_grids(lsm, torus_case):
     """Oriented per-axis grids with the degree ladder (the default) and full
     axis-aligned (p+1)^3 grids of one degree: both within the mixed bar and
