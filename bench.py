@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--tree-theta", type=float, default=0.0, help="treecode opening parameter (0: default)")
     ap.add_argument("--ff-block", type=int, default=0,
                     help="targets per CTA of the float-float kernel (64 or 128; 0: library default)")
+    ap.add_argument("--mixed-block", type=int, default=0,
+                    help="targets per CTA of the mixed kernel (64, 128 or 256; 0: the autotuner's choice)")
     ap.add_argument("--tree-grid", type=int, default=0,
                     help="proxy grids: 1 per-axis point counts (default), 2 full (degree + 1)^3")
     ap.add_argument("--sigma-x", action="store_true",
@@ -671,7 +673,7 @@ def main():
     w = workload(args, rank if args.replicas else 0)
     m = w["mesh"]
     ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid,
-                      ff_block=args.ff_block)
+                      ff_block=args.ff_block, mixed_block=args.mixed_block)
     # the pipes' measured throughput (roofline denominators), clocks sampled around the probe
     pclk = ClockSampler(local)
     pclk.start()

@@ -153,6 +153,11 @@ typedef struct {
      * streaming each source tile.  The target-dependent sigma(x) mode and
      * batches always use 128. */
     int32_t ff_block;
+    /* Targets per CTA of the mixed kernel (64, 128 or 256; 0: the mesh's
+     * autotuned choice, else 256).  A nonzero value overrides the
+     * autotuner's; sigma(x) mode always uses 256. */
+    int32_t mixed_block;
+    int32_t reserved;   /* keeps the size a multiple of 8 without padding; set 0 */
 } lsm_options;
 
 /* Statistics of one chart solve. */
@@ -489,8 +494,9 @@ int lsm_refine_adaptive(lsm_mesh* mesh, int order, double newton_tol, double flu
  * With that far field it then chooses the mixed kernel's near-field radius
  * (6.4, 6.5 or 7 sigma: those where the smoothed kernel differs from the
  * Laplace double layer by at most 1e-8 relative, Sec. 4.4) and its target
- * tile (128 or 256 targets per thread block), again the fastest within the
- * budget.
+ * tile (64, 128 or 256 targets per thread block of 128 threads: two threads
+ * per target, one, or a thread for two targets; 256 only in sigma(x) mode),
+ * again the fastest within the budget.
  * Cost: one float-float evaluation of the sample, and a tree build plus two
  * mixed evaluations of it per candidate.  Synchronises `stream`.
  * Errors: LSM_E_INVALID_ARG (n < 1, bad budget), LSM_E_OOM, LSM_E_CUDA. */
@@ -505,7 +511,7 @@ typedef struct {
     double ms_direct;         /* the direct far field's time on the sample */
     double err_direct;        /* and its error */
     double cutoff;            /* chosen near-field radius of the mixed kernel, in sigma */
-    int32_t targets_per_block;/* chosen target tile of the mixed kernel (128 or 256) */
+    int32_t targets_per_block;/* chosen target tile of the mixed kernel (64, 128 or 256) */
     int32_t reserved;
 } lsm_tune_result;
 int lsm_autotune(lsm_mesh* mesh, const double* x, int64_t n, double err_budget, lsm_tune_result* out,

@@ -397,7 +397,8 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
             opt->tree_ff_cluster > (1 << 20) || (opt->tree_ff_cluster > 0 && opt->tree_ff_cluster % kEvalThreads) ||
             opt->tree_cluster < -1 || opt->tree_cluster > (1 << 20) ||
             (opt->tree_cluster > 0 && opt->tree_cluster % (2 * kEvalThreads)) ||
-            (opt->ff_block != 0 && opt->ff_block != 64 && opt->ff_block != 128)) {
+            (opt->ff_block != 0 && opt->ff_block != 64 && opt->ff_block != 128) ||
+            (opt->mixed_block != 0 && opt->mixed_block != 64 && opt->mixed_block != 128 && opt->mixed_block != 256)) {
             delete c;
             return LSM_E_INVALID_ARG;
         }
@@ -415,6 +416,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
         if (opt->tree_ff_cluster != 0) ctx->opt.tree_ff_cluster = opt->tree_ff_cluster > 0 ? opt->tree_ff_cluster : 0;
         if (opt->tree_cluster != 0) ctx->opt.tree_cluster = opt->tree_cluster > 0 ? opt->tree_cluster : 0;
         if (opt->ff_block != 0) ctx->opt.ff_block = opt->ff_block;
+        ctx->opt.mixed_block = opt->mixed_block;
     }
     DeviceGuard g(device);
     int rc = LSM_OK;

@@ -43,6 +43,14 @@
 #ifndef LSM_RSQRT_REFINE
 #define LSM_RSQRT_REFINE 1
 #endif
+// near tiles: sources beyond the cutoff from the whole target box take the
+// Laplace pair (float-float kernel, mixed kernel)
+#ifndef LSM_REACH_SPLIT_FF
+#define LSM_REACH_SPLIT_FF 1
+#endif
+#ifndef LSM_REACH_SPLIT_MIXED
+#define LSM_REACH_SPLIT_MIXED 1
+#endif
 #ifndef LSM_PACKED_F32X2
 #define LSM_PACKED_F32X2 1
 #endif
@@ -525,7 +533,7 @@ __device__ __forceinline__ void ff_far_pair(const float4& y, const float4& n, co
 }
 
 // ---------------------------------------------------------------- mixed kernel
-template <int TPT, bool SIGX>
+template <int TPT, bool SIGX, int SPL = 1>
 __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __restrict__ spos,
                                                             const float4* __restrict__ snw,
                                                             const float4* __restrict__ slo,
@@ -539,8 +547,16 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float s_bb[6];
     __shared__ float s_smax;
+    __shared__ unsigned char s_perm[kTile];   // near tile: its sources, those within reach of the block first
+    __shared__ int s_cnt[2][kEvalThreads / 32];
 
+    // SPL threads share each target (SPL 2: one target per pair of threads,
+    // 64 per CTA), each taking its share of every tile's sources
+    static_assert(SPL == 1 || (SPL == 2 && TPT == 1), "two threads per target with one target per thread");
+    constexpr int TPB = kEvalThreads * TPT / SPL;
     const int tid = threadIdx.x;
+    const int lane = SPL == 1 ? 0 : tid / TPB;
+    const int tix = SPL == 1 ? tid : tid % TPB;   // the thread's target within its row of the block
     int base, tend, t0, t1;
     if (A.items) {
         if ((int)blockIdx.x >= *A.n_items) return;  // whole CTA, before any barrier
@@ -552,14 +568,14 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
     } else if (A.list) {
         // this split's part of the block's interaction list
         const int blk = A.border[blockIdx.x];
-        base = blk * (kEvalThreads * TPT);
+        base = blk * TPB;
         tend = A.nt;
         const int2 r = A.blist[blk];
         const int per = (r.y + (int)gridDim.y - 1) / (int)gridDim.y;
         t0 = min(r.x + (int)blockIdx.y * per, r.x + r.y);
         t1 = min(r.x + r.y, t0 + per);
     } else {
-        base = blockIdx.x * (kEvalThreads * TPT);
+        base = blockIdx.x * TPB;
         tend = A.nt;
         t0 = blockIdx.y * A.tiles_per_split;
         t1 = min(A.ntiles, t0 + A.tiles_per_split);
@@ -571,7 +587,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
     int nvalid = 0;
 #pragma unroll
     for (int k = 0; k < TPT; k++) {
-        const int i = base + k * kEvalThreads + tid;
+        const int i = base + k * kEvalThreads + tix;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const double v = i < tend ? A.tx[c * A.ld + i] : 0.0;
@@ -582,7 +598,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                 hi[c] = fmaxf(hi[c], __double2float_ru(v));
             }
         }
-        nvalid += i < tend ? 1 : 0;
+        nvalid += i < tend && lane == 0 ? 1 : 0;   // pairs counted once per target
     }
     block_bbox(lo, hi, s_bb);
     // sigma(x) mode: each target's a = 1/(sqrt2 sigma(x)) as a float pair, and
@@ -594,7 +610,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         float smax = 0.0f;
 #pragma unroll
         for (int k = 0; k < TPT; k++) {
-            const int i = base + k * kEvalThreads + tid;
+            const int i = base + k * kEvalThreads + tix;
             if (i < tend) {
                 const double sg = A.tsig[i];
                 const double a = 1.0 / (kSqrt2 * sg);
@@ -757,10 +773,14 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                         P2 = __ffma2_rn(tq, ndy, __ffma2_rn(mny, ri3, P2));
                         P3 = __ffma2_rn(tq, ndz, __ffma2_rn(mnz, ri3, P3));
                     };
-                    int s = c0;
+                    const int npair = (c1 - c0) >> 1;
 #pragma unroll 2
-                    for (; s + 1 < c1; s += 2) step(sp[s], sp[s + 1], sn[s], sn[s + 1]);
-                    if (s < c1) step(sp[s], sp[s], sn[s], make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+                    for (int q = lane; q < npair; q += SPL) {
+                        const int s = c0 + 2 * q;
+                        step(sp[s], sp[s + 1], sn[s], sn[s + 1]);
+                    }
+                    if (((c1 - c0) & 1) && lane == npair % SPL)
+                        step(sp[c1 - 1], sp[c1 - 1], sn[c1 - 1], make_float4(0.0f, 0.0f, 0.0f, 0.0f));
                     two_sum_acc(acc_h[0][0], acc_l[0][0], -(P0.x + P0.y));
                     two_sum_acc(acc_h[0][1], acc_l[0][1], P1.x + P1.y);
                     two_sum_acc(acc_h[0][2], acc_l[0][2], P2.x + P2.y);
@@ -774,7 +794,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
 #pragma unroll
                 for (int k = 0; k < TPT; k++) p[k][0] = p[k][1] = p[k][2] = p[k][3] = 0.0f;
 #pragma unroll 4
-                for (int s = c0; s < c1; s++) {
+                for (int s = c0 + lane; s < c1; s += SPL) {
                     const float4 y = sp[s];
                     const float4 n = sn[s];
 #pragma unroll
@@ -799,7 +819,44 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                     for (int c = 0; c < 4; c++) two_sum_acc(acc_h[k][c], acc_l[k][c], p[k][c]);
             }
         } else {
-            pairs_near += (unsigned long long)cnt * nvalid;
+            // A near tile's sources beyond the cutoff from the whole target box
+            // take the far field's Laplace pair (Sec. 4.4's split is by
+            // distance).  Thread tid tests source tid (FP32 position against
+            // the box, with a 1e-3 margin); s_perm lists the sources within
+            // reach first, each group in source order.
+            bool reach = !LSM_REACH_SPLIT_MIXED;
+            if (LSM_REACH_SPLIT_MIXED && tid < cnt) {
+                const float4 y = sp[tid];
+                const float a = SIGX ? 0.70710678f / s_smax : y.w;
+                const float px = ch.x + y.x, py = ch.y + y.y, pz = ch.z + y.z;
+                const float gx = fmaxf(0.0f, fmaxf(s_bb[0] - px, px - s_bb[3]));
+                const float gy = fmaxf(0.0f, fmaxf(s_bb[1] - py, py - s_bb[4]));
+                const float gz = fmaxf(0.0f, fmaxf(s_bb[2] - pz, pz - s_bb[5]));
+                reach = !((gx * gx + gy * gy + gz * gz) * (2.0f * a * a) > A.cut2 * 1.001f);
+            }
+            const int wl = tid & 31, wp = tid >> 5;
+            const unsigned bn = __ballot_sync(0xffffffffu, tid < cnt && reach);
+            const unsigned bf = __ballot_sync(0xffffffffu, tid < cnt && !reach);
+            if (wl == 0) {
+                s_cnt[0][wp] = __popc(bn);
+                s_cnt[1][wp] = __popc(bf);
+            }
+            __syncthreads();
+            int nn = 0, pn = 0, pf = 0;
+#pragma unroll
+            for (int w = 0; w < kEvalThreads / 32; w++) {
+                nn += s_cnt[0][w];
+                if (w < wp) {
+                    pn += s_cnt[0][w];
+                    pf += s_cnt[1][w];
+                }
+            }
+            const unsigned below = (1u << wl) - 1u;
+            if (tid < cnt) s_perm[reach ? pn + __popc(bn & below) : nn + pf + __popc(bf & below)] = (unsigned char)tid;
+            __syncthreads();
+            // pairs counted by the kernel they take
+            pairs_near += (unsigned long long)nn * nvalid;
+            pairs_far += (unsigned long long)(cnt - nn) * nvalid;
             // target offset from the tile centre as a float-float pair
             float qh[TPT][3], ql[TPT][3];
 #pragma unroll
@@ -831,7 +888,8 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
 #pragma unroll
             for (int k = 0; k < TPT; k++) cd[k] = 0.0f;
 #pragma unroll 1
-            for (int s = 0; s < cnt; s++) {
+            for (int k = lane; k < nn; k += SPL) {
+                const int s = s_perm[k];
                 const float4 y = sp[s];
                 const float4 n = sn[s];
                 const float4 yl = sl[s];
@@ -853,6 +911,32 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                     two_sum_acc(cg[k][1], cgl[k][1], -fmaf(n.y, fH, tq * dyh));
                     two_sum_acc(cg[k][2], cgl[k][2], -fmaf(n.z, fH, tq * dzh));
                     if constexpr (SIGX) cd[k] = fmaf(dh, expf(-rh * ya.w * ya.w), cd[k]);
+                }
+            }
+            // the rest with the Laplace pair in FP32 (tile-local coordinates,
+            // the target offset's high part), folded into the same tile sums
+#pragma unroll 2
+            for (int k = nn + lane; k < cnt; k += SPL) {
+                const int s = s_perm[k];
+                const float4 y = sp[s];
+                const float4 n = sn[s];
+#pragma unroll
+                for (int q = 0; q < TPT; q++) {
+                    const float dx = y.x - qh[q][0], dy = y.y - qh[q][1], dz = y.z - qh[q][2];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float ri = rsqrt_refined(r2);
+                    const float ri2 = ri * ri;
+                    const float ri3 = ri2 * ri;
+                    const float d = fmaf(n.x, dx, fmaf(n.y, dy, n.z * dz));
+                    const float qv = d * ri3;
+                    float sph, tph;
+                    two_sum(cph[q], qv, sph, tph);
+                    cph[q] = sph;
+                    cpl[q] += tph;
+                    const float tq = 3.0f * qv * ri2;
+                    two_sum_acc(cg[q][0], cgl[q][0], fmaf(tq, dx, -n.x * ri3));
+                    two_sum_acc(cg[q][1], cgl[q][1], fmaf(tq, dy, -n.y * ri3));
+                    two_sum_acc(cg[q][2], cgl[q][2], fmaf(tq, dz, -n.z * ri3));
                 }
             }
             if constexpr (SIGX) {
@@ -881,12 +965,41 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
             for (int c = 0; c < 4; c++) renorm(acc_h[k][c], acc_l[k][c]);
         __syncthreads();
     }
+    if constexpr (SPL == 2) {
+        // the second thread's sums join the first's, through the stage buffer
+        // (idle: every copy has been waited for unless a stage was lost)
+        if (!failed) {
+            float* xch = reinterpret_cast<float*>(&sh_pos[0][0]);   // both stages: 1,024 floats
+            if (lane == 1) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    xch[(2 * c) * TPB + tix] = acc_h[0][c];
+                    xch[(2 * c + 1) * TPB + tix] = acc_l[0][c];
+                }
+                xch[8 * TPB + tix] = dsum_h[0];
+                xch[9 * TPB + tix] = dsum_l[0];
+            }
+            __syncthreads();
+            if (lane == 0) {
+                float nh_, nl_;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    ff_add(acc_h[0][c], acc_l[0][c], xch[(2 * c) * TPB + tix], xch[(2 * c + 1) * TPB + tix], nh_, nl_);
+                    acc_h[0][c] = nh_;
+                    acc_l[0][c] = nl_;
+                }
+                ff_add(dsum_h[0], dsum_l[0], xch[8 * TPB + tix], xch[9 * TPB + tix], nh_, nl_);
+                dsum_h[0] = nh_;
+                dsum_l[0] = nl_;
+            }
+        }
+    }
     const int64_t plane = (int64_t)A.nt;
     double* out = A.out + (int64_t)blockIdx.y * 4 * plane;
 #pragma unroll
     for (int k = 0; k < TPT; k++) {
-        const int i = base + k * kEvalThreads + tid;
-        if (i < tend) {
+        const int i = base + k * kEvalThreads + tix;
+        if (i < tend && lane == 0) {
             double r[4];
 #pragma unroll
             for (int c = 0; c < 4; c++) r[c] = failed ? kNaN : (double)acc_h[k][c] + (double)acc_l[k][c];
@@ -1123,6 +1236,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     __shared__ int s_nnear;
     __shared__ float s_smax;
     __shared__ float4 s_dref[2][2];   // per stage: tile centre - block reference, float pair
+    __shared__ unsigned char s_perm[kTile];   // near tile: its sources, those within reach of the block first
+    __shared__ int s_cnt[2][kEvalThreads / 32];
 
     const int tid = threadIdx.x;
     int base, tend, t0, t1;
@@ -1297,7 +1412,6 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             continue;
         }
         if (far) pairs_far += valid && lane == 0 ? cnt : 0;
-        else pairs_near += valid && lane == 0 ? cnt : 0;
         const float4 ch = s_dref[b][0], cl = s_dref[b][1];
         const float cc[3] = {ch.x, ch.y, ch.z}, cc2[3] = {cl.x, cl.y, cl.z};
         float qh[3], ql[3];
@@ -1313,17 +1427,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         const float4* sn = sp + kTile;
         const float4* sl = sp + 2 * kTile;
         const float4* snl = sp + 3 * kTile;
-        for (int c0 = 0; c0 < cnt; c0 += kChunk) {
-            const int c1 = min(cnt, c0 + kChunk);
-            float g[3] = {0.0f, 0.0f, 0.0f}, gn[3] = {0.0f, 0.0f, 0.0f};
-            float cph = 0.0f, cpl = 0.0f;   // this chunk's Phi, float-float
-            float cd = 0.0f;                // sigma(x) mode: sum of (nw . r) e^{-w}
-            // the pair loop, compiled once for far tiles and once for near
-            // ones (far is uniform over the tile)
-            auto pairs = [&](auto far_c) {
-                constexpr bool FAR = decltype(far_c)::value;
+        // Pairs k0 .. k1 of the tile in chunks of kChunk (through s_perm when
+        // PERM), with the smoothed kernel or the far field's Laplace kernel
+        // (FAR), folded into the far sums or the near ones (TO_FAR).
+        auto run = [&](int k0, int k1, auto far_c, auto perm_c, bool to_far) {
+            constexpr bool FAR = decltype(far_c)::value;
+            constexpr bool PERM = decltype(perm_c)::value;
+            for (int c0 = k0; c0 < k1; c0 += kChunk) {
+                const int c1 = min(k1, c0 + kChunk);
+                float g[3] = {0.0f, 0.0f, 0.0f}, gn[3] = {0.0f, 0.0f, 0.0f};
+                float cph = 0.0f, cpl = 0.0f;   // this chunk's Phi, float-float
+                float cd = 0.0f;                // sigma(x) mode: sum of (nw . r) e^{-w}
 #pragma unroll 4
-                for (int s = c0 + lane; s < c1; s += SPL) {
+                for (int k = c0 + lane; k < c1; k += SPL) {
+                    const int s = PERM ? (int)s_perm[k] : k;
                     const float4 y0 = sp[s], n = sn[s], yl0 = sl[s], nl = snl[s];
                     // the pair's a: the source's, or the target's in sigma(x) mode
                     const float4 y = SIGX ? make_float4(y0.x, y0.y, y0.z, ta_h) : y0;
@@ -1356,40 +1473,83 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                         if constexpr (SIGX) cd = fmaf(dh, expf(-rh * y.w * y.w), cd);
                     }
                 }
-            };
-            if (far)
-                pairs(std::true_type{});
-            else
-                pairs(std::false_type{});
-            if constexpr (SIGX) {
-                if (!far) {
+                if constexpr (SIGX && !FAR) {
                     two_sum_acc(dsum_h, dsum_l, cd);
                     renorm(dsum_h, dsum_l);
                 }
-            }
-            // fold the chunk into the running float-float sums, renormalised
-            float nh_, nl_;
-            if (far) {
+                // fold the chunk into the running float-float sums, renormalised
+                float nh_, nl_;
+                if (to_far) {
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    two_sum_acc(fgh[c], fgl[c], g[c]);
-                    renorm(fgh[c], fgl[c]);
-                }
-                ff_add(fph, fpl, cph, cpl, nh_, nl_);
-                fph = nh_;
-                fpl = nl_;
-            } else {
+                    for (int c = 0; c < 3; c++) {
+                        two_sum_acc(fgh[c], fgl[c], g[c]);
+                        renorm(fgh[c], fgl[c]);
+                    }
+                    ff_add(fph, fpl, cph, cpl, nh_, nl_);
+                    fph = nh_;
+                    fpl = nl_;
+                } else {
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    float ah, al;
-                    ff_add(gh[c], gl[c], g[c], gn[c], ah, al);
-                    gh[c] = ah;
-                    gl[c] = al;
+                    for (int c = 0; c < 3; c++) {
+                        float ah, al;
+                        ff_add(gh[c], gl[c], g[c], gn[c], ah, al);
+                        gh[c] = ah;
+                        gl[c] = al;
+                    }
+                    ff_add(ph, pl, cph, cpl, nh_, nl_);
+                    ph = nh_;
+                    pl = nl_;
                 }
-                ff_add(ph, pl, cph, cpl, nh_, nl_);
-                ph = nh_;
-                pl = nl_;
             }
+        };
+        if (far) {
+            run(0, cnt, std::true_type{}, std::false_type{}, true);
+        } else if (!LSM_REACH_SPLIT_FF) {
+            pairs_near += valid && lane == 0 ? cnt : 0;
+            run(0, cnt, std::false_type{}, std::false_type{}, false);
+        } else {
+            // A near tile's sources beyond the cutoff from the whole target box
+            // take the Laplace pair, as in a far tile (Sec. 4.4's split is by
+            // distance); they stay in the near sums, which the near-only call
+            // recomputes.  Thread tid tests source tid (FP32 position against
+            // the box, with a 1e-3 margin), and s_perm lists the sources
+            // within reach first, each group in source order.
+            bool reach = false;
+            if (tid < cnt) {
+                const float4 y = sp[tid];
+                const float a = SIGX ? 0.70710678f / s_smax : y.w;
+                const float px = (float)bref[0] + (ch.x + y.x), py = (float)bref[1] + (ch.y + y.y),
+                            pz = (float)bref[2] + (ch.z + y.z);
+                const float gx = fmaxf(0.0f, fmaxf(s_bb[0] - px, px - s_bb[3]));
+                const float gy = fmaxf(0.0f, fmaxf(s_bb[1] - py, py - s_bb[4]));
+                const float gz = fmaxf(0.0f, fmaxf(s_bb[2] - pz, pz - s_bb[5]));
+                reach = !((gx * gx + gy * gy + gz * gz) * (2.0f * a * a) > A.cut2 * 1.001f);
+            }
+            const int wl = tid & 31, wp = tid >> 5;
+            const unsigned bn = __ballot_sync(0xffffffffu, tid < cnt && reach);
+            const unsigned bf = __ballot_sync(0xffffffffu, tid < cnt && !reach);
+            if (wl == 0) {
+                s_cnt[0][wp] = __popc(bn);
+                s_cnt[1][wp] = __popc(bf);
+            }
+            __syncthreads();
+            int nn = 0, pn = 0, pf = 0;
+#pragma unroll
+            for (int w = 0; w < kEvalThreads / 32; w++) {
+                nn += s_cnt[0][w];
+                if (w < wp) {
+                    pn += s_cnt[0][w];
+                    pf += s_cnt[1][w];
+                }
+            }
+            const unsigned below = (1u << wl) - 1u;
+            if (tid < cnt) s_perm[reach ? pn + __popc(bn & below) : nn + pf + __popc(bf & below)] = (unsigned char)tid;
+            __syncthreads();
+            // pairs counted by the kernel they take
+            pairs_near += valid && lane == 0 ? nn : 0;
+            pairs_far += valid && lane == 0 ? cnt - nn : 0;
+            run(0, nn, std::false_type{}, std::true_type{}, false);
+            run(nn, cnt, std::true_type{}, std::true_type{}, false);
         }
         __syncthreads();
     }
@@ -1608,7 +1768,12 @@ constexpr int kTPT64 = 1;
 
 int eval_init_constants(Ctx* ctx) { return upload_series_constants(ctx); }
 
-int mixed_tpt(const Mesh* me) { return me->tune_tpt == 1 && !me->sigx ? 1 : kTPT32; }
+int mixed_tpb(const Ctx* ctx, const Mesh* me)
+{
+    const int t = ctx->opt.mixed_block > 0 ? ctx->opt.mixed_block : me->tune_tpb;
+    if (!me->sigx && (t == 64 || t == kEvalThreads)) return t;
+    return kEvalThreads * kTPT32;
+}
 double mixed_cut(const Ctx* ctx, const Mesh* me) { return me->tune_cut > 0.0 ? me->tune_cut : ctx->opt.cutoff_mixed; }
 
 // Phi and grad at n sorted targets (SoA x with stride ld) into res [4][n]
@@ -1619,10 +1784,10 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     if (t.n <= 0) return LSM_OK;
     const bool mixed = precision == LSM_MIXED;
     const bool ff = precision == LSM_FF;
-    const int tpt = mixed ? mixed_tpt(me) : kTPT64;
-    // float-float CTAs of 64 targets (the option's default) outside sigma(x) mode
+    // targets per CTA: the mixed kernel's tuned layout (64, 128 or 256); the
+    // float-float kernel's 64 (the option's default) outside sigma(x) mode
     const bool ff64 = ff && !me->sigx && ctx->opt.ff_block == 64;
-    const int tpb = ff64 ? 64 : kEvalThreads * tpt;
+    const int tpb = mixed ? mixed_tpb(ctx, me) : (ff64 ? 64 : kEvalThreads * kTPT64);
     const int nblk = (t.n + tpb - 1) / tpb;
     const int ntiles = (int)me->ntiles;
     // split the tile range so that the grid covers the GPU a few times over
@@ -1734,7 +1899,10 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
             k_eval_ff<true><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
         else
             k_eval_fp64<kTPT64, true><<<grid, kEvalThreads, 0, st>>>(me->s64_pos, me->s64_nw, A);
-    } else if (mixed && tpt == 1) {
+    } else if (mixed && tpb == 64) {
+        k_eval_mixed<1, false, 2><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo,
+                                                                  A);
+    } else if (mixed && tpb == kEvalThreads) {
         k_eval_mixed<1, false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
     } else if (mixed) {
         k_eval_mixed<kTPT32, false><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
@@ -1768,7 +1936,10 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
             k_eval_ff<false, 64><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, G);
         else if (ff)
             k_eval_ff<false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, G);
-        else if (tpt == 1)
+        else if (tpb == 64)
+            k_eval_mixed<1, false, 2><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
+                                                                        me->s32_nwlo, G);
+        else if (tpb == kEvalThreads)
             k_eval_mixed<1, false><<<cp.ngblk, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
                                                                      me->s32_nwlo, G);
         else

@@ -152,10 +152,10 @@ struct Mesh {
     int tune_mode = -1;
     int tune_degree = 0;
     float tune_theta = 0.0f;
-    // and its near-field radius (in sigma) and targets per thread of the
-    // mixed kernel (0: the context's cutoff_mixed, two targets per thread)
+    // and its near-field radius (in sigma) and targets per CTA of the mixed
+    // kernel (64, 128 or 256; 0: the context's cutoff_mixed, 256)
     double tune_cut = 0.0;
-    int tune_tpt = 0;
+    int tune_tpb = 0;
     int64_t nv = 0, m = 0, ns = 0, ntiles = 0;
     int nq = 0;
     lsm_quad rule{4, 0};
@@ -370,7 +370,7 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
                int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc = nullptr,
                int tpt = 0, double cut = 0.0);
 // the mixed kernel's settings for a mesh: its autotuned ones, else the defaults
-int mixed_tpt(const Mesh* me);
+int mixed_tpb(const Ctx* ctx, const Mesh* me);   // targets per CTA of the mixed kernel on this mesh
 double mixed_cut(const Ctx* ctx, const Mesh* me);
 int eval_noalloc(Ctx* ctx, const Mesh* mesh, const double* x, int64_t n, double* phi, double* grad,
                  int precision, cudaStream_t st);

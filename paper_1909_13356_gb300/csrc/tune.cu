@@ -112,11 +112,11 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
         double ms, err;
     };
     std::vector<Meas> meas;
-    const int saved_mode = me->tune_mode, saved_deg = me->tune_degree, saved_tpt = me->tune_tpt;
+    const int saved_mode = me->tune_mode, saved_deg = me->tune_degree, saved_tpb = me->tune_tpb;
     const float saved_theta = me->tune_theta;
     const double saved_cut = me->tune_cut;
     me->tune_cut = 0.0;   // the far field is chosen at the default radius and tile
-    me->tune_tpt = 0;
+    me->tune_tpb = 0;
     for (const Candidate& c : kCandidates) {
         me->tune_mode = c.mode;
         me->tune_degree = c.degree;
@@ -143,7 +143,7 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
         me->tune_degree = saved_deg;
         me->tune_theta = saved_theta;
         me->tune_cut = saved_cut;
-        me->tune_tpt = saved_tpt;
+        me->tune_tpb = saved_tpb;
         return rc;
     }
     // fastest within the budget; else the most accurate
@@ -165,10 +165,10 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
     }
     // second stage, with that far field: the near-field radius (among the
     // values whose neglected kernel difference stays within the mixed path's
-    // bound, Sec. 4.4) and the targets per thread of the mixed kernel
+    // bound, Sec. 4.4) and the targets per CTA of the mixed kernel
     double best_ms = meas[best].ms, best_err = meas[best].err;
     double best_cut = 0.0;
-    int best_tpt = 0;
+    int best_tpb = 0;
     int stage2 = 0;
     {
         cudaEvent_t f0, f1;
@@ -176,10 +176,10 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
         LSM_CUDA_TRY(ctx, cudaEventCreate(&f1));
         for (double cut : kCutCandidates) {
             if (cutoff_bound(cut) > kCutBound) continue;
-            for (int tpt : {1, 2}) {
-                if (tpt == 1 && me->sigx) continue;
+            for (int tpb : {64, kEvalThreads, 2 * kEvalThreads}) {
+                if (tpb < 2 * kEvalThreads && me->sigx) continue;
                 me->tune_cut = cut;
-                me->tune_tpt = tpt;
+                me->tune_tpb = tpb;
                 rc = eval_sorted(ctx, me, ts, R, LSM_MIXED, st);   // warm: lists and launch shapes
                 if (rc == LSM_OK) {
                     cudaEventRecord(f0, st);
@@ -196,7 +196,7 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
                     best_ms = ms;
                     best_err = err;
                     best_cut = cut;
-                    best_tpt = tpt;
+                    best_tpb = tpb;
                 }
             }
             if (rc != LSM_OK) break;
@@ -206,7 +206,7 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
         if (rc != LSM_OK) return rc;
     }
     me->tune_cut = best_cut;
-    me->tune_tpt = best_tpt;
+    me->tune_tpb = best_tpb;
     if (res) {
         res->use_tree = c.mode;
         res->tree_degree = c.degree;
@@ -218,7 +218,7 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
         res->ms_direct = meas[0].ms;
         res->err_direct = meas[0].err;
         res->cutoff = mixed_cut(ctx, me);
-        res->targets_per_block = kEvalThreads * mixed_tpt(me);
+        res->targets_per_block = mixed_tpb(ctx, me);
     }
     return LSM_OK;
 }

@@ -78,7 +78,9 @@ def test_options_struct_matches_header_layout():
     fields = re.findall(r"\b(double|float|int32_t)\s+(\w+)\s*;", body)
     ctypes_of = {"double": ctypes.c_double, "float": ctypes.c_float, "int32_t": ctypes.c_int32}
     assert [(n, ctypes_of[t]) for t, n in fields] == list(lsm._Options._fields_)
-    assert ctypes.sizeof(lsm._Options) == sum(ctypes.sizeof(ctypes_of[t]) for t, _ in fields)
+    size = sum(ctypes.sizeof(ctypes_of[t]) for t, _ in fields)
+    assert size % 8 == 0   # no tail padding: the same size under any packing
+    assert ctypes.sizeof(lsm._Options) == size
 
 
 def test_refined_nodes_match_the_oracle_rule(oracle_mod):
@@ -100,7 +102,8 @@ def test_out_of_range_options_are_rejected_before_any_device_call():
     returns LSM_E_INVALID_ARG (-1), with or without a GPU."""
     L = lsm.load()
     for field, value in (("tree_grid", 3), ("tree_grid", -1), ("tree_degree", 13), ("tree_theta", 1.0),
-                         ("tree_ff_degree", 17), ("tree_min_sources", -2)):
+                         ("tree_ff_degree", 17), ("tree_min_sources", -2), ("ff_block", 96),
+                         ("mixed_block", 32)):
         opt = lsm._Options()
         setattr(opt, field, value)
         h = ctypes.c_void_p()

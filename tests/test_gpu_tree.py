@@ -179,7 +179,7 @@ def test_autotune_choice_within_budget(lsm, oracle_mod):
     assert r["ms_sample"] <= r["ms_direct"] * 1.05
     # second stage: the near-field radius (within the mixed bound) and the target tile
     assert min(abs(r["cutoff"] - c) for c in (6.4, 6.5, 7.0)) < 1e-12
-    assert r["targets_per_block"] in (128, 256)
+    assert r["targets_per_block"] in (64, 128, 256)
     phi, grad = _eval(lsm, ctx, mesh, w["targets"])
     y, nw, sg = oracle_mod.sources(m.verts, m.tris, m.sigma, 6, 0)
     sel = np.random.default_rng(5).choice(len(w["targets"]), 400, replace=False)
@@ -227,6 +227,30 @@ def test_ff_tree_dense_against_direct(lsm):
     assert np.abs(gt - gd).max() <= TOL32 / m.sigma.min()
     assert st_t["pairs_near"] == st_d["pairs_near"]
     assert st_t["pairs_far"] < st_d["pairs_far"]
+
+
+def test_mixed_block_layouts(lsm, torus_case):
+    """The mixed kernel with 64 targets per CTA (two threads per target, each
+    taking every other pair of sources), 128 (one thread, two sources per
+    packed lane pair) and 256 (two targets per thread in the packed lanes):
+    all within the mixed bar of the oracle, and smaller target boxes put
+    fewer pairs in the near field."""
+    w = torus_case["w"]
+    m = w["mesh"]
+    near = {}
+    for blk in (64, 128, 256):
+        ctx = lsm.Context(0, mixed_block=blk, tree_degree=8, tree_theta=0.5)
+        mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=6)
+        _eval(lsm, ctx, mesh, w["targets"][:4096])    # builds the tree
+        ctx.read_stats(reset=True)
+        phi, grad = _eval(lsm, ctx, mesh, w["targets"])
+        st = ctx.read_stats(reset=True)
+        assert np.abs(phi - torus_case["phi"]).max() <= TOL32, blk
+        assert np.abs(grad - torus_case["grad"]).max() <= TOL32 / m.sigma.min(), blk
+        near[blk] = st["pairs_near"]
+    assert near[64] < near[128] < near[256], near
+    with pytest.raises(lsm.LsmError):
+        lsm.Context(0, mixed_block=32)
 
 
 def test_ff_block_sizes(lsm, torus_case):
