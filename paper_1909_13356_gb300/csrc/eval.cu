@@ -44,9 +44,12 @@
 #define LSM_RSQRT_REFINE 1
 #endif
 // near tiles: sources beyond the cutoff from the whole target box take the
-// Laplace pair (float-float kernel, mixed kernel)
+// Laplace pair.  On in the mixed kernel (its near pair costs about five far
+// pairs: -7% on the torus bench step's mixed launches); off in the float-float
+// kernel, where the two pairs cost nearly the same and the tile's
+// classification cost more than it saved (+1.7% per launch).
 #ifndef LSM_REACH_SPLIT_FF
-#define LSM_REACH_SPLIT_FF 1
+#define LSM_REACH_SPLIT_FF 0
 #endif
 #ifndef LSM_REACH_SPLIT_MIXED
 #define LSM_REACH_SPLIT_MIXED 1
