@@ -742,7 +742,31 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
             } else if constexpr (TPT == 1) {
                 // one target per thread: two consecutive sources ride in the
                 // two lanes (an odd tail pairs the last source with a zero
-                // weight), and the lanes are added before each chunk's fold
+                // weight), and the lanes are added before each chunk's fold.
+                // The tile is first rewritten pair-interleaved and negated into
+                // this stage's low-part buffers (idle for a far tile): -y and
+                // -nw, three planes of 128 floats each, so that every packed
+                // operand is one 64-bit shared load with no lane assembly.
+                float* tpos = reinterpret_cast<float*>(&sh_lo[b][0]);
+                float* tnw = reinterpret_cast<float*>(&sh_nl[b][0]);
+                if (tid < ((cnt + 1) & ~1)) {
+                    const int s = min(tid, cnt - 1);
+                    const float4 y = sp[s];
+                    const float4 n = tid < cnt ? sn[s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    tpos[tid] = -y.x;
+                    tpos[kTile + tid] = -y.y;
+                    tpos[2 * kTile + tid] = -y.z;
+                    tnw[tid] = -n.x;
+                    tnw[kTile + tid] = -n.y;
+                    tnw[2 * kTile + tid] = -n.z;
+                }
+                __syncthreads();
+                const float2* PX = reinterpret_cast<const float2*>(tpos);
+                const float2* PY = PX + kTile / 2;
+                const float2* PZ = PX + kTile;
+                const float2* MX = reinterpret_cast<const float2*>(tnw);
+                const float2* MY = MX + kTile / 2;
+                const float2* MZ = MX + kTile;
                 const float2 qx = make_float2(xq[0][0], xq[0][0]);
                 const float2 qy = make_float2(xq[0][1], xq[0][1]);
                 const float2 qz = make_float2(xq[0][2], xq[0][2]);
@@ -750,11 +774,16 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                 const float2 p3 = make_float2(3.0f, 3.0f), m1 = make_float2(-1.0f, -1.0f);
                 for (int c0 = 0; c0 < cnt; c0 += kChunk) {
                     const int c1 = min(cnt, c0 + kChunk);
-                    float2 P0 = make_float2(0.0f, 0.0f), P1 = P0, P2 = P0, P3 = P0;
-                    auto step = [&](const float4& ya, const float4& yb, const float4& na, const float4& nb) {
-                        const float2 ndx = __fadd2_rn(qx, make_float2(-ya.x, -yb.x));
-                        const float2 ndy = __fadd2_rn(qy, make_float2(-ya.y, -yb.y));
-                        const float2 ndz = __fadd2_rn(qz, make_float2(-ya.z, -yb.z));
+                    // P0 = Phi; grad = P - R (P: -nw/|r|^3 terms, R: the 3 (nw . r) r/|r|^5 terms negated)
+                    float2 P0 = make_float2(0.0f, 0.0f), P1 = P0, P2 = P0, P3 = P0, R1 = P0, R2 = P0, R3 = P0;
+                    const int k0 = c0 >> 1, npair = (c1 - c0 + 1) >> 1;
+#pragma unroll 2
+                    for (int q = lane; q < npair; q += SPL) {
+                        const int k = k0 + q;
+                        const float2 mx = MX[k], my = MY[k], mz = MZ[k];
+                        const float2 ndx = __fadd2_rn(qx, PX[k]);   // x - y
+                        const float2 ndy = __fadd2_rn(qy, PY[k]);
+                        const float2 ndz = __fadd2_rn(qz, PZ[k]);
                         const float2 r2 = __ffma2_rn(ndx, ndx, __ffma2_rn(ndy, ndy, __fmul2_rn(ndz, ndz)));
                         float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
 #if LSM_RSQRT_REFINE
@@ -764,30 +793,21 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
 #endif
                         const float2 ri2 = __fmul2_rn(ri, ri);
                         const float2 ri3 = __fmul2_rn(ri2, ri);
-                        const float2 nx = make_float2(na.x, nb.x), ny = make_float2(na.y, nb.y),
-                                     nz = make_float2(na.z, nb.z);
-                        const float2 dneg = __ffma2_rn(nx, ndx, __ffma2_rn(ny, ndy, __fmul2_rn(nz, ndz)));
-                        const float2 qn = __fmul2_rn(dneg, ri3);          // -(nw . r)/|r|^3
-                        P0 = __fadd2_rn(P0, qn);                          // -Phi
-                        const float2 tq = __fmul2_rn(qn, __fmul2_rn(ri2, p3));
-                        const float2 mnx = make_float2(-na.x, -nb.x), mny = make_float2(-na.y, -nb.y),
-                                     mnz = make_float2(-na.z, -nb.z);
-                        P1 = __ffma2_rn(tq, ndx, __ffma2_rn(mnx, ri3, P1));
-                        P2 = __ffma2_rn(tq, ndy, __ffma2_rn(mny, ri3, P2));
-                        P3 = __ffma2_rn(tq, ndz, __ffma2_rn(mnz, ri3, P3));
-                    };
-                    const int npair = (c1 - c0) >> 1;
-#pragma unroll 2
-                    for (int q = lane; q < npair; q += SPL) {
-                        const int s = c0 + 2 * q;
-                        step(sp[s], sp[s + 1], sn[s], sn[s + 1]);
+                        const float2 dn = __ffma2_rn(mx, ndx, __ffma2_rn(my, ndy, __fmul2_rn(mz, ndz)));   // nw . r
+                        const float2 sv = __fmul2_rn(dn, ri3);            // (nw . r)/|r|^3
+                        P0 = __fadd2_rn(P0, sv);
+                        const float2 tq = __fmul2_rn(sv, __fmul2_rn(ri2, p3));
+                        R1 = __ffma2_rn(tq, ndx, R1);
+                        R2 = __ffma2_rn(tq, ndy, R2);
+                        R3 = __ffma2_rn(tq, ndz, R3);
+                        P1 = __ffma2_rn(mx, ri3, P1);
+                        P2 = __ffma2_rn(my, ri3, P2);
+                        P3 = __ffma2_rn(mz, ri3, P3);
                     }
-                    if (((c1 - c0) & 1) && lane == npair % SPL)
-                        step(sp[c1 - 1], sp[c1 - 1], sn[c1 - 1], make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-                    two_sum_acc(acc_h[0][0], acc_l[0][0], -(P0.x + P0.y));
-                    two_sum_acc(acc_h[0][1], acc_l[0][1], P1.x + P1.y);
-                    two_sum_acc(acc_h[0][2], acc_l[0][2], P2.x + P2.y);
-                    two_sum_acc(acc_h[0][3], acc_l[0][3], P3.x + P3.y);
+                    two_sum_acc(acc_h[0][0], acc_l[0][0], P0.x + P0.y);
+                    two_sum_acc(acc_h[0][1], acc_l[0][1], (P1.x + P1.y) - (R1.x + R1.y));
+                    two_sum_acc(acc_h[0][2], acc_l[0][2], (P2.x + P2.y) - (R2.x + R2.y));
+                    two_sum_acc(acc_h[0][3], acc_l[0][3], (P3.x + P3.y) - (R3.x + R3.y));
                 }
             } else
 #endif
