@@ -535,6 +535,65 @@ __device__ __forceinline__ void ff_far_pair(const float4& y, const float4& n, co
     ri3 = fHh;
 }
 
+// The far pair when the tile's source offsets and the target's offset have
+// been re-split on a common grid (the high parts multiples of one power of two
+// 2^k, all below 2^(k+23) in magnitude): the high parts' difference is then
+// exact, and the low parts' difference is one addition.  The low part can then
+// be as large as 2^(k-1), far above the high part's rounding unit when the
+// pair is much closer than the grid's range, and the first-order steps below
+// drop its square, so the pair is renormalised (a fast two-sum: the far pair's
+// high part dominates).  Four operations per component instead of eight; the
+// rest is ff_far_pair.
+__device__ __forceinline__ void ff_far_pair_grid(const float4& y, const float4& n, const float4& yl,
+                                                 const float4& nl, const float* qh, const float* ql, float& qhi,
+                                                 float& qlo, float& dxh, float& dyh, float& dzh, float& dh,
+                                                 float& ri2, float& ri3)
+{
+    float dxl, dyl, dzl;
+    {
+        const float hx = y.x - qh[0], hy = y.y - qh[1], hz = y.z - qh[2];
+        const float lx = yl.x - ql[0], ly = yl.y - ql[1], lz = yl.z - ql[2];
+        dxh = hx + lx;
+        dyh = hy + ly;
+        dzh = hz + lz;
+        dxl = lx - (dxh - hx);
+        dyl = ly - (dyh - hy);
+        dzl = lz - (dzh - hz);
+    }
+    const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
+    float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
+    e0 = fmaf(2.0f * dxh, dxl, e0);
+    e1 = fmaf(2.0f * dyh, dyl, e1);
+    e2 = fmaf(2.0f * dzh, dzl, e2);
+    float s01, t01, t2, rh;
+    two_sum(p0, p1, s01, t01);
+    two_sum(s01, p2, rh, t2);
+    const float rl = ((e0 + e1) + e2) + (t01 + t2);
+    const float r0 = rsqrtf(rh);
+    const float t = rh * r0;
+    const float te = fmaf(rh, r0, -t);
+    const float u = fmaf(rl, r0, te);
+    const float delta = fmaf(-u, r0, fmaf(-t, r0, 1.0f));
+    const float a = r0 * r0, ae = fmaf(r0, r0, -a);
+    const float fHh = a * r0;
+    const float c3l = fmaf(ae, r0, fmaf(a, r0, -fHh));
+    const float fHl = fmaf(fHh, delta * fmaf(1.875f, delta, 1.5f), c3l);
+    const float d0 = n.x * dxh, d1 = n.y * dyh, d2 = n.z * dzh;
+    const float f0 = fmaf(n.x, dxh, -d0), f1 = fmaf(n.y, dyh, -d1), f2 = fmaf(n.z, dzh, -d2);
+    float sd, u1, u2;
+    two_sum(d0, d1, sd, u1);
+    two_sum(sd, d2, dh, u2);
+    const float dl = fmaf(n.x, dxl, fmaf(n.y, dyl, fmaf(n.z, dzl, fmaf(nl.x, dxh, fmaf(nl.y, dyh,
+                     fmaf(nl.z, dzh, ((f0 + f1) + f2) + (u1 + u2)))))));
+    ff_mul(dh, dl, fHh, fHl, qhi, qlo);
+    ri2 = a;
+    ri3 = fHh;
+}
+
+// Round v to a multiple of 2^k given c = 3 * 2^(k+22) and |v| < 2^(k+22):
+// v + c lies in [2^(k+23), 2^(k+24)), where the float spacing is 2^k.
+__device__ __forceinline__ float round_to_grid(float v, float c) { return (v + c) - c; }
+
 // ---------------------------------------------------------------- mixed kernel
 template <int TPT, bool SIGX, int SPL = 1>
 __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __restrict__ spos,
@@ -1401,7 +1460,23 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         const double d0 = ((double)ch.x - bref[0]) + (double)cl.x, d1 = ((double)ch.y - bref[1]) + (double)cl.y,
                      d2 = ((double)ch.z - bref[2]) + (double)cl.z;
         const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
-        s_dref[b][0] = make_float4(h0, h1, h2, 0.0f);
+        // far tiles re-split the offsets on a grid of spacing 2^k (see
+        // ff_far_pair_grid): Q bounds every component of the targets' offsets
+        // from the tile centre (block box) and of the tile's own offsets (tile
+        // box), 2^(k+22) >= Q, and c = 3 * 2^(k+22)
+        float Q = 0.0f;
+        {
+            const float4 tlo = A.tlo[t], thi = A.thi[t];
+            const float cx[3] = {ch.x, ch.y, ch.z}, lo_t[3] = {tlo.x, tlo.y, tlo.z}, hi_t[3] = {thi.x, thi.y, thi.z};
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                Q = fmaxf(Q, fmaxf(fabsf(s_bb[c] - cx[c]), fabsf(s_bb[3 + c] - cx[c])));
+                Q = fmaxf(Q, fmaxf(fabsf(lo_t[c] - cx[c]), fabsf(hi_t[c] - cx[c])));
+            }
+        }
+        int ex;
+        frexpf(fmaxf(Q * 1.0625f, 1e-30f), &ex);   // Q * 1.0625 < 2^ex
+        s_dref[b][0] = make_float4(h0, h1, h2, ldexpf(3.0f, ex));
         s_dref[b][1] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1), (float)(d2 - (double)h2), 0.0f);
         mbar_expect_tx(&bar[b], 4u * by);
         if (arm_only) return;
@@ -1422,14 +1497,25 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
         const int b = it & 1;
         if (tid == 0 && it + 1 < nlist) issue(tile_at(it + 1), b ^ 1, false);
         const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), A.wait_limit);
+        const int cnt = (int)A.thi[t].w;
+        const bool far =
+            t >= A.ntiles || tile_is_far(s_bb, SIGX ? with_sigma(A.tlo[t], s_smax) : A.tlo[t], A.thi[t], A.cut2);
+        if (ok && far && !scan && tid < cnt) {
+            // this thread's source of a far tile, re-split on the tile's grid
+            // (its copy has landed: the thread's own wait succeeded)
+            float4* py = reinterpret_cast<float4*>(sh[b]);
+            float4* pl = py + 2 * kTile;
+            const float gc = s_dref[b][0].w;
+            const float4 yh = py[tid], yl = pl[tid];
+            const float hx = round_to_grid(yh.x, gc), hy = round_to_grid(yh.y, gc), hz = round_to_grid(yh.z, gc);
+            py[tid] = make_float4(hx, hy, hz, yh.w);
+            pl[tid] = make_float4((yh.x - hx) + yl.x, (yh.y - hy) + yl.y, (yh.z - hz) + yl.z, yl.w);
+        }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) give_up(A, bar, b, it, it + 1 < nlist);
             failed = true;
             break;
         }
-        const int cnt = (int)A.thi[t].w;
-        const bool far =
-            t >= A.ntiles || tile_is_far(s_bb, SIGX ? with_sigma(A.tlo[t], s_smax) : A.tlo[t], A.thi[t], A.cut2);
         if (scan && far) {   // near-only call walking its whole range: the far part is the recorded one
             __syncthreads();
             continue;
@@ -1445,6 +1531,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             const float tt = (xl[c] - cc2[c]) + e0;
             qh[c] = s0 + tt;
             ql[c] = tt - (qh[c] - s0);
+            if (far) {   // the target's offset on the tile's grid, as the sources'
+                const float h = round_to_grid(qh[c], ch.w);
+                ql[c] = (qh[c] - h) + ql[c];
+                qh[c] = h;
+            }
         }
         const float4* sp = reinterpret_cast<const float4*>(sh[b]);
         const float4* sn = sp + kTile;
@@ -1471,7 +1562,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
                     float qh_, ql_, dxh, dyh, dzh, rh, dh;
                     if constexpr (FAR) {
                         float ri2, ri3;
-                        ff_far_pair(y, n, yl, nl, qh, ql, qh_, ql_, dxh, dyh, dzh, dh, ri2, ri3);
+                        // far tiles are on the grid; far sources of a near tile are not
+                        if constexpr (PERM)
+                            ff_far_pair(y, n, yl, nl, qh, ql, qh_, ql_, dxh, dyh, dzh, dh, ri2, ri3);
+                        else
+                            ff_far_pair_grid(y, n, yl, nl, qh, ql, qh_, ql_, dxh, dyh, dzh, dh, ri2, ri3);
                         float sph, tph;
                         two_sum(cph, qh_, sph, tph);
                         cph = sph;
