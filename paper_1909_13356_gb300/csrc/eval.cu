@@ -723,13 +723,16 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         const int it = j - t0;
         const int b = it & 1;
         const int t = tile_at(j);
-        if (tid == 0 && j + 1 < t1) issue(tile_at(j + 1), b ^ 1, false);
         const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), A.wait_limit);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) give_up(A, bar, b, it, j + 1 < t1);
+            if (tid == 0) give_up(A, bar, b, it, false);
             failed = true;
             break;
         }
+        // past this barrier every thread has finished the previous tile, so
+        // its stage (b ^ 1) takes the next tile's copy, which lands while this
+        // tile is computed (one barrier per tile)
+        if (tid == 0 && j + 1 < t1) issue(tile_at(j + 1), b ^ 1, false);
         const float4 tl = A.tlo[t], th = A.thi[t];
         const float4 ch = A.tchi[t], cl = A.tclo[t];
         const int cnt = (int)A.thi[t].w;
@@ -1045,11 +1048,12 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
         for (int k = 0; k < TPT; k++)
 #pragma unroll
             for (int c = 0; c < 4; c++) renorm(acc_h[k][c], acc_l[k][c]);
-        __syncthreads();
     }
     if constexpr (SPL == 2) {
         // the second thread's sums join the first's, through the stage buffer
-        // (idle: every copy has been waited for unless a stage was lost)
+        // (idle once every thread is past the last tile: every copy has been
+        // waited for unless a stage was lost)
+        __syncthreads();
         if (!failed) {
             float* xch = reinterpret_cast<float*>(&sh_pos[0][0]);   // both stages: 1,024 floats
             if (lane == 1) {
@@ -1495,7 +1499,6 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
     for (int it = 0; it < nlist; it++) {
         const int t = tile_at(it);
         const int b = it & 1;
-        if (tid == 0 && it + 1 < nlist) issue(tile_at(it + 1), b ^ 1, false);
         const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), A.wait_limit);
         const int cnt = (int)A.thi[t].w;
         const bool far =
@@ -1512,14 +1515,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             pl[tid] = make_float4((yh.x - hx) + yl.x, (yh.y - hy) + yl.y, (yh.z - hz) + yl.z, yl.w);
         }
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) give_up(A, bar, b, it, it + 1 < nlist);
+            if (tid == 0) give_up(A, bar, b, it, false);
             failed = true;
             break;
         }
-        if (scan && far) {   // near-only call walking its whole range: the far part is the recorded one
-            __syncthreads();
-            continue;
-        }
+        // past this barrier every thread has finished the previous tile, so
+        // its stage (b ^ 1) takes the next tile's copy, which lands while this
+        // tile is computed (one barrier per tile)
+        if (tid == 0 && it + 1 < nlist) issue(tile_at(it + 1), b ^ 1, false);
+        if (scan && far) continue;   // near-only call walking its whole range: the far part is the recorded one
         if (far) pairs_far += valid && lane == 0 ? cnt : 0;
         const float4 ch = s_dref[b][0], cl = s_dref[b][1];
         const float cc[3] = {ch.x, ch.y, ch.z}, cc2[3] = {cl.x, cl.y, cl.z};
@@ -1669,11 +1673,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_ff(
             run(0, nn, std::false_type{}, std::true_type{}, false);
             run(nn, cnt, std::true_type{}, std::true_type{}, false);
         }
-        __syncthreads();
     }
     if constexpr (SPL == 2) {
         // the second lane's partial sums join the first's, through the stage
-        // buffers (idle: every copy has been waited for unless a stage was lost)
+        // buffers (idle once every thread is past the last tile: every copy
+        // has been waited for unless a stage was lost)
+        __syncthreads();
         if (!failed) {
             float* xch = reinterpret_cast<float*>(sh[0]);
             const int k = tid % TPB;
