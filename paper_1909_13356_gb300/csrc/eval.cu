@@ -329,8 +329,8 @@ __device__ __forceinline__ void count_pairs(unsigned long long* dst, unsigned lo
 }
 
 // A stage's copy did not complete within the wait limit: record the error in
-// the device word and wait (bounded again) for both stages, the lost one and
-// the prefetched next one (when `next` was issued), so that no bulk copy is
+// the device word and wait (bounded again) for the lost stage and, when
+// `next` was issued, the prefetched next one, so that no bulk copy is
 // still writing into shared memory when the CTA exits.  Called by thread 0.
 __device__ __forceinline__ void give_up(const EvalArgs& A, uint64_t* bar, int b, int it, bool next)
 {
@@ -355,6 +355,15 @@ __device__ __forceinline__ void two_diff(float a, float b, float& s, float& e)
     e = (a - (s - bb)) - (b + bb);
 }
 
+
+// two_sum for a, b >= 0: the larger first makes Dekker's fast two-sum exact;
+// the ordering runs on the ALU pipe, the sum on three FP32 additions
+__device__ __forceinline__ void two_sum_nonneg(float a, float b, float& s, float& e)
+{
+    const float hi = fmaxf(a, b), lo = fminf(a, b);
+    s = hi + lo;
+    e = lo - (s - hi);
+}
 
 // ff product of (ah, al) and (bh, bl)
 __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& h, float& l)
@@ -398,15 +407,15 @@ __device__ __forceinline__ void ff_pair(const float4& y, const float4& n, const 
     dyl = e + (yl.y - ql[1]);
     two_diff(y.z, qh[2], dzh, e);
     dzl = e + (yl.z - ql[2]);
+    // |r|^2 as in ff_far_pair_grid: squares' errors, non-negative two-sums,
+    // the cross terms summed in FP32
     const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
-    float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
-    e0 = fmaf(2.0f * dxh, dxl, e0);
-    e1 = fmaf(2.0f * dyh, dyl, e1);
-    e2 = fmaf(2.0f * dzh, dzl, e2);
+    const float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
+    const float cr = fmaf(dxh, dxl, fmaf(dyh, dyl, dzh * dzl));
     float s01, t01, t2;
-    two_sum(p0, p1, s01, t01);
-    two_sum(s01, p2, rh, t2);
-    const float rl = ((e0 + e1) + e2) + (t01 + t2);
+    two_sum_nonneg(p0, p1, s01, t01);
+    two_sum_nonneg(s01, p2, rh, t2);
+    const float rl = fmaf(2.0f, cr, ((e0 + e1) + e2) + (t01 + t2));
     float fHh, fHl;
     float wh = 0.0f, aah = 0.0f, aal = 0.0f;
     r0 = 0.0f;
@@ -560,15 +569,15 @@ __device__ __forceinline__ void ff_far_pair_grid(const float4& y, const float4& 
         dyl = ly - (dyh - hy);
         dzl = lz - (dzh - hz);
     }
+    // |r|^2: the squares' rounding errors, their sum (non-negative terms),
+    // and the cross terms 2 r_hi . r_lo summed in FP32 (2^-23 of |r|^2)
     const float p0 = dxh * dxh, p1 = dyh * dyh, p2 = dzh * dzh;
-    float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
-    e0 = fmaf(2.0f * dxh, dxl, e0);
-    e1 = fmaf(2.0f * dyh, dyl, e1);
-    e2 = fmaf(2.0f * dzh, dzl, e2);
+    const float e0 = fmaf(dxh, dxh, -p0), e1 = fmaf(dyh, dyh, -p1), e2 = fmaf(dzh, dzh, -p2);
+    const float cr = fmaf(dxh, dxl, fmaf(dyh, dyl, dzh * dzl));
     float s01, t01, t2, rh;
-    two_sum(p0, p1, s01, t01);
-    two_sum(s01, p2, rh, t2);
-    const float rl = ((e0 + e1) + e2) + (t01 + t2);
+    two_sum_nonneg(p0, p1, s01, t01);
+    two_sum_nonneg(s01, p2, rh, t2);
+    const float rl = fmaf(2.0f, cr, ((e0 + e1) + e2) + (t01 + t2));
     const float r0 = rsqrtf(rh);
     const float t = rh * r0;
     const float te = fmaf(rh, r0, -t);
