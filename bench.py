@@ -592,6 +592,28 @@ def _peak_fp32(peaks):
     return max(peaks["ffma_tflops"], peaks["ffma2_tflops"])
 
 
+# DRAM bytes per launch of a pair kernel on the bench step, from a one-pass ncu
+# capture of that step (dram__bytes_read.sum + dram__bytes_write.sum over the
+# timed step's launches, divided by the launches the library times), kept with
+# the SHA-256 of the kernel source it was taken on: a changed kernel reports
+# null until it is captured again.
+DRAM_FILE = os.path.join(ROOT, "paper_1909_13356_gb300", "ncu_dram.json")
+
+
+def _dram_traffic(kernel: str):
+    import hashlib
+    try:
+        with open(DRAM_FILE) as f:
+            rec = json.load(f).get(kernel)
+        with open(os.path.join(ROOT, "paper_1909_13356_gb300", "csrc", "eval.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None, None
+    if not rec or rec.get("eval_cu_sha256") != sha:
+        return None, None
+    return rec["dram_bytes_per_launch"], rec["summary"]
+
+
 def _kernel_rooflines(stats, peaks, step_ms_total, kinds=(0, 1, 2)):
     """Rooflines of the pair kernels timed per launch by the library: counted
     algorithmic flops (FLOPS_FAR_PAIR per far pair, FLOPS_NEAR_PAIR per near
@@ -609,9 +631,11 @@ def _kernel_rooflines(stats, peaks, step_ms_total, kinds=(0, 1, 2)):
         fl = far * FLOPS_FAR_PAIR + near * FLOPS_NEAR_PAIR
         pk = _peak_fp32(peaks) if k < 2 else peaks["dfma_tflops"]
         ach = fl / (ms_k / 1e3) / 1e12
+        traffic, tsrc = _dram_traffic(names[k])
         kern[names[k]] = {
             "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-            "traffic": None, "launches": stats["kind_launches"][k],
+            "traffic": traffic, "traffic_unit": "bytes per launch (DRAM read + write)",
+            "traffic_source": tsrc, "launches": stats["kind_launches"][k],
             "avg_launch_ms": ms_k / max(1, stats["kind_launches"][k]),
             "pairs_far": far, "pairs_near": near,
             "share_of_step": ms_k / step_ms_total if step_ms_total else None,
