@@ -595,21 +595,30 @@ def _peak_fp32(peaks):
 # DRAM bytes per launch of a pair kernel on the bench step, from a one-pass ncu
 # capture of that step (dram__bytes_read.sum + dram__bytes_write.sum over the
 # timed step's launches, divided by the launches the library times), kept with
-# the SHA-256 of the kernel source it was taken on: a changed kernel reports
-# null until it is captured again.
+# the SHA-256 of the sources that decide it (the pair kernels and the
+# interaction lists with their launch order): a change there reports null
+# until the step is captured again.
 DRAM_FILE = os.path.join(ROOT, "paper_1909_13356_gb300", "ncu_dram.json")
+DRAM_SOURCES = ("eval.cu", "tree.cu")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in DRAM_SOURCES:
+        with open(os.path.join(ROOT, "paper_1909_13356_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def _dram_traffic(kernel: str):
-    import hashlib
     try:
         with open(DRAM_FILE) as f:
             rec = json.load(f).get(kernel)
-        with open(os.path.join(ROOT, "paper_1909_13356_gb300", "csrc", "eval.cu"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        sha = kernel_sources_sha256()
     except (OSError, ValueError):
         return None, None
-    if not rec or rec.get("eval_cu_sha256") != sha:
+    if not rec or rec.get("sources_sha256") != sha:
         return None, None
     return rec["dram_bytes_per_launch"], rec["summary"]
 

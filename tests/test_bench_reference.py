@@ -45,21 +45,25 @@ def test_product_arm_fails_without_a_gpu():
 
 def test_dram_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     """The roofline's DRAM traffic comes from a recorded ncu capture only while
-    the kernel source it was taken on is unchanged (its SHA-256 matches)."""
+    the sources it was taken on are unchanged (their SHA-256 matches)."""
     import hashlib
     import importlib.util
     spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
-    with open(os.path.join(ROOT, "paper_1909_13356_gb300", "csrc", "eval.cu"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
-    rec = {"k_eval_ff": {"dram_bytes_per_launch": 1234.0, "eval_cu_sha256": sha, "summary": "profiles/x.md"}}
+    h = hashlib.sha256()
+    for name in ("eval.cu", "tree.cu"):
+        with open(os.path.join(ROOT, "paper_1909_13356_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    sha = h.hexdigest()
+    assert bench.kernel_sources_sha256() == sha
+    rec = {"k_eval_ff": {"dram_bytes_per_launch": 1234.0, "sources_sha256": sha, "summary": "profiles/x.md"}}
     path = tmp_path / "dram.json"
     path.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "DRAM_FILE", str(path))
     assert bench._dram_traffic("k_eval_ff") == (1234.0, "profiles/x.md")
     assert bench._dram_traffic("k_eval_mixed") == (None, None)
-    rec["k_eval_ff"]["eval_cu_sha256"] = "0" * 64
+    rec["k_eval_ff"]["sources_sha256"] = "0" * 64
     path.write_text(json.dumps(rec))
     assert bench._dram_traffic("k_eval_ff") == (None, None)
     monkeypatch.setattr(bench, "DRAM_FILE", str(tmp_path / "missing.json"))
