@@ -154,8 +154,8 @@ typedef struct {
      * batches always use 128. */
     int32_t ff_block;
     /* Targets per CTA of the mixed kernel (64, 128 or 256; 0: the mesh's
-     * autotuned choice, else 256).  A nonzero value overrides the
-     * autotuner's; sigma(x) mode always uses 256. */
+     * or the batch's autotuned choice, else 64).  A nonzero value
+     * overrides the autotuner's; sigma(x) mode always uses 256. */
     int32_t mixed_block;
     int32_t reserved;   /* keeps the size a multiple of 8 without padding; set 0 */
 } lsm_options;
@@ -562,7 +562,7 @@ int lsm_batch_solve_charts(lsm_batch* batch, int order, double tol, int max_iter
 /*
  * Autotuner of a batch (this library's addition, as lsm_autotune): chooses
  * the mixed kernel's near-field radius (6.4, 6.5 or 7 sigma, as
- * lsm_autotune) and target tile (128 or 256 targets per thread block) for the
+ * lsm_autotune) and target tile (64, 128 or 256 targets per work item) for the
  * batch's later lsm_batch_solve_charts calls: the fastest within err_budget
  * of the float-float evaluation, measured on the chart nodes' starting
  * points of every stride-th mesh (about 64 meshes), in the work items the

@@ -278,7 +278,7 @@ class Context:
         the same for the mixed treecode (0 or -1: off, the default).  ff_block:
         targets per CTA of the float-float kernel (64, the default, or 128).
         mixed_block: targets per CTA of the mixed kernel (64, 128 or 256; 0:
-        the autotuner's choice, else 256)."""
+        the autotuner's choice, else 64)."""
         self._L = load()
         opt = _Options(cutoff_fp64, cutoff_mixed, mixed_switch, mixed_accept, int(tree_degree),
                        float(tree_theta), int(tree_min_sources), int(tree_ff_degree), float(tree_ff_theta),

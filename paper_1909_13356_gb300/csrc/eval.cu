@@ -1902,9 +1902,10 @@ int eval_init_constants(Ctx* ctx) { return upload_series_constants(ctx); }
 
 int mixed_tpb(const Ctx* ctx, const Mesh* me)
 {
+    if (me->sigx) return kEvalThreads * kTPT32;
     const int t = ctx->opt.mixed_block > 0 ? ctx->opt.mixed_block : me->tune_tpb;
-    if (!me->sigx && (t == 64 || t == kEvalThreads)) return t;
-    return kEvalThreads * kTPT32;
+    // untuned: 64 targets per CTA (the autotuner's choice on the torus and the icosphere)
+    return t == kEvalThreads || t == kEvalThreads * kTPT32 ? t : 64;
 }
 double mixed_cut(const Ctx* ctx, const Mesh* me) { return me->tune_cut > 0.0 ? me->tune_cut : ctx->opt.cutoff_mixed; }
 
@@ -2098,13 +2099,18 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     return LSM_OK;
 }
 
-int eval_item_targets(int precision, int tpt)
+int eval_item_targets(const Ctx* ctx, int precision, int tpb)
 {
-    return kEvalThreads * (precision == LSM_MIXED ? (tpt == 1 ? 1 : kTPT32) : kTPT64);
+    if (precision == LSM_MIXED) {
+        const int t = tpb > 0 ? tpb : ctx->opt.mixed_block;
+        return t == kEvalThreads || t == kEvalThreads * kTPT32 ? t : 64;
+    }
+    if (precision == LSM_FF) return ctx->opt.ff_block == 64 ? 64 : kEvalThreads;
+    return kEvalThreads * kTPT64;
 }
 
 int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* items, const int* n_items,
-               int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc, int tpt,
+               int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc, int tpb,
                double cut_mixed)
 {
     if (max_items <= 0) return LSM_OK;
@@ -2138,11 +2144,16 @@ int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* item
         A.x_old = inc->x_old;
         A.bb_io = inc->bb_io;
     }
-    if (mixed && tpt == 1) {
+    const int bs = eval_item_targets(ctx, precision, tpb);
+    if (mixed && bs == 64) {
+        k_eval_mixed<1, false, 2><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
+    } else if (mixed && bs == kEvalThreads) {
         k_eval_mixed<1, false><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
     } else if (mixed) {
         k_eval_mixed<kTPT32, false><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo,
                                                                         A);
+    } else if (precision == LSM_FF && bs == 64) {
+        k_eval_ff<false, 64><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
     } else if (precision == LSM_FF) {
         k_eval_ff<false><<<max_items, kEvalThreads, 0, st>>>(v.s32_pos, v.s32_nw, v.s32_lo, v.s32_nwlo, A);
     } else {

@@ -201,9 +201,10 @@ struct Batch {
     float4 *tile_lo = nullptr, *tile_hi = nullptr, *tile_chi = nullptr, *tile_clo = nullptr;
     int2* mesh_tiles = nullptr;  // [nmesh] (first tile, end tile)
     std::vector<int64_t> tri_off;  // host [nmesh + 1]
-    // mixed kernel settings chosen by lsm_batch_autotune (0: defaults)
+    // mixed kernel settings chosen by lsm_batch_autotune (0: defaults): the
+    // near-field radius and the targets per work item (64, 128 or 256)
     double cut_mixed = 0.0;
-    int tpt = 0;
+    int tpb = 0;
 };
 
 // ---------------------------------------------------------------- patch map
@@ -361,14 +362,15 @@ struct FFIncremental {
 int eval_sorted(Ctx* ctx, const Mesh* mesh, const Targets& t, double* res, int precision,
                 cudaStream_t st, const FFIncremental* inc = nullptr);
 // Targets grouped by work items (int4: first target, count, first tile, end
-// tile; at most eval_item_targets(precision) targets each); the number of
-// items is read on the device from *n_items, the grid covers max_items.
-// tpt: targets per thread of the mixed kernel (1 or 2; 0 the default 2);
+// tile; at most eval_item_targets(ctx, precision, tpb) targets each); the
+// number of items is read on the device from *n_items, the grid covers
+// max_items.  tpb: targets per item of the mixed kernel (64, 128 or 256; 0
+// the default 256; the float-float kernel takes the context's ff_block);
 // cut: its near-field radius in sigma (0: the context's cutoff_mixed)
-int eval_item_targets(int precision, int tpt = 0);
+int eval_item_targets(const Ctx* ctx, int precision, int tpb = 0);
 int eval_items(Ctx* ctx, const SourceView& v, const Targets& t, const int4* items, const int* n_items,
                int max_items, double* res, int precision, cudaStream_t st, const FFIncremental* inc = nullptr,
-               int tpt = 0, double cut = 0.0);
+               int tpb = 0, double cut = 0.0);
 // the mixed kernel's settings for a mesh: its autotuned ones, else the defaults
 int mixed_tpb(const Ctx* ctx, const Mesh* me);   // targets per CTA of the mixed kernel on this mesh
 double mixed_cut(const Ctx* ctx, const Mesh* me);
@@ -495,9 +497,11 @@ int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, i
                        cudaStream_t st);
 int batch_build(Ctx* ctx, Batch* b, lsm_mesh* const* meshes, int n, cudaStream_t st);
 void batch_release(Batch* b);
+// Work items of at most bs listed nodes of one mesh each; cap: the items
+// buffer's length (no item is written past it)
 int build_items(Ctx* ctx, const int32_t* list, const int* n_list, int n_max, const int32_t* node_mesh,
                 const int2* mesh_tiles, int nmesh, int bs, uint32_t* cnt, uint32_t* nblk, int4* items, int* n_items,
-                cudaStream_t st);
+                int cap, cudaStream_t st);
 
 // host helpers (api.cu)
 void simplex_rule_host(int n, int subdiv, double* uvw);  // [cnt][3]

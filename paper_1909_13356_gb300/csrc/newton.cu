@@ -192,7 +192,7 @@ __global__ void k_mesh_blocks(const uint32_t* __restrict__ cnt, int nmesh, int b
 
 __global__ void k_write_items(const uint32_t* __restrict__ seg, const uint32_t* __restrict__ cnt,
                               const uint32_t* __restrict__ blk, const int2* __restrict__ mesh_tiles, int nmesh,
-                              int bs, int4* __restrict__ items)
+                              int bs, int cap, int4* __restrict__ items)
 {
     const int m = blockIdx.x;
     if (m >= nmesh) return;
@@ -201,7 +201,8 @@ __global__ void k_write_items(const uint32_t* __restrict__ seg, const uint32_t* 
     const int2 tr = mesh_tiles[m];
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         const int first = (int)seg[m] + j * bs;
-        items[blk[m] + j] = make_int4(first, min(bs, c - j * bs), tr.x, tr.y);
+        if ((int64_t)blk[m] + j < cap)   // never past the buffer (its size is computed for bs on the host)
+            items[blk[m] + j] = make_int4(first, min(bs, c - j * bs), tr.x, tr.y);
     }
 }
 
@@ -419,7 +420,7 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
 // number of items written.  Launch shapes depend on n_max and nmesh only.
 int build_items(Ctx* ctx, const int32_t* list, const int* n_list, int n_max, const int32_t* node_mesh,
                 const int2* mesh_tiles, int nmesh, int bs, uint32_t* cnt, uint32_t* nblk, int4* items, int* n_items,
-                cudaStream_t st)
+                int cap, cudaStream_t st)
 {
     uint32_t* seg = cnt + nmesh;
     LSM_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nmesh, st));
@@ -432,7 +433,7 @@ int build_items(Ctx* ctx, const int32_t* list, const int* n_list, int n_max, con
     if (rc) return rc;
     rc = scan_exclusive(ctx, nblk, nmesh, reinterpret_cast<uint32_t*>(n_items), st);
     if (rc) return rc;
-    k_write_items<<<nmesh, 128, 0, st>>>(seg, cnt, nblk, mesh_tiles, nmesh, bs, items);
+    k_write_items<<<nmesh, 128, 0, st>>>(seg, cnt, nblk, mesh_tiles, nmesh, bs, cap, items);
     LSM_LAUNCHED(ctx);
     return LSM_OK;
 }
@@ -487,7 +488,7 @@ struct BatchSweep {
     bool mixed;
     int accept_mixed, max_iter;
     double tol, sw;
-    int tpt;          // mixed kernel: targets per thread (0: default)
+    int tpb;          // mixed kernel: targets per work item (0: default)
     double cut;       // mixed kernel: near-field radius in sigma (0: default)
 };
 
@@ -513,15 +514,15 @@ int batch_sweep(Ctx* ctx, const BatchSweep& B, const int32_t* act, const int* n_
         }
         k_gather_targets_dev<<<nb(B.N), 256, 0, st>>>(L, nL, B.S, B.T, B.N);
         LSM_LAUNCHED(ctx);
-        const int bs = eval_item_targets(prec, B.tpt);
+        const int bs = eval_item_targets(ctx, prec, B.tpb);
         rc = build_items(ctx, L, nL, B.N, B.node_mesh, B.mesh_tiles, B.nmesh, bs, B.cnt, B.nblk, B.items, B.n_items,
-                         st);
+                         std::max(B.max_items_mixed, B.max_items_other), st);
         if (rc) return rc;
         Targets tg{B.T, B.N, B.N};
         FFIncremental inc{verify ? 2 : 1, B.Rfar, verify ? B.Trec : nullptr, B.BBrec};
         const bool ffpair = B.mixed && m == 1;
         rc = eval_items(ctx, B.view, tg, B.items, B.n_items, prec == LSM_MIXED ? B.max_items_mixed : B.max_items_other,
-                        B.R, prec, st, ffpair ? &inc : nullptr, B.tpt, B.cut);
+                        B.R, prec, st, ffpair ? &inc : nullptr, B.tpb, B.cut);
         if (rc) return rc;
         if (ffpair && !verify) {
             k_copy_record<<<nb(B.N), 256, 0, st>>>(L, nL, B.Lrec, B.n_rec, B.T, B.Trec, B.N);
@@ -604,14 +605,15 @@ int solve_charts_batch(Ctx* ctx, Batch* b, int n_gl, double tol, int max_iter, i
         BatchSweep B;
         B.N = N;
         B.nmesh = b->nmesh;
-        B.tpt = b->tpt;
+        B.mixed = precision == LSM_MIXED;   // before the item sizes, which depend on it
+        B.tpb = b->tpb;
         B.cut = b->cut_mixed;
-        B.max_items_mixed = (N + eval_item_targets(LSM_MIXED, B.tpt) - 1) / eval_item_targets(LSM_MIXED, B.tpt) +
+        B.max_items_mixed = (N + eval_item_targets(ctx, LSM_MIXED, B.tpb) - 1) / eval_item_targets(ctx, LSM_MIXED, B.tpb) +
                             b->nmesh;
-        B.max_items_other = (N + eval_item_targets(LSM_FP64) - 1) / eval_item_targets(LSM_FP64) + b->nmesh;
+        const int bs_other = eval_item_targets(ctx, B.mixed ? LSM_FF : LSM_FP64);
+        B.max_items_other = (N + bs_other - 1) / bs_other + b->nmesh;
         B.mesh_tiles = b->mesh_tiles;
         B.view = view_of_batch(b);
-        B.mixed = precision == LSM_MIXED;
         B.accept_mixed = tol >= ctx->opt.mixed_accept ? 1 : 0;
         B.max_iter = max_iter;
         B.tol = tol;

@@ -324,7 +324,7 @@ int batch_autotune(Ctx* ctx, Batch* b, int n_gl, double budget, lsm_tune_result*
     LSM_CUDA_TRY(ctx, s.get(&R, 4 * (size_t)nL));
     k_tune_gather<<<nbk(nL), 256, 0, st>>>(L, nL, perm, x0a, nL, T);
     LSM_LAUNCHED(ctx);
-    const int max_items = nL / eval_item_targets(LSM_FF) + b->nmesh + 1;
+    const int max_items = nL / 64 + b->nmesh + 1;   // the smallest work item has 64 targets
     int4* items;
     int* n_items;
     uint32_t *cnt, *nblk;
@@ -336,12 +336,12 @@ int batch_autotune(Ctx* ctx, Batch* b, int n_gl, double budget, lsm_tune_result*
     LSM_CUDA_TRY(ctx, s.get(&word, 1));
     const SourceView view = view_of_batch(b);
     Targets tg{T, nL, nL};
-    auto evaluate = [&](int prec, int tpt, double cut, double* out) -> int {
-        const int bs = eval_item_targets(prec, tpt);
+    auto evaluate = [&](int prec, int tpb, double cut, double* out) -> int {
+        const int bs = eval_item_targets(ctx, prec, tpb);
         int r = build_items(ctx, L, cnts, nL, mesh_sorted, b->mesh_tiles, b->nmesh, bs, cnt, nblk, items, n_items,
-                            st);
+                            max_items, st);
         if (r) return r;
-        return eval_items(ctx, view, tg, items, n_items, nL / bs + b->nmesh + 1, out, prec, st, nullptr, tpt, cut);
+        return eval_items(ctx, view, tg, items, n_items, nL / bs + b->nmesh + 1, out, prec, st, nullptr, tpb, cut);
     };
     rc = evaluate(LSM_FF, 0, 0.0, Rref);
     if (rc) return rc;
@@ -349,14 +349,14 @@ int batch_autotune(Ctx* ctx, Batch* b, int n_gl, double budget, lsm_tune_result*
     LSM_CUDA_TRY(ctx, cudaEventCreate(&e0));
     LSM_CUDA_TRY(ctx, cudaEventCreate(&e1));
     double best_ms = 1e300, best_err = 0.0, best_cut = 0.0, def_ms = 0.0, def_err = 0.0;
-    int best_tpt = 0, tried = 0;
+    int best_tpb = 0, tried = 0;
     for (double cut : kCutCandidates) {
         if (cutoff_bound(cut) > kCutBound) continue;
-        for (int tpt : {1, 2}) {
-            rc = evaluate(LSM_MIXED, tpt, cut, R);   // warm
+        for (int tpb : {64, 128, 256}) {
+            rc = evaluate(LSM_MIXED, tpb, cut, R);   // warm
             if (rc == LSM_OK) {
                 cudaEventRecord(e0, st);
-                rc = evaluate(LSM_MIXED, tpt, cut, R);
+                rc = evaluate(LSM_MIXED, tpb, cut, R);
                 cudaEventRecord(e1, st);
             }
             double err = 0.0;
@@ -365,7 +365,7 @@ int batch_autotune(Ctx* ctx, Batch* b, int n_gl, double budget, lsm_tune_result*
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
             tried++;
-            if (tpt == 2 && std::fabs(cut - ctx->opt.cutoff_mixed) < 1e-12) {
+            if (tpb == 64 && std::fabs(cut - ctx->opt.cutoff_mixed) < 1e-12) {   // the default settings
                 def_ms = ms;
                 def_err = err;
             }
@@ -373,7 +373,7 @@ int batch_autotune(Ctx* ctx, Batch* b, int n_gl, double budget, lsm_tune_result*
                 best_ms = ms;
                 best_err = err;
                 best_cut = cut;
-                best_tpt = tpt;
+                best_tpb = tpb;
             }
         }
         if (rc != LSM_OK) break;
@@ -381,13 +381,13 @@ int batch_autotune(Ctx* ctx, Batch* b, int n_gl, double budget, lsm_tune_result*
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LSM_OK) return rc;
-    if (best_tpt == 0) {   // nothing within the budget: keep the defaults
+    if (best_tpb == 0) {   // nothing within the budget: keep the defaults
         best_cut = 0.0;
         best_ms = def_ms;
         best_err = def_err;
     }
     b->cut_mixed = best_cut;
-    b->tpt = best_tpt;
+    b->tpb = best_tpb;
     if (res) {
         res->use_tree = 0;
         res->tree_degree = 0;
@@ -399,7 +399,7 @@ int batch_autotune(Ctx* ctx, Batch* b, int n_gl, double budget, lsm_tune_result*
         res->ms_direct = def_ms;
         res->err_direct = def_err;
         res->cutoff = best_cut > 0.0 ? best_cut : ctx->opt.cutoff_mixed;
-        res->targets_per_block = eval_item_targets(LSM_MIXED, best_tpt);
+        res->targets_per_block = eval_item_targets(ctx, LSM_MIXED, best_tpb);
         res->reserved = 0;
     }
     return LSM_OK;
