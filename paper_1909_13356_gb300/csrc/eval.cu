@@ -54,6 +54,11 @@
 #ifndef LSM_REACH_SPLIT_MIXED
 #define LSM_REACH_SPLIT_MIXED 1
 #endif
+// unrolling of the mixed kernel's packed far loop (pairs of sources per step;
+// 4 measured no faster and drops the 64-target layout to 4 CTAs per SM)
+#ifndef LSM_MIXED_UNROLL
+#define LSM_MIXED_UNROLL 2
+#endif
 #ifndef LSM_PACKED_F32X2
 #define LSM_PACKED_F32X2 1
 #endif
@@ -123,6 +128,7 @@ constexpr double kSqrt2 = 1.41421356237309505;
 constexpr double kSigC = 0.063493635934240970;
 constexpr double kFourPiD = 12.566370614359172954;
 constexpr int kChunk = 64;  // far-tile sources summed in FP32 before compensation
+constexpr int kMixedUnroll = LSM_MIXED_UNROLL;
 constexpr int kErrWaitTimeout = 1;
 
 // ---------------------------------------------------------------- radial factors
@@ -848,7 +854,7 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_mixed(const float4* __
                     // P0 = Phi; grad = P - R (P: -nw/|r|^3 terms, R: the 3 (nw . r) r/|r|^5 terms negated)
                     float2 P0 = make_float2(0.0f, 0.0f), P1 = P0, P2 = P0, P3 = P0, R1 = P0, R2 = P0, R3 = P0;
                     const int k0 = c0 >> 1, npair = (c1 - c0 + 1) >> 1;
-#pragma unroll 2
+#pragma unroll kMixedUnroll
                     for (int q = lane; q < npair; q += SPL) {
                         const int k = k0 + q;
                         const float2 mx = MX[k], my = MY[k], mz = MZ[k];
