@@ -40,6 +40,33 @@ def test_batch_matches_each_mesh_alone(setup, prec, tol, pos_tol, use_graph):
     b.free()
 
 
+@pytest.mark.parametrize("ff_block,mixed_block", [(128, 256), (128, 128), (64, 64)])
+def test_batch_layouts_match_each_mesh_alone(ff_block, mixed_block):
+    """Work items of the other target-tile sizes (float-float 128 and 64,
+    mixed 256, 128 and 64 targets): the batched solve still equals each
+    mesh's own solve under the same options, and the nodes meet the bar."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1909_13356_gb300 as lsm
+    ctx = lsm.Context(0, ff_block=ff_block, mixed_block=mixed_block)
+    g = synth.rng(45)
+    ms = [synth.ellipsoid(int(T), g) for T in (240, 610, 330)]
+    meshes = [ctx.upload(m.verts, m.tris, m.sigma, n_gl=4) for m in ms]
+    b = lsm.Batch(ctx, meshes)
+    x, h, st, stats = b.solve_charts(order=6, tol=1e-10, precision=lsm.MIXED, use_graph=True)
+    assert np.all(st & 255 == 0), np.unique(st)
+    o = 0
+    for mesh in meshes:
+        xa, ha, sa, _ = mesh.solve_charts(order=6, tol=1e-10, precision=lsm.MIXED)
+        n = len(ha)
+        assert np.abs(x[o:o + n] - xa).max() < 1e-9
+        o += n
+    b.free()
+    for mesh in meshes:
+        mesh.free()
+    ctx.close()
+
+
 def test_batch_residual_against_oracle(setup, oracle_mod):
     lsm, ctx, ms, meshes = setup
     b = lsm.Batch(ctx, meshes[:3])
