@@ -39,6 +39,7 @@
 #include <type_traits>
 
 #include "lsm_internal.cuh"
+#include "ff.cuh"
 
 #ifndef LSM_RSQRT_REFINE
 #define LSM_RSQRT_REFINE 1
@@ -185,32 +186,6 @@ constexpr int kHTabN = 520;                   // covers w < 32.5 (u < 5.70)
 constexpr float kHTabWmax = (float)kHTabN / kHTabPerUnit;
 __device__ float4 g_htab[kHTabN * 3];         // filled once per device by the host
 
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
-{
-    const float s = hi + x;
-    const float bp = s - hi;
-    const float err = (hi - (s - bp)) + (x - bp);
-    hi = s;
-    lo += err;
-}
-
-// Fold the low word back into the high word (Fast2Sum), so that the low word
-// never grows into a running FP32 sum of its own over many additions.
-__device__ __forceinline__ void renorm(float& hi, float& lo)
-{
-    const float s = hi + lo;
-    lo = lo - (s - hi);
-    hi = s;
-}
-
-__device__ __forceinline__ void two_sum_acc64(double& hi, double& lo, double x)
-{
-    const double s = hi + x;
-    const double bp = s - hi;
-    const double err = (hi - (s - bp)) + (x - bp);
-    hi = s;
-    lo += err;
-}
 
 // Block-wide min/max of three floats each, result in shared s[0..6).
 __device__ __forceinline__ void block_bbox(float lo[3], float hi[3], float* s)
@@ -347,45 +322,6 @@ __device__ __forceinline__ void give_up(const EvalArgs& A, uint64_t* bar, int b,
 // Targets of a CTA that gave up get NaN results.
 constexpr double kNaN = __builtin_nan("");
 
-// ---------------------------------------------------------------- float-float arithmetic
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e)
-{
-    s = a - b;
-    const float bb = s - a;
-    e = (a - (s - bb)) - (b + bb);
-}
-
-
-// two_sum for a, b >= 0: the larger first makes Dekker's fast two-sum exact;
-// the ordering runs on the ALU pipe, the sum on three FP32 additions
-__device__ __forceinline__ void two_sum_nonneg(float a, float b, float& s, float& e)
-{
-    const float hi = fmaxf(a, b), lo = fminf(a, b);
-    s = hi + lo;
-    e = lo - (s - hi);
-}
-
-// ff product of (ah, al) and (bh, bl)
-__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& h, float& l)
-{
-    h = ah * bh;
-    l = fmaf(ah, bh, -h) + fmaf(ah, bl, al * bh);
-}
-// ff sum (ah, al) + (bh, bl), renormalised
-__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& h, float& l)
-{
-    float s, e;
-    two_sum(ah, bh, s, e);
-    e += al + bl;
-    h = s + e;
-    l = e - (h - s);
-}
 
 
 // One source's Phi term for one target in float-float: the tile-local pair
@@ -1942,7 +1878,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     if (me->sigx) {
         LSM_CUDA_TRY(ctx, s.get(&tsig, (size_t)t.n));
         LSM_CUDA_TRY(ctx, s.get(&tgsig, 3 * (size_t)t.n));
-        int rc = sigma_x_eval(ctx, me, t, tsig, tgsig, st, mixed);
+        int rc = sigma_x_eval(ctx, me, t, tsig, tgsig, st, precision);
         if (rc != LSM_OK) return rc;
     }
     // mixed path on a large mesh: the treecode's interaction lists

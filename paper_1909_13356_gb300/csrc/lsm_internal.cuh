@@ -478,9 +478,10 @@ double sigma_sources_host(const double* verts, const int32_t* tris, int64_t nt, 
                           double* cen);
 int sigma_attach(Ctx* ctx, Mesh* me, const double* sj, const double* cen, int64_t nt, double sigma0,
                  cudaStream_t st);
-// sigma(x) [n] and grad sigma [3][n] (SoA) at sorted targets
+// sigma(x) [n] and grad sigma [3][n] (SoA) at sorted targets, for the pair
+// kernels of `precision` (LSM_FP64: FP64 sums; else float-float sums)
 int sigma_x_eval(Ctx* ctx, const Mesh* me, const Targets& t, double* sig, double* gsig, cudaStream_t st,
-                 bool mixed = false);
+                 int precision = LSM_FP64);
 
 // tune.cu: the autotuner on sorted SoA targets (lsm_autotune)
 int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tune_result* res, cudaStream_t st);
