@@ -1828,6 +1828,9 @@ int upload_series_constants(Ctx* ctx)
         build_h_table(tab.data());
         LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(g_htab, tab.data(), sizeof(float4) * tab.size()));
     }
+    // copies from pageable memory may return before they land, and nothing
+    // orders them with kernels on the caller's (possibly non-blocking) stream
+    LSM_CUDA_TRY(ctx, cudaDeviceSynchronize());
     if (ctx->device >= 0 && ctx->device < 64) g_consts_ready[ctx->device] = true;
     return LSM_OK;
 }
@@ -1844,7 +1847,6 @@ int eval_init_constants(Ctx* ctx) { return upload_series_constants(ctx); }
 
 int mixed_tpb(const Ctx* ctx, const Mesh* me)
 {
-    if (me->sigx) return kEvalThreads * kTPT32;
     const int t = ctx->opt.mixed_block > 0 ? ctx->opt.mixed_block : me->tune_tpb;
     // untuned: 64 targets per CTA (the autotuner's choice on the torus and the icosphere)
     return t == kEvalThreads || t == kEvalThreads * kTPT32 ? t : 64;
@@ -1860,8 +1862,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     const bool mixed = precision == LSM_MIXED;
     const bool ff = precision == LSM_FF;
     // targets per CTA: the mixed kernel's tuned layout (64, 128 or 256); the
-    // float-float kernel's 64 (the option's default) outside sigma(x) mode
-    const bool ff64 = ff && !me->sigx && ctx->opt.ff_block == 64;
+    // float-float kernel's 64 (the option's default) or 128
+    const bool ff64 = ff && ctx->opt.ff_block == 64;
     const int tpb = mixed ? mixed_tpb(ctx, me) : (ff64 ? 64 : kEvalThreads * kTPT64);
     const int nblk = (t.n + tpb - 1) / tpb;
     const int ntiles = (int)me->ntiles;
@@ -1967,9 +1969,17 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         LSM_CUDA_TRY(ctx, cudaEventRecord(ev0, st));
     }
     if (me->sigx) {
-        if (mixed)
+        if (mixed && tpb == 64)
+            k_eval_mixed<1, true, 2><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
+                                                                     me->s32_nwlo, A);
+        else if (mixed && tpb == kEvalThreads)
+            k_eval_mixed<1, true><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo,
+                                                                 A);
+        else if (mixed)
             k_eval_mixed<kTPT32, true><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo,
                                                                       me->s32_nwlo, A);
+        else if (ff64)
+            k_eval_ff<true, 64><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
         else if (ff)
             k_eval_ff<true><<<grid, kEvalThreads, 0, st>>>(me->s32_pos, me->s32_nw, me->s32_lo, me->s32_nwlo, A);
         else

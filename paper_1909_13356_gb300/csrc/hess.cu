@@ -272,6 +272,9 @@ int hess_constants(Ctx* ctx)
         for (int j = 0; j < 7; j++) tab[8 * (size_t)k + j] = (double)cf[j];
     }
     LSM_CUDA_TRY(ctx, cudaMemcpyToSymbol(g_htab64, tab.data(), sizeof(double) * tab.size()));
+    // a copy from pageable memory may return before it lands, and nothing
+    // orders it with kernels on the caller's (possibly non-blocking) stream
+    LSM_CUDA_TRY(ctx, cudaDeviceSynchronize());
     if (ctx->device >= 0 && ctx->device < 64) g_hess_consts[ctx->device] = true;
     return LSM_OK;
 }

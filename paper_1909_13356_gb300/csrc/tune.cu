@@ -177,7 +177,6 @@ int autotune_sorted(Ctx* ctx, Mesh* me, const Targets& t, double budget, lsm_tun
         for (double cut : kCutCandidates) {
             if (cutoff_bound(cut) > kCutBound) continue;
             for (int tpb : {64, kEvalThreads, 2 * kEvalThreads}) {
-                if (tpb < 2 * kEvalThreads && me->sigx) continue;
                 me->tune_cut = cut;
                 me->tune_tpb = tpb;
                 rc = eval_sorted(ctx, me, ts, R, LSM_MIXED, st);   // warm: lists and launch shapes

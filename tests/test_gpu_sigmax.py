@@ -54,6 +54,20 @@ def test_phi_grad_sigma_x_matches_oracle(lsm, graded, prec, tphi, tgrad):
     assert np.abs(grad - graded["grad"]).max() <= tgrad / smin
 
 
+@pytest.mark.parametrize("prec,block", [("FF", 64), ("FF", 128), ("MIXED", 64), ("MIXED", 128), ("MIXED", 256)])
+def test_phi_grad_sigma_x_target_tiles(lsm, graded, prec, block):
+    """Every target-tile layout of the float-float (64, 128 targets per CTA)
+    and mixed (64, 128, 256) kernels in sigma(x) mode against the oracle."""
+    opt = {"ff_block": block} if prec == "FF" else {"mixed_block": block}
+    ctx = lsm.Context(0, **opt)
+    mesh = ctx.upload_sigma_x(graded["m"].verts, graded["m"].tris, n_gl=6)
+    phi, grad = mesh.eval_phi_grad(graded["x"], getattr(lsm, prec))
+    smin = graded["sj"].min()
+    tphi = 1e-12 if prec == "FF" else 1e-7
+    assert np.abs(phi - graded["phi"]).max() <= tphi
+    assert np.abs(grad - graded["grad"]).max() <= 1e-7 / smin
+
+
 def test_sigma_x_equal_widths_reduce_to_constant(lsm):
     """Cube: every triangle has the same D_j, so sigma(x) is constant and the
     results equal the per-triangle mesh's with that sigma.  The float-float
