@@ -1893,13 +1893,13 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     // treecodes: target clusters take the nodes far from them (tpc a multiple of the block)
     ClusterPlan cp;
     const int tpc = (ff ? ctx->opt.tree_ff_cluster : ctx->opt.tree_cluster) / tpb * tpb;
-    const bool clusters = use_tree && (ff || mixed) && !me->sigx && tpc > 0 && t.n >= 2 * tpc;
+    const bool clusters = use_tree && (ff || mixed) && tpc > 0 && t.n >= 2 * tpc;
     if (use_tree) {
         int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff);
         if (rc != LSM_OK) return rc;
         if (clusters) {
             rc = cluster_setup(ctx, ff ? me->tree_ff : me->tree, t, tpc, tpb, ff ? ctx->opt.cutoff_fp64 : mixed_cut(ctx, me),
-                               s, &cp, st);
+                               tsig, s, &cp, st);
             if (rc != LSM_OK) return rc;
         }
         int64_t total = 0;

@@ -436,9 +436,11 @@ struct ClusterPlan {
     int64_t cwords = 0;
 };
 // tpb: targets per block of the pair kernel that evaluates the lists (and
-// the grid points); cut: its near radius in sigma
-int cluster_setup(Ctx* ctx, const Tree* tree, const Targets& t, int tpc, int tpb, double cut, Scratch& s,
-                  ClusterPlan* plan, cudaStream_t st);
+// the grid points); cut: its near radius in sigma; tsig: the sorted targets'
+// sigma in sigma(x) mode (the near width of a cluster or block is then its
+// largest target sigma), else null
+int cluster_setup(Ctx* ctx, const Tree* tree, const Targets& t, int tpc, int tpb, double cut, const double* tsig,
+                  Scratch& s, ClusterPlan* plan, cudaStream_t st);
 // Adds the clusters' interpolated far field to res [4][n] (and to far_io [4][n]
 // when not null) from the grid values rg [4][ng].
 int cluster_l2p(Ctx* ctx, const ClusterPlan& plan, const Targets& t, const double* rg, double* res,

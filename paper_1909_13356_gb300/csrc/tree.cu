@@ -714,7 +714,7 @@ __device__ __forceinline__ bool box_takes(const WalkArgs& A, int64_t node, float
 // the cluster's box for its grid: target side).  FP32 with a 1e-4 margin.
 __device__ __forceinline__ bool cluster_takes(const WalkArgs& A, int64_t node, int c)
 {
-    if (!box_takes(A, node, A.c_lo[c], A.c_hi[c], A.nlo[node].w)) return false;
+    if (!box_takes(A, node, A.c_lo[c], A.c_hi[c], A.sigx ? A.c_lo[c].w : A.nlo[node].w)) return false;
     const float4 ac = A.acc[node];
     const float4 cc = A.c_acc[c];
     const float ex = ac.x - cc.x, ey = ac.y - cc.y, ez = ac.z - cc.z;
@@ -886,14 +886,17 @@ __device__ int4 grid_counts_dev(const double h[3], int p, double C)
 }
 
 // One CTA per cluster: frame (centre, axes as rows, half-widths) into
-// frame[16 c ...], grid counts, the outward box of the oriented box, and the
-// centre with the squared opening radius (r + q_p h_max)^2.
+// frame[16 c ...], grid counts, the outward box of the oriented box (in
+// sigma(x) mode with the cluster's largest target sigma, rounded up, in
+// clo.w), and the centre with the squared opening radius (r + q_p h_max)^2.
 __global__ void __launch_bounds__(kFrameThreads) k_cluster_frames(const double* __restrict__ x, int64_t ld, int n,
-                                                                  int tpc, double C, int p, double* __restrict__ frame,
+                                                                  int tpc, double C, int p,
+                                                                  const double* __restrict__ tsig,
+                                                                  double* __restrict__ frame,
                                                                   int4* __restrict__ counts, float4* __restrict__ clo,
                                                                   float4* __restrict__ chi, float4* __restrict__ cacc)
 {
-    __shared__ double sm[(kFrameThreads / 32) * 6];
+    __shared__ double sm[(kFrameThreads / 32) * 7];
     __shared__ double s_e[3][3];
     const int c = blockIdx.x;
     const int64_t i0 = (int64_t)c * tpc, i1 = min((int64_t)n, i0 + tpc);
@@ -924,7 +927,7 @@ __global__ void __launch_bounds__(kFrameThreads) k_cluster_frames(const double* 
     double e[3][3];
     for (int ax = 0; ax < 3; ax++)
         for (int k = 0; k < 3; k++) e[ax][k] = s_e[ax][k];
-    double ext[6] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    double ext[7] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
     for (int64_t i = i0 + threadIdx.x; i < i1; i += kFrameThreads) {
         const double d[3] = {x[i] - m[0], x[ld + i] - m[1], x[2 * ld + i] - m[2]};
         for (int ax = 0; ax < 3; ax++) {
@@ -932,16 +935,17 @@ __global__ void __launch_bounds__(kFrameThreads) k_cluster_frames(const double* 
             ext[ax] = fmax(ext[ax], t);
             ext[3 + ax] = fmax(ext[3 + ax], -t);
         }
+        if (tsig) ext[6] = fmax(ext[6], tsig[i]);
     }
-    for (int k = 0; k < 6; k++)
+    for (int k = 0; k < 7; k++)
         for (int o = 16; o > 0; o >>= 1) ext[k] = fmax(ext[k], __shfl_xor_sync(0xffffffffu, ext[k], o));
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0)
-        for (int k = 0; k < 6; k++) sm[w * 6 + k] = ext[k];
+        for (int k = 0; k < 7; k++) sm[w * 7 + k] = ext[k];
     __syncthreads();
     if (threadIdx.x != 0) return;
-    for (int k = 0; k < 6; k++)
-        for (int j = 1; j < kFrameThreads / 32; j++) ext[k] = fmax(ext[k], sm[j * 6 + k]);
+    for (int k = 0; k < 7; k++)
+        for (int j = 1; j < kFrameThreads / 32; j++) ext[k] = fmax(ext[k], sm[j * 7 + k]);
     double h[3], r2 = 0.0;
     for (int ax = 0; ax < 3; ax++) {
         const double hi = ext[ax], lo = -ext[3 + ax];
@@ -971,7 +975,7 @@ __global__ void __launch_bounds__(kFrameThreads) k_cluster_frames(const double* 
         lo[k] = __double2float_rd(m[k] - ext_k * (1.0 + 1e-12));
         hi[k] = __double2float_ru(m[k] + ext_k * (1.0 + 1e-12));
     }
-    clo[c] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    clo[c] = make_float4(lo[0], lo[1], lo[2], __double2float_ru(ext[6]));
     chi[c] = make_float4(hi[0], hi[1], hi[2], 0.0f);
     const double R = sqrt(r2) + cosh(C / p) * hmax;
     cacc[c] = make_float4((float)m[0], (float)m[1], (float)m[2], __double2float_ru(R * R));
@@ -1034,7 +1038,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_cluster_walk(ClusterWalkArgs A
                 return (int)kEmitProxies;
             }
             for (int b = b0; b < b1; b++)
-                if (box_takes(A.W, node, A.blo[b], A.bhi[b], A.W.nlo[node].w)) return (int)kSkip;
+                if (box_takes(A.W, node, A.blo[b], A.bhi[b], A.W.sigx ? A.blo[b].w : A.W.nlo[node].w))
+                    return (int)kSkip;
         }
         return l == 0 ? (int)kSkip : (int)kOpen;
     });
@@ -1428,8 +1433,8 @@ static void fill_walk_tree(WalkArgs& W, const Tree* T, double cut)
     W.cut2 = (float)(cut * cut);
 }
 
-int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, int tpb, double cut, Scratch& s,
-                  ClusterPlan* P, cudaStream_t st)
+int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, int tpb, double cut, const double* tsig,
+                  Scratch& s, ClusterPlan* P, cudaStream_t st)
 {
     ClusterPlan& cp = *P;
     cp.tpc = tpc;
@@ -1441,7 +1446,8 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, int tpb, d
     LSM_CUDA_TRY(ctx, s.get(&cp.frame, 16 * (size_t)ncl));
     LSM_CUDA_TRY(ctx, s.get(&cp.counts, ncl));
     const double C = tree_bound(T->degree, T->theta);
-    k_cluster_frames<<<ncl, kFrameThreads, 0, st>>>(t.x, t.ld, t.n, tpc, C, T->degree, cp.frame, cp.counts, cp.box_lo,
+    k_cluster_frames<<<ncl, kFrameThreads, 0, st>>>(t.x, t.ld, t.n, tpc, C, T->degree, tsig, cp.frame, cp.counts,
+                                                    cp.box_lo,
                                                     cp.box_hi, cp.cacc);
     LSM_LAUNCHED(ctx);
     // grid offsets on the host: each cluster's points start on a block boundary
@@ -1475,7 +1481,7 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, int tpb, d
     const int nblk = (t.n + tpb - 1) / tpb;
     LSM_CUDA_TRY(ctx, s.get(&cp.blo, nblk));
     LSM_CUDA_TRY(ctx, s.get(&cp.bhi, nblk));
-    k_block_boxes<<<nblk, kEvalThreads, 0, st>>>(t.x, t.ld, t.n, tpb, nullptr, cp.blo, cp.bhi);
+    k_block_boxes<<<nblk, kEvalThreads, 0, st>>>(t.x, t.ld, t.n, tpb, tsig, cp.blo, cp.bhi);
     LSM_LAUNCHED(ctx);
     cp.cwords = (T->nnodes + 31) / 32;
     LSM_CUDA_TRY(ctx, s.get(&cp.cbits, (size_t)cp.cwords * ncl));
@@ -1483,6 +1489,7 @@ int cluster_setup(Ctx* ctx, const Tree* T, const Targets& t, int tpc, int tpb, d
     // the clusters' lists: count, scan, write
     ClusterWalkArgs A;
     fill_walk_tree(A.W, T, cut);
+    A.W.sigx = tsig != nullptr;
     A.W.c_lo = cp.box_lo;
     A.W.c_hi = cp.box_hi;
     A.W.c_acc = cp.cacc;

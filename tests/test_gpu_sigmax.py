@@ -127,6 +127,44 @@ def test_sigma_x_with_treecodes(lsm, oracle_mod):
     assert np.abs(gm[sel] - go).max() <= 1e-7 / sj.min()
 
 
+def test_sigma_x_target_clusters(lsm, oracle_mod):
+    """Target clusters in sigma(x) mode (the float-float treecode's 4,096-target
+    clusters, the default, and the mixed treecode's on request), whose near
+    width is their largest target sigma: against the same trees without
+    clusters, Phi within 5e-13 (float-float) and 1e-8 (mixed), the gradients
+    within the paths' bars, and the float-float bar against the oracle on
+    sampled targets."""
+    m = synth.torus(1.0, 0.3, 120, 32, 20.0, 0.05, 55)
+    x = synth.targets_near_surface(m, 100_000, synth.rng(58), 3.0)
+    c, sj, dmax = oracle_mod.sigma_sources(m.verts, m.tris)
+    smin = sj.min()
+    out = {}
+    for name, kw in (("clusters", {"tree_cluster": 2048}), ("plain", {"tree_ff_cluster": -1})):
+        ctx = lsm.Context(0, **kw)
+        mesh = ctx.upload_sigma_x(m.verts, m.tris, n_gl=6)
+        mesh.eval_phi_grad(x[:4096], lsm.FF)       # builds the trees
+        mesh.eval_phi_grad(x[:4096], lsm.MIXED)
+        ctx.read_stats(reset=True)
+        pf, gf = mesh.eval_phi_grad(x, lsm.FF)
+        far = ctx.read_stats(reset=True)["kind_pairs_far"][1]
+        pm, gm = mesh.eval_phi_grad(x, lsm.MIXED)
+        out[name] = (pf, gf, pm, gm, far)
+        mesh.free()
+        ctx.close()
+    (pf, gf, pm, gm, far_c), (pf0, gf0, pm0, gm0, far_p) = out["clusters"], out["plain"]
+    assert np.abs(pf - pf0).max() <= 5e-13
+    assert np.abs(gf - gf0).max() <= 1e-7 / smin
+    assert np.abs(pm - pm0).max() <= 1e-8
+    assert np.abs(gm - gm0).max() <= 1e-7 / smin
+    assert far_c != far_p, (far_c, far_p)   # the clusters' grids took part of the far field
+    sel = np.random.default_rng(59).choice(len(x), 100, replace=False)
+    sg, gs = oracle_mod.sigma_x(c, sj, oracle_mod.sigma0_default(dmax), x[sel])
+    y, nw, _ = oracle_mod.sources(m.verts, m.tris, sj, 6, 0)
+    po, go = oracle_mod.phi_grad_sigx(y, nw, x[sel], sg, gs)
+    assert np.abs(pf[sel] - po).max() <= 1e-12
+    assert np.abs(pm[sel] - po).max() <= 1e-7
+
+
 def test_sigma_x_mesh_rejected_by_batch_and_noalloc(lsm):
     m = synth.cube(1.0, 2)
     ctx = lsm.Context(0)
