@@ -150,12 +150,12 @@ typedef struct {
     /* Targets per CTA of the float-float kernel (64 or 128; 0 selects 64):
      * the near/far split and the treecode's lists are per CTA, so a smaller
      * target box means fewer pairs per target, at the price of more CTAs
-     * streaming each source tile.  The target-dependent sigma(x) mode and
-     * batches always use 128. */
+     * streaming each source tile.  Every mode takes it: per-triangle sigma,
+     * the target-dependent sigma(x) and batches. */
     int32_t ff_block;
     /* Targets per CTA of the mixed kernel (64, 128 or 256; 0: the mesh's
      * or the batch's autotuned choice, else 64).  A nonzero value
-     * overrides the autotuner's; sigma(x) mode always uses 256. */
+     * overrides the autotuner's, in sigma(x) mode too. */
     int32_t mixed_block;
     int32_t reserved;   /* keeps the size a multiple of 8 without padding; set 0 */
 } lsm_options;
