@@ -7,6 +7,8 @@ FP64 oracle computed one by one.
 Bumped icosphere, level 8 (1,310,720 triangles, 20,971,520 nodes): a
 1e5-target evaluation against the float-float path at every target, the FP64
 direct sum on 10,240 targets and the oracle on 1,000.
+The same torus with the paper's sigma(x): 1,000 targets and 1,000 chart
+nodes against the oracle.
 """
 import numpy as np
 import pytest
@@ -159,3 +161,36 @@ def test_icosphere_full_evaluation_sampled(lsm, oracle_mod):
     assert np.abs(phi.cpu().numpy()[so] - po).max() <= 1e-7
     assert np.abs(grad.cpu().numpy()[so] - go).max() <= 1e-7 / m.sigma.min()
     assert np.abs(pff.cpu().numpy()[so] - po).max() <= 1e-12
+
+
+def test_torus_sigma_x_full_sampled(lsm, oracle_mod):
+    """The bench's sigma(x) leg at its full size: the graded torus with the
+    paper's target-dependent width (eq. sigma2) in place of per-triangle
+    sigma, 10^6 targets, mixed and float-float evaluations against the oracle
+    (sigma(x), grad sigma and Phi, grad Phi in FP64, one target at a time) on
+    1,000 sampled targets, and the order-8 chart solve to |Phi - 1/2| <
+    1e-12 re-evaluated by the oracle at 1,000 sampled nodes."""
+    w = synth.torus_c2(1_000_000)
+    m = w["mesh"]
+    ctx = lsm.Context(0)
+    mesh = ctx.upload_sigma_x(m.verts, m.tris, n_gl=6)
+    x = torch.from_numpy(w["targets"]).cuda()
+    c, sj, dmax = oracle_mod.sigma_sources(m.verts, m.tris)
+    s0 = oracle_mod.sigma0_default(dmax)
+    y, nw, _ = oracle_mod.sources(m.verts, m.tris, sj, 6, 0)
+    sel = np.random.default_rng(60).choice(len(w["targets"]), 1000, replace=False)
+    sg, gs = oracle_mod.sigma_x(c, sj, s0, w["targets"][sel])
+    po, go = oracle_mod.phi_grad_sigx(y, nw, w["targets"][sel], sg, gs)
+    for prec, tol in ((lsm.MIXED, 1e-7), (lsm.FF, 1e-12)):
+        phi, grad = mesh.eval_phi_grad(x, prec)
+        assert np.abs(phi.cpu().numpy()[sel] - po).max() <= tol
+        assert np.abs(grad.cpu().numpy()[sel] - go).max() <= 1e-7 / sj.min()
+    xs, h, st, stats = mesh.solve_charts(order=8, tol=1e-12, precision=lsm.MIXED, device_out=True)
+    assert stats.n_nodes == 1_105_920 and stats.n_failed == 0
+    sel = np.random.default_rng(61).choice(stats.n_nodes, 1000, replace=False)
+    xn = xs.cpu().numpy()[sel]
+    sg, gs = oracle_mod.sigma_x(c, sj, s0, xn)
+    pn, _ = oracle_mod.phi_grad_sigx(y, nw, xn, sg, gs)
+    assert np.abs(pn - 0.5).max() < 1e-12
+    mesh.free()
+    ctx.close()
