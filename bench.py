@@ -66,6 +66,10 @@ def parse():
                     help="targets per CTA of the float-float kernel (64 or 128; 0: library default)")
     ap.add_argument("--mixed-block", type=int, default=0,
                     help="targets per CTA of the mixed kernel (64, 128 or 256; 0: the autotuner's choice)")
+    ap.add_argument("--newton-tree-degree", type=int, default=0,
+                    help="treecode degree of the mixed Newton sweeps (0: library default 5; -1: the mesh's own)")
+    ap.add_argument("--newton-tree-theta", type=float, default=0.0,
+                    help="opening parameter of the mixed Newton sweeps' treecode (0: library default 0.5)")
     ap.add_argument("--tree-grid", type=int, default=0,
                     help="proxy grids: 1 per-axis point counts (default), 2 full (degree + 1)^3")
     ap.add_argument("--sigma-x", action="store_true",
@@ -706,7 +710,8 @@ def main():
     w = workload(args, rank if args.replicas else 0)
     m = w["mesh"]
     ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid,
-                      ff_block=args.ff_block, mixed_block=args.mixed_block)
+                      ff_block=args.ff_block, mixed_block=args.mixed_block,
+                      newton_tree_degree=args.newton_tree_degree, newton_tree_theta=args.newton_tree_theta)
     # the pipes' measured throughput (roofline denominators), clocks sampled around the probe
     pclk = ClockSampler(local)
     pclk.start()
@@ -960,6 +965,10 @@ def main():
                        "cutoff_sigma": {"fp64_and_float_float": 8.0,
                                         "mixed": (tune or {}).get("cutoff", 6.5) or 6.5},
                        "ff_targets_per_cta": args.ff_block or 64,
+                       # the mixed Newton sweeps' own treecode (used where coarser than the mesh's)
+                       "newton_mixed_tree": ("the mesh's mixed treecode" if args.newton_tree_degree < 0 else
+                                             {"degree": args.newton_tree_degree or 5,
+                                              "theta": args.newton_tree_theta or 0.5}),
                        "sigma": ("sigma(x), eq. sigma2: lambda 2.5, sigma0 = max D / sqrt(2 ln 2) = "
                                  f"{mesh.sigma0:.5g}" if args.sigma_x else "per triangle, 0.5 sqrt(2 area)"),
                        "parallelism": (f"{world} ranks, targets and chart nodes in Morton ranges, mesh replicated"
@@ -971,6 +980,15 @@ def main():
                                 "newton_float_float_full": st.evals_fp64 - st.evals_near_only,
                                 "newton_float_float_near_only_not_counted": st.evals_near_only}
                                if st else {"targets": nt}),
+            # rank 0's units per second, by the error each is made to: the
+            # mixed evaluation (1e-7), the mixed Newton sweeps (about 1e-6 on
+            # their coarser treecode: they only steer the nodes, which the
+            # float-float sweeps take to the tolerance) and the float-float
+            # record sweeps (FP64 accuracy)
+            "value_by_error_rank0": ({"mixed_1e-7": nt / (t_ms / args.steps / 1e3),
+                                      "newton_mixed_steering_about_1e-6": st.evals_fp32 / (t_ms / args.steps / 1e3),
+                                      "float_float_fp64_accuracy": (st.evals_fp64 - st.evals_near_only)
+                                      / (t_ms / args.steps / 1e3)} if st else None),
             "chart_nodes_per_s": st.n_converged * world / (t_ms / args.steps / 1e3) if st else None,
             "newton": {"iterations": st.iterations, "active_per_iter": st.active_per_iter,
                        "n_failed": st.n_failed, "eps_newton": st.eps_newton,

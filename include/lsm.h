@@ -157,6 +157,17 @@ typedef struct {
      * or the batch's autotuned choice, else 64).  A nonzero value
      * overrides the autotuner's, in sigma(x) mode too. */
     int32_t mixed_block;
+    /* The mixed Newton sweeps of a chart solve only carry each node to
+     * |Phi - 1/2| < mixed_switch; the float-float steps after them decide
+     * the result.  On meshes with the mixed treecode they take a coarser
+     * treecode of their own, with Chebyshev degree newton_tree_degree and
+     * opening parameter newton_tree_theta (0 selects 5 and 0.5: errors near
+     * 1e-6, far below the switch; the graded torus's order-8 solve at 10^6
+     * nodes then takes 1.53 s instead of 1.67 s, its nodes as accurate).
+     * The mesh's own mixed treecode is used when it is no finer than that;
+     * -1: always.  Evaluations (lsm_eval_phi_grad) never use it. */
+    int32_t newton_tree_degree;   /* 0: 5; 1..12; -1: off */
+    float newton_tree_theta;      /* 0: 0.5; (0, 1) */
     int32_t reserved;   /* keeps the size a multiple of 8 without padding; set 0 */
 } lsm_options;
 

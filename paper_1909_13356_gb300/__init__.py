@@ -66,6 +66,7 @@ class _Options(ctypes.Structure):
                 ("tree_ff_theta", ctypes.c_float), ("tree_ff_min_sources", ctypes.c_int32),
                 ("tree_grid", ctypes.c_int32), ("tree_ff_cluster", ctypes.c_int32), ("tree_cluster", ctypes.c_int32),
                 ("ff_block", ctypes.c_int32), ("mixed_block", ctypes.c_int32),
+                ("newton_tree_degree", ctypes.c_int32), ("newton_tree_theta", ctypes.c_float),
                 ("reserved", ctypes.c_int32)]
 
 
@@ -267,7 +268,8 @@ class Context:
                  mixed_switch: float = 0.0, mixed_accept: float = 0.0, tree_degree: int = 0,
                  tree_theta: float = 0.0, tree_min_sources: int = 0, tree_ff_degree: int = 0,
                  tree_ff_theta: float = 0.0, tree_ff_min_sources: int = 0, tree_grid: int = 0,
-                 tree_ff_cluster: int = 0, tree_cluster: int = 0, ff_block: int = 0, mixed_block: int = 0):
+                 tree_ff_cluster: int = 0, tree_cluster: int = 0, ff_block: int = 0, mixed_block: int = 0,
+                 newton_tree_degree: int = 0, newton_tree_theta: float = 0.0):
         """Zero selects a default.  tree_*: the treecode far field of the mixed
         path (Chebyshev degree, opening parameter, and the source count from
         which a mesh uses it; tree_min_sources=-1 turns it off); tree_ff_*: the
@@ -278,12 +280,14 @@ class Context:
         the same for the mixed treecode (0 or -1: off, the default).  ff_block:
         targets per CTA of the float-float kernel (64, the default, or 128).
         mixed_block: targets per CTA of the mixed kernel (64, 128 or 256; 0:
-        the autotuner's choice, else 64)."""
+        the autotuner's choice, else 64).  newton_tree_degree/theta: the
+        coarser mixed treecode of a chart solve's mixed Newton sweeps (0: 5
+        and 0.5; degree -1: the mesh's mixed treecode)."""
         self._L = load()
         opt = _Options(cutoff_fp64, cutoff_mixed, mixed_switch, mixed_accept, int(tree_degree),
                        float(tree_theta), int(tree_min_sources), int(tree_ff_degree), float(tree_ff_theta),
                        int(tree_ff_min_sources), int(tree_grid), int(tree_ff_cluster), int(tree_cluster), int(ff_block),
-                       int(mixed_block), 0)
+                       int(mixed_block), int(newton_tree_degree), float(newton_tree_theta), 0)
         h = ctypes.c_void_p()
         rc = self._L.lsm_create(ctypes.byref(h), int(device), ctypes.byref(opt))
         if rc != 0:

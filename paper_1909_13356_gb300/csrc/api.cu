@@ -389,6 +389,8 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.tree_ff_cluster = 4096;
     ctx->opt.tree_cluster = 0;   // off: at 10^6 targets it saves 2% of a mixed evaluation
     ctx->opt.ff_block = 64;
+    ctx->opt.newton_tree_degree = 5;
+    ctx->opt.newton_tree_theta = 0.5f;
     if (opt) {
         if (opt->tree_degree < 0 || opt->tree_degree > 12 || opt->tree_theta < 0.0f ||
             opt->tree_theta >= 1.0f || opt->tree_min_sources < -1 || opt->tree_ff_degree < 0 ||
@@ -398,7 +400,9 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
             opt->tree_cluster < -1 || opt->tree_cluster > (1 << 20) ||
             (opt->tree_cluster > 0 && opt->tree_cluster % (2 * kEvalThreads)) ||
             (opt->ff_block != 0 && opt->ff_block != 64 && opt->ff_block != 128) ||
-            (opt->mixed_block != 0 && opt->mixed_block != 64 && opt->mixed_block != 128 && opt->mixed_block != 256)) {
+            (opt->mixed_block != 0 && opt->mixed_block != 64 && opt->mixed_block != 128 && opt->mixed_block != 256) ||
+            opt->newton_tree_degree < -1 || opt->newton_tree_degree > 12 || opt->newton_tree_theta < 0.0f ||
+            opt->newton_tree_theta >= 1.0f) {
             delete c;
             return LSM_E_INVALID_ARG;
         }
@@ -417,6 +421,8 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
         if (opt->tree_cluster != 0) ctx->opt.tree_cluster = opt->tree_cluster > 0 ? opt->tree_cluster : 0;
         if (opt->ff_block != 0) ctx->opt.ff_block = opt->ff_block;
         ctx->opt.mixed_block = opt->mixed_block;
+        if (opt->newton_tree_degree != 0) ctx->opt.newton_tree_degree = opt->newton_tree_degree;
+        if (opt->newton_tree_theta > 0.0f) ctx->opt.newton_tree_theta = opt->newton_tree_theta;
     }
     DeviceGuard g(device);
     int rc = LSM_OK;
@@ -709,6 +715,8 @@ int lsm_mesh_free(lsm_mesh* mh)
     me->tree = nullptr;
     tree_free(me->tree_ff);
     me->tree_ff = nullptr;
+    tree_free(me->tree_newton);
+    me->tree_newton = nullptr;
     for (void* p : {(void*)me->cent, (void*)me->cent_lo, (void*)me->cent_hi})
         if (p) cudaFree(p);
     void* ps[] = {me->verts, me->tris, me->tris6, me->tri_sigma, me->tri_n, me->vpn, me->s64_pos, me->s64_nw,

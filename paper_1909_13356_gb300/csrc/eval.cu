@@ -1859,6 +1859,8 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
                 const FFIncremental* inc)
 {
     if (t.n <= 0) return LSM_OK;
+    const bool newton = precision == kPrecMixedNewton;
+    if (newton) precision = LSM_MIXED;
     const bool mixed = precision == LSM_MIXED;
     const bool ff = precision == LSM_FF;
     // targets per CTA: the mixed kernel's tuned layout (64, 128 or 256); the
@@ -1894,16 +1896,19 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     ClusterPlan cp;
     const int tpc = (ff ? ctx->opt.tree_ff_cluster : ctx->opt.tree_cluster) / tpb * tpb;
     const bool clusters = use_tree && (ff || mixed) && tpc > 0 && t.n >= 2 * tpc;
+    // the mixed Newton sweeps' coarser treecode
+    const bool ntree = use_tree && newton && newton_tree_wanted(ctx, me);
+    const Tree* TT = nullptr;
     if (use_tree) {
-        int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff);
+        int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff, ntree);
         if (rc != LSM_OK) return rc;
+        TT = ff ? me->tree_ff : (ntree ? me->tree_newton : me->tree);
         if (clusters) {
-            rc = cluster_setup(ctx, ff ? me->tree_ff : me->tree, t, tpc, tpb, ff ? ctx->opt.cutoff_fp64 : mixed_cut(ctx, me),
-                               tsig, s, &cp, st);
+            rc = cluster_setup(ctx, TT, t, tpc, tpb, ff ? ctx->opt.cutoff_fp64 : mixed_cut(ctx, me), tsig, s, &cp, st);
             if (rc != LSM_OK) return rc;
         }
         int64_t total = 0;
-        rc = tree_lists(ctx, ff ? me->tree_ff : me->tree, t, tpb, tsig, s, &list, &blist, &border, &total, st,
+        rc = tree_lists(ctx, TT, t, tpb, tsig, s, &list, &blist, &border, &total, st,
                         mixed ? mixed_cut(ctx, me) : 0.0, clusters ? &cp : nullptr);
         if (rc != LSM_OK) return rc;
         const int64_t avg = total / nblk;
@@ -1946,7 +1951,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
         A.bb_io = inc->bb_io;
     }
     if (use_tree) {
-        const Tree* T = ff ? me->tree_ff : me->tree;
+        const Tree* T = TT;
         A.tlo = T->tile_lo;
         A.thi = T->tile_hi;
         A.tchi = T->tile_chi;

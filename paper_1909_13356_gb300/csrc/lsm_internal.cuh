@@ -140,6 +140,7 @@ struct Mesh {
     Ctx* ctx = nullptr;
     Tree* tree = nullptr;        // treecode far field of the mixed path, built on first use
     Tree* tree_ff = nullptr;     // and of the float-float path
+    Tree* tree_newton = nullptr; // the coarser mixed treecode of the mixed Newton sweeps
     // target-dependent sigma (eq. sigma2): centroids in Morton order (x, y, z,
     // sigma_j), in tiles of kTile with outward-rounded boxes
     bool sigx = false;
@@ -353,6 +354,10 @@ int eval_init_constants(Ctx* ctx);
 // bb_io [grid blocks][8]: mode 1 stores each block's box (and its largest
 // sigma in sigma(x) mode), mode 2 reuses it, so both calls split near and far
 // tiles identically however little the targets moved.
+// Internal precision code for eval_sorted: the mixed path as the mixed Newton
+// sweeps of a chart solve that finishes with float-float steps take it (their
+// own coarser treecode where newton_tree_wanted)
+constexpr int kPrecMixedNewton = 16;
 struct FFIncremental {
     int mode;
     double* far_io;
@@ -402,7 +407,12 @@ struct Tree {
     size_t bytes = 0;
 };
 bool tree_wanted(const Ctx* ctx, const Mesh* me, bool ff);
-int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff);
+// newton: the mixed Newton sweeps' own treecode (options newton_tree_*)
+int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff, bool newton = false);
+// True when the mixed Newton sweeps take their own treecode: on, and coarser
+// than the mesh's mixed treecode (lower degree or larger opening parameter,
+// neither finer)
+bool newton_tree_wanted(const Ctx* ctx, const Mesh* me);
 void tree_free(Tree* t);
 // Interaction lists of sorted targets in blocks of tpb: for block b, the
 // tile ids list[blist[b].x .. + blist[b].y) in tree order; order = the

@@ -373,7 +373,9 @@ int solve_charts_device(Ctx* ctx, Mesh* me, int n_gl, double tol, int max_iter, 
                 nrec = nl;
                 ff_stage = 1;
             } else {
-                rc = eval_sorted(ctx, me, tg, R, m == 0 ? LSM_MIXED : LSM_FP64, st);
+                // mixed sweeps that float-float steps finish take the coarser Newton treecode
+                rc = eval_sorted(ctx, me, tg, R, m == 0 ? (accept_mixed ? LSM_MIXED : kPrecMixedNewton) : LSM_FP64,
+                                 st);
                 if (rc) return rc;
             }
             k_newton_update<<<nb(nl), 256, 0, st>>>(L, nl, R, S, m == 0 ? 1 : 0, accept_mixed, tol,

@@ -1136,13 +1136,29 @@ void tree_free(Tree* t)
     delete t;
 }
 
-int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff)
+bool newton_tree_wanted(const Ctx* ctx, const Mesh* me)
+{
+    if (ctx->opt.newton_tree_degree <= 0) return false;
+    const bool tuned = me->tune_mode == 1;
+    const int d = tuned ? me->tune_degree : ctx->opt.tree_degree;
+    const float th = tuned ? me->tune_theta : ctx->opt.tree_theta;
+    const int nd = ctx->opt.newton_tree_degree;
+    const float nth = ctx->opt.newton_tree_theta;
+    return nd <= d && nth >= th && (nd < d || nth > th);
+}
+
+int tree_ensure(Ctx* ctx, Mesh* me, cudaStream_t st, bool ff, bool newton)
 {
     const bool tuned = !ff && me->tune_mode == 1;
-    const int degree = ff ? ctx->opt.tree_ff_degree : (tuned ? me->tune_degree : ctx->opt.tree_degree);
-    const float theta = ff ? ctx->opt.tree_ff_theta : (tuned ? me->tune_theta : ctx->opt.tree_theta);
+    int degree = ff ? ctx->opt.tree_ff_degree : (tuned ? me->tune_degree : ctx->opt.tree_degree);
+    float theta = ff ? ctx->opt.tree_ff_theta : (tuned ? me->tune_theta : ctx->opt.tree_theta);
+    newton = newton && !ff;
+    if (newton) {
+        degree = ctx->opt.newton_tree_degree;
+        theta = ctx->opt.newton_tree_theta;
+    }
     const int grid = ctx->opt.tree_grid;
-    Tree*& slot = ff ? me->tree_ff : me->tree;
+    Tree*& slot = ff ? me->tree_ff : (newton ? me->tree_newton : me->tree);
     if (slot && slot->degree == degree && slot->theta == theta && slot->grid == grid) return LSM_OK;
     if (!ff && degree > kMaxDeg32) {
         ctx->err = "tree: the mixed path's degree is at most 12";

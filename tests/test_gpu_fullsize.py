@@ -129,6 +129,33 @@ def test_torus_full_chart_solve_sampled(lsm, oracle_mod, torus):
     assert np.abs(po - 0.5).max() < 1e-12
 
 
+def test_torus_newton_tree(lsm, oracle_mod, torus):
+    """The mixed Newton sweeps' own coarser treecode (degree 5, theta 0.5, the
+    default) against the same solve on the mesh's mixed treecode
+    (newton_tree_degree=-1): no failed node, the same nodes to 1e-11, fewer
+    mixed far pairs, and the oracle's |Phi - 1/2| below 1e-12 at 2,000
+    sampled nodes of the default solve."""
+    w, ctx, mesh, (y, nw, sg) = torus
+    m = w["mesh"]
+    ctx_p = lsm.Context(0, newton_tree_degree=-1)
+    mesh_p = ctx_p.upload(m.verts, m.tris, m.sigma, n_gl=6)
+    out = {}
+    for name, c, me in (("newton_tree", ctx, mesh), ("mesh_tree", ctx_p, mesh_p)):
+        me.solve_charts(order=4, tol=1e-12, precision=lsm.MIXED, device_out=True)   # builds the trees
+        c.read_stats(reset=True)
+        x, h, st, stats = me.solve_charts(order=8, tol=1e-12, precision=lsm.MIXED, device_out=True)
+        out[name] = (x, stats, c.read_stats(reset=True)["kind_pairs_far"][0])
+    (xn, sn, fn), (xp, sp, fp) = out["newton_tree"], out["mesh_tree"]
+    assert sn.n_failed == 0 and sp.n_failed == 0
+    assert (xn - xp).abs().max().item() < 1e-11
+    assert fn < 0.9 * fp, (fn, fp)
+    sel = np.random.default_rng(62).choice(sn.n_nodes, 2000, replace=False)
+    po, _ = oracle_mod.phi_grad(y, nw, sg, xn.cpu().numpy()[sel])
+    assert np.abs(po - 0.5).max() < 1e-12
+    mesh_p.free()
+    ctx_p.close()
+
+
 def test_icosphere_full_evaluation_sampled(lsm, oracle_mod):
     """The 2.1e7-node bumped icosphere, mixed path with its treecode at 1e5
     targets, against: the float-float path at all 1e5 targets, the FP64
