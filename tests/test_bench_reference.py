@@ -52,7 +52,7 @@ def test_dram_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
     h = hashlib.sha256()
-    for name in ("eval.cu", "tree.cu"):
+    for name in ("eval.cu", "tree.cu", "ff.cuh"):
         with open(os.path.join(ROOT, "paper_1909_13356_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     sha = h.hexdigest()
