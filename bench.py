@@ -70,6 +70,8 @@ def parse():
                     help="treecode degree of the mixed Newton sweeps (0: library default 5; -1: the mesh's own)")
     ap.add_argument("--newton-tree-theta", type=float, default=0.0,
                     help="opening parameter of the mixed Newton sweeps' treecode (0: library default 0.5)")
+    ap.add_argument("--newton-cutoff", type=float, default=0.0,
+                    help="near-field radius in sigma of the mixed Newton sweeps (0: library default 5.0)")
     ap.add_argument("--tree-grid", type=int, default=0,
                     help="proxy grids: 1 per-axis point counts (default), 2 full (degree + 1)^3")
     ap.add_argument("--sigma-x", action="store_true",
@@ -711,7 +713,8 @@ def main():
     m = w["mesh"]
     ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid,
                       ff_block=args.ff_block, mixed_block=args.mixed_block,
-                      newton_tree_degree=args.newton_tree_degree, newton_tree_theta=args.newton_tree_theta)
+                      newton_tree_degree=args.newton_tree_degree, newton_tree_theta=args.newton_tree_theta,
+                      newton_cutoff=args.newton_cutoff)
     # the pipes' measured throughput (roofline denominators), clocks sampled around the probe
     pclk = ClockSampler(local)
     pclk.start()
@@ -969,6 +972,7 @@ def main():
                        "newton_mixed_tree": ("the mesh's mixed treecode" if args.newton_tree_degree < 0 else
                                              {"degree": args.newton_tree_degree or 5,
                                               "theta": args.newton_tree_theta or 0.5}),
+                       "newton_mixed_cutoff_sigma": args.newton_cutoff or 5.0,
                        "sigma": ("sigma(x), eq. sigma2: lambda 2.5, sigma0 = max D / sqrt(2 ln 2) = "
                                  f"{mesh.sigma0:.5g}" if args.sigma_x else "per triangle, 0.5 sqrt(2 area)"),
                        "parallelism": (f"{world} ranks, targets and chart nodes in Morton ranges, mesh replicated"

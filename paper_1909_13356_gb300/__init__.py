@@ -67,7 +67,7 @@ class _Options(ctypes.Structure):
                 ("tree_grid", ctypes.c_int32), ("tree_ff_cluster", ctypes.c_int32), ("tree_cluster", ctypes.c_int32),
                 ("ff_block", ctypes.c_int32), ("mixed_block", ctypes.c_int32),
                 ("newton_tree_degree", ctypes.c_int32), ("newton_tree_theta", ctypes.c_float),
-                ("reserved", ctypes.c_int32)]
+                ("newton_cutoff", ctypes.c_float)]
 
 
 class _Stats(ctypes.Structure):
@@ -269,7 +269,7 @@ class Context:
                  tree_theta: float = 0.0, tree_min_sources: int = 0, tree_ff_degree: int = 0,
                  tree_ff_theta: float = 0.0, tree_ff_min_sources: int = 0, tree_grid: int = 0,
                  tree_ff_cluster: int = 0, tree_cluster: int = 0, ff_block: int = 0, mixed_block: int = 0,
-                 newton_tree_degree: int = 0, newton_tree_theta: float = 0.0):
+                 newton_tree_degree: int = 0, newton_tree_theta: float = 0.0, newton_cutoff: float = 0.0):
         """Zero selects a default.  tree_*: the treecode far field of the mixed
         path (Chebyshev degree, opening parameter, and the source count from
         which a mesh uses it; tree_min_sources=-1 turns it off); tree_ff_*: the
@@ -282,12 +282,13 @@ class Context:
         mixed_block: targets per CTA of the mixed kernel (64, 128 or 256; 0:
         the autotuner's choice, else 64).  newton_tree_degree/theta: the
         coarser mixed treecode of a chart solve's mixed Newton sweeps (0: 5
-        and 0.5; degree -1: the mesh's mixed treecode)."""
+        and 0.5; degree -1: the mesh's mixed treecode); newton_cutoff: their
+        near-field radius in sigma (0: 5.0)."""
         self._L = load()
         opt = _Options(cutoff_fp64, cutoff_mixed, mixed_switch, mixed_accept, int(tree_degree),
                        float(tree_theta), int(tree_min_sources), int(tree_ff_degree), float(tree_ff_theta),
                        int(tree_ff_min_sources), int(tree_grid), int(tree_ff_cluster), int(tree_cluster), int(ff_block),
-                       int(mixed_block), int(newton_tree_degree), float(newton_tree_theta), 0)
+                       int(mixed_block), int(newton_tree_degree), float(newton_tree_theta), float(newton_cutoff))
         h = ctypes.c_void_p()
         rc = self._L.lsm_create(ctypes.byref(h), int(device), ctypes.byref(opt))
         if rc != 0:

@@ -391,6 +391,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
     ctx->opt.ff_block = 64;
     ctx->opt.newton_tree_degree = 5;
     ctx->opt.newton_tree_theta = 0.5f;
+    ctx->opt.newton_cutoff = 5.0f;
     if (opt) {
         if (opt->tree_degree < 0 || opt->tree_degree > 12 || opt->tree_theta < 0.0f ||
             opt->tree_theta >= 1.0f || opt->tree_min_sources < -1 || opt->tree_ff_degree < 0 ||
@@ -402,7 +403,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
             (opt->ff_block != 0 && opt->ff_block != 64 && opt->ff_block != 128) ||
             (opt->mixed_block != 0 && opt->mixed_block != 64 && opt->mixed_block != 128 && opt->mixed_block != 256) ||
             opt->newton_tree_degree < -1 || opt->newton_tree_degree > 12 || opt->newton_tree_theta < 0.0f ||
-            opt->newton_tree_theta >= 1.0f) {
+            opt->newton_tree_theta >= 1.0f || opt->newton_cutoff < 0.0f || opt->newton_cutoff > 16.0f) {
             delete c;
             return LSM_E_INVALID_ARG;
         }
@@ -423,6 +424,7 @@ int lsm_create(lsm_ctx** out, int device, const lsm_options* opt)
         ctx->opt.mixed_block = opt->mixed_block;
         if (opt->newton_tree_degree != 0) ctx->opt.newton_tree_degree = opt->newton_tree_degree;
         if (opt->newton_tree_theta > 0.0f) ctx->opt.newton_tree_theta = opt->newton_tree_theta;
+        if (opt->newton_cutoff > 0.0f) ctx->opt.newton_cutoff = opt->newton_cutoff;
     }
     DeviceGuard g(device);
     int rc = LSM_OK;

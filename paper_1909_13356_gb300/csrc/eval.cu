@@ -1896,20 +1896,21 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     ClusterPlan cp;
     const int tpc = (ff ? ctx->opt.tree_ff_cluster : ctx->opt.tree_cluster) / tpb * tpb;
     const bool clusters = use_tree && (ff || mixed) && tpc > 0 && t.n >= 2 * tpc;
-    // the mixed Newton sweeps' coarser treecode
+    // the mixed Newton sweeps' coarser treecode and near-field radius
     const bool ntree = use_tree && newton && newton_tree_wanted(ctx, me);
+    const double mcut = newton ? std::min(mixed_cut(ctx, me), (double)ctx->opt.newton_cutoff) : mixed_cut(ctx, me);
     const Tree* TT = nullptr;
     if (use_tree) {
         int rc = tree_ensure(ctx, const_cast<Mesh*>(me), st, ff, ntree);
         if (rc != LSM_OK) return rc;
         TT = ff ? me->tree_ff : (ntree ? me->tree_newton : me->tree);
         if (clusters) {
-            rc = cluster_setup(ctx, TT, t, tpc, tpb, ff ? ctx->opt.cutoff_fp64 : mixed_cut(ctx, me), tsig, s, &cp, st);
+            rc = cluster_setup(ctx, TT, t, tpc, tpb, ff ? ctx->opt.cutoff_fp64 : mcut, tsig, s, &cp, st);
             if (rc != LSM_OK) return rc;
         }
         int64_t total = 0;
         rc = tree_lists(ctx, TT, t, tpb, tsig, s, &list, &blist, &border, &total, st,
-                        mixed ? mixed_cut(ctx, me) : 0.0, clusters ? &cp : nullptr);
+                        mixed ? mcut : 0.0, clusters ? &cp : nullptr);
         if (rc != LSM_OK) return rc;
         const int64_t avg = total / nblk;
         nsplit = 1;
@@ -1932,7 +1933,7 @@ int eval_sorted(Ctx* ctx, const Mesh* me, const Targets& t, double* res, int pre
     A.tx = t.x;
     A.ld = t.ld;
     A.nt = t.n;
-    const double cut = mixed ? mixed_cut(ctx, me) : ctx->opt.cutoff_fp64;
+    const double cut = mixed ? mcut : ctx->opt.cutoff_fp64;
     A.cut2 = (float)(cut * cut);
     A.out = part;
     A.flag = flag_word(ctx);

@@ -523,8 +523,12 @@ int batch_sweep(Ctx* ctx, const BatchSweep& B, const int32_t* act, const int* n_
         Targets tg{B.T, B.N, B.N};
         FFIncremental inc{verify ? 2 : 1, B.Rfar, verify ? B.Trec : nullptr, B.BBrec};
         const bool ffpair = B.mixed && m == 1;
+        // mixed sweeps that float-float steps finish take the Newton near-field radius
+        const double cut = prec == LSM_MIXED && !B.accept_mixed
+                               ? std::min(B.cut > 0.0 ? B.cut : ctx->opt.cutoff_mixed, (double)ctx->opt.newton_cutoff)
+                               : B.cut;
         rc = eval_items(ctx, B.view, tg, B.items, B.n_items, prec == LSM_MIXED ? B.max_items_mixed : B.max_items_other,
-                        B.R, prec, st, ffpair ? &inc : nullptr, B.tpb, B.cut);
+                        B.R, prec, st, ffpair ? &inc : nullptr, B.tpb, cut);
         if (rc) return rc;
         if (ffpair && !verify) {
             k_copy_record<<<nb(B.N), 256, 0, st>>>(L, nL, B.Lrec, B.n_rec, B.T, B.Trec, B.N);

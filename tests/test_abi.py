@@ -103,7 +103,8 @@ def test_out_of_range_options_are_rejected_before_any_device_call():
     L = lsm.load()
     for field, value in (("tree_grid", 3), ("tree_grid", -1), ("tree_degree", 13), ("tree_theta", 1.0),
                          ("tree_ff_degree", 17), ("tree_min_sources", -2), ("ff_block", 96),
-                         ("mixed_block", 32)):
+                         ("mixed_block", 32), ("newton_tree_degree", 13), ("newton_tree_degree", -2),
+                         ("newton_tree_theta", 1.0), ("newton_cutoff", -1.0), ("newton_cutoff", 17.0)):
         opt = lsm._Options()
         setattr(opt, field, value)
         h = ctypes.c_void_p()
