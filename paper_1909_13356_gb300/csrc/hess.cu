@@ -14,7 +14,9 @@
 // Near the level set the Hessian's curvature part is a small fraction of
 // its terms, which cancel: near tiles are summed in FP64.  Far tiles (the
 // Laplace double layer, no cancellation of note) are summed in FP32 on
-// tile-local coordinates with compensated accumulation.  A CTA owns 128
+// tile-local coordinates with compensated accumulation, and so are the
+// sources of a near tile that lie beyond the cutoff from the CTA's whole
+// target box (Sec. 4.4, eq. kerdecomp: the split by distance, per source).  A CTA owns 128
 // sorted targets and walks a range of tiles (a grid row per split, partials
 // reduced in a fixed order): all tiles, or on a large mesh the interaction
 // list of the mixed path's treecode built for this kernel's near radius
@@ -102,6 +104,7 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
     __shared__ double s_tab[kH64N * 8];
     __shared__ float part[6][kHessThreads / 32];
     __shared__ float bb[6];
+    __shared__ unsigned char s_far[kTile];   // near tile: the source is beyond the cutoff from the whole block
     const int tid = threadIdx.x;
     int blk = blockIdx.x, t0, t1;
     if (A.list) {
@@ -168,55 +171,72 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
         const float gz = fmaxf(0.0f, fmaxf(tl.z - bb[5], bb[2] - th.z));
         const bool far = proxy || gx * gx + gy * gy + gz * gz > A.cut2 * tl.w * tl.w * 1.0001f;
         const int cnt = (int)th.w;
-        if (valid) {
-            if (far)
-                pf += cnt;
-            else
-                pn += cnt;
-        }
         const int64_t j = (int64_t)(proxy ? t - A.ntiles : t) * kTile + tid;
+        bool src_far = false;
         if (tid < cnt) {
             if (proxy) {
                 sp[tid] = A.ppos[j];
                 sn[tid] = A.pnw[j];
-            } else if (far) {
+            } else {
                 sp[tid] = A.s32_pos[j];
                 sn[tid] = A.s32_nw[j];
-            } else {
-                dp[tid] = A.s64_pos[j];
-                dn[tid] = A.s64_nw[j];
+            }
+            if (!far) {
+                // near tile: a source beyond the cutoff from every point of the
+                // block's box (its own sigma, FP64 distance to the outward
+                // box) takes the FP32 Laplace pair of the far tiles
+                const double4_32a y = A.s64_pos[j], n = A.s64_nw[j];
+                dp[tid] = y;
+                dn[tid] = n;
+                const double gx = fmax(0.0, fmax((double)bb[0] - y.x, y.x - (double)bb[3]));
+                const double gy = fmax(0.0, fmax((double)bb[1] - y.y, y.y - (double)bb[4]));
+                const double gz = fmax(0.0, fmax((double)bb[2] - y.z, y.z - (double)bb[5]));
+                src_far = gx * gx + gy * gy + gz * gz > (double)A.cut2 * 0.5 * n.w * n.w * (1.0 + 1e-9);
+                s_far[tid] = src_far ? 1 : 0;
             }
         }
-        __syncthreads();
+        const int nfar = far ? cnt : __syncthreads_count(src_far);
+        if (far) __syncthreads();
+        if (valid) {
+            pf += nfar;
+            pn += cnt - nfar;
+        }
+        // the FP32 Laplace pair on tile-local coordinates (far tiles, and far
+        // sources of a near tile), r = y - x
+        auto far_pair = [&](const float4& y, const float4& n, float qx, float qy, float qz, float (&p)[6]) {
+            const float r0 = y.x - qx, r1 = y.y - qy, r2c = y.z - qz;
+            const float r2 = fmaf(r0, r0, fmaf(r1, r1, r2c * r2c));
+            float ri = rsqrtf(r2);
+            ri = ri * fmaf(-0.5f * r2 * ri, ri, 1.5f);   // one Newton step for 1/sqrt
+            const float ri2 = ri * ri;
+            const float ri5 = ri2 * ri2 * ri;
+            const float q = fmaf(n.x, r0, fmaf(n.y, r1, n.z * r2c));
+            const float F = -3.0f * ri5;
+            const float qG = 15.0f * q * ri5 * ri2;
+            p[0] += F * (2.0f * n.x * r0 + q) + qG * r0 * r0;
+            p[1] += F * (n.x * r1 + n.y * r0) + qG * r0 * r1;
+            p[2] += F * (n.x * r2c + n.z * r0) + qG * r0 * r2c;
+            p[3] += F * (2.0f * n.y * r1 + q) + qG * r1 * r1;
+            p[4] += F * (n.y * r2c + n.z * r1) + qG * r1 * r2c;
+            p[5] += F * (2.0f * n.z * r2c + q) + qG * r2c * r2c;
+        };
+        // target in tile-local coordinates
+        const float4 ch = A.tchi[t], cl = A.tclo[t];
+        const float qx = (xh[0] - ch.x) + (xl[0] - cl.x);
+        const float qy = (xh[1] - ch.y) + (xl[1] - cl.y);
+        const float qz = (xh[2] - ch.z) + (xl[2] - cl.z);
         if (far) {
-            const float4 ch = A.tchi[t], cl = A.tclo[t];
-            // target in tile-local coordinates; r = y - x
-            const float qx = (xh[0] - ch.x) + (xl[0] - cl.x);
-            const float qy = (xh[1] - ch.y) + (xl[1] - cl.y);
-            const float qz = (xh[2] - ch.z) + (xl[2] - cl.z);
             float p[6] = {0, 0, 0, 0, 0, 0};
-            for (int s = 0; s < cnt; s++) {
-                const float4 y = sp[s], n = sn[s];
-                const float r0 = y.x - qx, r1 = y.y - qy, r2c = y.z - qz;
-                const float r2 = fmaf(r0, r0, fmaf(r1, r1, r2c * r2c));
-                float ri = rsqrtf(r2);
-                ri = ri * fmaf(-0.5f * r2 * ri, ri, 1.5f);   // one Newton step for 1/sqrt
-                const float ri2 = ri * ri;
-                const float ri5 = ri2 * ri2 * ri;
-                const float q = fmaf(n.x, r0, fmaf(n.y, r1, n.z * r2c));
-                const float F = -3.0f * ri5;
-                const float qG = 15.0f * q * ri5 * ri2;
-                p[0] += F * (2.0f * n.x * r0 + q) + qG * r0 * r0;
-                p[1] += F * (n.x * r1 + n.y * r0) + qG * r0 * r1;
-                p[2] += F * (n.x * r2c + n.z * r0) + qG * r0 * r2c;
-                p[3] += F * (2.0f * n.y * r1 + q) + qG * r1 * r1;
-                p[4] += F * (n.y * r2c + n.z * r1) + qG * r1 * r2c;
-                p[5] += F * (2.0f * n.z * r2c + q) + qG * r2c * r2c;
-            }
+            for (int s = 0; s < cnt; s++) far_pair(sp[s], sn[s], qx, qy, qz, p);
             for (int c = 0; c < 6; c++) tsum(fh[c], fl[c], p[c]);
         } else {
             double p[6] = {0, 0, 0, 0, 0, 0};
+            float pf32[6] = {0, 0, 0, 0, 0, 0};
             for (int s = 0; s < cnt; s++) {
+                if (s_far[s]) {   // uniform over the CTA
+                    far_pair(sp[s], sn[s], qx, qy, qz, pf32);
+                    continue;
+                }
                 const double4_32a y = dp[s], n = dn[s];
                 const double r0 = y.x - x[0], r1 = y.y - x[1], r2c = y.z - x[2];
                 const double r2 = fma(r0, r0, fma(r1, r1, r2c * r2c));
@@ -231,7 +251,10 @@ __global__ void __launch_bounds__(kHessThreads) k_eval_hess(HessArgs A)
                 p[4] += F * (n.y * r2c + n.z * r1) + qG * r1 * r2c;
                 p[5] += F * (2.0 * n.z * r2c + q) + qG * r2c * r2c;
             }
-            for (int c = 0; c < 6; c++) nh[c] += p[c];
+            for (int c = 0; c < 6; c++) {
+                nh[c] += p[c];
+                tsum(fh[c], fl[c], pf32[c]);
+            }
         }
         __syncthreads();
     }
