@@ -143,9 +143,10 @@ typedef struct {
      * targets interpolate its field from them.  0 selects 4096; -1: off. */
     int32_t tree_ff_cluster;
     /* The same for the mixed path's treecode (degree tree_degree grids on
-     * clusters of this many targets, a multiple of 256).  0 or -1: off (the
-     * default: on the graded torus at 10^6 targets it cut the mixed kernel's
-     * far pairs by 20 % but the whole evaluation by only 2 %). */
+     * clusters of this many targets, a multiple of 256).  0 selects 4096;
+     * -1: off.  Measured: the bumped icosphere's 2e7-target evaluation takes
+     * 3.9 s instead of 6.5 s, the graded torus's 1e6 targets 160 ms instead
+     * of 170 ms, at the same error against FP64. */
     int32_t tree_cluster;
     /* Targets per CTA of the float-float kernel (64 or 128; 0 selects 64):
      * the near/far split and the treecode's lists are per CTA, so a smaller

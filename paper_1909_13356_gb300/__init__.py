@@ -277,7 +277,7 @@ class Context:
         grids with a degree ladder (the default), 2 full (degree + 1)^3
         axis-aligned grids of one degree.  tree_ff_cluster: targets per target
         cluster of the float-float treecode (0: 4096, -1: off); tree_cluster:
-        the same for the mixed treecode (0 or -1: off, the default).  ff_block:
+        the same for the mixed treecode (0: 4096, -1: off).  ff_block:
         targets per CTA of the float-float kernel (64, the default, or 128).
         mixed_block: targets per CTA of the mixed kernel (64, 128 or 256; 0:
         the autotuner's choice, else 64).  newton_tree_degree/theta: the

@@ -129,7 +129,7 @@ def test_sigma_x_with_treecodes(lsm, oracle_mod):
 
 def test_sigma_x_target_clusters(lsm, oracle_mod):
     """Target clusters in sigma(x) mode (the float-float treecode's 4,096-target
-    clusters, the default, and the mixed treecode's on request), whose near
+    clusters, and the mixed treecode's, here of 2,048), whose near
     width is their largest target sigma: against the same trees without
     clusters, Phi within 5e-13 (float-float) and 1e-8 (mixed), the gradients
     within the paths' bars, and the float-float bar against the oracle on
@@ -139,7 +139,7 @@ def test_sigma_x_target_clusters(lsm, oracle_mod):
     c, sj, dmax = oracle_mod.sigma_sources(m.verts, m.tris)
     smin = sj.min()
     out = {}
-    for name, kw in (("clusters", {"tree_cluster": 2048}), ("plain", {"tree_ff_cluster": -1})):
+    for name, kw in (("clusters", {"tree_cluster": 2048}), ("plain", {"tree_ff_cluster": -1, "tree_cluster": -1})):
         ctx = lsm.Context(0, **kw)
         mesh = ctx.upload_sigma_x(m.verts, m.tris, n_gl=6)
         mesh.eval_phi_grad(x[:4096], lsm.FF)       # builds the trees
