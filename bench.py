@@ -70,6 +70,8 @@ def parse():
                     help="treecode degree of the mixed Newton sweeps (0: library default 5; -1: the mesh's own)")
     ap.add_argument("--newton-tree-theta", type=float, default=0.0,
                     help="opening parameter of the mixed Newton sweeps' treecode (0: library default 0.5)")
+    ap.add_argument("--tree-cluster", type=int, default=0,
+                    help="targets per target cluster of the mixed treecode (0: library default 4096; -1: off)")
     ap.add_argument("--newton-cutoff", type=float, default=0.0,
                     help="near-field radius in sigma of the mixed Newton sweeps (0: library default 5.0)")
     ap.add_argument("--tree-grid", type=int, default=0,
@@ -420,7 +422,7 @@ def bench_icosphere(args):
     w = synth.icosphere_c3(n_targets=n)
     m = w["mesh"]
     ctx = lsm.Context(0, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid,
-                      ff_block=args.ff_block)
+                      ff_block=args.ff_block, tree_cluster=args.tree_cluster)
     t0 = time.perf_counter()
     mesh = ctx.upload(m.verts, m.tris, m.sigma, n_gl=4)
     torch.cuda.synchronize()
@@ -714,7 +716,7 @@ def main():
     ctx = lsm.Context(local, tree_degree=args.tree_degree, tree_theta=args.tree_theta, tree_grid=args.tree_grid,
                       ff_block=args.ff_block, mixed_block=args.mixed_block,
                       newton_tree_degree=args.newton_tree_degree, newton_tree_theta=args.newton_tree_theta,
-                      newton_cutoff=args.newton_cutoff)
+                      newton_cutoff=args.newton_cutoff, tree_cluster=args.tree_cluster)
     # the pipes' measured throughput (roofline denominators), clocks sampled around the probe
     pclk = ClockSampler(local)
     pclk.start()
